@@ -1,0 +1,130 @@
+"""Per-event leading-order integrand (oracle).
+
+Fig. 1 of the paper: the integrand is the parton luminosity L(x1, x2) times
+the partonic cross section built from the matrix element and the RAMBO phase
+space.  For a point x in the unit hypercube (no Vegas Jacobian here; Vegas
+multiplies its own):
+
+  hadronic:   (x1, x2, tau, J_x) = xmap(x_0, x_1, tau_min),  s-hat = tau S,
+              tau_min = (sum of final masses)^2 / S
+  lepton:     s-hat = S, J_x = 1, no densities
+  momenta:    flat massless phase space from the remaining 3n-4 numbers,
+              rescaled to the final-state masses (weight W)
+  cuts:       every final gluon pT > pT_min, every final gluon pair
+              Delta R = sqrt(Delta y^2 + Delta phi^2) > Delta R_min
+              (Delta phi in (-pi, pi]); failing points get f = 0
+  f(x)   =    J_x W f_1(x1, mu_F^2) f_2(x2, mu_F^2) |M|^2-bar / (2 s-hat)
+              x 0.3893793721e9 pb GeV^2
+
+Incoming partons are p_a = sqrt(s-hat)/2 (1,0,0,1), p_b = sqrt(s-hat)/2
+(1,0,0,-1); outgoing momenta are those of the phase-space generator, in the
+partonic centre-of-mass frame (the cuts are longitudinally boost invariant).
+|M|^2-bar is averaged over initial spins and colours and carries 1/k! for k
+identical final particles.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+import workloads as W
+from . import phasespace as ps
+from .feynman import Process, PARTICLES
+from .pdf import PdfTable
+
+MASSES_OF = {"t": "m_top"}
+
+
+def oracle_process(wl: W.Workload, m_top=None, alpha_s=None) -> Process:
+    mt = wl.m_top if m_top is None else m_top
+    a_s = wl.alpha_s if alpha_s is None else alpha_s
+    legs = [(l.particle, l.incoming) for l in wl.legs]
+    return Process(legs, {"t": mt}, g_s=math.sqrt(4 * math.pi * a_s),
+                   e=math.sqrt(4 * math.pi * wl.alpha))
+
+
+def _pdf(name: str, q2_slope: float = 0.0) -> PdfTable:
+    return PdfTable(W.pdf_table(name, q2_slope), W.PDF_X_MIN, W.PDF_X_MAX, W.PDF_Q2_MIN, W.PDF_Q2_MAX)
+
+
+class Integrand:
+    def __init__(self, wl: W.Workload, m_top=None, alpha_s=None, q2_slope: float = 0.0,
+                 process: Process | None = None):
+        self.wl = wl
+        self.m_top = wl.m_top if m_top is None else m_top
+        self.proc = process if process is not None else oracle_process(wl, m_top, alpha_s)
+        if process is not None:
+            self.proc.masses["t"] = self.m_top
+        self.pdfs = tuple(_pdf(b, q2_slope) for b in wl.beams)
+        self.final_masses = []
+        for l in wl.legs:
+            if not l.incoming:
+                flav = PARTICLES[l.particle][1]
+                self.final_masses.append(self.m_top if flav == "t" else 0.0)
+        self.final_masses = np.array(self.final_masses)
+        S = wl.sqrt_s ** 2
+        self.S = S
+        self.tau_min = (np.sum(self.final_masses) ** 2) / S if wl.beams else None
+        self.gluon_finals = [i for i, l in enumerate(wl.legs) if not l.incoming and l.particle == "g"]
+
+    # ------------------------------------------------------------------
+    def kinematics(self, x):
+        """Momenta [N, n, 4], s-hat, x1, x2, J_x and W for points x [ndim, N]."""
+        x = np.asarray(x, dtype=np.float64)
+        N = x.shape[1]
+        if self.wl.beams:
+            x1, x2, tau, jx = ps.xmap(x[0], x[1], self.tau_min)
+            s_hat = tau * self.S
+            u = x[2:]
+        else:
+            x1 = x2 = np.ones(N)
+            jx = np.ones(N)
+            s_hat = np.full(N, self.S)
+            u = x
+        rs = np.sqrt(s_hat)
+        n_out = self.wl.n_out
+        p0 = ps.massless_diet(u, rs)
+        k, wfac, ok = ps.massive(p0, self.final_masses, rs)
+        w = ps.massless_weight(n_out, s_hat) * wfac
+        p = np.zeros((N, n_out + 2, 4))
+        p[:, 0] = np.stack([rs / 2, 0 * rs, 0 * rs, rs / 2], axis=1)
+        p[:, 1] = np.stack([rs / 2, 0 * rs, 0 * rs, -rs / 2], axis=1)
+        p[:, 2:] = k
+        return p, s_hat, x1, x2, jx, w, ok
+
+    def cuts(self, p):
+        N = p.shape[0]
+        keep = np.ones(N, dtype=bool)
+        wl = self.wl
+        for i in self.gluon_finals:
+            pt = np.hypot(p[:, i, 1], p[:, i, 2])
+            keep &= pt > wl.pt_min_gluon
+        if wl.dr_min_gluon > 0:
+            for a in range(len(self.gluon_finals)):
+                for b in range(a + 1, len(self.gluon_finals)):
+                    i, j = self.gluon_finals[a], self.gluon_finals[b]
+                    yi = 0.5 * np.log((p[:, i, 0] + p[:, i, 3]) / (p[:, i, 0] - p[:, i, 3]))
+                    yj = 0.5 * np.log((p[:, j, 0] + p[:, j, 3]) / (p[:, j, 0] - p[:, j, 3]))
+                    dphi = np.arctan2(p[:, i, 2], p[:, i, 1]) - np.arctan2(p[:, j, 2], p[:, j, 1])
+                    dphi = np.angle(np.exp(1j * dphi))
+                    dr = np.sqrt((yi - yj) ** 2 + dphi ** 2)
+                    keep &= dr > wl.dr_min_gluon
+        return keep
+
+    def __call__(self, x, return_parts=False):
+        x = np.asarray(x, dtype=np.float64)
+        N = x.shape[1]
+        p, s_hat, x1, x2, jx, w, ok = self.kinematics(x)
+        keep = ok & self.cuts(p)
+        f = np.zeros(N)
+        if np.any(keep):
+            idx = np.nonzero(keep)[0]
+            msq = self.proc.msq_avg(p[idx])
+            lum = np.ones(len(idx))
+            if self.wl.beams:
+                lum = (self.pdfs[0].f(x1[idx], self.wl.mu_f2) * self.pdfs[1].f(x2[idx], self.wl.mu_f2))
+            f[idx] = jx[idx] * w[idx] * lum * msq / (2.0 * s_hat[idx]) * W.GEV2_TO_PB
+        if return_parts:
+            return f, dict(p=p, s_hat=s_hat, x1=x1, x2=x2, jx=jx, w=w, keep=keep)
+        return f

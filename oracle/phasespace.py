@@ -1,0 +1,178 @@
+"""Phase space of the oracle (Sec. 2.4 of the MadFlow paper: a vectorised
+RAMBO maps the integrator's random variables to flat phase space).
+
+Definitions used here (all FP64, vectorised over events, momenta [N, n, 4] as
+(E, px, py, pz), metric (+,-,-,-)):
+
+* ``xmap``: parton momentum fractions from two unit numbers (the paper's
+  L(x1, x2) of Fig. 1 has no stated map; reading: tau = tau_min^y1,
+  x1 = tau^y2, x2 = tau / x1, Jacobian tau ln(1/tau_min) ln(1/tau)).
+* ``massless_diet``: flat massless n-body phase space from 3n-4 unit numbers
+  ("RAMBO on diet", S. Platzer, arXiv:1308.2922): a chain of two-body decays
+  Q_k -> q_k + Q_{k+1}, with the squared-mass ratio x = M_{k+1}^2 / M_k^2 of a
+  daughter system of m massless particles drawn from the density
+  (1-x) x^(m-2) (CDF m x^(m-1) - (m-1) x^m) and isotropic decay angles.
+  Per decay step k the unit numbers are (cos-theta, phi[, mass ratio]).
+* ``massive``: the momentum rescaling of RAMBO (R. Kleiss, W.J. Stirling,
+  S.D. Ellis, Comput. Phys. Commun. 40 (1986) 359): solve
+  sum_i sqrt(m_i^2 + xi^2 |p_i|^2) = sqrt(s) for xi, rescale the 3-momenta,
+  and multiply the massless weight by
+  (sum|k|/sqrt s)^(2n-3) prod(|k_i|/k_i^0) sqrt(s) / sum(|k_i|^2/k_i^0).
+* ``massless_weight``: (2 pi)^(4-3n) (pi/2)^(n-1) s^(n-2) / ((n-1)! (n-2)!).
+* ``rambo_classic``: the original 4n-number massless RAMBO, kept only as an
+  independent check of the flat measure.
+
+The oracle finds xi by bisection to the last bit (the GPU path uses Newton):
+the root is unique, so both must agree to rounding.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def massless_weight(n: int, s):
+    return ((2.0 * math.pi) ** (4 - 3 * n) * (math.pi / 2.0) ** (n - 1)
+            * np.asarray(s, dtype=np.float64) ** (n - 2)
+            / (math.factorial(n - 1) * math.factorial(n - 2)))
+
+
+def xmap(y1, y2, tau_min: float):
+    """(x1, x2, tau, jacobian) from two unit numbers."""
+    if not tau_min > 0.0:
+        raise ValueError("the tau map needs a positive threshold")
+    y1 = np.asarray(y1, dtype=np.float64)
+    y2 = np.asarray(y2, dtype=np.float64)
+    tau = np.exp(y1 * math.log(tau_min))
+    x1 = np.exp(y2 * np.log(tau))
+    x2 = tau / x1
+    jac = tau * math.log(1.0 / tau_min) * np.log(1.0 / tau)
+    return x1, x2, tau, jac
+
+
+def _boost_from_rest(p, Q, M):
+    """Boost p (given in the rest frame of Q, mass M) to the frame where Q is given."""
+    p0 = p[..., 0]
+    pv = p[..., 1:]
+    Qv = Q[..., 1:]
+    e = (Q[..., 0] * p0 + np.sum(Qv * pv, axis=-1)) / M
+    c = (p0 + e) / (Q[..., 0] + M)
+    out = np.empty_like(p)
+    out[..., 0] = e
+    out[..., 1:] = pv + c[..., None] * Qv
+    return out
+
+
+def _mass_ratio(r, m: int):
+    """Solve m x^(m-1) - (m-1) x^m = r for x in [0, 1] (bisection to the last bit)."""
+    r = np.asarray(r, dtype=np.float64)
+    lo = np.zeros_like(r)
+    hi = np.ones_like(r)
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        F = m * mid ** (m - 1) - (m - 1) * mid ** m
+        below = F < r
+        lo = np.where(below, mid, lo)
+        hi = np.where(below, hi, mid)
+    return 0.5 * (lo + hi)
+
+
+def massless_diet(u, sqrt_s):
+    """Flat massless momenta from unit numbers u [3n-4, N]; returns p [N, n, 4].
+
+    Step k (k = 0 .. n-2) consumes (cos-theta, phi) and, for k <= n-3, the
+    mass-ratio number, in that order.
+    """
+    u = np.asarray(u, dtype=np.float64)
+    nr, N = u.shape
+    n = (nr + 4) // 3
+    if 3 * n - 4 != nr or n < 2:
+        raise ValueError("need 3n-4 unit numbers with n >= 2")
+    sqrt_s = np.broadcast_to(np.asarray(sqrt_s, dtype=np.float64), (N,))
+    p = np.zeros((N, n, 4))
+    Q = np.zeros((N, 4))
+    Q[:, 0] = sqrt_s
+    M = sqrt_s.copy()
+    col = 0
+    for k in range(n - 1):
+        cth = 2.0 * u[col] - 1.0
+        phi = 2.0 * math.pi * u[col + 1]
+        col += 2
+        m_daughter = n - k - 1            # massless particles left in Q_{k+1}
+        if m_daughter >= 2:
+            x = _mass_ratio(u[col], m_daughter)
+            col += 1
+            M_next = M * np.sqrt(x)
+        else:
+            M_next = np.zeros_like(M)
+        e = (M * M - M_next * M_next) / (2.0 * M)
+        sth = np.sqrt(np.maximum(0.0, 1.0 - cth * cth))
+        q = np.stack([e, e * sth * np.cos(phi), e * sth * np.sin(phi), e * cth], axis=-1)
+        rest = np.stack([M - e, -q[:, 1], -q[:, 2], -q[:, 3]], axis=-1)
+        p[:, k] = _boost_from_rest(q, Q, M)
+        Qn = _boost_from_rest(rest, Q, M)
+        if k == n - 2:
+            p[:, n - 1] = Qn
+        Q = Qn
+        M = M_next
+    return p
+
+
+def massive(p, masses, sqrt_s):
+    """Rescale massless momenta p [N, n, 4] (sum = (sqrt s, 0)) to the masses.
+
+    Returns (k [N, n, 4], weight factor relative to the massless weight,
+    ok mask).  Events below threshold get ok = False and zero weight.
+    """
+    p = np.asarray(p, dtype=np.float64)
+    N, n, _ = p.shape
+    m = np.asarray(masses, dtype=np.float64)
+    sqrt_s = np.broadcast_to(np.asarray(sqrt_s, dtype=np.float64), (N,))
+    ok = sqrt_s > np.sum(m)
+    if np.all(m == 0.0):
+        return p.copy(), np.ones(N), ok
+    E = p[:, :, 0]
+    lo = np.zeros(N)
+    hi = np.ones(N)
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        F = np.sum(np.sqrt(m[None, :] ** 2 + (mid[:, None] * E) ** 2), axis=1) - sqrt_s
+        below = F < 0.0
+        lo = np.where(below, mid, lo)
+        hi = np.where(below, hi, mid)
+    xi = 0.5 * (lo + hi)
+    k = np.empty_like(p)
+    k[:, :, 1:] = xi[:, None, None] * p[:, :, 1:]
+    kabs = xi[:, None] * E
+    k[:, :, 0] = np.sqrt(m[None, :] ** 2 + kabs ** 2)
+    w = ((np.sum(kabs, axis=1) / sqrt_s) ** (2 * n - 3)
+         * np.prod(kabs / k[:, :, 0], axis=1)
+         * sqrt_s / np.sum(kabs ** 2 / k[:, :, 0], axis=1))
+    w = np.where(ok, w, 0.0)
+    return k, w, ok
+
+
+def rambo_classic(u, sqrt_s, n: int):
+    """Original massless RAMBO from 4n unit numbers u [4n, N]."""
+    u = np.asarray(u, dtype=np.float64)
+    N = u.shape[1]
+    q = np.zeros((N, n, 4))
+    for i in range(n):
+        c = 2.0 * u[4 * i] - 1.0
+        phi = 2.0 * math.pi * u[4 * i + 1]
+        q0 = -np.log(u[4 * i + 2] * u[4 * i + 3])
+        s = np.sqrt(1.0 - c * c)
+        q[:, i] = np.stack([q0, q0 * s * np.cos(phi), q0 * s * np.sin(phi), q0 * c], axis=-1)
+    Qs = q.sum(axis=1)
+    M = np.sqrt(Qs[:, 0] ** 2 - np.sum(Qs[:, 1:] ** 2, axis=1))
+    b = -Qs[:, 1:] / M[:, None]
+    x = sqrt_s / M
+    gamma = Qs[:, 0] / M
+    a = 1.0 / (1.0 + gamma)
+    p = np.zeros_like(q)
+    for i in range(n):
+        bq = np.sum(b * q[:, i, 1:], axis=1)
+        p[:, i, 0] = x * (gamma * q[:, i, 0] + bq)
+        p[:, i, 1:] = x[:, None] * (q[:, i, 1:] + b * q[:, i, 0:1] + (a * bq)[:, None] * b)
+    return p
