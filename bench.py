@@ -1,0 +1,299 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused leading-order integrand: one step = one Vegas
+iteration of gg -> tt~gg (random numbers -> Vegas map -> x1,x2 -> phase space
+-> cuts -> PDFs -> helicity amplitudes -> colour sum -> weight -> Vegas
+accumulators -> grid refinement), 4e7 events per iteration, all on the GPU.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  `value` is events/s of the mixed-precision path (f32
+amplitudes, f64 kinematics and accumulators) over the whole job; the FP64 path
+and the per-event agreement of the two are reported beside it.  With
+--impl reference the oracle (CPU, numpy) is timed on a bounded sample of the
+same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "events/s of gg→tt̄g(g) LO integrand: mixed/batched vs FP64 at ≤1e-5 rel err"
+WORKLOAD = "gg_ttxgg"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--events", type=int, default=0, help="events per step (default: the workload's 4e7)")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--fp64-events", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+def cpu_baseline_oracle(wl, n_sample):
+    """The oracle as it stands, single-threaded numpy, on n_sample points."""
+    import numpy as np
+    import workloads as W
+    from oracle.integrand import Integrand
+    from oracle import vegas
+    from oracle.philox import vegas_uniforms
+    I = Integrand(wl)
+    I.proc.colour_matrix()                      # one-time set-up, not timed
+    grid = vegas.uniform_grid(wl.ndim, wl.n_bins)
+    t0 = time.perf_counter()
+    y = vegas_uniforms(1, 0, 0, 0, n_sample, wl.ndim)
+    x, jac, bins = vegas.vegas_map(grid, y)
+    w = I(x) * jac
+    vegas.accumulate(w, bins, wl.n_bins)
+    dt = time.perf_counter() - t0
+    return n_sample / dt, dt
+
+
+def run_reference(args):
+    import workloads as W
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    wl = W.WORKLOADS[args.workload]
+    sample = 120 if wl.name == "gg_ttxgg" else 2000
+    times = []
+    for i in range(args.warmup + args.steps):
+        rate, dt = cpu_baseline_oracle(wl, sample)
+        if i >= args.warmup:
+            times.append(dt)
+    dt = statistics.median(times)
+    value = sample / dt
+    line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"{wl.name}: oracle (numpy, 1 thread) on {sample} points of one Vegas "
+                                   f"iteration per step"},
+            "cpu_baseline": {"value": value, "unit": "events/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{sample} points of the {wl.name} Vegas iteration"},
+            "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args):
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2106_10279_gb300 import api
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    wl = W.WORKLOADS[args.workload]
+    n_events = args.events or wl.n_events
+    proc = api.Process.from_workload(wl)
+    info = proc.info
+    stream = torch.cuda.current_stream()
+    vg = api.Vegas(wl.ndim, wl.n_bins, wl.alpha_vegas)
+    seed = 1000 + rank
+
+    def step(prec, n, refine=True):
+        return api.mf_vegas_iterate([vg.handle], [proc.handle], [n], seed, prec, refine, stream)[0]
+
+    # warm-up (also JIT-compiles the mixed kernel)
+    for _ in range(max(args.warmup, 3)):
+        step("mixed", n_events)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    kernel_ms, results = [], []
+    barrier()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        results.append(step("mixed", n_events))
+        kernel_ms.append(api.mf_process_last_kernel_ms(proc.handle))
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    total_ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * n_events * args.steps / (total_ms / 1e3)
+
+    # FP64 path on a sample of the same iteration
+    n64 = args.fp64_events or min(n_events, 2_000_000)
+    step("fp64", n64, refine=False)
+    torch.cuda.synchronize()
+    t64 = []
+    for _ in range(2):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step("fp64", n64, refine=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t64.append(a.elapsed_time(b))
+    fp64_rate = n64 / (min(t64) / 1e3)
+
+    # per-event agreement of the mixed path with the FP64 path
+    x = torch.from_numpy(W.uniform_points(wl.ndim, 20000, 77)).cuda()
+    f64 = proc.integrand(x, "fp64").cpu().numpy()
+    fmx = proc.integrand(x, "mixed").cpu().numpy()
+    nz = f64 != 0
+    rel = np.abs(fmx[nz] - f64[nz]) / np.abs(f64[nz])
+
+    # end to end through the public API with host buffers: upload the grid
+    # from pinned host memory, run the iteration, read results and grid back
+    grid_host = torch.from_numpy(vg.grid).pin_memory()
+    h2d = grid_host.numel() * 8
+    d2h = 7 * 8 + grid_host.numel() * 8
+    t_e2e = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        vg.grid = grid_host.numpy()
+        r = step("mixed", n_events)
+        g_back = vg.grid
+        t_e2e.append(time.perf_counter() - t0)
+    e2e_value = world * n_events / min(t_e2e)
+
+    # roofline of the dominant kernel: algorithmic FLOPs / its device time
+    kms = statistics.median(kernel_ms)
+    passing = statistics.median([r["n_nonzero"] for r in results])
+    flops = passing * info["n_hel"] * info["flops_per_hel"] + n_events * info["flops_kinematics"]
+    achieved = flops / (kms / 1e3) / 1e12
+    peaks = _peaks()
+    sm_max = (peaks.get("sm_max_mhz") or 2070.0)
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        sample = 200
+        rate, dt = cpu_baseline_oracle(wl, sample)
+        cpu = {"value": rate, "unit": "events/s", "cores": 1, "kind": "oracle",
+               "sample": f"{sample} points of one {wl.name} Vegas iteration (Philox, map, integrand, "
+                         f"accumulate), {dt:.1f} s"}
+    launches_per_step = 5          # integrand, accumulate, reduce, finalize, refine
+    line = {
+        "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"{wl.name}: gg->tt~gg at 13 TeV, {n_events:.0e} events per Vegas iteration "
+                               f"per GPU, {wl.ndim} dims, 50 bins, cuts pT(g)>20 GeV and dR(g,g)>0.4, synthetic "
+                               f"PDF table; f32 amplitudes/colour sum, f64 kinematics and accumulators",
+                   "events_per_step_per_gpu": n_events, "diagrams": 123, "helicities": info["n_hel"],
+                   "colour_flows": info["n_jamp"],
+                   "l2": "random numbers generated in-kernel; per-step outputs (w, bins) "
+                         f"{n_events * (8 + wl.ndim) / 1e6:.0f} MB > 129 MB L2"},
+        "fp64": {"value": fp64_rate, "unit": "events/s", "events": n64},
+        "accuracy": {"median_rel_mixed_vs_fp64": float(np.median(rel)), "max_rel_mixed_vs_fp64": float(rel.max()),
+                     "points": int(nz.sum())},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": None,
+                     "kernel": "mf_kernel (fused integrand)", "kernel_ms": kms,
+                     "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"},
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "sigma_pb": results[-1]["sigma"], "sigma_err_pb": results[-1]["sigma_error"],
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

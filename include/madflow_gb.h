@@ -1,0 +1,258 @@
+/*
+ * madflow_gb.h -- C ABI of the GB300-native leading-order integrand library.
+ *
+ * The library evaluates the per-event leading-order integrand of the MadFlow
+ * method (arXiv:2106.10279): for each phase-space point, flat RAMBO momenta and
+ * weight (Sec. 2.4), the parton luminosity from interpolated PDF tables (Sec. 1,
+ * Fig. 1), and the helicity-amplitude matrix element summed over helicities and
+ * colours (Sec. 2.3), combined as L(x1,x2) x sigma-hat (Fig. 1); and it drives the
+ * Vegas iteration around it (Sec. 2.2: random numbers -> phase space -> matrix
+ * element -> histogram accumulation).
+ *
+ * Conventions shared by every entry point:
+ *   - All functions return an mf_status.  Nothing aborts, throws across the ABI
+ *     or traps on the device.  mf_last_error() returns a thread-local message.
+ *   - "device" pointers are CUDA global-memory pointers of the current device;
+ *     "host" pointers are ordinary CPU memory.  The caller owns every buffer it
+ *     passes; the library owns the objects it creates (mf_process, mf_vegas) and
+ *     their internal device scratch, and frees them in the matching destroy call.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Calls are asynchronous on that stream unless stated otherwise.
+ *   - Momenta are (E, px, py, pz) in GeV, metric (+,-,-,-).
+ *   - Arrays of events are structure-of-arrays: x[j * n + i] is coordinate j of
+ *     event i.
+ */
+#ifndef MADFLOW_GB_H
+#define MADFLOW_GB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MF_OK = 0,
+    MF_EINVAL = 1,        /* malformed argument or descriptor */
+    MF_ENOMEM = 2,        /* device or host allocation failed */
+    MF_ECUDA = 3,         /* a CUDA runtime/driver call failed */
+    MF_ENAN = 4,          /* results were written, but some events were not finite */
+    MF_ETIMEOUT = 5,      /* a bounded device wait gave up */
+    MF_EUNSUPPORTED = 6,  /* valid request outside what this build implements */
+    MF_EJIT = 7           /* run-time compilation of the process kernels failed */
+} mf_status;
+
+/* Arithmetic of the matrix element (Sec. 2.3).  MF_FP64: everything in double
+ * precision.  MF_MIXED: spinors, currents, amplitudes and the colour sum in
+ * single precision; phase space, invariants and propagator denominators, PDFs,
+ * weights and all accumulators in double precision. */
+typedef enum { MF_FP64 = 0, MF_MIXED = 1 } mf_precision;
+
+/* ------------------------------------------------------------------------ */
+/* Process descriptor: the diagram program of Sec. 2.3 (the Matrix class the   */
+/* MadFlow exporter writes, here as data).                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Role of an external leg in the fermion flow. */
+typedef enum {
+    MF_LEG_FERMION_IN = 0,   /* column spinor: u of an incoming fermion, v of an outgoing antifermion */
+    MF_LEG_FERMION_OUT = 1,  /* row spinor: u-bar of an outgoing fermion, v-bar of an incoming antifermion */
+    MF_LEG_VECTOR = 2        /* massless vector boson: eps (incoming) or eps* (outgoing) */
+} mf_leg_kind;
+
+/* Routines of the diagram program (HELAS/ALOHA roles, Sec. 2.3).  Every
+ * wavefunction carries the momentum flowing INTO the diagram through the legs it
+ * contains.  "coupling" is the complex vertex factor c; "inv_den" below means
+ * 1 / (P^2 - M^2) of the current's momentum P and propagator mass M.
+ *   MF_R_IXX, MF_R_OXX, MF_R_VXX  external column spinor / row spinor / vector
+ *   MF_R_FFV_AMP(row, col, V)     c * row . (gamma^mu V_mu) . col
+ *   MF_R_FFV_FIN(col, V)          i inv_den (q-slash + M) c (V-slash) col,  q = P
+ *   MF_R_FFV_FOUT(row, V)         i inv_den row c (V-slash) (q-slash + M),  q = -P
+ *   MF_R_FFV_VEC(row, col)        -i inv_den c row gamma^mu col
+ *   MF_R_VVV_AMP(A, B, C)         c V3(A,B,C),  V3 = (A.B)((kA-kB).C) + (B.C)((kB-kC).A)
+ *                                                + (C.A)((kC-kA).B), k = incoming momenta
+ *   MF_R_VVV_VEC(A, B)            -i inv_den c [(A.B)(kA-kB) + B ((kB-kC).A) + A ((kC-kA).B)],
+ *                                 kC = -(kA+kB)
+ *   MF_R_VVVVs_AMP(A, B, C, D)    c x  s=1: (A.C)(B.D)-(A.D)(B.C)   s=2: (A.B)(C.D)-(A.D)(B.C)
+ *                                      s=3: (A.B)(C.D)-(A.C)(B.D)   (colour f^abe f^cde,
+ *                                      f^ace f^bde, f^ade f^bce of the four-gluon vertex)
+ *   MF_R_VVVVs_VEC(A, B, C)       -i inv_den c x  s=1: (A.C)B-(B.C)A  s=2: (A.B)C-(B.C)A
+ *                                                  s=3: (A.B)C-(A.C)B
+ */
+typedef enum {
+    MF_R_IXX = 0, MF_R_OXX = 1, MF_R_VXX = 2,
+    MF_R_FFV_AMP = 10, MF_R_FFV_FIN = 11, MF_R_FFV_FOUT = 12, MF_R_FFV_VEC = 13,
+    MF_R_VVV_AMP = 20, MF_R_VVV_VEC = 21,
+    MF_R_VVVV1_AMP = 30, MF_R_VVVV2_AMP = 31, MF_R_VVVV3_AMP = 32,
+    MF_R_VVVV1_VEC = 33, MF_R_VVVV2_VEC = 34, MF_R_VVVV3_VEC = 35
+} mf_routine;
+
+typedef enum { MF_OP_EXT = 0, MF_OP_CUR = 1, MF_OP_AMP = 2 } mf_op_kind;
+
+/* One op of the program.  Ops are evaluated in order; op k's result is
+ * wavefunction k (EXT and CUR ops).  Inputs name earlier ops. */
+typedef struct {
+    int32_t kind;          /* mf_op_kind */
+    int32_t routine;       /* mf_routine */
+    int32_t in[4];         /* input op indices, -1 when unused */
+    int32_t leg;           /* EXT: external leg index */
+    int32_t coupling;      /* CUR/AMP: index into couplings[] */
+    int32_t mass_id;       /* CUR: propagator mass = masses[mass_id], -1 = massless */
+    int32_t first_term;    /* AMP: colour terms terms[first_term .. first_term+n_terms) */
+    int32_t n_terms;
+} mf_op;
+
+/* AMP op contributes (re + i im) * amplitude to JAMP[jamp]. */
+typedef struct {
+    int32_t jamp;
+    int32_t pad_;
+    double re, im;
+} mf_colour_term;
+
+#define MF_MAX_LEGS 8
+#define MF_MAX_JAMP 128
+#define MF_MAX_DIM 20
+
+typedef struct {
+    /* external legs; legs 0 and 1 are the incoming partons along +z and -z */
+    int32_t n_legs;
+    const int32_t *leg_kind;        /* host [n_legs] mf_leg_kind */
+    const int32_t *leg_incoming;    /* host [n_legs] 1 incoming, 0 outgoing */
+    const int32_t *leg_mass_id;     /* host [n_legs] index into masses[], -1 = massless */
+    const int32_t *leg_cut;         /* host [n_legs] 1 = subject to the pT / Delta R cuts */
+    int32_t n_masses;
+    const double *masses;           /* host [n_masses] GeV; masses[0] is the top mass m_t */
+    /* diagram program */
+    int32_t n_ops;
+    const mf_op *ops;               /* host [n_ops] */
+    int32_t n_terms;
+    const mf_colour_term *terms;    /* host [n_terms] */
+    int32_t n_couplings;
+    const double *couplings;        /* host [2 * n_couplings] (re, im) pairs */
+    /* colour matrix C = colour_num / colour_den, symmetric, [n_jamp][n_jamp] */
+    int32_t n_jamp;
+    const int32_t *colour_num;      /* host [n_jamp * n_jamp] */
+    int32_t colour_den;
+    /* helicities: n_hel rows of n_legs values +-1 (NULL: all 2^n_legs); rows
+       that vanish identically are dropped at create time */
+    int32_t n_hel;
+    const int8_t *helicities;
+    double average;                 /* 1/(initial spins x colours) x identical-final factor */
+    int32_t alpha_s_power;          /* |M|^2 ~ alpha_s^power */
+    double alpha_s;
+    /* collision */
+    double sqrt_s;                  /* collider energy, GeV */
+    int32_t hadronic;               /* 1: two PDF beams and the x1, x2 map; 0: fixed sqrt_s */
+    const double *pdf[2];           /* host [pdf_nq][pdf_nx] tables of x f(x, Q^2), beam 1 / 2 */
+    int32_t pdf_nx, pdf_nq;         /* knots uniform in ln x and in ln Q^2 */
+    double pdf_x_min, pdf_x_max, pdf_q2_min, pdf_q2_max;
+    double mu_f2;                   /* factorisation scale squared, GeV^2 */
+    /* cuts on the legs flagged in leg_cut */
+    double pt_min;                  /* pT > pt_min (GeV), 0 = none */
+    double dr_min;                  /* Delta R > dr_min between flagged pairs, 0 = none */
+} mf_process_desc;
+
+typedef struct mf_process mf_process;   /* opaque, library-owned */
+typedef struct mf_vegas mf_vegas;       /* opaque, library-owned */
+
+/* mf_create_process: validate and deep-copy *desc, drop vanishing helicities,
+ * generate CUDA source specialised to the diagram program and compile it for
+ * sm_103a at run time (NVRTC; cached on disk when MF_JIT_CACHE names a
+ * directory).  Synchronous.  Errors: MF_EINVAL (malformed descriptor),
+ * MF_EUNSUPPORTED (more than MF_MAX_LEGS legs, n_jamp > MF_MAX_JAMP),
+ * MF_EJIT (compilation failed; mf_last_error has the log), MF_ECUDA, MF_ENOMEM.
+ * On error *out is left NULL. */
+mf_status mf_create_process(const mf_process_desc *desc, mf_process **out);
+mf_status mf_destroy_process(mf_process *p);
+
+typedef struct {
+    int32_t ndim;            /* integration dimensions: 3 n_out - 4 (+2 if hadronic) */
+    int32_t n_legs;
+    int32_t n_hel;           /* helicities kept after filtering */
+    int32_t n_hel_all;       /* helicities before filtering */
+    int32_t n_jamp;
+    int32_t n_ops;
+    int32_t n_den;           /* distinct propagator denominators per event */
+    double flops_per_hel;    /* algorithmic FLOPs of one helicity (program + colour sum) */
+    double flops_kinematics; /* algorithmic FLOPs per event outside the helicity loop */
+} mf_process_info;
+
+mf_status mf_process_get_info(const mf_process *p, mf_process_info *info);
+
+/* mf_integrand (Fig. 1: L(x1,x2) x sigma-hat({p})): for n points x in the open
+ * unit hypercube (device, SoA [ndim][n]) write the integrand in pb to f (device
+ * [n]); sigma = integral of f over the hypercube.  Hadronic processes use x_0,
+ * x_1 for the momentum fractions (tau = tau_min^x0, x1 = tau^x1, x2 = tau/x1)
+ * and the rest for the phase space; points failing the cuts or below threshold
+ * give f = 0.  No Vegas Jacobian is applied.  Asynchronous.  n = 0 is a no-op.
+ * MF_EINVAL for NULL pointers with n > 0 or n < 0. */
+mf_status mf_integrand(mf_process *p, const double *x, int64_t n, double *f,
+                       mf_precision prec, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Vegas (Sec. 2.2; G.P. Lepage, J. Comput. Phys. 27 (1978) 192).              */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t iteration;       /* index of the iteration these numbers belong to */
+    int64_t n_events;        /* points sampled (including points with f = 0) */
+    int64_t n_nonzero;       /* points with f != 0 */
+    int64_t n_nan;           /* points whose weight was not finite (counted as 0) */
+    double integral;         /* this iteration's estimate, pb */
+    double error;            /* its standard error */
+    double sigma;            /* inverse-variance combination of all iterations so far */
+    double sigma_error;
+    double chi2_dof;
+} mf_iter_result;
+
+/* mf_vegas_create: a grid of ndim dimensions x nbins bins (uniform), refinement
+ * damping alpha (1.5 is the customary value).  nbins in [2, 256]. */
+mf_status mf_vegas_create(int32_t ndim, int32_t nbins, double alpha, mf_vegas **out);
+mf_status mf_vegas_destroy(mf_vegas *v);
+
+/* mf_vegas_iterate: one Vegas iteration for each of nproc subprocesses, each
+ * with its own grid.  Point i of subprocess k in iteration t draws its unit
+ * numbers from Philox4x64-10 with key (seed, 0) and counter (i, t, k, block),
+ * maps them through its grid, evaluates the integrand, accumulates sum w,
+ * sum w^2 and, per dimension and bin, sum w^2 and counts in a fixed order
+ * (bit-reproducible for a given seed whatever the launch configuration), then
+ * refines the grid (unless refine == 0) and combines the iteration with the
+ * previous ones.  Synchronous: returns after out[k] (host [nproc]) is filled.
+ * MF_ENAN if any point's weight was not finite (results still written). */
+mf_status mf_vegas_iterate(mf_vegas *const *grids, mf_process *const *procs,
+                           const int64_t *n_events, int32_t nproc, uint64_t seed,
+                           mf_precision prec, int32_t refine, mf_iter_result *out,
+                           void *stream);
+
+/* Device time, in ms, of the last fused integrand kernel that mf_vegas_iterate
+ * launched for this process (CUDA events recorded on the launching stream
+ * around that one launch; the accumulation and refinement kernels excluded).
+ * Valid after mf_vegas_iterate returned; 0 before the first call. */
+mf_status mf_process_last_kernel_ms(const mf_process *p, double *ms);
+
+/* Copy the grid edges (host [ndim][nbins+1]) out of / into the object. */
+mf_status mf_vegas_get_grid(const mf_vegas *v, double *edges);
+mf_status mf_vegas_set_grid(mf_vegas *v, const double *edges);
+/* The last iteration's accumulators: per dimension and bin sum of w^2 (host
+ * [ndim][nbins]) and counts (host [ndim][nbins]); either pointer may be NULL. */
+mf_status mf_vegas_get_histogram(const mf_vegas *v, double *sum_w2, int64_t *counts);
+/* Dimensions, bins and the next iteration's index. */
+mf_status mf_vegas_get_shape(const mf_vegas *v, int32_t *ndim, int32_t *nbins, int32_t *iteration);
+
+/* Diagnostic: write the CUDA source that mf_create_process would generate for
+ * *desc at precision prec into buf (host, capacity *len bytes; *len receives
+ * the size including the terminating NUL).  With compile != 0 the source is
+ * also compiled for sm_103a with NVRTC (no GPU needed) and MF_EJIT returned on
+ * failure.  buf may be NULL to query the size. */
+mf_status mf_generate_kernel_source(const mf_process_desc *desc, mf_precision prec, int32_t compile,
+                                    char *buf, size_t *len);
+
+/* Thread-local description of the last error (empty string if none). */
+const char *mf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MADFLOW_GB_H */

@@ -1,0 +1,289 @@
+"""Python binding of libmadflow_gb: the C entry points under the same names,
+plus small convenience classes.  Marshalling only: torch tensors provide device
+memory and streams, every computation runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as L
+from .process import ProcessProgram, build_program
+
+MF_FP64, MF_MIXED = L.MF_FP64, L.MF_MIXED
+_PREC = {"fp64": L.MF_FP64, "mixed": L.MF_MIXED, L.MF_FP64: L.MF_FP64, L.MF_MIXED: L.MF_MIXED}
+
+
+def _arr(ctype, values):
+    values = list(values)
+    return (ctype * max(len(values), 1))(*values)
+
+
+class Descriptor:
+    """An mf_process_desc and the host arrays it points into (kept alive)."""
+
+    def __init__(self, prog: ProcessProgram, *, sqrt_s: float, m_top: float, alpha_s: float,
+                 pdf_tables=None, pdf_axes=None, mu_f2: float = 0.0, pt_min: float = 0.0,
+                 dr_min: float = 0.0, helicities=None):
+        n = len(prog.legs)
+        self.prog = prog
+        masses = [m_top]
+        leg_mass_id = []
+        for m in prog.leg_mass:
+            if m == 0.0:
+                leg_mass_id.append(-1)
+            elif abs(m - m_top) < 1e-12 * m_top:
+                leg_mass_id.append(0)
+            else:
+                masses.append(m)
+                leg_mass_id.append(len(masses) - 1)
+        ops, terms = [], []
+        for op in prog.ops:
+            o = L.mf_op()
+            o.kind, o.routine = op.kind, op.routine
+            ins = list(op.inputs) + [-1] * (4 - len(op.inputs))
+            for q in range(4):
+                o.in_[q] = ins[q]
+            o.leg = op.leg
+            o.coupling = op.coupling
+            if op.kind == 1 and op.mass != 0.0:
+                o.mass_id = 0 if abs(op.mass - m_top) < 1e-12 * m_top else masses.index(op.mass)
+            else:
+                o.mass_id = -1
+            o.first_term = len(terms)
+            o.n_terms = len(op.terms)
+            for (k, re, im) in op.terms:
+                terms.append(L.mf_colour_term(k, 0, re, im))
+            ops.append(o)
+        cut = [0] * n
+        if pt_min > 0 or dr_min > 0:
+            for i, (p, inc) in enumerate(prog.legs):
+                if p == "g" and not inc:
+                    cut[i] = 1
+        self._keep = []
+        d = L.mf_process_desc()
+        d.n_legs = n
+        d.leg_kind = self._k(_arr(C.c_int32, prog.leg_kind))
+        d.leg_incoming = self._k(_arr(C.c_int32, [1 if inc else 0 for _, inc in prog.legs]))
+        d.leg_mass_id = self._k(_arr(C.c_int32, leg_mass_id))
+        d.leg_cut = self._k(_arr(C.c_int32, cut))
+        d.n_masses = len(masses)
+        d.masses = self._k(_arr(C.c_double, masses))
+        d.n_ops = len(ops)
+        d.ops = self._k((L.mf_op * len(ops))(*ops))
+        d.n_terms = len(terms)
+        d.terms = self._k((L.mf_colour_term * max(len(terms), 1))(*terms))
+        cpl = []
+        for c in prog.couplings:
+            cpl += [float(np.real(c)), float(np.imag(c))]
+        d.n_couplings = len(prog.couplings)
+        d.couplings = self._k(_arr(C.c_double, cpl))
+        nj = prog.colour_num.shape[0]
+        d.n_jamp = nj
+        d.colour_num = self._k(_arr(C.c_int32, [int(v) for v in prog.colour_num.reshape(-1)]))
+        d.colour_den = int(prog.colour_den)
+        if helicities is not None:
+            h = np.asarray(helicities, dtype=np.int8).reshape(-1, n)
+            d.n_hel = h.shape[0]
+            d.helicities = self._k(_arr(C.c_int8, h.reshape(-1).tolist()))
+        d.average = prog.average
+        d.alpha_s_power = prog.alpha_s_power
+        d.alpha_s = alpha_s
+        d.sqrt_s = sqrt_s
+        if pdf_tables is not None:
+            d.hadronic = 1
+            for b in range(2):
+                t = np.ascontiguousarray(pdf_tables[b], dtype=np.float64)
+                self._keep.append(t)
+                d.pdf[b] = t.ctypes.data_as(C.POINTER(C.c_double))
+            nq, nx = np.asarray(pdf_tables[0]).shape
+            d.pdf_nx, d.pdf_nq = nx, nq
+            d.pdf_x_min, d.pdf_x_max, d.pdf_q2_min, d.pdf_q2_max = pdf_axes
+            d.mu_f2 = mu_f2
+        d.pt_min = pt_min
+        d.dr_min = dr_min
+        self.desc = d
+
+    def _k(self, arr):
+        self._keep.append(arr)
+        return C.cast(arr, C.POINTER(arr._type_))
+
+
+def descriptor_for_workload(wl, m_top=None, alpha_s=None, q2_slope: float = 0.0, helicities=None):
+    """Descriptor of one of the synthetic workloads (``workloads`` module)."""
+    import workloads as W
+    mt = wl.m_top if m_top is None else m_top
+    a_s = wl.alpha_s if alpha_s is None else alpha_s
+    prog = build_program(wl.name, [(l.particle, l.incoming) for l in wl.legs], {"t": mt}, a_s, wl.alpha)
+    tables = axes = None
+    if wl.beams:
+        tables = [W.pdf_table(b, q2_slope) for b in wl.beams]
+        axes = (W.PDF_X_MIN, W.PDF_X_MAX, W.PDF_Q2_MIN, W.PDF_Q2_MAX)
+    return Descriptor(prog, sqrt_s=wl.sqrt_s, m_top=mt, alpha_s=a_s, pdf_tables=tables, pdf_axes=axes,
+                      mu_f2=wl.mu_f2, pt_min=wl.pt_min_gluon, dr_min=wl.dr_min_gluon, helicities=helicities)
+
+
+# ---------------------------------------------------------------- C entry points
+def mf_create_process(desc: Descriptor):
+    h = C.c_void_p()
+    L.check(L.lib().mf_create_process(C.byref(desc.desc), C.byref(h)), "mf_create_process")
+    return h
+
+
+def mf_destroy_process(h):
+    L.check(L.lib().mf_destroy_process(h), "mf_destroy_process")
+
+
+def mf_process_get_info(h) -> dict:
+    info = L.mf_process_info()
+    L.check(L.lib().mf_process_get_info(h, C.byref(info)), "mf_process_get_info")
+    return {k: getattr(info, k) for k, _ in info._fields_}
+
+
+def mf_process_last_kernel_ms(h) -> float:
+    ms = C.c_double()
+    L.check(L.lib().mf_process_last_kernel_ms(h, C.byref(ms)), "mf_process_last_kernel_ms")
+    return ms.value
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def mf_integrand(h, x, n: int, f, precision="fp64", stream=None):
+    """x, f: device pointers (int) or CUDA tensors (x [ndim, n] float64, f [n] float64)."""
+    xp = x if isinstance(x, int) else x.data_ptr()
+    fp = f if isinstance(f, int) else f.data_ptr()
+    return L.check(L.lib().mf_integrand(h, C.c_void_p(xp), n, C.c_void_p(fp), _PREC[precision],
+                                        _stream_ptr(stream)), "mf_integrand")
+
+
+def mf_vegas_create(ndim: int, nbins: int = 50, alpha: float = 1.5):
+    h = C.c_void_p()
+    L.check(L.lib().mf_vegas_create(ndim, nbins, alpha, C.byref(h)), "mf_vegas_create")
+    return h
+
+
+def mf_vegas_destroy(h):
+    L.check(L.lib().mf_vegas_destroy(h), "mf_vegas_destroy")
+
+
+def mf_vegas_iterate(grids, procs, n_events, seed: int, precision="fp64", refine: bool = True, stream=None):
+    k = len(grids)
+    G = (C.c_void_p * k)(*[g.value for g in grids])
+    Pp = (C.c_void_p * k)(*[p.value for p in procs])
+    N = (C.c_int64 * k)(*n_events)
+    out = (L.mf_iter_result * k)()
+    st = L.lib().mf_vegas_iterate(G, Pp, N, k, seed, _PREC[precision], 1 if refine else 0, out,
+                                  _stream_ptr(stream))
+    L.check(st, "mf_vegas_iterate", allow=(L.MF_OK, L.MF_ENAN))
+    return [{name: getattr(r, name) for name, _ in r._fields_} for r in out]
+
+
+def mf_vegas_get_grid(h):
+    nd, nb, it = C.c_int32(), C.c_int32(), C.c_int32()
+    L.check(L.lib().mf_vegas_get_shape(h, C.byref(nd), C.byref(nb), C.byref(it)), "mf_vegas_get_shape")
+    g = np.zeros((nd.value, nb.value + 1))
+    L.check(L.lib().mf_vegas_get_grid(h, g.ctypes.data_as(C.POINTER(C.c_double))), "mf_vegas_get_grid")
+    return g
+
+
+def mf_vegas_set_grid(h, edges):
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    L.check(L.lib().mf_vegas_set_grid(h, e.ctypes.data_as(C.POINTER(C.c_double))), "mf_vegas_set_grid")
+
+
+def mf_vegas_get_histogram(h):
+    nd, nb, it = C.c_int32(), C.c_int32(), C.c_int32()
+    L.check(L.lib().mf_vegas_get_shape(h, C.byref(nd), C.byref(nb), C.byref(it)), "mf_vegas_get_shape")
+    s = np.zeros((nd.value, nb.value))
+    c = np.zeros((nd.value, nb.value), dtype=np.int64)
+    L.check(L.lib().mf_vegas_get_histogram(h, s.ctypes.data_as(C.POINTER(C.c_double)),
+                                           c.ctypes.data_as(C.POINTER(C.c_int64))), "mf_vegas_get_histogram")
+    return s, c
+
+
+def mf_generate_kernel_source(desc: Descriptor, precision="fp64", compile: bool = False) -> str:
+    n = C.c_size_t(0)
+    L.check(L.lib().mf_generate_kernel_source(C.byref(desc.desc), _PREC[precision], 0, None, C.byref(n)),
+            "mf_generate_kernel_source")
+    buf = C.create_string_buffer(n.value)
+    L.check(L.lib().mf_generate_kernel_source(C.byref(desc.desc), _PREC[precision], 1 if compile else 0, buf,
+                                              C.byref(n)), "mf_generate_kernel_source")
+    return buf.value.decode()
+
+
+# ---------------------------------------------------------------- classes
+class Process:
+    """A compiled process; ``integrand(x)`` evaluates f at points x [ndim, n]."""
+
+    def __init__(self, desc: Descriptor):
+        self.desc = desc
+        self.handle = mf_create_process(desc)
+        self.info = mf_process_get_info(self.handle)
+
+    @classmethod
+    def from_workload(cls, wl, **kw):
+        return cls(descriptor_for_workload(wl, **kw))
+
+    @property
+    def ndim(self):
+        return self.info["ndim"]
+
+    def integrand(self, x, precision="fp64", out=None, stream=None):
+        import torch
+        if x.dtype != torch.float64 or not x.is_cuda or not x.is_contiguous():
+            raise ValueError("x must be a contiguous float64 CUDA tensor [ndim, n]")
+        if x.shape[0] != self.ndim:
+            raise ValueError(f"x must have {self.ndim} rows")
+        n = x.shape[1]
+        f = torch.empty(n, dtype=torch.float64, device=x.device) if out is None else out
+        mf_integrand(self.handle, x, n, f, precision, stream)
+        return f
+
+    def close(self):
+        if self.handle:
+            mf_destroy_process(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Vegas:
+    def __init__(self, ndim: int, nbins: int = 50, alpha: float = 1.5):
+        self.handle = mf_vegas_create(ndim, nbins, alpha)
+
+    def iterate(self, proc: Process, n_events: int, seed: int, precision="fp64", refine=True, stream=None):
+        return mf_vegas_iterate([self.handle], [proc.handle], [n_events], seed, precision, refine, stream)[0]
+
+    @property
+    def grid(self):
+        return mf_vegas_get_grid(self.handle)
+
+    @grid.setter
+    def grid(self, edges):
+        mf_vegas_set_grid(self.handle, edges)
+
+    def histogram(self):
+        return mf_vegas_get_histogram(self.handle)
+
+    def close(self):
+        if self.handle:
+            mf_vegas_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

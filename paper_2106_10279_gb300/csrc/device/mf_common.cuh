@@ -1,0 +1,66 @@
+// Common device definitions for the run-time-compiled process kernels.
+// Compiled by NVRTC (no standard headers): fixed-width integer types and a
+// small complex type are defined here.
+#pragma once
+
+#ifdef __CUDACC_RTC__
+typedef unsigned long long uint64_t;
+typedef long long int64_t;
+typedef unsigned int uint32_t;
+typedef int int32_t;
+typedef signed char int8_t;
+typedef unsigned char uint8_t;
+#else
+#include <cstdint>
+#endif
+
+#define MF_DEV __device__ __forceinline__
+
+namespace mf {
+
+template <typename R>
+struct cx {
+    R re, im;
+};
+
+template <typename R> MF_DEV cx<R> C(R a, R b) { return cx<R>{a, b}; }
+template <typename R> MF_DEV cx<R> operator+(cx<R> a, cx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename R> MF_DEV cx<R> operator-(cx<R> a, cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename R> MF_DEV cx<R> operator-(cx<R> a) { return {-a.re, -a.im}; }
+template <typename R> MF_DEV cx<R> operator*(cx<R> a, cx<R> b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R> MF_DEV cx<R> operator*(R s, cx<R> a) { return {s * a.re, s * a.im}; }
+template <typename R> MF_DEV cx<R> operator*(cx<R> a, R s) { return {s * a.re, s * a.im}; }
+template <typename R> MF_DEV cx<R> conj(cx<R> a) { return {a.re, -a.im}; }
+// i * a and -i * a
+template <typename R> MF_DEV cx<R> mul_i(cx<R> a) { return {-a.im, a.re}; }
+template <typename R> MF_DEV cx<R> mul_mi(cx<R> a) { return {a.im, -a.re}; }
+// a + b * c (complex fused form)
+template <typename R> MF_DEV cx<R> cfma(cx<R> b, cx<R> c, cx<R> a) {
+    return {a.re + b.re * c.re - b.im * c.im, a.im + b.re * c.im + b.im * c.re};
+}
+
+// Wavefunction: four complex components and the momentum flowing into the
+// diagram through the legs it contains (real).
+template <typename R>
+struct W {
+    cx<R> c[4];
+    R p[4];
+};
+
+// Minkowski product of two complex 4-vectors, no conjugation.
+template <typename R> MF_DEV cx<R> mdot(const cx<R> *a, const cx<R> *b) {
+    cx<R> r = a[0] * b[0];
+    r = r - a[1] * b[1];
+    r = r - a[2] * b[2];
+    r = r - a[3] * b[3];
+    return r;
+}
+// Minkowski product of a real and a complex 4-vector.
+template <typename R> MF_DEV cx<R> mdot(const R *k, const cx<R> *b) {
+    return {k[0] * b[0].re - k[1] * b[1].re - k[2] * b[2].re - k[3] * b[3].re,
+            k[0] * b[0].im - k[1] * b[1].im - k[2] * b[2].im - k[3] * b[3].im};
+}
+
+}  // namespace mf

@@ -1,0 +1,233 @@
+// Kernel body of the fused per-event integrand (Fig. 1: L(x1,x2) x sigma-hat),
+// included by the run-time generated source after it has defined namespace
+// `proc` (the process's diagram program and constants).
+//
+// One CUDA block works on tiles of BLOCK events:
+//   phase A  one thread per event, double precision: unit numbers (given x, or
+//            Philox + Vegas map), x1/x2 map, phase space + massive rescaling,
+//            cuts, PDFs, weight prefactor, invariants and propagator
+//            denominators -> shared memory; events that pass are compacted;
+//   phase B  HT threads per passing event, each running the diagram program
+//            for its share of the helicities in precision R (float or double)
+//            and the colour sum J^dagger C J; the per-helicity |M|^2 are summed
+//            in a fixed pairwise tree (independent of HT) across the HT lanes;
+//   phase C  one thread per event writes f (integrand) or w = f J_V and the
+//            bin indices (Vegas).
+#pragma once
+#include "mf_common.cuh"
+#include "mf_kinematics.cuh"
+#include "mf_helas.cuh"
+#include "mf_kparams.h"
+
+namespace mf {
+
+typedef mf_kparams KParams;
+
+// fixed pairwise summation over a power-of-two count, as a binary counter:
+// after adding item k (0-based), merge levels while bit j of k+1 is zero
+struct PairSum {
+    double lvl[9];          // enough for 256 items per lane
+    int count;
+    MF_DEV void init() { count = 0; }
+    MF_DEV void add(double v) {
+        int c = count;
+        double s = v;
+        int j = 0;
+        while ((c >> j) & 1) { s = lvl[j] + s; ++j; }
+        lvl[j] = s;
+        count = c + 1;
+    }
+    // total of a power-of-two count
+    MF_DEV double total() const {
+        int j = 0;
+        while ((1 << (j + 1)) <= count) ++j;
+        return count ? lvl[j] : 0.0;
+    }
+};
+
+template <typename R, int BLOCK, int HT>
+MF_DEV void kernel_body(const KParams &kp) {
+    using namespace proc;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *s_mom = reinterpret_cast<R *>(smem_raw);                                   // [BLOCK][NLEG][4]
+    R *s_den = s_mom + BLOCK * NLEG * 4;                                           // [BLOCK][NDEN1]
+    constexpr int NDEN1 = NDEN > 0 ? NDEN : 1;
+    double *s_pref = reinterpret_cast<double *>(
+        reinterpret_cast<unsigned char *>(s_den + BLOCK * NDEN1) +
+        ((16 - ((BLOCK * NDEN1 * sizeof(R)) % 16)) % 16));
+    double *s_msq = s_pref + BLOCK;
+    int *s_list = reinterpret_cast<int *>(s_msq + BLOCK);
+    int *s_warp = s_list + BLOCK;                                                  // [BLOCK/32 + 1]
+    __shared__ double s_grid[NDIM * 65];
+
+    const int tid = threadIdx.x;
+    const int lane32 = tid & 31, warp = tid >> 5;
+    const int64_t ntiles = (kp.n + BLOCK - 1) / BLOCK;
+
+    if (kp.mode == 1) {
+        for (int i = tid; i < NDIM * (kp.nb + 1); i += BLOCK) s_grid[i] = kp.grid[i];
+    }
+    __syncthreads();
+
+    R mass_r[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) mass_r[i] = (R)kp.masses[i];
+    cx<R> cpl[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) cpl[i] = C<R>((R)kp.couplings[2 * i], (R)kp.couplings[2 * i + 1]);
+
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t e = tile * BLOCK + tid;
+        bool ok = false;
+        double pref = 0.0, jv = 1.0;
+        uint8_t bins[NDIM];
+        if (e < kp.n) {
+            // ---------------- phase A: kinematics in double precision
+            double y[NDIM];
+            if (kp.mode != 1) {
+#pragma unroll
+                for (int j = 0; j < NDIM; ++j) y[j] = kp.x[(int64_t)j * kp.n + e];
+            } else {
+#pragma unroll
+                for (int b = 0; b < (NDIM + 3) / 4; ++b) {
+                    uint64_t c[4] = {(uint64_t)e, kp.iteration, kp.subprocess, (uint64_t)b};
+                    philox4x64_10(c, kp.seed, 0ull);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (4 * b + q < NDIM) y[4 * b + q] = unit_from_bits(c[q]);
+                }
+#pragma unroll
+                for (int j = 0; j < NDIM; ++j) {
+                    double xj;
+                    int bj;
+                    jv *= vegas_map1(s_grid + j * (kp.nb + 1), kp.nb, y[j], xj, bj);
+                    y[j] = xj;
+                    bins[j] = (uint8_t)bj;
+                }
+            }
+            double s_hat = kp.S, jx = 1.0, lum = 1.0;
+            XMap xm;
+            const double *u = y;
+            if (HADRONIC) {
+                xm = xmap(y[0], y[1], kp.ln_tau_min);
+                s_hat = xm.tau * kp.S;
+                jx = xm.jac;
+                u = y + 2;
+            }
+            double rs = sqrt(s_hat);
+            double p[NLEG][4];
+            p[0][0] = 0.5 * rs; p[0][1] = 0.0; p[0][2] = 0.0; p[0][3] = 0.5 * rs;
+            p[1][0] = 0.5 * rs; p[1][1] = 0.0; p[1][2] = 0.0; p[1][3] = -0.5 * rs;
+            double (*pout)[4] = reinterpret_cast<double (*)[4]>(&p[2][0]);
+            massless_diet<NOUT>(u, rs, pout);
+            double mout[NOUT];
+#pragma unroll
+            for (int i = 0; i < NOUT; ++i) mout[i] = LEG_MASS_ID[2 + i] >= 0 ? kp.masses[LEG_MASS_ID[2 + i]] : 0.0;
+            double wfac = massive_rescale<NOUT>(pout, mout, rs);
+            ok = wfac > 0.0;
+            // cuts on the flagged legs
+            if (ok && NCUT > 0) {
+#pragma unroll
+                for (int a = 0; a < NCUT; ++a) ok &= pt2(p[CUT_LEGS[a]]) > kp.pt_min2;
+                if (kp.dr_min2 > 0.0) {
+#pragma unroll
+                    for (int a = 0; a < NCUT; ++a)
+#pragma unroll
+                        for (int b = a + 1; b < NCUT; ++b)
+                            ok &= delta_r2(p[CUT_LEGS[a]], p[CUT_LEGS[b]]) > kp.dr_min2;
+                }
+            }
+            if (ok) {
+                double wps = kp.w0_const * wfac;
+#pragma unroll
+                for (int i = 0; i < NOUT - 2; ++i) wps *= s_hat;
+                if (HADRONIC) {
+                    const double *r = kp.pdf_rows;
+                    const int nx = kp.pdf_nx;
+                    double f1 = pdf_eval(r, r + nx, nx, kp.pdf_a0, kp.pdf_h, xm.ln_x1, xm.x1);
+                    double f2 = pdf_eval(r + 2 * nx, r + 3 * nx, nx, kp.pdf_a0, kp.pdf_h, xm.ln_x2, xm.x2);
+                    lum = f1 * f2;
+                }
+                pref = jx * wps * lum * kp.pref_const / s_hat;
+                // propagator denominators from double-precision invariants
+                double den[NDEN1];
+                denominators(p, kp.masses, den);
+                R *sd = s_den + tid * NDEN1;
+#pragma unroll
+                for (int k = 0; k < NDEN; ++k) sd[k] = (R)(1.0 / den[k]);
+                R *sm = s_mom + tid * NLEG * 4;
+#pragma unroll
+                for (int i = 0; i < NLEG; ++i)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) sm[4 * i + q] = (R)p[i][q];
+            }
+        }
+        s_pref[tid] = pref;
+        // ---------------- compaction of passing events
+        unsigned bal = __ballot_sync(0xffffffffu, ok);
+        if (lane32 == 0) s_warp[warp] = __popc(bal);
+        __syncthreads();
+        if (tid == 0) {
+            int acc = 0;
+            for (int w = 0; w < BLOCK / 32; ++w) { int c = s_warp[w]; s_warp[w] = acc; acc += c; }
+            s_warp[BLOCK / 32] = acc;
+        }
+        __syncthreads();
+        if (ok) s_list[s_warp[warp] + __popc(bal & ((1u << lane32) - 1u))] = tid;
+        const int npass = s_warp[BLOCK / 32];
+        __syncthreads();
+        // ---------------- phase B: helicity amplitudes, HT lanes per event
+        {
+            constexpr int EPR = BLOCK / HT;     // events per round
+            const int sub = tid % HT;
+            const int nhp = kp.nhel_pow2;       // padded helicity count (power of two)
+            const int per = nhp >= HT ? nhp / HT : 1;   // contiguous helicities per lane
+            for (int base = 0; base < npass; base += EPR) {
+                const int slot = base + tid / HT;
+                PairSum ps;
+                ps.init();
+                if (slot < npass) {
+                    const int ev = s_list[slot];
+                    R mom[NLEG][4];
+#pragma unroll
+                    for (int i = 0; i < NLEG; ++i)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) mom[i][q] = s_mom[ev * NLEG * 4 + 4 * i + q];
+                    const R *idn = s_den + ev * NDEN1;
+                    for (int k = 0; k < per; ++k) {
+                        const int h = sub * per + k;
+                        double v = 0.0;
+                        if (h < kp.nhel) v = (double)helicity_msq<R>(mom, idn, kp.hel[h], cpl, mass_r);
+                        if (kp.mode == 2 && h < kp.nhel) kp.f[(int64_t)h * kp.n + tile * BLOCK + ev] = v;
+                        ps.add(v);
+                    }
+                } else {
+                    for (int k = 0; k < per; ++k) ps.add(0.0);
+                }
+                double part = ps.total();
+#pragma unroll
+                for (int off = 1; off < HT; off <<= 1) {
+                    double o = __shfl_xor_sync(0xffffffffu, part, off);
+                    // lanes combine (lower block) + (upper block) in that order
+                    part = (sub & off) ? (o + part) : (part + o);
+                }
+                if (sub == 0 && slot < npass) s_msq[s_list[slot]] = part;
+            }
+        }
+        __syncthreads();
+        // ---------------- phase C: outputs
+        if (e < kp.n) {
+            double fval = ok ? s_pref[tid] * s_msq[tid] : 0.0;
+            if (kp.mode == 0) {
+                kp.f[e] = fval;
+            } else if (kp.mode == 1) {
+                kp.w_out[e] = fval * jv;
+#pragma unroll
+                for (int j = 0; j < NDIM; ++j) kp.bins_out[(int64_t)j * kp.n + e] = bins[j];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace mf

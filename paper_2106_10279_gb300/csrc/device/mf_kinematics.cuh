@@ -1,0 +1,223 @@
+// Double-precision per-event kinematics: counter-based random numbers, the
+// Vegas map, the x1/x2 map, flat phase space with the RAMBO massive
+// rescaling (Sec. 2.4), cuts and the PDF interpolation (Sec. 1, Fig. 1).
+#pragma once
+#include "mf_common.cuh"
+
+namespace mf {
+
+// ---------------------------------------------------------------- Philox4x64-10
+// Salmon, Moraes, Dror, Shaw, SC'11: ten rounds of the 4x64 Philox bijection.
+MF_DEV void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += W0; k1 += W1; }
+        uint64_t hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
+        uint64_t hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
+        uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    }
+}
+// odd multiples of 2^-53: strictly inside (0, 1), exact
+MF_DEV double unit_from_bits(uint64_t r) { return (double)((r >> 11) | 1ull) * 0x1p-53; }
+
+// ---------------------------------------------------------------- Vegas map
+// y -> x through per-dimension edges; returns the Jacobian factor, bin index.
+MF_DEV double vegas_map1(const double *edges, int nb, double y, double &x, int &bin) {
+    double ynb = y * nb;
+    int i = (int)floor(ynb);
+    if (i > nb - 1) i = nb - 1;
+    if (i < 0) i = 0;
+    double lo = edges[i], w = edges[i + 1] - lo;
+    x = lo + (ynb - i) * w;
+    bin = i;
+    return nb * w;
+}
+
+// ---------------------------------------------------------------- x1, x2 map
+// tau = tau_min^y0, x1 = tau^y1, x2 = tau / x1, J = tau ln(1/tau_min) ln(1/tau).
+struct XMap {
+    double x1, x2, tau, ln_x1, ln_x2, jac;
+};
+MF_DEV XMap xmap(double y0, double y1, double ln_tau_min) {
+    XMap m;
+    double ln_tau = y0 * ln_tau_min;
+    m.tau = exp(ln_tau);
+    m.ln_x1 = y1 * ln_tau;
+    m.x1 = exp(m.ln_x1);
+    m.x2 = m.tau / m.x1;
+    m.ln_x2 = ln_tau - m.ln_x1;
+    m.jac = m.tau * (-ln_tau_min) * (-ln_tau);
+    return m;
+}
+
+// ---------------------------------------------------------------- phase space
+// Boost p (given in the rest frame of Q, mass M) into the frame of Q.
+MF_DEV void boost_from_rest(const double *p, const double *Q, double M, double *out) {
+    double e = (Q[0] * p[0] + Q[1] * p[1] + Q[2] * p[2] + Q[3] * p[3]) / M;
+    double c = (p[0] + e) / (Q[0] + M);
+    out[0] = e;
+    out[1] = p[1] + c * Q[1];
+    out[2] = p[2] + c * Q[2];
+    out[3] = p[3] + c * Q[3];
+}
+
+// Squared-mass ratio x of a daughter system of m massless particles:
+// solves m x^(m-1) - (m-1) x^m = r on [0, 1].
+MF_DEV double mass_ratio(int m, double r) {
+    if (m == 2) {
+        // 2x - x^2 = r  ->  x = 1 - sqrt(1 - r) = r / (1 + sqrt(1 - r))
+        return r / (1.0 + sqrt(1.0 - r));
+    }
+    if (m == 3) {
+        // 3x^2 - 2x^3 = r is symmetric under (x, r) -> (1-x, 1-r): solve the
+        // half with x <= 1/2 by Newton from sqrt(t/3), which is then monotone.
+        bool upper = r > 0.5;
+        double t = upper ? 1.0 - r : r;
+        double s = sqrt(t / 3.0);
+        for (int it = 0; it < 60; ++it) {
+            double f = s * s * (3.0 - 2.0 * s) - t;
+            double d = 6.0 * s * (1.0 - s);
+            if (d <= 0.0) break;
+            double ns = s - f / d;
+            if (ns < 0.0) ns = 0.5 * s;
+            if (ns > 0.5) ns = 0.5 * (s + 0.5);
+            double step = fabs(ns - s);
+            s = ns;
+            if (step <= 1e-17 + 4e-16 * s) break;
+        }
+        return upper ? 1.0 - s : s;
+    }
+    // general m: Newton safeguarded by bisection on [lo, hi]
+    double lo = 0.0, hi = 1.0, x = pow(r, 1.0 / (m - 1));
+    for (int it = 0; it < 200; ++it) {
+        double xm2 = pow(x, m - 2);
+        double f = m * xm2 * x - (m - 1) * xm2 * x * x - r;
+        if (f < 0.0) lo = x; else hi = x;
+        double d = m * (m - 1) * xm2 * (1.0 - x);
+        double nx = (d > 0.0) ? x - f / d : 0.5 * (lo + hi);
+        if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
+        if (fabs(nx - x) <= 4e-16 * x || hi - lo <= 4e-16 * hi) { x = nx; break; }
+        x = nx;
+    }
+    return x;
+}
+
+// Flat massless n-body momenta in the centre-of-mass frame of energy rs from
+// 3n-4 unit numbers u (per decay step: cos-theta, phi[, mass ratio]).
+template <int N>
+MF_DEV void massless_diet(const double *u, double rs, double p[N][4]) {
+    double Q[4] = {rs, 0.0, 0.0, 0.0};
+    double M = rs;
+    int col = 0;
+#pragma unroll
+    for (int k = 0; k < N - 1; ++k) {
+        double cth = 2.0 * u[col] - 1.0;
+        double phi = 6.283185307179586 * u[col + 1];
+        col += 2;
+        int md = N - k - 1;
+        double Mn = 0.0;
+        if (md >= 2) {
+            double x = mass_ratio(md, u[col]);
+            col += 1;
+            Mn = M * sqrt(x);
+        }
+        double e = (M - Mn) * (M + Mn) / (2.0 * M);
+        double sth = sqrt(fmax(0.0, (1.0 - cth) * (1.0 + cth)));
+        double sp, cp;
+        sincos(phi, &sp, &cp);
+        double q[4] = {e, e * sth * cp, e * sth * sp, e * cth};
+        double rest[4] = {M - e, -q[1], -q[2], -q[3]};
+        double Qn[4];
+        boost_from_rest(q, Q, M, p[k]);
+        boost_from_rest(rest, Q, M, Qn);
+        if (k == N - 2) {
+            p[N - 1][0] = Qn[0]; p[N - 1][1] = Qn[1]; p[N - 1][2] = Qn[2]; p[N - 1][3] = Qn[3];
+        }
+        Q[0] = Qn[0]; Q[1] = Qn[1]; Q[2] = Qn[2]; Q[3] = Qn[3];
+        M = Mn;
+    }
+}
+
+// RAMBO massive rescaling (Kleiss, Stirling, Ellis, CPC 40 (1986) 359): scale
+// the 3-momenta by xi with sum_i sqrt(m_i^2 + xi^2 E_i^2) = rs (Newton), and
+// return the weight factor relative to the massless weight, or 0 below
+// threshold.  p is replaced by the massive momenta.
+template <int N>
+MF_DEV double massive_rescale(double p[N][4], const double *m, double rs) {
+    double msum = 0.0;
+    bool any = false;
+#pragma unroll
+    for (int i = 0; i < N; ++i) { msum += m[i]; any |= (m[i] != 0.0); }
+    if (!(rs > msum)) return 0.0;
+    if (!any) return 1.0;
+    double r = msum / rs;
+    double xi = sqrt((1.0 - r) * (1.0 + r));
+    for (int it = 0; it < 50; ++it) {
+        double f = -rs, d = 0.0;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            double e = sqrt(m[i] * m[i] + xi * xi * p[i][0] * p[i][0]);
+            f += e;
+            d += xi * p[i][0] * p[i][0] / e;
+        }
+        double step = f / d;
+        xi -= step;
+        if (fabs(step) <= 1e-15 * xi) break;
+    }
+    double sk = 0.0, prod = 1.0, sk2 = 0.0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        double kabs = xi * p[i][0];
+        double k0 = sqrt(m[i] * m[i] + kabs * kabs);
+        p[i][0] = k0;
+        p[i][1] *= xi; p[i][2] *= xi; p[i][3] *= xi;
+        sk += kabs;
+        prod *= kabs / k0;
+        sk2 += kabs * kabs / k0;
+    }
+    double a = sk / rs, pw = 1.0;
+#pragma unroll
+    for (int i = 0; i < 2 * N - 3; ++i) pw *= a;
+    return pw * prod * rs / sk2;
+}
+
+// ---------------------------------------------------------------- cuts
+// pT^2 of a momentum
+MF_DEV double pt2(const double *p) { return p[1] * p[1] + p[2] * p[2]; }
+// Delta R^2 = Delta y^2 + Delta phi^2 between two momenta (phi in [0, pi])
+MF_DEV double delta_r2(const double *a, const double *b) {
+    // E - pz without cancellation for pz > 0: (m^2 + pT^2)/(E + pz)
+    double apl = a[0] + fabs(a[3]), bpl = b[0] + fabs(b[3]);
+    double am2 = fmax(0.0, (a[0] - a[3]) * (a[0] + a[3]) - pt2(a));
+    double bm2 = fmax(0.0, (b[0] - b[3]) * (b[0] + b[3]) - pt2(b));
+    double amin = (am2 + pt2(a)) / apl, bmin = (bm2 + pt2(b)) / bpl;
+    double ap = a[3] >= 0 ? apl : amin, am = a[3] >= 0 ? amin : apl;   // E + pz, E - pz
+    double bp = b[3] >= 0 ? bpl : bmin, bm = b[3] >= 0 ? bmin : bpl;
+    double dy = 0.5 * log((ap * bm) / (am * bp));
+    double cr = a[1] * b[2] - a[2] * b[1];
+    double dt = a[1] * b[1] + a[2] * b[2];
+    double dphi = atan2(fabs(cr), dt);
+    return dy * dy + dphi * dphi;
+}
+
+// ---------------------------------------------------------------- PDF
+// One beam's density at fixed mu_F^2, collapsed on the host to a single row of
+// x f values over ln x knots (the ln Q^2 Hermite weights folded in) together
+// with that row's knot slopes.  Cubic Hermite in ln x; returns f = (x f) / x.
+MF_DEV double pdf_eval(const double *row, const double *slope, int nx, double a0, double h,
+                       double ln_x, double x) {
+    double s = (ln_x - a0) / h;
+    int i = (int)floor(s);
+    if (i < 0) i = 0;
+    if (i > nx - 2) i = nx - 2;
+    double t = s - i;
+    double t2 = t * t, t3 = t2 * t;
+    double v = (2.0 * t3 - 3.0 * t2 + 1.0) * row[i] + (t3 - 2.0 * t2 + t) * h * slope[i]
+             + (-2.0 * t3 + 3.0 * t2) * row[i + 1] + (t3 - t2) * h * slope[i + 1];
+    return v / x;
+}
+
+}  // namespace mf

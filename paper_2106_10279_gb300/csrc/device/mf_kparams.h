@@ -1,0 +1,33 @@
+// Kernel parameter block of the generated process kernel, shared verbatim by
+// the host library (C++) and the run-time compiled device code, so that both
+// sides agree on the layout.  Passed by value to the kernel.
+#pragma once
+
+#define MF_KP_MAX_HEL 256
+
+struct mf_kparams {
+    int64_t n;                 // events
+    int32_t mode;              // 0: integrand of given points, 1: Vegas,
+                               // 2: per-helicity |M|^2 of given points into f[h][n]
+    int32_t nhel;              // helicity rows in hel[]
+    int32_t nhel_pow2;         // a power of two >= nhel (pairwise-sum padding)
+    int32_t nb;                // Vegas bins per dimension
+    const double *x;           // modes 0, 2: points, SoA [NDIM][n]
+    double *f;                 // mode 0: f [n]; mode 2: [nhel][n]
+    const double *grid;        // mode 1: edges [NDIM][nb+1]
+    double *w_out;             // mode 1: w = f J_V [n]
+    uint8_t *bins_out;         // mode 1: bin indices, SoA [NDIM][n]
+    uint64_t seed, iteration, subprocess;
+    double S;                  // collider energy squared
+    double ln_tau_min;         // ln((sum of final masses)^2 / S)
+    double w0_const;           // massless phase-space volume / s-hat^(n-2)
+    double pref_const;         // averaging x GeV^-2 -> pb / 2 (flux 1/(2 s-hat))
+    double pt_min2, dr_min2;   // cuts
+    double pdf_a0, pdf_h;      // first ln-x knot and spacing
+    int32_t pdf_nx;
+    int32_t pad1;
+    const double *pdf_rows;    // [2 beams][2: values, slopes][pdf_nx]
+    double masses[8];
+    double couplings[16];      // 8 complex couplings (re, im)
+    int8_t hel[MF_KP_MAX_HEL][8];
+};

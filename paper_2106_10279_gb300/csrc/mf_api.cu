@@ -1,0 +1,856 @@
+// C entry points of libmadflow_gb and the statically compiled kernels of the
+// Vegas iteration (accumulation, fixed-order reduction, refinement and the
+// combination of iterations; Sec. 2.2 and Lepage 1978).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mf_internal.h"
+
+// ----------------------------------------------------------------------------
+// errors
+// ----------------------------------------------------------------------------
+namespace mfi {
+static thread_local std::string g_err;
+void set_error(const std::string &msg) { g_err = msg; }
+mf_status fail(mf_status st, const std::string &msg) {
+    g_err = msg;
+    return st;
+}
+}  // namespace mfi
+
+using mfi::fail;
+
+extern "C" const char *mf_last_error(void) { return mfi::g_err.c_str(); }
+
+#define MF_CUDA(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(e_ == cudaErrorMemoryAllocation ? MF_ENOMEM : MF_ECUDA,            \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));               \
+    } while (0)
+
+namespace {
+
+constexpr int kChunk = 4096;           // events per accumulation chunk (fixed: results
+                                       // do not depend on launch shapes)
+constexpr int kAccThreads = 256;
+constexpr int kRedThreads = 256;
+constexpr double kGeV2pb = 0.3893793721e9;
+constexpr double kPi = 3.14159265358979323846;
+
+// ----------------------------------------------------------------------------
+// PDF table collapse at fixed mu_F^2: cubic Hermite weights in ln Q^2 folded
+// into one row of x f values over the ln x knots, plus that row's knot slopes
+// (central differences, one-sided at the ends).
+// ----------------------------------------------------------------------------
+__global__ void pdf_collapse_kernel(const double *table, int nx, int nq, double b0, double hb,
+                                    double b, double *row, double *slope) {
+    // interval j of ln Q^2 and local coordinate t
+    double s = (b - b0) / hb;
+    int j = (int)floor(s);
+    if (j < 0) j = 0;
+    if (j > nq - 2) j = nq - 2;
+    double t = s - j;
+    double t2 = t * t, t3 = t2 * t;
+    double h00 = 2 * t3 - 3 * t2 + 1, h10 = t3 - 2 * t2 + t, h01 = -2 * t3 + 3 * t2, h11 = t3 - t2;
+    // slopes at knots j and j+1 (per unit ln Q^2) are linear in the rows:
+    // D_k = (g_hi - g_lo) / (b_hi - b_lo), lo = max(k-1, 0), hi = min(k+1, nq-1)
+    auto lo = [&](int k) { return k - 1 >= 0 ? k - 1 : k; };
+    auto hi = [&](int k) { return k + 1 <= nq - 1 ? k + 1 : k; };
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        auto g = [&](int k) { return table[(size_t)k * nx + i]; };
+        double d0 = (g(hi(j)) - g(lo(j))) / ((hi(j) - lo(j)) * hb);
+        double d1 = (g(hi(j + 1)) - g(lo(j + 1))) / ((hi(j + 1) - lo(j + 1)) * hb);
+        row[i] = h00 * g(j) + h10 * hb * d0 + h01 * g(j + 1) + h11 * hb * d1;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        int l = i - 1 >= 0 ? i - 1 : i, r = i + 1 <= nx - 1 ? i + 1 : i;
+        slope[i] = (row[r] - row[l]) / (r - l);   // per knot; divided by h on use below
+    }
+}
+
+__global__ void scale_kernel(double *v, int n, double s) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] *= s;
+}
+
+// ----------------------------------------------------------------------------
+// Vegas accumulation: one block per chunk of kChunk events.  Slot layout per
+// chunk: [sum w, sum w^2, nonzero, nan, hist[ndim][nb], counts[ndim][nb]].
+// Non-finite weights count as nan and contribute 0.
+// ----------------------------------------------------------------------------
+__device__ double block_tree_sum(double *buf, int m) {
+    // fixed pairwise tree over kChunk slots (zero padded): pairs (i, i + s)
+    for (int i = m + threadIdx.x; i < kChunk; i += blockDim.x) buf[i] = 0.0;
+    __syncthreads();
+    for (int s = kChunk / 2; s > 0; s >>= 1) {
+        for (int i = threadIdx.x; i < s; i += blockDim.x) buf[i] = buf[i] + buf[i + s];
+        __syncthreads();
+    }
+    double r = buf[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kAccThreads) vegas_accumulate_kernel(const double *w, const uint8_t *bins,
+                                                                       int64_t n, int ndim, int nb, double *slots) {
+    extern __shared__ double sh[];
+    double *sw = sh;                    // [kChunk] sanitised w
+    double *buf = sh + kChunk;          // [kChunk] tree buffer
+    uint8_t *sb = reinterpret_cast<uint8_t *>(buf + kChunk);   // [kChunk]
+    __shared__ double part[4][64];
+    __shared__ double cpart[4][64];
+    __shared__ int s_nz, s_nan;
+    const int64_t base = (int64_t)blockIdx.x * kChunk;
+    const int m = (int)((n - base) < kChunk ? (n - base) : kChunk);
+    const int K = 4 + 2 * ndim * nb;
+    double *slot = slots + (size_t)blockIdx.x * K;
+    if (threadIdx.x == 0) { s_nz = 0; s_nan = 0; }
+    __syncthreads();
+    int nz = 0, nn = 0;
+    for (int i = threadIdx.x; i < kChunk; i += blockDim.x) {
+        double v = 0.0;
+        if (i < m) {
+            v = w[base + i];
+            if (!isfinite(v)) { v = 0.0; ++nn; }
+            if (v != 0.0) ++nz;
+        }
+        sw[i] = v;
+        buf[i] = v;
+    }
+    atomicAdd(&s_nz, nz);
+    atomicAdd(&s_nan, nn);
+    __syncthreads();
+    double s1 = block_tree_sum(buf, m);
+    for (int i = threadIdx.x; i < kChunk; i += blockDim.x) buf[i] = sw[i] * sw[i];
+    __syncthreads();
+    double s2 = block_tree_sum(buf, m);
+    if (threadIdx.x == 0) {
+        slot[0] = s1; slot[1] = s2; slot[2] = (double)s_nz; slot[3] = (double)s_nan;
+    }
+    // per dimension and bin: 4 segments of kChunk/4 events, each summed in event
+    // order by the thread owning (segment, bin), then segments in order
+    const int seg = threadIdx.x / 64, b = threadIdx.x % 64;
+    for (int j = 0; j < ndim; ++j) {
+        for (int i = threadIdx.x; i < kChunk; i += blockDim.x) sb[i] = i < m ? bins[(int64_t)j * n + base + i] : 0xff;
+        __syncthreads();
+        double acc = 0.0, cnt = 0.0;
+        if (b < nb) {
+            const int lo = seg * (kChunk / 4), hi = lo + kChunk / 4;
+            for (int i = lo; i < hi; ++i)
+                if (sb[i] == b) { acc += sw[i] * sw[i]; cnt += 1.0; }
+        }
+        part[seg][b] = acc;
+        cpart[seg][b] = cnt;
+        __syncthreads();
+        if (threadIdx.x < nb) {
+            int q = threadIdx.x;
+            slot[4 + j * nb + q] = (part[0][q] + part[1][q]) + (part[2][q] + part[3][q]);
+            slot[4 + ndim * nb + j * nb + q] = (cpart[0][q] + cpart[1][q]) + (cpart[2][q] + cpart[3][q]);
+        }
+        __syncthreads();
+    }
+}
+
+// fixed-order reduction over chunks: block k sums component k
+__global__ void __launch_bounds__(kRedThreads) vegas_reduce_kernel(const double *slots, int64_t nchunks, int K,
+                                                                   double *tot) {
+    __shared__ double red[kRedThreads];
+    const int k = blockIdx.x;
+    double acc = 0.0;
+    for (int64_t c = threadIdx.x; c < nchunks; c += kRedThreads) acc += slots[(size_t)c * K + k];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) tot[k] = red[0];
+}
+
+// Iteration estimate, the histogram, and the inverse-variance combination of
+// all iterations so far (iterations with zero variance are exact: if any, the
+// result is their mean with zero error).  res: [I, err, sigma, sigma_err,
+// chi2/dof, nonzero, nan].
+__global__ void vegas_finalize_kernel(const double *tot, int64_t n, int ndim, int nb, int it, double *hist,
+                                      long long *count, double *iters, double *res) {
+    for (int i = threadIdx.x; i < ndim * nb; i += blockDim.x) {
+        hist[i] = tot[4 + i];
+        count[i] = (long long)tot[4 + ndim * nb + i];
+    }
+    if (threadIdx.x != 0) return;
+    double N = (double)n;
+    double I = tot[0] / N;
+    double var = (tot[1] / N - I * I) / (N - 1.0);
+    double err = sqrt(var > 0.0 ? var : 0.0);
+    iters[2 * it] = I;
+    iters[2 * it + 1] = err;
+    int nexact = 0;
+    double exact_sum = 0.0;
+    for (int k = 0; k <= it; ++k)
+        if (iters[2 * k + 1] == 0.0) { ++nexact; exact_sum += iters[2 * k]; }
+    double mean, merr, chi2 = 0.0;
+    if (nexact > 0) {
+        mean = exact_sum / nexact;
+        merr = 0.0;
+    } else {
+        double sw = 0.0, swi = 0.0;
+        for (int k = 0; k <= it; ++k) {
+            double wk = 1.0 / (iters[2 * k + 1] * iters[2 * k + 1]);
+            sw += wk;
+            swi += wk * iters[2 * k];
+        }
+        mean = swi / sw;
+        merr = 1.0 / sqrt(sw);
+        if (it > 0) {
+            for (int k = 0; k <= it; ++k) {
+                double d = iters[2 * k] - mean;
+                chi2 += d * d / (iters[2 * k + 1] * iters[2 * k + 1]);
+            }
+            chi2 /= it;
+        }
+    }
+    res[0] = I; res[1] = err; res[2] = mean; res[3] = merr; res[4] = chi2;
+    res[5] = tot[2]; res[6] = tot[3];
+}
+
+// Lepage refinement of every dimension (one thread per dimension).
+__global__ void vegas_refine_kernel(double *grid, const double *hist, int ndim, int nb, int64_t n, double alpha) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ndim) return;
+    double *g = grid + (size_t)j * (nb + 1);
+    const double *d = hist + (size_t)j * nb;
+    double sm[256], comp[256], newe[257];
+    double N = (double)n;
+    for (int i = 0; i < nb; ++i) {
+        double a = d[i] / N;
+        if (i == 0) sm[i] = (a + d[1] / N) / 2.0;
+        else if (i == nb - 1) sm[i] = (d[nb - 2] / N + a) / 2.0;
+        else sm[i] = (d[i - 1] / N + a + d[i + 1] / N) / 3.0;
+    }
+    double tot = 0.0;
+    for (int i = 0; i < nb; ++i) tot += sm[i];
+    if (!(tot > 0.0)) return;
+    double total = 0.0;
+    for (int i = 0; i < nb; ++i) {
+        double r = sm[i] / tot;
+        double c;
+        if (r <= 0.0) c = 0.0;
+        else if (r == 1.0) c = 1.0;
+        else c = pow((r - 1.0) / log(r), alpha);
+        comp[i] = c;
+        total += c;
+    }
+    double per = total / nb;
+    newe[0] = 0.0;
+    double acc = 0.0;
+    int io = -1;
+    for (int k = 1; k < nb; ++k) {
+        double target = k * per;
+        while (acc < target && io < nb - 1) { ++io; acc += comp[io]; }
+        double lo = g[io], hi = g[io + 1];
+        double frac = comp[io] > 0.0 ? (target - (acc - comp[io])) / comp[io] : 1.0;
+        newe[k] = lo + frac * (hi - lo);
+    }
+    newe[nb] = 1.0;
+    for (int i = 0; i <= nb; ++i) g[i] = newe[i];
+}
+
+// ----------------------------------------------------------------------------
+// helpers
+// ----------------------------------------------------------------------------
+uint64_t splitmix64(uint64_t &s) {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+double factorial(int k) {
+    double r = 1.0;
+    for (int i = 2; i <= k; ++i) r *= i;
+    return r;
+}
+
+mf_status ensure_context() {
+    cudaError_t e = cudaFree(nullptr);
+    if (e != cudaSuccess) return fail(MF_ECUDA, std::string("CUDA initialisation: ") + cudaGetErrorString(e));
+    return MF_OK;
+}
+
+size_t smem_bytes(const mf_process &p, int prec, int block) {
+    size_t R = prec == MF_FP64 ? 8 : 4;
+    int nden1 = p.gen.n_den > 0 ? p.gen.n_den : 1;
+    size_t a = (size_t)block * p.n_legs * 4 * R + (size_t)block * nden1 * R;
+    a += (16 - (((size_t)block * nden1 * R) % 16)) % 16;
+    a += (size_t)block * 8 * 2 + (size_t)block * 4 + (block / 32 + 1) * 4;
+    return a;
+}
+
+mf_status compile_precision(mf_process *p, int prec) {
+    mfi::Compiled &k = p->kern[prec];
+    if (k.fn) return MF_OK;
+    k.block = 128;
+    int nhp = 1;
+    while (nhp < (int)(p->hel_all.size() / p->n_legs)) nhp <<= 1;
+    k.ht = nhp < 32 ? nhp : 32;
+    mfi::GenInfo info;
+    p->source[prec] = mfi::generate_source(*p, prec, k.block, k.ht, info);
+    p->gen = info;
+    std::vector<char> cubin;
+    mf_status st = mfi::jit_compile(p->source[prec], prec == MF_FP64 ? "mf_proc_f64.cu" : "mf_proc_mixed.cu", cubin);
+    if (st != MF_OK) return st;
+    k.smem = smem_bytes(*p, prec, k.block);
+    return mfi::load_kernel(cubin, k);
+}
+
+void fill_common(const mf_process &p, mf_kparams &kp) {
+    std::memset(&kp, 0, sizeof kp);
+    kp.S = p.sqrt_s * p.sqrt_s;
+    kp.ln_tau_min = p.ln_tau_min;
+    kp.w0_const = p.w0_const;
+    kp.pref_const = p.pref_const;
+    kp.pt_min2 = p.pt_min * p.pt_min;
+    kp.dr_min2 = p.dr_min * p.dr_min;
+    kp.pdf_a0 = p.pdf_a0;
+    kp.pdf_h = p.pdf_h;
+    kp.pdf_nx = p.pdf_nx;
+    kp.pdf_rows = p.d_pdf_rows;
+    for (size_t i = 0; i < p.masses.size() && i < 8; ++i) kp.masses[i] = p.masses[i];
+    for (size_t i = 0; i < p.couplings.size() && i < 16; ++i) kp.couplings[i] = p.couplings[i];
+}
+
+void set_hel(mf_kparams &kp, const std::vector<int8_t> &hel, int n_legs) {
+    int nh = (int)(hel.size() / n_legs);
+    kp.nhel = nh;
+    int nhp = 1;
+    while (nhp < nh) nhp <<= 1;
+    kp.nhel_pow2 = nhp;
+    for (int h = 0; h < nh; ++h)
+        for (int l = 0; l < n_legs; ++l) kp.hel[h][l] = hel[(size_t)h * n_legs + l];
+}
+
+mf_status launch(mf_process *p, int prec, mf_kparams &kp, cudaStream_t s) {
+    mfi::Compiled &k = p->kern[prec];
+    int64_t ntiles = (kp.n + k.block - 1) / k.block;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int64_t grid = (int64_t)nsm * k.max_blocks_per_sm;
+    if (grid > ntiles) grid = ntiles;
+    if (grid < 1) grid = 1;
+    void *args[] = {&kp};
+    return mfi::launch_kernel(k, (unsigned)grid, args, s);
+}
+
+mf_status validate(const mf_process_desc *d) {
+    if (!d) return fail(MF_EINVAL, "NULL descriptor");
+    if (d->n_legs < 3) return fail(MF_EINVAL, "need at least 3 legs");
+    if (d->n_legs > MF_MAX_LEGS) return fail(MF_EUNSUPPORTED, "too many legs");
+    if (!d->leg_kind || !d->leg_incoming || !d->leg_mass_id || !d->leg_cut)
+        return fail(MF_EINVAL, "leg arrays must be non-NULL");
+    for (int i = 0; i < d->n_legs; ++i) {
+        if (d->leg_kind[i] < 0 || d->leg_kind[i] > 2) return fail(MF_EINVAL, "bad leg kind");
+        if ((i < 2) != (d->leg_incoming[i] != 0)) return fail(MF_EINVAL, "legs 0 and 1 must be the incoming ones");
+        if (d->leg_mass_id[i] < -1 || d->leg_mass_id[i] >= d->n_masses) return fail(MF_EINVAL, "bad leg mass id");
+        if (i < 2 && d->leg_mass_id[i] >= 0 && d->masses[d->leg_mass_id[i]] != 0.0)
+            return fail(MF_EUNSUPPORTED, "incoming legs must be massless");
+        if (d->leg_kind[i] == MF_LEG_VECTOR && d->leg_mass_id[i] >= 0 && d->masses[d->leg_mass_id[i]] != 0.0)
+            return fail(MF_EUNSUPPORTED, "only massless vector bosons");
+    }
+    if (d->n_masses < 0 || d->n_masses > 8 || (d->n_masses > 0 && !d->masses))
+        return fail(MF_EINVAL, "n_masses must be in [0, 8]");
+    if (d->n_couplings < 1 || d->n_couplings > 8 || !d->couplings) return fail(MF_EINVAL, "n_couplings must be in [1, 8]");
+    if (d->n_jamp < 1) return fail(MF_EINVAL, "n_jamp must be positive");
+    if (d->n_jamp > MF_MAX_JAMP) return fail(MF_EUNSUPPORTED, "too many colour flows");
+    if (!d->colour_num || d->colour_den <= 0) return fail(MF_EINVAL, "bad colour matrix");
+    for (int a = 0; a < d->n_jamp; ++a)
+        for (int b = 0; b < d->n_jamp; ++b)
+            if (d->colour_num[a * d->n_jamp + b] != d->colour_num[b * d->n_jamp + a])
+                return fail(MF_EINVAL, "colour matrix must be symmetric");
+    if (d->n_ops < 1 || !d->ops) return fail(MF_EINVAL, "empty program");
+    if (d->n_terms < 0 || (d->n_terms > 0 && !d->terms)) return fail(MF_EINVAL, "bad colour terms");
+    std::vector<int> is_wf(d->n_ops, 0);
+    std::vector<int> leg_seen(d->n_legs, 0);
+    int n_amp = 0;
+    for (int k = 0; k < d->n_ops; ++k) {
+        const mf_op &op = d->ops[k];
+        int nin = 0;
+        switch (op.routine) {
+            case MF_R_IXX: case MF_R_OXX: case MF_R_VXX: nin = 0; break;
+            case MF_R_FFV_FIN: case MF_R_FFV_FOUT: case MF_R_FFV_VEC: case MF_R_VVV_VEC: nin = 2; break;
+            case MF_R_FFV_AMP: case MF_R_VVV_AMP: case MF_R_VVVV1_VEC: case MF_R_VVVV2_VEC: case MF_R_VVVV3_VEC: nin = 3; break;
+            case MF_R_VVVV1_AMP: case MF_R_VVVV2_AMP: case MF_R_VVVV3_AMP: nin = 4; break;
+            default: return fail(MF_EINVAL, "unknown routine in op " + std::to_string(k));
+        }
+        bool ext_r = op.routine <= MF_R_VXX;
+        bool amp_r = op.routine == MF_R_FFV_AMP || op.routine == MF_R_VVV_AMP ||
+                     (op.routine >= MF_R_VVVV1_AMP && op.routine <= MF_R_VVVV3_AMP);
+        if (op.kind == MF_OP_EXT) {
+            if (!ext_r) return fail(MF_EINVAL, "EXT op with a vertex routine");
+            if (op.leg < 0 || op.leg >= d->n_legs || leg_seen[op.leg]) return fail(MF_EINVAL, "bad EXT leg");
+            int want = op.routine == MF_R_IXX ? MF_LEG_FERMION_IN : op.routine == MF_R_OXX ? MF_LEG_FERMION_OUT : MF_LEG_VECTOR;
+            if (d->leg_kind[op.leg] != want) return fail(MF_EINVAL, "EXT routine does not match the leg kind");
+            leg_seen[op.leg] = 1;
+            is_wf[k] = 1;
+        } else if (op.kind == MF_OP_CUR || op.kind == MF_OP_AMP) {
+            if (ext_r || (op.kind == MF_OP_AMP) != amp_r) return fail(MF_EINVAL, "op kind does not match its routine");
+            for (int q = 0; q < 4; ++q) {
+                if (q < nin) {
+                    if (op.in[q] < 0 || op.in[q] >= k || !is_wf[op.in[q]])
+                        return fail(MF_EINVAL, "op " + std::to_string(k) + " reads a missing wavefunction");
+                } else if (op.in[q] != -1) {
+                    return fail(MF_EINVAL, "unused inputs must be -1");
+                }
+            }
+            if (op.coupling < 0 || op.coupling >= d->n_couplings) return fail(MF_EINVAL, "bad coupling index");
+            if (op.kind == MF_OP_CUR) {
+                if (op.mass_id < -1 || op.mass_id >= d->n_masses) return fail(MF_EINVAL, "bad propagator mass id");
+                is_wf[k] = 1;
+            } else {
+                ++n_amp;
+                if (op.first_term < 0 || op.n_terms < 0 || op.first_term + op.n_terms > d->n_terms)
+                    return fail(MF_EINVAL, "bad colour-term range");
+                for (int t = 0; t < op.n_terms; ++t) {
+                    int j = d->terms[op.first_term + t].jamp;
+                    if (j < 0 || j >= d->n_jamp) return fail(MF_EINVAL, "colour term outside the flows");
+                }
+            }
+        } else {
+            return fail(MF_EINVAL, "bad op kind");
+        }
+    }
+    for (int i = 0; i < d->n_legs; ++i)
+        if (!leg_seen[i]) return fail(MF_EINVAL, "every leg needs one EXT op");
+    if (n_amp == 0) return fail(MF_EINVAL, "program has no amplitude");
+    if (d->n_hel < 0 || (d->n_hel > 0 && !d->helicities)) return fail(MF_EINVAL, "bad helicity table");
+    if (d->n_hel > MF_KP_MAX_HEL || (d->n_hel == 0 && (1 << d->n_legs) > MF_KP_MAX_HEL))
+        return fail(MF_EUNSUPPORTED, "too many helicity rows");
+    for (int h = 0; h < d->n_hel * d->n_legs; ++h)
+        if (d->helicities[h] != 1 && d->helicities[h] != -1) return fail(MF_EINVAL, "helicities must be +-1");
+    if (!(d->sqrt_s > 0.0)) return fail(MF_EINVAL, "sqrt_s must be positive");
+    if (!(d->average > 0.0)) return fail(MF_EINVAL, "average must be positive");
+    if (d->pt_min < 0.0 || d->dr_min < 0.0) return fail(MF_EINVAL, "cuts must be non-negative");
+    if (d->hadronic) {
+        if (!d->pdf[0] || !d->pdf[1]) return fail(MF_EINVAL, "hadronic process needs two PDF tables");
+        if (d->pdf_nx < 4 || d->pdf_nq < 4) return fail(MF_EINVAL, "PDF tables need at least 4 knots per axis");
+        if (!(d->pdf_x_min > 0.0 && d->pdf_x_max > d->pdf_x_min && d->pdf_q2_min > 0.0 && d->pdf_q2_max > d->pdf_q2_min))
+            return fail(MF_EINVAL, "bad PDF axes");
+        if (!(d->mu_f2 > 0.0)) return fail(MF_EINVAL, "mu_f2 must be positive");
+    }
+    int nout = d->n_legs - 2;
+    int ndim = 3 * nout - 4 + (d->hadronic ? 2 : 0);
+    if (ndim > MF_MAX_DIM) return fail(MF_EUNSUPPORTED, "too many integration dimensions");
+    return MF_OK;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------
+// process
+// ----------------------------------------------------------------------------
+extern "C" mf_status mf_create_process(const mf_process_desc *d, mf_process **out) {
+    if (!out) return fail(MF_EINVAL, "out is NULL");
+    *out = nullptr;
+    mf_status st = validate(d);
+    if (st != MF_OK) return st;
+    st = ensure_context();
+    if (st != MF_OK) return st;
+    mf_process *p = new (std::nothrow) mf_process();
+    if (!p) return fail(MF_ENOMEM, "host allocation");
+    cudaGetDevice(&p->device);
+    const int n = d->n_legs;
+    p->n_legs = n;
+    p->n_out = n - 2;
+    p->hadronic = d->hadronic ? 1 : 0;
+    p->ndim = 3 * p->n_out - 4 + 2 * p->hadronic;
+    p->leg_kind.assign(d->leg_kind, d->leg_kind + n);
+    p->leg_incoming.assign(d->leg_incoming, d->leg_incoming + n);
+    p->leg_mass_id.assign(d->leg_mass_id, d->leg_mass_id + n);
+    p->leg_cut.assign(d->leg_cut, d->leg_cut + n);
+    p->masses.assign(d->masses, d->masses + d->n_masses);
+    p->ops.assign(d->ops, d->ops + d->n_ops);
+    if (d->n_terms > 0) p->terms.assign(d->terms, d->terms + d->n_terms);
+    p->couplings.assign(d->couplings, d->couplings + 2 * d->n_couplings);
+    p->n_jamp = d->n_jamp;
+    p->colour_num.assign(d->colour_num, d->colour_num + d->n_jamp * d->n_jamp);
+    p->colour_den = d->colour_den;
+    if (d->n_hel > 0) {
+        p->hel_all.assign(d->helicities, d->helicities + (size_t)d->n_hel * n);
+    } else {
+        for (int h = 0; h < (1 << n); ++h)
+            for (int l = 0; l < n; ++l) p->hel_all.push_back((h >> (n - 1 - l)) & 1 ? 1 : -1);
+    }
+    p->average = d->average;
+    p->alpha_s_power = d->alpha_s_power;
+    p->alpha_s = d->alpha_s;
+    p->sqrt_s = d->sqrt_s;
+    p->mu_f2 = d->mu_f2;
+    p->pt_min = d->pt_min;
+    p->dr_min = d->dr_min;
+    // constants of the phase space and weight
+    double msum = 0.0;
+    for (int i = 2; i < n; ++i)
+        if (p->leg_mass_id[i] >= 0) msum += p->masses[p->leg_mass_id[i]];
+    const double S = d->sqrt_s * d->sqrt_s;
+    if (p->hadronic) {
+        if (!(msum > 0.0) || !(msum < d->sqrt_s)) {
+            delete p;
+            return fail(MF_EUNSUPPORTED, "the x1, x2 map needs 0 < sum of final masses < sqrt_s");
+        }
+        p->ln_tau_min = std::log(msum * msum / S);
+    }
+    const int no = p->n_out;
+    p->w0_const = std::pow(2.0 * kPi, 4 - 3 * no) * std::pow(kPi / 2.0, no - 1) / (factorial(no - 1) * factorial(no - 2));
+    p->pref_const = p->average * kGeV2pb / 2.0;
+    // PDF rows at fixed mu_F^2
+    if (p->hadronic) {
+        const int nx = d->pdf_nx, nq = d->pdf_nq;
+        p->pdf_nx = nx;
+        p->pdf_a0 = std::log(d->pdf_x_min);
+        p->pdf_h = (std::log(d->pdf_x_max) - std::log(d->pdf_x_min)) / (nx - 1);
+        double b0 = std::log(d->pdf_q2_min);
+        double hb = (std::log(d->pdf_q2_max) - b0) / (nq - 1);
+        double *d_tab = nullptr;
+        if (cudaMalloc(&p->d_pdf_rows, sizeof(double) * 4 * nx) != cudaSuccess ||
+            cudaMalloc(&d_tab, sizeof(double) * (size_t)nx * nq) != cudaSuccess) {
+            cudaFree(d_tab);
+            mf_destroy_process(p);
+            return fail(MF_ENOMEM, "PDF rows");
+        }
+        for (int b = 0; b < 2; ++b) {
+            cudaMemcpy(d_tab, d->pdf[b], sizeof(double) * (size_t)nx * nq, cudaMemcpyHostToDevice);
+            double *row = p->d_pdf_rows + (size_t)(2 * b) * nx;
+            pdf_collapse_kernel<<<1, 128>>>(d_tab, nx, nq, b0, hb, std::log(d->mu_f2), row, row + nx);
+            scale_kernel<<<1, 128>>>(row + nx, nx, 1.0 / p->pdf_h);
+        }
+        cudaError_t e = cudaDeviceSynchronize();
+        cudaFree(d_tab);
+        if (e != cudaSuccess) {
+            mf_destroy_process(p);
+            return fail(MF_ECUDA, std::string("PDF set-up: ") + cudaGetErrorString(e));
+        }
+    }
+    // compile the double-precision kernel and drop vanishing helicities
+    st = compile_precision(p, MF_FP64);
+    if (st != MF_OK) {
+        std::string msg = mf_last_error();
+        mf_destroy_process(p);
+        return fail(st, msg);
+    }
+    {
+        const int npts = 256;
+        std::vector<double> hx((size_t)p->ndim * npts);
+        uint64_t s = 0x5EEDu;
+        for (auto &v : hx) v = ((splitmix64(s) >> 11) | 1ull) * 0x1p-53;
+        const int nh = (int)(p->hel_all.size() / n);
+        double *dx = nullptr, *df = nullptr;
+        if (cudaMalloc(&dx, sizeof(double) * hx.size()) != cudaSuccess ||
+            cudaMalloc(&df, sizeof(double) * (size_t)nh * npts) != cudaSuccess) {
+            cudaFree(dx);
+            mf_destroy_process(p);
+            return fail(MF_ENOMEM, "helicity filter scratch");
+        }
+        cudaMemcpy(dx, hx.data(), sizeof(double) * hx.size(), cudaMemcpyHostToDevice);
+        cudaMemset(df, 0, sizeof(double) * (size_t)nh * npts);
+        mf_kparams kp;
+        fill_common(*p, kp);
+        set_hel(kp, p->hel_all, n);
+        kp.mode = 2;
+        kp.n = npts;
+        kp.x = dx;
+        kp.f = df;
+        st = launch(p, MF_FP64, kp, nullptr);
+        std::vector<double> hf((size_t)nh * npts);
+        cudaError_t e = cudaMemcpy(hf.data(), df, sizeof(double) * hf.size(), cudaMemcpyDeviceToHost);
+        cudaFree(dx);
+        cudaFree(df);
+        if (st != MF_OK || e != cudaSuccess) {
+            mf_destroy_process(p);
+            return fail(MF_ECUDA, "helicity filter run failed");
+        }
+        bool any = false;
+        for (double v : hf) any |= (v != 0.0);
+        for (int h = 0; h < nh; ++h) {
+            bool keep = !any;
+            for (int i = 0; i < npts && !keep; ++i) keep = hf[(size_t)h * npts + i] != 0.0;
+            if (keep)
+                for (int l = 0; l < n; ++l) p->hel.push_back(p->hel_all[(size_t)h * n + l]);
+        }
+    }
+    *out = p;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_generate_kernel_source(const mf_process_desc *d, mf_precision prec, int32_t compile,
+                                               char *buf, size_t *len) {
+    if (!len) return fail(MF_EINVAL, "len is NULL");
+    if (prec != MF_FP64 && prec != MF_MIXED) return fail(MF_EINVAL, "bad precision");
+    mf_status st = validate(d);
+    if (st != MF_OK) return st;
+    mf_process p;
+    const int n = d->n_legs;
+    p.n_legs = n;
+    p.n_out = n - 2;
+    p.hadronic = d->hadronic ? 1 : 0;
+    p.ndim = 3 * p.n_out - 4 + 2 * p.hadronic;
+    p.leg_kind.assign(d->leg_kind, d->leg_kind + n);
+    p.leg_incoming.assign(d->leg_incoming, d->leg_incoming + n);
+    p.leg_mass_id.assign(d->leg_mass_id, d->leg_mass_id + n);
+    p.leg_cut.assign(d->leg_cut, d->leg_cut + n);
+    p.masses.assign(d->masses, d->masses + d->n_masses);
+    p.ops.assign(d->ops, d->ops + d->n_ops);
+    if (d->n_terms > 0) p.terms.assign(d->terms, d->terms + d->n_terms);
+    p.n_jamp = d->n_jamp;
+    p.colour_num.assign(d->colour_num, d->colour_num + d->n_jamp * d->n_jamp);
+    p.colour_den = d->colour_den;
+    int nh = d->n_hel > 0 ? d->n_hel : (1 << n);
+    int nhp = 1;
+    while (nhp < nh) nhp <<= 1;
+    mfi::GenInfo info;
+    std::string src = mfi::generate_source(p, prec, 128, nhp < 32 ? nhp : 32, info);
+    if (compile) {
+        std::vector<char> cubin;
+        st = mfi::jit_compile(src, prec == MF_FP64 ? "mf_proc_f64.cu" : "mf_proc_mixed.cu", cubin);
+        if (st != MF_OK) return st;
+    }
+    size_t need = src.size() + 1;
+    if (buf && *len >= need) std::memcpy(buf, src.c_str(), need);
+    *len = need;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_destroy_process(mf_process *p) {
+    if (!p) return MF_OK;
+    for (auto &k : p->kern) mfi::unload_kernel(k);
+    if (p->ev_start) cudaEventDestroy(p->ev_start);
+    if (p->ev_stop) cudaEventDestroy(p->ev_stop);
+    cudaFree(p->d_pdf_rows);
+    cudaFree(p->d_w);
+    cudaFree(p->d_bins);
+    delete p;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_process_get_info(const mf_process *p, mf_process_info *info) {
+    if (!p || !info) return fail(MF_EINVAL, "NULL argument");
+    info->ndim = p->ndim;
+    info->n_legs = p->n_legs;
+    info->n_hel = (int)(p->hel.size() / p->n_legs);
+    info->n_hel_all = (int)(p->hel_all.size() / p->n_legs);
+    info->n_jamp = p->n_jamp;
+    info->n_ops = (int)p->ops.size();
+    info->n_den = p->gen.n_den;
+    info->flops_per_hel = p->gen.flops_per_hel;
+    info->flops_kinematics = p->gen.flops_kin;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_process_last_kernel_ms(const mf_process *p, double *ms) {
+    if (!p || !ms) return fail(MF_EINVAL, "NULL argument");
+    *ms = p->last_kernel_ms;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_integrand(mf_process *p, const double *x, int64_t n, double *f, mf_precision prec,
+                                  void *stream) {
+    if (!p) return fail(MF_EINVAL, "NULL process");
+    if (n < 0) return fail(MF_EINVAL, "negative n");
+    if (prec != MF_FP64 && prec != MF_MIXED) return fail(MF_EINVAL, "bad precision");
+    if (n == 0) return MF_OK;
+    if (!x || !f) return fail(MF_EINVAL, "NULL x or f");
+    mf_status st = compile_precision(p, prec);
+    if (st != MF_OK) return st;
+    mf_kparams kp;
+    fill_common(*p, kp);
+    set_hel(kp, p->hel, p->n_legs);
+    kp.mode = 0;
+    kp.n = n;
+    kp.x = x;
+    kp.f = f;
+    return launch(p, prec, kp, (cudaStream_t)stream);
+}
+
+// ----------------------------------------------------------------------------
+// Vegas
+// ----------------------------------------------------------------------------
+extern "C" mf_status mf_vegas_create(int32_t ndim, int32_t nbins, double alpha, mf_vegas **out) {
+    if (!out) return fail(MF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (ndim < 1 || ndim > MF_MAX_DIM) return fail(MF_EINVAL, "ndim out of range");
+    if (nbins < 2 || nbins > 64) return fail(MF_EINVAL, "nbins must be in [2, 64]");
+    if (!(alpha >= 0.0)) return fail(MF_EINVAL, "alpha must be non-negative");
+    mf_status st = ensure_context();
+    if (st != MF_OK) return st;
+    mf_vegas *v = new (std::nothrow) mf_vegas();
+    if (!v) return fail(MF_ENOMEM, "host allocation");
+    cudaGetDevice(&v->device);
+    v->ndim = ndim;
+    v->nbins = nbins;
+    v->alpha = alpha;
+    v->max_iter = 1024;
+    if (cudaMalloc(&v->d_grid, sizeof(double) * ndim * (nbins + 1)) != cudaSuccess ||
+        cudaMalloc(&v->d_hist, sizeof(double) * ndim * nbins) != cudaSuccess ||
+        cudaMalloc(&v->d_count, sizeof(long long) * ndim * nbins) != cudaSuccess ||
+        cudaMalloc(&v->d_hist_iter, sizeof(double) * 2 * v->max_iter) != cudaSuccess ||
+        cudaMalloc(&v->d_result, sizeof(double) * 8) != cudaSuccess) {
+        mf_vegas_destroy(v);
+        return fail(MF_ENOMEM, "Vegas grid");
+    }
+    std::vector<double> g((size_t)ndim * (nbins + 1));
+    for (int j = 0; j < ndim; ++j)
+        for (int i = 0; i <= nbins; ++i) g[(size_t)j * (nbins + 1) + i] = (double)i / nbins;
+    cudaMemcpy(v->d_grid, g.data(), sizeof(double) * g.size(), cudaMemcpyHostToDevice);
+    cudaMemset(v->d_hist, 0, sizeof(double) * ndim * nbins);
+    cudaMemset(v->d_count, 0, sizeof(long long) * ndim * nbins);
+    *out = v;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_vegas_destroy(mf_vegas *v) {
+    if (!v) return MF_OK;
+    cudaFree(v->d_grid);
+    cudaFree(v->d_hist);
+    cudaFree(v->d_count);
+    cudaFree(v->d_hist_iter);
+    cudaFree(v->d_result);
+    cudaFree(v->d_slots);
+    delete v;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_vegas_get_grid(const mf_vegas *v, double *edges) {
+    if (!v || !edges) return fail(MF_EINVAL, "NULL argument");
+    MF_CUDA(cudaMemcpy(edges, v->d_grid, sizeof(double) * v->ndim * (v->nbins + 1), cudaMemcpyDeviceToHost));
+    return MF_OK;
+}
+
+extern "C" mf_status mf_vegas_set_grid(mf_vegas *v, const double *edges) {
+    if (!v || !edges) return fail(MF_EINVAL, "NULL argument");
+    for (int j = 0; j < v->ndim; ++j) {
+        const double *g = edges + (size_t)j * (v->nbins + 1);
+        if (g[0] != 0.0 || g[v->nbins] != 1.0) return fail(MF_EINVAL, "grid edges must run from 0 to 1");
+        for (int i = 0; i < v->nbins; ++i)
+            if (!(g[i + 1] > g[i])) return fail(MF_EINVAL, "grid edges must increase");
+    }
+    MF_CUDA(cudaMemcpy(v->d_grid, edges, sizeof(double) * v->ndim * (v->nbins + 1), cudaMemcpyHostToDevice));
+    return MF_OK;
+}
+
+extern "C" mf_status mf_vegas_get_histogram(const mf_vegas *v, double *sum_w2, int64_t *counts) {
+    if (!v) return fail(MF_EINVAL, "NULL argument");
+    if (sum_w2) MF_CUDA(cudaMemcpy(sum_w2, v->d_hist, sizeof(double) * v->ndim * v->nbins, cudaMemcpyDeviceToHost));
+    if (counts) MF_CUDA(cudaMemcpy(counts, v->d_count, sizeof(long long) * v->ndim * v->nbins, cudaMemcpyDeviceToHost));
+    return MF_OK;
+}
+
+extern "C" mf_status mf_vegas_get_shape(const mf_vegas *v, int32_t *ndim, int32_t *nbins, int32_t *iteration) {
+    if (!v) return fail(MF_EINVAL, "NULL argument");
+    if (ndim) *ndim = v->ndim;
+    if (nbins) *nbins = v->nbins;
+    if (iteration) *iteration = v->iteration;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_vegas_iterate(mf_vegas *const *grids, mf_process *const *procs, const int64_t *n_events,
+                                      int32_t nproc, uint64_t seed, mf_precision prec, int32_t refine,
+                                      mf_iter_result *out, void *stream) {
+    if (nproc < 1 || !grids || !procs || !n_events || !out) return fail(MF_EINVAL, "bad arguments");
+    if (prec != MF_FP64 && prec != MF_MIXED) return fail(MF_EINVAL, "bad precision");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int k = 0; k < nproc; ++k) {
+        if (!grids[k] || !procs[k]) return fail(MF_EINVAL, "NULL grid or process");
+        if (grids[k]->ndim != procs[k]->ndim) return fail(MF_EINVAL, "grid and process dimensions differ");
+        if (n_events[k] < 2) return fail(MF_EINVAL, "need at least two events per iteration");
+        if (grids[k]->iteration >= grids[k]->max_iter) return fail(MF_EUNSUPPORTED, "too many iterations");
+    }
+    std::vector<std::vector<double>> res(nproc, std::vector<double>(8));
+    bool any_nan = false;
+    for (int k = 0; k < nproc; ++k) {
+        mf_process *p = procs[k];
+        mf_vegas *v = grids[k];
+        const int64_t n = n_events[k];
+        mf_status st = compile_precision(p, prec);
+        if (st != MF_OK) return st;
+        if (p->scratch_n < n) {
+            cudaFree(p->d_w);
+            cudaFree(p->d_bins);
+            p->d_w = nullptr;
+            p->d_bins = nullptr;
+            p->scratch_n = 0;
+            MF_CUDA(cudaMalloc(&p->d_w, sizeof(double) * n));
+            MF_CUDA(cudaMalloc(&p->d_bins, (size_t)p->ndim * n));
+            p->scratch_n = n;
+        }
+        const int64_t nchunks = (n + kChunk - 1) / kChunk;
+        const int K = 4 + 2 * v->ndim * v->nbins;
+        if (v->slots_cap < nchunks * K + K) {
+            cudaFree(v->d_slots);
+            v->d_slots = nullptr;
+            v->slots_cap = 0;
+            MF_CUDA(cudaMalloc(&v->d_slots, sizeof(double) * (nchunks * K + K)));
+            v->slots_cap = nchunks * K + K;
+        }
+        mf_kparams kp;
+        fill_common(*p, kp);
+        set_hel(kp, p->hel, p->n_legs);
+        kp.mode = 1;
+        kp.n = n;
+        kp.grid = v->d_grid;
+        kp.nb = v->nbins;
+        kp.w_out = p->d_w;
+        kp.bins_out = p->d_bins;
+        kp.seed = seed;
+        kp.iteration = (uint64_t)v->iteration;
+        kp.subprocess = (uint64_t)k;
+        if (!p->ev_start) {
+            MF_CUDA(cudaEventCreate(&p->ev_start));
+            MF_CUDA(cudaEventCreate(&p->ev_stop));
+        }
+        MF_CUDA(cudaEventRecord(p->ev_start, s));
+        st = launch(p, prec, kp, s);
+        if (st != MF_OK) return st;
+        MF_CUDA(cudaEventRecord(p->ev_stop, s));
+        size_t acc_smem = sizeof(double) * 2 * kChunk + kChunk;
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaFuncSetAttribute(vegas_accumulate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc_smem);
+            attr_set = true;
+        }
+        vegas_accumulate_kernel<<<(unsigned)nchunks, kAccThreads, acc_smem, s>>>(p->d_w, p->d_bins, n, v->ndim,
+                                                                                  v->nbins, v->d_slots);
+        double *tot = v->d_slots + nchunks * K;
+        vegas_reduce_kernel<<<K, kRedThreads, 0, s>>>(v->d_slots, nchunks, K, tot);
+        vegas_finalize_kernel<<<1, 128, 0, s>>>(tot, n, v->ndim, v->nbins, v->iteration, v->d_hist, v->d_count,
+                                                v->d_hist_iter, v->d_result);
+        if (refine) vegas_refine_kernel<<<1, 32, 0, s>>>(v->d_grid, v->d_hist, v->ndim, v->nbins, n, v->alpha);
+        MF_CUDA(cudaGetLastError());
+        MF_CUDA(cudaMemcpyAsync(res[k].data(), v->d_result, sizeof(double) * 7, cudaMemcpyDeviceToHost, s));
+    }
+    MF_CUDA(cudaStreamSynchronize(s));
+    for (int k = 0; k < nproc; ++k) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, procs[k]->ev_start, procs[k]->ev_stop) == cudaSuccess)
+            procs[k]->last_kernel_ms = ms;
+    }
+    for (int k = 0; k < nproc; ++k) {
+        mf_vegas *v = grids[k];
+        out[k].iteration = v->iteration;
+        out[k].n_events = n_events[k];
+        out[k].integral = res[k][0];
+        out[k].error = res[k][1];
+        out[k].sigma = res[k][2];
+        out[k].sigma_error = res[k][3];
+        out[k].chi2_dof = res[k][4];
+        out[k].n_nonzero = (int64_t)res[k][5];
+        out[k].n_nan = (int64_t)res[k][6];
+        any_nan |= out[k].n_nan > 0;
+        v->iteration += 1;
+    }
+    if (any_nan) return fail(MF_ENAN, "some points had non-finite weights (counted as zero)");
+    return MF_OK;
+}

@@ -1,0 +1,105 @@
+// Internal declarations of libmadflow_gb (host side).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/madflow_gb.h"
+#include "device/mf_kparams.h"
+
+namespace mfi {
+
+// thread-local error text
+void set_error(const std::string &msg);
+mf_status fail(mf_status st, const std::string &msg);
+
+struct DenSlot {
+    uint32_t mask;   // legs whose signed momenta sum to the current's momentum
+    int32_t mass_id; // -1 = massless propagator
+};
+
+struct Compiled {
+    CUmodule module = nullptr;
+    CUfunction fn = nullptr;
+    int block = 128;
+    int ht = 32;
+    size_t smem = 0;
+    int max_blocks_per_sm = 1;
+    int regs = 0;
+    size_t local_bytes = 0;
+};
+
+struct GenInfo {
+    int n_den = 0;
+    std::vector<DenSlot> dens;
+    std::vector<int> op_den;     // per op: denominator slot (CUR) or -1
+    double flops_per_hel = 0.0;
+    double flops_kin = 0.0;
+};
+
+}  // namespace mfi
+
+struct mf_process {
+    int device = 0;
+    // deep copy of the descriptor
+    int n_legs = 0, n_out = 0, ndim = 0;
+    std::vector<int32_t> leg_kind, leg_incoming, leg_mass_id, leg_cut;
+    std::vector<double> masses;
+    std::vector<mf_op> ops;
+    std::vector<mf_colour_term> terms;
+    std::vector<double> couplings;
+    int n_jamp = 0;
+    std::vector<int32_t> colour_num;
+    int colour_den = 1;
+    std::vector<int8_t> hel_all;   // [n_hel_all][n_legs]
+    std::vector<int8_t> hel;       // kept after filtering
+    double average = 1.0;
+    int alpha_s_power = 0;
+    double alpha_s = 0.0;
+    double sqrt_s = 0.0;
+    int hadronic = 0;
+    double mu_f2 = 0.0, pt_min = 0.0, dr_min = 0.0;
+    int pdf_nx = 0;
+    double pdf_a0 = 0.0, pdf_h = 0.0;
+    double *d_pdf_rows = nullptr;  // device [2][2][nx]
+    double ln_tau_min = 0.0, w0_const = 0.0, pref_const = 0.0;
+    mfi::GenInfo gen;
+    mfi::Compiled kern[2];         // per mf_precision
+    std::string source[2];
+    // events around the last process-kernel launch of mf_vegas_iterate
+    cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
+    double last_kernel_ms = 0.0;
+    // device scratch of mf_vegas_iterate (grown on demand)
+    double *d_w = nullptr;
+    uint8_t *d_bins = nullptr;
+    int64_t scratch_n = 0;
+};
+
+struct mf_vegas {
+    int device = 0;
+    int ndim = 0, nbins = 0;
+    double alpha = 1.5;
+    int iteration = 0;
+    double *d_grid = nullptr;      // [ndim][nbins+1]
+    double *d_hist = nullptr;      // [ndim][nbins] sum w^2 of the last iteration
+    long long *d_count = nullptr;  // [ndim][nbins]
+    double *d_hist_iter = nullptr; // [max_iter][2]: (I_k, sigma_k)
+    int max_iter = 0;
+    double *d_result = nullptr;    // small result block
+    double *d_slots = nullptr;     // chunk partial sums
+    int64_t slots_cap = 0;
+};
+
+namespace mfi {
+// code generation (mf_codegen.cpp)
+std::string generate_source(const mf_process &p, int precision, int block, int ht, GenInfo &info);
+// run-time compilation (mf_jit.cpp)
+mf_status jit_compile(const std::string &source, const std::string &name, std::vector<char> &cubin);
+mf_status load_kernel(const std::vector<char> &cubin, Compiled &out);
+void unload_kernel(Compiled &k);
+mf_status launch_kernel(const Compiled &k, unsigned grid, void **args, cudaStream_t s);
+}  // namespace mfi

@@ -1,0 +1,167 @@
+// Run-time compilation of the generated process kernels for sm_103a (NVRTC)
+// and loading them through the driver API, whose entry points are resolved at
+// run time (no link-time dependency on the driver library, so the shared
+// object loads on hosts without a GPU).  Compiled images are cached in the
+// directory named by MF_JIT_CACHE (if set), keyed by a hash of the source,
+// the options and the NVRTC version.
+#include <nvrtc.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <fstream>
+#include <mutex>
+#include <sstream>
+
+#include "mf_internal.h"
+
+namespace {
+#include "_embedded_sources.inc"   // kHeaderNames[], kHeaderSources[], kNumHeaders (from build.py)
+
+uint64_t fnv1a(const std::string &s, uint64_t h = 1469598103934665603ull) {
+    for (unsigned char c : s) { h ^= c; h *= 1099511628211ull; }
+    return h;
+}
+
+std::mutex g_jit_mutex;
+}  // namespace
+
+namespace mfi {
+
+mf_status jit_compile(const std::string &source, const std::string &name, std::vector<char> &cubin) {
+    std::lock_guard<std::mutex> lock(g_jit_mutex);
+    std::vector<const char *> opts = {"--gpu-architecture=sm_103a", "--std=c++17", "-lineinfo",
+                                      "--device-as-default-execution-space"};
+    const char *verbose = std::getenv("MF_JIT_VERBOSE");
+    if (verbose && *verbose == '1') opts.push_back("--ptxas-options=-v");
+    int vmaj = 0, vmin = 0;
+    nvrtcVersion(&vmaj, &vmin);
+    std::string key = source;
+    for (auto o : opts) key += o;
+    for (int i = 0; i < kNumHeaders; ++i) key += kHeaderSources[i];
+    key += std::to_string(vmaj) + "." + std::to_string(vmin);
+    char hex[32];
+    std::snprintf(hex, sizeof hex, "%016llx", (unsigned long long)fnv1a(key));
+    const char *dir = std::getenv("MF_JIT_CACHE");
+    std::string path = dir && *dir ? std::string(dir) + "/mf_" + hex + ".cubin" : std::string();
+    if (!path.empty()) {
+        std::ifstream in(path, std::ios::binary);
+        if (in) {
+            cubin.assign(std::istreambuf_iterator<char>(in), std::istreambuf_iterator<char>());
+            if (!cubin.empty()) return MF_OK;
+        }
+    }
+    nvrtcProgram prog;
+    if (nvrtcCreateProgram(&prog, source.c_str(), name.c_str(), kNumHeaders, kHeaderSources, kHeaderNames) !=
+        NVRTC_SUCCESS)
+        return fail(MF_EJIT, "nvrtcCreateProgram failed");
+    nvrtcResult r = nvrtcCompileProgram(prog, (int)opts.size(), opts.data());
+    size_t log_size = 0;
+    nvrtcGetProgramLogSize(prog, &log_size);
+    std::string log(log_size, '\0');
+    if (log_size) nvrtcGetProgramLog(prog, &log[0]);
+    if (r != NVRTC_SUCCESS) {
+        nvrtcDestroyProgram(&prog);
+        return fail(MF_EJIT, "NVRTC compilation of " + name + " failed: " + log);
+    }
+    if (verbose && *verbose == '1') std::fprintf(stderr, "[mf jit] %s\n%s\n", name.c_str(), log.c_str());
+    size_t n = 0;
+    nvrtcGetCUBINSize(prog, &n);
+    cubin.resize(n);
+    nvrtcGetCUBIN(prog, cubin.data());
+    nvrtcDestroyProgram(&prog);
+    if (!path.empty()) {
+        std::string tmp = path + ".tmp" + std::to_string((long long)std::rand());
+        std::ofstream out(tmp, std::ios::binary);
+        out.write(cubin.data(), (std::streamsize)cubin.size());
+        out.close();
+        std::rename(tmp.c_str(), path.c_str());
+    }
+    return MF_OK;
+}
+
+// Driver-API entry points resolved at run time through the runtime (so the
+// library has no link-time dependency on the driver library).
+namespace {
+struct DriverApi {
+    bool ok = false;
+    CUresult (*moduleLoadData)(CUmodule *, const void *) = nullptr;
+    CUresult (*moduleUnload)(CUmodule) = nullptr;
+    CUresult (*moduleGetFunction)(CUfunction *, CUmodule, const char *) = nullptr;
+    CUresult (*funcGetAttribute)(int *, CUfunction_attribute, CUfunction) = nullptr;
+    CUresult (*funcSetAttribute)(CUfunction, CUfunction_attribute, int) = nullptr;
+    CUresult (*occupancy)(int *, CUfunction, int, size_t) = nullptr;
+    CUresult (*launch)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned,
+                       CUstream, void **, void **) = nullptr;
+    CUresult (*errorString)(CUresult, const char **) = nullptr;
+};
+DriverApi g_drv;
+std::mutex g_drv_mutex;
+
+template <typename F>
+bool resolve(const char *name, F &fp) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p)
+        return false;
+    fp = reinterpret_cast<F>(p);
+    return true;
+}
+
+mf_status driver() {
+    std::lock_guard<std::mutex> lock(g_drv_mutex);
+    if (g_drv.ok) return MF_OK;
+    bool ok = resolve("cuModuleLoadData", g_drv.moduleLoadData) && resolve("cuModuleUnload", g_drv.moduleUnload) &&
+              resolve("cuModuleGetFunction", g_drv.moduleGetFunction) &&
+              resolve("cuFuncGetAttribute", g_drv.funcGetAttribute) &&
+              resolve("cuFuncSetAttribute", g_drv.funcSetAttribute) &&
+              resolve("cuOccupancyMaxActiveBlocksPerMultiprocessor", g_drv.occupancy) &&
+              resolve("cuLaunchKernel", g_drv.launch) && resolve("cuGetErrorString", g_drv.errorString);
+    if (!ok) return fail(MF_ECUDA, "cannot resolve the CUDA driver entry points");
+    g_drv.ok = true;
+    return MF_OK;
+}
+
+std::string drv_err(CUresult r) {
+    const char *s = nullptr;
+    if (g_drv.errorString) g_drv.errorString(r, &s);
+    return s ? s : ("CUresult " + std::to_string((int)r));
+}
+}  // namespace
+
+mf_status load_kernel(const std::vector<char> &cubin, Compiled &out) {
+    mf_status st = driver();
+    if (st != MF_OK) return st;
+    CUresult r = g_drv.moduleLoadData(&out.module, cubin.data());
+    if (r != CUDA_SUCCESS) return fail(MF_ECUDA, "cuModuleLoadData: " + drv_err(r));
+    r = g_drv.moduleGetFunction(&out.fn, out.module, "mf_kernel");
+    if (r != CUDA_SUCCESS) return fail(MF_ECUDA, "cuModuleGetFunction: " + drv_err(r));
+    int regs = 0, local = 0;
+    g_drv.funcGetAttribute(&regs, CU_FUNC_ATTRIBUTE_NUM_REGS, out.fn);
+    g_drv.funcGetAttribute(&local, CU_FUNC_ATTRIBUTE_LOCAL_SIZE_BYTES, out.fn);
+    out.regs = regs;
+    out.local_bytes = (size_t)local;
+    if (out.smem > 48 * 1024) {
+        r = g_drv.funcSetAttribute(out.fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)out.smem);
+        if (r != CUDA_SUCCESS) return fail(MF_ECUDA, "cannot reserve dynamic shared memory: " + drv_err(r));
+    }
+    int nb = 0;
+    r = g_drv.occupancy(&nb, out.fn, out.block, out.smem);
+    if (r != CUDA_SUCCESS || nb < 1) return fail(MF_ECUDA, "process kernel cannot be resident on an SM");
+    out.max_blocks_per_sm = nb;
+    return MF_OK;
+}
+
+void unload_kernel(Compiled &k) {
+    if (k.module && g_drv.ok) g_drv.moduleUnload(k.module);
+    k.module = nullptr;
+    k.fn = nullptr;
+}
+
+mf_status launch_kernel(const Compiled &k, unsigned grid, void **args, cudaStream_t s) {
+    CUresult r = g_drv.launch(k.fn, grid, 1, 1, (unsigned)k.block, 1, 1, (unsigned)k.smem, (CUstream)s, args, nullptr);
+    if (r != CUDA_SUCCESS) return fail(MF_ECUDA, "process kernel launch: " + drv_err(r));
+    return MF_OK;
+}
+
+}  // namespace mfi
