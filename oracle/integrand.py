@@ -126,5 +126,8 @@ class Integrand:
                 lum = (self.pdfs[0].f(x1[idx], self.wl.mu_f2) * self.pdfs[1].f(x2[idx], self.wl.mu_f2))
             f[idx] = jx[idx] * w[idx] * lum * msq / (2.0 * s_hat[idx]) * W.GEV2_TO_PB
         if return_parts:
-            return f, dict(p=p, s_hat=s_hat, x1=x1, x2=x2, jx=jx, w=w, keep=keep)
+            kappa = np.ones(N)
+            if self.wl.beams:
+                kappa = (self.pdfs[0].condition(x1, self.wl.mu_f2) + self.pdfs[1].condition(x2, self.wl.mu_f2))
+            return f, dict(p=p, s_hat=s_hat, x1=x1, x2=x2, jx=jx, w=w, keep=keep, pdf_condition=kappa)
         return f

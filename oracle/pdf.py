@@ -105,6 +105,52 @@ class PdfTable:
         t = (b - self.b[j]) / h
         return _hermite(t, h, g[0], g[1], e0, e1)
 
+    def condition(self, x, q2):
+        """Condition number of the interpolated value: the same interpolation
+        with every coefficient and table entry replaced by its absolute value
+        (slopes by (|v_hi| + |v_lo|)/Delta), divided by |x f|, plus the relative
+        sensitivity to a rounding-sized change of ln x.  Two evaluations of
+        the same definition in different operation orders agree to a small
+        multiple of eps times this."""
+        x = np.atleast_1d(np.asarray(x, dtype=np.float64))
+        q2 = np.broadcast_to(np.asarray(q2, dtype=np.float64), x.shape)
+        a, b = np.log(x), np.log(q2)
+        i = self._interval(self.a, a)
+        j = self._interval(self.b, b)
+        idx = np.arange(len(a))
+
+        def absherm(t, h, v0, v1, d0, d1):
+            t2, t3 = t * t, t * t * t
+            return (np.abs(2 * t3 - 3 * t2 + 1) * v0 + np.abs(t3 - 2 * t2 + t) * h * d0
+                    + np.abs(-2 * t3 + 3 * t2) * v1 + np.abs(t3 - t2) * h * d1)
+
+        def absrow(k):
+            row = np.abs(self.v[k])
+            n = self.nx
+            def sl(kk):
+                lo = np.maximum(kk - 1, 0)
+                hi = np.minimum(kk + 1, n - 1)
+                return (row[idx, hi] + row[idx, lo]) / (self.a[hi] - self.a[lo])
+            h = self.a[i + 1] - self.a[i]
+            return absherm((a - self.a[i]) / h, h, row[idx, i], row[idx, i + 1], sl(i), sl(i + 1))
+
+        g = {off: absrow(np.clip(j + off, 0, self.nq - 1)) for off in (-1, 0, 1, 2)}
+
+        def bsl(off):
+            lo = np.clip(j + off - 1, 0, self.nq - 1)
+            hi = np.clip(j + off + 1, 0, self.nq - 1)
+            lo_v = np.choose(np.clip(lo - j + 1, 0, 3), [g[-1], g[0], g[1], g[2]])
+            hi_v = np.choose(np.clip(hi - j + 1, 0, 3), [g[-1], g[0], g[1], g[2]])
+            return (hi_v + lo_v) / (self.b[hi] - self.b[lo])
+        h = self.b[j + 1] - self.b[j]
+        tot = absherm((b - self.b[j]) / h, h, g[0], g[1], bsl(0), bsl(1))
+        val = np.abs(self.xfx(x, q2))
+        # sensitivity to the argument: |d(xf)/d ln x| for a perturbation of
+        # ln x of relative size eps (absolute eps max(|ln x|, 1))
+        d = 1e-6
+        slope = np.abs(self.xfx(x * np.exp(d), q2) - self.xfx(x * np.exp(-d), q2)) / (2 * d)
+        return tot / val + slope * np.maximum(np.abs(a), 1.0) / val
+
     def f(self, x, q2):
         """Number density f(x, Q^2) = (x f) / x."""
         x = np.atleast_1d(np.asarray(x, dtype=np.float64))

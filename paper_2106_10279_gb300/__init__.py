@@ -11,4 +11,5 @@ import os as _os
 _HERE = _os.path.dirname(_os.path.abspath(__file__))
 # compiled process kernels are cached here unless the caller chose a directory
 _os.environ.setdefault("MF_JIT_CACHE", _os.path.join(_HERE, "_build", "jit_cache"))
-_os.makedirs(_os.environ["MF_JIT_CACHE"], exist_ok=True)
+if _os.environ["MF_JIT_CACHE"]:
+    _os.makedirs(_os.environ["MF_JIT_CACHE"], exist_ok=True)

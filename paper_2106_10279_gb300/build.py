@@ -67,8 +67,13 @@ def build(verbose: bool = False, force: bool = False) -> str:
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
     headers += [os.path.join(CSRC, "device", f) for f in os.listdir(os.path.join(CSRC, "device"))]
     headers += [os.path.join(os.path.dirname(HERE), "include", "madflow_gb.h"), inc]
+    lib64 = os.path.join(home, "lib64")
+    if not os.path.isdir(lib64):
+        lib64 = os.path.join(home, "lib")
+    nvrtc = [f for f in sorted(os.listdir(lib64)) if f.startswith("libnvrtc.so.") and f.count(".") == 2]
+    nvrtc_path = os.path.join(lib64, nvrtc[0]) if nvrtc else "libnvrtc.so.13"
     common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-lineinfo", "-I", BUILD, "-I", CSRC,
-              "-I", os.path.join(home, "include")]
+              "-I", os.path.join(home, "include"), f'-DMF_NVRTC_DEFAULT="{nvrtc_path}"']
     objs, jobs = [], []
     for src in SOURCES:
         obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
@@ -83,10 +88,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
             if res.returncode:
                 raise RuntimeError(f"nvcc failed for {cmd[-3]}")
     if force or _stale(LIB, objs):
-        lib64 = os.path.join(home, "lib64")
-        if not os.path.isdir(lib64):
-            lib64 = os.path.join(home, "lib")
-        cmd = [nvcc, *ARCH, "-shared", "-o", LIB, *objs, "-L", lib64, "-lnvrtc", "-cudart", "shared",
+        cmd = [nvcc, *ARCH, "-shared", "-o", LIB, *objs, "-L", lib64, "-ldl", "-cudart", "shared",
                "-Xlinker", f"-rpath={lib64}"]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if verbose or res.returncode:

@@ -41,12 +41,12 @@ template <typename R> MF_DEV cx<R> cfma(cx<R> b, cx<R> c, cx<R> a) {
     return {a.re + b.re * c.re - b.im * c.im, a.im + b.re * c.im + b.im * c.re};
 }
 
-// Wavefunction: four complex components and the momentum flowing into the
-// diagram through the legs it contains (real).
+// Wavefunction: four complex components.  Its momentum (flowing into the
+// diagram through the legs it contains) is a signed sum of external momenta
+// known when the program is generated, and is formed where a routine needs it.
 template <typename R>
 struct W {
     cx<R> c[4];
-    R p[4];
 };
 
 // Minkowski product of two complex 4-vectors, no conjugation.

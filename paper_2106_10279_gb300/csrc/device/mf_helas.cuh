@@ -46,10 +46,9 @@ MF_DEV void omegas(const R *p, R m, R &wm, R &wp) {
 }
 
 // Column spinor (flow-in): u of an incoming particle (anti=0) or v of an
-// outgoing antiparticle (anti=1).  sgn = +1 incoming / -1 outgoing sets the
-// wavefunction's momentum (momentum into the diagram).
+// outgoing antiparticle (anti=1).
 template <typename R>
-MF_DEV W<R> ixx(const R *p, R m, int l, int anti, R sgn) {
+MF_DEV W<R> ixx(const R *p, R m, int l, int anti) {
     W<R> w;
     R wm, wp;
     omegas(p, m, wm, wp);
@@ -63,25 +62,23 @@ MF_DEV W<R> ixx(const R *p, R m, int l, int anti, R sgn) {
         R c = (l > 0) ? -wp : wm, d = (l > 0) ? wm : -wp;      // -l sqrt(E + lP), l sqrt(E - lP)
         w.c[0] = c * c0; w.c[1] = c * c1; w.c[2] = d * c0; w.c[3] = d * c1;
     }
-    for (int k = 0; k < 4; ++k) w.p[k] = sgn * p[k];
     return w;
 }
 
 // Row spinor (flow-out): u-bar of an outgoing particle (anti=0) or v-bar of an
 // incoming antiparticle (anti=1).  psi-bar = psi^dagger gamma^0.
 template <typename R>
-MF_DEV W<R> oxx(const R *p, R m, int l, int anti, R sgn) {
-    W<R> col = ixx(p, m, l, anti, sgn);
+MF_DEV W<R> oxx(const R *p, R m, int l, int anti) {
+    W<R> col = ixx(p, m, l, anti);
     W<R> w;
     w.c[0] = conj(col.c[2]); w.c[1] = conj(col.c[3]);
     w.c[2] = conj(col.c[0]); w.c[3] = conj(col.c[1]);
-    for (int k = 0; k < 4; ++k) w.p[k] = col.p[k];
     return w;
 }
 
-// Massless vector: eps(k, l) for incoming, eps*(k, l) for outgoing (sgn = -1).
+// Massless vector: eps(k, l) for incoming, eps*(k, l) for outgoing.
 template <typename R>
-MF_DEV W<R> vxx(const R *k, int l, R sgn) {
+MF_DEV W<R> vxx(const R *k, int l, int incoming) {
     W<R> w;
     R kx = k[1], ky = k[2], kz = k[3];
     R kt = sqrt(kx * kx + ky * ky);
@@ -91,12 +88,11 @@ MF_DEV W<R> vxx(const R *k, int l, R sgn) {
     else { st = R(0); ct = (kz >= R(0)) ? R(1) : R(-1); cp = R(1); sp = R(0); }
     const R rs2 = R(0.70710678118654752440);
     R lr = R(-l) * rs2;                // -l/sqrt2 times e1
-    R im_sign = (sgn > R(0)) ? R(-1) : R(1);    // -i e2 (incoming), +i e2 (conjugated)
+    R im_sign = incoming ? R(-1) : R(1);    // -i e2 (incoming), +i e2 (conjugated)
     w.c[0] = C<R>(R(0), R(0));
     w.c[1] = C<R>(lr * ct * cp, im_sign * rs2 * (-sp));
     w.c[2] = C<R>(lr * ct * sp, im_sign * rs2 * cp);
     w.c[3] = C<R>(lr * (-st), R(0));
-    for (int q = 0; q < 4; ++q) w.p[q] = sgn * k[q];
     return w;
 }
 
@@ -155,23 +151,22 @@ MF_DEV cx<R> FFV_AMP(const W<R> &row, const W<R> &col, const W<R> &V, cx<R> g) {
     return g * s;
 }
 
+// P: momentum of the new current (into the diagram through its legs)
 template <typename R>
-MF_DEV W<R> FFV_FIN(const W<R> &col, const W<R> &V, cx<R> g, R M, R inv_den) {
+MF_DEV W<R> FFV_FIN(const W<R> &col, const W<R> &V, cx<R> g, R M, R inv_den, const R *P) {
     W<R> w;
-    for (int k = 0; k < 4; ++k) w.p[k] = col.p[k] + V.p[k];
     cx<R> t[4], u[4];
     vslash_col(V.c, col.c, t);
-    qslash_col(w.p, M, t, u);
+    qslash_col(P, M, t, u);
     cx<R> f = mul_i(g) * inv_den;
     for (int k = 0; k < 4; ++k) w.c[k] = f * u[k];
     return w;
 }
 
 template <typename R>
-MF_DEV W<R> FFV_FOUT(const W<R> &row, const W<R> &V, cx<R> g, R M, R inv_den) {
+MF_DEV W<R> FFV_FOUT(const W<R> &row, const W<R> &V, cx<R> g, R M, R inv_den, const R *P) {
     W<R> w;
-    for (int k = 0; k < 4; ++k) w.p[k] = row.p[k] + V.p[k];
-    R q[4] = {-w.p[0], -w.p[1], -w.p[2], -w.p[3]};
+    R q[4] = {-P[0], -P[1], -P[2], -P[3]};
     cx<R> t[4], u[4];
     vslash_row(row.c, V.c, t);
     qslash_row(t, q, M, u);
@@ -183,7 +178,6 @@ MF_DEV W<R> FFV_FOUT(const W<R> &row, const W<R> &V, cx<R> g, R M, R inv_den) {
 template <typename R>
 MF_DEV W<R> FFV_VEC(const W<R> &row, const W<R> &col, cx<R> g, R inv_den) {
     W<R> w;
-    for (int k = 0; k < 4; ++k) w.p[k] = row.p[k] + col.p[k];
     const cx<R> *a = row.c, *s = col.c;
     cx<R> j0 = a[0] * s[2] + a[1] * s[3] + a[2] * s[0] + a[3] * s[1];
     cx<R> j1 = a[0] * s[3] + a[1] * s[2] - a[2] * s[1] - a[3] * s[0];
@@ -194,13 +188,15 @@ MF_DEV W<R> FFV_VEC(const W<R> &row, const W<R> &col, cx<R> g, R inv_den) {
     return w;
 }
 
+// kA, kB, kC: momenta into the vertex along A, B, C
 template <typename R>
-MF_DEV cx<R> VVV_AMP(const W<R> &A, const W<R> &B, const W<R> &Cv, cx<R> g) {
+MF_DEV cx<R> VVV_AMP(const W<R> &A, const W<R> &B, const W<R> &Cv, const R *kA, const R *kB, const R *kC,
+                     cx<R> g) {
     R d12[4], d23[4], d31[4];
     for (int k = 0; k < 4; ++k) {
-        d12[k] = A.p[k] - B.p[k];
-        d23[k] = B.p[k] - Cv.p[k];
-        d31[k] = Cv.p[k] - A.p[k];
+        d12[k] = kA[k] - kB[k];
+        d23[k] = kB[k] - kC[k];
+        d31[k] = kC[k] - kA[k];
     }
     cx<R> r = mdot(A.c, B.c) * mdot(d12, Cv.c);
     r = cfma(mdot(B.c, Cv.c), mdot(d23, A.c), r);
@@ -209,15 +205,14 @@ MF_DEV cx<R> VVV_AMP(const W<R> &A, const W<R> &B, const W<R> &Cv, cx<R> g) {
 }
 
 template <typename R>
-MF_DEV W<R> VVV_VEC(const W<R> &A, const W<R> &B, cx<R> g, R inv_den) {
+MF_DEV W<R> VVV_VEC(const W<R> &A, const W<R> &B, const R *kA, const R *kB, cx<R> g, R inv_den) {
     W<R> w;
     R d12[4], d23[4], d31[4];
     for (int k = 0; k < 4; ++k) {
-        w.p[k] = A.p[k] + B.p[k];
         // k3 = -(kA + kB):  kB - k3 = kA + 2 kB,  k3 - kA = -2 kA - kB
-        d12[k] = A.p[k] - B.p[k];
-        d23[k] = A.p[k] + R(2) * B.p[k];
-        d31[k] = -R(2) * A.p[k] - B.p[k];
+        d12[k] = kA[k] - kB[k];
+        d23[k] = kA[k] + R(2) * kB[k];
+        d31[k] = -R(2) * kA[k] - kB[k];
     }
     cx<R> ab = mdot(A.c, B.c);
     cx<R> fb = mdot(d23, A.c);
@@ -244,7 +239,6 @@ MF_DEV cx<R> VVVV_AMP(const W<R> &A, const W<R> &B, const W<R> &Cv, const W<R> &
 template <typename R, int S>
 MF_DEV W<R> VVVV_VEC(const W<R> &A, const W<R> &B, const W<R> &Cv, cx<R> g, R inv_den) {
     W<R> w;
-    for (int k = 0; k < 4; ++k) w.p[k] = A.p[k] + B.p[k] + Cv.p[k];
     cx<R> f = mul_mi(g) * inv_den;
     cx<R> x, y;
     const W<R> *X, *Y;

@@ -67,14 +67,15 @@ MF_DEV void kernel_body(const KParams &kp) {
     if (kp.mode == 1) {
         for (int i = tid; i < NDIM * (kp.nb + 1); i += BLOCK) s_grid[i] = kp.grid[i];
     }
-    __syncthreads();
 
-    R mass_r[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) mass_r[i] = (R)kp.masses[i];
-    cx<R> cpl[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) cpl[i] = C<R>((R)kp.couplings[2 * i], (R)kp.couplings[2 * i + 1]);
+    // couplings and masses in the matrix-element precision, in shared memory
+    __shared__ cx<R> cpl[8];
+    __shared__ R mass_r[8];
+    if (tid < 8) {
+        mass_r[tid] = (R)kp.masses[tid];
+        cpl[tid] = C<R>((R)kp.couplings[2 * tid], (R)kp.couplings[2 * tid + 1]);
+    }
+    __syncthreads();
 
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t e = tile * BLOCK + tid;
@@ -188,16 +189,12 @@ MF_DEV void kernel_body(const KParams &kp) {
                 ps.init();
                 if (slot < npass) {
                     const int ev = s_list[slot];
-                    R mom[NLEG][4];
-#pragma unroll
-                    for (int i = 0; i < NLEG; ++i)
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) mom[i][q] = s_mom[ev * NLEG * 4 + 4 * i + q];
+                    const R *ms = s_mom + ev * NLEG * 4;
                     const R *idn = s_den + ev * NDEN1;
                     for (int k = 0; k < per; ++k) {
                         const int h = sub * per + k;
                         double v = 0.0;
-                        if (h < kp.nhel) v = (double)helicity_msq<R>(mom, idn, kp.hel[h], cpl, mass_r);
+                        if (h < kp.nhel) v = (double)helicity_msq<R>(ms, idn, kp.hel[h], cpl, mass_r);
                         if (kp.mode == 2 && h < kp.nhel) kp.f[(int64_t)h * kp.n + tile * BLOCK + ev] = v;
                         ps.add(v);
                     }

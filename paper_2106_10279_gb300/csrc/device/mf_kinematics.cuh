@@ -48,7 +48,8 @@ MF_DEV XMap xmap(double y0, double y1, double ln_tau_min) {
     m.ln_x1 = y1 * ln_tau;
     m.x1 = exp(m.ln_x1);
     m.x2 = m.tau / m.x1;
-    m.ln_x2 = ln_tau - m.ln_x1;
+    // ln x2 = (1 - y1) ln tau: no cancellation when x2 -> 1
+    m.ln_x2 = (1.0 - y1) * ln_tau;
     m.jac = m.tau * (-ln_tau_min) * (-ln_tau);
     return m;
 }

@@ -3,7 +3,9 @@
 // in registers and every routine is inlined.  This replaces the paper's
 // exporter to TensorFlow (Sec. 2.2) with specialisation at run time.
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
+#include <functional>
 #include <map>
 #include <sstream>
 
@@ -76,14 +78,14 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
     o << "namespace proc {\n";
     o << "constexpr int NLEG = " << n << ", NOUT = " << p.n_out << ", NDIM = " << p.ndim
       << ", NJAMP = " << p.n_jamp << ", NDEN = " << info.n_den << ", HADRONIC = " << p.hadronic << ";\n";
-    o << "constexpr int LEG_MASS_ID[NLEG] = {";
+    o << "__device__ constexpr int LEG_MASS_ID[NLEG] = {";
     for (int i = 0; i < n; ++i) o << (i ? ", " : "") << p.leg_mass_id[i];
     o << "};\n";
     std::vector<int> cuts;
     for (int i = 0; i < n; ++i)
         if (p.leg_cut[i] && !p.leg_incoming[i]) cuts.push_back(i);
     o << "constexpr int NCUT = " << cuts.size() << ";\n";
-    o << "constexpr int CUT_LEGS[" << (cuts.empty() ? 1 : cuts.size()) << "] = {";
+    o << "__device__ constexpr int CUT_LEGS[" << (cuts.empty() ? 1 : cuts.size()) << "] = {";
     if (cuts.empty()) o << "0";
     for (size_t i = 0; i < cuts.size(); ++i) o << (i ? ", " : "") << cuts[i];
     o << "};\n";
@@ -124,55 +126,154 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
     o << "}\n";
 
     // --- the program for one helicity
-    o << "template <typename R>\n"
-         "MF_DEV R helicity_msq(const R (*mom)[4], const R *__restrict__ idn, const int8_t *hel,\n"
-         "                      const mf::cx<R> *cpl, const R *mass) {\n"
-         "  using namespace mf;\n";
+    // momentum into the diagram through the legs of a mask, component q
+    auto mom = [&](uint32_t m, const std::string &name) {
+        std::ostringstream e;
+        e << "    const R " << name << "[4] = {";
+        for (int q = 0; q < 4; ++q) {
+            bool first = true;
+            for (int l = 0; l < n; ++l)
+                if (m >> l & 1) {
+                    bool plus = p.leg_incoming[l] != 0;
+                    e << (first ? (plus ? "" : "-") : (plus ? " + " : " - ")) << "ms[" << 4 * l + q << "]";
+                    first = false;
+                }
+            e << (q < 3 ? ", " : "};\n");
+        }
+        return e.str();
+    };
+    // amplitude order: greedy, the amplitude needing the fewest wavefunctions
+    // not yet computed first (ties: the one releasing most live values), which
+    // keeps the number of live wavefunctions small
+    std::vector<int> amps;
+    for (size_t k = 0; k < p.ops.size(); ++k)
+        if (p.ops[k].kind == MF_OP_AMP) amps.push_back((int)k);
+    std::vector<std::vector<int>> need_wf(p.ops.size());
+    std::function<void(int, std::vector<char> &)> closure = [&](int k, std::vector<char> &seen) {
+        for (int q = 0; q < 4; ++q) {
+            int i = p.ops[k].in[q];
+            if (i >= 0 && !seen[i]) { seen[i] = 1; closure(i, seen); }
+        }
+    };
+    for (int a : amps) {
+        std::vector<char> seen(p.ops.size(), 0);
+        closure(a, seen);
+        for (size_t i = 0; i < seen.size(); ++i)
+            if (seen[i]) need_wf[a].push_back((int)i);
+    }
+    std::vector<int> uses(p.ops.size(), 0);
+    for (auto &op : p.ops)
+        for (int q = 0; q < 4; ++q)
+            if (op.in[q] >= 0) uses[op.in[q]]++;
+    std::vector<char> done(p.ops.size(), 0);
+    std::vector<int> remaining_uses = uses;
+    std::vector<int> order;
+    std::vector<char> taken(p.ops.size(), 0);
+    for (size_t step = 0; step < amps.size(); ++step) {
+        int best = -1, bnew = 0, bfree = 0;
+        for (int a : amps) {
+            if (taken[a]) continue;
+            int nnew = 0;
+            for (int i : need_wf[a]) nnew += !done[i];
+            int nfree = 0;
+            for (int q = 0; q < 4; ++q) {
+                int i = p.ops[a].in[q];
+                if (i >= 0 && done[i] && remaining_uses[i] == 1) ++nfree;
+            }
+            if (best < 0 || nnew < bnew || (nnew == bnew && nfree > bfree)) { best = a; bnew = nnew; bfree = nfree; }
+        }
+        taken[best] = 1;
+        order.push_back(best);
+        for (int i : need_wf[best])
+            if (!done[i]) {
+                done[i] = 1;
+                for (int q = 0; q < 4; ++q)
+                    if (p.ops[i].in[q] >= 0) remaining_uses[p.ops[i].in[q]]--;
+            }
+        for (int q = 0; q < 4; ++q)
+            if (p.ops[best].in[q] >= 0) remaining_uses[p.ops[best].in[q]]--;
+    }
+    // Split the schedule into parts compiled as separate functions: ptxas
+    // falls back to a stack-based allocation for very large functions, so
+    // the program is cut into pieces below a size budget; each part recomputes
+    // the few shared wavefunctions it needs (a few per cent more work).
+    double weight = 0.0;
+    for (auto &op : p.ops) weight += routine_flops(op.routine);
+    if (precision == MF_FP64) weight *= 2.0;
+    int parts = (int)std::ceil(weight / 32000.0);
+    if (const char *e = std::getenv("MF_PROGRAM_PARTS")) parts = std::atoi(e);
+    if (parts < 1) parts = 1;
+    if (parts > (int)order.size()) parts = (int)order.size();
+    info.parts = parts;
+    // emission: each wavefunction just before the first amplitude needing it
     double fl = 0.0;
-    for (size_t k = 0; k < p.ops.size(); ++k) {
+    auto M = [&](int id) { return id >= 0 ? "mass[" + std::to_string(id) + "]" : std::string("R(0)"); };
+    std::function<void(int)> emit_wf = [&](int k) {
+        if (done[k]) return;
         const mf_op &op = p.ops[k];
+        for (int q = 0; q < 4; ++q)
+            if (op.in[q] >= 0) emit_wf(op.in[q]);
+        done[k] = 1;
         fl += routine_flops(op.routine);
-        auto M = [&](int id) { return id >= 0 ? "mass[" + std::to_string(id) + "]" : std::string("R(0)"); };
         if (op.kind == MF_OP_EXT) {
             int l = op.leg;
-            const char *sg = p.leg_incoming[l] ? "R(1)" : "R(-1)";
             if (op.routine == MF_R_VXX) {
-                o << "  const W<R> w" << k << " = vxx<R>(mom[" << l << "], hel[" << l << "], " << sg << ");\n";
+                o << "  const W<R> w" << k << " = vxx<R>(ms + " << 4 * l << ", hel[" << l << "], "
+                  << (p.leg_incoming[l] ? 1 : 0) << ");\n";
             } else {
                 // column: u (incoming particle) or v (outgoing antiparticle);
                 // row: u-bar (outgoing particle) or v-bar (incoming antiparticle)
                 int anti = (op.routine == MF_R_IXX) ? (p.leg_incoming[l] ? 0 : 1) : (p.leg_incoming[l] ? 1 : 0);
-                o << "  const W<R> w" << k << " = " << (op.routine == MF_R_IXX ? "ixx" : "oxx") << "<R>(mom[" << l
-                  << "], " << M(p.leg_mass_id[l]) << ", hel[" << l << "], " << anti << ", " << sg << ");\n";
+                o << "  const W<R> w" << k << " = " << (op.routine == MF_R_IXX ? "ixx" : "oxx") << "<R>(ms + " << 4 * l
+                  << ", " << M(p.leg_mass_id[l]) << ", hel[" << l << "], " << anti << ");\n";
             }
-        } else if (op.kind == MF_OP_CUR) {
-            std::string g = "cpl[" + std::to_string(op.coupling) + "]";
-            std::string den = "idn[" + std::to_string(info.op_den[k]) + "]";
-            o << "  const W<R> w" << k << " = ";
-            switch (op.routine) {
-                case MF_R_FFV_FIN: o << "FFV_FIN<R>(w" << op.in[0] << ", w" << op.in[1] << ", " << g << ", " << M(op.mass_id) << ", " << den << ")"; break;
-                case MF_R_FFV_FOUT: o << "FFV_FOUT<R>(w" << op.in[0] << ", w" << op.in[1] << ", " << g << ", " << M(op.mass_id) << ", " << den << ")"; break;
-                case MF_R_FFV_VEC: o << "FFV_VEC<R>(w" << op.in[0] << ", w" << op.in[1] << ", " << g << ", " << den << ")"; break;
-                case MF_R_VVV_VEC: o << "VVV_VEC<R>(w" << op.in[0] << ", w" << op.in[1] << ", " << g << ", " << den << ")"; break;
-                case MF_R_VVVV1_VEC: case MF_R_VVVV2_VEC: case MF_R_VVVV3_VEC:
-                    o << "VVVV_VEC<R, " << (op.routine - MF_R_VVVV1_VEC + 1) << ">(w" << op.in[0] << ", w" << op.in[1]
-                      << ", w" << op.in[2] << ", " << g << ", " << den << ")";
-                    break;
-                default: o << "/* bad routine */ w0"; break;
-            }
-            o << ";\n";
+            return;
         }
-    }
-    // amplitudes
-    o << "  cx<R> J[NJAMP];\n#pragma unroll\n  for (int k = 0; k < NJAMP; ++k) J[k] = C<R>(R(0), R(0));\n";
-    for (size_t k = 0; k < p.ops.size(); ++k) {
-        const mf_op &op = p.ops[k];
-        if (op.kind != MF_OP_AMP) continue;
         std::string g = "cpl[" + std::to_string(op.coupling) + "]";
-        o << "  { const cx<R> a = ";
+        std::string den = "idn[" + std::to_string(info.op_den[k]) + "]";
+        o << "  W<R> w" << k << ";\n  {\n";
+        switch (op.routine) {
+            case MF_R_FFV_FIN:
+            case MF_R_FFV_FOUT:
+                o << mom(mask[k], "P");
+                o << "    w" << k << " = " << (op.routine == MF_R_FFV_FIN ? "FFV_FIN" : "FFV_FOUT") << "<R>(w"
+                  << op.in[0] << ", w" << op.in[1] << ", " << g << ", " << M(op.mass_id) << ", " << den << ", P);\n";
+                break;
+            case MF_R_FFV_VEC:
+                o << "    w" << k << " = FFV_VEC<R>(w" << op.in[0] << ", w" << op.in[1] << ", " << g << ", " << den << ");\n";
+                break;
+            case MF_R_VVV_VEC:
+                o << mom(mask[op.in[0]], "kA") << mom(mask[op.in[1]], "kB");
+                o << "    w" << k << " = VVV_VEC<R>(w" << op.in[0] << ", w" << op.in[1] << ", kA, kB, " << g << ", "
+                  << den << ");\n";
+                break;
+            default:
+                o << "    w" << k << " = VVVV_VEC<R, " << (op.routine - MF_R_VVVV1_VEC + 1) << ">(w" << op.in[0]
+                  << ", w" << op.in[1] << ", w" << op.in[2] << ", " << g << ", " << den << ");\n";
+                break;
+        }
+        o << "  }\n";
+    };
+    for (int part = 0; part < parts; ++part) {
+    std::fill(done.begin(), done.end(), 0);
+    const size_t lo = order.size() * part / parts, hi = order.size() * (part + 1) / parts;
+    o << "template <typename R>\n" << (parts > 1 ? "__device__ __noinline__" : "MF_DEV") << " void program_part" << part
+      << "(const R *__restrict__ ms, const R *__restrict__ idn, const int8_t *__restrict__ hel,\n"
+         "    const mf::cx<R> *__restrict__ cpl, const R *__restrict__ mass, mf::cx<R> *__restrict__ J) {\n"
+         "  using namespace mf;\n";
+    for (size_t oi = lo; oi < hi; ++oi) {
+        const int k = order[oi];
+        const mf_op &op = p.ops[k];
+        for (int q = 0; q < 4; ++q)
+            if (op.in[q] >= 0) emit_wf(op.in[q]);
+        fl += routine_flops(op.routine);
+        std::string g = "cpl[" + std::to_string(op.coupling) + "]";
+        o << "  {\n";
+        if (op.routine == MF_R_VVV_AMP) o << mom(mask[op.in[0]], "kA") << mom(mask[op.in[1]], "kB") << mom(mask[op.in[2]], "kC");
+        o << "    const cx<R> a = ";
         switch (op.routine) {
             case MF_R_FFV_AMP: o << "FFV_AMP<R>(w" << op.in[0] << ", w" << op.in[1] << ", w" << op.in[2] << ", " << g << ")"; break;
-            case MF_R_VVV_AMP: o << "VVV_AMP<R>(w" << op.in[0] << ", w" << op.in[1] << ", w" << op.in[2] << ", " << g << ")"; break;
+            case MF_R_VVV_AMP: o << "VVV_AMP<R>(w" << op.in[0] << ", w" << op.in[1] << ", w" << op.in[2] << ", kA, kB, kC, " << g << ")"; break;
             default:
                 o << "VVVV_AMP<R, " << (op.routine - MF_R_VVVV1_AMP + 1) << ">(w" << op.in[0] << ", w" << op.in[1]
                   << ", w" << op.in[2] << ", w" << op.in[3] << ", " << g << ")";
@@ -192,6 +293,14 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
         }
         o << "  }\n";
     }
+    o << "}\n";
+    }
+    o << "template <typename R>\n"
+         "MF_DEV R helicity_msq(const R *__restrict__ ms, const R *__restrict__ idn, const int8_t *hel,\n"
+         "                      const mf::cx<R> *cpl, const R *mass) {\n"
+         "  using namespace mf;\n"
+         "  cx<R> J[NJAMP];\n#pragma unroll\n  for (int k = 0; k < NJAMP; ++k) J[k] = C<R>(R(0), R(0));\n";
+    for (int part = 0; part < parts; ++part) o << "  program_part" << part << "<R>(ms, idn, hel, cpl, mass, J);\n";
     // colour sum  sum_kl Re(conj(J_k) C_kl J_l) / den, C symmetric:
     // sum_k Re(conj(J_k) (C_kk J_k + 2 sum_{l>k} C_kl J_l))
     o << "  R m = R(0);\n";

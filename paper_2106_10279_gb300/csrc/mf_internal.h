@@ -39,6 +39,7 @@ struct GenInfo {
     std::vector<int> op_den;     // per op: denominator slot (CUR) or -1
     double flops_per_hel = 0.0;
     double flops_kin = 0.0;
+    int parts = 1;               // functions the helicity program is split into
 };
 
 }  // namespace mfi

@@ -4,6 +4,7 @@
 // object loads on hosts without a GPU).  Compiled images are cached in the
 // directory named by MF_JIT_CACHE (if set), keyed by a hash of the source,
 // the options and the NVRTC version.
+#include <dlfcn.h>
 #include <nvrtc.h>
 
 #include <cstdio>
@@ -23,18 +24,69 @@ uint64_t fnv1a(const std::string &s, uint64_t h = 1469598103934665603ull) {
 }
 
 std::mutex g_jit_mutex;
+
+// NVRTC is opened by path with local symbol binding, so that the toolkit's
+// compiler is used even when the process already holds another libnvrtc
+// with the same soname (e.g. one bundled with a Python framework).
+#ifndef MF_NVRTC_DEFAULT
+#define MF_NVRTC_DEFAULT "libnvrtc.so.13"
+#endif
+struct Nvrtc {
+    bool ok = false;
+    std::string path;
+    nvrtcResult (*version)(int *, int *);
+    nvrtcResult (*create)(nvrtcProgram *, const char *, const char *, int, const char *const *, const char *const *);
+    nvrtcResult (*compile)(nvrtcProgram, int, const char *const *);
+    nvrtcResult (*log_size)(nvrtcProgram, size_t *);
+    nvrtcResult (*log)(nvrtcProgram, char *);
+    nvrtcResult (*cubin_size)(nvrtcProgram, size_t *);
+    nvrtcResult (*cubin)(nvrtcProgram, char *);
+    nvrtcResult (*destroy)(nvrtcProgram *);
+};
+Nvrtc g_nvrtc;
+
+template <typename F>
+bool sym(void *h, const char *name, F &fp) {
+    fp = reinterpret_cast<F>(dlsym(h, name));
+    return fp != nullptr;
+}
+
+bool open_nvrtc(std::string &err) {
+    if (g_nvrtc.ok) return true;
+    const char *env = std::getenv("MF_NVRTC_LIBRARY");
+    const char *cands[] = {env && *env ? env : nullptr, MF_NVRTC_DEFAULT, "libnvrtc.so.13", "libnvrtc.so"};
+    for (const char *c : cands) {
+        if (!c) continue;
+        void *h = dlopen(c, RTLD_NOW | RTLD_LOCAL);
+        if (!h) { err += std::string(dlerror()) + "; "; continue; }
+        Nvrtc n;
+        if (sym(h, "nvrtcVersion", n.version) && sym(h, "nvrtcCreateProgram", n.create) &&
+            sym(h, "nvrtcCompileProgram", n.compile) && sym(h, "nvrtcGetProgramLogSize", n.log_size) &&
+            sym(h, "nvrtcGetProgramLog", n.log) && sym(h, "nvrtcGetCUBINSize", n.cubin_size) &&
+            sym(h, "nvrtcGetCUBIN", n.cubin) && sym(h, "nvrtcDestroyProgram", n.destroy)) {
+            n.ok = true;
+            n.path = c;
+            g_nvrtc = n;
+            return true;
+        }
+        err += std::string(c) + ": missing symbols; ";
+    }
+    return false;
+}
 }  // namespace
 
 namespace mfi {
 
 mf_status jit_compile(const std::string &source, const std::string &name, std::vector<char> &cubin) {
     std::lock_guard<std::mutex> lock(g_jit_mutex);
+    std::string oerr;
+    if (!open_nvrtc(oerr)) return fail(MF_EJIT, "cannot load NVRTC: " + oerr);
     std::vector<const char *> opts = {"--gpu-architecture=sm_103a", "--std=c++17", "-lineinfo",
                                       "--device-as-default-execution-space"};
     const char *verbose = std::getenv("MF_JIT_VERBOSE");
     if (verbose && *verbose == '1') opts.push_back("--ptxas-options=-v");
     int vmaj = 0, vmin = 0;
-    nvrtcVersion(&vmaj, &vmin);
+    g_nvrtc.version(&vmaj, &vmin);
     std::string key = source;
     for (auto o : opts) key += o;
     for (int i = 0; i < kNumHeaders; ++i) key += kHeaderSources[i];
@@ -51,24 +103,25 @@ mf_status jit_compile(const std::string &source, const std::string &name, std::v
         }
     }
     nvrtcProgram prog;
-    if (nvrtcCreateProgram(&prog, source.c_str(), name.c_str(), kNumHeaders, kHeaderSources, kHeaderNames) !=
+    if (g_nvrtc.create(&prog, source.c_str(), name.c_str(), kNumHeaders, kHeaderSources, kHeaderNames) !=
         NVRTC_SUCCESS)
         return fail(MF_EJIT, "nvrtcCreateProgram failed");
-    nvrtcResult r = nvrtcCompileProgram(prog, (int)opts.size(), opts.data());
+    nvrtcResult r = g_nvrtc.compile(prog, (int)opts.size(), opts.data());
     size_t log_size = 0;
-    nvrtcGetProgramLogSize(prog, &log_size);
+    g_nvrtc.log_size(prog, &log_size);
     std::string log(log_size, '\0');
-    if (log_size) nvrtcGetProgramLog(prog, &log[0]);
+    if (log_size) g_nvrtc.log(prog, &log[0]);
     if (r != NVRTC_SUCCESS) {
-        nvrtcDestroyProgram(&prog);
+        g_nvrtc.destroy(&prog);
         return fail(MF_EJIT, "NVRTC compilation of " + name + " failed: " + log);
     }
-    if (verbose && *verbose == '1') std::fprintf(stderr, "[mf jit] %s\n%s\n", name.c_str(), log.c_str());
+    if (verbose && *verbose == '1') std::fprintf(stderr, "[mf jit] %s (NVRTC %d.%d from %s)\n%s\n", name.c_str(), vmaj, vmin,
+                     g_nvrtc.path.c_str(), log.c_str());
     size_t n = 0;
-    nvrtcGetCUBINSize(prog, &n);
+    g_nvrtc.cubin_size(prog, &n);
     cubin.resize(n);
-    nvrtcGetCUBIN(prog, cubin.data());
-    nvrtcDestroyProgram(&prog);
+    g_nvrtc.cubin(prog, cubin.data());
+    g_nvrtc.destroy(&prog);
     if (!path.empty()) {
         std::string tmp = path + ".tmp" + std::to_string((long long)std::rand());
         std::ofstream out(tmp, std::ios::binary);

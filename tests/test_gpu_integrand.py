@@ -1,8 +1,10 @@
 """Parity of the CUDA integrand (mf_integrand, through the C ABI) with the
 oracle, element by element on the same seeded points.
 
-Tolerances: per-event relative error <= 1e-12 in the all-FP64 path; median
-<= 1e-5 and max <= 1e-3 in the mixed path.  Points whose f is zero (cuts,
+Tolerances: per-event relative error <= 1e-12 in the all-FP64 path (plus
+64 eps times the condition number of the two interpolated densities, which is
+O(1) except near x -> 1, where x g ~ (1-x)^5 is a cancellation with a steep
+relative slope); median <= 1e-5 and max <= 1e-3 in the mixed path.  Points whose f is zero (cuts,
 threshold) must be zero on both sides.  Sizes span several 128-event tiles
 with a ragged tail.
 """
@@ -62,6 +64,15 @@ def relerr(got, ref):
     return out
 
 
+EPS = np.finfo(np.float64).eps
+
+
+def fp64_tolerance(oracle, x):
+    """1e-12 plus 64 eps x (condition number of the PDF interpolation)."""
+    f, parts = oracle(x, return_parts=True)
+    return f, 1e-12 + 64 * EPS * parts["pdf_condition"]
+
+
 def _eval(torch, proc, x, prec):
     xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
     f = proc.integrand(xd, prec)
@@ -74,11 +85,12 @@ def test_fp64_parity(torch_cuda, gpu_process, oracle_integrand, name, n):
     wl = W.WORKLOADS[name]
     x = W.uniform_points(wl.ndim, n, 101)
     got = _eval(torch_cuda, gpu_process(name), x, "fp64")
-    ref = oracle_integrand(name)(x)
+    ref, tol = fp64_tolerance(oracle_integrand(name), x)
     assert np.array_equal(got == 0, ref == 0)
     assert np.count_nonzero(ref) > 0.5 * n
     r = relerr(got, ref)
-    assert r.max() <= 1e-12, (name, r.max(), int(np.argmax(r)))
+    assert np.all(r <= tol), (name, r.max(), int(np.argmax(r / tol)))
+    assert np.median(r) <= 1e-13
 
 
 @pytest.mark.parametrize("name,n", CASES)
@@ -98,11 +110,11 @@ def test_edge_points(torch_cuda, gpu_process, oracle_integrand, name):
     wl = W.WORKLOADS[name]
     x = W.edge_points(wl.ndim)
     got = _eval(torch_cuda, gpu_process(name), x, "fp64")
-    ref = oracle_integrand(name)(x)
+    ref, tol = fp64_tolerance(oracle_integrand(name), x)
     assert np.all(np.isfinite(got))
     assert np.array_equal(got == 0, ref == 0)
     r = relerr(got, ref)
-    assert r.max() <= 1e-11, r.max()
+    assert np.all(r <= 10 * tol), r.max()
 
 
 def test_empty_single_and_ragged(torch_cuda, gpu_process, oracle_integrand):
@@ -114,8 +126,8 @@ def test_empty_single_and_ragged(torch_cuda, gpu_process, oracle_integrand):
     for n in (1, 31, 127, 128, 129, 257):
         x = W.uniform_points(4, n, 7 + n)
         got = _eval(torch_cuda, proc, x, "fp64")
-        ref = oracle_integrand("gg_ttx")(x)
-        assert relerr(got, ref).max() <= 1e-12, n
+        ref, tol = fp64_tolerance(oracle_integrand("gg_ttx"), x)
+        assert np.all(relerr(got, ref) <= tol), n
 
 
 def test_bit_reproducible(torch_cuda, gpu_process):
