@@ -190,6 +190,16 @@ mf_status mf_process_get_info(const mf_process *p, mf_process_info *info);
 mf_status mf_integrand(mf_process *p, const double *x, int64_t n, double *f,
                        mf_precision prec, void *stream);
 
+/* mf_helicity_msq (the helicity loop of Sec. 2.3's smatrix, unrolled): for n
+ * points x (device, SoA [ndim][n]) write the colour-summed |M|^2 of every
+ * helicity row of the unfiltered table (rows of 2^n_legs in the order
+ * l_0 l_1 ... with -1 before +1, or the descriptor's rows), without spin or
+ * colour averaging, to out (device [n_hel_all][n]).  Rows of points that fail
+ * the cuts or the threshold are left untouched (callers zero out first).
+ * Asynchronous.  MF_EINVAL for NULL pointers with n > 0 or n < 0. */
+mf_status mf_helicity_msq(mf_process *p, const double *x, int64_t n, double *out,
+                          mf_precision prec, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Vegas (Sec. 2.2; G.P. Lepage, J. Comput. Phys. 27 (1978) 192).              */
 /* ------------------------------------------------------------------------ */

@@ -164,6 +164,14 @@ def mf_integrand(h, x, n: int, f, precision="fp64", stream=None):
                                         _stream_ptr(stream)), "mf_integrand")
 
 
+def mf_helicity_msq(h, x, n: int, out, precision="fp64", stream=None):
+    """x [ndim, n] and out [n_hel_all, n] device tensors (or pointers)."""
+    xp = x if isinstance(x, int) else x.data_ptr()
+    op = out if isinstance(out, int) else out.data_ptr()
+    return L.check(L.lib().mf_helicity_msq(h, C.c_void_p(xp), n, C.c_void_p(op), _PREC[precision],
+                                           _stream_ptr(stream)), "mf_helicity_msq")
+
+
 def mf_vegas_create(ndim: int, nbins: int = 50, alpha: float = 1.5):
     h = C.c_void_p()
     L.check(L.lib().mf_vegas_create(ndim, nbins, alpha, C.byref(h)), "mf_vegas_create")
@@ -246,6 +254,14 @@ class Process:
         f = torch.empty(n, dtype=torch.float64, device=x.device) if out is None else out
         mf_integrand(self.handle, x, n, f, precision, stream)
         return f
+
+    def helicity_msq(self, x, precision="fp64", stream=None):
+        """Colour-summed |M|^2 of every helicity row (unaveraged), [n_hel_all, n]."""
+        import torch
+        n = x.shape[1]
+        out = torch.zeros((self.info["n_hel_all"], n), dtype=torch.float64, device=x.device)
+        mf_helicity_msq(self.handle, x, n, out, precision, stream)
+        return out
 
     def close(self):
         if self.handle:

@@ -675,6 +675,25 @@ extern "C" mf_status mf_integrand(mf_process *p, const double *x, int64_t n, dou
     return launch(p, prec, kp, (cudaStream_t)stream);
 }
 
+extern "C" mf_status mf_helicity_msq(mf_process *p, const double *x, int64_t n, double *out, mf_precision prec,
+                                     void *stream) {
+    if (!p) return fail(MF_EINVAL, "NULL process");
+    if (n < 0) return fail(MF_EINVAL, "negative n");
+    if (prec != MF_FP64 && prec != MF_MIXED) return fail(MF_EINVAL, "bad precision");
+    if (n == 0) return MF_OK;
+    if (!x || !out) return fail(MF_EINVAL, "NULL x or out");
+    mf_status st = compile_precision(p, prec);
+    if (st != MF_OK) return st;
+    mf_kparams kp;
+    fill_common(*p, kp);
+    set_hel(kp, p->hel_all, p->n_legs);
+    kp.mode = 2;
+    kp.n = n;
+    kp.x = x;
+    kp.f = out;
+    return launch(p, prec, kp, (cudaStream_t)stream);
+}
+
 // ----------------------------------------------------------------------------
 // Vegas
 // ----------------------------------------------------------------------------
