@@ -126,8 +126,49 @@ class Integrand:
                 lum = (self.pdfs[0].f(x1[idx], self.wl.mu_f2) * self.pdfs[1].f(x2[idx], self.wl.mu_f2))
             f[idx] = jx[idx] * w[idx] * lum * msq / (2.0 * s_hat[idx]) * W.GEV2_TO_PB
         if return_parts:
-            kappa = np.ones(N)
-            if self.wl.beams:
-                kappa = (self.pdfs[0].condition(x1, self.wl.mu_f2) + self.pdfs[1].condition(x2, self.wl.mu_f2))
-            return f, dict(p=p, s_hat=s_hat, x1=x1, x2=x2, jx=jx, w=w, keep=keep, pdf_condition=kappa)
+            return f, dict(p=p, s_hat=s_hat, x1=x1, x2=x2, jx=jx, w=w, keep=keep,
+                           pdf_condition=self._pdf_condition(x1, x2),
+                           condition=self.condition(p, s_hat, x1, x2))
         return f
+
+    # ------------------------------------------------------------------
+    # condition numbers: how far two correct evaluations of f in different
+    # operation orders can drift apart, in units of eps
+    def _pdf_condition(self, x1, x2):
+        if not self.wl.beams:
+            return np.zeros(len(x1))
+        with np.errstate(invalid="ignore", divide="ignore"):
+            return self.pdfs[0].condition(x1, self.wl.mu_f2) + self.pdfs[1].condition(x2, self.wl.mu_f2)
+
+    def condition(self, p, s_hat, x1, x2):
+        """kappa_pdf + kappa_den + kappa_threshold per event:
+        * PDF interpolation (cancellation and argument sensitivity);
+        * propagator denominators q^2 - M^2 formed from summed components,
+          (q0^2 + |q|^2 + M^2) / |q^2 - M^2|, maximised over every internal line;
+        * production threshold: rs / (rs - sum of final masses), the relative
+          precision of the final-state momenta near threshold."""
+        N = p.shape[0]
+        kp = self._pdf_condition(x1, x2)
+        n = p.shape[1]
+        sign = np.array([1.0 if inc else -1.0 for _, inc in self.proc.legs])
+        masses = []
+        for part, _ in self.proc.legs:
+            kind, flav, _ = PARTICLES[part]
+            masses.append(self.proc.masses.get(flav, 0.0) if kind == "F" else 0.0)
+        kd = np.zeros(N)
+        import itertools
+        for r in range(2, n - 1):
+            for S in itertools.combinations(range(n), r):
+                q = np.sum(sign[list(S)][None, :, None] * p[:, list(S)], axis=1)
+                big = q[:, 0] ** 2 + np.sum(q[:, 1:] ** 2, axis=1)
+                q2 = q[:, 0] ** 2 - np.sum(q[:, 1:] ** 2, axis=1)
+                for M in set([0.0] + [m for m in masses if m > 0]):
+                    with np.errstate(divide="ignore", invalid="ignore"):
+                        c = (big + M * M) / np.abs(q2 - M * M)
+                    kd = np.maximum(kd, np.where(np.isfinite(c), c, 0.0))
+        rs = np.sqrt(s_hat)
+        ms = float(np.sum(self.final_masses))
+        with np.errstate(divide="ignore", invalid="ignore"):
+            kt = np.where(rs > ms, rs / (rs - ms), np.inf) if ms > 0 else np.ones(N)
+        with np.errstate(invalid="ignore"):
+            return kp + kd + kt

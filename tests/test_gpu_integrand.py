@@ -1,10 +1,11 @@
 """Parity of the CUDA integrand (mf_integrand, through the C ABI) with the
 oracle, element by element on the same seeded points.
 
-Tolerances: per-event relative error <= 1e-12 in the all-FP64 path (plus
-64 eps times the condition number of the two interpolated densities, which is
-O(1) except near x -> 1, where x g ~ (1-x)^5 is a cancellation with a steep
-relative slope); median <= 1e-5 and max <= 1e-3 in the mixed path.  Points whose f is zero (cuts,
+Tolerances: per-event relative error <= 1e-12 in the all-FP64 path, plus
+64 eps times the point's condition number computed by the oracle (PDF
+interpolation near x -> 1, propagator denominators q^2 - M^2 near their
+poles, the production threshold), which is O(10) for typical points; median
+<= 1e-5 and max <= 1e-3 in the mixed path.  Points whose f is zero (cuts,
 threshold) must be zero on both sides.  Sizes span several 128-event tiles
 with a ragged tail.
 """
@@ -68,12 +69,12 @@ EPS = np.finfo(np.float64).eps
 
 
 def fp64_tolerance(oracle, x):
-    """1e-12 plus 64 eps x (condition number of the PDF interpolation); where
-    the interpolated density vanishes the condition number is infinite and
-    only the zero pattern is compared."""
+    """1e-12 plus 64 eps x (the oracle's condition number of the point);
+    where it is infinite (a density or the phase space vanishing) only the
+    zero pattern is compared."""
     f, parts = oracle(x, return_parts=True)
     with np.errstate(invalid="ignore"):
-        tol = 1e-12 + 64 * EPS * parts["pdf_condition"]
+        tol = 1e-12 + 64 * EPS * parts["condition"]
     return f, np.where(np.isnan(tol), np.inf, tol)
 
 
@@ -118,7 +119,7 @@ def test_edge_points(torch_cuda, gpu_process, oracle_integrand, name):
     assert np.all(np.isfinite(got))
     assert np.array_equal(got == 0, ref == 0)
     r = relerr(got, ref)
-    assert np.all(r <= 10 * tol), r.max()
+    assert np.all(r <= tol), (r.max(), int(np.argmax(r / tol)))
 
 
 @pytest.mark.parametrize("name,n", [("ee_mumu", 200), ("gg_ttx", 300), ("uux_ttx", 200), ("gg_ttxg", 200),
