@@ -183,23 +183,24 @@ MF_DEV void kernel_body(const KParams &kp) {
             const int sub = tid % HT;
             const int nhp = kp.nhel_pow2;       // padded helicity count (power of two)
             const int per = nhp >= HT ? nhp / HT : 1;   // contiguous helicities per lane
+            // every thread runs the program the same number of times (lanes
+            // without an event or a helicity compute on a valid stand-in and
+            // discard it), so that the program may contain block barriers
             for (int base = 0; base < npass; base += EPR) {
                 const int slot = base + tid / HT;
+                const bool valid = slot < npass;
                 PairSum ps;
                 ps.init();
-                if (slot < npass) {
-                    const int ev = s_list[slot];
-                    const R *ms = s_mom + ev * NLEG * 4;
-                    const R *idn = s_den + ev * NDEN1;
-                    for (int k = 0; k < per; ++k) {
-                        const int h = sub * per + k;
-                        double v = 0.0;
-                        if (h < kp.nhel) v = (double)helicity_msq<R>(ms, idn, kp.hel[h], cpl, mass_r);
-                        if (kp.mode == 2 && h < kp.nhel) kp.f[(int64_t)h * kp.n + tile * BLOCK + ev] = v;
-                        ps.add(v);
-                    }
-                } else {
-                    for (int k = 0; k < per; ++k) ps.add(0.0);
+                const int ev = s_list[valid ? slot : 0];
+                const R *ms = s_mom + ev * NLEG * 4;
+                const R *idn = s_den + ev * NDEN1;
+                for (int k = 0; k < per; ++k) {
+                    const int h = sub * per + k;
+                    const bool hv = h < kp.nhel;
+                    double v = (double)helicity_msq<R>(ms, idn, kp.hel[hv ? h : 0], cpl, mass_r);
+                    if (!(hv && valid)) v = 0.0;
+                    if (kp.mode == 2 && hv && valid) kp.f[(int64_t)h * kp.n + tile * BLOCK + ev] = v;
+                    ps.add(v);
                 }
                 double part = ps.total();
 #pragma unroll

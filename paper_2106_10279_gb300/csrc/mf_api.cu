@@ -3,6 +3,7 @@
 // combination of iterations; Sec. 2.2 and Lepage 1978).
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -298,6 +299,15 @@ mf_status compile_precision(mf_process *p, int prec) {
     int nhp = 1;
     while (nhp < (int)(p->hel_all.size() / p->n_legs)) nhp <<= 1;
     k.ht = nhp < 32 ? nhp : 32;
+    // launch-shape overrides (used by the tuner): block size and lanes per event
+    if (const char *e = std::getenv("MF_BLOCK")) {
+        int b = std::atoi(e);
+        if (b == 64 || b == 128 || b == 256 || b == 512) k.block = b;
+    }
+    if (const char *e = std::getenv("MF_HT")) {
+        int h = std::atoi(e);
+        if (h >= 1 && h <= 32 && (h & (h - 1)) == 0 && h <= nhp) k.ht = h;
+    }
     mfi::GenInfo info;
     p->source[prec] = mfi::generate_source(*p, prec, k.block, k.ht, info);
     p->gen = info;

@@ -75,6 +75,7 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
 
     o << "// generated: diagram program of one process, precision " << R << "\n";
     o << "#include \"mf_common.cuh\"\n#include \"mf_kinematics.cuh\"\n#include \"mf_helas.cuh\"\n";
+    o << "#ifndef MF_PROG_SYNC\n#define MF_PROG_SYNC() __syncthreads()\n#endif\n";
     o << "namespace proc {\n";
     o << "constexpr int NLEG = " << n << ", NOUT = " << p.n_out << ", NDIM = " << p.ndim
       << ", NJAMP = " << p.n_jamp << ", NDEN = " << info.n_den << ", HADRONIC = " << p.hadronic << ";\n";
@@ -205,6 +206,8 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
     if (parts < 1) parts = 1;
     if (parts > (int)order.size()) parts = (int)order.size();
     info.parts = parts;
+    int sync_every = 16;
+    if (const char *e = std::getenv("MF_SYNC_EVERY")) sync_every = std::atoi(e);
     // emission: each wavefunction just before the first amplitude needing it
     double fl = 0.0;
     auto M = [&](int id) { return id >= 0 ? "mass[" + std::to_string(id) + "]" : std::string("R(0)"); };
@@ -259,10 +262,14 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
     const size_t lo = order.size() * part / parts, hi = order.size() * (part + 1) / parts;
     o << "template <typename R>\n" << (parts > 1 ? "__device__ __noinline__" : "MF_DEV") << " void program_part" << part
       << "(const R *__restrict__ ms, const R *__restrict__ idn, const int8_t *__restrict__ hel,\n"
-         "    const mf::cx<R> *__restrict__ cpl, const R *__restrict__ mass, mf::cx<R> *__restrict__ J) {\n"
-         "  using namespace mf;\n";
+         "    const mf::cx<R> *__restrict__ cpl, const R *__restrict__ mass, mf::cx<R> *__restrict__ Jout) {\n"
+         "  using namespace mf;\n"
+         "  cx<R> J[NJAMP];\n#pragma unroll\n  for (int k = 0; k < NJAMP; ++k) J[k] = C<R>(R(0), R(0));\n";
     for (size_t oi = lo; oi < hi; ++oi) {
         const int k = order[oi];
+        // keep the block's warps on the same stretch of code, so that fetched
+        // instructions serve all of them
+        if (sync_every > 0 && oi > lo && (oi - lo) % sync_every == 0) o << "  MF_PROG_SYNC();\n";
         const mf_op &op = p.ops[k];
         for (int q = 0; q < 4; ++q)
             if (op.in[q] >= 0) emit_wf(op.in[q]);
@@ -293,7 +300,7 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
         }
         o << "  }\n";
     }
-    o << "}\n";
+    o << "#pragma unroll\n  for (int k = 0; k < NJAMP; ++k) Jout[k] = Jout[k] + J[k];\n}\n";
     }
     o << "template <typename R>\n"
          "MF_DEV R helicity_msq(const R *__restrict__ ms, const R *__restrict__ idn, const int8_t *hel,\n"
