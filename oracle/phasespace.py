@@ -64,18 +64,34 @@ def _boost_from_rest(p, Q, M):
     return out
 
 
-def _mass_ratio(r, m: int):
-    """Solve m x^(m-1) - (m-1) x^m = r for x in [0, 1] (bisection to the last bit)."""
-    r = np.asarray(r, dtype=np.float64)
-    lo = np.zeros_like(r)
-    hi = np.ones_like(r)
-    for _ in range(200):
+def _bisect(G, target, iters=200):
+    """Root of the increasing function G on [0, 1] with G(root) = target."""
+    lo = np.zeros_like(target)
+    hi = np.ones_like(target)
+    for _ in range(iters):
         mid = 0.5 * (lo + hi)
-        F = m * mid ** (m - 1) - (m - 1) * mid ** m
-        below = F < r
+        below = G(mid) < target
         lo = np.where(below, mid, lo)
         hi = np.where(below, hi, mid)
     return 0.5 * (lo + hi)
+
+
+def _mass_ratio(r, m: int):
+    """Solve F(x) = m x^(m-1) - (m-1) x^m = r for x in [0, 1].
+
+    For r <= 1/2 by bisection on F(x) = r.  For r > 1/2 the root is close to
+    1, where F is flat and F(x) = r fixes 1 - x only to sqrt(eps); there the
+    same equation is solved for d = 1 - x in the form 1 - F(1 - d) = 1 - r,
+    with 1 - F(1 - d) = sum_{k>=2} c_k (-d)^k expanded with exact integer
+    coefficients c_k = (m-1) C(m, k) - m C(m-1, k) (1 - r is exact for
+    r >= 1/2).
+    """
+    r = np.asarray(r, dtype=np.float64)
+    low = _bisect(lambda x: m * x ** (m - 1) - (m - 1) * x ** m, r)
+    coef = [(m - 1) * math.comb(m, k) - m * math.comb(m - 1, k) for k in range(m + 1)]
+    G = lambda d: sum(coef[k] * (-d) ** k for k in range(2, m + 1))
+    high = 1.0 - _bisect(G, 1.0 - r)
+    return np.where(r <= 0.5, low, high)
 
 
 def massless_diet(u, sqrt_s):

@@ -7,6 +7,19 @@
 
 namespace mf {
 
+// keep the double-precision math functions visible next to the overloads
+using ::atan2;
+using ::cos;
+using ::exp;
+using ::fabs;
+using ::floor;
+using ::fmax;
+using ::log;
+using ::pow;
+using ::sin;
+using ::sincos;
+using ::sqrt;
+
 template <int K>
 struct Dual {
     double v;

@@ -107,7 +107,7 @@ MF_DEV void kernel_body(const KParams &kp) {
                 }
             }
             double s_hat = kp.S, jx = 1.0, lum = 1.0;
-            XMap xm;
+            XMap<double> xm;
             const double *u = y;
             if (HADRONIC) {
                 xm = xmap(y[0], y[1], kp.ln_tau_min);

@@ -3,6 +3,7 @@
 // rescaling (Sec. 2.4), cuts and the PDF interpolation (Sec. 1, Fig. 1).
 #pragma once
 #include "mf_common.cuh"
+#include "mf_dual.cuh"
 
 namespace mf {
 
@@ -38,12 +39,15 @@ MF_DEV double vegas_map1(const double *edges, int nb, double y, double &x, int &
 
 // ---------------------------------------------------------------- x1, x2 map
 // tau = tau_min^y0, x1 = tau^y1, x2 = tau / x1, J = tau ln(1/tau_min) ln(1/tau).
+// T is double, or a dual number carrying derivatives (gradient kernel).
+template <typename T>
 struct XMap {
-    double x1, x2, tau, ln_x1, ln_x2, jac;
+    T x1, x2, tau, ln_x1, ln_x2, jac;
 };
-MF_DEV XMap xmap(double y0, double y1, double ln_tau_min) {
-    XMap m;
-    double ln_tau = y0 * ln_tau_min;
+template <typename T>
+MF_DEV XMap<T> xmap(const T &y0, const T &y1, const T &ln_tau_min) {
+    XMap<T> m;
+    T ln_tau = y0 * ln_tau_min;
     m.tau = exp(ln_tau);
     m.ln_x1 = y1 * ln_tau;
     m.x1 = exp(m.ln_x1);
@@ -56,9 +60,10 @@ MF_DEV XMap xmap(double y0, double y1, double ln_tau_min) {
 
 // ---------------------------------------------------------------- phase space
 // Boost p (given in the rest frame of Q, mass M) into the frame of Q.
-MF_DEV void boost_from_rest(const double *p, const double *Q, double M, double *out) {
-    double e = (Q[0] * p[0] + Q[1] * p[1] + Q[2] * p[2] + Q[3] * p[3]) / M;
-    double c = (p[0] + e) / (Q[0] + M);
+template <typename T>
+MF_DEV void boost_from_rest(const T *p, const T *Q, const T &M, T *out) {
+    T e = (Q[0] * p[0] + Q[1] * p[1] + Q[2] * p[2] + Q[3] * p[3]) / M;
+    T c = (p[0] + e) / (Q[0] + M);
     out[0] = e;
     out[1] = p[1] + c * Q[1];
     out[2] = p[2] + c * Q[2];
@@ -105,33 +110,44 @@ MF_DEV double mass_ratio(int m, double r) {
     }
     return x;
 }
+// With derivatives: the root's value from the double solver, its tangent from
+// the implicit function theorem, dx = dr / F'(x), F' = m(m-1) x^(m-2) (1-x).
+template <int K>
+MF_DEV Dual<K> mass_ratio(int m, const Dual<K> &r) {
+    double x = mass_ratio(m, r.v);
+    double xm2 = 1.0;
+    for (int i = 0; i < m - 2; ++i) xm2 *= x;
+    double dF = m * (m - 1) * xm2 * (1.0 - x);
+    return chain(r, x, dF > 0.0 ? 1.0 / dF : 0.0);
+}
 
 // Flat massless n-body momenta in the centre-of-mass frame of energy rs from
 // 3n-4 unit numbers u (per decay step: cos-theta, phi[, mass ratio]).
-template <int N>
-MF_DEV void massless_diet(const double *u, double rs, double p[N][4]) {
-    double Q[4] = {rs, 0.0, 0.0, 0.0};
-    double M = rs;
+template <int N, typename T>
+MF_DEV void massless_diet(const T *u, const T &rs, T p[N][4]) {
+    T Q[4] = {rs, T(0.0), T(0.0), T(0.0)};
+    T M = rs;
     int col = 0;
 #pragma unroll
     for (int k = 0; k < N - 1; ++k) {
-        double cth = 2.0 * u[col] - 1.0;
-        double phi = 6.283185307179586 * u[col + 1];
+        T cth = 2.0 * u[col] - 1.0;
+        T phi = 6.283185307179586 * u[col + 1];
         col += 2;
         int md = N - k - 1;
-        double Mn = 0.0;
+        T Mn = T(0.0);
         if (md >= 2) {
-            double x = mass_ratio(md, u[col]);
+            T x = mass_ratio(md, u[col]);
             col += 1;
             Mn = M * sqrt(x);
         }
-        double e = (M - Mn) * (M + Mn) / (2.0 * M);
-        double sth = sqrt(fmax(0.0, (1.0 - cth) * (1.0 + cth)));
-        double sp, cp;
+        T e = (M - Mn) * (M + Mn) / (2.0 * M);
+        T s2 = (1.0 - cth) * (1.0 + cth);
+        T sth = value(s2) > 0.0 ? sqrt(s2) : T(0.0);
+        T sp, cp;
         sincos(phi, &sp, &cp);
-        double q[4] = {e, e * sth * cp, e * sth * sp, e * cth};
-        double rest[4] = {M - e, -q[1], -q[2], -q[3]};
-        double Qn[4];
+        T q[4] = {e, e * sth * cp, e * sth * sp, e * cth};
+        T rest[4] = {M - e, -q[1], -q[2], -q[3]};
+        T Qn[4];
         boost_from_rest(q, Q, M, p[k]);
         boost_from_rest(rest, Q, M, Qn);
         if (k == N - 2) {
@@ -142,44 +158,76 @@ MF_DEV void massless_diet(const double *u, double rs, double p[N][4]) {
     }
 }
 
-// RAMBO massive rescaling (Kleiss, Stirling, Ellis, CPC 40 (1986) 359): scale
-// the 3-momenta by xi with sum_i sqrt(m_i^2 + xi^2 E_i^2) = rs (Newton), and
-// return the weight factor relative to the massless weight, or 0 below
-// threshold.  p is replaced by the massive momenta.
+// Newton solution of sum_i sqrt(m_i^2 + xi^2 E_i^2) = rs for xi (values only)
 template <int N>
-MF_DEV double massive_rescale(double p[N][4], const double *m, double rs) {
+MF_DEV double rescale_factor(const double *E, const double *m, double rs) {
     double msum = 0.0;
-    bool any = false;
 #pragma unroll
-    for (int i = 0; i < N; ++i) { msum += m[i]; any |= (m[i] != 0.0); }
-    if (!(rs > msum)) return 0.0;
-    if (!any) return 1.0;
+    for (int i = 0; i < N; ++i) msum += m[i];
     double r = msum / rs;
     double xi = sqrt((1.0 - r) * (1.0 + r));
     for (int it = 0; it < 50; ++it) {
         double f = -rs, d = 0.0;
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-            double e = sqrt(m[i] * m[i] + xi * xi * p[i][0] * p[i][0]);
+            double e = sqrt(m[i] * m[i] + xi * xi * E[i] * E[i]);
             f += e;
-            d += xi * p[i][0] * p[i][0] / e;
+            d += xi * E[i] * E[i] / e;
         }
         double step = f / d;
         xi -= step;
         if (fabs(step) <= 1e-15 * xi) break;
     }
-    double sk = 0.0, prod = 1.0, sk2 = 0.0;
+    return xi;
+}
+MF_DEV double rescale_solve(const double *, const double *, double, double xi0, int) { return xi0; }
+// with derivatives: one Newton step from the converged value carries the
+// implicit-function tangent d xi = -dF / F'
+template <int K>
+MF_DEV Dual<K> rescale_solve(const Dual<K> *E, const Dual<K> *m, const Dual<K> &rs, double xi0, int n) {
+    Dual<K> F = -rs;
+    double dF = 0.0;
+    for (int i = 0; i < n; ++i) {
+        Dual<K> e = sqrt(m[i] * m[i] + xi0 * xi0 * E[i] * E[i]);
+        F += e;
+        dF += xi0 * E[i].v * E[i].v / e.v;
+    }
+    Dual<K> xi(xi0);
+    return xi - F * (1.0 / dF);
+}
+
+// RAMBO massive rescaling (Kleiss, Stirling, Ellis, CPC 40 (1986) 359): scale
+// the 3-momenta by xi with sum_i sqrt(m_i^2 + xi^2 E_i^2) = rs (Newton), and
+// return the weight factor relative to the massless weight, or 0 below
+// threshold.  p is replaced by the massive momenta.
+template <int N, typename T>
+MF_DEV T massive_rescale(T p[N][4], const T *m, const T &rs) {
+    double msum = 0.0;
+    bool any = false;
+#pragma unroll
+    for (int i = 0; i < N; ++i) { msum += value(m[i]); any |= (value(m[i]) != 0.0); }
+    if (!(value(rs) > msum)) return T(0.0);
+    if (!any) return T(1.0);
+    double Ev[N], mv[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) { Ev[i] = value(p[i][0]); mv[i] = value(m[i]); }
+    const double xi0 = rescale_factor<N>(Ev, mv, value(rs));
+    T E[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) E[i] = p[i][0];
+    T xi = rescale_solve(E, m, rs, xi0, N);
+    T sk = T(0.0), prod = T(1.0), sk2 = T(0.0);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        double kabs = xi * p[i][0];
-        double k0 = sqrt(m[i] * m[i] + kabs * kabs);
+        T kabs = xi * p[i][0];
+        T k0 = sqrt(m[i] * m[i] + kabs * kabs);
         p[i][0] = k0;
-        p[i][1] *= xi; p[i][2] *= xi; p[i][3] *= xi;
+        p[i][1] = p[i][1] * xi; p[i][2] = p[i][2] * xi; p[i][3] = p[i][3] * xi;
         sk += kabs;
         prod *= kabs / k0;
         sk2 += kabs * kabs / k0;
     }
-    double a = sk / rs, pw = 1.0;
+    T a = sk / rs, pw = T(1.0);
 #pragma unroll
     for (int i = 0; i < 2 * N - 3; ++i) pw *= a;
     return pw * prod * rs / sk2;
@@ -208,16 +256,16 @@ MF_DEV double delta_r2(const double *a, const double *b) {
 // One beam's density at fixed mu_F^2, collapsed on the host to a single row of
 // x f values over ln x knots (the ln Q^2 Hermite weights folded in) together
 // with that row's knot slopes.  Cubic Hermite in ln x; returns f = (x f) / x.
-MF_DEV double pdf_eval(const double *row, const double *slope, int nx, double a0, double h,
-                       double ln_x, double x) {
-    double s = (ln_x - a0) / h;
-    int i = (int)floor(s);
+template <typename T>
+MF_DEV T pdf_eval(const double *row, const double *slope, int nx, double a0, double h, const T &ln_x, const T &x) {
+    T s = (ln_x - a0) / h;
+    int i = (int)floor(value(s));
     if (i < 0) i = 0;
     if (i > nx - 2) i = nx - 2;
-    double t = s - i;
-    double t2 = t * t, t3 = t2 * t;
-    double v = (2.0 * t3 - 3.0 * t2 + 1.0) * row[i] + (t3 - 2.0 * t2 + t) * h * slope[i]
-             + (-2.0 * t3 + 3.0 * t2) * row[i + 1] + (t3 - t2) * h * slope[i + 1];
+    T t = s - (double)i;
+    T t2 = t * t, t3 = t2 * t;
+    T v = (2.0 * t3 - 3.0 * t2 + 1.0) * row[i] + (t3 - 2.0 * t2 + t) * (h * slope[i])
+        + (-2.0 * t3 + 3.0 * t2) * row[i + 1] + (t3 - t2) * (h * slope[i + 1]);
     return v / x;
 }
 

@@ -206,7 +206,7 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
     if (parts < 1) parts = 1;
     if (parts > (int)order.size()) parts = (int)order.size();
     info.parts = parts;
-    int sync_every = 16;
+    int sync_every = 0;
     if (const char *e = std::getenv("MF_SYNC_EVERY")) sync_every = std::atoi(e);
     // emission: each wavefunction just before the first amplitude needing it
     double fl = 0.0;

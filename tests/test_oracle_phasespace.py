@@ -138,3 +138,23 @@ def test_xmap_jacobian_integrates_luminosity_measure():
     assert abs(val / ref - 1) < 1e-9
     assert np.allclose(x1 * x2, tau, rtol=1e-15)
     assert np.all((x1 >= tau_min) & (x1 <= 1) & (x2 >= tau_min) & (x2 <= 1))
+
+
+@pytest.mark.parametrize("m", [2, 3, 4])
+def test_mass_ratio_root_full_precision_near_both_ends(m):
+    # the root of m x^(m-1) - (m-1) x^m = r: the residual of the form solved
+    # must vanish to rounding, including r -> 1 where x -> 1 (measured in
+    # d = 1 - x through 1 - F(1 - d) = 1 - r) and r -> 0
+    r = np.array([1e-14, 1e-9, 0.25, 0.5, 0.75, 1 - 1e-9, 1 - 1e-13])
+    x = ps._mass_ratio(r, m)
+    d = 1.0 - x
+    low = r <= 0.5
+    F = m * x ** (m - 1) - (m - 1) * x ** m
+    G = 1.0 - (m * (1 - d) ** (m - 1) - (m - 1) * (1 - d) ** m)
+    coef = [(m - 1) * math.comb(m, k) - m * math.comb(m - 1, k) for k in range(m + 1)]
+    G = sum(coef[k] * (-d) ** k for k in range(2, m + 1))
+    assert np.all(np.abs(F[low] - r[low]) <= 4e-16 * r[low] + 1e-300)
+    assert np.all(np.abs(G[~low] - (1 - r[~low])) <= 1e-14 * (1 - r[~low]))
+    if m == 2:
+        # closed form x = 1 - sqrt(1 - r), 1 - x = sqrt(1 - r)
+        assert np.allclose(d[~low], np.sqrt(1 - r[~low]), rtol=1e-14, atol=0)
