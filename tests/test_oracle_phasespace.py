@@ -142,19 +142,25 @@ def test_xmap_jacobian_integrates_luminosity_measure():
 
 @pytest.mark.parametrize("m", [2, 3, 4])
 def test_mass_ratio_root_full_precision_near_both_ends(m):
-    # the root of m x^(m-1) - (m-1) x^m = r: the residual of the form solved
-    # must vanish to rounding, including r -> 1 where x -> 1 (measured in
-    # d = 1 - x through 1 - F(1 - d) = 1 - r) and r -> 0
+    # the root of F(x) = m x^(m-1) - (m-1) x^m = r, returned as a double x:
+    # the residual of the form solved must vanish to rounding plus the change
+    # of that residual over one ulp of x, including r -> 1 (x -> 1, measured
+    # in d = 1 - x, exact for x >= 1/2, through 1 - F(1 - d) = 1 - r)
     r = np.array([1e-14, 1e-9, 0.25, 0.5, 0.75, 1 - 1e-9, 1 - 1e-13])
     x = ps._mass_ratio(r, m)
-    d = 1.0 - x
-    low = r <= 0.5
-    F = m * x ** (m - 1) - (m - 1) * x ** m
-    G = 1.0 - (m * (1 - d) ** (m - 1) - (m - 1) * (1 - d) ** m)
+    u = np.spacing(x)
+    F = lambda t: m * t ** (m - 1) - (m - 1) * t ** m
     coef = [(m - 1) * math.comb(m, k) - m * math.comb(m - 1, k) for k in range(m + 1)]
-    G = sum(coef[k] * (-d) ** k for k in range(2, m + 1))
-    assert np.all(np.abs(F[low] - r[low]) <= 4e-16 * r[low] + 1e-300)
-    assert np.all(np.abs(G[~low] - (1 - r[~low])) <= 1e-14 * (1 - r[~low]))
+    G = lambda d: sum(coef[k] * (-d) ** k for k in range(2, m + 1))
+    low = r <= 0.5
+    eps = np.finfo(float).eps
+    res_lo = np.abs(F(x) - r)
+    tol_lo = 4 * eps * r + np.abs(F(x + u) - F(x))
+    assert np.all(res_lo[low] <= tol_lo[low])
+    d = 1.0 - x
+    res_hi = np.abs(G(d) - (1 - r))
+    tol_hi = 4 * eps * (1 - r) + np.abs(G(d + u) - G(d))
+    assert np.all(res_hi[~low] <= tol_hi[~low])
+    # and 1 - x is resolved far beyond sqrt(eps): against the m = 2 closed form
     if m == 2:
-        # closed form x = 1 - sqrt(1 - r), 1 - x = sqrt(1 - r)
-        assert np.allclose(d[~low], np.sqrt(1 - r[~low]), rtol=1e-14, atol=0)
+        assert np.all(np.abs(d[~low] - np.sqrt(1 - r[~low])) <= 2 * u[~low])
