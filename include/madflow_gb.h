@@ -200,6 +200,23 @@ mf_status mf_integrand(mf_process *p, const double *x, int64_t n, double *f,
 mf_status mf_helicity_msq(mf_process *p, const double *x, int64_t n, double *out,
                           mf_precision prec, void *stream);
 
+/* mf_grad: the integrand and its derivatives, all in double precision, for n
+ * points x (device SoA [ndim][n]):
+ *   f          (device [n])       as mf_integrand;
+ *   df_dparam  (device [2][n])    row 0: df/dm_t (m_t = masses[0], entering the
+ *              phase-space masses, the threshold tau_min, spinors and
+ *              propagators; mu_F held fixed), row 1: df/dalpha_s = k f / alpha_s
+ *              (|M|^2 ~ alpha_s^k exactly);
+ *   df_dx      (device [ndim][n], or NULL)  df/dx_j.
+ * Derivatives are exact to rounding: forward tangents through the per-event
+ * kinematics, and the adjoint of the diagram program per helicity (wavefunctions
+ * recomputed in the kernel, nothing stored between helicities).  Points failing
+ * the cuts give f = 0 and zero derivatives; the moving cut boundary is not a
+ * derivative term.  The run-time compiled gradient kernel is built on the
+ * first call.  Asynchronous.  MF_EINVAL for NULL x, f or df_dparam with n > 0. */
+mf_status mf_grad(mf_process *p, const double *x, int64_t n, double *f, double *df_dparam,
+                  double *df_dx, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Vegas (Sec. 2.2; G.P. Lepage, J. Comput. Phys. 27 (1978) 192).              */
 /* ------------------------------------------------------------------------ */

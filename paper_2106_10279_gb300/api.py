@@ -12,7 +12,7 @@ from . import _lib as L
 from .process import ProcessProgram, build_program
 
 MF_FP64, MF_MIXED = L.MF_FP64, L.MF_MIXED
-_PREC = {"fp64": L.MF_FP64, "mixed": L.MF_MIXED, L.MF_FP64: L.MF_FP64, L.MF_MIXED: L.MF_MIXED}
+_PREC = {"fp64": L.MF_FP64, "mixed": L.MF_MIXED, L.MF_FP64: L.MF_FP64, L.MF_MIXED: L.MF_MIXED, "grad": 2}
 
 
 def _arr(ctype, values):
@@ -172,6 +172,13 @@ def mf_helicity_msq(h, x, n: int, out, precision="fp64", stream=None):
                                            _stream_ptr(stream)), "mf_helicity_msq")
 
 
+def mf_grad(h, x, n: int, f, df_dparam, df_dx=None, stream=None):
+    """Device tensors or pointers: x [ndim, n], f [n], df_dparam [2, n], df_dx [ndim, n] or None."""
+    ptr = lambda t: 0 if t is None else (t if isinstance(t, int) else t.data_ptr())
+    return L.check(L.lib().mf_grad(h, C.c_void_p(ptr(x)), n, C.c_void_p(ptr(f)), C.c_void_p(ptr(df_dparam)),
+                                   C.c_void_p(ptr(df_dx) or None), _stream_ptr(stream)), "mf_grad")
+
+
 def mf_vegas_create(ndim: int, nbins: int = 50, alpha: float = 1.5):
     h = C.c_void_p()
     L.check(L.lib().mf_vegas_create(ndim, nbins, alpha, C.byref(h)), "mf_vegas_create")
@@ -255,6 +262,16 @@ class Process:
         mf_integrand(self.handle, x, n, f, precision, stream)
         return f
 
+    def grad(self, x, with_dx=True, stream=None):
+        """(f [n], df/dparam [2, n] (m_t, alpha_s), df/dx [ndim, n] or None)."""
+        import torch
+        n = x.shape[1]
+        f = torch.empty(n, dtype=torch.float64, device=x.device)
+        dp = torch.empty((2, n), dtype=torch.float64, device=x.device)
+        dx = torch.empty((self.ndim, n), dtype=torch.float64, device=x.device) if with_dx else None
+        mf_grad(self.handle, x, n, f, dp, dx, stream)
+        return f, dp, dx
+
     def helicity_msq(self, x, precision="fp64", stream=None):
         """Colour-summed |M|^2 of every helicity row (unaveraged), [n_hel_all, n]."""
         import torch
@@ -303,3 +320,35 @@ class Vegas:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- autograd
+def integrand_with_grad(proc: "Process", x, params=None):
+    """f(x) as a differentiable torch function.
+
+    x: CUDA float64 [ndim, n] (may require grad); params: optional float64
+    tensor [m_t, alpha_s] (values must be those the process was built with)
+    that receives d(sum w f)/d(m_t, alpha_s) on backward.  The backward pass
+    uses the derivatives mf_grad computes in the forward call.
+    """
+    import torch
+
+    class _F(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, xin, prm):
+            f, dp, dx = proc.grad(xin.detach().contiguous(), with_dx=True)
+            ctx.save_for_backward(dp, dx)
+            return f
+
+        @staticmethod
+        def backward(ctx, gout):
+            dp, dx = ctx.saved_tensors
+            gx = dx * gout[None, :] if ctx.needs_input_grad[0] else None
+            gp = None
+            if ctx.needs_input_grad[1]:
+                gp = (dp * gout[None, :]).sum(dim=1).to(torch.float64)
+            return gx, gp
+
+    if params is None:
+        params = torch.zeros(2, dtype=torch.float64, device=x.device)
+    return _F.apply(x, params)

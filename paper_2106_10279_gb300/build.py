@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmadflow_gb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-EMBED = ["mf_common.cuh", "mf_dual.cuh", "mf_kinematics.cuh", "mf_helas.cuh", "mf_kparams.h", "mf_kernel.cuh"]
+EMBED = ["mf_common.cuh", "mf_dual.cuh", "mf_kinematics.cuh", "mf_helas.cuh", "mf_kparams.h", "mf_kernel.cuh",
+         "mf_helas_adj.cuh", "mf_grad.cuh"]
 SOURCES = ["mf_api.cu", "mf_codegen.cpp", "mf_jit.cpp"]
 
 

@@ -14,7 +14,14 @@ typedef unsigned char uint8_t;
 #include <cstdint>
 #endif
 
+#if defined(__CUDACC__) || defined(__CUDACC_RTC__)
 #define MF_DEV __device__ __forceinline__
+#else
+// host compilation of the arithmetic headers, used only by the unit tests of
+// the routines (tests/adjoint_check.cpp)
+#include <cmath>
+#define MF_DEV inline
+#endif
 
 namespace mf {
 

@@ -9,6 +9,7 @@
 // (nothing is stored by the forward sweep beyond the wavefunctions), and ADDS
 // into the adjoint arrays it is given.
 #pragma once
+#include "mf_dual.cuh"
 #include "mf_helas.cuh"
 
 namespace mf {

@@ -45,6 +45,73 @@ struct PairSum {
     }
 };
 
+// Per-event work that does not depend on helicity (phase A), for one point y
+// of the unit hypercube (after the Vegas map).  T is double in the integrand
+// kernel and a dual number (derivatives with respect to y and m_t) in the
+// gradient kernel.  Returns false if the point fails the threshold or the
+// cuts (the outputs are then unspecified).
+template <typename T>
+struct EventKin {
+    T pref;                    // f = pref * sum_h |M_h|^2
+    T p[proc::NLEG][4];        // momenta: incoming along +z / -z, outgoing from phase space
+    T den[proc::NDEN > 0 ? proc::NDEN : 1];   // propagator denominators P^2 - M^2
+};
+
+template <typename T>
+MF_DEV bool phase_a(const KParams &kp, const T *y, const T *masses, const T &ln_tau_min, EventKin<T> &ev) {
+    using namespace proc;
+    T s_hat = T(kp.S), jx = T(1.0), lum = T(1.0);
+    XMap<T> xm;
+    const T *u = y;
+    if (HADRONIC) {
+        xm = xmap(y[0], y[1], ln_tau_min);
+        s_hat = xm.tau * kp.S;
+        jx = xm.jac;
+        u = y + 2;
+    }
+    T rs = sqrt(s_hat);
+    T (*p)[4] = ev.p;
+    p[0][0] = 0.5 * rs; p[0][1] = T(0.0); p[0][2] = T(0.0); p[0][3] = 0.5 * rs;
+    p[1][0] = 0.5 * rs; p[1][1] = T(0.0); p[1][2] = T(0.0); p[1][3] = -0.5 * rs;
+    T (*pout)[4] = reinterpret_cast<T (*)[4]>(&p[2][0]);
+    massless_diet<NOUT>(u, rs, pout);
+    T mout[NOUT];
+#pragma unroll
+    for (int i = 0; i < NOUT; ++i) mout[i] = LEG_MASS_ID[2 + i] >= 0 ? masses[LEG_MASS_ID[2 + i]] : T(0.0);
+    T wfac = massive_rescale<NOUT>(pout, mout, rs);
+    bool ok = value(wfac) > 0.0;
+    // cuts on the flagged legs (decided on values)
+    if (ok && NCUT > 0) {
+        double pv[NLEG][4];
+#pragma unroll
+        for (int i = 0; i < NLEG; ++i)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) pv[i][q] = value(p[i][q]);
+#pragma unroll
+        for (int a = 0; a < NCUT; ++a) ok &= pt2(pv[CUT_LEGS[a]]) > kp.pt_min2;
+        if (kp.dr_min2 > 0.0) {
+#pragma unroll
+            for (int a = 0; a < NCUT; ++a)
+#pragma unroll
+                for (int b = a + 1; b < NCUT; ++b) ok &= delta_r2(pv[CUT_LEGS[a]], pv[CUT_LEGS[b]]) > kp.dr_min2;
+        }
+    }
+    if (!ok) return false;
+    T wps = kp.w0_const * wfac;
+#pragma unroll
+    for (int i = 0; i < NOUT - 2; ++i) wps = wps * s_hat;
+    if (HADRONIC) {
+        const double *r = kp.pdf_rows;
+        const int nx = kp.pdf_nx;
+        T f1 = pdf_eval(r, r + nx, nx, kp.pdf_a0, kp.pdf_h, xm.ln_x1, xm.x1);
+        T f2 = pdf_eval(r + 2 * nx, r + 3 * nx, nx, kp.pdf_a0, kp.pdf_h, xm.ln_x2, xm.x2);
+        lum = f1 * f2;
+    }
+    ev.pref = jx * wps * lum * kp.pref_const / s_hat;
+    denominators(p, masses, ev.den);
+    return true;
+}
+
 template <typename R, int BLOCK, int HT>
 MF_DEV void kernel_body(const KParams &kp) {
     using namespace proc;
@@ -106,61 +173,18 @@ MF_DEV void kernel_body(const KParams &kp) {
                     bins[j] = (uint8_t)bj;
                 }
             }
-            double s_hat = kp.S, jx = 1.0, lum = 1.0;
-            XMap<double> xm;
-            const double *u = y;
-            if (HADRONIC) {
-                xm = xmap(y[0], y[1], kp.ln_tau_min);
-                s_hat = xm.tau * kp.S;
-                jx = xm.jac;
-                u = y + 2;
-            }
-            double rs = sqrt(s_hat);
-            double p[NLEG][4];
-            p[0][0] = 0.5 * rs; p[0][1] = 0.0; p[0][2] = 0.0; p[0][3] = 0.5 * rs;
-            p[1][0] = 0.5 * rs; p[1][1] = 0.0; p[1][2] = 0.0; p[1][3] = -0.5 * rs;
-            double (*pout)[4] = reinterpret_cast<double (*)[4]>(&p[2][0]);
-            massless_diet<NOUT>(u, rs, pout);
-            double mout[NOUT];
-#pragma unroll
-            for (int i = 0; i < NOUT; ++i) mout[i] = LEG_MASS_ID[2 + i] >= 0 ? kp.masses[LEG_MASS_ID[2 + i]] : 0.0;
-            double wfac = massive_rescale<NOUT>(pout, mout, rs);
-            ok = wfac > 0.0;
-            // cuts on the flagged legs
-            if (ok && NCUT > 0) {
-#pragma unroll
-                for (int a = 0; a < NCUT; ++a) ok &= pt2(p[CUT_LEGS[a]]) > kp.pt_min2;
-                if (kp.dr_min2 > 0.0) {
-#pragma unroll
-                    for (int a = 0; a < NCUT; ++a)
-#pragma unroll
-                        for (int b = a + 1; b < NCUT; ++b)
-                            ok &= delta_r2(p[CUT_LEGS[a]], p[CUT_LEGS[b]]) > kp.dr_min2;
-                }
-            }
+            EventKin<double> ev;
+            ok = phase_a<double>(kp, y, kp.masses, kp.ln_tau_min, ev);
             if (ok) {
-                double wps = kp.w0_const * wfac;
-#pragma unroll
-                for (int i = 0; i < NOUT - 2; ++i) wps *= s_hat;
-                if (HADRONIC) {
-                    const double *r = kp.pdf_rows;
-                    const int nx = kp.pdf_nx;
-                    double f1 = pdf_eval(r, r + nx, nx, kp.pdf_a0, kp.pdf_h, xm.ln_x1, xm.x1);
-                    double f2 = pdf_eval(r + 2 * nx, r + 3 * nx, nx, kp.pdf_a0, kp.pdf_h, xm.ln_x2, xm.x2);
-                    lum = f1 * f2;
-                }
-                pref = jx * wps * lum * kp.pref_const / s_hat;
-                // propagator denominators from double-precision invariants
-                double den[NDEN1];
-                denominators(p, kp.masses, den);
+                pref = ev.pref;
                 R *sd = s_den + tid * NDEN1;
 #pragma unroll
-                for (int k = 0; k < NDEN; ++k) sd[k] = (R)(1.0 / den[k]);
+                for (int k = 0; k < NDEN; ++k) sd[k] = (R)(1.0 / ev.den[k]);
                 R *sm = s_mom + tid * NLEG * 4;
 #pragma unroll
                 for (int i = 0; i < NLEG; ++i)
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) sm[4 * i + q] = (R)p[i][q];
+                    for (int q = 0; q < 4; ++q) sm[4 * i + q] = (R)ev.p[i][q];
             }
         }
         s_pref[tid] = pref;

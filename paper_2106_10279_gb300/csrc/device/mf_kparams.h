@@ -27,6 +27,11 @@ struct mf_kparams {
     int32_t pdf_nx;
     int32_t pad1;
     const double *pdf_rows;    // [2 beams][2: values, slopes][pdf_nx]
+    double *g_dparam;          // gradient kernel: df/dm_t, df/dalpha_s, [2][n]
+    double *g_dx;              // gradient kernel: df/dx_j, [NDIM][n] (may be NULL)
+    double alpha_s;            // strong coupling the couplings were built with
+    int32_t alpha_s_power;     // |M|^2 ~ alpha_s^power
+    int32_t pad2;
     double masses[8];
     double couplings[16];      // 8 complex couplings (re, im)
     int8_t hel[MF_KP_MAX_HEL][8];

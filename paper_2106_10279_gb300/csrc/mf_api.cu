@@ -318,6 +318,19 @@ mf_status compile_precision(mf_process *p, int prec) {
     return mfi::load_kernel(cubin, k);
 }
 
+mf_status compile_grad(mf_process *p) {
+    mfi::Compiled &k = p->kern[2];
+    if (k.fn) return MF_OK;
+    k.block = 128;
+    k.smem = 0;
+    mfi::GenInfo info;
+    p->source[2] = mfi::generate_grad_source(*p, k.block, info);
+    std::vector<char> cubin;
+    mf_status st = mfi::jit_compile(p->source[2], "mf_proc_grad.cu", cubin);
+    if (st != MF_OK) return st;
+    return mfi::load_kernel(cubin, k, "mf_grad_kernel");
+}
+
 void fill_common(const mf_process &p, mf_kparams &kp) {
     std::memset(&kp, 0, sizeof kp);
     kp.S = p.sqrt_s * p.sqrt_s;
@@ -332,6 +345,8 @@ void fill_common(const mf_process &p, mf_kparams &kp) {
     kp.pdf_rows = p.d_pdf_rows;
     for (size_t i = 0; i < p.masses.size() && i < 8; ++i) kp.masses[i] = p.masses[i];
     for (size_t i = 0; i < p.couplings.size() && i < 16; ++i) kp.couplings[i] = p.couplings[i];
+    kp.alpha_s = p.alpha_s;
+    kp.alpha_s_power = p.alpha_s_power;
 }
 
 void set_hel(mf_kparams &kp, const std::vector<int8_t> &hel, int n_legs) {
@@ -599,7 +614,7 @@ extern "C" mf_status mf_create_process(const mf_process_desc *d, mf_process **ou
 extern "C" mf_status mf_generate_kernel_source(const mf_process_desc *d, mf_precision prec, int32_t compile,
                                                char *buf, size_t *len) {
     if (!len) return fail(MF_EINVAL, "len is NULL");
-    if (prec != MF_FP64 && prec != MF_MIXED) return fail(MF_EINVAL, "bad precision");
+    if (prec != MF_FP64 && prec != MF_MIXED && (int)prec != 2) return fail(MF_EINVAL, "bad precision");
     mf_status st = validate(d);
     if (st != MF_OK) return st;
     mf_process p;
@@ -622,10 +637,12 @@ extern "C" mf_status mf_generate_kernel_source(const mf_process_desc *d, mf_prec
     int nhp = 1;
     while (nhp < nh) nhp <<= 1;
     mfi::GenInfo info;
-    std::string src = mfi::generate_source(p, prec, 128, nhp < 32 ? nhp : 32, info);
+    std::string src = (int)prec == 2 ? mfi::generate_grad_source(p, 128, info)
+                                     : mfi::generate_source(p, prec, 128, nhp < 32 ? nhp : 32, info);
     if (compile) {
         std::vector<char> cubin;
-        st = mfi::jit_compile(src, prec == MF_FP64 ? "mf_proc_f64.cu" : "mf_proc_mixed.cu", cubin);
+        st = mfi::jit_compile(src, (int)prec == 2 ? "mf_proc_grad.cu" : prec == MF_FP64 ? "mf_proc_f64.cu" : "mf_proc_mixed.cu",
+                              cubin);
         if (st != MF_OK) return st;
     }
     size_t need = src.size() + 1;
@@ -702,6 +719,26 @@ extern "C" mf_status mf_helicity_msq(mf_process *p, const double *x, int64_t n, 
     kp.x = x;
     kp.f = out;
     return launch(p, prec, kp, (cudaStream_t)stream);
+}
+
+extern "C" mf_status mf_grad(mf_process *p, const double *x, int64_t n, double *f, double *df_dparam,
+                             double *df_dx, void *stream) {
+    if (!p) return fail(MF_EINVAL, "NULL process");
+    if (n < 0) return fail(MF_EINVAL, "negative n");
+    if (n == 0) return MF_OK;
+    if (!x || !f || !df_dparam) return fail(MF_EINVAL, "NULL x, f or df_dparam");
+    mf_status st = compile_grad(p);
+    if (st != MF_OK) return st;
+    mf_kparams kp;
+    fill_common(*p, kp);
+    set_hel(kp, p->hel, p->n_legs);
+    kp.mode = 0;
+    kp.n = n;
+    kp.x = x;
+    kp.f = f;
+    kp.g_dparam = df_dparam;
+    kp.g_dx = df_dx;
+    return launch(p, 2, kp, (cudaStream_t)stream);
 }
 
 // ----------------------------------------------------------------------------

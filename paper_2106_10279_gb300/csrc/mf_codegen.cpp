@@ -41,12 +41,13 @@ double routine_flops(int r) {
 
 }  // namespace
 
-std::string generate_source(const mf_process &p, int precision, int block, int ht, GenInfo &info) {
-    const char *R = precision == MF_FP64 ? "double" : "float";
+// Includes, the process constants and the double-precision propagator
+// denominators (shared by the integrand and the gradient sources).
+void emit_header(std::ostringstream &o, const mf_process &p, GenInfo &info, std::vector<uint32_t> &mask,
+                 const char *R) {
     const int n = p.n_legs;
-    std::ostringstream o;
     // --- wavefunction momenta as signed leg masks, denominator slots
-    std::vector<uint32_t> mask(p.ops.size(), 0);
+    mask.assign(p.ops.size(), 0);
     info = GenInfo{};
     info.op_den.assign(p.ops.size(), -1);
     std::map<std::pair<uint32_t, int>, int> slot_of;
@@ -92,7 +93,7 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
     o << "};\n";
 
     // --- propagator denominators from double-precision invariants
-    o << "MF_DEV void denominators(const double (*p)[4], const double *masses, double *den) {\n";
+    o << "template <typename T>\nMF_DEV void denominators(const T (*p)[4], const T *masses, T *den) {\n";
     std::vector<bool> need(n * n, false);
     for (auto &d : info.dens)
         for (int i = 0; i < n; ++i)
@@ -103,7 +104,7 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
             if (need[i * n + j]) {
                 // 2 P_i . P_j with P = momentum into the diagram (sign of the leg)
                 double sg = (p.leg_incoming[i] ? 1.0 : -1.0) * (p.leg_incoming[j] ? 1.0 : -1.0);
-                o << "  const double d" << i << "_" << j << " = " << (sg > 0 ? "" : "-")
+                o << "  const T d" << i << "_" << j << " = " << (sg > 0 ? "" : "-")
                   << "2.0 * (p[" << i << "][0] * p[" << j << "][0] - p[" << i << "][1] * p[" << j
                   << "][1] - p[" << i << "][2] * p[" << j << "][2] - p[" << i << "][3] * p[" << j
                   << "][3]);\n";
@@ -113,7 +114,7 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
         // P^2 - M^2 = (sum of the legs' m^2 - M^2) + sum of 2 P_i.P_j: the mass
         // terms first, so that an on-shell mass cancels exactly before the
         // (possibly small) invariants are added
-        o << "  den[" << s << "] = (0.0";
+        o << "  den[" << s << "] = (T(0.0)";
         for (int i = 0; i < n; ++i)
             if ((d.mask >> i & 1) && p.leg_mass_id[i] >= 0)
                 o << " + masses[" << p.leg_mass_id[i] << "] * masses[" << p.leg_mass_id[i] << "]";
@@ -125,6 +126,14 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
         o << ";\n";
     }
     o << "}\n";
+}
+
+std::string generate_source(const mf_process &p, int precision, int block, int ht, GenInfo &info) {
+    const char *R = precision == MF_FP64 ? "double" : "float";
+    const int n = p.n_legs;
+    std::ostringstream o;
+    std::vector<uint32_t> mask;
+    emit_header(o, p, info, mask, R);
 
     // --- the program for one helicity
     // momentum into the diagram through the legs of a mask, component q
@@ -330,6 +339,271 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
     info.flops_per_hel = fl;
     // kinematics per event (phase space, PDFs, denominators), rough count
     info.flops_kin = 400.0 + 10.0 * info.n_den;
+    return o.str();
+}
+
+
+// Momentum into the diagram through the legs of a mask, as a local array.
+static std::string mom_array(const mf_process &p, uint32_t m, const std::string &name) {
+    std::ostringstream e;
+    e << "    const R " << name << "[4] = {";
+    for (int q = 0; q < 4; ++q) {
+        bool first = true;
+        for (int l = 0; l < p.n_legs; ++l)
+            if (m >> l & 1) {
+                bool plus = p.leg_incoming[l] != 0;
+                e << (first ? (plus ? "" : "-") : (plus ? " + " : " - ")) << "ms[" << 4 * l + q << "]";
+                first = false;
+            }
+        e << (q < 3 ? ", " : "};\n");
+    }
+    return e.str();
+}
+
+// Adjoint of a momentum (array name) spread over the external legs of a mask.
+static std::string mom_scatter(const mf_process &p, uint32_t m, const std::string &name) {
+    std::ostringstream e;
+    for (int l = 0; l < p.n_legs; ++l)
+        if (m >> l & 1)
+            for (int q = 0; q < 4; ++q)
+                e << "    pbar[" << 4 * l + q << "] " << (p.leg_incoming[l] ? "+=" : "-=") << " " << name << "[" << q
+                  << "];\n";
+    return e.str();
+}
+
+std::string generate_grad_source(const mf_process &p, int block, GenInfo &info) {
+    std::ostringstream o;
+    std::vector<uint32_t> mask;
+    o << "#include \"mf_helas_adj.cuh\"\n";
+    emit_header(o, p, info, mask, "double");
+    // compact indices of the wavefunctions
+    std::vector<int> ci(p.ops.size(), -1);
+    int nwf = 0;
+    for (size_t k = 0; k < p.ops.size(); ++k)
+        if (p.ops[k].kind != MF_OP_AMP) ci[k] = nwf++;
+    auto W_ = [&](int k) { return "w[" + std::to_string(ci[k]) + "]"; };
+    auto WB = [&](int k) { return "wb[" + std::to_string(ci[k]) + "]"; };
+    auto M = [&](int id) { return id >= 0 ? "mass[" + std::to_string(id) + "]" : std::string("R(0)"); };
+    o << "template <typename R>\nMF_DEV R helicity_msq(const R *, const R *, const int8_t *, const mf::cx<R> *, const R *);\n";
+    // The program is emitted as many small non-inlined functions sharing the
+    // wavefunction arrays through pointers: one large function would fall
+    // into ptxas's low-quality allocation and compile slowly.
+    const int CH = 12;
+    const char *args =
+        "(const R *__restrict__ ms, const R *__restrict__ idn, const int8_t *__restrict__ hel, "
+        "const mf::cx<R> *__restrict__ cpl, const R *__restrict__ mass, mf::W<R> *__restrict__ w, "
+        "mf::W<R> *__restrict__ wb, mf::cx<R> *__restrict__ J, mf::cx<R> *__restrict__ Jb, R *__restrict__ pbar, "
+        "R *__restrict__ idnbar, R *__restrict__ mbar)";
+    std::vector<std::string> calls;
+    int nfun = 0;
+    auto open_fn = [&]() {
+        std::string name = "gchunk" + std::to_string(nfun++);
+        o << "template <typename R>\n__device__ __noinline__ void " << name << args << " {\n  using namespace mf;\n";
+        calls.push_back(name);
+    };
+    auto close_fn = [&]() { o << "}\n"; };
+    // forward sweep (wavefunctions), in op order
+    {
+        int cnt = 0;
+        for (size_t k = 0; k < p.ops.size(); ++k) {
+            const mf_op &op = p.ops[k];
+            if (op.kind == MF_OP_AMP) continue;
+            if (cnt % CH == 0) { if (cnt) close_fn(); open_fn(); }
+            ++cnt;
+            if (op.kind == MF_OP_EXT) {
+                int l = op.leg;
+                if (op.routine == MF_R_VXX)
+                    o << "  " << W_(k) << " = vxx<R>(ms + " << 4 * l << ", hel[" << l << "], "
+                      << (p.leg_incoming[l] ? 1 : 0) << ");\n";
+                else {
+                    int anti = (op.routine == MF_R_IXX) ? (p.leg_incoming[l] ? 0 : 1) : (p.leg_incoming[l] ? 1 : 0);
+                    o << "  " << W_(k) << " = " << (op.routine == MF_R_IXX ? "ixx" : "oxx") << "<R>(ms + " << 4 * l
+                      << ", " << M(p.leg_mass_id[l]) << ", hel[" << l << "], " << anti << ");\n";
+                }
+                continue;
+            }
+            std::string g = "cpl[" + std::to_string(op.coupling) + "]";
+            std::string den = "idn[" + std::to_string(info.op_den[k]) + "]";
+            o << "  {\n";
+            switch (op.routine) {
+                case MF_R_FFV_FIN: case MF_R_FFV_FOUT:
+                    o << mom_array(p, mask[k], "P") << "    " << W_(k) << " = "
+                      << (op.routine == MF_R_FFV_FIN ? "FFV_FIN" : "FFV_FOUT") << "<R>(" << W_(op.in[0]) << ", "
+                      << W_(op.in[1]) << ", " << g << ", " << M(op.mass_id) << ", " << den << ", P);\n";
+                    break;
+                case MF_R_FFV_VEC:
+                    o << "    " << W_(k) << " = FFV_VEC<R>(" << W_(op.in[0]) << ", " << W_(op.in[1]) << ", " << g
+                      << ", " << den << ");\n";
+                    break;
+                case MF_R_VVV_VEC:
+                    o << mom_array(p, mask[op.in[0]], "kA") << mom_array(p, mask[op.in[1]], "kB") << "    " << W_(k)
+                      << " = VVV_VEC<R>(" << W_(op.in[0]) << ", " << W_(op.in[1]) << ", kA, kB, " << g << ", " << den
+                      << ");\n";
+                    break;
+                default:
+                    o << "    " << W_(k) << " = VVVV_VEC<R, " << (op.routine - MF_R_VVVV1_VEC + 1) << ">("
+                      << W_(op.in[0]) << ", " << W_(op.in[1]) << ", " << W_(op.in[2]) << ", " << g << ", " << den
+                      << ");\n";
+            }
+            o << "  }\n";
+        }
+        if (cnt) close_fn();
+    }
+    // amplitudes -> colour flows
+    std::vector<int> amps;
+    for (size_t k = 0; k < p.ops.size(); ++k)
+        if (p.ops[k].kind == MF_OP_AMP) amps.push_back((int)k);
+    for (size_t a = 0; a < amps.size(); ++a) {
+        if (a % CH == 0) { if (a) close_fn(); open_fn(); }
+        const mf_op &op = p.ops[amps[a]];
+        std::string g = "cpl[" + std::to_string(op.coupling) + "]";
+        o << "  {\n";
+        if (op.routine == MF_R_VVV_AMP)
+            o << mom_array(p, mask[op.in[0]], "kA") << mom_array(p, mask[op.in[1]], "kB") << mom_array(p, mask[op.in[2]], "kC");
+        o << "    const cx<R> a = ";
+        switch (op.routine) {
+            case MF_R_FFV_AMP: o << "FFV_AMP<R>(" << W_(op.in[0]) << ", " << W_(op.in[1]) << ", " << W_(op.in[2]) << ", " << g << ")"; break;
+            case MF_R_VVV_AMP: o << "VVV_AMP<R>(" << W_(op.in[0]) << ", " << W_(op.in[1]) << ", " << W_(op.in[2]) << ", kA, kB, kC, " << g << ")"; break;
+            default:
+                o << "VVVV_AMP<R, " << (op.routine - MF_R_VVVV1_AMP + 1) << ">(" << W_(op.in[0]) << ", " << W_(op.in[1])
+                  << ", " << W_(op.in[2]) << ", " << W_(op.in[3]) << ", " << g << ")";
+        }
+        o << ";\n";
+        for (int t = 0; t < op.n_terms; ++t) {
+            const mf_colour_term &ct = p.terms[op.first_term + t];
+            o << "    J[" << ct.jamp << "] = cfma(C<R>(R(" << fmt_double(ct.re) << "), R(" << fmt_double(ct.im)
+              << ")), a, J[" << ct.jamp << "]);\n";
+        }
+        o << "  }\n";
+    }
+    if (!amps.empty()) close_fn();
+    const size_t n_forward = calls.size();
+    // adjoints of the amplitudes
+    for (size_t a = 0; a < amps.size(); ++a) {
+        if (a % CH == 0) { if (a) close_fn(); open_fn(); }
+        const mf_op &op = p.ops[amps[a]];
+        std::string g = "cpl[" + std::to_string(op.coupling) + "]";
+        o << "  {\n    cx<R> ab = C<R>(R(0), R(0));\n";
+        for (int t = 0; t < op.n_terms; ++t) {
+            const mf_colour_term &ct = p.terms[op.first_term + t];
+            o << "    ab = ab + conj(C<R>(R(" << fmt_double(ct.re) << "), R(" << fmt_double(ct.im) << "))) * Jb["
+              << ct.jamp << "];\n";
+        }
+        switch (op.routine) {
+            case MF_R_FFV_AMP:
+                o << "    FFV_AMP_adj<R>(" << W_(op.in[0]) << ", " << W_(op.in[1]) << ", " << W_(op.in[2]) << ", " << g
+                  << ", ab, " << WB(op.in[0]) << ", " << WB(op.in[1]) << ", " << WB(op.in[2]) << ");\n";
+                break;
+            case MF_R_VVV_AMP:
+                o << mom_array(p, mask[op.in[0]], "kA") << mom_array(p, mask[op.in[1]], "kB")
+                  << mom_array(p, mask[op.in[2]], "kC")
+                  << "    R kAb[4] = {R(0), R(0), R(0), R(0)}, kBb[4] = {R(0), R(0), R(0), R(0)}, kCb[4] = {R(0), R(0), R(0), R(0)};\n"
+                  << "    VVV_AMP_adj<R>(" << W_(op.in[0]) << ", " << W_(op.in[1]) << ", " << W_(op.in[2])
+                  << ", kA, kB, kC, " << g << ", ab, " << WB(op.in[0]) << ", " << WB(op.in[1]) << ", " << WB(op.in[2])
+                  << ", kAb, kBb, kCb);\n"
+                  << mom_scatter(p, mask[op.in[0]], "kAb") << mom_scatter(p, mask[op.in[1]], "kBb")
+                  << mom_scatter(p, mask[op.in[2]], "kCb");
+                break;
+            default:
+                o << "    VVVV_AMP_adj<R, " << (op.routine - MF_R_VVVV1_AMP + 1) << ">(" << W_(op.in[0]) << ", "
+                  << W_(op.in[1]) << ", " << W_(op.in[2]) << ", " << W_(op.in[3]) << ", " << g << ", ab, "
+                  << WB(op.in[0]) << ", " << WB(op.in[1]) << ", " << WB(op.in[2]) << ", " << WB(op.in[3]) << ");\n";
+        }
+        o << "  }\n";
+    }
+    if (!amps.empty()) close_fn();
+    // adjoints of the currents, last first
+    {
+        int cnt = 0;
+        for (size_t kk = p.ops.size(); kk-- > 0;) {
+            const mf_op &op = p.ops[kk];
+            const int k = (int)kk;
+            if (op.kind != MF_OP_CUR) continue;
+            if (cnt % CH == 0) { if (cnt) close_fn(); open_fn(); }
+            ++cnt;
+            std::string g = "cpl[" + std::to_string(op.coupling) + "]";
+            int sl = info.op_den[k];
+            std::string den = "idn[" + std::to_string(sl) + "]", denb = "idnbar[" + std::to_string(sl) + "]";
+            o << "  {\n";
+            switch (op.routine) {
+                case MF_R_FFV_FIN: case MF_R_FFV_FOUT:
+                    o << mom_array(p, mask[k], "P") << "    R Pb[4] = {R(0), R(0), R(0), R(0)}, Mb = R(0);\n    "
+                      << (op.routine == MF_R_FFV_FIN ? "FFV_FIN_adj" : "FFV_FOUT_adj") << "<R>(" << W_(op.in[0]) << ", "
+                      << W_(op.in[1]) << ", " << g << ", " << M(op.mass_id) << ", " << den << ", P, " << WB(k) << ", "
+                      << WB(op.in[0]) << ", " << WB(op.in[1]) << ", " << denb << ", Pb, Mb);\n" << mom_scatter(p, mask[k], "Pb");
+                    if (op.mass_id >= 0) o << "    mbar[" << op.mass_id << "] += Mb;\n";
+                    break;
+                case MF_R_FFV_VEC:
+                    o << "    FFV_VEC_adj<R>(" << W_(op.in[0]) << ", " << W_(op.in[1]) << ", " << g << ", " << den << ", "
+                      << WB(k) << ", " << WB(op.in[0]) << ", " << WB(op.in[1]) << ", " << denb << ");\n";
+                    break;
+                case MF_R_VVV_VEC:
+                    o << mom_array(p, mask[op.in[0]], "kA") << mom_array(p, mask[op.in[1]], "kB")
+                      << "    R kAb[4] = {R(0), R(0), R(0), R(0)}, kBb[4] = {R(0), R(0), R(0), R(0)};\n"
+                      << "    VVV_VEC_adj<R>(" << W_(op.in[0]) << ", " << W_(op.in[1]) << ", kA, kB, " << g << ", " << den
+                      << ", " << WB(k) << ", " << WB(op.in[0]) << ", " << WB(op.in[1]) << ", " << denb << ", kAb, kBb);\n"
+                      << mom_scatter(p, mask[op.in[0]], "kAb") << mom_scatter(p, mask[op.in[1]], "kBb");
+                    break;
+                default:
+                    o << "    VVVV_VEC_adj<R, " << (op.routine - MF_R_VVVV1_VEC + 1) << ">(" << W_(op.in[0]) << ", "
+                      << W_(op.in[1]) << ", " << W_(op.in[2]) << ", " << g << ", " << den << ", " << WB(k) << ", "
+                      << WB(op.in[0]) << ", " << WB(op.in[1]) << ", " << WB(op.in[2]) << ", " << denb << ");\n";
+            }
+            o << "  }\n";
+        }
+        if (cnt) close_fn();
+    }
+    // external legs: tangents of the wavefunction in its momentum and mass
+    {
+        int cnt = 0;
+        for (size_t k = 0; k < p.ops.size(); ++k) {
+            const mf_op &op = p.ops[k];
+            if (op.kind != MF_OP_EXT) continue;
+            if (cnt % 2 == 0) { if (cnt) close_fn(); open_fn(); }
+            ++cnt;
+            int l = op.leg;
+            int mid = p.leg_mass_id[l];
+            std::string mv = mid >= 0 ? "mass[" + std::to_string(mid) + "]" : std::string("R(0)");
+            o << "  {\n    R mdummy = R(0);\n    external_adj([&](const Dual<5> *pd, const Dual<5> &md) { return ";
+            if (op.routine == MF_R_VXX)
+                o << "vxx<Dual<5>>(pd, hel[" << l << "], " << (p.leg_incoming[l] ? 1 : 0) << ");";
+            else {
+                int anti = (op.routine == MF_R_IXX) ? (p.leg_incoming[l] ? 0 : 1) : (p.leg_incoming[l] ? 1 : 0);
+                o << (op.routine == MF_R_IXX ? "ixx" : "oxx") << "<Dual<5>>(pd, md, hel[" << l << "], " << anti << ");";
+            }
+            o << " }, ms + " << 4 * l << ", " << mv << ", " << WB(k) << ", pbar + " << 4 * l << ", "
+              << (mid >= 0 ? "mbar[" + std::to_string(mid) + "]" : std::string("mdummy")) << ");\n  }\n";
+        }
+        if (cnt) close_fn();
+    }
+    // driver: forward, |M|^2 and dL/dJ = 2 C J / den, then the adjoint chunks
+    const int nj = p.n_jamp;
+    o << "template <typename R>\n"
+         "MF_DEV R helicity_grad(const R *__restrict__ ms, const R *__restrict__ idn, const int8_t *hel,\n"
+         "    const mf::cx<R> *cpl, const R *mass, R *pbar, R *idnbar, R *mbar) {\n"
+         "  using namespace mf;\n"
+         "  W<R> w[" << nwf << "], wb[" << nwf << "];\n  cx<R> J[NJAMP], Jb[NJAMP];\n"
+         "  for (int k = 0; k < NJAMP; ++k) J[k] = C<R>(R(0), R(0));\n";
+    for (size_t c = 0; c < n_forward; ++c)
+        o << "  " << calls[c] << "<R>(ms, idn, hel, cpl, mass, w, wb, J, Jb, pbar, idnbar, mbar);\n";
+    o << "  R m = R(0);\n";
+    for (int k = 0; k < nj; ++k) {
+        o << "  { cx<R> z = C<R>(R(0), R(0));\n";
+        for (int l = 0; l < nj; ++l) {
+            int c = p.colour_num[k * nj + l];
+            if (c) o << "    z = z + R(" << c << ") * J[" << l << "];\n";
+        }
+        o << "    m += J[" << k << "].re * z.re + J[" << k << "].im * z.im;\n"
+          << "    Jb[" << k << "] = R(" << fmt_double(2.0 / p.colour_den) << ") * z; }\n";
+    }
+    o << "  m *= R(" << fmt_double(1.0 / p.colour_den) << ");\n";
+    o << "  for (int i = 0; i < " << nwf << "; ++i) for (int c = 0; c < 4; ++c) wb[i].c[c] = C<R>(R(0), R(0));\n";
+    for (size_t c = n_forward; c < calls.size(); ++c)
+        o << "  " << calls[c] << "<R>(ms, idn, hel, cpl, mass, w, wb, J, Jb, pbar, idnbar, mbar);\n";
+    o << "  return m;\n}\n}  // namespace proc\n";
+    o << "#include \"mf_grad.cuh\"\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(" << block << ") mf_grad_kernel(const mf::KParams kp) {\n"
+      << "  mf::grad_body<proc::NDIM + 1>(kp);\n}\n";
     return o.str();
 }
 

@@ -69,8 +69,8 @@ struct mf_process {
     double *d_pdf_rows = nullptr;  // device [2][2][nx]
     double ln_tau_min = 0.0, w0_const = 0.0, pref_const = 0.0;
     mfi::GenInfo gen;
-    mfi::Compiled kern[2];         // per mf_precision
-    std::string source[2];
+    mfi::Compiled kern[3];         // per mf_precision, and [2] the gradient kernel
+    std::string source[3];
     // events around the last process-kernel launch of mf_vegas_iterate
     cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
     double last_kernel_ms = 0.0;
@@ -98,9 +98,10 @@ struct mf_vegas {
 namespace mfi {
 // code generation (mf_codegen.cpp)
 std::string generate_source(const mf_process &p, int precision, int block, int ht, GenInfo &info);
+std::string generate_grad_source(const mf_process &p, int block, GenInfo &info);
 // run-time compilation (mf_jit.cpp)
 mf_status jit_compile(const std::string &source, const std::string &name, std::vector<char> &cubin);
-mf_status load_kernel(const std::vector<char> &cubin, Compiled &out);
+mf_status load_kernel(const std::vector<char> &cubin, Compiled &out, const char *name = "mf_kernel");
 void unload_kernel(Compiled &k);
 mf_status launch_kernel(const Compiled &k, unsigned grid, void **args, cudaStream_t s);
 }  // namespace mfi

@@ -182,12 +182,12 @@ std::string drv_err(CUresult r) {
 }
 }  // namespace
 
-mf_status load_kernel(const std::vector<char> &cubin, Compiled &out) {
+mf_status load_kernel(const std::vector<char> &cubin, Compiled &out, const char *name) {
     mf_status st = driver();
     if (st != MF_OK) return st;
     CUresult r = g_drv.moduleLoadData(&out.module, cubin.data());
     if (r != CUDA_SUCCESS) return fail(MF_ECUDA, "cuModuleLoadData: " + drv_err(r));
-    r = g_drv.moduleGetFunction(&out.fn, out.module, "mf_kernel");
+    r = g_drv.moduleGetFunction(&out.fn, out.module, name);
     if (r != CUDA_SUCCESS) return fail(MF_ECUDA, "cuModuleGetFunction: " + drv_err(r));
     int regs = 0, local = 0;
     g_drv.funcGetAttribute(&regs, CU_FUNC_ATTRIBUTE_NUM_REGS, out.fn);

@@ -5,7 +5,8 @@
 * descriptor validation rejects malformed programs with MF_EINVAL or
   MF_EUNSUPPORTED (through mf_generate_kernel_source, which validates exactly
   like mf_create_process but needs no device);
-* the generated process kernels compile for sm_103a with NVRTC.
+* the generated process kernels (integrand and gradient) compile for
+  sm_103a with NVRTC.
 """
 import ctypes as C
 import os
@@ -145,3 +146,10 @@ def test_generated_kernels_compile_for_sm103a(built, name):
     for prec in ("fp64", "mixed"):
         src = api.mf_generate_kernel_source(d, prec, compile=True)
         assert "mf_kernel" in src and "helicity_msq" in src
+
+
+@pytest.mark.parametrize("name", ["ee_mumu", "gg_ttx", "uux_ttxg"])
+def test_gradient_kernels_compile_for_sm103a(built, name):
+    from paper_2106_10279_gb300 import api
+    src = api.mf_generate_kernel_source(_desc(name), "grad", compile=True)
+    assert "mf_grad_kernel" in src and "helicity_grad" in src

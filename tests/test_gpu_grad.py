@@ -1,0 +1,192 @@
+"""Gradients (mf_grad) against finite differences and the oracle.
+
+* df/dx_j against central differences of mf_integrand (h = 1e-6);
+* df/dm_t against central differences over processes built with
+  m_t (1 +- 1e-3) (relative <= 1e-4), excluding points whose cut or threshold
+  status differs between m_t +- h (the moving cut boundary is not part of the
+  pathwise derivative);
+* df/dalpha_s = k f / alpha_s against central differences in alpha_s;
+* df/dm_t and df/dx_j against Richardson-extrapolated central differences of
+  the oracle (relative <= 1e-6);
+* the summed pathwise dsigma/dm_t against the finite difference of sigma over
+  the same points, and the boundary term reported separately;
+* the torch.autograd wrapper.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+NAMES = ["ee_mumu", "gg_ttx", "uux_ttx", "gg_ttxg", "uux_ttxg", "gg_ttxgg"]
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    return torch
+
+
+@pytest.fixture(scope="module")
+def procs(torch_cuda):
+    from paper_2106_10279_gb300 import api
+    cache = {}
+
+    def get(name, **kw):
+        key = (name, tuple(sorted(kw.items())))
+        if key not in cache:
+            cache[key] = api.Process.from_workload(W.WORKLOADS[name], **kw)
+        return cache[key]
+    return get
+
+
+def _f(torch, proc, x):
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    out = proc.integrand(xd, "fp64").cpu().numpy()
+    return out
+
+
+def _grad(torch, proc, x):
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    f, dp, dx = proc.grad(xd)
+    torch.cuda.synchronize()
+    return f.cpu().numpy(), dp.cpu().numpy(), dx.cpu().numpy()
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_grad_value_equals_integrand(torch_cuda, procs, name):
+    wl = W.WORKLOADS[name]
+    x = W.uniform_points(wl.ndim, 200, 41)
+    p = procs(name)
+    f, dp, dx = _grad(torch_cuda, p, x)
+    ref = _f(torch_cuda, p, x)
+    assert np.array_equal(f == 0, ref == 0)
+    nz = ref != 0
+    assert np.max(np.abs(f[nz] / ref[nz] - 1)) < 1e-13
+    assert np.all(dp[:, ~nz] == 0) and np.all(dx[:, ~nz] == 0)
+
+
+@pytest.mark.parametrize("name,n", [("ee_mumu", 64), ("gg_ttx", 64), ("uux_ttx", 64), ("gg_ttxg", 48),
+                                    ("uux_ttxg", 48), ("gg_ttxgg", 24)])
+def test_dx_matches_central_differences(torch_cuda, procs, name, n):
+    wl = W.WORKLOADS[name]
+    x = np.clip(W.uniform_points(wl.ndim, n, 42), 1e-3, 1 - 1e-3)
+    p = procs(name)
+    f, dp, dx = _grad(torch_cuda, p, x)
+    h = 1e-6
+    for j in range(wl.ndim):
+        xp, xm = x.copy(), x.copy()
+        xp[j] += h
+        xm[j] -= h
+        fp, fm = _f(torch_cuda, p, xp), _f(torch_cuda, p, xm)
+        same = (fp != 0) & (fm != 0) & (f != 0)
+        fd = (fp - fm) / (2 * h)
+        scale = np.abs(fd) + np.abs(f)          # derivative relative to the value's scale
+        err = np.abs(dx[j] - fd)[same] / scale[same]
+        assert err.max() < 1e-5, (name, j, err.max())
+
+
+@pytest.mark.parametrize("name,n", [("gg_ttx", 200), ("uux_ttx", 100), ("gg_ttxg", 100), ("uux_ttxg", 80),
+                                    ("gg_ttxgg", 40)])
+def test_dmt_matches_central_differences(torch_cuda, procs, name, n):
+    wl = W.WORKLOADS[name]
+    x = W.uniform_points(wl.ndim, n, 43)
+    h = 1e-3 * wl.m_top
+    f, dp, dx = _grad(torch_cuda, procs(name), x)
+    fp = _f(torch_cuda, procs(name, m_top=wl.m_top + h), x)
+    fm = _f(torch_cuda, procs(name, m_top=wl.m_top - h), x)
+    same = (fp != 0) & (fm != 0) & (f != 0)
+    assert same.sum() > 0.5 * n
+    fd = (fp - fm) / (2 * h)
+    # relative to |f|/m_t: the natural scale of a mass derivative
+    err = np.abs(dp[0] - fd)[same] / (np.abs(fd) + np.abs(f) / wl.m_top)[same]
+    assert err.max() < 1e-4, (name, err.max())
+
+
+@pytest.mark.parametrize("name", ["gg_ttx", "gg_ttxg", "uux_ttxg"])
+def test_dalphas_is_exact(torch_cuda, procs, name):
+    wl = W.WORKLOADS[name]
+    x = W.uniform_points(wl.ndim, 100, 44)
+    f, dp, dx = _grad(torch_cuda, procs(name), x)
+    k = {"gg_ttx": 2, "gg_ttxg": 3, "uux_ttxg": 3}[name]
+    nz = f != 0
+    assert np.allclose(dp[1][nz], k * f[nz] / wl.alpha_s, rtol=1e-14)
+    h = 1e-3 * wl.alpha_s
+    fp = _f(torch_cuda, procs(name, alpha_s=wl.alpha_s + h), x)
+    fm = _f(torch_cuda, procs(name, alpha_s=wl.alpha_s - h), x)
+    fd = (fp - fm) / (2 * h)
+    assert np.max(np.abs(dp[1][nz] / fd[nz] - 1)) < 1e-5
+
+
+@pytest.mark.parametrize("name,n", [("gg_ttx", 12), ("gg_ttxg", 8)])
+def test_grad_matches_oracle_richardson(torch_cuda, procs, name, n):
+    from oracle.integrand import Integrand
+    wl = W.WORKLOADS[name]
+    x = W.uniform_points(wl.ndim, n, 45)
+    f, dp, dx = _grad(torch_cuda, procs(name), x)
+
+    def fo(mt):
+        return Integrand(wl, m_top=mt)(x)
+
+    def rich(fun, x0, h):
+        d1 = (fun(x0 + h) - fun(x0 - h)) / (2 * h)
+        d2 = (fun(x0 + h / 2) - fun(x0 - h / 2)) / h
+        return d2 + (d2 - d1) / 3
+    mt = wl.m_top
+    ref = rich(fo, mt, 1e-2 * mt)
+    nz = f != 0
+    err = np.abs(dp[0] - ref)[nz] / (np.abs(ref) + np.abs(f) / mt)[nz]
+    assert err.max() < 1e-6, err.max()
+    I = Integrand(wl)
+    for j in (0, wl.ndim - 1):
+        def fx(v, j=j):
+            xx = x.copy()
+            xx[j] = v
+            return I(xx)
+        ref = rich(fx, x[j], 1e-4)
+        err = np.abs(dx[j] - ref)[nz] / (np.abs(ref) + np.abs(f))[nz]
+        assert err.max() < 1e-6, (j, err.max())
+
+
+def test_summed_dsigma_dmt_and_boundary_term(torch_cuda, procs):
+    # pathwise estimator of dsigma/dm_t = mean df/dm_t against the finite
+    # difference of the same-point mean, restricted to points that keep their
+    # cut status; the full finite difference also contains the boundary term
+    wl = W.GG_TTXG
+    n = 20000
+    x = W.uniform_points(wl.ndim, n, 46)
+    h = 1e-3 * wl.m_top
+    f, dp, dx = _grad(torch_cuda, procs("gg_ttxg"), x)
+    fp = _f(torch_cuda, procs("gg_ttxg", m_top=wl.m_top + h), x)
+    fm = _f(torch_cuda, procs("gg_ttxg", m_top=wl.m_top - h), x)
+    same = (fp != 0) & (fm != 0) & (f != 0)
+    pathwise = np.mean(np.where(same, dp[0], 0.0))
+    fd_same = np.mean(np.where(same, (fp - fm) / (2 * h), 0.0))
+    fd_all = np.mean((fp - fm) / (2 * h))
+    assert abs(pathwise / fd_same - 1) < 1e-4
+    boundary = fd_all - fd_same
+    # moving the cut boundary is a small effect at pT > 20 GeV
+    assert abs(boundary) < 0.05 * abs(fd_all)
+
+
+def test_autograd_wrapper(torch_cuda, procs):
+    torch = torch_cuda
+    from paper_2106_10279_gb300 import api
+    wl = W.GG_TTX
+    p = procs("gg_ttx")
+    x = torch.from_numpy(W.uniform_points(wl.ndim, 500, 47)).cuda().requires_grad_(True)
+    prm = torch.tensor([wl.m_top, wl.alpha_s], dtype=torch.float64, device="cuda", requires_grad=True)
+    f = api.integrand_with_grad(p, x, prm)
+    sigma = f.mean()
+    sigma.backward()
+    f2, dp, dx = p.grad(x.detach())
+    assert torch.allclose(x.grad, dx / 500, rtol=1e-14, atol=0)
+    assert torch.allclose(prm.grad, dp.mean(dim=1), rtol=1e-12)
+    assert prm.grad[1].item() == pytest.approx(2 * sigma.item() / wl.alpha_s, rel=1e-12)
