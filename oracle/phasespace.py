@@ -76,7 +76,7 @@ def _bisect(G, target, iters=200):
     return 0.5 * (lo + hi)
 
 
-def _mass_ratio(r, m: int):
+def _mass_ratio(r, m: int, complement: bool = False):
     """Solve F(x) = m x^(m-1) - (m-1) x^m = r for x in [0, 1].
 
     For r <= 1/2 by bisection on F(x) = r.  For r > 1/2 the root is close to
@@ -84,14 +84,18 @@ def _mass_ratio(r, m: int):
     same equation is solved for d = 1 - x in the form 1 - F(1 - d) = 1 - r,
     with 1 - F(1 - d) = sum_{k>=2} c_k (-d)^k expanded with exact integer
     coefficients c_k = (m-1) C(m, k) - m C(m-1, k) (1 - r is exact for
-    r >= 1/2).
+    r >= 1/2).  With complement=True returns (x, d) with d = 1 - x carried
+    to full relative precision (rounding x to a double near 1 would lose it).
     """
     r = np.asarray(r, dtype=np.float64)
     low = _bisect(lambda x: m * x ** (m - 1) - (m - 1) * x ** m, r)
     coef = [(m - 1) * math.comb(m, k) - m * math.comb(m - 1, k) for k in range(m + 1)]
     G = lambda d: sum(coef[k] * (-d) ** k for k in range(2, m + 1))
-    high = 1.0 - _bisect(G, 1.0 - r)
-    return np.where(r <= 0.5, low, high)
+    d_high = _bisect(G, 1.0 - r)
+    x = np.where(r <= 0.5, low, 1.0 - d_high)
+    if complement:
+        return x, np.where(r <= 0.5, 1.0 - low, d_high)
+    return x
 
 
 def massless_diet(u, sqrt_s):
@@ -117,12 +121,15 @@ def massless_diet(u, sqrt_s):
         col += 2
         m_daughter = n - k - 1            # massless particles left in Q_{k+1}
         if m_daughter >= 2:
-            x = _mass_ratio(u[col], m_daughter)
+            x, d = _mass_ratio(u[col], m_daughter, complement=True)
             col += 1
             M_next = M * np.sqrt(x)
         else:
+            d = np.ones_like(M)
             M_next = np.zeros_like(M)
-        e = (M * M - M_next * M_next) / (2.0 * M)
+        # energy of the massless daughter in the rest frame of Q_k:
+        # (M^2 - M_next^2) / (2M) = M (1 - x) / 2, taken from 1 - x directly
+        e = 0.5 * M * d
         sth = np.sqrt(np.maximum(0.0, 1.0 - cth * cth))
         q = np.stack([e, e * sth * np.cos(phi), e * sth * np.sin(phi), e * cth], axis=-1)
         rest = np.stack([M - e, -q[:, 1], -q[:, 2], -q[:, 3]], axis=-1)

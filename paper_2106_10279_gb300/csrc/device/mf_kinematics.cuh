@@ -70,12 +70,37 @@ MF_DEV void boost_from_rest(const T *p, const T *Q, const T &M, T *out) {
     out[3] = p[3] + c * Q[3];
 }
 
-// Squared-mass ratio x of a daughter system of m massless particles:
-// solves m x^(m-1) - (m-1) x^m = r on [0, 1].
-MF_DEV double mass_ratio(int m, double r) {
+#define MF_MAX_MASS_RATIO_M 8   // daughter systems of up to 8 massless particles
+
+// Safeguarded Newton solve of an increasing G on [0, 1] for G(z) = t, with
+// G and G' from g(z, &dG).
+template <typename Gf>
+MF_DEV double increasing_root(Gf g, double t, double z) {
+    double lo = 0.0, hi = 1.0;
+    for (int it = 0; it < 200; ++it) {
+        double dG;
+        double f = g(z, dG) - t;
+        if (f < 0.0) lo = z; else hi = z;
+        double nz = (dG > 0.0) ? z - f / dG : 0.5 * (lo + hi);
+        if (!(nz > lo && nz < hi)) nz = 0.5 * (lo + hi);
+        if (fabs(nz - z) <= 4e-16 * z || hi - lo <= 4e-16 * hi) return nz;
+        z = nz;
+    }
+    return z;
+}
+
+// Squared-mass ratio x of a daughter system of m massless particles: solves
+// F(x) = m x^(m-1) - (m-1) x^m = r on [0, 1], and returns x with its
+// complement d = 1 - x, both to full relative precision.  For r > 1/2 the
+// root is near 1, where F is flat and x as a double fixes 1 - x only to
+// ~sqrt(eps); there d solves the complementary equation
+// G(d) = 1 - F(1 - d) = sum_{k>=2} c_k (-d)^k = 1 - r with the exact integer
+// coefficients c_k = (m-1) C(m, k) - m C(m-1, k) (1 - r is exact).
+MF_DEV double mass_ratio(int m, double r, double &d) {
     if (m == 2) {
-        // 2x - x^2 = r  ->  x = 1 - sqrt(1 - r) = r / (1 + sqrt(1 - r))
-        return r / (1.0 + sqrt(1.0 - r));
+        // 2x - x^2 = r  ->  d = sqrt(1 - r), x = r / (1 + d)
+        d = sqrt(1.0 - r);
+        return r / (1.0 + d);
     }
     if (m == 3) {
         // 3x^2 - 2x^3 = r is symmetric under (x, r) -> (1-x, 1-r): solve the
@@ -85,40 +110,54 @@ MF_DEV double mass_ratio(int m, double r) {
         double s = sqrt(t / 3.0);
         for (int it = 0; it < 60; ++it) {
             double f = s * s * (3.0 - 2.0 * s) - t;
-            double d = 6.0 * s * (1.0 - s);
-            if (d <= 0.0) break;
-            double ns = s - f / d;
+            double dd = 6.0 * s * (1.0 - s);
+            if (dd <= 0.0) break;
+            double ns = s - f / dd;
             if (ns < 0.0) ns = 0.5 * s;
             if (ns > 0.5) ns = 0.5 * (s + 0.5);
             double step = fabs(ns - s);
             s = ns;
             if (step <= 1e-17 + 4e-16 * s) break;
         }
+        d = upper ? s : 1.0 - s;
         return upper ? 1.0 - s : s;
     }
-    // general m: Newton safeguarded by bisection on [lo, hi]
-    double lo = 0.0, hi = 1.0, x = pow(r, 1.0 / (m - 1));
-    for (int it = 0; it < 200; ++it) {
-        double xm2 = pow(x, m - 2);
-        double f = m * xm2 * x - (m - 1) * xm2 * x * x - r;
-        if (f < 0.0) lo = x; else hi = x;
-        double d = m * (m - 1) * xm2 * (1.0 - x);
-        double nx = (d > 0.0) ? x - f / d : 0.5 * (lo + hi);
-        if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
-        if (fabs(nx - x) <= 4e-16 * x || hi - lo <= 4e-16 * hi) { x = nx; break; }
-        x = nx;
+    if (r <= 0.5) {
+        double x = increasing_root([m](double z, double &dG) {
+            double zm2 = pow(z, m - 2);
+            dG = m * (m - 1) * zm2 * (1.0 - z);
+            return m * zm2 * z - (m - 1) * zm2 * z * z;
+        }, r, pow(r, 1.0 / (m - 1)));
+        d = 1.0 - x;
+        return x;
     }
-    return x;
+    d = increasing_root([m](double z, double &dG) {
+        // Horner in -z over k = m .. 2 of c_k, then times z^2
+        double acc = 0.0, cm = 1.0, cm1 = 1.0;     // C(m, k), C(m-1, k) from k = 0 upwards
+        double c[MF_MAX_MASS_RATIO_M + 1];
+        for (int k = 0; k <= m; ++k) {
+            c[k] = (m - 1) * cm - m * (k <= m - 1 ? cm1 : 0.0);
+            cm = cm * (m - k) / (k + 1);
+            cm1 = cm1 * (m - 1 - k) / (k + 1);
+        }
+        for (int k = m; k >= 2; --k) acc = acc * (-z) + c[k];
+        dG = m * (m - 1) * pow(1.0 - z, m - 2) * z;
+        return acc * z * z;
+    }, 1.0 - r, sqrt((1.0 - r) / (0.5 * m * (m - 1))));
+    return 1.0 - d;
 }
 // With derivatives: the root's value from the double solver, its tangent from
-// the implicit function theorem, dx = dr / F'(x), F' = m(m-1) x^(m-2) (1-x).
+// the implicit function theorem, dx = -dd = dr / F'(x), F' = m(m-1) x^(m-2) (1-x).
 template <int K>
-MF_DEV Dual<K> mass_ratio(int m, const Dual<K> &r) {
-    double x = mass_ratio(m, r.v);
+MF_DEV Dual<K> mass_ratio(int m, const Dual<K> &r, Dual<K> &d) {
+    double dv;
+    double x = mass_ratio(m, r.v, dv);
     double xm2 = 1.0;
     for (int i = 0; i < m - 2; ++i) xm2 *= x;
-    double dF = m * (m - 1) * xm2 * (1.0 - x);
-    return chain(r, x, dF > 0.0 ? 1.0 / dF : 0.0);
+    double dF = m * (m - 1) * xm2 * dv;
+    double inv = dF > 0.0 ? 1.0 / dF : 0.0;
+    d = chain(r, dv, -inv);
+    return chain(r, x, inv);
 }
 
 // Flat massless n-body momenta in the centre-of-mass frame of energy rs from
@@ -134,13 +173,14 @@ MF_DEV void massless_diet(const T *u, const T &rs, T p[N][4]) {
         T phi = 6.283185307179586 * u[col + 1];
         col += 2;
         int md = N - k - 1;
-        T Mn = T(0.0);
+        T Mn = T(0.0), d = T(1.0);
         if (md >= 2) {
-            T x = mass_ratio(md, u[col]);
+            T x = mass_ratio(md, u[col], d);
             col += 1;
             Mn = M * sqrt(x);
         }
-        T e = (M - Mn) * (M + Mn) / (2.0 * M);
+        // daughter energy in the rest frame of Q: (M^2 - Mn^2) / (2M) = M (1 - x) / 2
+        T e = 0.5 * M * d;
         T s2 = (1.0 - cth) * (1.0 + cth);
         T sth = value(s2) > 0.0 ? sqrt(s2) : T(0.0);
         T sp, cp;

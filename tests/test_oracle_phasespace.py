@@ -164,3 +164,17 @@ def test_mass_ratio_root_full_precision_near_both_ends(m):
     # and 1 - x is resolved far beyond sqrt(eps): against the m = 2 closed form
     if m == 2:
         assert np.all(np.abs(d[~low] - np.sqrt(1 - r[~low])) <= 2 * u[~low])
+
+
+def test_daughter_energy_keeps_precision_at_mass_ratio_near_one():
+    # first decay of n = 3 in the CM frame: the massless daughter has
+    # E = sqrt(s)(1 - x)/2 with 1 - x = sqrt(1 - r) (m = 2 closed form); for r
+    # next to 1 it is ~1e-6 sqrt(s) and must still be exact to rounding
+    r = np.array([0.5, 0.9, 1 - 1e-9, 1 - 1e-12, 1 - 2.0 ** -52])
+    N = r.size
+    u = np.vstack([np.full(N, 0.3), np.full(N, 0.6), r, np.full(N, 0.7), np.full(N, 0.2)])
+    rs = 1000.0
+    p = ps.massless_diet(u, rs)
+    e = p[:, 0, 0]
+    assert np.all(np.abs(e / (rs * np.sqrt(1 - r) / 2) - 1) <= 4 * np.finfo(float).eps)
+    assert np.max(np.abs(p.sum(axis=1)[:, 0] - rs)) <= 4e-13 * rs
