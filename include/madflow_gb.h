@@ -113,6 +113,9 @@ typedef struct {
 #define MF_MAX_LEGS 8
 #define MF_MAX_JAMP 128
 #define MF_MAX_DIM 20
+#define MF_MAX_ITER 1024        /* Vegas iterations per grid */
+#define MF_MAX_TREE_NODES 128  /* tree nodes one shard returns */
+#define MF_CHUNK 4096          /* points per accumulation chunk */
 
 typedef struct {
     /* external legs; legs 0 and 1 are the incoming partons along +z and -z */
@@ -234,7 +237,7 @@ typedef struct {
 } mf_iter_result;
 
 /* mf_vegas_create: a grid of ndim dimensions x nbins bins (uniform), refinement
- * damping alpha (1.5 is the customary value).  nbins in [2, 256]. */
+ * damping alpha (1.5 is the customary value).  nbins in [2, 64]. */
 mf_status mf_vegas_create(int32_t ndim, int32_t nbins, double alpha, mf_vegas **out);
 mf_status mf_vegas_destroy(mf_vegas *v);
 
@@ -243,7 +246,9 @@ mf_status mf_vegas_destroy(mf_vegas *v);
  * numbers from Philox4x64-10 with key (seed, 0) and counter (i, t, k, block),
  * maps them through its grid, evaluates the integrand, accumulates sum w,
  * sum w^2 and, per dimension and bin, sum w^2 and counts in a fixed order
- * (bit-reproducible for a given seed whatever the launch configuration), then
+ * (bit-reproducible for a given seed whatever the launch configuration: per
+ * chunk of MF_CHUNK points a fixed in-chunk order, across chunks the pairwise
+ * tree of mf_tree_reduce), then
  * refines the grid (unless refine == 0) and combines the iteration with the
  * previous ones.  Synchronous: returns after out[k] (host [nproc]) is filled.
  * MF_ENAN if any point's weight was not finite (results still written). */
@@ -251,6 +256,67 @@ mf_status mf_vegas_iterate(mf_vegas *const *grids, mf_process *const *procs,
                            const int64_t *n_events, int32_t nproc, uint64_t seed,
                            mf_precision prec, int32_t refine, mf_iter_result *out,
                            void *stream);
+
+/* ---- Data-parallel iterations (Sec. 2.3: points are independent, so one
+ * iteration splits across devices with one exchange of partial sums).
+ *
+ * The n_total points of an iteration form nchunks = ceil(n_total / MF_CHUNK)
+ * chunks of MF_CHUNK consecutive points.  Their partial sums (K numbers per
+ * chunk, K = mf_vegas_partial_size: sum w, sum w^2, non-zero count, nan count,
+ * per dimension and bin sum w^2, then per dimension and bin counts) are added
+ * along a fixed binary tree: node (l, i) covers chunks [i 2^l, (i+1) 2^l) and
+ * exists when i 2^l < nchunks; its value is the sum of its two children, or
+ * its left child when the right one does not exist; the root is (L, 0) with
+ * 2^L >= nchunks.  A rank that evaluates chunks [c0, c1) returns the maximal
+ * aligned nodes inside its range (mf_tree_frontier); any set of ranks whose
+ * ranges partition [0, nchunks) then rebuilds exactly the root that
+ * mf_vegas_iterate computes on one device, so every rank refines its own copy
+ * of the grid to the same bits and no broadcast is needed.
+ *
+ * A tree node is exchanged as a record of 2 + K doubles: (level, index, K
+ * values). */
+mf_status mf_vegas_partial_size(const mf_vegas *v, int32_t *K);
+
+/* mf_vegas_shard_accumulate: evaluate chunks [chunk_begin, chunk_end) of the
+ * next iteration (points chunk_begin*MF_CHUNK ... min(chunk_end*MF_CHUNK,
+ * n_total) - 1, with the Philox counters of their global indices and the
+ * subprocess index `subprocess`) through the grid v, and write this range's
+ * tree nodes into nodes (host, capacity MF_MAX_TREE_NODES records of 2 + K
+ * doubles); *n_nodes receives their number.  An empty range returns no node.
+ * Does not advance the iteration counter.  Synchronous on stream. */
+mf_status mf_vegas_shard_accumulate(mf_vegas *v, mf_process *p, int64_t n_total, int64_t chunk_begin,
+                                    int64_t chunk_end, int32_t subprocess, uint64_t seed, mf_precision prec,
+                                    double *nodes, int32_t *n_nodes, void *stream);
+
+/* mf_vegas_shard_finish: combine the nodes of all ranks (host, n_nodes
+ * records, in any order) into the iteration totals, then finish the iteration
+ * as mf_vegas_iterate does (histogram, estimate, combination, refinement
+ * unless refine == 0) and advance the iteration counter.  MF_EINVAL if the
+ * nodes do not partition the chunk range exactly (missing, overlapping or
+ * duplicate nodes).  MF_ENAN as mf_vegas_iterate.  Synchronous on stream. */
+mf_status mf_vegas_shard_finish(mf_vegas *v, int64_t n_total, const double *nodes, int32_t n_nodes,
+                                int32_t refine, mf_iter_result *out, void *stream);
+
+/* Host-only helpers of the tree (no device needed).  mf_tree_frontier writes
+ * the (level, index) pairs of the maximal aligned nodes of chunks
+ * [chunk_begin, chunk_end) of an nchunks-chunk tree into ids (host, capacity
+ * pairs; *n receives the count; MF_EINVAL if capacity is too small); the range
+ * ending at nchunks also owns the truncated right edge.  mf_tree_reduce
+ * combines records (2 + K doubles each) that partition node (level, index)
+ * into that node's K values (host out[K]). */
+mf_status mf_tree_frontier(int64_t chunk_begin, int64_t chunk_end, int64_t nchunks, int64_t *ids,
+                           int32_t capacity, int32_t *n);
+mf_status mf_tree_reduce(const double *nodes, int32_t n_nodes, int32_t K, int64_t nchunks, int32_t level,
+                         int64_t index, double *out);
+
+/* ---- Checkpoint of a grid: edges, last histogram and counts, and the
+ * (I_k, sigma_k) of the iterations so far, so that a run resumes with the same
+ * combination.  mf_vegas_save with buf == NULL stores the size needed in *len;
+ * otherwise *len is the capacity on entry and the size written on return
+ * (MF_EINVAL if too small).  mf_vegas_load checks the record (tag, shape,
+ * size, edges) and restores it into a grid of the same ndim and nbins. */
+mf_status mf_vegas_save(const mf_vegas *v, void *buf, size_t *len);
+mf_status mf_vegas_load(mf_vegas *v, const void *buf, size_t len);
 
 /* Device time, in ms, of the last fused integrand kernel that mf_vegas_iterate
  * launched for this process (CUDA events recorded on the launching stream

@@ -76,9 +76,21 @@ SIGNATURES = {
     "mf_vegas_set_grid": (c_i32, [C.c_void_p, P(C.c_double)]),
     "mf_vegas_get_histogram": (c_i32, [C.c_void_p, P(C.c_double), P(c_i64)]),
     "mf_vegas_get_shape": (c_i32, [C.c_void_p, P(c_i32), P(c_i32), P(c_i32)]),
+    "mf_vegas_partial_size": (c_i32, [C.c_void_p, P(c_i32)]),
+    "mf_vegas_shard_accumulate": (c_i32, [C.c_void_p, C.c_void_p, c_i64, c_i64, c_i64, c_i32, C.c_uint64, c_i32,
+                                          P(C.c_double), P(c_i32), C.c_void_p]),
+    "mf_vegas_shard_finish": (c_i32, [C.c_void_p, c_i64, P(C.c_double), c_i32, c_i32, P(mf_iter_result),
+                                      C.c_void_p]),
+    "mf_tree_frontier": (c_i32, [c_i64, c_i64, c_i64, P(c_i64), c_i32, P(c_i32)]),
+    "mf_tree_reduce": (c_i32, [P(C.c_double), c_i32, c_i32, c_i64, c_i32, c_i64, P(C.c_double)]),
+    "mf_vegas_save": (c_i32, [C.c_void_p, C.c_void_p, P(C.c_size_t)]),
+    "mf_vegas_load": (c_i32, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "mf_generate_kernel_source": (c_i32, [P(mf_process_desc), c_i32, c_i32, C.c_char_p, P(C.c_size_t)]),
     "mf_last_error": (C.c_char_p, []),
 }
+
+MF_CHUNK = 4096
+MF_MAX_TREE_NODES = 128
 
 _lib = None
 

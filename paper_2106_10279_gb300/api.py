@@ -198,7 +198,86 @@ def mf_vegas_iterate(grids, procs, n_events, seed: int, precision="fp64", refine
     st = L.lib().mf_vegas_iterate(G, Pp, N, k, seed, _PREC[precision], 1 if refine else 0, out,
                                   _stream_ptr(stream))
     L.check(st, "mf_vegas_iterate", allow=(L.MF_OK, L.MF_ENAN))
-    return [{name: getattr(r, name) for name, _ in r._fields_} for r in out]
+    return [_result(r) for r in out]
+
+
+def _result(r):
+    return {name: getattr(r, name) for name, _ in r._fields_}
+
+
+def mf_vegas_partial_size(h) -> int:
+    k = C.c_int32()
+    L.check(L.lib().mf_vegas_partial_size(h, C.byref(k)), "mf_vegas_partial_size")
+    return k.value
+
+
+def mf_vegas_shard_accumulate(h, proc_h, n_total: int, chunk_begin: int, chunk_end: int, subprocess: int,
+                              seed: int, precision="fp64", stream=None):
+    """This rank's tree nodes, float64 [n_nodes, 2 + K] (level, index, values)."""
+    K = mf_vegas_partial_size(h)
+    buf = np.zeros((L.MF_MAX_TREE_NODES, 2 + K))
+    nn = C.c_int32()
+    st = L.lib().mf_vegas_shard_accumulate(h, proc_h, n_total, chunk_begin, chunk_end, subprocess, seed,
+                                           _PREC[precision], buf.ctypes.data_as(C.POINTER(C.c_double)),
+                                           C.byref(nn), _stream_ptr(stream))
+    L.check(st, "mf_vegas_shard_accumulate")
+    return buf[:nn.value].copy()
+
+
+def mf_vegas_shard_finish(h, n_total: int, nodes, refine: bool = True, stream=None):
+    nodes = np.ascontiguousarray(nodes, dtype=np.float64).reshape(-1, mf_vegas_partial_size(h) + 2)
+    out = L.mf_iter_result()
+    st = L.lib().mf_vegas_shard_finish(h, n_total, nodes.ctypes.data_as(C.POINTER(C.c_double)), nodes.shape[0],
+                                       1 if refine else 0, C.byref(out), _stream_ptr(stream))
+    L.check(st, "mf_vegas_shard_finish", allow=(L.MF_OK, L.MF_ENAN))
+    return _result(out)
+
+
+def mf_tree_frontier(chunk_begin: int, chunk_end: int, nchunks: int):
+    """(level, index) pairs, int64 [n, 2], of the maximal aligned nodes of a chunk range."""
+    ids = np.zeros((L.MF_MAX_TREE_NODES, 2), dtype=np.int64)
+    n = C.c_int32()
+    L.check(L.lib().mf_tree_frontier(chunk_begin, chunk_end, nchunks, ids.ctypes.data_as(C.POINTER(C.c_int64)),
+                                     L.MF_MAX_TREE_NODES, C.byref(n)), "mf_tree_frontier")
+    return ids[:n.value].copy()
+
+
+def mf_tree_reduce(nodes, nchunks: int, level: int, index: int):
+    """Values [K] of node (level, index) from records [n, 2 + K] that partition it."""
+    nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+    if nodes.ndim != 2 or nodes.shape[1] < 3:
+        raise ValueError("nodes must be [n, 2 + K]")
+    K = nodes.shape[1] - 2
+    out = np.zeros(K)
+    L.check(L.lib().mf_tree_reduce(nodes.ctypes.data_as(C.POINTER(C.c_double)), nodes.shape[0], K, nchunks,
+                                   level, index, out.ctypes.data_as(C.POINTER(C.c_double))), "mf_tree_reduce")
+    return out
+
+
+def tree_levels(nchunks: int) -> int:
+    L_ = 0
+    while (1 << L_) < nchunks:
+        L_ += 1
+    return L_
+
+
+def shard_chunks(n_total: int, rank: int, world: int):
+    """Chunk range [c0, c1) of rank `rank` out of `world` (whole chunks, balanced)."""
+    nchunks = (n_total + L.MF_CHUNK - 1) // L.MF_CHUNK
+    return nchunks * rank // world, nchunks * (rank + 1) // world
+
+
+def mf_vegas_save(h) -> bytes:
+    n = C.c_size_t(0)
+    L.check(L.lib().mf_vegas_save(h, None, C.byref(n)), "mf_vegas_save")
+    buf = C.create_string_buffer(n.value)
+    L.check(L.lib().mf_vegas_save(h, buf, C.byref(n)), "mf_vegas_save")
+    return buf.raw[:n.value]
+
+
+def mf_vegas_load(h, data: bytes):
+    buf = C.create_string_buffer(bytes(data), len(data))
+    L.check(L.lib().mf_vegas_load(h, buf, len(data)), "mf_vegas_load")
 
 
 def mf_vegas_get_grid(h):
@@ -309,6 +388,22 @@ class Vegas:
 
     def histogram(self):
         return mf_vegas_get_histogram(self.handle)
+
+    def iterate_shard(self, proc: Process, n_total: int, chunk_begin: int, chunk_end: int, seed: int,
+                      subprocess: int = 0, precision="fp64", stream=None):
+        """This rank's tree nodes of the next iteration (see mf_vegas_shard_accumulate)."""
+        return mf_vegas_shard_accumulate(self.handle, proc.handle, n_total, chunk_begin, chunk_end, subprocess,
+                                         seed, precision, stream)
+
+    def finish_shards(self, n_total: int, nodes, refine=True, stream=None):
+        """Combine every rank's nodes and finish the iteration (see mf_vegas_shard_finish)."""
+        return mf_vegas_shard_finish(self.handle, n_total, nodes, refine, stream)
+
+    def save(self) -> bytes:
+        return mf_vegas_save(self.handle)
+
+    def load(self, data: bytes):
+        mf_vegas_load(self.handle, data)
 
     def close(self):
         if self.handle:

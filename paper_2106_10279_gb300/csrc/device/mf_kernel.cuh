@@ -158,7 +158,7 @@ MF_DEV void kernel_body(const KParams &kp) {
             } else {
 #pragma unroll
                 for (int b = 0; b < (NDIM + 3) / 4; ++b) {
-                    uint64_t c[4] = {(uint64_t)e, kp.iteration, kp.subprocess, (uint64_t)b};
+                    uint64_t c[4] = {(uint64_t)(e + kp.ev0), kp.iteration, kp.subprocess, (uint64_t)b};
                     philox4x64_10(c, kp.seed, 0ull);
 #pragma unroll
                     for (int q = 0; q < 4; ++q)

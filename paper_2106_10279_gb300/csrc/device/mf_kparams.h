@@ -18,6 +18,7 @@ struct mf_kparams {
     double *w_out;             // mode 1: w = f J_V [n]
     uint8_t *bins_out;         // mode 1: bin indices, SoA [NDIM][n]
     uint64_t seed, iteration, subprocess;
+    int64_t ev0;               // mode 1: Philox counter of the first point
     double S;                  // collider energy squared
     double ln_tau_min;         // ln((sum of final masses)^2 / S)
     double w0_const;           // massless phase-space volume / s-hat^(n-2)

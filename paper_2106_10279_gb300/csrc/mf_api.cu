@@ -1,10 +1,12 @@
 // C entry points of libmadflow_gb and the statically compiled kernels of the
-// Vegas iteration (accumulation, fixed-order reduction, refinement and the
-// combination of iterations; Sec. 2.2 and Lepage 1978).
+// Vegas iteration (accumulation, fixed pairwise-tree reduction over chunks,
+// refinement and the combination of iterations; Sec. 2.2 and Lepage 1978).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -39,7 +41,9 @@ namespace {
 constexpr int kChunk = 4096;           // events per accumulation chunk (fixed: results
                                        // do not depend on launch shapes)
 constexpr int kAccThreads = 256;
-constexpr int kRedThreads = 256;
+constexpr int kTreeLog = 8;            // vegas_tree_kernel: 2^kTreeLog threads
+constexpr int kTreeThreads = 1 << kTreeLog;
+constexpr int kTreeMaxLevel = 40;      // at most 2^40 chunks per iteration
 constexpr double kGeV2pb = 0.3893793721e9;
 constexpr double kPi = 3.14159265358979323846;
 
@@ -80,9 +84,10 @@ __global__ void scale_kernel(double *v, int n, double s) {
 }
 
 // ----------------------------------------------------------------------------
-// Vegas accumulation: one block per chunk of kChunk events.  Slot layout per
-// chunk: [sum w, sum w^2, nonzero, nan, hist[ndim][nb], counts[ndim][nb]].
-// Non-finite weights count as nan and contribute 0.
+// Vegas accumulation: one block per chunk of kChunk events.  Components per
+// chunk: [sum w, sum w^2, nonzero, nan, hist[ndim][nb], counts[ndim][nb]],
+// stored component-major: slots[k * ld + chunk].  Non-finite weights count as
+// nan and contribute 0.
 // ----------------------------------------------------------------------------
 __device__ double block_tree_sum(double *buf, int m) {
     // fixed pairwise tree over kChunk slots (zero padded): pairs (i, i + s)
@@ -98,7 +103,8 @@ __device__ double block_tree_sum(double *buf, int m) {
 }
 
 __global__ void __launch_bounds__(kAccThreads) vegas_accumulate_kernel(const double *w, const uint8_t *bins,
-                                                                       int64_t n, int ndim, int nb, double *slots) {
+                                                                       int64_t n, int ndim, int nb, double *slots,
+                                                                       int64_t ld) {
     extern __shared__ double sh[];
     double *sw = sh;                    // [kChunk] sanitised w
     double *buf = sh + kChunk;          // [kChunk] tree buffer
@@ -108,8 +114,7 @@ __global__ void __launch_bounds__(kAccThreads) vegas_accumulate_kernel(const dou
     __shared__ int s_nz, s_nan;
     const int64_t base = (int64_t)blockIdx.x * kChunk;
     const int m = (int)((n - base) < kChunk ? (n - base) : kChunk);
-    const int K = 4 + 2 * ndim * nb;
-    double *slot = slots + (size_t)blockIdx.x * K;
+    double *slot = slots + blockIdx.x;      // component k at slot[k * ld]
     if (threadIdx.x == 0) { s_nz = 0; s_nan = 0; }
     __syncthreads();
     int nz = 0, nn = 0;
@@ -131,7 +136,7 @@ __global__ void __launch_bounds__(kAccThreads) vegas_accumulate_kernel(const dou
     __syncthreads();
     double s2 = block_tree_sum(buf, m);
     if (threadIdx.x == 0) {
-        slot[0] = s1; slot[1] = s2; slot[2] = (double)s_nz; slot[3] = (double)s_nan;
+        slot[0] = s1; slot[ld] = s2; slot[2 * ld] = (double)s_nz; slot[3 * ld] = (double)s_nan;
     }
     // per dimension and bin: 4 segments of kChunk/4 events, each summed in event
     // order by the thread owning (segment, bin), then segments in order
@@ -150,27 +155,66 @@ __global__ void __launch_bounds__(kAccThreads) vegas_accumulate_kernel(const dou
         __syncthreads();
         if (threadIdx.x < nb) {
             int q = threadIdx.x;
-            slot[4 + j * nb + q] = (part[0][q] + part[1][q]) + (part[2][q] + part[3][q]);
-            slot[4 + ndim * nb + j * nb + q] = (cpart[0][q] + cpart[1][q]) + (cpart[2][q] + cpart[3][q]);
+            slot[(size_t)(4 + j * nb + q) * ld] = (part[0][q] + part[1][q]) + (part[2][q] + part[3][q]);
+            slot[(size_t)(4 + ndim * nb + j * nb + q) * ld] = (cpart[0][q] + cpart[1][q]) + (cpart[2][q] + cpart[3][q]);
         }
         __syncthreads();
     }
 }
 
-// fixed-order reduction over chunks: block k sums component k
-__global__ void __launch_bounds__(kRedThreads) vegas_reduce_kernel(const double *slots, int64_t nchunks, int K,
-                                                                   double *tot) {
-    __shared__ double red[kRedThreads];
+// Reduction over chunks along a fixed pairwise tree (mf_tree_reduce states the
+// tree).  Block (k, j) computes component k of node j = (level, index) from the
+// chunk partials slots[k * ld + c - c0] of the chunks the node covers: each
+// thread folds an aligned segment of 2^s chunks with a binary-counter stack
+// (which performs exactly the tree's additions, the last incomplete subtree
+// folded from its right end), then the segments are paired in shared memory.
+__global__ void __launch_bounds__(kTreeThreads) vegas_tree_kernel(const double *slots, int64_t ld, int64_t c0,
+                                                                  int64_t nchunks, int K, const int64_t *node_ids,
+                                                                  double *out) {
+    __shared__ double red[kTreeThreads];
     const int k = blockIdx.x;
-    double acc = 0.0;
-    for (int64_t c = threadIdx.x; c < nchunks; c += kRedThreads) acc += slots[(size_t)c * K + k];
-    red[threadIdx.x] = acc;
+    const int level = (int)node_ids[2 * blockIdx.y];
+    const int64_t first = node_ids[2 * blockIdx.y + 1] << level;
+    const int s = level > kTreeLog ? level - kTreeLog : 0;
+    const int64_t nseg = ((int64_t)1 << level) >> s;                // <= kTreeThreads
+    const int64_t seg_first = first + ((int64_t)threadIdx.x << s);
+    // segments whose first chunk exists
+    const int64_t exist = (nchunks - first + ((int64_t)1 << s) - 1) >> s;
+    int64_t m = exist < nseg ? exist : nseg;
+    double v = 0.0;
+    if ((int64_t)threadIdx.x < m) {
+        double st[kTreeMaxLevel + 2];
+        int lv[kTreeMaxLevel + 2];
+        int top = 0;
+        int64_t end = seg_first + ((int64_t)1 << s);
+        if (end > nchunks) end = nchunks;
+        for (int64_t c = seg_first; c < end; ++c) {
+            double x = slots[(size_t)k * ld + (size_t)(c - c0)];
+            int xl = 0;
+            while (top > 0 && lv[top - 1] == xl) {
+                x = st[top - 1] + x;
+                --top;
+                ++xl;
+            }
+            st[top] = x;
+            lv[top] = xl;
+            ++top;
+        }
+        v = st[top - 1];
+        for (int q = top - 2; q >= 0; --q) v = st[q] + v;
+    }
+    red[threadIdx.x] = v;
     __syncthreads();
-    for (int s = kRedThreads / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + s];
+    for (int64_t w = nseg; w > 1; w >>= 1) {
+        const int64_t i = threadIdx.x;
+        double nv = 0.0;
+        if (i < (w >> 1) && 2 * i < m) nv = (2 * i + 1 < m) ? red[2 * i] + red[2 * i + 1] : red[2 * i];
+        __syncthreads();
+        if (i < (w >> 1)) red[i] = nv;
+        m = (m + 1) >> 1;
         __syncthreads();
     }
-    if (threadIdx.x == 0) tot[k] = red[0];
+    if (threadIdx.x == 0) out[(size_t)blockIdx.y * K + k] = red[0];
 }
 
 // Iteration estimate, the histogram, and the inverse-variance combination of
@@ -744,6 +788,176 @@ extern "C" mf_status mf_grad(mf_process *p, const double *x, int64_t n, double *
 // ----------------------------------------------------------------------------
 // Vegas
 // ----------------------------------------------------------------------------
+namespace {
+
+// The pairwise tree over the chunks of one iteration (host side; the device
+// side is vegas_tree_kernel, which performs the same additions).
+int tree_levels(int64_t nchunks) {
+    int L = 0;
+    while (((int64_t)1 << L) < nchunks) ++L;
+    return L;
+}
+
+// Maximal aligned nodes covering chunks [c0, c1); the shard that ends at the
+// last chunk also owns the tree's truncated right edge.
+void tree_frontier(int64_t c0, int64_t c1, int64_t nchunks, std::vector<int64_t> &ids) {
+    ids.clear();
+    const int L = tree_levels(nchunks);
+    const int64_t hi = c1 >= nchunks ? ((int64_t)1 << L) : c1;
+    int64_t c = c0;
+    while (c < hi) {
+        int l = 0;
+        while (l < L && c % ((int64_t)2 << l) == 0 && c + ((int64_t)2 << l) <= hi) ++l;
+        if (c < nchunks) {
+            ids.push_back(l);
+            ids.push_back(c >> l);
+        }
+        c += (int64_t)1 << l;
+    }
+}
+
+// Combine nodes (records [level, index, K values]) that partition the chunks
+// of node (level, index) into that node's K values.
+mf_status tree_reduce(const double *nodes, int n_nodes, int K, int64_t nchunks, int level, int64_t index,
+                      double *out) {
+    using Key = std::pair<int, int64_t>;
+    std::map<Key, std::vector<double>> cur;
+    for (int j = 0; j < n_nodes; ++j) {
+        const double *r = nodes + (size_t)j * (2 + K);
+        const int l = (int)r[0];
+        const int64_t i = (int64_t)r[1];
+        if (r[0] != (double)l || r[1] != (double)i || l < 0 || l > kTreeMaxLevel || i < 0)
+            return fail(MF_EINVAL, "malformed tree node");
+        if ((i << l) >= nchunks) return fail(MF_EINVAL, "tree node beyond the last chunk");
+        if (l > level || (i >> (level - l)) != index) return fail(MF_EINVAL, "tree node outside the target node");
+        if (!cur.emplace(Key(l, i), std::vector<double>(r + 2, r + 2 + K)).second)
+            return fail(MF_EINVAL, "duplicate tree node");
+    }
+    for (int l = 0; l < level; ++l) {
+        std::vector<std::pair<Key, std::vector<double>>> made;
+        for (auto it = cur.begin(); it != cur.end() && it->first.first == l; ++it) {
+            const int64_t i = it->first.second;
+            if (i & 1) {
+                if (!cur.count(Key(l, i - 1))) return fail(MF_EINVAL, "tree nodes do not cover the range");
+                continue;
+            }
+            auto sib = cur.find(Key(l, i + 1));
+            std::vector<double> v = it->second;
+            if (sib != cur.end()) {
+                for (int k = 0; k < K; ++k) v[k] = v[k] + sib->second[k];
+            } else if (((i + 1) << l) < nchunks) {
+                return fail(MF_EINVAL, "tree nodes do not cover the range");
+            }
+            made.emplace_back(Key(l + 1, i >> 1), std::move(v));
+        }
+        cur.erase(cur.begin(), cur.lower_bound(Key(l + 1, 0)));
+        for (auto &m : made)
+            if (!cur.emplace(m.first, std::move(m.second)).second) return fail(MF_EINVAL, "overlapping tree nodes");
+    }
+    auto root = cur.find(Key(level, index));
+    if (root == cur.end() || cur.size() != 1) return fail(MF_EINVAL, "tree nodes do not cover the range");
+    std::copy(root->second.begin(), root->second.end(), out);
+    return MF_OK;
+}
+
+int partial_size(const mf_vegas *v) { return 4 + 2 * v->ndim * v->nbins; }
+
+// Evaluate points [ev0, ev0 + n) of iteration v->iteration into the process
+// scratch (w, bins) and accumulate their chunks into v->d_slots.
+mf_status run_points(mf_process *p, mf_vegas *v, int prec, int64_t n, int64_t ev0, int subprocess, uint64_t seed,
+                     cudaStream_t s) {
+    mf_status st = compile_precision(p, prec);
+    if (st != MF_OK) return st;
+    if (p->scratch_n < n) {
+        cudaFree(p->d_w);
+        cudaFree(p->d_bins);
+        p->d_w = nullptr;
+        p->d_bins = nullptr;
+        p->scratch_n = 0;
+        MF_CUDA(cudaMalloc(&p->d_w, sizeof(double) * n));
+        MF_CUDA(cudaMalloc(&p->d_bins, (size_t)p->ndim * n));
+        p->scratch_n = n;
+    }
+    const int64_t nchunks = (n + kChunk - 1) / kChunk;
+    const int K = partial_size(v);
+    if (v->slots_cap < nchunks * K + K) {
+        cudaFree(v->d_slots);
+        v->d_slots = nullptr;
+        v->slots_cap = 0;
+        MF_CUDA(cudaMalloc(&v->d_slots, sizeof(double) * (nchunks * K + K)));
+        v->slots_cap = nchunks * K + K;
+    }
+    if (!p->ev_start) {
+        MF_CUDA(cudaEventCreate(&p->ev_start));
+        MF_CUDA(cudaEventCreate(&p->ev_stop));
+    }
+    if (n == 0) return MF_OK;
+    mf_kparams kp;
+    fill_common(*p, kp);
+    set_hel(kp, p->hel, p->n_legs);
+    kp.mode = 1;
+    kp.n = n;
+    kp.ev0 = ev0;
+    kp.grid = v->d_grid;
+    kp.nb = v->nbins;
+    kp.w_out = p->d_w;
+    kp.bins_out = p->d_bins;
+    kp.seed = seed;
+    kp.iteration = (uint64_t)v->iteration;
+    kp.subprocess = (uint64_t)subprocess;
+    MF_CUDA(cudaEventRecord(p->ev_start, s));
+    st = launch(p, prec, kp, s);
+    if (st != MF_OK) return st;
+    MF_CUDA(cudaEventRecord(p->ev_stop, s));
+    const size_t acc_smem = sizeof(double) * 2 * kChunk + kChunk;
+    static bool attr_set = false;
+    if (!attr_set) {
+        MF_CUDA(cudaFuncSetAttribute(vegas_accumulate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)acc_smem));
+        attr_set = true;
+    }
+    vegas_accumulate_kernel<<<(unsigned)nchunks, kAccThreads, acc_smem, s>>>(p->d_w, p->d_bins, n, v->ndim, v->nbins,
+                                                                              v->d_slots, nchunks);
+    MF_CUDA(cudaGetLastError());
+    return MF_OK;
+}
+
+// Nodes ids (host, [n][2]) of the accumulated chunks -> device values [n][K].
+mf_status tree_nodes(mf_vegas *v, int64_t ld, int64_t c0, int64_t nchunks, const std::vector<int64_t> &ids,
+                     cudaStream_t s) {
+    const int n = (int)ids.size() / 2;
+    if (n == 0) return MF_OK;
+    MF_CUDA(cudaMemcpyAsync(v->d_tree_ids, ids.data(), sizeof(int64_t) * ids.size(), cudaMemcpyHostToDevice, s));
+    vegas_tree_kernel<<<dim3((unsigned)partial_size(v), (unsigned)n), kTreeThreads, 0, s>>>(
+        v->d_slots, ld, c0, nchunks, partial_size(v), v->d_tree_ids, v->d_tree_out);
+    MF_CUDA(cudaGetLastError());
+    return MF_OK;
+}
+
+// Iteration estimate, histogram, combination and (optionally) refinement from
+// the totals tot (device [K]) of n points.
+mf_status finish(mf_vegas *v, const double *tot, int64_t n, int refine, cudaStream_t s) {
+    vegas_finalize_kernel<<<1, 128, 0, s>>>(tot, n, v->ndim, v->nbins, v->iteration, v->d_hist, v->d_count,
+                                            v->d_hist_iter, v->d_result);
+    if (refine) vegas_refine_kernel<<<1, 32, 0, s>>>(v->d_grid, v->d_hist, v->ndim, v->nbins, n, v->alpha);
+    MF_CUDA(cudaGetLastError());
+    return MF_OK;
+}
+
+void fill_result(mf_iter_result &o, const mf_vegas *v, int64_t n, const double *r) {
+    o.iteration = v->iteration;
+    o.n_events = n;
+    o.integral = r[0];
+    o.error = r[1];
+    o.sigma = r[2];
+    o.sigma_error = r[3];
+    o.chi2_dof = r[4];
+    o.n_nonzero = (int64_t)r[5];
+    o.n_nan = (int64_t)r[6];
+}
+
+}  // namespace
+
 extern "C" mf_status mf_vegas_create(int32_t ndim, int32_t nbins, double alpha, mf_vegas **out) {
     if (!out) return fail(MF_EINVAL, "out is NULL");
     *out = nullptr;
@@ -758,12 +972,16 @@ extern "C" mf_status mf_vegas_create(int32_t ndim, int32_t nbins, double alpha, 
     v->ndim = ndim;
     v->nbins = nbins;
     v->alpha = alpha;
-    v->max_iter = 1024;
+    v->max_iter = MF_MAX_ITER;
+    const int K = partial_size(v);
     if (cudaMalloc(&v->d_grid, sizeof(double) * ndim * (nbins + 1)) != cudaSuccess ||
         cudaMalloc(&v->d_hist, sizeof(double) * ndim * nbins) != cudaSuccess ||
         cudaMalloc(&v->d_count, sizeof(long long) * ndim * nbins) != cudaSuccess ||
         cudaMalloc(&v->d_hist_iter, sizeof(double) * 2 * v->max_iter) != cudaSuccess ||
-        cudaMalloc(&v->d_result, sizeof(double) * 8) != cudaSuccess) {
+        cudaMalloc(&v->d_result, sizeof(double) * 8) != cudaSuccess ||
+        cudaMalloc(&v->d_tree_ids, sizeof(int64_t) * 2 * MF_MAX_TREE_NODES) != cudaSuccess ||
+        cudaMalloc(&v->d_tree_out, sizeof(double) * (size_t)K * MF_MAX_TREE_NODES) != cudaSuccess ||
+        cudaMalloc(&v->d_tot, sizeof(double) * K) != cudaSuccess) {
         mf_vegas_destroy(v);
         return fail(MF_ENOMEM, "Vegas grid");
     }
@@ -785,6 +1003,9 @@ extern "C" mf_status mf_vegas_destroy(mf_vegas *v) {
     cudaFree(v->d_hist_iter);
     cudaFree(v->d_result);
     cudaFree(v->d_slots);
+    cudaFree(v->d_tree_ids);
+    cudaFree(v->d_tree_out);
+    cudaFree(v->d_tot);
     delete v;
     return MF_OK;
 }
@@ -795,14 +1016,22 @@ extern "C" mf_status mf_vegas_get_grid(const mf_vegas *v, double *edges) {
     return MF_OK;
 }
 
-extern "C" mf_status mf_vegas_set_grid(mf_vegas *v, const double *edges) {
-    if (!v || !edges) return fail(MF_EINVAL, "NULL argument");
+namespace {
+mf_status check_edges(const mf_vegas *v, const double *edges) {
     for (int j = 0; j < v->ndim; ++j) {
         const double *g = edges + (size_t)j * (v->nbins + 1);
         if (g[0] != 0.0 || g[v->nbins] != 1.0) return fail(MF_EINVAL, "grid edges must run from 0 to 1");
         for (int i = 0; i < v->nbins; ++i)
             if (!(g[i + 1] > g[i])) return fail(MF_EINVAL, "grid edges must increase");
     }
+    return MF_OK;
+}
+}  // namespace
+
+extern "C" mf_status mf_vegas_set_grid(mf_vegas *v, const double *edges) {
+    if (!v || !edges) return fail(MF_EINVAL, "NULL argument");
+    mf_status st = check_edges(v, edges);
+    if (st != MF_OK) return st;
     MF_CUDA(cudaMemcpy(v->d_grid, edges, sizeof(double) * v->ndim * (v->nbins + 1), cudaMemcpyHostToDevice));
     return MF_OK;
 }
@@ -832,69 +1061,26 @@ extern "C" mf_status mf_vegas_iterate(mf_vegas *const *grids, mf_process *const 
         if (!grids[k] || !procs[k]) return fail(MF_EINVAL, "NULL grid or process");
         if (grids[k]->ndim != procs[k]->ndim) return fail(MF_EINVAL, "grid and process dimensions differ");
         if (n_events[k] < 2) return fail(MF_EINVAL, "need at least two events per iteration");
+        if ((n_events[k] + kChunk - 1) / kChunk > ((int64_t)1 << kTreeMaxLevel))
+            return fail(MF_EINVAL, "too many events per iteration");
         if (grids[k]->iteration >= grids[k]->max_iter) return fail(MF_EUNSUPPORTED, "too many iterations");
+        for (int q = 0; q < k; ++q)
+            if (grids[q] == grids[k]) return fail(MF_EINVAL, "a grid appears twice");
     }
     std::vector<std::vector<double>> res(nproc, std::vector<double>(8));
-    bool any_nan = false;
     for (int k = 0; k < nproc; ++k) {
         mf_process *p = procs[k];
         mf_vegas *v = grids[k];
         const int64_t n = n_events[k];
-        mf_status st = compile_precision(p, prec);
+        mf_status st = run_points(p, v, prec, n, 0, k, seed, s);
         if (st != MF_OK) return st;
-        if (p->scratch_n < n) {
-            cudaFree(p->d_w);
-            cudaFree(p->d_bins);
-            p->d_w = nullptr;
-            p->d_bins = nullptr;
-            p->scratch_n = 0;
-            MF_CUDA(cudaMalloc(&p->d_w, sizeof(double) * n));
-            MF_CUDA(cudaMalloc(&p->d_bins, (size_t)p->ndim * n));
-            p->scratch_n = n;
-        }
+        // the whole chunk range is the root node of the tree
         const int64_t nchunks = (n + kChunk - 1) / kChunk;
-        const int K = 4 + 2 * v->ndim * v->nbins;
-        if (v->slots_cap < nchunks * K + K) {
-            cudaFree(v->d_slots);
-            v->d_slots = nullptr;
-            v->slots_cap = 0;
-            MF_CUDA(cudaMalloc(&v->d_slots, sizeof(double) * (nchunks * K + K)));
-            v->slots_cap = nchunks * K + K;
-        }
-        mf_kparams kp;
-        fill_common(*p, kp);
-        set_hel(kp, p->hel, p->n_legs);
-        kp.mode = 1;
-        kp.n = n;
-        kp.grid = v->d_grid;
-        kp.nb = v->nbins;
-        kp.w_out = p->d_w;
-        kp.bins_out = p->d_bins;
-        kp.seed = seed;
-        kp.iteration = (uint64_t)v->iteration;
-        kp.subprocess = (uint64_t)k;
-        if (!p->ev_start) {
-            MF_CUDA(cudaEventCreate(&p->ev_start));
-            MF_CUDA(cudaEventCreate(&p->ev_stop));
-        }
-        MF_CUDA(cudaEventRecord(p->ev_start, s));
-        st = launch(p, prec, kp, s);
+        const std::vector<int64_t> root = {tree_levels(nchunks), 0};
+        st = tree_nodes(v, nchunks, 0, nchunks, root, s);
         if (st != MF_OK) return st;
-        MF_CUDA(cudaEventRecord(p->ev_stop, s));
-        size_t acc_smem = sizeof(double) * 2 * kChunk + kChunk;
-        static bool attr_set = false;
-        if (!attr_set) {
-            cudaFuncSetAttribute(vegas_accumulate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc_smem);
-            attr_set = true;
-        }
-        vegas_accumulate_kernel<<<(unsigned)nchunks, kAccThreads, acc_smem, s>>>(p->d_w, p->d_bins, n, v->ndim,
-                                                                                  v->nbins, v->d_slots);
-        double *tot = v->d_slots + nchunks * K;
-        vegas_reduce_kernel<<<K, kRedThreads, 0, s>>>(v->d_slots, nchunks, K, tot);
-        vegas_finalize_kernel<<<1, 128, 0, s>>>(tot, n, v->ndim, v->nbins, v->iteration, v->d_hist, v->d_count,
-                                                v->d_hist_iter, v->d_result);
-        if (refine) vegas_refine_kernel<<<1, 32, 0, s>>>(v->d_grid, v->d_hist, v->ndim, v->nbins, n, v->alpha);
-        MF_CUDA(cudaGetLastError());
+        st = finish(v, v->d_tree_out, n, refine, s);
+        if (st != MF_OK) return st;
         MF_CUDA(cudaMemcpyAsync(res[k].data(), v->d_result, sizeof(double) * 7, cudaMemcpyDeviceToHost, s));
     }
     MF_CUDA(cudaStreamSynchronize(s));
@@ -903,20 +1089,187 @@ extern "C" mf_status mf_vegas_iterate(mf_vegas *const *grids, mf_process *const 
         if (cudaEventElapsedTime(&ms, procs[k]->ev_start, procs[k]->ev_stop) == cudaSuccess)
             procs[k]->last_kernel_ms = ms;
     }
+    bool any_nan = false;
     for (int k = 0; k < nproc; ++k) {
-        mf_vegas *v = grids[k];
-        out[k].iteration = v->iteration;
-        out[k].n_events = n_events[k];
-        out[k].integral = res[k][0];
-        out[k].error = res[k][1];
-        out[k].sigma = res[k][2];
-        out[k].sigma_error = res[k][3];
-        out[k].chi2_dof = res[k][4];
-        out[k].n_nonzero = (int64_t)res[k][5];
-        out[k].n_nan = (int64_t)res[k][6];
+        fill_result(out[k], grids[k], n_events[k], res[k].data());
         any_nan |= out[k].n_nan > 0;
-        v->iteration += 1;
+        grids[k]->iteration += 1;
     }
     if (any_nan) return fail(MF_ENAN, "some points had non-finite weights (counted as zero)");
+    return MF_OK;
+}
+
+extern "C" mf_status mf_vegas_partial_size(const mf_vegas *v, int32_t *K) {
+    if (!v || !K) return fail(MF_EINVAL, "NULL argument");
+    *K = partial_size(v);
+    return MF_OK;
+}
+
+extern "C" mf_status mf_vegas_shard_accumulate(mf_vegas *v, mf_process *p, int64_t n_total, int64_t chunk_begin,
+                                               int64_t chunk_end, int32_t subprocess, uint64_t seed,
+                                               mf_precision prec, double *nodes, int32_t *n_nodes, void *stream) {
+    if (!v || !p || !nodes || !n_nodes) return fail(MF_EINVAL, "NULL argument");
+    if (prec != MF_FP64 && prec != MF_MIXED) return fail(MF_EINVAL, "bad precision");
+    if (v->ndim != p->ndim) return fail(MF_EINVAL, "grid and process dimensions differ");
+    if (n_total < 2) return fail(MF_EINVAL, "need at least two events per iteration");
+    const int64_t nchunks = (n_total + kChunk - 1) / kChunk;
+    if (nchunks > ((int64_t)1 << kTreeMaxLevel)) return fail(MF_EINVAL, "too many events per iteration");
+    if (chunk_begin < 0 || chunk_end < chunk_begin || chunk_end > nchunks) return fail(MF_EINVAL, "bad chunk range");
+    if (subprocess < 0) return fail(MF_EINVAL, "bad subprocess index");
+    if (v->iteration >= v->max_iter) return fail(MF_EUNSUPPORTED, "too many iterations");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t e0 = chunk_begin * kChunk;
+    const int64_t e1 = std::min(chunk_end * kChunk, n_total);
+    const int64_t n = e1 > e0 ? e1 - e0 : 0;
+    mf_status st = run_points(p, v, prec, n, e0, subprocess, seed, s);
+    if (st != MF_OK) return st;
+    std::vector<int64_t> ids;
+    tree_frontier(chunk_begin, chunk_end, nchunks, ids);
+    const int nn = (int)ids.size() / 2;
+    if (nn > MF_MAX_TREE_NODES) return fail(MF_EUNSUPPORTED, "too many tree nodes");
+    st = tree_nodes(v, (n + kChunk - 1) / kChunk, chunk_begin, nchunks, ids, s);
+    if (st != MF_OK) return st;
+    const int K = partial_size(v);
+    std::vector<double> vals((size_t)nn * K);
+    if (nn) MF_CUDA(cudaMemcpyAsync(vals.data(), v->d_tree_out, sizeof(double) * vals.size(), cudaMemcpyDeviceToHost, s));
+    MF_CUDA(cudaStreamSynchronize(s));
+    if (n > 0) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p->ev_start, p->ev_stop) == cudaSuccess) p->last_kernel_ms = ms;
+    }
+    for (int j = 0; j < nn; ++j) {
+        double *r = nodes + (size_t)j * (2 + K);
+        r[0] = (double)ids[2 * j];
+        r[1] = (double)ids[2 * j + 1];
+        std::copy(vals.begin() + (size_t)j * K, vals.begin() + (size_t)(j + 1) * K, r + 2);
+    }
+    *n_nodes = nn;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_vegas_shard_finish(mf_vegas *v, int64_t n_total, const double *nodes, int32_t n_nodes,
+                                           int32_t refine, mf_iter_result *out, void *stream) {
+    if (!v || !out || (n_nodes > 0 && !nodes) || n_nodes < 0) return fail(MF_EINVAL, "bad arguments");
+    if (n_total < 2) return fail(MF_EINVAL, "need at least two events per iteration");
+    if (v->iteration >= v->max_iter) return fail(MF_EUNSUPPORTED, "too many iterations");
+    const int64_t nchunks = (n_total + kChunk - 1) / kChunk;
+    if (nchunks > ((int64_t)1 << kTreeMaxLevel)) return fail(MF_EINVAL, "too many events per iteration");
+    const int K = partial_size(v);
+    std::vector<double> tot(K);
+    mf_status st = tree_reduce(nodes, n_nodes, K, nchunks, tree_levels(nchunks), 0, tot.data());
+    if (st != MF_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    MF_CUDA(cudaMemcpyAsync(v->d_tot, tot.data(), sizeof(double) * K, cudaMemcpyHostToDevice, s));
+    st = finish(v, v->d_tot, n_total, refine, s);
+    if (st != MF_OK) return st;
+    double r[8];
+    MF_CUDA(cudaMemcpyAsync(r, v->d_result, sizeof(double) * 7, cudaMemcpyDeviceToHost, s));
+    MF_CUDA(cudaStreamSynchronize(s));
+    fill_result(*out, v, n_total, r);
+    v->iteration += 1;
+    if (out->n_nan > 0) return fail(MF_ENAN, "some points had non-finite weights (counted as zero)");
+    return MF_OK;
+}
+
+extern "C" mf_status mf_tree_frontier(int64_t chunk_begin, int64_t chunk_end, int64_t nchunks, int64_t *ids,
+                                      int32_t capacity, int32_t *n) {
+    if (!n || (capacity > 0 && !ids)) return fail(MF_EINVAL, "NULL argument");
+    if (nchunks < 1 || nchunks > ((int64_t)1 << kTreeMaxLevel)) return fail(MF_EINVAL, "chunk count out of range");
+    if (chunk_begin < 0 || chunk_end < chunk_begin || chunk_end > nchunks) return fail(MF_EINVAL, "bad chunk range");
+    std::vector<int64_t> v;
+    tree_frontier(chunk_begin, chunk_end, nchunks, v);
+    *n = (int32_t)(v.size() / 2);
+    if ((int64_t)v.size() > 2 * (int64_t)capacity) return fail(MF_EINVAL, "capacity too small");
+    std::copy(v.begin(), v.end(), ids);
+    return MF_OK;
+}
+
+extern "C" mf_status mf_tree_reduce(const double *nodes, int32_t n_nodes, int32_t K, int64_t nchunks, int32_t level,
+                                    int64_t index, double *out) {
+    if (!out || (n_nodes > 0 && !nodes) || n_nodes < 0 || K < 1) return fail(MF_EINVAL, "bad arguments");
+    if (nchunks < 1 || nchunks > ((int64_t)1 << kTreeMaxLevel)) return fail(MF_EINVAL, "chunk count out of range");
+    if (level < 0 || level > kTreeMaxLevel || index < 0 || (index << level) >= nchunks)
+        return fail(MF_EINVAL, "target node does not exist");
+    return tree_reduce(nodes, n_nodes, K, nchunks, level, index, out);
+}
+
+// ----------------------------------------------------------------------------
+// Checkpoint: a flat little-endian record of the grid state.
+// ----------------------------------------------------------------------------
+namespace {
+constexpr char kMagic[8] = {'M', 'F', 'V', 'E', 'G', 'A', 'S', '1'};
+struct CkptHeader {
+    char magic[8];
+    int32_t ndim, nbins, iteration, pad;
+    double alpha;
+};
+size_t ckpt_size(const mf_vegas *v) {
+    const size_t g = (size_t)v->ndim * (v->nbins + 1), h = (size_t)v->ndim * v->nbins;
+    return sizeof(CkptHeader) + sizeof(double) * (g + h) + sizeof(int64_t) * h + sizeof(double) * 2 * v->iteration;
+}
+}  // namespace
+
+extern "C" mf_status mf_vegas_save(const mf_vegas *v, void *buf, size_t *len) {
+    if (!v || !len) return fail(MF_EINVAL, "NULL argument");
+    const size_t need = ckpt_size(v);
+    if (!buf) {
+        *len = need;
+        return MF_OK;
+    }
+    if (*len < need) {
+        *len = need;
+        return fail(MF_EINVAL, "buffer too small");
+    }
+    char *b = (char *)buf;
+    CkptHeader h{};
+    std::memcpy(h.magic, kMagic, 8);
+    h.ndim = v->ndim;
+    h.nbins = v->nbins;
+    h.iteration = v->iteration;
+    h.alpha = v->alpha;
+    std::memcpy(b, &h, sizeof h);
+    b += sizeof h;
+    const size_t g = (size_t)v->ndim * (v->nbins + 1), hs = (size_t)v->ndim * v->nbins;
+    MF_CUDA(cudaMemcpy(b, v->d_grid, sizeof(double) * g, cudaMemcpyDeviceToHost));
+    b += sizeof(double) * g;
+    MF_CUDA(cudaMemcpy(b, v->d_hist, sizeof(double) * hs, cudaMemcpyDeviceToHost));
+    b += sizeof(double) * hs;
+    MF_CUDA(cudaMemcpy(b, v->d_count, sizeof(int64_t) * hs, cudaMemcpyDeviceToHost));
+    b += sizeof(int64_t) * hs;
+    if (v->iteration > 0)
+        MF_CUDA(cudaMemcpy(b, v->d_hist_iter, sizeof(double) * 2 * v->iteration, cudaMemcpyDeviceToHost));
+    *len = need;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_vegas_load(mf_vegas *v, const void *buf, size_t len) {
+    if (!v || !buf) return fail(MF_EINVAL, "NULL argument");
+    CkptHeader h;
+    if (len < sizeof h) return fail(MF_EINVAL, "checkpoint too short");
+    std::memcpy(&h, buf, sizeof h);
+    if (std::memcmp(h.magic, kMagic, 8) != 0) return fail(MF_EINVAL, "not a Vegas checkpoint");
+    if (h.ndim != v->ndim || h.nbins != v->nbins) return fail(MF_EINVAL, "checkpoint shape differs from the grid");
+    if (h.iteration < 0 || h.iteration > v->max_iter) return fail(MF_EINVAL, "bad iteration count");
+    if (!(h.alpha >= 0.0)) return fail(MF_EINVAL, "bad alpha");
+    mf_vegas tmp;
+    tmp.ndim = h.ndim;
+    tmp.nbins = h.nbins;
+    tmp.iteration = h.iteration;
+    if (len != ckpt_size(&tmp)) return fail(MF_EINVAL, "checkpoint size does not match its header");
+    const char *b = (const char *)buf + sizeof h;
+    const size_t g = (size_t)v->ndim * (v->nbins + 1), hs = (size_t)v->ndim * v->nbins;
+    std::vector<double> edges(g);
+    std::memcpy(edges.data(), b, sizeof(double) * g);
+    mf_status st = check_edges(v, edges.data());
+    if (st != MF_OK) return st;
+    MF_CUDA(cudaMemcpy(v->d_grid, b, sizeof(double) * g, cudaMemcpyHostToDevice));
+    b += sizeof(double) * g;
+    MF_CUDA(cudaMemcpy(v->d_hist, b, sizeof(double) * hs, cudaMemcpyHostToDevice));
+    b += sizeof(double) * hs;
+    MF_CUDA(cudaMemcpy(v->d_count, b, sizeof(int64_t) * hs, cudaMemcpyHostToDevice));
+    b += sizeof(int64_t) * hs;
+    if (h.iteration > 0) MF_CUDA(cudaMemcpy(v->d_hist_iter, b, sizeof(double) * 2 * h.iteration, cudaMemcpyHostToDevice));
+    v->iteration = h.iteration;
+    v->alpha = h.alpha;
     return MF_OK;
 }

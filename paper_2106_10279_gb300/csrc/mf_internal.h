@@ -91,8 +91,11 @@ struct mf_vegas {
     double *d_hist_iter = nullptr; // [max_iter][2]: (I_k, sigma_k)
     int max_iter = 0;
     double *d_result = nullptr;    // small result block
-    double *d_slots = nullptr;     // chunk partial sums
+    double *d_slots = nullptr;     // chunk partial sums [K][chunks] + K
     int64_t slots_cap = 0;
+    int64_t *d_tree_ids = nullptr; // [MF_MAX_TREE_NODES][2] (level, index)
+    double *d_tree_out = nullptr;  // [MF_MAX_TREE_NODES][K] node values
+    double *d_tot = nullptr;       // [K] combined totals of a sharded iteration
 };
 
 namespace mfi {

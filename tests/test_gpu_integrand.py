@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from _tolerance import fp64_tolerance, relerr
 
 pytestmark = pytest.mark.gpu
 
@@ -52,30 +53,6 @@ def oracle_integrand(oracle_processes):
             cache[name] = Integrand(W.WORKLOADS[name], process=oracle_processes(name))
         return cache[name]
     return get
-
-
-def relerr(got, ref):
-    got = np.asarray(got)
-    ref = np.asarray(ref)
-    both0 = (got == 0) & (ref == 0)
-    out = np.full(got.shape, np.inf)
-    nz = ref != 0
-    out[nz] = np.abs(got[nz] - ref[nz]) / np.abs(ref[nz])
-    out[both0] = 0.0
-    return out
-
-
-EPS = np.finfo(np.float64).eps
-
-
-def fp64_tolerance(oracle, x):
-    """1e-12 plus 64 eps x (the oracle's condition number of the point);
-    where it is infinite (a density or the phase space vanishing) only the
-    zero pattern is compared."""
-    f, parts = oracle(x, return_parts=True)
-    with np.errstate(invalid="ignore"):
-        tol = 1e-12 + 64 * EPS * parts["condition"]
-    return f, np.where(np.isnan(tol), np.inf, tol)
 
 
 def _eval(torch, proc, x, prec):
