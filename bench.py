@@ -167,10 +167,23 @@ def run_native(args):
     info = proc.info
     stream = torch.cuda.current_stream()
     vg = api.Vegas(wl.ndim, wl.n_bins, wl.alpha_vegas)
-    seed = 1000 + rank
+    seed = 1000
+    K = api.mf_vegas_partial_size(vg.handle)
 
     def step(prec, n, refine=True):
-        return api.mf_vegas_iterate([vg.handle], [proc.handle], [n], seed, prec, refine, stream)[0]
+        """One Vegas iteration of n points per GPU.  On one GPU a single call;
+        on N GPUs each rank evaluates its whole chunks of the N n points, the
+        ranks exchange their partial-sum tree nodes (one all-gather) and every
+        rank finishes the iteration to the same bits."""
+        if dist is None:
+            return api.mf_vegas_iterate([vg.handle], [proc.handle], [n], seed, prec, refine, stream)[0]
+        n_total = world * n
+        c0, c1 = api.shard_chunks(n_total, rank, world)
+        mine = vg.iterate_shard(proc, n_total, c0, c1, seed, 0, prec, stream)
+        buf = torch.from_numpy(api.pack_nodes(mine, K)).cuda()
+        parts = [torch.empty_like(buf) for _ in range(world)]
+        dist.all_gather(parts, buf)
+        return vg.finish_shards(n_total, api.unpack_nodes(torch.stack(parts).cpu().numpy(), K), refine, stream)
 
     # warm-up (also JIT-compiles the mixed kernel)
     for _ in range(max(args.warmup, 3)):
@@ -184,6 +197,7 @@ def run_native(args):
 
     clocks = Clocks(local)
     kernel_ms, results = [], []
+    start_state = vg.save()          # the e2e leg below replays these same iterations
     barrier()
     clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -225,20 +239,27 @@ def run_native(args):
     nz = f64 != 0
     rel = np.abs(fmx[nz] - f64[nz]) / np.abs(f64[nz])
 
-    # end to end through the public API with host buffers: upload the grid
-    # from pinned host memory, run the iteration, read results and grid back
+    # end to end through the public API with host buffers, replaying the
+    # timed iterations from the same grid state: each step uploads the grid
+    # from pinned host memory, runs the iteration and reads the result and
+    # the refined grid back
+    vg.load(start_state)
     grid_host = torch.from_numpy(vg.grid).pin_memory()
     h2d = grid_host.numel() * 8
     d2h = 7 * 8 + grid_host.numel() * 8
-    t_e2e = []
-    for _ in range(2):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
         vg.grid = grid_host.numpy()
         r = step("mixed", n_events)
-        g_back = vg.grid
-        t_e2e.append(time.perf_counter() - t0)
-    e2e_value = world * n_events / min(t_e2e)
+        grid_host.copy_(torch.from_numpy(vg.grid))
+    barrier()
+    t_e2e = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e_value = world * n_events * args.steps / t_e2e
 
     # roofline of the dominant kernel: algorithmic FLOPs / its device time
     kms = statistics.median(kernel_ms)
@@ -251,15 +272,17 @@ def run_native(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        sample = 200
+        sample = 2000 if wl.name == "gg_ttxgg" else 20000
         rate, dt = cpu_baseline_oracle(wl, sample)
         cpu = {"value": rate, "unit": "events/s", "cores": 1, "kind": "oracle",
                "sample": f"{sample} points of one {wl.name} Vegas iteration (Philox, map, integrand, "
                          f"accumulate), {dt:.1f} s"}
-    launches_per_step = 5          # integrand, accumulate, reduce, finalize, refine
+    launches_per_step = 5          # integrand, accumulate, tree reduction, finalize, refine
     line = {
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "parallelism": "one Vegas iteration of N x events_per_step_per_gpu points split in whole 4096-point "
+                       "chunks; one all-gather of partial-sum tree nodes per iteration" if world > 1 else "1 GPU",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": f"{wl.name}: gg->tt~gg at 13 TeV, {n_events:.0e} events per Vegas iteration "
                                f"per GPU, {wl.ndim} dims, 50 bins, cuts pT(g)>20 GeV and dR(g,g)>0.4, synthetic "

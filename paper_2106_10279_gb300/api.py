@@ -267,6 +267,25 @@ def shard_chunks(n_total: int, rank: int, world: int):
     return nchunks * rank // world, nchunks * (rank + 1) // world
 
 
+def pack_nodes(nodes, K: int):
+    """Fixed-size float64 record [1 + MF_MAX_TREE_NODES (2 + K)] of one rank's
+    tree nodes (count first), for an all-gather of equal-sized buffers."""
+    nodes = np.asarray(nodes, dtype=np.float64).reshape(-1, 2 + K)
+    if nodes.shape[0] > L.MF_MAX_TREE_NODES:
+        raise ValueError("too many tree nodes")
+    buf = np.zeros(1 + L.MF_MAX_TREE_NODES * (2 + K))
+    buf[0] = nodes.shape[0]
+    buf[1:1 + nodes.size] = nodes.ravel()
+    return buf
+
+
+def unpack_nodes(gathered, K: int):
+    """All ranks' nodes [n, 2 + K] from the gathered records [world, len]."""
+    g = np.asarray(gathered, dtype=np.float64)
+    rec = 2 + K
+    return np.concatenate([g[r, 1:1 + int(g[r, 0]) * rec].reshape(-1, rec) for r in range(g.shape[0])])
+
+
 def mf_vegas_save(h) -> bytes:
     n = C.c_size_t(0)
     L.check(L.lib().mf_vegas_save(h, None, C.byref(n)), "mf_vegas_save")

@@ -7,8 +7,9 @@ bit-identical to the single-device one (host only, no GPU).
   the per-rank frontier values reproduces the single-range root bit for bit;
 * malformed node sets (missing, duplicate, overlapping, out of range) are
   rejected with MF_EINVAL;
-* two gloo ranks exchange their nodes with all_gather_object and both rebuild
-  the same root as one rank alone.
+* two gloo ranks exchange their nodes as the data-parallel benchmark does
+  (fixed-size records, one all-gather) and both rebuild the same root as one
+  rank alone.
 """
 import socket
 
@@ -153,12 +154,19 @@ def _gloo_rank(rank, world, port, n, q):
         nchunks = n
         c0, c1 = nchunks * rank // world, nchunks * (rank + 1) // world
         mine = _rank_nodes(api, leaves, c0, c1)
-        gathered = [None] * world
-        dist.all_gather_object(gathered, mine)
-        allnodes = np.concatenate(gathered)
+        # the exchange of the data-parallel benchmark: fixed-size records,
+        # one all-gather
+        import torch
+        K = leaves.shape[1]
+        buf = torch.from_numpy(api.pack_nodes(mine, K))
+        parts = [torch.empty_like(buf) for _ in range(world)]
+        dist.all_gather(parts, buf)
+        allnodes = api.unpack_nodes(torch.stack(parts).numpy(), K)
         got = api.mf_tree_reduce(allnodes, n, api.tree_levels(n), 0)
         ref = api.mf_tree_reduce(_leaf_records(leaves, 0, n), n, api.tree_levels(n), 0)
         q.put((rank, bool(np.array_equal(got, ref)), got.tobytes()))
+    except Exception as e:                        # report instead of leaving the parent waiting
+        q.put((rank, False, repr(e).encode()))
     finally:
         dist.destroy_process_group()
 
@@ -172,9 +180,9 @@ def test_two_gloo_ranks_rebuild_the_same_root(api):
     procs = [ctx.Process(target=_gloo_rank, args=(r, 2, port, n, q)) for r in range(2)]
     for p in procs:
         p.start()
-    res = [q.get(timeout=300) for _ in procs]
+    res = [q.get(timeout=240) for _ in procs]
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    assert all(ok for _, ok, _ in res)
+    assert all(ok for _, ok, _ in res), res
     assert res[0][2] == res[1][2]
