@@ -116,6 +116,7 @@ typedef struct {
 #define MF_MAX_ITER 1024        /* Vegas iterations per grid */
 #define MF_MAX_TREE_NODES 128  /* tree nodes one shard returns */
 #define MF_CHUNK 4096          /* points per accumulation chunk */
+#define MF_STATIC_MAX_EVENTS 262144  /* points per mf_vegas_iterate_static call */
 
 typedef struct {
     /* external legs; legs 0 and 1 are the incoming partons along +z and -z */
@@ -308,6 +309,34 @@ mf_status mf_tree_frontier(int64_t chunk_begin, int64_t chunk_end, int64_t nchun
                            int32_t capacity, int32_t *n);
 mf_status mf_tree_reduce(const double *nodes, int32_t n_nodes, int32_t K, int64_t nchunks, int32_t level,
                          int64_t index, double *out);
+
+/* ---- mf_vegas_iterate_static: one Vegas iteration of one subprocess (as
+ * mf_vegas_iterate with nproc = 1 and subprocess index 0: same points, same
+ * results) that allocates no memory.  The paper has no counterpart: this
+ * entry point exists for callers that must not have a library allocate
+ * device memory while they run (applications whose device memory is all
+ * handed out by their own pool, loops that cannot take the device-wide
+ * synchronisation of cudaMalloc / cudaFree).
+ *
+ * Scratch: one array of 8,673,328 bytes compiled into the library
+ * (file-scope device memory, one copy per device), enough for
+ * n_events <= MF_STATIC_MAX_EVENTS points of up to MF_MAX_DIM dimensions and
+ * 64 bins; larger n_events are rejected with MF_EINVAL.  Nothing in it needs
+ * to start at zero: every call writes each element before reading it.
+ *
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, which may load the library's device code); make that
+ * first call before any stream capture.  The process kernel of the requested
+ * precision must already be compiled, by an earlier mf_integrand or
+ * mf_vegas_iterate call with that precision (compiling allocates): otherwise
+ * MF_EINVAL.
+ *
+ * Calls that overlap in time on the same device share the one array and race:
+ * serialise them (one stream, or synchronise between calls, across all
+ * threads).  Synchronous: returns after *out (host) is filled.  MF_ENAN as
+ * mf_vegas_iterate. */
+mf_status mf_vegas_iterate_static(mf_vegas *v, mf_process *p, int64_t n_events, uint64_t seed,
+                                  mf_precision prec, int32_t refine, mf_iter_result *out, void *stream);
 
 /* ---- Checkpoint of a grid: edges, last histogram and counts, and the
  * (I_k, sigma_k) of the iterations so far, so that a run resumes with the same

@@ -83,6 +83,8 @@ SIGNATURES = {
                                       C.c_void_p]),
     "mf_tree_frontier": (c_i32, [c_i64, c_i64, c_i64, P(c_i64), c_i32, P(c_i32)]),
     "mf_tree_reduce": (c_i32, [P(C.c_double), c_i32, c_i32, c_i64, c_i32, c_i64, P(C.c_double)]),
+    "mf_vegas_iterate_static": (c_i32, [C.c_void_p, C.c_void_p, c_i64, C.c_uint64, c_i32, c_i32,
+                                        P(mf_iter_result), C.c_void_p]),
     "mf_vegas_save": (c_i32, [C.c_void_p, C.c_void_p, P(C.c_size_t)]),
     "mf_vegas_load": (c_i32, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "mf_generate_kernel_source": (c_i32, [P(mf_process_desc), c_i32, c_i32, C.c_char_p, P(C.c_size_t)]),
@@ -91,6 +93,7 @@ SIGNATURES = {
 
 MF_CHUNK = 4096
 MF_MAX_TREE_NODES = 128
+MF_STATIC_MAX_EVENTS = 262144
 
 _lib = None
 

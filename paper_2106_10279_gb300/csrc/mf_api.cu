@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1271,5 +1272,119 @@ extern "C" mf_status mf_vegas_load(mf_vegas *v, const void *buf, size_t len) {
     if (h.iteration > 0) MF_CUDA(cudaMemcpy(v->d_hist_iter, b, sizeof(double) * 2 * h.iteration, cudaMemcpyHostToDevice));
     v->iteration = h.iteration;
     v->alpha = h.alpha;
+    return MF_OK;
+}
+
+// ----------------------------------------------------------------------------
+// One Vegas iteration that allocates nothing.
+//
+// Some callers cannot let a library allocate device memory while they run:
+// an application whose device memory is carved out by its own pool up front
+// (a cudaMalloc would fail or fight that pool for memory), and loops that must
+// not stall on the implicit device-wide synchronisation that cudaMalloc and
+// cudaFree bring.  mf_vegas_iterate_static serves them: the scratch that
+// mf_vegas_iterate keeps per process and grid (weights, bin indices, chunk
+// partial sums, totals) lives here in one fixed array compiled into the
+// library, and the call uses only memory that already exists.
+// ----------------------------------------------------------------------------
+namespace {
+constexpr int64_t kStaticChunks = MF_STATIC_MAX_EVENTS / kChunk;
+constexpr int kStaticMaxK = 4 + 2 * MF_MAX_DIM * 64;          // largest partial-sum vector
+// layout: w [MAX_EVENTS] doubles | slots [K][chunks] + totals [K] doubles |
+//         root node id [2] int64 | bins [MF_MAX_DIM][MAX_EVENTS] bytes
+constexpr size_t kStaticW = 0;
+constexpr size_t kStaticSlots = kStaticW + sizeof(double) * MF_STATIC_MAX_EVENTS;
+constexpr size_t kStaticTot = kStaticSlots + sizeof(double) * (size_t)kStaticMaxK * kStaticChunks;
+constexpr size_t kStaticIds = kStaticTot + sizeof(double) * kStaticMaxK;
+constexpr size_t kStaticBins = kStaticIds + 2 * sizeof(int64_t);
+constexpr size_t kStaticBytes = kStaticBins + (size_t)MF_MAX_DIM * MF_STATIC_MAX_EVENTS;   // 8,673,328 bytes
+static_assert(MF_STATIC_MAX_EVENTS % kChunk == 0, "whole chunks");
+
+__device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mutex;
+void *g_static_base[kStaticMaxDevices];
+
+// Address of the array on the current device, looked up once per device.
+mf_status static_scratch(void **base) {
+    int dev = 0;
+    MF_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kStaticMaxDevices) return fail(MF_EUNSUPPORTED, "device index beyond the static table");
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_base[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(MF_ECUDA, std::string("cudaGetSymbolAddress of the static scratch: ") + cudaGetErrorString(e));
+        g_static_base[dev] = p;
+    }
+    *base = g_static_base[dev];
+    return MF_OK;
+}
+
+__global__ void static_root_kernel(int64_t *ids, int level) {
+    ids[0] = level;
+    ids[1] = 0;
+}
+}  // namespace
+
+extern "C" mf_status mf_vegas_iterate_static(mf_vegas *v, mf_process *p, int64_t n_events, uint64_t seed,
+                                             mf_precision prec, int32_t refine, mf_iter_result *out, void *stream) {
+    if (!v || !p || !out) return fail(MF_EINVAL, "NULL argument");
+    if (prec != MF_FP64 && prec != MF_MIXED) return fail(MF_EINVAL, "bad precision");
+    if (v->ndim != p->ndim) return fail(MF_EINVAL, "grid and process dimensions differ");
+    if (n_events < 2) return fail(MF_EINVAL, "need at least two events per iteration");
+    if (n_events > MF_STATIC_MAX_EVENTS)
+        return fail(MF_EINVAL, "n_events exceeds MF_STATIC_MAX_EVENTS (" + std::to_string(MF_STATIC_MAX_EVENTS) +
+                                   " points), the capacity of the static scratch; use mf_vegas_iterate");
+    if (v->iteration >= v->max_iter) return fail(MF_EUNSUPPORTED, "too many iterations");
+    if (!p->kern[prec].fn)
+        return fail(MF_EINVAL, "the process kernel of this precision is not compiled yet (compiling allocates): "
+                               "call mf_integrand or mf_vegas_iterate with it once first");
+    void *base = nullptr;
+    mf_status st = static_scratch(&base);
+    if (st != MF_OK) return st;
+    unsigned char *b = (unsigned char *)base;
+    double *w = (double *)(b + kStaticW);
+    double *slots = (double *)(b + kStaticSlots);
+    double *tot = (double *)(b + kStaticTot);
+    int64_t *ids = (int64_t *)(b + kStaticIds);
+    uint8_t *bins = (uint8_t *)(b + kStaticBins);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = n_events;
+    const int64_t nchunks = (n + kChunk - 1) / kChunk;
+    const int K = partial_size(v);
+
+    mf_kparams kp;
+    fill_common(*p, kp);
+    set_hel(kp, p->hel, p->n_legs);
+    kp.mode = 1;
+    kp.n = n;
+    kp.ev0 = 0;
+    kp.grid = v->d_grid;
+    kp.nb = v->nbins;
+    kp.w_out = w;
+    kp.bins_out = bins;
+    kp.seed = seed;
+    kp.iteration = (uint64_t)v->iteration;
+    kp.subprocess = 0;
+    st = launch(p, prec, kp, s);
+    if (st != MF_OK) return st;
+    const size_t acc_smem = sizeof(double) * 2 * kChunk + kChunk;
+    MF_CUDA(cudaFuncSetAttribute(vegas_accumulate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc_smem));
+    vegas_accumulate_kernel<<<(unsigned)nchunks, kAccThreads, acc_smem, s>>>(w, bins, n, v->ndim, v->nbins, slots,
+                                                                              nchunks);
+    static_root_kernel<<<1, 1, 0, s>>>(ids, tree_levels(nchunks));
+    vegas_tree_kernel<<<dim3((unsigned)K, 1), kTreeThreads, 0, s>>>(slots, nchunks, 0, nchunks, K, ids, tot);
+    MF_CUDA(cudaGetLastError());
+    st = finish(v, tot, n, refine, s);
+    if (st != MF_OK) return st;
+    double r[8];
+    MF_CUDA(cudaMemcpyAsync(r, v->d_result, sizeof(double) * 7, cudaMemcpyDeviceToHost, s));
+    MF_CUDA(cudaStreamSynchronize(s));
+    fill_result(*out, v, n, r);
+    v->iteration += 1;
+    if (out->n_nan > 0) return fail(MF_ENAN, "some points had non-finite weights (counted as zero)");
     return MF_OK;
 }
