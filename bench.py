@@ -41,6 +41,7 @@ def _args():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--fp64-events", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the mixed-batch measurement")
     return ap.parse_args()
 
 
@@ -261,6 +262,40 @@ def run_native(args):
         t_e2e = float(t.item())
     e2e_value = world * n_events * args.steps / t_e2e
 
+    # the mixed batch of five subprocesses (gg->tt~, uu~->tt~, gg->tt~g,
+    # uu~->tt~g, gg->tt~gg; 4e7 points per iteration in all), each with its own
+    # grid: one persistent launch per iteration against one launch per
+    # subprocess, same points and results
+    batch = None
+    if not args.no_batch:
+        names = [name for name, _ in W.MIXED_BATCH]
+        nb_ev = [nev for _, nev in W.MIXED_BATCH]
+        procs = [proc if name == wl.name else api.Process.from_workload(W.WORKLOADS[name]) for name in names]
+        bt = api.Batch(procs, "mixed")
+
+        def timed(run, reps=3):
+            for _ in range(2):
+                run()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                out = run()
+            b.record(stream)
+            torch.cuda.synchronize()
+            return sum(nb_ev) * reps / (a.elapsed_time(b) / 1e3), out
+        gb = [api.Vegas(p.ndim) for p in procs]
+        rate_b, res_b = timed(lambda: bt.iterate(gb, nb_ev, 4242, True, stream))
+        gs = [api.Vegas(p.ndim) for p in procs]
+        rate_s, res_s = timed(lambda: api.mf_vegas_iterate([g.handle for g in gs], [p.handle for p in procs],
+                                                           nb_ev, 4242, "mixed", True, stream))
+        batch = {"workload": "mixed batch " + ", ".join(f"{n} {e:.0e}" for n, e in W.MIXED_BATCH),
+                 "value": rate_b, "unit": "events/s", "separate_launches": rate_s,
+                 "sigma_total_pb": sum(r["sigma"] for r in res_b),
+                 "same_sigma_as_separate": all(a["sigma"] == b["sigma"] for a, b in zip(res_b, res_s)),
+                 "kernel_ms": bt.info()["last_kernel_ms"]}
+
     # roofline of the dominant kernel: algorithmic FLOPs / its device time
     kms = statistics.median(kernel_ms)
     passing = statistics.median([r["n_nonzero"] for r in results])
@@ -292,6 +327,7 @@ def run_native(args):
                    "l2": "random numbers generated in-kernel; per-step outputs (w, bins) "
                          f"{n_events * (8 + wl.ndim) / 1e6:.0f} MB > 129 MB L2"},
         "fp64": {"value": fp64_rate, "unit": "events/s", "events": n64},
+        "batch": batch,
         "accuracy": {"median_rel_mixed_vs_fp64": float(np.median(rel)), "max_rel_mixed_vs_fp64": float(rel.max()),
                      "points": int(nz.sum())},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",

@@ -46,8 +46,11 @@ typedef enum {
 /* Arithmetic of the matrix element (Sec. 2.3).  MF_FP64: everything in double
  * precision.  MF_MIXED: spinors, currents, amplitudes and the colour sum in
  * single precision; phase space, invariants and propagator denominators, PDFs,
- * weights and all accumulators in double precision. */
-typedef enum { MF_FP64 = 0, MF_MIXED = 1 } mf_precision;
+ * weights and all accumulators in double precision.  MF_MIXED_TC: MF_MIXED
+ * with the colour sum on the tensor cores (tcgen05, split TF32; see
+ * mf_colour_sum), 128 threads per block.  (Value 2 is the gradient kernel in
+ * mf_generate_kernel_source.) */
+typedef enum { MF_FP64 = 0, MF_MIXED = 1, MF_MIXED_TC = 3 } mf_precision;
 
 /* ------------------------------------------------------------------------ */
 /* Process descriptor: the diagram program of Sec. 2.3 (the Matrix class the   */
@@ -159,6 +162,7 @@ typedef struct {
 
 typedef struct mf_process mf_process;   /* opaque, library-owned */
 typedef struct mf_vegas mf_vegas;       /* opaque, library-owned */
+typedef struct mf_batch mf_batch;       /* opaque, library-owned */
 
 /* mf_create_process: validate and deep-copy *desc, drop vanishing helicities,
  * generate CUDA source specialised to the diagram program and compile it for
@@ -310,6 +314,82 @@ mf_status mf_tree_frontier(int64_t chunk_begin, int64_t chunk_end, int64_t nchun
 mf_status mf_tree_reduce(const double *nodes, int32_t n_nodes, int32_t K, int64_t nchunks, int32_t level,
                          int64_t index, double *out);
 
+/* mf_process_tune: time the kernel of precision prec for every launch shape
+ * (128 or 256 threads per block; 8, 16 or 32 lanes per event, at most the
+ * padded helicity count) on n_sample (>= 1024) Vegas points of a uniform grid
+ * and keep the fastest for later calls (and for batches created afterwards).
+ * The helicity sum is a fixed pairwise tree whatever the shape, so the
+ * results are the same bits for every shape: only the speed changes.  Each
+ * shape is compiled once (cached on disk).  *block and *ht (may be NULL)
+ * receive the choice.  Synchronous on stream. */
+mf_status mf_process_tune(mf_process *p, mf_precision prec, int64_t n_sample, void *stream, int32_t *block,
+                          int32_t *ht);
+
+/* ---- Batched iterations (the subprocesses of a hadronic cross section
+ * summed in Sec. 2.1 evaluated together): mf_batch_create compiles the
+ * programs of nproc processes (1..8, each at most once, all on the current
+ * device) into one persistent kernel; blocks draw tiles of 128 points from one
+ * counter, the tiles of the costliest process first, so the subprocesses share
+ * the GPU without a tail per subprocess.  mf_batch_iterate then runs one Vegas
+ * iteration of every subprocess k with grid grids[k] and n_events[k] points:
+ * same points (subprocess index k), same estimator and same refinement as
+ * mf_vegas_iterate with the same arrays, in one kernel launch plus the
+ * per-subprocess accumulation.  Synchronous; out[k] (host [nproc]).
+ * mf_batch_get_info: the batch order (order[slot] = the caller's index,
+ * host [nproc]), the kernel's registers per thread and the device time of
+ * its last launch in ms; any pointer may be NULL.  The processes must outlive
+ * the batch. */
+mf_status mf_batch_create(mf_process *const *procs, int32_t nproc, mf_precision prec, mf_batch **out);
+mf_status mf_batch_destroy(mf_batch *b);
+mf_status mf_batch_iterate(mf_batch *b, mf_vegas *const *grids, const int64_t *n_events, uint64_t seed,
+                           int32_t refine, mf_iter_result *out, void *stream);
+mf_status mf_batch_get_info(const mf_batch *b, int32_t *order, int32_t *regs, double *last_kernel_ms);
+
+/* ---- Unweighted events and the Les Houches Event writer (Sec. 2.5).
+ *
+ * mf_lhe_open writes the header and <init> block of an LHE 3.0 text file
+ * and starts a writer thread; events handed to it are formatted and written
+ * while the caller's GPU work goes on.  mf_lhe_close drains the queue, ends
+ * the file, joins the thread and frees the writer (*n_written, may be NULL:
+ * the number of events written).  Colour tags are not assigned (0). */
+typedef struct mf_lhe_writer mf_lhe_writer;
+typedef struct {
+    int32_t n_legs;                /* particles per event, incoming first */
+    int32_t pdg[MF_MAX_LEGS];      /* PDG ids per leg */
+    double mass[MF_MAX_LEGS];      /* masses written per leg (GeV) */
+    int32_t beam_pdg[2];
+    double beam_energy[2];         /* GeV */
+    double xsec, xsec_error;       /* pb */
+    double w_max;                  /* maximum event weight (pb) */
+    int32_t process_id;
+    double scale;                  /* event scale (GeV) */
+    double alpha_qed, alpha_s;
+} mf_lhe_init;
+mf_status mf_lhe_open(const char *path, const mf_lhe_init *init, mf_lhe_writer **out);
+/* Queue n events given as host records (3 + 4 n_legs doubles each: weight,
+ * x1, x2, then per leg E, px, py, pz); the data are copied. */
+mf_status mf_lhe_write(mf_lhe_writer *w, const double *records, int64_t n);
+mf_status mf_lhe_close(mf_lhe_writer *w, int64_t *n_written);
+
+/* mf_vegas_unweight: one pass of n_events Vegas points through the grid as it
+ * stands (points of the grid's current iteration index, subprocess index
+ * `subprocess`, Philox key seed; the grid is neither refined nor advanced),
+ * then hit-or-miss unweighting: point i with weight w_i = f J_V is kept when
+ * |w_i| > u_i w_max, u_i the first unit number of Philox counter
+ * (i, iteration, subprocess, 15).  A kept point becomes an event of weight
+ * sign(w_i) max(|w_i|, w_max) / n_events (pb), so the events' weights add up
+ * to the integral estimate.  Records (host [capacity][3 + 4 n_legs], may be
+ * NULL): event weight, x1, x2, then per leg (E, px, py, pz) in the collider
+ * frame, in point order; at most capacity are written, *n_accepted receives
+ * the number kept.  With lhe != NULL the events also go to that writer.
+ * Synchronous. */
+mf_status mf_vegas_unweight(mf_vegas *v, mf_process *p, int64_t n_events, uint64_t seed, int32_t subprocess,
+                            mf_precision prec, double w_max, mf_lhe_writer *lhe, double *records, int64_t capacity,
+                            int64_t *n_accepted, void *stream);
+/* mf_process_max_weight: max |w| over the points of the process's last
+ * Vegas pass (mf_vegas_iterate, shard or unweighting pass).  Synchronous. */
+mf_status mf_process_max_weight(mf_process *p, double *w_max, void *stream);
+
 /* ---- mf_vegas_iterate_static: one Vegas iteration of one subprocess (as
  * mf_vegas_iterate with nproc = 1 and subprocess index 0: same points, same
  * results) that allocates no memory.  The paper has no counterpart: this
@@ -347,6 +427,15 @@ mf_status mf_vegas_iterate_static(mf_vegas *v, mf_process *p, int64_t n_events, 
 mf_status mf_vegas_save(const mf_vegas *v, void *buf, size_t *len);
 mf_status mf_vegas_load(mf_vegas *v, const void *buf, size_t len);
 
+/* mf_process_check: whether a kernel of this process flagged an error: a
+ * bounded wait expired (the tensor-core colour sum waits on the completion
+ * of its MMAs; that launch's results are unspecified): MF_ETIMEOUT; or the
+ * launch gave less dynamic shared memory than the kernel needs (nothing
+ * written): MF_ECUDA.  Reads and clears the flag (synchronises the device).
+ * The synchronous entry points (mf_create_process, mf_vegas_iterate, the
+ * shard and batch iterations) check it by themselves. */
+mf_status mf_process_check(mf_process *p);
+
 /* Device time, in ms, of the last fused integrand kernel that mf_vegas_iterate
  * launched for this process (CUDA events recorded on the launching stream
  * around that one launch; the accumulation and refinement kernels excluded).
@@ -369,6 +458,11 @@ mf_status mf_vegas_get_shape(const mf_vegas *v, int32_t *ndim, int32_t *nbins, i
  * failure.  buf may be NULL to query the size. */
 mf_status mf_generate_kernel_source(const mf_process_desc *desc, mf_precision prec, int32_t compile,
                                     char *buf, size_t *len);
+
+/* Diagnostic: the source of the batched kernel of nproc descriptors (in the
+ * given order), as mf_generate_kernel_source. */
+mf_status mf_generate_batch_source(const mf_process_desc *const *descs, int32_t nproc, mf_precision prec,
+                                   int32_t compile, char *buf, size_t *len);
 
 /* Thread-local description of the last error (empty string if none). */
 const char *mf_last_error(void);

@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libmadflow_gb.so")
 
 MF_OK, MF_EINVAL, MF_ENOMEM, MF_ECUDA, MF_ENAN, MF_ETIMEOUT, MF_EUNSUPPORTED, MF_EJIT = range(8)
-MF_FP64, MF_MIXED = 0, 1
+MF_FP64, MF_MIXED, MF_MIXED_TC = 0, 1, 3
 STATUS_NAMES = {0: "MF_OK", 1: "MF_EINVAL", 2: "MF_ENOMEM", 3: "MF_ECUDA", 4: "MF_ENAN",
                 5: "MF_ETIMEOUT", 6: "MF_EUNSUPPORTED", 7: "MF_EJIT"}
 
@@ -53,6 +53,13 @@ class mf_process_info(C.Structure):
                 ("flops_per_hel", C.c_double), ("flops_kinematics", C.c_double)]
 
 
+class mf_lhe_init(C.Structure):
+    _fields_ = [("n_legs", c_i32), ("pdg", c_i32 * 8), ("mass", C.c_double * 8), ("beam_pdg", c_i32 * 2),
+                ("beam_energy", C.c_double * 2), ("xsec", C.c_double), ("xsec_error", C.c_double),
+                ("w_max", C.c_double), ("process_id", c_i32), ("scale", C.c_double), ("alpha_qed", C.c_double),
+                ("alpha_s", C.c_double)]
+
+
 class mf_iter_result(C.Structure):
     _fields_ = [("iteration", c_i32), ("n_events", c_i64), ("n_nonzero", c_i64), ("n_nan", c_i64),
                 ("integral", C.c_double), ("error", C.c_double), ("sigma", C.c_double),
@@ -85,6 +92,20 @@ SIGNATURES = {
     "mf_tree_reduce": (c_i32, [P(C.c_double), c_i32, c_i32, c_i64, c_i32, c_i64, P(C.c_double)]),
     "mf_vegas_iterate_static": (c_i32, [C.c_void_p, C.c_void_p, c_i64, C.c_uint64, c_i32, c_i32,
                                         P(mf_iter_result), C.c_void_p]),
+    "mf_process_check": (c_i32, [C.c_void_p]),
+    "mf_process_tune": (c_i32, [C.c_void_p, c_i32, c_i64, C.c_void_p, P(c_i32), P(c_i32)]),
+    "mf_batch_create": (c_i32, [P(C.c_void_p), c_i32, c_i32, P(C.c_void_p)]),
+    "mf_batch_destroy": (c_i32, [C.c_void_p]),
+    "mf_batch_iterate": (c_i32, [C.c_void_p, P(C.c_void_p), P(c_i64), C.c_uint64, c_i32, P(mf_iter_result),
+                                 C.c_void_p]),
+    "mf_batch_get_info": (c_i32, [C.c_void_p, P(c_i32), P(c_i32), P(C.c_double)]),
+    "mf_generate_batch_source": (c_i32, [P(P(mf_process_desc)), c_i32, c_i32, c_i32, C.c_char_p, P(C.c_size_t)]),
+    "mf_lhe_open": (c_i32, [C.c_char_p, P(mf_lhe_init), P(C.c_void_p)]),
+    "mf_lhe_close": (c_i32, [C.c_void_p, P(c_i64)]),
+    "mf_lhe_write": (c_i32, [C.c_void_p, P(C.c_double), c_i64]),
+    "mf_vegas_unweight": (c_i32, [C.c_void_p, C.c_void_p, c_i64, C.c_uint64, c_i32, c_i32, C.c_double, C.c_void_p,
+                                  P(C.c_double), c_i64, P(c_i64), C.c_void_p]),
+    "mf_process_max_weight": (c_i32, [C.c_void_p, P(C.c_double), C.c_void_p]),
     "mf_vegas_save": (c_i32, [C.c_void_p, C.c_void_p, P(C.c_size_t)]),
     "mf_vegas_load": (c_i32, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "mf_generate_kernel_source": (c_i32, [P(mf_process_desc), c_i32, c_i32, C.c_char_p, P(C.c_size_t)]),

@@ -12,7 +12,8 @@ from . import _lib as L
 from .process import ProcessProgram, build_program
 
 MF_FP64, MF_MIXED = L.MF_FP64, L.MF_MIXED
-_PREC = {"fp64": L.MF_FP64, "mixed": L.MF_MIXED, L.MF_FP64: L.MF_FP64, L.MF_MIXED: L.MF_MIXED, "grad": 2}
+_PREC = {"fp64": L.MF_FP64, "mixed": L.MF_MIXED, "mixed_tc": L.MF_MIXED_TC, L.MF_FP64: L.MF_FP64,
+         L.MF_MIXED: L.MF_MIXED, L.MF_MIXED_TC: L.MF_MIXED_TC, "grad": 2}
 
 
 def _arr(ctype, values):
@@ -332,6 +333,18 @@ def mf_generate_kernel_source(desc: Descriptor, precision="fp64", compile: bool 
     return buf.value.decode()
 
 
+def mf_generate_batch_source(descs, precision="mixed", compile: bool = False) -> str:
+    k = len(descs)
+    arr = (C.POINTER(L.mf_process_desc) * k)(*[C.pointer(d.desc) for d in descs])
+    n = C.c_size_t(0)
+    L.check(L.lib().mf_generate_batch_source(arr, k, _PREC[precision], 0, None, C.byref(n)),
+            "mf_generate_batch_source")
+    buf = C.create_string_buffer(n.value)
+    L.check(L.lib().mf_generate_batch_source(arr, k, _PREC[precision], 1 if compile else 0, buf, C.byref(n)),
+            "mf_generate_batch_source")
+    return buf.value.decode()
+
+
 # ---------------------------------------------------------------- classes
 class Process:
     """A compiled process; ``integrand(x)`` evaluates f at points x [ndim, n]."""
@@ -359,6 +372,17 @@ class Process:
         f = torch.empty(n, dtype=torch.float64, device=x.device) if out is None else out
         mf_integrand(self.handle, x, n, f, precision, stream)
         return f
+
+    def check(self):
+        """Raise if a bounded wait of one of this process's kernels expired."""
+        L.check(L.lib().mf_process_check(self.handle), "mf_process_check")
+
+    def tune(self, precision="mixed", n_sample=200_000, stream=None):
+        """Pick the fastest launch shape (same results); returns (block, lanes per event)."""
+        b, h = C.c_int32(), C.c_int32()
+        L.check(L.lib().mf_process_tune(self.handle, _PREC[precision], n_sample, _stream_ptr(stream), C.byref(b),
+                                        C.byref(h)), "mf_process_tune")
+        return b.value, h.value
 
     def grad(self, x, with_dx=True, stream=None):
         """(f [n], df/dparam [2, n] (m_t, alpha_s), df/dx [ndim, n] or None)."""
@@ -427,6 +451,105 @@ class Vegas:
     def close(self):
         if self.handle:
             mf_vegas_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class LheWriter:
+    """An LHE 3.0 file written by a background thread (see mf_lhe_open)."""
+
+    def __init__(self, path, pdg, masses, beam_pdg=(2212, 2212), beam_energy=(6500.0, 6500.0), xsec=0.0,
+                 xsec_error=0.0, w_max=0.0, process_id=1, scale=173.0, alpha_qed=1 / 128, alpha_s=0.118):
+        init = L.mf_lhe_init()
+        init.n_legs = len(pdg)
+        for i, (p, m) in enumerate(zip(pdg, masses)):
+            init.pdg[i] = p
+            init.mass[i] = m
+        init.beam_pdg[:] = list(beam_pdg)
+        init.beam_energy[:] = list(beam_energy)
+        init.xsec, init.xsec_error, init.w_max = xsec, xsec_error, w_max
+        init.process_id, init.scale, init.alpha_qed, init.alpha_s = process_id, scale, alpha_qed, alpha_s
+        h = C.c_void_p()
+        L.check(L.lib().mf_lhe_open(str(path).encode(), C.byref(init), C.byref(h)), "mf_lhe_open")
+        self.handle = h
+        self.n_legs = len(pdg)
+
+    def write(self, records):
+        r = np.ascontiguousarray(records, dtype=np.float64).reshape(-1, 3 + 4 * self.n_legs)
+        L.check(L.lib().mf_lhe_write(self.handle, r.ctypes.data_as(C.POINTER(C.c_double)), r.shape[0]),
+                "mf_lhe_write")
+
+    def close(self) -> int:
+        n = C.c_int64(0)
+        if self.handle:
+            h, self.handle = self.handle, None
+            L.check(L.lib().mf_lhe_close(h, C.byref(n)), "mf_lhe_close")
+        return n.value
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def unweight(grid: "Vegas", proc: "Process", n_events: int, seed: int, w_max: float, precision="mixed",
+             subprocess=0, lhe: LheWriter = None, capacity=None, stream=None):
+    """Hit-or-miss unweighted events of one pass (see mf_vegas_unweight):
+    (number kept, records [min(kept, capacity), 3 + 4 n_legs])."""
+    nl = proc.info["n_legs"]
+    cap = n_events if capacity is None else capacity
+    rec = np.zeros((max(cap, 0), 3 + 4 * nl))
+    nacc = C.c_int64()
+    st = L.lib().mf_vegas_unweight(grid.handle, proc.handle, n_events, seed, subprocess, _PREC[precision], w_max,
+                                   lhe.handle if lhe else None, rec.ctypes.data_as(C.POINTER(C.c_double)), cap,
+                                   C.byref(nacc), _stream_ptr(stream))
+    L.check(st, "mf_vegas_unweight")
+    return nacc.value, rec[:min(nacc.value, cap)]
+
+
+def max_weight(proc: "Process", stream=None) -> float:
+    w = C.c_double()
+    L.check(L.lib().mf_process_max_weight(proc.handle, C.byref(w), _stream_ptr(stream)), "mf_process_max_weight")
+    return w.value
+
+
+class Batch:
+    """Several processes in one persistent kernel (see mf_batch_create)."""
+
+    def __init__(self, procs, precision="mixed"):
+        self.procs = list(procs)            # keeps the processes alive
+        k = len(self.procs)
+        arr = (C.c_void_p * k)(*[p.handle.value for p in self.procs])
+        h = C.c_void_p()
+        L.check(L.lib().mf_batch_create(arr, k, _PREC[precision], C.byref(h)), "mf_batch_create")
+        self.handle = h
+
+    def iterate(self, grids, n_events, seed: int, refine=True, stream=None):
+        k = len(self.procs)
+        G = (C.c_void_p * k)(*[g.handle.value for g in grids])
+        N = (C.c_int64 * k)(*n_events)
+        out = (L.mf_iter_result * k)()
+        st = L.lib().mf_batch_iterate(self.handle, G, N, seed, 1 if refine else 0, out, _stream_ptr(stream))
+        L.check(st, "mf_batch_iterate", allow=(L.MF_OK, L.MF_ENAN))
+        return [_result(r) for r in out]
+
+    def info(self):
+        k = len(self.procs)
+        order = (C.c_int32 * k)()
+        regs = C.c_int32()
+        ms = C.c_double()
+        L.check(L.lib().mf_batch_get_info(self.handle, order, C.byref(regs), C.byref(ms)), "mf_batch_get_info")
+        return {"order": list(order), "regs": regs.value, "last_kernel_ms": ms.value}
+
+    def close(self):
+        if self.handle:
+            L.lib().mf_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -18,8 +18,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmadflow_gb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 EMBED = ["mf_common.cuh", "mf_dual.cuh", "mf_kinematics.cuh", "mf_helas.cuh", "mf_kparams.h", "mf_kernel.cuh",
-         "mf_helas_adj.cuh", "mf_grad.cuh"]
-SOURCES = ["mf_api.cu", "mf_codegen.cpp", "mf_jit.cpp"]
+         "mf_helas_adj.cuh", "mf_grad.cuh", "mf_tc.cuh"]
+SOURCES = ["mf_api.cu", "mf_colour.cu", "mf_codegen.cpp", "mf_jit.cpp", "mf_lhe.cpp"]
 
 
 def _nvcc() -> str:
@@ -89,7 +89,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
             if res.returncode:
                 raise RuntimeError(f"nvcc failed for {cmd[-3]}")
     if force or _stale(LIB, objs):
-        cmd = [nvcc, *ARCH, "-shared", "-o", LIB, *objs, "-L", lib64, "-ldl", "-cudart", "shared",
+        cmd = [nvcc, *ARCH, "-shared", "-o", LIB, *objs, "-L", lib64, "-ldl", "-lpthread", "-cudart", "shared",
                "-Xlinker", f"-rpath={lib64}"]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if verbose or res.returncode:

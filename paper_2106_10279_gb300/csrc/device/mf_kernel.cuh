@@ -13,11 +13,19 @@
 //            in a fixed pairwise tree (independent of HT) across the HT lanes;
 //   phase C  one thread per event writes f (integrand) or w = f J_V and the
 //            bin indices (Vegas).
-#pragma once
+//
+// The process-independent part below is included once.  The process-dependent
+// part (EventKin, phase_a, tile_body, kernel_body) may be included several
+// times in one translation unit, once per process of a batched kernel: the
+// includer names the process namespace in MF_PROC and the namespace that
+// receives these definitions in MF_BODY (defaults: proc and mf).
+#ifndef MF_KERNEL_COMMON_DEFINED
+#define MF_KERNEL_COMMON_DEFINED
 #include "mf_common.cuh"
 #include "mf_kinematics.cuh"
 #include "mf_helas.cuh"
 #include "mf_kparams.h"
+#include "mf_tc.cuh"
 
 namespace mf {
 
@@ -45,6 +53,17 @@ struct PairSum {
     }
 };
 
+}  // namespace mf
+#endif  // MF_KERNEL_COMMON_DEFINED
+
+#ifndef MF_PROC
+#define MF_PROC proc
+#define MF_BODY mf
+#endif
+
+namespace MF_BODY {
+using namespace ::mf;
+
 // Per-event work that does not depend on helicity (phase A), for one point y
 // of the unit hypercube (after the Vegas map).  T is double in the integrand
 // kernel and a dual number (derivatives with respect to y and m_t) in the
@@ -53,21 +72,28 @@ struct PairSum {
 template <typename T>
 struct EventKin {
     T pref;                    // f = pref * sum_h |M_h|^2
-    T p[proc::NLEG][4];        // momenta: incoming along +z / -z, outgoing from phase space
-    T den[proc::NDEN > 0 ? proc::NDEN : 1];   // propagator denominators P^2 - M^2
+    T x1, x2, yb;              // momentum fractions and the rapidity of the partonic frame
+    T p[MF_PROC::NLEG][4];     // momenta: incoming along +z / -z, outgoing from phase space
+    T den[MF_PROC::NDEN > 0 ? MF_PROC::NDEN : 1];   // propagator denominators P^2 - M^2
 };
 
 template <typename T>
 MF_DEV bool phase_a(const KParams &kp, const T *y, const T *masses, const T &ln_tau_min, EventKin<T> &ev) {
-    using namespace proc;
+    using namespace MF_PROC;
     T s_hat = T(kp.S), jx = T(1.0), lum = T(1.0);
     XMap<T> xm;
     const T *u = y;
+    ev.x1 = T(1.0);
+    ev.x2 = T(1.0);
+    ev.yb = T(0.0);
     if (HADRONIC) {
         xm = xmap(y[0], y[1], ln_tau_min);
         s_hat = xm.tau * kp.S;
         jx = xm.jac;
         u = y + 2;
+        ev.x1 = xm.x1;
+        ev.x2 = xm.x2;
+        ev.yb = 0.5 * (xm.ln_x1 - xm.ln_x2);
     }
     T rs = sqrt(s_hat);
     T (*p)[4] = ev.p;
@@ -112,10 +138,37 @@ MF_DEV bool phase_a(const KParams &kp, const T *y, const T *masses, const T &ln_
     return true;
 }
 
-template <typename R, int BLOCK, int HT>
-MF_DEV void kernel_body(const KParams &kp) {
-    using namespace proc;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+// Shared-memory bytes of tile_body's dynamic buffers.
+template <typename R, int BLOCK>
+constexpr size_t tile_smem_bytes() {
+    constexpr int NDEN1 = MF_PROC::NDEN > 0 ? MF_PROC::NDEN : 1;
+    return (size_t)BLOCK * MF_PROC::NLEG * 4 * sizeof(R) + (size_t)BLOCK * NDEN1 * sizeof(R) +
+           (16 - ((BLOCK * NDEN1 * sizeof(R)) % 16)) % 16 + (size_t)BLOCK * 8 * 2 + (size_t)BLOCK * 4 +
+           (BLOCK / 32 + 1) * 4;
+}
+
+// Per-block constants of a process: the Vegas grid (mode 1) and the
+// couplings and masses in the matrix-element precision.
+template <typename R, int BLOCK>
+MF_DEV void load_block_constants(const KParams &kp, double *s_grid, cx<R> *cpl, R *mass_r) {
+    using namespace MF_PROC;
+    const int tid = threadIdx.x;
+    if (kp.mode == 1 || kp.mode == 3) {
+        for (int i = tid; i < NDIM * (kp.nb + 1); i += BLOCK) s_grid[i] = kp.grid[i];
+    }
+    if (tid < 8) {
+        mass_r[tid] = (R)kp.masses[tid];
+        cpl[tid] = C<R>((R)kp.couplings[2 * tid], (R)kp.couplings[2 * tid + 1]);
+    }
+}
+
+// One tile of BLOCK events: phases A, B and C.  Ends with a block barrier.
+// With TC the colour sum of phase B runs on the tensor cores (R = float,
+// BLOCK = 128, tcs set up by the caller).
+template <typename R, int BLOCK, int HT, bool TC = false>
+MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem_raw, const double *s_grid,
+                      const cx<R> *cpl, const R *mass_r, tc::State *tcs = nullptr) {
+    using namespace MF_PROC;
     R *s_mom = reinterpret_cast<R *>(smem_raw);                                   // [BLOCK][NLEG][4]
     R *s_den = s_mom + BLOCK * NLEG * 4;                                           // [BLOCK][NDEN1]
     constexpr int NDEN1 = NDEN > 0 ? NDEN : 1;
@@ -125,26 +178,9 @@ MF_DEV void kernel_body(const KParams &kp) {
     double *s_msq = s_pref + BLOCK;
     int *s_list = reinterpret_cast<int *>(s_msq + BLOCK);
     int *s_warp = s_list + BLOCK;                                                  // [BLOCK/32 + 1]
-    __shared__ double s_grid[NDIM * 65];
-
     const int tid = threadIdx.x;
     const int lane32 = tid & 31, warp = tid >> 5;
-    const int64_t ntiles = (kp.n + BLOCK - 1) / BLOCK;
-
-    if (kp.mode == 1) {
-        for (int i = tid; i < NDIM * (kp.nb + 1); i += BLOCK) s_grid[i] = kp.grid[i];
-    }
-
-    // couplings and masses in the matrix-element precision, in shared memory
-    __shared__ cx<R> cpl[8];
-    __shared__ R mass_r[8];
-    if (tid < 8) {
-        mass_r[tid] = (R)kp.masses[tid];
-        cpl[tid] = C<R>((R)kp.couplings[2 * tid], (R)kp.couplings[2 * tid + 1]);
-    }
-    __syncthreads();
-
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    {
         const int64_t e = tile * BLOCK + tid;
         bool ok = false;
         double pref = 0.0, jv = 1.0;
@@ -152,13 +188,14 @@ MF_DEV void kernel_body(const KParams &kp) {
         if (e < kp.n) {
             // ---------------- phase A: kinematics in double precision
             double y[NDIM];
-            if (kp.mode != 1) {
+            if (kp.mode != 1 && kp.mode != 3) {
 #pragma unroll
                 for (int j = 0; j < NDIM; ++j) y[j] = kp.x[(int64_t)j * kp.n + e];
             } else {
+                const uint64_t gi = kp.mode == 3 ? (uint64_t)kp.idx[e] : (uint64_t)(e + kp.ev0);
 #pragma unroll
                 for (int b = 0; b < (NDIM + 3) / 4; ++b) {
-                    uint64_t c[4] = {(uint64_t)(e + kp.ev0), kp.iteration, kp.subprocess, (uint64_t)b};
+                    uint64_t c[4] = {gi, kp.iteration, kp.subprocess, (uint64_t)b};
                     philox4x64_10(c, kp.seed, 0ull);
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
@@ -175,6 +212,22 @@ MF_DEV void kernel_body(const KParams &kp) {
             }
             EventKin<double> ev;
             ok = phase_a<double>(kp, y, kp.masses, kp.ln_tau_min, ev);
+            if (kp.mode == 3) {
+                // event record: x1, x2 and the momenta boosted along z from the
+                // partonic centre-of-mass frame to the collider frame
+                double *rec = kp.f + e * (2 + 4 * NLEG);
+                const double ch = cosh(ev.yb), sh = sinh(ev.yb);
+                rec[0] = ok ? ev.x1 : 0.0;
+                rec[1] = ok ? ev.x2 : 0.0;
+#pragma unroll
+                for (int i = 0; i < NLEG; ++i) {
+                    rec[2 + 4 * i] = ok ? ch * ev.p[i][0] + sh * ev.p[i][3] : 0.0;
+                    rec[3 + 4 * i] = ok ? ev.p[i][1] : 0.0;
+                    rec[4 + 4 * i] = ok ? ev.p[i][2] : 0.0;
+                    rec[5 + 4 * i] = ok ? sh * ev.p[i][0] + ch * ev.p[i][3] : 0.0;
+                }
+                ok = false;            // no helicity work for records
+            }
             if (ok) {
                 pref = ev.pref;
                 R *sd = s_den + tid * NDEN1;
@@ -221,7 +274,14 @@ MF_DEV void kernel_body(const KParams &kp) {
                 for (int k = 0; k < per; ++k) {
                     const int h = sub * per + k;
                     const bool hv = h < kp.nhel;
-                    double v = (double)helicity_msq<R>(ms, idn, kp.hel[hv ? h : 0], cpl, mass_r);
+                    double v;
+                    if constexpr (TC) {
+                        cx<float> J[NJAMP];
+                        helicity_jamp<float>(ms, idn, kp.hel[hv ? h : 0], cpl, mass_r, J);
+                        v = (double)(tc::colour_sum<NJAMP>(*tcs, J) * (float)INV_COLOUR_DEN);
+                    } else {
+                        v = (double)helicity_msq<R>(ms, idn, kp.hel[hv ? h : 0], cpl, mass_r);
+                    }
                     if (!(hv && valid)) v = 0.0;
                     if (kp.mode == 2 && hv && valid) kp.f[(int64_t)h * kp.n + tile * BLOCK + ev] = v;
                     ps.add(v);
@@ -252,4 +312,56 @@ MF_DEV void kernel_body(const KParams &kp) {
     }
 }
 
-}  // namespace mf
+// Whether the launch provided at least `need` bytes of dynamic shared memory;
+// if not, flag the error (code 2) and let the whole block return.
+MF_DEV bool smem_ok(const KParams &kp, size_t need) {
+    uint32_t have;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(have));
+    if (have >= need) return true;
+    if (threadIdx.x == 0 && kp.err) atomicExch(kp.err, 2);
+    return false;
+}
+
+// The single-process kernel: a grid-stride loop over tiles.
+template <typename R, int BLOCK, int HT>
+MF_DEV void kernel_body(const KParams &kp) {
+    using namespace MF_PROC;
+    if (!smem_ok(kp, tile_smem_bytes<R, BLOCK>())) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double s_grid[NDIM * 65];
+    __shared__ cx<R> cpl[8];
+    __shared__ R mass_r[8];
+    load_block_constants<R, BLOCK>(kp, s_grid, cpl, mass_r);
+    __syncthreads();
+    const int64_t ntiles = (kp.n + BLOCK - 1) / BLOCK;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+        tile_body<R, BLOCK, HT>(kp, tile, smem_raw, s_grid, cpl, mass_r);
+}
+
+// The single-process kernel with the colour sum on the tensor cores
+// (FP32 amplitudes, 128 threads): tensor memory and the operand buffers are
+// set up once per block, after the tile buffers in dynamic shared memory.
+template <int HT>
+MF_DEV void kernel_body_tc(const KParams &kp) {
+    using namespace MF_PROC;
+    constexpr int BLOCK = 128;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ double s_grid[NDIM * 65];
+    __shared__ cx<float> cpl[8];
+    __shared__ float mass_r[8];
+    constexpr size_t tile_bytes = (tile_smem_bytes<float, BLOCK>() + 1023) / 1024 * 1024;
+    if (!smem_ok(kp, tile_bytes + tc::Plan<NJAMP>::SMEM)) return;
+    tc::State tcs;
+    tc::setup<NJAMP>(tcs, smem_raw + tile_bytes, kp.err);
+    tc::load_colour<NJAMP>(tcs, COLOUR_NUM);
+    load_block_constants<float, BLOCK>(kp, s_grid, cpl, mass_r);
+    __syncthreads();
+    const int64_t ntiles = (kp.n + BLOCK - 1) / BLOCK;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+        tile_body<float, BLOCK, HT, true>(kp, tile, smem_raw, s_grid, cpl, mass_r, &tcs);
+    tc::teardown<NJAMP>(tcs);
+}
+
+}  // namespace MF_BODY
+#undef MF_PROC
+#undef MF_BODY

@@ -8,7 +8,9 @@
 struct mf_kparams {
     int64_t n;                 // events
     int32_t mode;              // 0: integrand of given points, 1: Vegas,
-                               // 2: per-helicity |M|^2 of given points into f[h][n]
+                               // 2: per-helicity |M|^2 of given points into f[h][n],
+                               // 3: event records of the Vegas points idx[0..n) into
+                               //    f[n][2 + 4 NLEG] (x1, x2, lab-frame momenta)
     int32_t nhel;              // helicity rows in hel[]
     int32_t nhel_pow2;         // a power of two >= nhel (pairwise-sum padding)
     int32_t nb;                // Vegas bins per dimension
@@ -33,7 +35,21 @@ struct mf_kparams {
     double alpha_s;            // strong coupling the couplings were built with
     int32_t alpha_s_power;     // |M|^2 ~ alpha_s^power
     int32_t pad2;
+    int *err;                  // device error flag (expired waits), may be NULL
+    const int64_t *idx;        // mode 3: global point indices
     double masses[8];
     double couplings[16];      // 8 complex couplings (re, im)
     int8_t hel[MF_KP_MAX_HEL][8];
+};
+
+// Parameters of the batched kernel: several processes' parameter blocks, the
+// tile ranges of the batch (process k owns tiles [start[k], start[k+1])) and
+// the work counter the blocks draw tiles from (zeroed before each launch).
+#define MF_KP_MAX_BATCH 8
+struct mf_batch_params {
+    long long *counter;
+    int32_t nproc;
+    int32_t pad;
+    long long start[MF_KP_MAX_BATCH + 1];
+    mf_kparams kp[MF_KP_MAX_BATCH];
 };

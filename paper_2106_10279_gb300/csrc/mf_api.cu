@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "mf_internal.h"
+#include "device/mf_kinematics.cuh"
 
 // ----------------------------------------------------------------------------
 // errors
@@ -328,7 +329,10 @@ mf_status ensure_context() {
     return MF_OK;
 }
 
+size_t smem_bytes_tc(const mf_process &p);
+
 size_t smem_bytes(const mf_process &p, int prec, int block) {
+    if (prec == MF_MIXED_TC) return smem_bytes_tc(p);
     size_t R = prec == MF_FP64 ? 8 : 4;
     int nden1 = p.gen.n_den > 0 ? p.gen.n_den : 1;
     size_t a = (size_t)block * p.n_legs * 4 * R + (size_t)block * nden1 * R;
@@ -337,30 +341,58 @@ size_t smem_bytes(const mf_process &p, int prec, int block) {
     return a;
 }
 
+// Generate, compile and load the process kernel of precision prec with the
+// launch shape (block, ht) into k.
+mf_status compile_shape(mf_process *p, int prec, int block, int ht, mfi::Compiled &k) {
+    k.block = block;
+    k.ht = ht;
+    mfi::GenInfo info;
+    std::string src = mfi::generate_source(*p, prec, k.block, k.ht, info);
+    std::vector<char> cubin;
+    mf_status st = mfi::jit_compile(src, prec == MF_FP64 ? "mf_proc_f64.cu" : prec == MF_MIXED ? "mf_proc_mixed.cu"
+                                                                                  : "mf_proc_mixed_tc.cu", cubin);
+    if (st != MF_OK) return st;
+    // the shared-memory size depends on the program's denominator count
+    p->source[prec] = src;
+    p->gen = info;
+    k.smem = smem_bytes(*p, prec, k.block);
+    return mfi::load_kernel(cubin, k);
+}
+
+// Tile buffers (FP32, 128 threads) rounded up to 1 KB, then the tensor-core
+// operands: A_hi and A_lo (128 x KP), B (NP x KP), barrier and address.
+size_t smem_bytes_tc(const mf_process &p) {
+    const int K2 = 2 * p.n_jamp, KP = (K2 + 7) / 8 * 8, NP = (K2 + 15) / 16 * 16;
+    const int nden1 = p.gen.n_den > 0 ? p.gen.n_den : 1, block = 128;
+    size_t tile = (size_t)block * p.n_legs * 4 * 4 + (size_t)block * nden1 * 4;
+    tile += (16 - (((size_t)block * nden1 * 4) % 16)) % 16;
+    tile += (size_t)block * 8 * 2 + (size_t)block * 4 + (block / 32 + 1) * 4;
+    tile = (tile + 1023) / 1024 * 1024;
+    return tile + 2 * (size_t)128 * KP * 4 + (size_t)NP * KP * 4 + 16;
+}
+
+int padded_hel(const mf_process *p) {
+    int nhp = 1;
+    while (nhp < (int)(p->hel_all.size() / p->n_legs)) nhp <<= 1;
+    return nhp;
+}
+
 mf_status compile_precision(mf_process *p, int prec) {
     mfi::Compiled &k = p->kern[prec];
     if (k.fn) return MF_OK;
-    k.block = 128;
-    int nhp = 1;
-    while (nhp < (int)(p->hel_all.size() / p->n_legs)) nhp <<= 1;
-    k.ht = nhp < 32 ? nhp : 32;
-    // launch-shape overrides (used by the tuner): block size and lanes per event
+    int block = 128;
+    const int nhp = padded_hel(p);
+    int ht = nhp < 32 ? nhp : 32;
+    // launch-shape overrides: block size and lanes per event
     if (const char *e = std::getenv("MF_BLOCK")) {
         int b = std::atoi(e);
-        if (b == 64 || b == 128 || b == 256 || b == 512) k.block = b;
+        if ((b == 64 || b == 128 || b == 256 || b == 512) && prec != MF_MIXED_TC) block = b;
     }
     if (const char *e = std::getenv("MF_HT")) {
         int h = std::atoi(e);
-        if (h >= 1 && h <= 32 && (h & (h - 1)) == 0 && h <= nhp) k.ht = h;
+        if (h >= 1 && h <= 32 && (h & (h - 1)) == 0 && h <= nhp) ht = h;
     }
-    mfi::GenInfo info;
-    p->source[prec] = mfi::generate_source(*p, prec, k.block, k.ht, info);
-    p->gen = info;
-    std::vector<char> cubin;
-    mf_status st = mfi::jit_compile(p->source[prec], prec == MF_FP64 ? "mf_proc_f64.cu" : "mf_proc_mixed.cu", cubin);
-    if (st != MF_OK) return st;
-    k.smem = smem_bytes(*p, prec, k.block);
-    return mfi::load_kernel(cubin, k);
+    return compile_shape(p, prec, block, ht, k);
 }
 
 mf_status compile_grad(mf_process *p) {
@@ -392,6 +424,19 @@ void fill_common(const mf_process &p, mf_kparams &kp) {
     for (size_t i = 0; i < p.couplings.size() && i < 16; ++i) kp.couplings[i] = p.couplings[i];
     kp.alpha_s = p.alpha_s;
     kp.alpha_s_power = p.alpha_s_power;
+    kp.err = p.d_err;
+}
+
+bool valid_prec(int prec) { return prec == MF_FP64 || prec == MF_MIXED || prec == MF_MIXED_TC; }
+
+// A process kernel's error flag: 1 = a bounded wait expired, 2 = the launch
+// gave less dynamic shared memory than the kernel needs.  Read after the
+// stream has been synchronised; clears the flag.
+mf_status flag_status(mf_process *p, int flag) {
+    if (!flag) return MF_OK;
+    cudaMemset(p->d_err, 0, sizeof(int));
+    if (flag == 2) return fail(MF_ECUDA, "process kernel launched with too little shared memory (results not written)");
+    return fail(MF_ETIMEOUT, "a bounded wait in a process kernel expired; that launch's results are unspecified");
 }
 
 void set_hel(mf_kparams &kp, const std::vector<int8_t> &hel, int n_legs) {
@@ -577,6 +622,10 @@ extern "C" mf_status mf_create_process(const mf_process_desc *d, mf_process **ou
     const int no = p->n_out;
     p->w0_const = std::pow(2.0 * kPi, 4 - 3 * no) * std::pow(kPi / 2.0, no - 1) / (factorial(no - 1) * factorial(no - 2));
     p->pref_const = p->average * kGeV2pb / 2.0;
+    if (cudaMalloc(&p->d_err, sizeof(int)) != cudaSuccess || cudaMemset(p->d_err, 0, sizeof(int)) != cudaSuccess) {
+        mf_destroy_process(p);
+        return fail(MF_ENOMEM, "error flag");
+    }
     // PDF rows at fixed mu_F^2
     if (p->hadronic) {
         const int nx = d->pdf_nx, nq = d->pdf_nq;
@@ -637,11 +686,14 @@ extern "C" mf_status mf_create_process(const mf_process_desc *d, mf_process **ou
         st = launch(p, MF_FP64, kp, nullptr);
         std::vector<double> hf((size_t)nh * npts);
         cudaError_t e = cudaMemcpy(hf.data(), df, sizeof(double) * hf.size(), cudaMemcpyDeviceToHost);
+        int flag = 0;
+        if (e == cudaSuccess) e = cudaMemcpy(&flag, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);
         cudaFree(dx);
         cudaFree(df);
+        if (st == MF_OK && e == cudaSuccess) st = flag_status(p, flag);
         if (st != MF_OK || e != cudaSuccess) {
             mf_destroy_process(p);
-            return fail(MF_ECUDA, "helicity filter run failed");
+            return st != MF_OK ? st : fail(MF_ECUDA, std::string("helicity filter run failed: ") + cudaGetErrorString(e));
         }
         bool any = false;
         for (double v : hf) any |= (v != 0.0);
@@ -656,13 +708,10 @@ extern "C" mf_status mf_create_process(const mf_process_desc *d, mf_process **ou
     return MF_OK;
 }
 
-extern "C" mf_status mf_generate_kernel_source(const mf_process_desc *d, mf_precision prec, int32_t compile,
-                                               char *buf, size_t *len) {
-    if (!len) return fail(MF_EINVAL, "len is NULL");
-    if (prec != MF_FP64 && prec != MF_MIXED && (int)prec != 2) return fail(MF_EINVAL, "bad precision");
-    mf_status st = validate(d);
-    if (st != MF_OK) return st;
-    mf_process p;
+namespace {
+// The parts of a process that code generation reads, from a validated
+// descriptor (no device work).
+int shell_from_desc(const mf_process_desc *d, mf_process &p) {
     const int n = d->n_legs;
     p.n_legs = n;
     p.n_out = n - 2;
@@ -681,19 +730,55 @@ extern "C" mf_status mf_generate_kernel_source(const mf_process_desc *d, mf_prec
     int nh = d->n_hel > 0 ? d->n_hel : (1 << n);
     int nhp = 1;
     while (nhp < nh) nhp <<= 1;
-    mfi::GenInfo info;
-    std::string src = (int)prec == 2 ? mfi::generate_grad_source(p, 128, info)
-                                     : mfi::generate_source(p, prec, 128, nhp < 32 ? nhp : 32, info);
+    return nhp < 32 ? nhp : 32;
+}
+
+mf_status emit_source(const std::string &src, const char *name, int32_t compile, char *buf, size_t *len) {
     if (compile) {
         std::vector<char> cubin;
-        st = mfi::jit_compile(src, (int)prec == 2 ? "mf_proc_grad.cu" : prec == MF_FP64 ? "mf_proc_f64.cu" : "mf_proc_mixed.cu",
-                              cubin);
+        mf_status st = mfi::jit_compile(src, name, cubin);
         if (st != MF_OK) return st;
     }
     size_t need = src.size() + 1;
     if (buf && *len >= need) std::memcpy(buf, src.c_str(), need);
     *len = need;
     return MF_OK;
+}
+}  // namespace
+
+extern "C" mf_status mf_generate_kernel_source(const mf_process_desc *d, mf_precision prec, int32_t compile,
+                                               char *buf, size_t *len) {
+    if (!len) return fail(MF_EINVAL, "len is NULL");
+    if (!valid_prec(prec) && (int)prec != 2) return fail(MF_EINVAL, "bad precision");
+    mf_status st = validate(d);
+    if (st != MF_OK) return st;
+    mf_process p;
+    const int ht = shell_from_desc(d, p);
+    mfi::GenInfo info;
+    std::string src = (int)prec == 2 ? mfi::generate_grad_source(p, 128, info)
+                                     : mfi::generate_source(p, prec, 128, ht, info);
+    return emit_source(src, (int)prec == 2 ? "mf_proc_grad.cu" : prec == MF_FP64 ? "mf_proc_f64.cu"
+                                              : prec == MF_MIXED ? "mf_proc_mixed.cu" : "mf_proc_mixed_tc.cu",
+                       compile, buf, len);
+}
+
+extern "C" mf_status mf_generate_batch_source(const mf_process_desc *const *descs, int32_t nproc, mf_precision prec,
+                                              int32_t compile, char *buf, size_t *len) {
+    if (!len || !descs) return fail(MF_EINVAL, "NULL argument");
+    if (nproc < 1 || nproc > MF_KP_MAX_BATCH) return fail(MF_EINVAL, "need 1 to 8 processes");
+    if (prec != MF_FP64 && prec != MF_MIXED) return fail(MF_EINVAL, "bad precision");
+    std::vector<mf_process> shells(nproc);
+    std::vector<const mf_process *> ps;
+    std::vector<int> hts;
+    for (int k = 0; k < nproc; ++k) {
+        mf_status st = validate(descs[k]);
+        if (st != MF_OK) return st;
+        hts.push_back(shell_from_desc(descs[k], shells[k]));
+        ps.push_back(&shells[k]);
+    }
+    std::vector<mfi::GenInfo> infos;
+    std::string src = mfi::generate_batch_source(ps, prec, 128, hts, infos);
+    return emit_source(src, prec == MF_FP64 ? "mf_batch_f64.cu" : "mf_batch_mixed.cu", compile, buf, len);
 }
 
 extern "C" mf_status mf_destroy_process(mf_process *p) {
@@ -702,6 +787,7 @@ extern "C" mf_status mf_destroy_process(mf_process *p) {
     if (p->ev_start) cudaEventDestroy(p->ev_start);
     if (p->ev_stop) cudaEventDestroy(p->ev_stop);
     cudaFree(p->d_pdf_rows);
+    cudaFree(p->d_err);
     cudaFree(p->d_w);
     cudaFree(p->d_bins);
     delete p;
@@ -728,11 +814,19 @@ extern "C" mf_status mf_process_last_kernel_ms(const mf_process *p, double *ms) 
     return MF_OK;
 }
 
+extern "C" mf_status mf_process_check(mf_process *p) {
+    if (!p) return fail(MF_EINVAL, "NULL process");
+    int flag = 0;
+    MF_CUDA(cudaDeviceSynchronize());
+    MF_CUDA(cudaMemcpy(&flag, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    return flag_status(p, flag);
+}
+
 extern "C" mf_status mf_integrand(mf_process *p, const double *x, int64_t n, double *f, mf_precision prec,
                                   void *stream) {
     if (!p) return fail(MF_EINVAL, "NULL process");
     if (n < 0) return fail(MF_EINVAL, "negative n");
-    if (prec != MF_FP64 && prec != MF_MIXED) return fail(MF_EINVAL, "bad precision");
+    if (!valid_prec(prec)) return fail(MF_EINVAL, "bad precision");
     if (n == 0) return MF_OK;
     if (!x || !f) return fail(MF_EINVAL, "NULL x or f");
     mf_status st = compile_precision(p, prec);
@@ -751,7 +845,7 @@ extern "C" mf_status mf_helicity_msq(mf_process *p, const double *x, int64_t n, 
                                      void *stream) {
     if (!p) return fail(MF_EINVAL, "NULL process");
     if (n < 0) return fail(MF_EINVAL, "negative n");
-    if (prec != MF_FP64 && prec != MF_MIXED) return fail(MF_EINVAL, "bad precision");
+    if (!valid_prec(prec)) return fail(MF_EINVAL, "bad precision");
     if (n == 0) return MF_OK;
     if (!x || !out) return fail(MF_EINVAL, "NULL x or out");
     mf_status st = compile_precision(p, prec);
@@ -863,12 +957,8 @@ mf_status tree_reduce(const double *nodes, int n_nodes, int K, int64_t nchunks, 
 
 int partial_size(const mf_vegas *v) { return 4 + 2 * v->ndim * v->nbins; }
 
-// Evaluate points [ev0, ev0 + n) of iteration v->iteration into the process
-// scratch (w, bins) and accumulate their chunks into v->d_slots.
-mf_status run_points(mf_process *p, mf_vegas *v, int prec, int64_t n, int64_t ev0, int subprocess, uint64_t seed,
-                     cudaStream_t s) {
-    mf_status st = compile_precision(p, prec);
-    if (st != MF_OK) return st;
+// Process scratch (w, bins) for n points and grid slots for their chunks.
+mf_status ensure_scratch(mf_process *p, mf_vegas *v, int64_t n) {
     if (p->scratch_n < n) {
         cudaFree(p->d_w);
         cudaFree(p->d_bins);
@@ -892,8 +982,12 @@ mf_status run_points(mf_process *p, mf_vegas *v, int prec, int64_t n, int64_t ev
         MF_CUDA(cudaEventCreate(&p->ev_start));
         MF_CUDA(cudaEventCreate(&p->ev_stop));
     }
-    if (n == 0) return MF_OK;
-    mf_kparams kp;
+    return MF_OK;
+}
+
+// Parameters of the Vegas-mode kernel for points [ev0, ev0 + n).
+void vegas_params(const mf_process *p, const mf_vegas *v, int64_t n, int64_t ev0, int subprocess, uint64_t seed,
+                  mf_kparams &kp) {
     fill_common(*p, kp);
     set_hel(kp, p->hel, p->n_legs);
     kp.mode = 1;
@@ -906,10 +1000,11 @@ mf_status run_points(mf_process *p, mf_vegas *v, int prec, int64_t n, int64_t ev
     kp.seed = seed;
     kp.iteration = (uint64_t)v->iteration;
     kp.subprocess = (uint64_t)subprocess;
-    MF_CUDA(cudaEventRecord(p->ev_start, s));
-    st = launch(p, prec, kp, s);
-    if (st != MF_OK) return st;
-    MF_CUDA(cudaEventRecord(p->ev_stop, s));
+}
+
+// Chunk partial sums of the process scratch's n points into v->d_slots.
+mf_status accumulate(mf_process *p, mf_vegas *v, int64_t n, cudaStream_t s) {
+    const int64_t nchunks = (n + kChunk - 1) / kChunk;
     const size_t acc_smem = sizeof(double) * 2 * kChunk + kChunk;
     static bool attr_set = false;
     if (!attr_set) {
@@ -921,6 +1016,25 @@ mf_status run_points(mf_process *p, mf_vegas *v, int prec, int64_t n, int64_t ev
                                                                               v->d_slots, nchunks);
     MF_CUDA(cudaGetLastError());
     return MF_OK;
+}
+
+// Evaluate points [ev0, ev0 + n) of iteration v->iteration into the process
+// scratch (w, bins) and accumulate their chunks into v->d_slots.
+mf_status run_points(mf_process *p, mf_vegas *v, int prec, int64_t n, int64_t ev0, int subprocess, uint64_t seed,
+                     cudaStream_t s) {
+    mf_status st = compile_precision(p, prec);
+    if (st != MF_OK) return st;
+    st = ensure_scratch(p, v, n);
+    if (st != MF_OK) return st;
+    p->last_n = n;
+    if (n == 0) return MF_OK;
+    mf_kparams kp;
+    vegas_params(p, v, n, ev0, subprocess, seed, kp);
+    MF_CUDA(cudaEventRecord(p->ev_start, s));
+    st = launch(p, prec, kp, s);
+    if (st != MF_OK) return st;
+    MF_CUDA(cudaEventRecord(p->ev_stop, s));
+    return accumulate(p, v, n, s);
 }
 
 // Nodes ids (host, [n][2]) of the accumulated chunks -> device values [n][K].
@@ -1056,7 +1170,7 @@ extern "C" mf_status mf_vegas_iterate(mf_vegas *const *grids, mf_process *const 
                                       int32_t nproc, uint64_t seed, mf_precision prec, int32_t refine,
                                       mf_iter_result *out, void *stream) {
     if (nproc < 1 || !grids || !procs || !n_events || !out) return fail(MF_EINVAL, "bad arguments");
-    if (prec != MF_FP64 && prec != MF_MIXED) return fail(MF_EINVAL, "bad precision");
+    if (!valid_prec(prec)) return fail(MF_EINVAL, "bad precision");
     cudaStream_t s = (cudaStream_t)stream;
     for (int k = 0; k < nproc; ++k) {
         if (!grids[k] || !procs[k]) return fail(MF_EINVAL, "NULL grid or process");
@@ -1069,6 +1183,7 @@ extern "C" mf_status mf_vegas_iterate(mf_vegas *const *grids, mf_process *const 
             if (grids[q] == grids[k]) return fail(MF_EINVAL, "a grid appears twice");
     }
     std::vector<std::vector<double>> res(nproc, std::vector<double>(8));
+    std::vector<int> flags(nproc, 0);
     for (int k = 0; k < nproc; ++k) {
         mf_process *p = procs[k];
         mf_vegas *v = grids[k];
@@ -1083,12 +1198,17 @@ extern "C" mf_status mf_vegas_iterate(mf_vegas *const *grids, mf_process *const 
         st = finish(v, v->d_tree_out, n, refine, s);
         if (st != MF_OK) return st;
         MF_CUDA(cudaMemcpyAsync(res[k].data(), v->d_result, sizeof(double) * 7, cudaMemcpyDeviceToHost, s));
+        MF_CUDA(cudaMemcpyAsync(&flags[k], p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     }
     MF_CUDA(cudaStreamSynchronize(s));
     for (int k = 0; k < nproc; ++k) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, procs[k]->ev_start, procs[k]->ev_stop) == cudaSuccess)
             procs[k]->last_kernel_ms = ms;
+    }
+    for (int k = 0; k < nproc; ++k) {
+        mf_status st = flag_status(procs[k], flags[k]);
+        if (st != MF_OK) return st;
     }
     bool any_nan = false;
     for (int k = 0; k < nproc; ++k) {
@@ -1110,7 +1230,7 @@ extern "C" mf_status mf_vegas_shard_accumulate(mf_vegas *v, mf_process *p, int64
                                                int64_t chunk_end, int32_t subprocess, uint64_t seed,
                                                mf_precision prec, double *nodes, int32_t *n_nodes, void *stream) {
     if (!v || !p || !nodes || !n_nodes) return fail(MF_EINVAL, "NULL argument");
-    if (prec != MF_FP64 && prec != MF_MIXED) return fail(MF_EINVAL, "bad precision");
+    if (!valid_prec(prec)) return fail(MF_EINVAL, "bad precision");
     if (v->ndim != p->ndim) return fail(MF_EINVAL, "grid and process dimensions differ");
     if (n_total < 2) return fail(MF_EINVAL, "need at least two events per iteration");
     const int64_t nchunks = (n_total + kChunk - 1) / kChunk;
@@ -1133,7 +1253,11 @@ extern "C" mf_status mf_vegas_shard_accumulate(mf_vegas *v, mf_process *p, int64
     const int K = partial_size(v);
     std::vector<double> vals((size_t)nn * K);
     if (nn) MF_CUDA(cudaMemcpyAsync(vals.data(), v->d_tree_out, sizeof(double) * vals.size(), cudaMemcpyDeviceToHost, s));
+    int flag = 0;
+    MF_CUDA(cudaMemcpyAsync(&flag, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     MF_CUDA(cudaStreamSynchronize(s));
+    st = flag_status(p, flag);
+    if (st != MF_OK) return st;
     if (n > 0) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, p->ev_start, p->ev_stop) == cudaSuccess) p->last_kernel_ms = ms;
@@ -1192,6 +1316,443 @@ extern "C" mf_status mf_tree_reduce(const double *nodes, int32_t n_nodes, int32_
     if (level < 0 || level > kTreeMaxLevel || index < 0 || (index << level) >= nchunks)
         return fail(MF_EINVAL, "target node does not exist");
     return tree_reduce(nodes, n_nodes, K, nchunks, level, index, out);
+}
+
+// ----------------------------------------------------------------------------
+// Launch-shape tuner: the helicity sum is a fixed pairwise tree whatever the
+// lanes per event, and no event's arithmetic depends on the block size, so
+// every shape gives the same bits and the fastest one can be kept.
+// ----------------------------------------------------------------------------
+extern "C" mf_status mf_process_tune(mf_process *p, mf_precision prec, int64_t n_sample, void *stream, int32_t *block,
+                                     int32_t *ht) {
+    if (!p) return fail(MF_EINVAL, "NULL process");
+    if (!valid_prec(prec)) return fail(MF_EINVAL, "bad precision");
+    if (n_sample < 1024 || n_sample > ((int64_t)1 << 30)) return fail(MF_EINVAL, "n_sample out of range");
+    cudaStream_t s = (cudaStream_t)stream;
+    mf_vegas *v = nullptr;
+    mf_status st = mf_vegas_create(p->ndim, 50, 1.5, &v);
+    if (st != MF_OK) return st;
+    st = ensure_scratch(p, v, n_sample);
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (st == MF_OK && (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess))
+        st = fail(MF_ECUDA, "events");
+    const int nhp = padded_hel(p);
+    float best_ms = 0.f;
+    mfi::Compiled best;
+    for (int bl : {128, 256}) {
+        if (prec == MF_MIXED_TC && bl != 128) continue;      // one MMA row per thread of 128
+        for (int h : {8, 16, 32}) {
+            if (st != MF_OK) break;
+            if (h > nhp && h != 8) continue;
+            const int hh = h <= nhp ? h : nhp;
+            mfi::Compiled k;
+            st = compile_shape(p, prec, bl, hh, k);
+            if (st != MF_OK) break;
+            mf_kparams kp;
+            vegas_params(p, v, n_sample, 0, 0, 12345, kp);
+            float ms = 1e30f;
+            mfi::Compiled saved = p->kern[prec];
+            p->kern[prec] = k;
+            for (int rep = 0; rep < 3 && st == MF_OK; ++rep) {
+                if (cudaEventRecord(a, s) != cudaSuccess) st = fail(MF_ECUDA, "event");
+                if (st == MF_OK) st = launch(p, prec, kp, s);
+                if (st == MF_OK && cudaEventRecord(b, s) != cudaSuccess) st = fail(MF_ECUDA, "event");
+                if (st == MF_OK && cudaEventSynchronize(b) != cudaSuccess) st = fail(MF_ECUDA, "tuning launch failed");
+                float t = 0.f;
+                if (st == MF_OK && rep > 0 && cudaEventElapsedTime(&t, a, b) == cudaSuccess) ms = std::min(ms, t);
+            }
+            p->kern[prec] = saved;
+            if (st != MF_OK) {
+                mfi::unload_kernel(k);
+                break;
+            }
+            if (!best.fn || ms < best_ms) {
+                if (best.fn) mfi::unload_kernel(best);
+                best = k;
+                best_ms = ms;
+            } else {
+                mfi::unload_kernel(k);
+            }
+        }
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    mf_vegas_destroy(v);
+    if (st != MF_OK) {
+        if (best.fn) mfi::unload_kernel(best);
+        return st;
+    }
+    mfi::unload_kernel(p->kern[prec]);
+    p->kern[prec] = best;
+    // the generated source and counts of the kept shape
+    mfi::GenInfo info;
+    p->source[prec] = mfi::generate_source(*p, prec, best.block, best.ht, info);
+    p->gen = info;
+    if (block) *block = best.block;
+    if (ht) *ht = best.ht;
+    return MF_OK;
+}
+
+// ----------------------------------------------------------------------------
+// Batched iteration: the subprocesses of one Vegas iteration in one
+// persistent launch (tiles of every subprocess drawn from one counter, the
+// costliest subprocess first, so that no SM idles while another subprocess's
+// tail finishes), then the per-subprocess accumulation and refinement.
+// ----------------------------------------------------------------------------
+extern "C" mf_status mf_batch_create(mf_process *const *procs, int32_t nproc, mf_precision prec, mf_batch **out) {
+    if (!out) return fail(MF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!procs || nproc < 1 || nproc > MF_KP_MAX_BATCH) return fail(MF_EINVAL, "need 1 to 8 processes");
+    if (prec == MF_MIXED_TC) return fail(MF_EUNSUPPORTED, "batches use the FP32 colour sum");
+    if (prec != MF_FP64 && prec != MF_MIXED) return fail(MF_EINVAL, "bad precision");
+    for (int k = 0; k < nproc; ++k) {
+        if (!procs[k]) return fail(MF_EINVAL, "NULL process");
+        for (int q = 0; q < k; ++q)
+            if (procs[q] == procs[k]) return fail(MF_EINVAL, "a process appears twice");
+    }
+    std::vector<double> cost(nproc);
+    std::vector<int> hts(nproc);
+    for (int k = 0; k < nproc; ++k) {
+        mf_status st = compile_precision(procs[k], prec);          // also fixes HT and the FLOP counts
+        if (st != MF_OK) return st;
+        hts[k] = procs[k]->kern[prec].ht;
+        cost[k] = procs[k]->gen.flops_per_hel * (double)(procs[k]->hel.size() / procs[k]->n_legs) +
+                  procs[k]->gen.flops_kin;
+    }
+    mf_batch *b = new (std::nothrow) mf_batch();
+    if (!b) return fail(MF_ENOMEM, "host allocation");
+    cudaGetDevice(&b->device);
+    b->precision = prec;
+    b->procs.assign(procs, procs + nproc);
+    b->order.resize(nproc);
+    for (int k = 0; k < nproc; ++k) b->order[k] = k;
+    std::stable_sort(b->order.begin(), b->order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+    std::vector<const mf_process *> ps;
+    std::vector<int> hs;
+    size_t smem = 0;
+    for (int slot = 0; slot < nproc; ++slot) {
+        const mf_process *p = procs[b->order[slot]];
+        ps.push_back(p);
+        hs.push_back(hts[b->order[slot]]);
+        smem = std::max(smem, smem_bytes(*p, prec, 128));
+    }
+    std::vector<mfi::GenInfo> infos;
+    b->source = mfi::generate_batch_source(ps, prec, 128, hs, infos);
+    std::vector<char> cubin;
+    mf_status st = mfi::jit_compile(b->source, prec == MF_FP64 ? "mf_batch_f64.cu" : "mf_batch_mixed.cu", cubin);
+    if (st == MF_OK) {
+        b->kern.block = 128;
+        b->kern.smem = smem;
+        st = mfi::load_kernel(cubin, b->kern, "mf_batch_kernel");
+    }
+    if (st == MF_OK && cudaMalloc(&b->d_counter, sizeof(long long)) != cudaSuccess)
+        st = fail(MF_ENOMEM, "batch counter");
+    if (st == MF_OK && (cudaEventCreate(&b->ev_start) != cudaSuccess || cudaEventCreate(&b->ev_stop) != cudaSuccess))
+        st = fail(MF_ECUDA, "batch events");
+    if (st != MF_OK) {
+        mf_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_batch_destroy(mf_batch *b) {
+    if (!b) return MF_OK;
+    mfi::unload_kernel(b->kern);
+    cudaFree(b->d_counter);
+    if (b->ev_start) cudaEventDestroy(b->ev_start);
+    if (b->ev_stop) cudaEventDestroy(b->ev_stop);
+    delete b;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_batch_get_info(const mf_batch *b, int32_t *order, int32_t *regs, double *last_kernel_ms) {
+    if (!b) return fail(MF_EINVAL, "NULL batch");
+    if (order)
+        for (size_t k = 0; k < b->order.size(); ++k) order[k] = b->order[k];
+    if (regs) *regs = b->kern.regs;
+    if (last_kernel_ms) *last_kernel_ms = b->last_kernel_ms;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_batch_iterate(mf_batch *b, mf_vegas *const *grids, const int64_t *n_events, uint64_t seed,
+                                      int32_t refine, mf_iter_result *out, void *stream) {
+    if (!b || !grids || !n_events || !out) return fail(MF_EINVAL, "NULL argument");
+    const int nproc = (int)b->procs.size();
+    for (int k = 0; k < nproc; ++k) {
+        if (!grids[k]) return fail(MF_EINVAL, "NULL grid");
+        if (grids[k]->ndim != b->procs[k]->ndim) return fail(MF_EINVAL, "grid and process dimensions differ");
+        if (n_events[k] < 2) return fail(MF_EINVAL, "need at least two events per iteration");
+        if ((n_events[k] + kChunk - 1) / kChunk > ((int64_t)1 << kTreeMaxLevel))
+            return fail(MF_EINVAL, "too many events per iteration");
+        if (grids[k]->iteration >= grids[k]->max_iter) return fail(MF_EUNSUPPORTED, "too many iterations");
+        for (int q = 0; q < k; ++q)
+            if (grids[q] == grids[k]) return fail(MF_EINVAL, "a grid appears twice");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    mf_batch_params bp;
+    std::memset(&bp, 0, sizeof bp);
+    bp.counter = b->d_counter;
+    bp.nproc = nproc;
+    bp.start[0] = 0;
+    for (int slot = 0; slot < nproc; ++slot) {
+        const int u = b->order[slot];
+        mf_process *p = b->procs[u];
+        mf_status st = ensure_scratch(p, grids[u], n_events[u]);
+        if (st != MF_OK) return st;
+        vegas_params(p, grids[u], n_events[u], 0, u, seed, bp.kp[slot]);
+        bp.start[slot + 1] = bp.start[slot] + (n_events[u] + b->kern.block - 1) / b->kern.block;
+    }
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
+    int64_t grid = (int64_t)nsm * b->kern.max_blocks_per_sm;
+    if (grid > bp.start[nproc]) grid = bp.start[nproc];
+    MF_CUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(long long), s));
+    MF_CUDA(cudaEventRecord(b->ev_start, s));
+    void *args[] = {&bp};
+    mf_status st = mfi::launch_kernel(b->kern, (unsigned)grid, args, s);
+    if (st != MF_OK) return st;
+    MF_CUDA(cudaEventRecord(b->ev_stop, s));
+    std::vector<std::vector<double>> res(nproc, std::vector<double>(8));
+    std::vector<int> flags(nproc, 0);
+    for (int k = 0; k < nproc; ++k) {
+        mf_process *p = b->procs[k];
+        mf_vegas *v = grids[k];
+        const int64_t n = n_events[k];
+        st = accumulate(p, v, n, s);
+        if (st != MF_OK) return st;
+        const int64_t nchunks = (n + kChunk - 1) / kChunk;
+        const std::vector<int64_t> root = {tree_levels(nchunks), 0};
+        st = tree_nodes(v, nchunks, 0, nchunks, root, s);
+        if (st != MF_OK) return st;
+        st = finish(v, v->d_tree_out, n, refine, s);
+        if (st != MF_OK) return st;
+        MF_CUDA(cudaMemcpyAsync(res[k].data(), v->d_result, sizeof(double) * 7, cudaMemcpyDeviceToHost, s));
+        MF_CUDA(cudaMemcpyAsync(&flags[k], p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    }
+    MF_CUDA(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, b->ev_start, b->ev_stop) == cudaSuccess) b->last_kernel_ms = ms;
+    for (int k = 0; k < nproc; ++k) {
+        st = flag_status(b->procs[k], flags[k]);
+        if (st != MF_OK) return st;
+    }
+    bool any_nan = false;
+    for (int k = 0; k < nproc; ++k) {
+        fill_result(out[k], grids[k], n_events[k], res[k].data());
+        any_nan |= out[k].n_nan > 0;
+        grids[k]->iteration += 1;
+    }
+    if (any_nan) return fail(MF_ENAN, "some points had non-finite weights (counted as zero)");
+    return MF_OK;
+}
+
+// ----------------------------------------------------------------------------
+// Unweighting (hit or miss against w_max) and event records.
+// ----------------------------------------------------------------------------
+namespace {
+constexpr int kUwThreads = 256;
+constexpr int kUwPer = kChunk / kUwThreads;          // consecutive points per thread
+
+// Per chunk: the accept decision of every point and the chunk's count.
+__global__ void __launch_bounds__(kUwThreads) unweight_count_kernel(const double *w, int64_t n, uint64_t seed,
+                                                                    uint64_t iteration, uint64_t subprocess,
+                                                                    double w_max, uint8_t *acc, int *count) {
+    __shared__ int s_cnt;
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    int local = 0;
+    const int64_t base = (int64_t)blockIdx.x * kChunk + (int64_t)threadIdx.x * kUwPer;
+    for (int k = 0; k < kUwPer; ++k) {
+        const int64_t g = base + k;
+        if (g >= n) break;
+        uint64_t c[4] = {(uint64_t)g, iteration, subprocess, 15ull};
+        mf::philox4x64_10(c, seed, 0ull);
+        const double u = mf::unit_from_bits(c[0]);
+        const bool a = fabs(w[g]) > u * w_max;
+        acc[g] = a ? 1 : 0;
+        local += a ? 1 : 0;
+    }
+    atomicAdd(&s_cnt, local);
+    __syncthreads();
+    if (threadIdx.x == 0) count[blockIdx.x] = s_cnt;
+}
+
+// Indices and weights of the kept points, in point order: chunk offsets from
+// the host, within a chunk a block-wide exclusive scan of per-thread counts.
+__global__ void __launch_bounds__(kUwThreads) unweight_compact_kernel(const uint8_t *acc, const double *w, int64_t n,
+                                                                      const int64_t *offset, int64_t *idx,
+                                                                      double *wk) {
+    __shared__ int s_scan[kUwThreads];
+    const int64_t base = (int64_t)blockIdx.x * kChunk + (int64_t)threadIdx.x * kUwPer;
+    int mine = 0;
+    for (int k = 0; k < kUwPer; ++k) {
+        const int64_t g = base + k;
+        if (g < n) mine += acc[g];
+    }
+    s_scan[threadIdx.x] = mine;
+    __syncthreads();
+    for (int off = 1; off < kUwThreads; off <<= 1) {
+        const int v = threadIdx.x >= off ? s_scan[threadIdx.x - off] : 0;
+        __syncthreads();
+        s_scan[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int64_t pos = offset[blockIdx.x] + s_scan[threadIdx.x] - mine;
+    for (int k = 0; k < kUwPer; ++k) {
+        const int64_t g = base + k;
+        if (g < n && acc[g]) {
+            idx[pos] = g;
+            wk[pos] = w[g];
+            ++pos;
+        }
+    }
+}
+
+__global__ void max_abs_kernel(const double *w, int64_t n, unsigned long long *out) {
+    double m = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double a = fabs(w[i]);
+        if (a > m) m = a;            // NaN never wins
+    }
+    // non-negative doubles order like their bit patterns
+    atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+}  // namespace
+
+extern "C" mf_status mf_process_max_weight(mf_process *p, double *w_max, void *stream) {
+    if (!p || !w_max) return fail(MF_EINVAL, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long *d = nullptr;
+    MF_CUDA(cudaMalloc(&d, sizeof(unsigned long long)));
+    unsigned long long h = 0;
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof h, s);
+    if (e == cudaSuccess && p->last_n > 0) {
+        max_abs_kernel<<<304, 256, 0, s>>>(p->d_w, p->last_n, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(MF_ECUDA, std::string("max weight: ") + cudaGetErrorString(e));
+    double m;
+    std::memcpy(&m, &h, sizeof m);
+    *w_max = m;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_vegas_unweight(mf_vegas *v, mf_process *p, int64_t n_events, uint64_t seed,
+                                       int32_t subprocess, mf_precision prec, double w_max, mf_lhe_writer *lhe,
+                                       double *records, int64_t capacity, int64_t *n_accepted, void *stream) {
+    if (!v || !p || !n_accepted) return fail(MF_EINVAL, "NULL argument");
+    if (!valid_prec(prec)) return fail(MF_EINVAL, "bad precision");
+    if (v->ndim != p->ndim) return fail(MF_EINVAL, "grid and process dimensions differ");
+    if (n_events < 1) return fail(MF_EINVAL, "need at least one point");
+    if (!(w_max > 0.0) || !std::isfinite(w_max)) return fail(MF_EINVAL, "w_max must be positive and finite");
+    if (capacity < 0 || (capacity > 0 && !records)) return fail(MF_EINVAL, "bad record buffer");
+    if (subprocess < 0) return fail(MF_EINVAL, "bad subprocess index");
+    if (lhe && mfi::lhe_legs(lhe) != p->n_legs) return fail(MF_EINVAL, "LHE writer and process have different legs");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = n_events;
+    mf_status st = compile_precision(p, prec);
+    if (st != MF_OK) return st;
+    st = ensure_scratch(p, v, n);
+    if (st != MF_OK) return st;
+    // the weights of the pass
+    mf_kparams kp;
+    vegas_params(p, v, n, 0, subprocess, seed, kp);
+    st = launch(p, prec, kp, s);
+    if (st != MF_OK) return st;
+    p->last_n = n;
+    const int64_t nchunks = (n + kChunk - 1) / kChunk;
+    uint8_t *d_acc = nullptr;
+    int *d_cnt = nullptr;
+    int64_t *d_off = nullptr, *d_idx = nullptr;
+    double *d_wk = nullptr, *d_rec = nullptr;
+    std::vector<int> cnt(nchunks);
+    std::vector<int64_t> off(nchunks);
+    int64_t nacc = 0;
+    const int RW = 2 + 4 * p->n_legs;
+    auto cleanup = [&]() {
+        cudaFree(d_acc);
+        cudaFree(d_cnt);
+        cudaFree(d_off);
+        cudaFree(d_idx);
+        cudaFree(d_wk);
+        cudaFree(d_rec);
+    };
+#define MF_UW(call)                                                                            \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            cleanup();                                                                         \
+            return fail(MF_ECUDA, std::string("unweighting: ") + cudaGetErrorString(e_));       \
+        }                                                                                      \
+    } while (0)
+    MF_UW(cudaMalloc(&d_acc, (size_t)n));
+    MF_UW(cudaMalloc(&d_cnt, sizeof(int) * nchunks));
+    MF_UW(cudaMalloc(&d_off, sizeof(int64_t) * nchunks));
+    unweight_count_kernel<<<(unsigned)nchunks, kUwThreads, 0, s>>>(p->d_w, n, seed, (uint64_t)v->iteration,
+                                                                   (uint64_t)subprocess, w_max, d_acc, d_cnt);
+    MF_UW(cudaGetLastError());
+    MF_UW(cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int) * nchunks, cudaMemcpyDeviceToHost, s));
+    int flag = 0;
+    MF_UW(cudaMemcpyAsync(&flag, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MF_UW(cudaStreamSynchronize(s));
+    st = flag_status(p, flag);
+    if (st != MF_OK) {
+        cleanup();
+        return st;
+    }
+    for (int64_t c = 0; c < nchunks; ++c) {
+        off[c] = nacc;
+        nacc += cnt[c];
+    }
+    *n_accepted = nacc;
+    if (nacc > 0 && (capacity > 0 || lhe)) {
+        MF_UW(cudaMemcpyAsync(d_off, off.data(), sizeof(int64_t) * nchunks, cudaMemcpyHostToDevice, s));
+        MF_UW(cudaMalloc(&d_idx, sizeof(int64_t) * nacc));
+        MF_UW(cudaMalloc(&d_wk, sizeof(double) * nacc));
+        MF_UW(cudaMalloc(&d_rec, sizeof(double) * RW * nacc));
+        unweight_compact_kernel<<<(unsigned)nchunks, kUwThreads, 0, s>>>(d_acc, p->d_w, n, d_off, d_idx, d_wk);
+        MF_UW(cudaGetLastError());
+        // the kept points' kinematics, recomputed from their Philox counters
+        mf_kparams kr;
+        vegas_params(p, v, nacc, 0, subprocess, seed, kr);
+        kr.mode = 3;
+        kr.idx = d_idx;
+        kr.f = d_rec;
+        st = launch(p, prec, kr, s);
+        if (st != MF_OK) {
+            cleanup();
+            return st;
+        }
+        std::vector<double> wk(nacc), rec((size_t)RW * nacc);
+        MF_UW(cudaMemcpyAsync(wk.data(), d_wk, sizeof(double) * nacc, cudaMemcpyDeviceToHost, s));
+        MF_UW(cudaMemcpyAsync(rec.data(), d_rec, sizeof(double) * RW * nacc, cudaMemcpyDeviceToHost, s));
+        MF_UW(cudaStreamSynchronize(s));
+        const int OW = RW + 1;
+        std::vector<double> out((size_t)OW * nacc);
+        for (int64_t k = 0; k < nacc; ++k) {
+            const double w = wk[k];
+            const double ew = (w < 0.0 ? -1.0 : 1.0) * std::max(std::fabs(w), w_max) / (double)n;
+            out[(size_t)k * OW] = ew;
+            std::copy(rec.begin() + (size_t)k * RW, rec.begin() + (size_t)(k + 1) * RW, out.begin() + (size_t)k * OW + 1);
+        }
+        if (capacity > 0)
+            std::copy(out.begin(), out.begin() + (size_t)OW * std::min(capacity, nacc), records);
+        if (lhe) {
+            st = mfi::lhe_push(lhe, std::move(out));
+            if (st != MF_OK) {
+                cleanup();
+                return st;
+            }
+        }
+    }
+#undef MF_UW
+    cleanup();
+    return MF_OK;
 }
 
 // ----------------------------------------------------------------------------

@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstdio>
 #include <functional>
+#include <algorithm>
 #include <map>
 #include <sstream>
 
@@ -44,7 +45,7 @@ double routine_flops(int r) {
 // Includes, the process constants and the double-precision propagator
 // denominators (shared by the integrand and the gradient sources).
 void emit_header(std::ostringstream &o, const mf_process &p, GenInfo &info, std::vector<uint32_t> &mask,
-                 const char *R) {
+                 const char *R, const char *ns = "proc") {
     const int n = p.n_legs;
     // --- wavefunction momenta as signed leg masks, denominator slots
     mask.assign(p.ops.size(), 0);
@@ -77,7 +78,7 @@ void emit_header(std::ostringstream &o, const mf_process &p, GenInfo &info, std:
     o << "// generated: diagram program of one process, precision " << R << "\n";
     o << "#include \"mf_common.cuh\"\n#include \"mf_kinematics.cuh\"\n#include \"mf_helas.cuh\"\n";
     o << "#ifndef MF_PROG_SYNC\n#define MF_PROG_SYNC() __syncthreads()\n#endif\n";
-    o << "namespace proc {\n";
+    o << "namespace " << ns << " {\n";
     o << "constexpr int NLEG = " << n << ", NOUT = " << p.n_out << ", NDIM = " << p.ndim
       << ", NJAMP = " << p.n_jamp << ", NDEN = " << info.n_den << ", HADRONIC = " << p.hadronic << ";\n";
     o << "__device__ constexpr int LEG_MASS_ID[NLEG] = {";
@@ -128,12 +129,13 @@ void emit_header(std::ostringstream &o, const mf_process &p, GenInfo &info, std:
     o << "}\n";
 }
 
-std::string generate_source(const mf_process &p, int precision, int block, int ht, GenInfo &info) {
+std::string generate_source(const mf_process &p, int precision, int block, int ht, GenInfo &info, const char *ns,
+                            bool kernel) {
     const char *R = precision == MF_FP64 ? "double" : "float";
     const int n = p.n_legs;
     std::ostringstream o;
     std::vector<uint32_t> mask;
-    emit_header(o, p, info, mask, R);
+    emit_header(o, p, info, mask, R, ns);
 
     // --- the program for one helicity
     // momentum into the diagram through the legs of a mask, component q
@@ -332,10 +334,28 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
     }
     fl += 4.0 * nj * (nj - 1) / 2 + 6.0 * nj;
     o << "  return m * R(" << fmt_double(1.0 / p.colour_den) << ");\n}\n";
-    o << "}  // namespace proc\n";
-    o << "#include \"mf_kernel.cuh\"\n";
-    o << "extern \"C\" __global__ void __launch_bounds__(" << block << ") mf_kernel(const mf::KParams kp) {\n"
-      << "  mf::kernel_body<" << R << ", " << block << ", " << ht << ">(kp);\n}\n";
+    // the colour flows alone (the colour sum done by the caller), the colour
+    // matrix's integer numerators and the inverse denominator
+    o << "template <typename R>\n"
+         "MF_DEV void helicity_jamp(const R *__restrict__ ms, const R *__restrict__ idn, const int8_t *hel,\n"
+         "                          const mf::cx<R> *cpl, const R *mass, mf::cx<R> *J) {\n"
+         "  using namespace mf;\n#pragma unroll\n  for (int k = 0; k < NJAMP; ++k) J[k] = C<R>(R(0), R(0));\n";
+    for (int part = 0; part < parts; ++part) o << "  program_part" << part << "<R>(ms, idn, hel, cpl, mass, J);\n";
+    o << "}\n__device__ const int COLOUR_NUM[NJAMP * NJAMP] = {";
+    for (int k = 0; k < nj * nj; ++k) o << (k ? ", " : "") << p.colour_num[k];
+    o << "};\nconstexpr double INV_COLOUR_DEN = " << fmt_double(1.0 / p.colour_den) << ";\n";
+    o << "}  // namespace " << ns << "\n";
+    if (kernel) {
+        o << "#include \"mf_kernel.cuh\"\n";
+        // optional minimum of resident blocks per SM (trades registers for occupancy)
+        int min_blocks = 0;
+        if (const char *e = std::getenv("MF_MIN_BLOCKS")) min_blocks = std::atoi(e);
+        o << "extern \"C\" __global__ void __launch_bounds__(" << block;
+        if (min_blocks >= 1 && min_blocks <= 8) o << ", " << min_blocks;
+        o << ") mf_kernel(const mf::KParams kp) {\n";
+        if (precision == MF_MIXED_TC) o << "  mf::kernel_body_tc<" << ht << ">(kp);\n}\n";
+        else o << "  mf::kernel_body<" << R << ", " << block << ", " << ht << ">(kp);\n}\n";
+    }
     info.flops_per_hel = fl;
     // kinematics per event (phase space, PDFs, denominators), rough count
     info.flops_kin = 400.0 + 10.0 * info.n_den;
@@ -604,6 +624,61 @@ std::string generate_grad_source(const mf_process &p, int block, GenInfo &info) 
     o << "#include \"mf_grad.cuh\"\n";
     o << "extern \"C\" __global__ void __launch_bounds__(" << block << ") mf_grad_kernel(const mf::KParams kp) {\n"
       << "  mf::grad_body<proc::NDIM + 1>(kp);\n}\n";
+    return o.str();
+}
+
+// Several processes in one module: each process's program in its own
+// namespace proc<k> with the tile body instantiated for it in body<k>, and one
+// persistent kernel in which every block takes the next tile of the batch
+// from a global counter (tiles of the costliest process first) and runs it
+// with that process's code.
+std::string generate_batch_source(const std::vector<const mf_process *> &ps, int precision, int block,
+                                  const std::vector<int> &hts, std::vector<GenInfo> &infos) {
+    const char *R = precision == MF_FP64 ? "double" : "float";
+    std::ostringstream o;
+    infos.assign(ps.size(), GenInfo{});
+    int maxdim = 1;
+    for (size_t k = 0; k < ps.size(); ++k) {
+        const std::string ns = "proc" + std::to_string(k);
+        o << generate_source(*ps[k], precision, block, hts[k], infos[k], ns.c_str(), false);
+        o << "#define MF_PROC proc" << k << "\n#define MF_BODY body" << k << "\n#include \"mf_kernel.cuh\"\n";
+        maxdim = std::max(maxdim, ps[k]->ndim);
+    }
+    o << "extern \"C\" __global__ void __launch_bounds__(" << block << ") mf_batch_kernel(const mf_batch_params bp) {\n"
+      << "  extern __shared__ __align__(16) unsigned char smem_raw[];\n"
+      << "  __shared__ double s_grid[" << maxdim * 65 << "];\n"
+      << "  __shared__ mf::cx<" << R << "> cpl[8];\n"
+      << "  __shared__ " << R << " mass_r[8];\n"
+      << "  __shared__ long long s_item;\n"
+      << "  {\n    size_t need = 0;\n";
+    for (size_t k = 0; k < ps.size(); ++k)
+        o << "    if (body" << k << "::tile_smem_bytes<" << R << ", " << block << ">() > need) need = body" << k
+          << "::tile_smem_bytes<" << R << ", " << block << ">();\n";
+    o << "    uint32_t have;\n    asm(\"mov.u32 %0, %%dynamic_smem_size;\" : \"=r\"(have));\n"
+      << "    if (have < need) {\n"
+      << "      if (threadIdx.x == 0) for (int k = 0; k < bp.nproc; ++k) if (bp.kp[k].err) atomicExch(bp.kp[k].err, 2);\n"
+      << "      return;\n    }\n  }\n"
+      << "  int cur = -1;\n"
+      << "  for (;;) {\n"
+      << "    __syncthreads();\n"
+      << "    if (threadIdx.x == 0) s_item = (long long)atomicAdd((unsigned long long *)bp.counter, 1ull);\n"
+      << "    __syncthreads();\n"
+      << "    const long long item = s_item;\n"
+      << "    if (item >= bp.start[bp.nproc]) break;\n"
+      << "    int k = 0;\n"
+      << "    while (k + 1 < bp.nproc && item >= bp.start[k + 1]) ++k;\n"
+      << "    if (k != cur) {\n"
+      << "      switch (k) {\n";
+    for (size_t k = 0; k < ps.size(); ++k)
+        o << "        case " << k << ": body" << k << "::load_block_constants<" << R << ", " << block
+          << ">(bp.kp[" << k << "], s_grid, cpl, mass_r); break;\n";
+    o << "      }\n      __syncthreads();\n      cur = k;\n    }\n"
+      << "    const long long tile = item - bp.start[k];\n"
+      << "    switch (k) {\n";
+    for (size_t k = 0; k < ps.size(); ++k)
+        o << "      case " << k << ": body" << k << "::tile_body<" << R << ", " << block << ", " << hts[k]
+          << ">(bp.kp[" << k << "], tile, smem_raw, s_grid, cpl, mass_r); break;\n";
+    o << "    }\n  }\n}\n";
     return o.str();
 }
 

@@ -69,8 +69,9 @@ struct mf_process {
     double *d_pdf_rows = nullptr;  // device [2][2][nx]
     double ln_tau_min = 0.0, w0_const = 0.0, pref_const = 0.0;
     mfi::GenInfo gen;
-    mfi::Compiled kern[3];         // per mf_precision, and [2] the gradient kernel
-    std::string source[3];
+    mfi::Compiled kern[4];         // per mf_precision, and [2] the gradient kernel
+    std::string source[4];
+    int *d_err = nullptr;          // device error flag of the process kernels
     // events around the last process-kernel launch of mf_vegas_iterate
     cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
     double last_kernel_ms = 0.0;
@@ -78,6 +79,7 @@ struct mf_process {
     double *d_w = nullptr;
     uint8_t *d_bins = nullptr;
     int64_t scratch_n = 0;
+    int64_t last_n = 0;            // points of the last Vegas pass held in d_w
 };
 
 struct mf_vegas {
@@ -98,9 +100,30 @@ struct mf_vegas {
     double *d_tot = nullptr;       // [K] combined totals of a sharded iteration
 };
 
+// Several processes compiled into one persistent kernel (mf_batch_create).
+struct mf_batch {
+    int device = 0;
+    int precision = 0;
+    std::vector<mf_process *> procs;   // caller's order
+    std::vector<int> order;            // batch slot -> caller's index, costliest first
+    mfi::Compiled kern;
+    std::string source;
+    long long *d_counter = nullptr;    // tile counter of the persistent kernel
+    cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
+    double last_kernel_ms = 0.0;
+};
+
+struct mf_lhe_writer;
+
 namespace mfi {
+// the event writer (mf_lhe.cpp)
+mf_status lhe_push(mf_lhe_writer *w, std::vector<double> &&records);
+int lhe_legs(const mf_lhe_writer *w);
 // code generation (mf_codegen.cpp)
-std::string generate_source(const mf_process &p, int precision, int block, int ht, GenInfo &info);
+std::string generate_source(const mf_process &p, int precision, int block, int ht, GenInfo &info,
+                            const char *ns = "proc", bool kernel = true);
+std::string generate_batch_source(const std::vector<const mf_process *> &ps, int precision, int block,
+                                  const std::vector<int> &hts, std::vector<GenInfo> &infos);
 std::string generate_grad_source(const mf_process &p, int block, GenInfo &info);
 // run-time compilation (mf_jit.cpp)
 mf_status jit_compile(const std::string &source, const std::string &name, std::vector<char> &cubin);

@@ -52,7 +52,7 @@ def test_struct_layouts_match_the_c_compiler(built, tmp_path):
     # the header, against the ctypes mirror used by the binding
     structs = {"mf_op": built.mf_op, "mf_colour_term": built.mf_colour_term,
                "mf_process_desc": built.mf_process_desc, "mf_process_info": built.mf_process_info,
-               "mf_iter_result": built.mf_iter_result}
+               "mf_iter_result": built.mf_iter_result, "mf_lhe_init": built.mf_lhe_init}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "madflow_gb.h"', "int main(void) {"]
     for sname, cls in structs.items():
         lines.append(f'printf("{sname} size %zu\\n", sizeof({sname}));')
@@ -153,3 +153,16 @@ def test_gradient_kernels_compile_for_sm103a(built, name):
     from paper_2106_10279_gb300 import api
     src = api.mf_generate_kernel_source(_desc(name), "grad", compile=True)
     assert "mf_grad_kernel" in src and "helicity_grad" in src
+
+
+def test_batched_kernel_of_the_mixed_batch_compiles(built):
+    # the five subprocesses of the mixed batch in one module, costliest first
+    from paper_2106_10279_gb300 import api
+    names = ["gg_ttxgg", "gg_ttxg", "uux_ttxg", "gg_ttx", "uux_ttx"]
+    src = api.mf_generate_batch_source([_desc(n) for n in names], "mixed", compile=True)
+    assert "mf_batch_kernel" in src
+    for k in range(5):
+        assert f"namespace proc{k}" in src and f"body{k}::tile_body" in src
+    from paper_2106_10279_gb300 import _lib as L
+    with pytest.raises(L.MfError):
+        api.mf_generate_batch_source([_desc("gg_ttx")] * 9, "mixed")

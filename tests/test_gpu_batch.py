@@ -1,0 +1,69 @@
+"""The batched persistent kernel (mf_batch_*) against per-subprocess
+mf_vegas_iterate on the mixed batch of five subprocesses (sizes scaled down
+1:100): same points, so per subprocess the same non-zero counts and bin
+counts, and estimates, errors, histograms and refined grids within 1e-12
+relative (the two kernels are compiled separately, so contraction of
+multiply-adds may differ), over two iterations; the batch runs the costliest
+subprocess's tiles first."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+SCALE = 100
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2106_10279_gb300 import api
+    procs = {name: api.Process.from_workload(W.WORKLOADS[name]) for name, _ in W.MIXED_BATCH}
+    return api, procs
+
+
+@pytest.mark.parametrize("prec,rel", [("fp64", 1e-12), ("mixed", 1e-12)])
+def test_batch_matches_separate_iterations(env, prec, rel):
+    api, procs = env
+    names = [name for name, _ in W.MIXED_BATCH]
+    n = [max(4096, nev // SCALE) + 17 for _, nev in W.MIXED_BATCH]      # ragged chunk tails
+    plist = [procs[k] for k in names]
+    batch = api.Batch(plist, prec)
+    order = batch.info()["order"]
+    assert names[order[0]] == "gg_ttxgg"
+    g_ref = [api.Vegas(procs[k].ndim) for k in names]
+    g_bat = [api.Vegas(procs[k].ndim) for k in names]
+    for it in range(2):
+        r_ref = api.mf_vegas_iterate([g.handle for g in g_ref], [p.handle for p in plist], n, 9, prec)
+        r_bat = batch.iterate(g_bat, n, 9)
+        for k, name in enumerate(names):
+            a, b = r_ref[k], r_bat[k]
+            for key in ("iteration", "n_events", "n_nonzero", "n_nan"):
+                assert a[key] == b[key], (name, it, key)
+            for key in ("integral", "error", "sigma", "sigma_error"):
+                assert abs(a[key] - b[key]) <= rel * abs(a[key]), (name, it, key, a[key], b[key])
+            h1, c1 = g_ref[k].histogram()
+            h2, c2 = g_bat[k].histogram()
+            assert np.array_equal(c1, c2)
+            assert np.allclose(h1, h2, rtol=rel, atol=0)
+            assert np.allclose(g_ref[k].grid, g_bat[k].grid, rtol=rel, atol=1e-15)
+    assert batch.info()["last_kernel_ms"] > 0
+
+
+def test_batch_rejects_bad_input(env):
+    api, procs = env
+    from paper_2106_10279_gb300 import _lib as L
+    p = procs["gg_ttx"]
+    with pytest.raises(L.MfError):
+        api.Batch([p, p])
+    b = api.Batch([p, procs["uux_ttx"]], "fp64")
+    g = api.Vegas(p.ndim)
+    with pytest.raises(L.MfError):
+        b.iterate([g, g], [10000, 10000], 1)                 # one grid twice
+    with pytest.raises(L.MfError):
+        b.iterate([g, api.Vegas(7)], [10000, 10000], 1)      # dimensions differ
