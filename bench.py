@@ -262,6 +262,25 @@ def run_native(args):
         t_e2e = float(t.item())
     e2e_value = world * n_events * args.steps / t_e2e
 
+    # variants of the same kernel on a sample of the workload: the colour sum
+    # on the tensor cores, and one sampled helicity per point (a different,
+    # unbiased estimator with more variance: reported with its error)
+    variants = {}
+    if not args.no_batch:
+        nv = min(n_events, 2_000_000)
+        gv = api.Vegas(wl.ndim, wl.n_bins, wl.alpha_vegas)
+        gv.load(start_state)
+        for tag, prec, sample in (("mixed", "mixed", False), ("mixed_tc", "mixed_tc", False),
+                                  ("mixed_helicity_sampling", "mixed", True)):
+            proc.set_helicity_sampling(sample, seed=5)
+            api.mf_vegas_iterate([gv.handle], [proc.handle], [nv], seed, prec, False, stream)
+            torch.cuda.synchronize()
+            r = api.mf_vegas_iterate([gv.handle], [proc.handle], [nv], seed, prec, False, stream)[0]
+            kms_v = api.mf_process_last_kernel_ms(proc.handle)
+            variants[tag] = {"events": nv, "kernel_ms": kms_v, "events_per_s": nv / (kms_v / 1e3),
+                             "integral_pb": r["integral"], "error_pb": r["error"]}
+        proc.set_helicity_sampling(False)
+
     # the mixed batch of five subprocesses (gg->tt~, uu~->tt~, gg->tt~g,
     # uu~->tt~g, gg->tt~gg; 4e7 points per iteration in all), each with its own
     # grid: one persistent launch per iteration against one launch per
@@ -328,6 +347,7 @@ def run_native(args):
                          f"{n_events * (8 + wl.ndim) / 1e6:.0f} MB > 129 MB L2"},
         "fp64": {"value": fp64_rate, "unit": "events/s", "events": n64},
         "batch": batch,
+        "kernel_variants": variants,
         "accuracy": {"median_rel_mixed_vs_fp64": float(np.median(rel)), "max_rel_mixed_vs_fp64": float(rel.max()),
                      "points": int(nz.sum())},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",

@@ -142,7 +142,8 @@ typedef struct {
     const int32_t *colour_num;      /* host [n_jamp * n_jamp] */
     int32_t colour_den;
     /* helicities: n_hel rows of n_legs values +-1 (NULL: all 2^n_legs); rows
-       that vanish identically are dropped at create time */
+       that vanish are dropped at create time (below 1e-12 of the helicity
+       sum at each of 256 seeded points: chirality zeros are rounding residues) */
     int32_t n_hel;
     const int8_t *helicities;
     double average;                 /* 1/(initial spins x colours) x identical-final factor */
@@ -426,6 +427,20 @@ mf_status mf_vegas_iterate_static(mf_vegas *v, mf_process *p, int64_t n_events, 
  * size, edges) and restores it into a grid of the same ndim and nbins. */
 mf_status mf_vegas_save(const mf_vegas *v, void *buf, size_t *len);
 mf_status mf_vegas_load(mf_vegas *v, const void *buf, size_t len);
+
+/* Helicity sampling (the Monte Carlo over helicities that Sec. 4 names as a
+ * way to cut the cost per point): with on != 0 the integrand kernels of this
+ * process evaluate one helicity per point, drawn uniformly from the
+ * non-vanishing helicities with the first unit number of Philox counter
+ * (i, iteration, subprocess, 14) (Vegas passes: their key; given points:
+ * counter (i, 0, 0, 14) with key (seed, 0)), and multiply its |M|^2 by their
+ * number: an unbiased estimate of the helicity sum with a larger variance.
+ * mf_helicity_msq and mf_grad always sum over helicities. */
+mf_status mf_process_set_helicity_sampling(mf_process *p, int32_t on, uint64_t seed);
+/* The non-vanishing helicity assignments kept at creation, in the order the
+ * sampling indexes them (host [n_hel][n_legs], +1/-1; may be NULL to query
+ * *n_hel). */
+mf_status mf_process_get_helicities(const mf_process *p, int8_t *hel, int32_t *n_hel);
 
 /* mf_process_check: whether a kernel of this process flagged an error: a
  * bounded wait expired (the tensor-core colour sum waits on the completion

@@ -132,6 +132,52 @@ class Integrand:
         return f
 
     # ------------------------------------------------------------------
+    # helicity sampling: one helicity per point, uniform over a list of
+    # non-vanishing helicities, |M_h|^2 scaled by the list's length (an
+    # unbiased estimate of the helicity sum)
+    def nonzero_helicities(self, n_points: int = 64, seed: int = 99):
+        """Helicity assignments (in the oracle's order) whose |M|^2 does not
+        vanish, judged on seeded random points passing the cuts; an
+        assignment vanishes when it stays below 1e-12 of the helicity sum at
+        every point (the explicit-matrix products leave rounding residues,
+        ~1e-16 of the sum, where chirality makes an amplitude zero)."""
+        rng = np.random.default_rng(seed)
+        x = rng.random((self.wl.ndim, 4 * n_points))
+        p, s_hat, x1, x2, jx, w, ok = self.kinematics(x)
+        keep = ok & self.cuts(p)
+        tot, per = self.proc.msq_summed(p[keep][:n_points], per_helicity=True)
+        hels = self.proc.helicities()
+        return [hels[h] for h in range(len(hels)) if np.any(np.abs(per[h]) > 1e-12 * tot)]
+
+    def sampled(self, x, seed: int, helicities, pick=None):
+        """f with the helicity of point i drawn from the first unit number of
+        Philox counter (i, 0, 0, 14), key (seed, 0) (or given by pick)."""
+        from oracle.philox import philox4x64_10, to_unit
+        x = np.asarray(x, dtype=np.float64)
+        N = x.shape[1]
+        nh = len(helicities)
+        if pick is None:
+            ctr = np.zeros((N, 4), dtype=np.uint64)
+            ctr[:, 0] = np.arange(N, dtype=np.uint64)
+            ctr[:, 3] = np.uint64(14)
+            u = to_unit(philox4x64_10(ctr, np.array([seed, 0], dtype=np.uint64))[:, 0])
+            pick = np.minimum((u * nh).astype(np.int64), nh - 1)
+        p, s_hat, x1, x2, jx, w, ok = self.kinematics(x)
+        keep = ok & self.cuts(p)
+        f = np.zeros(N)
+        idx = np.nonzero(keep)[0]
+        if len(idx):
+            order = {h: k for k, h in enumerate(self.proc.helicities())}
+            _, per = self.proc.msq_summed(p[idx], per_helicity=True)
+            rows = np.array([order[tuple(helicities[k])] for k in pick[idx]])
+            msq = nh * per[rows, np.arange(len(idx))] * self.proc.average_factor()
+            lum = np.ones(len(idx))
+            if self.wl.beams:
+                lum = (self.pdfs[0].f(x1[idx], self.wl.mu_f2) * self.pdfs[1].f(x2[idx], self.wl.mu_f2))
+            f[idx] = jx[idx] * w[idx] * lum * msq / (2.0 * s_hat[idx]) * W.GEV2_TO_PB
+        return f, pick
+
+    # ------------------------------------------------------------------
     # condition numbers: how far two correct evaluations of f in different
     # operation orders can drift apart, in units of eps
     def _pdf_condition(self, x1, x2):

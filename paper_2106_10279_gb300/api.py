@@ -373,6 +373,20 @@ class Process:
         mf_integrand(self.handle, x, n, f, precision, stream)
         return f
 
+    def set_helicity_sampling(self, on=True, seed=0):
+        """One uniformly drawn helicity per point instead of the sum (unbiased)."""
+        L.check(L.lib().mf_process_set_helicity_sampling(self.handle, 1 if on else 0, seed),
+                "mf_process_set_helicity_sampling")
+
+    def helicities(self):
+        """The non-vanishing helicity assignments, int8 [n_hel, n_legs]."""
+        n = C.c_int32()
+        L.check(L.lib().mf_process_get_helicities(self.handle, None, C.byref(n)), "mf_process_get_helicities")
+        out = np.zeros((n.value, self.info["n_legs"]), dtype=np.int8)
+        L.check(L.lib().mf_process_get_helicities(self.handle, out.ctypes.data_as(C.POINTER(C.c_int8)),
+                                                  C.byref(n)), "mf_process_get_helicities")
+        return out
+
     def check(self):
         """Raise if a bounded wait of one of this process's kernels expired."""
         L.check(L.lib().mf_process_check(self.handle), "mf_process_check")

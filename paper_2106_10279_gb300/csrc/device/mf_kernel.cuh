@@ -228,6 +228,17 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
                 }
                 ok = false;            // no helicity work for records
             }
+            if (ok && kp.hel_sample) {
+                // helicity sampling: one helicity per point, uniform over the
+                // non-vanishing ones, from Philox block 14 of the point's counter
+                uint64_t c[4] = {kp.mode == 0 ? (uint64_t)e
+                                 : (kp.mode == 3 ? (uint64_t)kp.idx[e] : (uint64_t)(e + kp.ev0)),
+                                 kp.mode == 0 ? 0ull : kp.iteration, kp.mode == 0 ? 0ull : kp.subprocess, 14ull};
+                philox4x64_10(c, kp.seed, 0ull);
+                int h = (int)(unit_from_bits(c[0]) * kp.nhel);
+                if (h >= kp.nhel) h = kp.nhel - 1;
+                s_msq[tid] = (double)h;
+            }
             if (ok) {
                 pref = ev.pref;
                 R *sd = s_den + tid * NDEN1;
@@ -256,6 +267,25 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
         __syncthreads();
         // ---------------- phase B: helicity amplitudes, HT lanes per event
         {
+            if (kp.hel_sample) {
+                // one lane per passing point (npass <= BLOCK: a single round),
+                // its sampled helicity, |M_h|^2 scaled by the helicity count
+                const bool valid = tid < npass;
+                const int ev = s_list[valid ? tid : 0];
+                const int h = valid ? (int)s_msq[ev] : 0;
+                const R *ms = s_mom + ev * NLEG * 4;
+                const R *idn = s_den + ev * NDEN1;
+                double v;
+                if constexpr (TC) {
+                    cx<float> J[NJAMP];
+                    helicity_jamp<float>(ms, idn, kp.hel[h], cpl, mass_r, J);
+                    v = (double)(tc::colour_sum<NJAMP>(*tcs, J) * (float)INV_COLOUR_DEN);
+                } else {
+                    v = (double)helicity_msq<R>(ms, idn, kp.hel[h], cpl, mass_r);
+                }
+                __syncthreads();        // every lane has read its helicity index
+                if (valid) s_msq[ev] = v * (double)kp.nhel;
+            } else {
             constexpr int EPR = BLOCK / HT;     // events per round
             const int sub = tid % HT;
             const int nhp = kp.nhel_pow2;       // padded helicity count (power of two)
@@ -294,6 +324,7 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
                     part = (sub & off) ? (o + part) : (part + o);
                 }
                 if (sub == 0 && slot < npass) s_msq[s_list[slot]] = part;
+            }
             }
         }
         __syncthreads();

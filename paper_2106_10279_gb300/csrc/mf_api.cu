@@ -425,6 +425,8 @@ void fill_common(const mf_process &p, mf_kparams &kp) {
     kp.alpha_s = p.alpha_s;
     kp.alpha_s_power = p.alpha_s_power;
     kp.err = p.d_err;
+    kp.hel_sample = p.hel_sample;
+    kp.seed = p.hel_seed;          // Vegas passes overwrite it with their own key
 }
 
 bool valid_prec(int prec) { return prec == MF_FP64 || prec == MF_MIXED || prec == MF_MIXED_TC; }
@@ -695,11 +697,17 @@ extern "C" mf_status mf_create_process(const mf_process_desc *d, mf_process **ou
             mf_destroy_process(p);
             return st != MF_OK ? st : fail(MF_ECUDA, std::string("helicity filter run failed: ") + cudaGetErrorString(e));
         }
+        // a helicity vanishes when it stays below 1e-12 of the helicity sum at
+        // every test point: amplitudes that chirality makes zero come out as
+        // rounding residues (~1e-16 of the sum), physical ones far above
+        std::vector<double> tot(npts, 0.0);
+        for (int h = 0; h < nh; ++h)
+            for (int i = 0; i < npts; ++i) tot[i] += std::fabs(hf[(size_t)h * npts + i]);
         bool any = false;
-        for (double v : hf) any |= (v != 0.0);
+        for (double v : tot) any |= (v > 0.0);
         for (int h = 0; h < nh; ++h) {
             bool keep = !any;
-            for (int i = 0; i < npts && !keep; ++i) keep = hf[(size_t)h * npts + i] != 0.0;
+            for (int i = 0; i < npts && !keep; ++i) keep = std::fabs(hf[(size_t)h * npts + i]) > 1e-12 * tot[i];
             if (keep)
                 for (int l = 0; l < n; ++l) p->hel.push_back(p->hel_all[(size_t)h * n + l]);
         }
@@ -814,6 +822,20 @@ extern "C" mf_status mf_process_last_kernel_ms(const mf_process *p, double *ms) 
     return MF_OK;
 }
 
+extern "C" mf_status mf_process_set_helicity_sampling(mf_process *p, int32_t on, uint64_t seed) {
+    if (!p) return fail(MF_EINVAL, "NULL process");
+    p->hel_sample = on ? 1 : 0;
+    p->hel_seed = seed;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_process_get_helicities(const mf_process *p, int8_t *hel, int32_t *n_hel) {
+    if (!p || !n_hel) return fail(MF_EINVAL, "NULL argument");
+    *n_hel = (int32_t)(p->hel.size() / p->n_legs);
+    if (hel) std::copy(p->hel.begin(), p->hel.end(), hel);
+    return MF_OK;
+}
+
 extern "C" mf_status mf_process_check(mf_process *p) {
     if (!p) return fail(MF_EINVAL, "NULL process");
     int flag = 0;
@@ -854,6 +876,7 @@ extern "C" mf_status mf_helicity_msq(mf_process *p, const double *x, int64_t n, 
     fill_common(*p, kp);
     set_hel(kp, p->hel_all, p->n_legs);
     kp.mode = 2;
+    kp.hel_sample = 0;
     kp.n = n;
     kp.x = x;
     kp.f = out;

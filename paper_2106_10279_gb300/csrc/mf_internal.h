@@ -80,6 +80,8 @@ struct mf_process {
     uint8_t *d_bins = nullptr;
     int64_t scratch_n = 0;
     int64_t last_n = 0;            // points of the last Vegas pass held in d_w
+    int hel_sample = 0;            // one sampled helicity per point
+    uint64_t hel_seed = 0;         // Philox key of the sampling of given points
 };
 
 struct mf_vegas {

@@ -1,0 +1,64 @@
+"""Helicity sampling on the GPU (one uniformly drawn helicity per point,
+scaled by the helicity count) against the oracle's restatement on the same
+points and draws, and a sampled Vegas iteration against the full sum within
+the combined Monte Carlo errors."""
+import numpy as np
+import pytest
+
+import workloads as W
+from _tolerance import fp64_tolerance, relerr
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2106_10279_gb300 import api
+    return torch, api
+
+
+@pytest.mark.parametrize("name,n", [("gg_ttx", 1500), ("uux_ttxg", 400), ("gg_ttxg", 500)])
+def test_sampled_integrand_matches_the_oracle(env, oracle_processes, name, n):
+    torch, api = env
+    from oracle.integrand import Integrand
+    wl = W.WORKLOADS[name]
+    I = Integrand(wl, process=oracle_processes(name))
+    hels = I.nonzero_helicities()
+    proc = api.Process.from_workload(wl)
+    assert np.array_equal(proc.helicities(), np.array(hels, dtype=np.int8))
+    proc.set_helicity_sampling(True, seed=77)
+    x = W.uniform_points(wl.ndim, n, 404)
+    xd = torch.from_numpy(x).cuda()
+    got = proc.integrand(xd, "fp64").cpu().numpy()
+    ref, pick = I.sampled(x, 77, hels)
+    _, tol = fp64_tolerance(I, x)
+    assert np.array_equal(got == 0, ref == 0)
+    r = relerr(got, ref)
+    assert np.all(r <= tol), (r.max(), int(np.argmax(r / tol)))
+    mixed = proc.integrand(xd, "mixed").cpu().numpy()
+    rm = relerr(mixed, ref)[ref != 0]
+    assert np.median(rm) <= 1e-5 and rm.max() <= 1e-3
+    # switching it off restores the full helicity sum
+    proc.set_helicity_sampling(False)
+    full = proc.integrand(xd, "fp64").cpu().numpy()
+    ref_full, tol_full = fp64_tolerance(I, x)
+    assert np.all(relerr(full, ref_full) <= tol_full)
+
+
+def test_sampled_vegas_iteration_is_consistent(env):
+    torch, api = env
+    wl = W.GG_TTXG
+    proc = api.Process.from_workload(wl)
+    g_full, g_samp = api.Vegas(wl.ndim), api.Vegas(wl.ndim)
+    r_full = g_full.iterate(proc, 400_000, 5, "mixed")
+    proc.set_helicity_sampling(True, seed=1)
+    r_samp = g_samp.iterate(proc, 400_000, 5, "mixed")
+    assert r_samp["n_nonzero"] == r_full["n_nonzero"]          # same points pass the cuts
+    d = abs(r_samp["integral"] - r_full["integral"])
+    assert d < 5 * np.hypot(r_samp["error"], r_full["error"])
+    assert r_samp["error"] > r_full["error"]                  # sampling adds variance

@@ -143,3 +143,31 @@ def test_vegas_histogram_counts_sum_to_events():
     res = vegas.run(lambda x: x[0] + x[1], ndim=2, n_events=5000, n_iter=2, seed=9, nbins=10)
     for dsum, cnt, grid in res["hist"]:
         assert np.all(cnt.sum(axis=1) == 5000)
+
+
+def test_helicity_sampling_is_unbiased(oracle_processes):
+    # averaging the sampled integrand over the helicity choice gives the full
+    # helicity sum exactly; over random seeds, within the sampling spread
+    import workloads as W
+    from oracle.integrand import Integrand
+    wl = W.GG_TTX
+    I = Integrand(wl, process=oracle_processes("gg_ttx"))
+    hels = I.nonzero_helicities()
+    # gg -> tt~: the four assignments with equal gluon helicities and opposite
+    # top helicities vanish
+    assert len(hels) == 12
+    assert all(not (h[0] == h[1] and h[2] != h[3]) for h in hels)
+    # massless e+e- -> mu+mu- through a photon: 4 of 16 survive (chirality)
+    assert len(Integrand(W.EE_MUMU, process=oracle_processes("ee_mumu")).nonzero_helicities()) == 4
+    x = W.uniform_points(wl.ndim, 40, 5)
+    full = I(x)
+    # every helicity choice in turn: their mean is the full sum
+    nh = len(hels)
+    mean = sum(I.sampled(x, 0, hels, pick=np.full(40, h))[0] for h in range(nh)) / nh
+    nz = full != 0
+    assert np.all((mean == 0) == (full == 0))
+    assert np.max(np.abs(mean[nz] / full[nz] - 1)) < 1e-13
+    # the Philox choice is uniform over the list
+    _, pick = I.sampled(W.uniform_points(wl.ndim, 4000, 6), 3, hels)
+    counts = np.bincount(pick, minlength=nh)
+    assert counts.sum() == 4000 and np.all(np.abs(counts - 4000 / nh) < 5 * np.sqrt(4000 / nh))
