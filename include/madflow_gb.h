@@ -437,6 +437,13 @@ mf_status mf_vegas_load(mf_vegas *v, const void *buf, size_t len);
  * number: an unbiased estimate of the helicity sum with a larger variance.
  * mf_helicity_msq and mf_grad always sum over helicities. */
 mf_status mf_process_set_helicity_sampling(mf_process *p, int32_t on, uint64_t seed);
+/* Leading-colour approximation (the other cut of the cost per point that
+ * Sec. 4 names): with on != 0 the integrand kernels keep only the diagonal
+ * of the colour matrix in the colour-flow basis, sum_k C_kk |J_k|^2 / den,
+ * i.e. the leading term in 1/N_c.  The kernels are regenerated on their next
+ * use (synchronises the device); mf_helicity_msq follows the setting,
+ * mf_grad and batches created earlier do not. */
+mf_status mf_process_set_leading_colour(mf_process *p, int32_t on);
 /* The non-vanishing helicity assignments kept at creation, in the order the
  * sampling indexes them (host [n_hel][n_legs], +1/-1; may be NULL to query
  * *n_hel). */

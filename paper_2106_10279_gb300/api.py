@@ -378,6 +378,10 @@ class Process:
         L.check(L.lib().mf_process_set_helicity_sampling(self.handle, 1 if on else 0, seed),
                 "mf_process_set_helicity_sampling")
 
+    def set_leading_colour(self, on=True):
+        """Keep only the diagonal of the colour matrix (leading colour)."""
+        L.check(L.lib().mf_process_set_leading_colour(self.handle, 1 if on else 0), "mf_process_set_leading_colour")
+
     def helicities(self):
         """The non-vanishing helicity assignments, int8 [n_hel, n_legs]."""
         n = C.c_int32()

@@ -162,6 +162,25 @@ MF_DEV void load_block_constants(const KParams &kp, double *s_grid, cx<R> *cpl, 
     }
 }
 
+// Colour-summed |M|^2 of one helicity: the colour flows of the program, then
+// the full colour sum (FMA units, or the tensor cores with TC) or, for a
+// process generated with the leading-colour approximation, only the diagonal
+// of the colour matrix.  With TC every thread of the block must call it the
+// same number of times.
+template <typename R, bool TC>
+MF_DEV double helicity_value(const KParams &kp, const R *ms, const R *idn, const int8_t *hel, const cx<R> *cpl,
+                             const R *mass_r, tc::State *tcs) {
+    using namespace MF_PROC;
+    if constexpr (LEADING_COLOUR || TC) {
+        cx<R> J[NJAMP];
+        helicity_jamp<R>(ms, idn, hel, cpl, mass_r, J);
+        if constexpr (LEADING_COLOUR) return (double)colour_sum_lc<R>(J);
+        else return (double)(tc::colour_sum<NJAMP>(*tcs, J) * (float)INV_COLOUR_DEN);
+    } else {
+        return (double)helicity_msq<R>(ms, idn, hel, cpl, mass_r);
+    }
+}
+
 // One tile of BLOCK events: phases A, B and C.  Ends with a block barrier.
 // With TC the colour sum of phase B runs on the tensor cores (R = float,
 // BLOCK = 128, tcs set up by the caller).
@@ -267,64 +286,46 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
         __syncthreads();
         // ---------------- phase B: helicity amplitudes, HT lanes per event
         {
-            if (kp.hel_sample) {
-                // one lane per passing point (npass <= BLOCK: a single round),
-                // its sampled helicity, |M_h|^2 scaled by the helicity count
-                const bool valid = tid < npass;
-                const int ev = s_list[valid ? tid : 0];
-                const int h = valid ? (int)s_msq[ev] : 0;
-                const R *ms = s_mom + ev * NLEG * 4;
-                const R *idn = s_den + ev * NDEN1;
-                double v;
-                if constexpr (TC) {
-                    cx<float> J[NJAMP];
-                    helicity_jamp<float>(ms, idn, kp.hel[h], cpl, mass_r, J);
-                    v = (double)(tc::colour_sum<NJAMP>(*tcs, J) * (float)INV_COLOUR_DEN);
-                } else {
-                    v = (double)helicity_msq<R>(ms, idn, kp.hel[h], cpl, mass_r);
-                }
-                __syncthreads();        // every lane has read its helicity index
-                if (valid) s_msq[ev] = v * (double)kp.nhel;
-            } else {
-            constexpr int EPR = BLOCK / HT;     // events per round
-            const int sub = tid % HT;
+            // HT lanes per point, each running the program for a contiguous
+            // block of helicities; with helicity sampling one lane per point
+            // and its sampled helicity (one call site of the program either way)
+            const bool samp = kp.hel_sample != 0;
+            const int EPR = samp ? BLOCK : BLOCK / HT;  // points per round
+            const int sub = samp ? 0 : tid % HT;
             const int nhp = kp.nhel_pow2;       // padded helicity count (power of two)
-            const int per = nhp >= HT ? nhp / HT : 1;   // contiguous helicities per lane
+            const int per = samp ? 1 : (nhp >= HT ? nhp / HT : 1);   // helicities per lane
             // every thread runs the program the same number of times (lanes
             // without an event or a helicity compute on a valid stand-in and
             // discard it), so that the program may contain block barriers
             for (int base = 0; base < npass; base += EPR) {
-                const int slot = base + tid / HT;
+                const int slot = base + (samp ? tid : tid / HT);
                 const bool valid = slot < npass;
                 PairSum ps;
                 ps.init();
                 const int ev = s_list[valid ? slot : 0];
+                const int hs = (samp && valid) ? (int)s_msq[ev] : 0;
                 const R *ms = s_mom + ev * NLEG * 4;
                 const R *idn = s_den + ev * NDEN1;
                 for (int k = 0; k < per; ++k) {
-                    const int h = sub * per + k;
+                    const int h = samp ? hs : sub * per + k;
                     const bool hv = h < kp.nhel;
-                    double v;
-                    if constexpr (TC) {
-                        cx<float> J[NJAMP];
-                        helicity_jamp<float>(ms, idn, kp.hel[hv ? h : 0], cpl, mass_r, J);
-                        v = (double)(tc::colour_sum<NJAMP>(*tcs, J) * (float)INV_COLOUR_DEN);
-                    } else {
-                        v = (double)helicity_msq<R>(ms, idn, kp.hel[hv ? h : 0], cpl, mass_r);
-                    }
+                    double v = helicity_value<R, TC>(kp, ms, idn, kp.hel[hv ? h : 0], cpl, mass_r, tcs);
                     if (!(hv && valid)) v = 0.0;
                     if (kp.mode == 2 && hv && valid) kp.f[(int64_t)h * kp.n + tile * BLOCK + ev] = v;
                     ps.add(v);
                 }
                 double part = ps.total();
+                if (samp) {
+                    if (valid) s_msq[ev] = part * (double)kp.nhel;
+                } else {
 #pragma unroll
-                for (int off = 1; off < HT; off <<= 1) {
-                    double o = __shfl_xor_sync(0xffffffffu, part, off);
-                    // lanes combine (lower block) + (upper block) in that order
-                    part = (sub & off) ? (o + part) : (part + o);
+                    for (int off = 1; off < HT; off <<= 1) {
+                        double o = __shfl_xor_sync(0xffffffffu, part, off);
+                        // lanes combine (lower block) + (upper block) in that order
+                        part = (sub & off) ? (o + part) : (part + o);
+                    }
+                    if (sub == 0 && slot < npass) s_msq[s_list[slot]] = part;
                 }
-                if (sub == 0 && slot < npass) s_msq[s_list[slot]] = part;
-            }
             }
         }
         __syncthreads();

@@ -829,6 +829,17 @@ extern "C" mf_status mf_process_set_helicity_sampling(mf_process *p, int32_t on,
     return MF_OK;
 }
 
+extern "C" mf_status mf_process_set_leading_colour(mf_process *p, int32_t on) {
+    if (!p) return fail(MF_EINVAL, "NULL process");
+    const int v = on ? 1 : 0;
+    if (v == p->leading_colour) return MF_OK;
+    // the integrand kernels are regenerated on their next use
+    MF_CUDA(cudaDeviceSynchronize());
+    for (int prec : {(int)MF_FP64, (int)MF_MIXED, (int)MF_MIXED_TC}) mfi::unload_kernel(p->kern[prec]);
+    p->leading_colour = v;
+    return MF_OK;
+}
+
 extern "C" mf_status mf_process_get_helicities(const mf_process *p, int8_t *hel, int32_t *n_hel) {
     if (!p || !n_hel) return fail(MF_EINVAL, "NULL argument");
     *n_hel = (int32_t)(p->hel.size() / p->n_legs);

@@ -79,6 +79,7 @@ void emit_header(std::ostringstream &o, const mf_process &p, GenInfo &info, std:
     o << "#include \"mf_common.cuh\"\n#include \"mf_kinematics.cuh\"\n#include \"mf_helas.cuh\"\n";
     o << "#ifndef MF_PROG_SYNC\n#define MF_PROG_SYNC() __syncthreads()\n#endif\n";
     o << "namespace " << ns << " {\n";
+    o << "constexpr bool LEADING_COLOUR = " << (p.leading_colour ? "true" : "false") << ";\n";
     o << "constexpr int NLEG = " << n << ", NOUT = " << p.n_out << ", NDIM = " << p.ndim
       << ", NJAMP = " << p.n_jamp << ", NDEN = " << info.n_den << ", HADRONIC = " << p.hadronic << ";\n";
     o << "__device__ constexpr int LEG_MASS_ID[NLEG] = {";
@@ -313,16 +314,10 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
     }
     o << "#pragma unroll\n  for (int k = 0; k < NJAMP; ++k) Jout[k] = Jout[k] + J[k];\n}\n";
     }
-    o << "template <typename R>\n"
-         "MF_DEV R helicity_msq(const R *__restrict__ ms, const R *__restrict__ idn, const int8_t *hel,\n"
-         "                      const mf::cx<R> *cpl, const R *mass) {\n"
-         "  using namespace mf;\n"
-         "  cx<R> J[NJAMP];\n#pragma unroll\n  for (int k = 0; k < NJAMP; ++k) J[k] = C<R>(R(0), R(0));\n";
-    for (int part = 0; part < parts; ++part) o << "  program_part" << part << "<R>(ms, idn, hel, cpl, mass, J);\n";
     // colour sum  sum_kl Re(conj(J_k) C_kl J_l) / den, C symmetric:
     // sum_k Re(conj(J_k) (C_kk J_k + 2 sum_{l>k} C_kl J_l))
-    o << "  R m = R(0);\n";
     const int nj = p.n_jamp;
+    o << "template <typename R>\nMF_DEV R colour_sum_full(const mf::cx<R> *J) {\n  using namespace mf;\n  R m = R(0);\n";
     for (int k = 0; k < nj; ++k) {
         o << "  { cx<R> z = R(" << p.colour_num[k * nj + k] << ") * J[" << k << "];\n";
         for (int l = k + 1; l < nj; ++l) {
@@ -334,6 +329,19 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
     }
     fl += 4.0 * nj * (nj - 1) / 2 + 6.0 * nj;
     o << "  return m * R(" << fmt_double(1.0 / p.colour_den) << ");\n}\n";
+    // leading colour: the diagonal of the colour matrix in the flow basis
+    o << "template <typename R>\nMF_DEV R colour_sum_lc(const mf::cx<R> *J) {\n  using namespace mf;\n  R m = R(0);\n";
+    for (int k = 0; k < nj; ++k)
+        o << "  m += R(" << p.colour_num[k * nj + k] << ") * (J[" << k << "].re * J[" << k << "].re + J[" << k
+          << "].im * J[" << k << "].im);\n";
+    o << "  return m * R(" << fmt_double(1.0 / p.colour_den) << ");\n}\n";
+    o << "template <typename R>\n"
+         "MF_DEV R helicity_msq(const R *__restrict__ ms, const R *__restrict__ idn, const int8_t *hel,\n"
+         "                      const mf::cx<R> *cpl, const R *mass) {\n"
+         "  using namespace mf;\n"
+         "  cx<R> J[NJAMP];\n#pragma unroll\n  for (int k = 0; k < NJAMP; ++k) J[k] = C<R>(R(0), R(0));\n";
+    for (int part = 0; part < parts; ++part) o << "  program_part" << part << "<R>(ms, idn, hel, cpl, mass, J);\n";
+    o << "  return colour_sum_full<R>(J);\n}\n";
     // the colour flows alone (the colour sum done by the caller), the colour
     // matrix's integer numerators and the inverse denominator
     o << "template <typename R>\n"

@@ -81,6 +81,7 @@ struct mf_process {
     int64_t scratch_n = 0;
     int64_t last_n = 0;            // points of the last Vegas pass held in d_w
     int hel_sample = 0;            // one sampled helicity per point
+    int leading_colour = 0;        // generate the leading-colour approximation
     uint64_t hel_seed = 0;         // Philox key of the sampling of given points
 };
 
