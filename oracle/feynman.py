@@ -349,9 +349,10 @@ class Process:
         out = np.einsum(*ops, list(legs) + [45])
         return legs, out
 
-    def colour_matrix(self):
-        """G[t1, t2] = sum over all external colours of conj(c_t1) c_t2."""
-        if self._G is None:
+    def colour_tensors(self):
+        """C[colours, t]: the colour factor of every term over all external
+        colour assignments (axes in leg order, flattened)."""
+        if getattr(self, "_C", None) is None:
             cols = []
             for t in self.terms:
                 legs, arr = self._colour(t)
@@ -359,9 +360,74 @@ class Process:
                 order = list(legs) + [self.n - 1]
                 arr = np.transpose(arr, np.argsort(order))
                 cols.append(arr.reshape(-1))
-            C = np.stack(cols, axis=1)
+            self._C = np.stack(cols, axis=1)
+        return self._C
+
+    def colour_matrix(self):
+        """G[t1, t2] = sum over all external colours of conj(c_t1) c_t2."""
+        if self._G is None:
+            C = self.colour_tensors()
             self._G = C.conj().T @ C
         return self._G
+
+    # ---------------------------------------------------------------- leading colour
+    def string_basis(self):
+        """Colour strings: every pairing of the row-index quark legs (outgoing
+        quarks, incoming antiquarks) with the column-index legs (incoming
+        quarks, outgoing antiquarks), every distribution of the gluons over the
+        strings and every order along each string; element
+        prod_strings (T^{a_1} ... T^{a_m})_{row, col} over all external
+        colours (axes in leg order, flattened), [colours, basis]."""
+        if getattr(self, "_B", None) is not None:
+            return self._B
+        rows, cols, gluons = [], [], []
+        for i, (part, inc) in enumerate(self.legs):
+            kind, flav, _ = PARTICLES[part]
+            if COLOUR_DIM[flav] == 8:
+                gluons.append(i)
+            elif COLOUR_DIM[flav] == 3:
+                (rows if self.lines[i][2] == "out" else cols).append(i)
+        dims = [self._colour_dim_leg(i) for i in range(self.n)]
+        basis = []
+        for perm in itertools.permutations(cols):
+            for assign in itertools.product(range(len(rows)), repeat=len(gluons)):
+                groups = [[g for g, s in zip(gluons, assign) if s == k] for k in range(len(rows))]
+                for orders in itertools.product(*[list(itertools.permutations(gr)) for gr in groups]):
+                    ops = []
+                    for k, order in enumerate(orders):
+                        r, c = rows[k], perm[k]
+                        if not order:
+                            ops += [np.eye(3), [r, c]]
+                            continue
+                        # chain T^{a_1}_{r x1} T^{a_2}_{x1 x2} ... T^{a_m}_{x_{m-1} c}
+                        # (einsum labels: legs 0..n-1, chain indices from 10)
+                        idx = [r] + [10 + 6 * k + j for j in range(len(order) - 1)] + [c]
+                        for j, g in enumerate(order):
+                            ops += [T_SU3, [g, idx[j], idx[j + 1]]]
+                    out_axes = [i for i in range(self.n) if dims[i] > 1]
+                    arr = np.einsum(*ops, out_axes) if ops else np.ones(())
+                    basis.append(arr.reshape(-1))
+        self._B = np.stack(basis, axis=1) if basis else np.ones((1, 1))
+        return self._B
+
+    def msq_leading_colour(self, p):
+        """sum over helicities of sum_s G_ss |A_s|^2 (no averaging), with A the
+        exact coefficients of the colour-dressed amplitude in the string basis
+        and G_ss the basis elements' squared norms, [N]."""
+        p = np.asarray(p, dtype=np.float64)
+        B = self.string_basis()
+        C = self.colour_tensors()
+        P = np.linalg.pinv(B) @ C                      # terms -> string coefficients
+        if np.max(np.abs(B @ P - C)) > 1e-12 * np.max(np.abs(C)):
+            raise RuntimeError("colour factors outside the string basis")
+        norms = np.real(np.sum(np.conj(B) * B, axis=0))
+        cache = {}
+        tot = np.zeros(p.shape[0])
+        for hel in self.helicities():
+            a = self.amplitudes(p, hel, cache)          # [T, N]
+            A = P @ a                                   # [basis, N]
+            tot += np.einsum("s,sn->n", norms, np.abs(A) ** 2)
+        return tot
 
     # ---------------------------------------------------------------- kinematics
     def _sign(self, leg):

@@ -132,6 +132,23 @@ class Integrand:
         return f
 
     # ------------------------------------------------------------------
+    # leading colour: the diagonal of the colour matrix in the string basis
+    def leading_colour(self, x):
+        x = np.asarray(x, dtype=np.float64)
+        N = x.shape[1]
+        p, s_hat, x1, x2, jx, w, ok = self.kinematics(x)
+        keep = ok & self.cuts(p)
+        f = np.zeros(N)
+        idx = np.nonzero(keep)[0]
+        if len(idx):
+            msq = self.proc.msq_leading_colour(p[idx]) * self.proc.average_factor()
+            lum = np.ones(len(idx))
+            if self.wl.beams:
+                lum = (self.pdfs[0].f(x1[idx], self.wl.mu_f2) * self.pdfs[1].f(x2[idx], self.wl.mu_f2))
+            f[idx] = jx[idx] * w[idx] * lum * msq / (2.0 * s_hat[idx]) * W.GEV2_TO_PB
+        return f
+
+    # ------------------------------------------------------------------
     # helicity sampling: one helicity per point, uniform over a list of
     # non-vanishing helicities, |M_h|^2 scaled by the list's length (an
     # unbiased estimate of the helicity sum)

@@ -89,3 +89,31 @@ def test_vegas_iteration_with_tensor_core_colour_sum(env):
     ra = a.iterate(proc, 100_000, 8, "mixed_tc")
     rb = b.iterate(proc, 100_000, 8, "mixed")
     assert abs(ra["sigma"] / rb["sigma"] - 1) < 1e-4
+
+
+@pytest.mark.parametrize("name,n", [("gg_ttx", 800), ("uux_ttx", 800), ("uux_ttxg", 300), ("gg_ttxg", 300)])
+def test_leading_colour_matches_the_oracle(env, oracle_processes, name, n):
+    # the diagonal of the colour matrix in the colour-flow (string) basis, on
+    # both sides; turning it off restores the full colour sum
+    torch, L, api = env
+    from oracle.integrand import Integrand
+    from _tolerance import fp64_tolerance, relerr
+    wl = W.WORKLOADS[name]
+    I = Integrand(wl, process=oracle_processes(name))
+    proc = api.Process.from_workload(wl)
+    x = W.uniform_points(wl.ndim, n, 505)
+    xd = torch.from_numpy(x).cuda()
+    proc.set_leading_colour(True)
+    got = proc.integrand(xd, "fp64").cpu().numpy()
+    got_mixed = proc.integrand(xd, "mixed").cpu().numpy()
+    ref = I.leading_colour(x)
+    full, tol = fp64_tolerance(I, x)
+    assert np.array_equal(got == 0, ref == 0)
+    err = np.abs(got - ref)
+    scale = np.maximum(np.abs(ref), np.abs(full))
+    assert np.all(err <= tol * scale), np.max(err / scale)
+    rm = relerr(got_mixed, ref)[ref != 0]
+    assert np.median(rm) <= 1e-5 and rm.max() <= 1e-3
+    proc.set_leading_colour(False)
+    back = proc.integrand(xd, "fp64").cpu().numpy()
+    assert np.all(relerr(back, full) <= tol)

@@ -263,3 +263,25 @@ def test_massless_mhv_formula(final):
     gluons = [i for i, (part, _) in enumerate(legs) if part == "g"]
     mhv = _mhv_total(k, qb=3, q=2, gluons=gluons, g=g_s)
     assert np.max(np.abs(mhv / ref - 1)) < 1e-11
+
+
+def test_string_basis_norms_and_leading_colour(oracle_processes):
+    # each basis element's squared norm is prod over its strings of
+    # N C_F^m (m gluons on the string, C_F = 4/3); for uu~ -> tt~ the Fierz
+    # identity gives the colour factor 1/2 B1 - 1/6 B2, so the leading-colour
+    # sum (diagonal of the colour matrix in this basis) is 9/4 + 1/4 against
+    # the full 2: a ratio of exactly 5/4 at every point
+    import workloads as W
+    from oracle.integrand import Integrand
+    expect = {"gg_ttx": [16 / 3] * 2, "uux_ttx": [9.0] * 2, "uux_ttxg": [12.0] * 4, "gg_ttxg": [64 / 9] * 6,
+              "gg_ttxgg": [256 / 27] * 24}
+    for name, norms in expect.items():
+        B = oracle_processes(name).string_basis()
+        got = np.real(np.sum(np.conj(B) * B, axis=0))
+        assert np.allclose(got, norms, rtol=1e-13), name
+    I = Integrand(W.UUX_TTX, process=oracle_processes("uux_ttx"))
+    x = W.uniform_points(4, 30, 8)
+    full = I(x)
+    lc = I.leading_colour(x)
+    nz = full != 0
+    assert np.allclose(lc[nz] / full[nz], 1.25, rtol=1e-12)
