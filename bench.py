@@ -41,7 +41,9 @@ def _args():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--fp64-events", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-batch", action="store_true", help="skip the mixed-batch measurement")
+    ap.add_argument("--no-batch", action="store_true", help="skip the mixed-batch and variant measurements")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_tc"],
+                    help="arithmetic of the timed iterations (mixed_tc: colour sum on the tensor cores)")
     return ap.parse_args()
 
 
@@ -188,7 +190,7 @@ def run_native(args):
 
     # warm-up (also JIT-compiles the mixed kernel)
     for _ in range(max(args.warmup, 3)):
-        step("mixed", n_events)
+        step(args.precision, n_events)
     torch.cuda.synchronize()
 
     def barrier():
@@ -205,7 +207,7 @@ def run_native(args):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        results.append(step("mixed", n_events))
+        results.append(step(args.precision, n_events))
         kernel_ms.append(api.mf_process_last_kernel_ms(proc.handle))
     e1.record(stream)
     barrier()
@@ -252,7 +254,7 @@ def run_native(args):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         vg.grid = grid_host.numpy()
-        r = step("mixed", n_events)
+        r = step(args.precision, n_events)
         grid_host.copy_(torch.from_numpy(vg.grid))
     barrier()
     t_e2e = time.perf_counter() - t0
@@ -341,6 +343,7 @@ def run_native(args):
         "config": {"workload": f"{wl.name}: gg->tt~gg at 13 TeV, {n_events:.0e} events per Vegas iteration "
                                f"per GPU, {wl.ndim} dims, 50 bins, cuts pT(g)>20 GeV and dR(g,g)>0.4, synthetic "
                                f"PDF table; f32 amplitudes/colour sum, f64 kinematics and accumulators",
+                   "precision": args.precision + (" (colour sum on the tensor cores)" if args.precision == "mixed_tc" else ""),
                    "events_per_step_per_gpu": n_events, "diagrams": 123, "helicities": info["n_hel"],
                    "colour_flows": info["n_jamp"],
                    "l2": "random numbers generated in-kernel; per-step outputs (w, bins) "
