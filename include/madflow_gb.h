@@ -345,6 +345,16 @@ mf_status mf_batch_destroy(mf_batch *b);
 mf_status mf_batch_iterate(mf_batch *b, mf_vegas *const *grids, const int64_t *n_events, uint64_t seed,
                            int32_t refine, mf_iter_result *out, void *stream);
 mf_status mf_batch_get_info(const mf_batch *b, int32_t *order, int32_t *regs, double *last_kernel_ms);
+/* mf_batch_iterate_graph: mf_batch_iterate as one CUDA graph replay.  The
+ * first call (and any call whose grids, point counts, seed or refine flag
+ * differ from the captured ones) captures the whole iteration — tile counter
+ * reset, the persistent kernel, every subprocess's accumulation, tree
+ * reduction, finalisation, refinement and the copies of the results — on an
+ * internal stream and instantiates it; later calls copy the grids' iteration
+ * indices to the device and replay the graph on `stream`.  Same points and
+ * results as mf_batch_iterate.  Synchronous. */
+mf_status mf_batch_iterate_graph(mf_batch *b, mf_vegas *const *grids, const int64_t *n_events, uint64_t seed,
+                                 int32_t refine, mf_iter_result *out, void *stream);
 
 /* ---- Unweighted events and the Les Houches Event writer (Sec. 2.5).
  *

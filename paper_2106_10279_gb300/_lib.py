@@ -101,6 +101,8 @@ SIGNATURES = {
     "mf_batch_destroy": (c_i32, [C.c_void_p]),
     "mf_batch_iterate": (c_i32, [C.c_void_p, P(C.c_void_p), P(c_i64), C.c_uint64, c_i32, P(mf_iter_result),
                                  C.c_void_p]),
+    "mf_batch_iterate_graph": (c_i32, [C.c_void_p, P(C.c_void_p), P(c_i64), C.c_uint64, c_i32, P(mf_iter_result),
+                                       C.c_void_p]),
     "mf_batch_get_info": (c_i32, [C.c_void_p, P(c_i32), P(c_i32), P(C.c_double)]),
     "mf_generate_batch_source": (c_i32, [P(P(mf_process_desc)), c_i32, c_i32, c_i32, C.c_char_p, P(C.c_size_t)]),
     "mf_lhe_open": (c_i32, [C.c_char_p, P(mf_lhe_init), P(C.c_void_p)]),

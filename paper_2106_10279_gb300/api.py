@@ -548,13 +548,15 @@ class Batch:
         L.check(L.lib().mf_batch_create(arr, k, _PREC[precision], C.byref(h)), "mf_batch_create")
         self.handle = h
 
-    def iterate(self, grids, n_events, seed: int, refine=True, stream=None):
+    def iterate(self, grids, n_events, seed: int, refine=True, stream=None, graph=False):
+        """One iteration of every subprocess; graph=True replays a captured CUDA graph."""
         k = len(self.procs)
         G = (C.c_void_p * k)(*[g.handle.value for g in grids])
         N = (C.c_int64 * k)(*n_events)
         out = (L.mf_iter_result * k)()
-        st = L.lib().mf_batch_iterate(self.handle, G, N, seed, 1 if refine else 0, out, _stream_ptr(stream))
-        L.check(st, "mf_batch_iterate", allow=(L.MF_OK, L.MF_ENAN))
+        fn = L.lib().mf_batch_iterate_graph if graph else L.lib().mf_batch_iterate
+        st = fn(self.handle, G, N, seed, 1 if refine else 0, out, _stream_ptr(stream))
+        L.check(st, "mf_batch_iterate_graph" if graph else "mf_batch_iterate", allow=(L.MF_OK, L.MF_ENAN))
         return [_result(r) for r in out]
 
     def info(self):

@@ -249,4 +249,44 @@ MF_DEV W<R> VVVV_VEC(const W<R> &A, const W<R> &B, const W<R> &Cv, cx<R> g, R in
     return w;
 }
 
+
+// The vertex routines as non-inlined functions taking everything by value
+// (momenta as four scalars): a program made of calls to these holds one copy
+// of each routine's code.
+#if defined(__CUDACC__) || defined(__CUDACC_RTC__)
+#define MF_NOINL __device__ __noinline__
+#else
+#define MF_NOINL inline
+#endif
+template <typename R>
+MF_NOINL W<R> nFFV_FIN(W<R> col, W<R> V, cx<R> g, R M, R inv_den, R p0, R p1, R p2, R p3) {
+    const R P[4] = {p0, p1, p2, p3};
+    return FFV_FIN<R>(col, V, g, M, inv_den, P);
+}
+template <typename R>
+MF_NOINL W<R> nFFV_FOUT(W<R> row, W<R> V, cx<R> g, R M, R inv_den, R p0, R p1, R p2, R p3) {
+    const R P[4] = {p0, p1, p2, p3};
+    return FFV_FOUT<R>(row, V, g, M, inv_den, P);
+}
+template <typename R>
+MF_NOINL W<R> nFFV_VEC(W<R> row, W<R> col, cx<R> g, R inv_den) { return FFV_VEC<R>(row, col, g, inv_den); }
+template <typename R>
+MF_NOINL W<R> nVVV_VEC(W<R> A, W<R> B, R a0, R a1, R a2, R a3, R b0, R b1, R b2, R b3, cx<R> g, R inv_den) {
+    const R kA[4] = {a0, a1, a2, a3}, kB[4] = {b0, b1, b2, b3};
+    return VVV_VEC<R>(A, B, kA, kB, g, inv_den);
+}
+template <typename R, int S>
+MF_NOINL W<R> nVVVV_VEC(W<R> A, W<R> B, W<R> Cv, cx<R> g, R inv_den) { return VVVV_VEC<R, S>(A, B, Cv, g, inv_den); }
+template <typename R>
+MF_NOINL cx<R> nFFV_AMP(W<R> row, W<R> col, W<R> V, cx<R> g) { return FFV_AMP<R>(row, col, V, g); }
+template <typename R>
+MF_NOINL cx<R> nVVV_AMP(W<R> A, W<R> B, W<R> Cv, R a0, R a1, R a2, R a3, R b0, R b1, R b2, R b3, R c0, R c1, R c2,
+                        R c3, cx<R> g) {
+    const R kA[4] = {a0, a1, a2, a3}, kB[4] = {b0, b1, b2, b3}, kC[4] = {c0, c1, c2, c3};
+    return VVV_AMP<R>(A, B, Cv, kA, kB, kC, g);
+}
+template <typename R, int S>
+MF_NOINL cx<R> nVVVV_AMP(W<R> A, W<R> B, W<R> Cv, W<R> D, cx<R> g) { return VVVV_AMP<R, S>(A, B, Cv, D, g); }
+#undef MF_NOINL
+
 }  // namespace mf

@@ -199,6 +199,7 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
     int *s_warp = s_list + BLOCK;                                                  // [BLOCK/32 + 1]
     const int tid = threadIdx.x;
     const int lane32 = tid & 31, warp = tid >> 5;
+    const uint64_t iteration = kp.iter_dev ? (uint64_t)*kp.iter_dev : kp.iteration;
     {
         const int64_t e = tile * BLOCK + tid;
         bool ok = false;
@@ -214,7 +215,7 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
                 const uint64_t gi = kp.mode == 3 ? (uint64_t)kp.idx[e] : (uint64_t)(e + kp.ev0);
 #pragma unroll
                 for (int b = 0; b < (NDIM + 3) / 4; ++b) {
-                    uint64_t c[4] = {gi, kp.iteration, kp.subprocess, (uint64_t)b};
+                    uint64_t c[4] = {gi, iteration, kp.subprocess, (uint64_t)b};
                     philox4x64_10(c, kp.seed, 0ull);
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
@@ -252,7 +253,7 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
                 // non-vanishing ones, from Philox block 14 of the point's counter
                 uint64_t c[4] = {kp.mode == 0 ? (uint64_t)e
                                  : (kp.mode == 3 ? (uint64_t)kp.idx[e] : (uint64_t)(e + kp.ev0)),
-                                 kp.mode == 0 ? 0ull : kp.iteration, kp.mode == 0 ? 0ull : kp.subprocess, 14ull};
+                                 kp.mode == 0 ? 0ull : iteration, kp.mode == 0 ? 0ull : kp.subprocess, 14ull};
                 philox4x64_10(c, kp.seed, 0ull);
                 int h = (int)(unit_from_bits(c[0]) * kp.nhel);
                 if (h >= kp.nhel) h = kp.nhel - 1;

@@ -39,6 +39,7 @@ struct mf_kparams {
     const int64_t *idx;        // mode 3: global point indices
     int32_t hel_sample;        // 1: one helicity per point, drawn uniformly, f scaled by nhel
     int32_t pad3;
+    const long long *iter_dev; // if set, the iteration index is read here (graph replays)
     double masses[8];
     double couplings[16];      // 8 complex couplings (re, im)
     int8_t hel[MF_KP_MAX_HEL][8];

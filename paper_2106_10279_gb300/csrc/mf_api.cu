@@ -110,9 +110,9 @@ __global__ void __launch_bounds__(kAccThreads) vegas_accumulate_kernel(const dou
     extern __shared__ double sh[];
     double *sw = sh;                    // [kChunk] sanitised w
     double *buf = sh + kChunk;          // [kChunk] tree buffer
-    uint8_t *sb = reinterpret_cast<uint8_t *>(buf + kChunk);   // [kChunk]
-    __shared__ double part[4][64];
-    __shared__ double cpart[4][64];
+    __shared__ double whist[kAccThreads / 32][64];
+    __shared__ int wcnt[kAccThreads / 32][64];
+    __shared__ double stage[kAccThreads / 32][32];
     __shared__ int s_nz, s_nan;
     const int64_t base = (int64_t)blockIdx.x * kChunk;
     const int m = (int)((n - base) < kChunk ? (n - base) : kChunk);
@@ -140,25 +140,46 @@ __global__ void __launch_bounds__(kAccThreads) vegas_accumulate_kernel(const dou
     if (threadIdx.x == 0) {
         slot[0] = s1; slot[ld] = s2; slot[2 * ld] = (double)s_nz; slot[3 * ld] = (double)s_nan;
     }
-    // per dimension and bin: 4 segments of kChunk/4 events, each summed in event
-    // order by the thread owning (segment, bin), then segments in order
-    const int seg = threadIdx.x / 64, b = threadIdx.x % 64;
+    // per dimension and bin: warp k sums its kChunk/8 consecutive events in
+    // event order (32 at a time; lanes of one bin are added by the lowest of
+    // them in lane order), then the 8 warps' sums are added in a fixed tree
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int kWarps = kAccThreads / 32, kPerWarp = kChunk / kWarps;
     for (int j = 0; j < ndim; ++j) {
-        for (int i = threadIdx.x; i < kChunk; i += blockDim.x) sb[i] = i < m ? bins[(int64_t)j * n + base + i] : 0xff;
-        __syncthreads();
-        double acc = 0.0, cnt = 0.0;
-        if (b < nb) {
-            const int lo = seg * (kChunk / 4), hi = lo + kChunk / 4;
-            for (int i = lo; i < hi; ++i)
-                if (sb[i] == b) { acc += sw[i] * sw[i]; cnt += 1.0; }
+        for (int q = lane; q < 64; q += 32) {
+            whist[warp][q] = 0.0;
+            wcnt[warp][q] = 0;
         }
-        part[seg][b] = acc;
-        cpart[seg][b] = cnt;
+        __syncwarp();
+        for (int step = 0; step < kPerWarp / 32; ++step) {
+            const int i = warp * kPerWarp + step * 32 + lane;
+            const bool valid = i < m;
+            const int b = valid ? (int)bins[(int64_t)j * n + base + i] : 255;
+            stage[warp][lane] = valid ? sw[i] * sw[i] : 0.0;
+            const unsigned peers = __match_any_sync(0xffffffffu, b);
+            __syncwarp();
+            if (b < 64 && lane == __ffs(peers) - 1) {
+                double acc = whist[warp][b];
+                int cnt = wcnt[warp][b];
+                for (unsigned mk = peers; mk; mk &= mk - 1) {
+                    acc += stage[warp][__ffs(mk) - 1];
+                    ++cnt;
+                }
+                whist[warp][b] = acc;
+                wcnt[warp][b] = cnt;
+            }
+            __syncwarp();
+        }
         __syncthreads();
         if (threadIdx.x < nb) {
-            int q = threadIdx.x;
-            slot[(size_t)(4 + j * nb + q) * ld] = (part[0][q] + part[1][q]) + (part[2][q] + part[3][q]);
-            slot[(size_t)(4 + ndim * nb + j * nb + q) * ld] = (cpart[0][q] + cpart[1][q]) + (cpart[2][q] + cpart[3][q]);
+            const int q = threadIdx.x;
+            static_assert(kWarps == 8, "fixed 8-warp tree");
+            const double h = ((whist[0][q] + whist[1][q]) + (whist[2][q] + whist[3][q])) +
+                             ((whist[4][q] + whist[5][q]) + (whist[6][q] + whist[7][q]));
+            int c = 0;
+            for (int w = 0; w < kWarps; ++w) c += wcnt[w][q];
+            slot[(size_t)(4 + j * nb + q) * ld] = h;
+            slot[(size_t)(4 + ndim * nb + j * nb + q) * ld] = (double)c;
         }
         __syncthreads();
     }
@@ -259,6 +280,54 @@ __global__ void vegas_finalize_kernel(const double *tot, int64_t n, int ndim, in
                 chi2 += d * d / (iters[2 * k + 1] * iters[2 * k + 1]);
             }
             chi2 /= it;
+        }
+    }
+    res[0] = I; res[1] = err; res[2] = mean; res[3] = merr; res[4] = chi2;
+    res[5] = tot[2]; res[6] = tot[3];
+}
+
+// The same with the iteration index read from device memory (graph replays).
+__global__ void vegas_finalize_dev_kernel(const double *tot, int64_t n, int ndim, int nb, const long long *it,
+                                          double *hist, long long *count, double *iters, double *res) {
+    __shared__ int s_it;
+    if (threadIdx.x == 0) s_it = (int)*it;
+    __syncthreads();
+    const int k = s_it;
+    for (int i = threadIdx.x; i < ndim * nb; i += blockDim.x) {
+        hist[i] = tot[4 + i];
+        count[i] = (long long)tot[4 + ndim * nb + i];
+    }
+    if (threadIdx.x != 0) return;
+    // the rest as vegas_finalize_kernel, for iteration k
+    double N = (double)n;
+    double I = tot[0] / N;
+    double var = (tot[1] / N - I * I) / (N - 1.0);
+    double err = sqrt(var > 0.0 ? var : 0.0);
+    iters[2 * k] = I;
+    iters[2 * k + 1] = err;
+    int nexact = 0;
+    double exact_sum = 0.0;
+    for (int q = 0; q <= k; ++q)
+        if (iters[2 * q + 1] == 0.0) { ++nexact; exact_sum += iters[2 * q]; }
+    double mean, merr, chi2 = 0.0;
+    if (nexact > 0) {
+        mean = exact_sum / nexact;
+        merr = 0.0;
+    } else {
+        double sw = 0.0, swi = 0.0;
+        for (int q = 0; q <= k; ++q) {
+            double wq = 1.0 / (iters[2 * q + 1] * iters[2 * q + 1]);
+            sw += wq;
+            swi += wq * iters[2 * q];
+        }
+        mean = swi / sw;
+        merr = 1.0 / sqrt(sw);
+        if (k > 0) {
+            for (int q = 0; q <= k; ++q) {
+                double d = iters[2 * q] - mean;
+                chi2 += d * d / (iters[2 * q + 1] * iters[2 * q + 1]);
+            }
+            chi2 /= k;
         }
     }
     res[0] = I; res[1] = err; res[2] = mean; res[3] = merr; res[4] = chi2;
@@ -1039,7 +1108,7 @@ void vegas_params(const mf_process *p, const mf_vegas *v, int64_t n, int64_t ev0
 // Chunk partial sums of the process scratch's n points into v->d_slots.
 mf_status accumulate(mf_process *p, mf_vegas *v, int64_t n, cudaStream_t s) {
     const int64_t nchunks = (n + kChunk - 1) / kChunk;
-    const size_t acc_smem = sizeof(double) * 2 * kChunk + kChunk;
+    const size_t acc_smem = sizeof(double) * 2 * kChunk;
     static bool attr_set = false;
     if (!attr_set) {
         MF_CUDA(cudaFuncSetAttribute(vegas_accumulate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1493,6 +1562,13 @@ extern "C" mf_status mf_batch_create(mf_process *const *procs, int32_t nproc, mf
 
 extern "C" mf_status mf_batch_destroy(mf_batch *b) {
     if (!b) return MF_OK;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    cudaFree(b->d_iters);
+    cudaFree(b->d_root_ids);
+    cudaFreeHost(b->h_iters);
+    cudaFreeHost(b->h_res);
+    cudaFreeHost(b->h_flags);
     mfi::unload_kernel(b->kern);
     cudaFree(b->d_counter);
     if (b->ev_start) cudaEventDestroy(b->ev_start);
@@ -1575,6 +1651,148 @@ extern "C" mf_status mf_batch_iterate(mf_batch *b, mf_vegas *const *grids, const
     bool any_nan = false;
     for (int k = 0; k < nproc; ++k) {
         fill_result(out[k], grids[k], n_events[k], res[k].data());
+        any_nan |= out[k].n_nan > 0;
+        grids[k]->iteration += 1;
+    }
+    if (any_nan) return fail(MF_ENAN, "some points had non-finite weights (counted as zero)");
+    return MF_OK;
+}
+
+// One batched iteration as a CUDA graph: captured once for given grids,
+// point counts, seed and refine flag, then replayed; the only per-iteration
+// inputs are the grids' iteration indices, copied to the device before each
+// replay (the kernels read them there).
+namespace {
+// Every device buffer a captured iteration touches: a graph is replayed only
+// while all of them are still the ones it was captured with.
+std::vector<const void *> graph_buffers(const mf_batch *b, mf_vegas *const *grids) {
+    std::vector<const void *> v;
+    for (size_t k = 0; k < b->procs.size(); ++k) {
+        const mf_process *p = b->procs[k];
+        const mf_vegas *g = grids[k];
+        v.insert(v.end(), {p->d_w, p->d_bins, p->d_err, g->d_slots, g->d_tree_out, g->d_grid, g->d_hist,
+                           g->d_count, g->d_hist_iter, g->d_result});
+    }
+    return v;
+}
+
+mf_status capture_batch(mf_batch *b, mf_vegas *const *grids, const int64_t *n_events, uint64_t seed, int refine) {
+    const int nproc = (int)b->procs.size();
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    if (!b->capture_stream) MF_CUDA(cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking));
+    if (!b->d_iters) {
+        MF_CUDA(cudaMalloc(&b->d_iters, sizeof(long long) * nproc));
+        MF_CUDA(cudaMalloc(&b->d_root_ids, sizeof(int64_t) * 2 * nproc));
+        MF_CUDA(cudaMallocHost(&b->h_iters, sizeof(long long) * nproc));
+        MF_CUDA(cudaMallocHost(&b->h_res, sizeof(double) * 8 * nproc));
+        MF_CUDA(cudaMallocHost(&b->h_flags, sizeof(int) * nproc));
+    }
+    std::vector<int64_t> roots(2 * nproc);
+    for (int k = 0; k < nproc; ++k) {
+        mf_status st = ensure_scratch(b->procs[k], grids[k], n_events[k]);
+        if (st != MF_OK) return st;
+        const int64_t nchunks = (n_events[k] + kChunk - 1) / kChunk;
+        roots[2 * k] = tree_levels(nchunks);
+        roots[2 * k + 1] = 0;
+    }
+    MF_CUDA(cudaMemcpy(b->d_root_ids, roots.data(), sizeof(int64_t) * roots.size(), cudaMemcpyHostToDevice));
+    const size_t acc_smem = sizeof(double) * 2 * kChunk;
+    MF_CUDA(cudaFuncSetAttribute(vegas_accumulate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc_smem));
+    mf_batch_params bp;
+    std::memset(&bp, 0, sizeof bp);
+    bp.counter = b->d_counter;
+    bp.nproc = nproc;
+    for (int slot = 0; slot < nproc; ++slot) {
+        const int u = b->order[slot];
+        vegas_params(b->procs[u], grids[u], n_events[u], 0, u, seed, bp.kp[slot]);
+        bp.kp[slot].iter_dev = b->d_iters + u;
+        bp.start[slot + 1] = bp.start[slot] + (n_events[u] + b->kern.block - 1) / b->kern.block;
+    }
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
+    int64_t grid = (int64_t)nsm * b->kern.max_blocks_per_sm;
+    if (grid > bp.start[nproc]) grid = bp.start[nproc];
+    cudaStream_t c = b->capture_stream;
+    MF_CUDA(cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ce = cudaMemsetAsync(b->d_counter, 0, sizeof(long long), c);
+    void *args[] = {&bp};
+    mf_status st = ce == cudaSuccess ? mfi::launch_kernel(b->kern, (unsigned)grid, args, c) : MF_ECUDA;
+    for (int k = 0; k < nproc && st == MF_OK; ++k) {
+        mf_process *p = b->procs[k];
+        mf_vegas *v = grids[k];
+        const int64_t n = n_events[k];
+        const int64_t nchunks = (n + kChunk - 1) / kChunk;
+        const int K = partial_size(v);
+        vegas_accumulate_kernel<<<(unsigned)nchunks, kAccThreads, acc_smem, c>>>(p->d_w, p->d_bins, n, v->ndim,
+                                                                                  v->nbins, v->d_slots, nchunks);
+        vegas_tree_kernel<<<dim3((unsigned)K, 1), kTreeThreads, 0, c>>>(v->d_slots, nchunks, 0, nchunks, K,
+                                                                         b->d_root_ids + 2 * k, v->d_tree_out);
+        vegas_finalize_dev_kernel<<<1, 128, 0, c>>>(v->d_tree_out, n, v->ndim, v->nbins, b->d_iters + k, v->d_hist,
+                                                    v->d_count, v->d_hist_iter, v->d_result);
+        if (refine) vegas_refine_kernel<<<1, 32, 0, c>>>(v->d_grid, v->d_hist, v->ndim, v->nbins, n, v->alpha);
+        if (cudaMemcpyAsync(b->h_res + 8 * k, v->d_result, sizeof(double) * 7, cudaMemcpyDeviceToHost, c) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(b->h_flags + k, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, c) != cudaSuccess)
+            st = MF_ECUDA;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(c, &g);
+    if (st != MF_OK || ee != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return fail(MF_ECUDA, std::string("capturing the batched iteration failed: ") + cudaGetErrorString(ee));
+    }
+    cudaError_t ie = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+        b->graph = nullptr;
+        return fail(MF_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+    }
+    b->graph_grids.assign(grids, grids + nproc);
+    b->graph_n.assign(n_events, n_events + nproc);
+    b->graph_ptrs = graph_buffers(b, grids);
+    b->graph_seed = seed;
+    b->graph_refine = refine ? 1 : 0;
+    return MF_OK;
+}
+}  // namespace
+
+extern "C" mf_status mf_batch_iterate_graph(mf_batch *b, mf_vegas *const *grids, const int64_t *n_events,
+                                            uint64_t seed, int32_t refine, mf_iter_result *out, void *stream) {
+    if (!b || !grids || !n_events || !out) return fail(MF_EINVAL, "NULL argument");
+    const int nproc = (int)b->procs.size();
+    for (int k = 0; k < nproc; ++k) {
+        if (!grids[k]) return fail(MF_EINVAL, "NULL grid");
+        if (grids[k]->ndim != b->procs[k]->ndim) return fail(MF_EINVAL, "grid and process dimensions differ");
+        if (n_events[k] < 2) return fail(MF_EINVAL, "need at least two events per iteration");
+        if ((n_events[k] + kChunk - 1) / kChunk > ((int64_t)1 << kTreeMaxLevel))
+            return fail(MF_EINVAL, "too many events per iteration");
+        if (grids[k]->iteration >= grids[k]->max_iter) return fail(MF_EUNSUPPORTED, "too many iterations");
+        for (int q = 0; q < k; ++q)
+            if (grids[q] == grids[k]) return fail(MF_EINVAL, "a grid appears twice");
+    }
+    bool same = b->graph && b->graph_seed == seed && b->graph_refine == (refine ? 1 : 0);
+    for (int k = 0; k < nproc && same; ++k) same = b->graph_grids[k] == grids[k] && b->graph_n[k] == n_events[k];
+    if (same) same = graph_buffers(b, grids) == b->graph_ptrs;
+    if (!same) {
+        mf_status st = capture_batch(b, grids, n_events, seed, refine);
+        if (st != MF_OK) return st;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int k = 0; k < nproc; ++k) b->h_iters[k] = grids[k]->iteration;
+    MF_CUDA(cudaMemcpyAsync(b->d_iters, b->h_iters, sizeof(long long) * nproc, cudaMemcpyHostToDevice, s));
+    MF_CUDA(cudaGraphLaunch(b->graph, s));
+    MF_CUDA(cudaStreamSynchronize(s));
+    for (int k = 0; k < nproc; ++k) {
+        mf_status st = flag_status(b->procs[k], b->h_flags[k]);
+        if (st != MF_OK) return st;
+    }
+    bool any_nan = false;
+    for (int k = 0; k < nproc; ++k) {
+        fill_result(out[k], grids[k], n_events[k], b->h_res + 8 * k);
         any_nan |= out[k].n_nan > 0;
         grids[k]->iteration += 1;
     }

@@ -137,6 +137,17 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
     std::ostringstream o;
     std::vector<uint32_t> mask;
     emit_header(o, p, info, mask, R, ns);
+    // The vertex routines are called as non-inlined functions: one copy of each
+    // routine's code instead of one per use.  The program then fits the
+    // instruction caches far better (the inlined form is fetch-bound), at the
+    // price of argument passing.  MF_CALL_ROUTINES=0 inlines them.
+    const bool calls = !(std::getenv("MF_CALL_ROUTINES") && std::atoi(std::getenv("MF_CALL_ROUTINES")) == 0);
+    auto rt = [&](const char *name) { return std::string(calls ? "n" : "") + name; };
+    auto a4 = [&](const char *name) {
+        if (!calls) return std::string(name);
+        std::string n(name);
+        return n + "[0], " + n + "[1], " + n + "[2], " + n + "[3]";
+    };
 
     // --- the program for one helicity
     // momentum into the diagram through the legs of a mask, component q
@@ -206,14 +217,15 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
         for (int q = 0; q < 4; ++q)
             if (p.ops[best].in[q] >= 0) remaining_uses[p.ops[best].in[q]]--;
     }
-    // Split the schedule into parts compiled as separate functions: ptxas
-    // falls back to a stack-based allocation for very large functions, so
-    // the program is cut into pieces below a size budget; each part recomputes
-    // the few shared wavefunctions it needs (a few per cent more work).
+    // With inlined routines the schedule is split into parts compiled as
+    // separate functions: ptxas falls back to a stack-based allocation for
+    // very large functions, so the program is cut into pieces below a size
+    // budget; each part recomputes the few shared wavefunctions it needs.
+    // Called routines keep the program small enough for twice the budget.
     double weight = 0.0;
     for (auto &op : p.ops) weight += routine_flops(op.routine);
     if (precision == MF_FP64) weight *= 2.0;
-    int parts = (int)std::ceil(weight / 32000.0);
+    int parts = (int)std::ceil(weight / (calls ? 64000.0 : 32000.0));
     if (const char *e = std::getenv("MF_PROGRAM_PARTS")) parts = std::atoi(e);
     if (parts < 1) parts = 1;
     if (parts > (int)order.size()) parts = (int)order.size();
@@ -251,20 +263,22 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
             case MF_R_FFV_FIN:
             case MF_R_FFV_FOUT:
                 o << mom(mask[k], "P");
-                o << "    w" << k << " = " << (op.routine == MF_R_FFV_FIN ? "FFV_FIN" : "FFV_FOUT") << "<R>(w"
-                  << op.in[0] << ", w" << op.in[1] << ", " << g << ", " << M(op.mass_id) << ", " << den << ", P);\n";
+                o << "    w" << k << " = " << rt(op.routine == MF_R_FFV_FIN ? "FFV_FIN" : "FFV_FOUT") << "<R>(w"
+                  << op.in[0] << ", w" << op.in[1] << ", " << g << ", " << M(op.mass_id) << ", " << den << ", "
+                  << a4("P") << ");\n";
                 break;
             case MF_R_FFV_VEC:
-                o << "    w" << k << " = FFV_VEC<R>(w" << op.in[0] << ", w" << op.in[1] << ", " << g << ", " << den << ");\n";
+                o << "    w" << k << " = " << rt("FFV_VEC") << "<R>(w" << op.in[0] << ", w" << op.in[1] << ", " << g
+                  << ", " << den << ");\n";
                 break;
             case MF_R_VVV_VEC:
                 o << mom(mask[op.in[0]], "kA") << mom(mask[op.in[1]], "kB");
-                o << "    w" << k << " = VVV_VEC<R>(w" << op.in[0] << ", w" << op.in[1] << ", kA, kB, " << g << ", "
-                  << den << ");\n";
+                o << "    w" << k << " = " << rt("VVV_VEC") << "<R>(w" << op.in[0] << ", w" << op.in[1] << ", "
+                  << a4("kA") << ", " << a4("kB") << ", " << g << ", " << den << ");\n";
                 break;
             default:
-                o << "    w" << k << " = VVVV_VEC<R, " << (op.routine - MF_R_VVVV1_VEC + 1) << ">(w" << op.in[0]
-                  << ", w" << op.in[1] << ", w" << op.in[2] << ", " << g << ", " << den << ");\n";
+                o << "    w" << k << " = " << rt("VVVV_VEC") << "<R, " << (op.routine - MF_R_VVVV1_VEC + 1) << ">(w"
+                  << op.in[0] << ", w" << op.in[1] << ", w" << op.in[2] << ", " << g << ", " << den << ");\n";
                 break;
         }
         o << "  }\n";
@@ -291,11 +305,16 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
         if (op.routine == MF_R_VVV_AMP) o << mom(mask[op.in[0]], "kA") << mom(mask[op.in[1]], "kB") << mom(mask[op.in[2]], "kC");
         o << "    const cx<R> a = ";
         switch (op.routine) {
-            case MF_R_FFV_AMP: o << "FFV_AMP<R>(w" << op.in[0] << ", w" << op.in[1] << ", w" << op.in[2] << ", " << g << ")"; break;
-            case MF_R_VVV_AMP: o << "VVV_AMP<R>(w" << op.in[0] << ", w" << op.in[1] << ", w" << op.in[2] << ", kA, kB, kC, " << g << ")"; break;
+            case MF_R_FFV_AMP:
+                o << rt("FFV_AMP") << "<R>(w" << op.in[0] << ", w" << op.in[1] << ", w" << op.in[2] << ", " << g << ")";
+                break;
+            case MF_R_VVV_AMP:
+                o << rt("VVV_AMP") << "<R>(w" << op.in[0] << ", w" << op.in[1] << ", w" << op.in[2] << ", " << a4("kA")
+                  << ", " << a4("kB") << ", " << a4("kC") << ", " << g << ")";
+                break;
             default:
-                o << "VVVV_AMP<R, " << (op.routine - MF_R_VVVV1_AMP + 1) << ">(w" << op.in[0] << ", w" << op.in[1]
-                  << ", w" << op.in[2] << ", w" << op.in[3] << ", " << g << ")";
+                o << rt("VVVV_AMP") << "<R, " << (op.routine - MF_R_VVVV1_AMP + 1) << ">(w" << op.in[0] << ", w"
+                  << op.in[1] << ", w" << op.in[2] << ", w" << op.in[3] << ", " << g << ")";
         }
         o << ";\n";
         for (int t = 0; t < op.n_terms; ++t) {

@@ -114,6 +114,20 @@ struct mf_batch {
     long long *d_counter = nullptr;    // tile counter of the persistent kernel
     cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
     double last_kernel_ms = 0.0;
+    // CUDA graph of one iteration (mf_batch_iterate_graph), valid for the
+    // grids, point counts, seed and refine flag it was captured with
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    std::vector<mf_vegas *> graph_grids;
+    std::vector<int64_t> graph_n;
+    std::vector<const void *> graph_ptrs;  // scratch and grid buffers the graph writes
+    uint64_t graph_seed = 0;
+    int graph_refine = -1;
+    long long *d_iters = nullptr;      // [nproc] iteration index per grid, read by the graph
+    int64_t *d_root_ids = nullptr;     // [nproc][2] root node of each grid's chunk tree
+    long long *h_iters = nullptr;      // pinned [nproc]
+    double *h_res = nullptr;           // pinned [nproc][8]
+    int *h_flags = nullptr;            // pinned [nproc]
 };
 
 struct mf_lhe_writer;

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <fstream>
+#include <cmath>
 #include <mutex>
 #include <sstream>
 
@@ -198,7 +199,18 @@ mf_status load_kernel(const std::vector<char> &cubin, Compiled &out, const char 
         r = g_drv.funcSetAttribute(out.fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)out.smem);
         if (r != CUDA_SUCCESS) return fail(MF_ECUDA, "cannot reserve dynamic shared memory: " + drv_err(r));
     }
-    int nb = 0;
+    // shared-memory carve-out: just enough for every block the registers
+    // allow on an SM, so that the rest stays L1 cache (the programs spill to
+    // local memory, which lives there)
+    int nb = 0, nb_regs = 0, stat = 0;
+    g_drv.funcGetAttribute(&stat, CU_FUNC_ATTRIBUTE_SHARED_SIZE_BYTES, out.fn);
+    if (g_drv.occupancy(&nb_regs, out.fn, out.block, 0) == CUDA_SUCCESS && nb_regs > 0) {
+        const double per_sm = (double)nb_regs * (double)(out.smem + (size_t)stat + 1024);
+        int pct = (int)std::ceil(100.0 * per_sm / (228.0 * 1024.0));
+        if (pct < 1) pct = 1;
+        if (pct > 100) pct = 100;
+        g_drv.funcSetAttribute(out.fn, CU_FUNC_ATTRIBUTE_PREFERRED_SHARED_MEMORY_CARVEOUT, pct);
+    }
     r = g_drv.occupancy(&nb, out.fn, out.block, out.smem);
     if (r != CUDA_SUCCESS || nb < 1) return fail(MF_ECUDA, "process kernel cannot be resident on an SM");
     out.max_blocks_per_sm = nb;

@@ -67,3 +67,22 @@ def test_batch_rejects_bad_input(env):
         b.iterate([g, g], [10000, 10000], 1)                 # one grid twice
     with pytest.raises(L.MfError):
         b.iterate([g, api.Vegas(7)], [10000, 10000], 1)      # dimensions differ
+
+
+def test_graph_replay_matches_plain_batch_iterations(env):
+    # the captured iteration replayed three times gives the bits of three plain
+    # batched iterations; another seed is captured anew
+    api, procs = env
+    names = [name for name, _ in W.MIXED_BATCH]
+    n = [max(4096, nev // SCALE) + 5 for _, nev in W.MIXED_BATCH]
+    plist = [procs[k] for k in names]
+    batch = api.Batch(plist, "fp64")
+    ga = [api.Vegas(procs[k].ndim) for k in names]
+    gb = [api.Vegas(procs[k].ndim) for k in names]
+    for seed in (3, 3, 3, 4):
+        ra = batch.iterate(ga, n, seed)
+        rb = batch.iterate(gb, n, seed, graph=True)
+        assert ra == rb
+        for a, b in zip(ga, gb):
+            assert np.array_equal(a.grid, b.grid)
+            assert np.array_equal(a.histogram()[0], b.histogram()[0])
