@@ -28,6 +28,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "events/s of gg→tt̄g(g) LO integrand: mixed/batched vs FP64 at ≤1e-5 rel err"
+# DRAM bytes per point of the fused integrand kernel, mixed precision:
+# dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of a
+# 1e6-point gg->tt~gg iteration divided by its points (the traffic grows with
+# the points; the capture's kernel is the one built from this source)
+KERNEL_DRAM_BYTES_PER_POINT = {("gg_ttxgg", "mixed"): (1.031936e6 + 12.530688e6) / 1e6}
 WORKLOAD = "gg_ttxgg"
 
 
@@ -280,7 +285,8 @@ def run_native(args):
             r = api.mf_vegas_iterate([gv.handle], [proc.handle], [nv], seed, prec, False, stream)[0]
             kms_v = api.mf_process_last_kernel_ms(proc.handle)
             variants[tag] = {"events": nv, "kernel_ms": kms_v, "events_per_s": nv / (kms_v / 1e3),
-                             "integral_pb": r["integral"], "error_pb": r["error"]}
+                             "integral_pb": r["integral"], "error_pb": r["error"],
+                             "launch": proc.kernel_info(prec)}
         proc.set_helicity_sampling(False)
 
     # the mixed batch of five subprocesses (gg->tt~, uu~->tt~, gg->tt~g,
@@ -354,7 +360,11 @@ def run_native(args):
         "accuracy": {"median_rel_mixed_vs_fp64": float(np.median(rel)), "max_rel_mixed_vs_fp64": float(rel.max()),
                      "points": int(nz.sum())},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": None,
+                     "frac": achieved / fp32_peak,
+                     "traffic": (KERNEL_DRAM_BYTES_PER_POINT[(wl.name, args.precision)] * n_events
+                                 if (wl.name, args.precision) in KERNEL_DRAM_BYTES_PER_POINT else None),
+                     "traffic_note": "bytes per launch, scaled by points from a 1e6-point ncu capture; "
+                                     f"algorithmic output {n_events * (8 + wl.ndim) / 1e6:.0f} MB",
                      "kernel": "mf_kernel (fused integrand)", "kernel_ms": kms,
                      "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"},
         "cpu_baseline": cpu,

@@ -459,6 +459,12 @@ mf_status mf_process_set_leading_colour(mf_process *p, int32_t on);
  * *n_hel). */
 mf_status mf_process_get_helicities(const mf_process *p, int8_t *hel, int32_t *n_hel);
 
+/* The launch shape of the compiled kernel of precision prec: threads per
+ * block, lanes per point, registers per thread and resident blocks per SM
+ * (any pointer may be NULL); MF_EINVAL if that kernel is not compiled yet. */
+mf_status mf_process_kernel_info(const mf_process *p, mf_precision prec, int32_t *block, int32_t *ht,
+                                 int32_t *regs, int32_t *blocks_per_sm);
+
 /* mf_process_check: whether a kernel of this process flagged an error: a
  * bounded wait expired (the tensor-core colour sum waits on the completion
  * of its MMAs; that launch's results are unspecified): MF_ETIMEOUT; or the

@@ -391,6 +391,13 @@ class Process:
                                                   C.byref(n)), "mf_process_get_helicities")
         return out
 
+    def kernel_info(self, precision="mixed"):
+        """Launch shape of a compiled kernel: block, lanes per point, registers, blocks per SM."""
+        v = [C.c_int32() for _ in range(4)]
+        L.check(L.lib().mf_process_kernel_info(self.handle, _PREC[precision], *[C.byref(x) for x in v]),
+                "mf_process_kernel_info")
+        return dict(zip(("block", "ht", "regs", "blocks_per_sm"), (x.value for x in v)))
+
     def check(self):
         """Raise if a bounded wait of one of this process's kernels expired."""
         L.check(L.lib().mf_process_check(self.handle), "mf_process_check")

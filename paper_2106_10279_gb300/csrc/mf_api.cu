@@ -909,6 +909,19 @@ extern "C" mf_status mf_process_set_leading_colour(mf_process *p, int32_t on) {
     return MF_OK;
 }
 
+extern "C" mf_status mf_process_kernel_info(const mf_process *p, mf_precision prec, int32_t *block, int32_t *ht,
+                                            int32_t *regs, int32_t *blocks_per_sm) {
+    if (!p) return fail(MF_EINVAL, "NULL process");
+    if (!valid_prec(prec)) return fail(MF_EINVAL, "bad precision");
+    const mfi::Compiled &k = p->kern[prec];
+    if (!k.fn) return fail(MF_EINVAL, "the kernel of this precision is not compiled yet");
+    if (block) *block = k.block;
+    if (ht) *ht = k.ht;
+    if (regs) *regs = k.regs;
+    if (blocks_per_sm) *blocks_per_sm = k.max_blocks_per_sm;
+    return MF_OK;
+}
+
 extern "C" mf_status mf_process_get_helicities(const mf_process *p, int8_t *hel, int32_t *n_hel) {
     if (!p || !n_hel) return fail(MF_EINVAL, "NULL argument");
     *n_hel = (int32_t)(p->hel.size() / p->n_legs);
