@@ -108,7 +108,7 @@ def _chi(p, lam):
     ppz = np.where(pz >= 0, P + pz, pt2 / np.where(P - pz > 0, P - pz, 1.0))
     good = ppz > 0
     den = np.sqrt(np.where(good, 2.0 * P * ppz, 1.0))
-    out = np.zeros((len(px), 2), dtype=np.complex128)
+    out = np.zeros((len(px), 2), dtype=np.complex128, like=px)
     if lam == 1:
         out[:, 0] = np.where(good, ppz / den, 0.0)
         out[:, 1] = np.where(good, (px + 1j * py) / den, 1.0)
@@ -437,7 +437,8 @@ class Process:
         return sum(self._sign(l) * p[:, l] for l in self.legs_of(tree))
 
     def _mass(self, flav):
-        return float(self.masses.get(flav, 0.0))
+        m = self.masses.get(flav, 0.0)
+        return m if hasattr(m, "d") else float(m)       # dual masses pass through
 
     def _coupling_ffv(self, flav):
         if BOSON_OF[flav] == "g":
@@ -544,7 +545,7 @@ class Process:
 
     def msq_summed(self, p, gauge_leg=None, per_helicity=False):
         """sum over colours and helicities of |M|^2 (no averaging), [N]."""
-        p = np.asarray(p, dtype=np.float64)
+        p = p if hasattr(p, "d") else np.asarray(p, dtype=np.float64)
         G = self.colour_matrix()
         cache = {}
         tot = np.zeros(p.shape[0])
@@ -552,7 +553,7 @@ class Process:
         for hel in self.helicities():
             a = self.amplitudes(p, hel, cache, gauge_leg)      # [T, N]
             val = np.real(np.einsum("tn,ts,sn->n", np.conj(a), G, a))
-            tot += val
+            tot = tot + val
             if per_helicity:
                 per.append(val)
         return (tot, np.array(per)) if per_helicity else tot

@@ -69,12 +69,17 @@ class Integrand:
         self.gluon_finals = [i for i, l in enumerate(wl.legs) if not l.incoming and l.particle == "g"]
 
     # ------------------------------------------------------------------
-    def kinematics(self, x):
-        """Momenta [N, n, 4], s-hat, x1, x2, J_x and W for points x [ndim, N]."""
-        x = np.asarray(x, dtype=np.float64)
+    def kinematics(self, x, final_masses=None):
+        """Momenta [N, n, 4], s-hat, x1, x2, J_x and W for points x [ndim, N]
+        (final-state masses as given, else the workload's)."""
+        from oracle.dual import as_f64
+        x = as_f64(x)
         N = x.shape[1]
+        fm = self.final_masses if final_masses is None else final_masses
         if self.wl.beams:
-            x1, x2, tau, jx = ps.xmap(x[0], x[1], self.tau_min)
+            msum = sum(fm[i] for i in range(len(fm)))
+            tau_min = self.tau_min if final_masses is None else msum * msum / self.S
+            x1, x2, tau, jx = ps.xmap(x[0], x[1], tau_min)
             s_hat = tau * self.S
             u = x[2:]
         else:
@@ -85,9 +90,9 @@ class Integrand:
         rs = np.sqrt(s_hat)
         n_out = self.wl.n_out
         p0 = ps.massless_diet(u, rs)
-        k, wfac, ok = ps.massive(p0, self.final_masses, rs)
+        k, wfac, ok = ps.massive(p0, fm, rs)
         w = ps.massless_weight(n_out, s_hat) * wfac
-        p = np.zeros((N, n_out + 2, 4))
+        p = np.zeros((N, n_out + 2, 4), like=k)
         p[:, 0] = np.stack([rs / 2, 0 * rs, 0 * rs, rs / 2], axis=1)
         p[:, 1] = np.stack([rs / 2, 0 * rs, 0 * rs, -rs / 2], axis=1)
         p[:, 2:] = k
@@ -130,6 +135,43 @@ class Integrand:
                            pdf_condition=self._pdf_condition(x1, x2),
                            condition=self.condition(p, s_hat, x1, x2))
         return f
+
+    # ------------------------------------------------------------------
+    # derivatives by forward-mode dual numbers
+    def gradient(self, x):
+        """(f [N], df/dx [ndim, N], df/dm_t [N]) at points x [ndim, N]: the
+        integrand evaluated once in dual arithmetic with tangents along every
+        coordinate of x and along the top mass (which enters the threshold
+        tau_min, the phase-space rescaling, the spinors' momenta and the
+        propagators; mu_F is held at its value).  Cut decisions are taken on
+        values: the derivative is the pathwise one."""
+        from oracle.dual import Dual
+        x = np.asarray(x, dtype=np.float64)
+        ndim, N = x.shape
+        K = ndim + 1
+        dx = np.zeros((ndim, N, K))
+        for j in range(ndim):
+            dx[j, :, j] = 1.0
+        X = Dual(x, dx)
+        mt = Dual(np.array(float(self.m_top)), np.eye(K)[ndim])
+        fm = [mt if m > 0 else Dual(np.array(0.0), np.zeros(K)) for m in self.final_masses]
+        saved = self.proc.masses
+        self.proc.masses = {**saved, "t": mt}
+        try:
+            p, s_hat, x1, x2, jx, w, ok = self.kinematics(X, final_masses=fm)
+            pv = p.v if isinstance(p, Dual) else p
+            keep = ok & self.cuts(pv)
+            f = Dual(np.zeros(N), np.zeros((N, K)))
+            idx = np.nonzero(keep)[0]
+            if len(idx):
+                msq = self.proc.msq_avg(p[idx])
+                lum = 1.0
+                if self.wl.beams:
+                    lum = (self.pdfs[0].f(x1[idx], self.wl.mu_f2) * self.pdfs[1].f(x2[idx], self.wl.mu_f2))
+                f[idx] = jx[idx] * w[idx] * lum * msq / (2.0 * s_hat[idx]) * W.GEV2_TO_PB
+        finally:
+            self.proc.masses = saved
+        return f.v, np.moveaxis(f.d[:, :ndim], 1, 0), f.d[:, ndim]
 
     # ------------------------------------------------------------------
     # leading colour: the diagonal of the colour matrix in the string basis

@@ -24,6 +24,8 @@ import math
 
 import numpy as np
 
+from oracle.dual import as_f64
+
 
 def _hermite(t, h, v0, v1, d0, d1):
     """Cubic Hermite on one interval: values v0, v1 and slopes d0, d1 (per unit
@@ -80,7 +82,7 @@ class PdfTable:
 
     def xfx(self, x, q2):
         """x f(x, Q^2), vectorised."""
-        x = np.atleast_1d(np.asarray(x, dtype=np.float64))
+        x = np.atleast_1d(as_f64(x))
         q2 = np.broadcast_to(np.asarray(q2, dtype=np.float64), x.shape)
         a = np.log(x)
         b = np.log(q2)
@@ -112,7 +114,7 @@ class PdfTable:
         sensitivity to a rounding-sized change of ln x.  Two evaluations of
         the same definition in different operation orders agree to a small
         multiple of eps times this."""
-        x = np.atleast_1d(np.asarray(x, dtype=np.float64))
+        x = np.atleast_1d(as_f64(x))
         q2 = np.broadcast_to(np.asarray(q2, dtype=np.float64), x.shape)
         a, b = np.log(x), np.log(q2)
         i = self._interval(self.a, a)
@@ -153,7 +155,7 @@ class PdfTable:
 
     def f(self, x, q2):
         """Number density f(x, Q^2) = (x f) / x."""
-        x = np.atleast_1d(np.asarray(x, dtype=np.float64))
+        x = np.atleast_1d(as_f64(x))
         return self.xfx(x, q2) / x
 
 

@@ -31,23 +31,25 @@ import math
 
 import numpy as np
 
+from oracle.dual import Dual, as_f64, newton_root, value
+
 
 def massless_weight(n: int, s):
     return ((2.0 * math.pi) ** (4 - 3 * n) * (math.pi / 2.0) ** (n - 1)
-            * np.asarray(s, dtype=np.float64) ** (n - 2)
+            * as_f64(s) ** (n - 2)
             / (math.factorial(n - 1) * math.factorial(n - 2)))
 
 
 def xmap(y1, y2, tau_min: float):
     """(x1, x2, tau, jacobian) from two unit numbers."""
-    if not tau_min > 0.0:
+    if not value(tau_min) > 0.0:
         raise ValueError("the tau map needs a positive threshold")
-    y1 = np.asarray(y1, dtype=np.float64)
-    y2 = np.asarray(y2, dtype=np.float64)
-    tau = np.exp(y1 * math.log(tau_min))
+    y1 = as_f64(y1)
+    y2 = as_f64(y2)
+    tau = np.exp(y1 * np.log(tau_min))
     x1 = np.exp(y2 * np.log(tau))
     x2 = tau / x1
-    jac = tau * math.log(1.0 / tau_min) * np.log(1.0 / tau)
+    jac = tau * np.log(1.0 / tau_min) * np.log(1.0 / tau)
     return x1, x2, tau, jac
 
 
@@ -87,6 +89,14 @@ def _mass_ratio(r, m: int, complement: bool = False):
     r >= 1/2).  With complement=True returns (x, d) with d = 1 - x carried
     to full relative precision (rounding x to a double near 1 would lose it).
     """
+    if isinstance(r, Dual):
+        # the root's value as for plain numbers, its tangent from the implicit
+        # function theorem: dx = dr / F'(x), F'(x) = m (m-1) x^(m-2) (1 - x)
+        xv, dv = _mass_ratio(r.v, m, complement=True)
+        slope = m * (m - 1) * xv ** (m - 2) * dv
+        dx = r.d / np.where(slope > 0, slope, np.inf)[..., None]
+        x = Dual(xv, dx)
+        return (x, Dual(dv, -dx)) if complement else x
     r = np.asarray(r, dtype=np.float64)
     low = _bisect(lambda x: m * x ** (m - 1) - (m - 1) * x ** m, r)
     coef = [(m - 1) * math.comb(m, k) - m * math.comb(m - 1, k) for k in range(m + 1)]
@@ -104,14 +114,15 @@ def massless_diet(u, sqrt_s):
     Step k (k = 0 .. n-2) consumes (cos-theta, phi) and, for k <= n-3, the
     mass-ratio number, in that order.
     """
-    u = np.asarray(u, dtype=np.float64)
+    u = as_f64(u)
     nr, N = u.shape
     n = (nr + 4) // 3
     if 3 * n - 4 != nr or n < 2:
         raise ValueError("need 3n-4 unit numbers with n >= 2")
-    sqrt_s = np.broadcast_to(np.asarray(sqrt_s, dtype=np.float64), (N,))
-    p = np.zeros((N, n, 4))
-    Q = np.zeros((N, 4))
+    sqrt_s = np.broadcast_to(as_f64(sqrt_s), (N,))
+    like = u if isinstance(u, Dual) else sqrt_s
+    p = np.zeros((N, n, 4), like=like)
+    Q = np.zeros((N, 4), like=like)
     Q[:, 0] = sqrt_s
     M = sqrt_s.copy()
     col = 0
@@ -148,24 +159,29 @@ def massive(p, masses, sqrt_s):
     Returns (k [N, n, 4], weight factor relative to the massless weight,
     ok mask).  Events below threshold get ok = False and zero weight.
     """
-    p = np.asarray(p, dtype=np.float64)
+    p = as_f64(p)
     N, n, _ = p.shape
-    m = np.asarray(masses, dtype=np.float64)
-    sqrt_s = np.broadcast_to(np.asarray(sqrt_s, dtype=np.float64), (N,))
+    m = np.stack(list(masses)) if any(isinstance(q, Dual) for q in masses) else np.asarray(masses, dtype=np.float64)
+    sqrt_s = np.broadcast_to(as_f64(sqrt_s), (N,))
     ok = sqrt_s > np.sum(m)
     if np.all(m == 0.0):
         return p.copy(), np.ones(N), ok
     E = p[:, :, 0]
+    mv, Ev, sv = value(m), value(E), value(sqrt_s)
     lo = np.zeros(N)
     hi = np.ones(N)
     for _ in range(200):
         mid = 0.5 * (lo + hi)
-        F = np.sum(np.sqrt(m[None, :] ** 2 + (mid[:, None] * E) ** 2), axis=1) - sqrt_s
+        F = np.sum(np.sqrt(mv[None, :] ** 2 + (mid[:, None] * Ev) ** 2), axis=1) - sv
         below = F < 0.0
         lo = np.where(below, mid, lo)
         hi = np.where(below, hi, mid)
     xi = 0.5 * (lo + hi)
-    k = np.empty_like(p)
+    # dual inputs: the root's tangent by one Newton step in dual arithmetic
+    xi = newton_root(lambda z: np.sum(np.sqrt(m[None, :] ** 2 + (z[:, None] * E) ** 2), axis=1) - sqrt_s,
+                     lambda z: np.sum(z[:, None] * Ev ** 2 / np.sqrt(mv[None, :] ** 2 + (z[:, None] * Ev) ** 2),
+                                      axis=1), xi)
+    k = np.zeros(p.shape, like=xi) if isinstance(xi, Dual) else np.empty_like(p)
     k[:, :, 1:] = xi[:, None, None] * p[:, :, 1:]
     kabs = xi[:, None] * E
     k[:, :, 0] = np.sqrt(m[None, :] ** 2 + kabs ** 2)

@@ -206,8 +206,10 @@ mf_status load_kernel(const std::vector<char> &cubin, Compiled &out, const char 
     g_drv.funcGetAttribute(&stat, CU_FUNC_ATTRIBUTE_SHARED_SIZE_BYTES, out.fn);
     if (g_drv.occupancy(&nb_regs, out.fn, out.block, 0) == CUDA_SUCCESS && nb_regs > 0) {
         const double per_sm = (double)nb_regs * (double)(out.smem + (size_t)stat + 1024);
-        // (a margin above the need: the driver picks a nearby supported size)
+        // (a margin above the need: the driver picks a nearby supported size;
+        // kernels that need most of the SM's shared memory ask for all of it)
         int pct = (int)std::ceil(100.0 * per_sm / (228.0 * 1024.0)) + 10;
+        if (pct > 60) pct = 100;
         if (pct < 1) pct = 1;
         if (pct > 100) pct = 100;
         g_drv.funcSetAttribute(out.fn, CU_FUNC_ATTRIBUTE_PREFERRED_SHARED_MEMORY_CARVEOUT, pct);

@@ -7,7 +7,8 @@
   pathwise derivative);
 * df/dalpha_s = k f / alpha_s against central differences in alpha_s;
 * df/dm_t and df/dx_j against Richardson-extrapolated central differences of
-  the oracle (relative <= 1e-6);
+  the oracle (relative <= 1e-6) and against the oracle's forward-mode dual
+  numbers (relative <= 1e-9);
 * the value it returns against the oracle with the FP64 parity bound;
 * the summed pathwise dsigma/dm_t against the finite difference of sigma over
   the same points, and the boundary term reported separately;
@@ -200,3 +201,23 @@ def test_autograd_wrapper(torch_cuda, procs):
     assert torch.allclose(x.grad, dx / 500, rtol=1e-14, atol=0)
     assert torch.allclose(prm.grad, dp.mean(dim=1), rtol=1e-12)
     assert prm.grad[1].item() == pytest.approx(2 * sigma.item() / wl.alpha_s, rel=1e-12)
+
+
+@pytest.mark.parametrize("name,n", [("ee_mumu", 30), ("gg_ttx", 40), ("uux_ttx", 40), ("gg_ttxg", 20),
+                                    ("uux_ttxg", 20), ("gg_ttxgg", 4)])
+def test_grad_matches_oracle_dual_numbers(torch_cuda, procs, oracle_processes, name, n):
+    # both sides exact to rounding: the GPU's forward tangents plus
+    # hand-written adjoints against the oracle's forward-mode dual numbers
+    from oracle.integrand import Integrand
+    wl = W.WORKLOADS[name]
+    I = Integrand(wl, process=oracle_processes(name))
+    x = np.clip(W.uniform_points(wl.ndim, n, 48), 1e-3, 1 - 1e-3)
+    f, dp, dx = _grad(torch_cuda, procs(name), x)
+    fo, dxo, dmo = I.gradient(x)
+    nz = fo != 0
+    assert np.array_equal(f == 0, fo == 0)
+    err = np.abs(dx - dxo)[:, nz] / (np.abs(dxo) + np.abs(fo))[:, nz]
+    assert err.max() < 1e-9, err.max()
+    mt = wl.m_top
+    errm = np.abs(dp[0] - dmo)[nz] / (np.abs(dmo) + np.abs(fo) / mt)[nz]
+    assert errm.max() < 1e-9, errm.max()
