@@ -229,16 +229,21 @@ def run_native(args):
     n64 = args.fp64_events or min(n_events, 2_000_000)
     step("fp64", n64, refine=False)
     torch.cuda.synchronize()
-    t64 = []
+    t64, k64, r64 = [], [], None
     for _ in range(2):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        step("fp64", n64, refine=False)
+        r64 = step("fp64", n64, refine=False)
         b.record(stream)
         torch.cuda.synchronize()
         t64.append(a.elapsed_time(b))
+        k64.append(api.mf_process_last_kernel_ms(proc.handle))
     fp64_rate = n64 / (min(t64) / 1e3)
+    # the FP64 kernel against the GPU's FP64 rate (nominal 1.25 TFLOP/s on
+    # GB300; no measured figure is available)
+    fl64 = r64["n_nonzero"] * info["n_hel"] * info["flops_per_hel"] + n64 * info["flops_kinematics"]
+    fp64_tflops = fl64 / (min(k64) / 1e3) / 1e12
 
     # per-event agreement of the mixed path with the FP64 path
     x = torch.from_numpy(W.uniform_points(wl.ndim, 20000, 77)).cuda()
@@ -354,7 +359,9 @@ def run_native(args):
                    "colour_flows": info["n_jamp"],
                    "l2": "random numbers generated in-kernel; per-step outputs (w, bins) "
                          f"{n_events * (8 + wl.ndim) / 1e6:.0f} MB > 129 MB L2"},
-        "fp64": {"value": fp64_rate, "unit": "events/s", "events": n64},
+        "fp64": {"value": fp64_rate, "unit": "events/s", "events": n64,
+                 "roofline": {"bound": "alu", "achieved": fp64_tflops, "peak": 1.25, "unit": "TFLOP/s",
+                              "frac": fp64_tflops / 1.25, "peak_source": "nominal GB300 FP64 rate"}},
         "batch": batch,
         "kernel_variants": variants,
         "accuracy": {"median_rel_mixed_vs_fp64": float(np.median(rel)), "max_rel_mixed_vs_fp64": float(rel.max()),
@@ -372,6 +379,7 @@ def run_native(args):
         "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
         "sigma_pb": results[-1]["sigma"], "sigma_err_pb": results[-1]["sigma_error"],
+        "accepted_events_per_s": value * statistics.median([r["n_nonzero"] for r in results]) / n_events,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

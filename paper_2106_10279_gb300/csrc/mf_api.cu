@@ -2,6 +2,7 @@
 // Vegas iteration (accumulation, fixed pairwise-tree reduction over chunks,
 // refinement and the combination of iterations; Sec. 2.2 and Lepage 1978).
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -412,11 +413,12 @@ size_t smem_bytes(const mf_process &p, int prec, int block) {
 
 // Generate, compile and load the process kernel of precision prec with the
 // launch shape (block, ht) into k.
-mf_status compile_shape(mf_process *p, int prec, int block, int ht, mfi::Compiled &k) {
+mf_status compile_shape(mf_process *p, int prec, int block, int ht, mfi::Compiled &k, int min_blocks = -1) {
     k.block = block;
     k.ht = ht;
+    k.min_blocks = min_blocks;
     mfi::GenInfo info;
-    std::string src = mfi::generate_source(*p, prec, k.block, k.ht, info);
+    std::string src = mfi::generate_source(*p, prec, k.block, k.ht, info, "proc", true, min_blocks);
     std::vector<char> cubin;
     mf_status st = mfi::jit_compile(src, prec == MF_FP64 ? "mf_proc_f64.cu" : prec == MF_MIXED ? "mf_proc_mixed.cu"
                                                                                   : "mf_proc_mixed_tc.cu", cubin);
@@ -526,7 +528,13 @@ mf_status launch(mf_process *p, int prec, mf_kparams &kp, cudaStream_t s) {
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    int64_t grid = (int64_t)nsm * k.max_blocks_per_sm;
+    int per_sm = k.max_blocks_per_sm;
+    // launch-shape override (for measurements): resident blocks per SM assumed
+    if (const char *e = std::getenv("MF_BLOCKS_PER_SM")) {
+        int b = std::atoi(e);
+        if (b >= 1 && b <= 8) per_sm = b;
+    }
+    int64_t grid = (int64_t)nsm * per_sm;
     if (grid > ntiles) grid = ntiles;
     if (grid < 1) grid = 1;
     void *args[] = {&kp};
@@ -1455,14 +1463,27 @@ extern "C" mf_status mf_process_tune(mf_process *p, mf_precision prec, int64_t n
     const int nhp = padded_hel(p);
     float best_ms = 0.f;
     mfi::Compiled best;
+    // stage 1: block size x lanes per point; stage 2: a minimum of resident
+    // blocks per SM (fewer registers, more warps) for the best of stage 1
+    std::vector<std::array<int, 3>> shapes;
     for (int bl : {128, 256}) {
         if (prec == MF_MIXED_TC && bl != 128) continue;      // one MMA row per thread of 128
         for (int h : {8, 16, 32}) {
-            if (st != MF_OK) break;
             if (h > nhp && h != 8) continue;
-            const int hh = h <= nhp ? h : nhp;
+            shapes.push_back({bl, h <= nhp ? h : nhp, -1});
+        }
+    }
+    const size_t n_stage1 = shapes.size();
+    for (size_t si = 0; si <= shapes.size(); ++si) {
+        if (si == n_stage1 && best.fn && best.min_blocks < 0)
+            for (int mb : {3, 4}) shapes.push_back({best.block, best.ht, mb});
+        if (si == shapes.size()) break;
+        {
+            const int bl = shapes[si][0], hh = shapes[si][1], mb = shapes[si][2];
+            if (st != MF_OK) break;
+            if (mb > 0 && bl * mb > 1024) continue;
             mfi::Compiled k;
-            st = compile_shape(p, prec, bl, hh, k);
+            st = compile_shape(p, prec, bl, hh, k, mb);
             if (st != MF_OK) break;
             mf_kparams kp;
             vegas_params(p, v, n_sample, 0, 0, 12345, kp);
@@ -1502,7 +1523,7 @@ extern "C" mf_status mf_process_tune(mf_process *p, mf_precision prec, int64_t n
     p->kern[prec] = best;
     // the generated source and counts of the kept shape
     mfi::GenInfo info;
-    p->source[prec] = mfi::generate_source(*p, prec, best.block, best.ht, info);
+    p->source[prec] = mfi::generate_source(*p, prec, best.block, best.ht, info, "proc", true, best.min_blocks);
     p->gen = info;
     if (block) *block = best.block;
     if (ht) *ht = best.ht;

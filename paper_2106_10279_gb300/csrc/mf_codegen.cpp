@@ -131,7 +131,7 @@ void emit_header(std::ostringstream &o, const mf_process &p, GenInfo &info, std:
 }
 
 std::string generate_source(const mf_process &p, int precision, int block, int ht, GenInfo &info, const char *ns,
-                            bool kernel) {
+                            bool kernel, int min_blocks) {
     const char *R = precision == MF_FP64 ? "double" : "float";
     const int n = p.n_legs;
     std::ostringstream o;
@@ -375,15 +375,28 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
     if (kernel) {
         o << "#include \"mf_kernel.cuh\"\n";
         // optional minimum of resident blocks per SM (trades registers for occupancy)
-        int min_blocks = 0;
-        if (const char *e = std::getenv("MF_MIN_BLOCKS")) min_blocks = std::atoi(e);
+        if (min_blocks < 0) {
+            min_blocks = 0;
+            if (const char *e = std::getenv("MF_MIN_BLOCKS")) min_blocks = std::atoi(e);
+        }
         o << "extern \"C\" __global__ void __launch_bounds__(" << block;
         if (min_blocks >= 1 && min_blocks <= 8) o << ", " << min_blocks;
         o << ") mf_kernel(const mf::KParams kp) {\n";
         if (precision == MF_MIXED_TC) o << "  mf::kernel_body_tc<" << ht << ">(kp);\n}\n";
         else o << "  mf::kernel_body<" << R << ", " << block << ", " << ht << ">(kp);\n}\n";
     }
-    info.flops_per_hel = fl;
+    // algorithmic count: every operation of the diagram program once, external
+    // wavefunctions included (the emission above also counts the few
+    // wavefunctions a later program part recomputes), the colour
+    // coefficients' multiply-adds, the colour sum
+    (void)fl;
+    double alg = 0.0;
+    for (const mf_op &op : p.ops) {
+        alg += routine_flops(op.routine);
+        if (op.kind == MF_OP_AMP) alg += 8.0 * op.n_terms;
+    }
+    alg += 4.0 * nj * (nj - 1) / 2 + 6.0 * nj;
+    info.flops_per_hel = alg;
     // kinematics per event (phase space, PDFs, denominators), rough count
     info.flops_kin = 400.0 + 10.0 * info.n_den;
     return o.str();

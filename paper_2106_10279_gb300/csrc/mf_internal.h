@@ -31,6 +31,7 @@ struct Compiled {
     int max_blocks_per_sm = 1;
     int regs = 0;
     size_t local_bytes = 0;
+    int min_blocks = -1;           // __launch_bounds__ minimum (-1: the default)
 };
 
 struct GenInfo {
@@ -138,7 +139,7 @@ mf_status lhe_push(mf_lhe_writer *w, std::vector<double> &&records);
 int lhe_legs(const mf_lhe_writer *w);
 // code generation (mf_codegen.cpp)
 std::string generate_source(const mf_process &p, int precision, int block, int ht, GenInfo &info,
-                            const char *ns = "proc", bool kernel = true);
+                            const char *ns = "proc", bool kernel = true, int min_blocks = -1);
 std::string generate_batch_source(const std::vector<const mf_process *> &ps, int precision, int block,
                                   const std::vector<int> &hts, std::vector<GenInfo> &infos);
 std::string generate_grad_source(const mf_process &p, int block, GenInfo &info);
