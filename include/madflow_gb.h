@@ -317,12 +317,15 @@ mf_status mf_tree_reduce(const double *nodes, int32_t n_nodes, int32_t K, int64_
 
 /* mf_process_tune: time the kernel of precision prec for every launch shape
  * (128 or 256 threads per block; 8, 16 or 32 lanes per event, at most the
- * padded helicity count) on n_sample (>= 1024) Vegas points of a uniform grid
- * and keep the fastest for later calls (and for batches created afterwards).
- * The helicity sum is a fixed pairwise tree whatever the shape, so the
- * results are the same bits for every shape: only the speed changes.  Each
- * shape is compiled once (cached on disk).  *block and *ht (may be NULL)
- * receive the choice.  Synchronous on stream. */
+ * padded helicity count), then for the fastest a compiled-in minimum of 3 or
+ * 4 resident blocks per SM, on n_sample (>= 1024) Vegas points of a uniform
+ * grid, and keep the fastest for later calls (and for batches created
+ * afterwards).  The helicity sum is a fixed pairwise tree whatever the lanes
+ * per point, so block size and lanes never change the results; a minimum of
+ * resident blocks changes the compiler's register budget and with it the
+ * order of a few multiply-adds, i.e. the last bits.  Each shape is compiled
+ * once (cached on disk).  *block and *ht (may be NULL) receive the choice
+ * (mf_process_kernel_info gives the rest).  Synchronous on stream. */
 mf_status mf_process_tune(mf_process *p, mf_precision prec, int64_t n_sample, void *stream, int32_t *block,
                           int32_t *ht);
 
@@ -460,10 +463,11 @@ mf_status mf_process_set_leading_colour(mf_process *p, int32_t on);
 mf_status mf_process_get_helicities(const mf_process *p, int8_t *hel, int32_t *n_hel);
 
 /* The launch shape of the compiled kernel of precision prec: threads per
- * block, lanes per point, registers per thread and resident blocks per SM
- * (any pointer may be NULL); MF_EINVAL if that kernel is not compiled yet. */
+ * block, lanes per point, registers per thread, resident blocks per SM and
+ * the minimum of resident blocks it was compiled for (0: none) (any pointer
+ * may be NULL); MF_EINVAL if that kernel is not compiled yet. */
 mf_status mf_process_kernel_info(const mf_process *p, mf_precision prec, int32_t *block, int32_t *ht,
-                                 int32_t *regs, int32_t *blocks_per_sm);
+                                 int32_t *regs, int32_t *blocks_per_sm, int32_t *min_blocks);
 
 /* mf_process_check: whether a kernel of this process flagged an error: a
  * bounded wait expired (the tensor-core colour sum waits on the completion

@@ -93,7 +93,7 @@ SIGNATURES = {
     "mf_vegas_iterate_static": (c_i32, [C.c_void_p, C.c_void_p, c_i64, C.c_uint64, c_i32, c_i32,
                                         P(mf_iter_result), C.c_void_p]),
     "mf_process_check": (c_i32, [C.c_void_p]),
-    "mf_process_kernel_info": (c_i32, [C.c_void_p, c_i32, P(c_i32), P(c_i32), P(c_i32), P(c_i32)]),
+    "mf_process_kernel_info": (c_i32, [C.c_void_p, c_i32, P(c_i32), P(c_i32), P(c_i32), P(c_i32), P(c_i32)]),
     "mf_process_set_helicity_sampling": (c_i32, [C.c_void_p, c_i32, C.c_uint64]),
     "mf_process_set_leading_colour": (c_i32, [C.c_void_p, c_i32]),
     "mf_process_get_helicities": (c_i32, [C.c_void_p, P(C.c_int8), P(c_i32)]),

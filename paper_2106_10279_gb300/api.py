@@ -393,10 +393,10 @@ class Process:
 
     def kernel_info(self, precision="mixed"):
         """Launch shape of a compiled kernel: block, lanes per point, registers, blocks per SM."""
-        v = [C.c_int32() for _ in range(4)]
+        v = [C.c_int32() for _ in range(5)]
         L.check(L.lib().mf_process_kernel_info(self.handle, _PREC[precision], *[C.byref(x) for x in v]),
                 "mf_process_kernel_info")
-        return dict(zip(("block", "ht", "regs", "blocks_per_sm"), (x.value for x in v)))
+        return dict(zip(("block", "ht", "regs", "blocks_per_sm", "min_blocks"), (x.value for x in v)))
 
     def check(self):
         """Raise if a bounded wait of one of this process's kernels expired."""

@@ -46,13 +46,16 @@ struct mf_kparams {
 };
 
 // Parameters of the batched kernel: several processes' parameter blocks, the
-// tile ranges of the batch (process k owns tiles [start[k], start[k+1])) and
-// the work counter the blocks draw tiles from (zeroed before each launch).
+// work items of the batch (groups of tiles, fewer tiles per item for the
+// costlier processes so that items cost about the same) and the work counter
+// the blocks draw items from (zeroed before each launch).
 #define MF_KP_MAX_BATCH 8
 struct mf_batch_params {
     long long *counter;
     int32_t nproc;
     int32_t pad;
-    long long start[MF_KP_MAX_BATCH + 1];
+    long long start[MF_KP_MAX_BATCH + 1];     // work items of process k: [start[k], start[k+1])
+    long long group[MF_KP_MAX_BATCH];         // tiles per work item of process k
+    long long ntiles[MF_KP_MAX_BATCH];        // tiles of process k
     mf_kparams kp[MF_KP_MAX_BATCH];
 };

@@ -918,7 +918,7 @@ extern "C" mf_status mf_process_set_leading_colour(mf_process *p, int32_t on) {
 }
 
 extern "C" mf_status mf_process_kernel_info(const mf_process *p, mf_precision prec, int32_t *block, int32_t *ht,
-                                            int32_t *regs, int32_t *blocks_per_sm) {
+                                            int32_t *regs, int32_t *blocks_per_sm, int32_t *min_blocks) {
     if (!p) return fail(MF_EINVAL, "NULL process");
     if (!valid_prec(prec)) return fail(MF_EINVAL, "bad precision");
     const mfi::Compiled &k = p->kern[prec];
@@ -927,6 +927,7 @@ extern "C" mf_status mf_process_kernel_info(const mf_process *p, mf_precision pr
     if (ht) *ht = k.ht;
     if (regs) *regs = k.regs;
     if (blocks_per_sm) *blocks_per_sm = k.max_blocks_per_sm;
+    if (min_blocks) *min_blocks = k.min_blocks > 0 ? k.min_blocks : 0;
     return MF_OK;
 }
 
@@ -1536,6 +1537,20 @@ extern "C" mf_status mf_process_tune(mf_process *p, mf_precision prec, int64_t n
 // costliest subprocess first, so that no SM idles while another subprocess's
 // tail finishes), then the per-subprocess accumulation and refinement.
 // ----------------------------------------------------------------------------
+namespace {
+// Work items of batch slot `slot` with n points: groups of tiles sized so
+// that an item of every process costs about as much as one tile of the
+// costliest (the per-item dispatch is then amortised for the cheap ones).
+void set_items(const mf_batch *b, int slot, int64_t n, mf_batch_params &bp) {
+    const int64_t ntiles = (n + b->kern.block - 1) / b->kern.block;
+    int64_t g = (int64_t)std::llround(b->cost[b->order[0]] / std::max(b->cost[b->order[slot]], 1.0));
+    g = std::max<int64_t>(1, std::min<int64_t>(g, 64));
+    bp.group[slot] = g;
+    bp.ntiles[slot] = ntiles;
+    bp.start[slot + 1] = bp.start[slot] + (ntiles + g - 1) / g;
+}
+}  // namespace
+
 extern "C" mf_status mf_batch_create(mf_process *const *procs, int32_t nproc, mf_precision prec, mf_batch **out) {
     if (!out) return fail(MF_EINVAL, "out is NULL");
     *out = nullptr;
@@ -1561,6 +1576,7 @@ extern "C" mf_status mf_batch_create(mf_process *const *procs, int32_t nproc, mf
     cudaGetDevice(&b->device);
     b->precision = prec;
     b->procs.assign(procs, procs + nproc);
+    b->cost = cost;
     b->order.resize(nproc);
     for (int k = 0; k < nproc; ++k) b->order[k] = k;
     std::stable_sort(b->order.begin(), b->order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
@@ -1646,7 +1662,7 @@ extern "C" mf_status mf_batch_iterate(mf_batch *b, mf_vegas *const *grids, const
         mf_status st = ensure_scratch(p, grids[u], n_events[u]);
         if (st != MF_OK) return st;
         vegas_params(p, grids[u], n_events[u], 0, u, seed, bp.kp[slot]);
-        bp.start[slot + 1] = bp.start[slot] + (n_events[u] + b->kern.block - 1) / b->kern.block;
+        set_items(b, slot, n_events[u], bp);
     }
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
@@ -1743,7 +1759,7 @@ mf_status capture_batch(mf_batch *b, mf_vegas *const *grids, const int64_t *n_ev
         const int u = b->order[slot];
         vegas_params(b->procs[u], grids[u], n_events[u], 0, u, seed, bp.kp[slot]);
         bp.kp[slot].iter_dev = b->d_iters + u;
-        bp.start[slot + 1] = bp.start[slot] + (n_events[u] + b->kern.block - 1) / b->kern.block;
+        set_items(b, slot, n_events[u], bp);
     }
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);

@@ -669,9 +669,9 @@ std::string generate_grad_source(const mf_process &p, int block, GenInfo &info) 
 
 // Several processes in one module: each process's program in its own
 // namespace proc<k> with the tile body instantiated for it in body<k>, and one
-// persistent kernel in which every block takes the next tile of the batch
-// from a global counter (tiles of the costliest process first) and runs it
-// with that process's code.
+// persistent kernel in which every block takes the next work item of the
+// batch from a global counter (a group of tiles of one process, items of the
+// costliest process first) and runs it with that process's code.
 std::string generate_batch_source(const std::vector<const mf_process *> &ps, int precision, int block,
                                   const std::vector<int> &hts, std::vector<GenInfo> &infos) {
     const char *R = precision == MF_FP64 ? "double" : "float";
@@ -713,12 +713,14 @@ std::string generate_batch_source(const std::vector<const mf_process *> &ps, int
         o << "        case " << k << ": body" << k << "::load_block_constants<" << R << ", " << block
           << ">(bp.kp[" << k << "], s_grid, cpl, mass_r); break;\n";
     o << "      }\n      __syncthreads();\n      cur = k;\n    }\n"
-      << "    const long long tile = item - bp.start[k];\n"
-      << "    switch (k) {\n";
+      << "    const long long first = (item - bp.start[k]) * bp.group[k];\n"
+      << "    const long long last = first + bp.group[k] < bp.ntiles[k] ? first + bp.group[k] : bp.ntiles[k];\n"
+      << "    for (long long tile = first; tile < last; ++tile) {\n"
+      << "      switch (k) {\n";
     for (size_t k = 0; k < ps.size(); ++k)
-        o << "      case " << k << ": body" << k << "::tile_body<" << R << ", " << block << ", " << hts[k]
+        o << "        case " << k << ": body" << k << "::tile_body<" << R << ", " << block << ", " << hts[k]
           << ">(bp.kp[" << k << "], tile, smem_raw, s_grid, cpl, mass_r); break;\n";
-    o << "    }\n  }\n}\n";
+    o << "      }\n    }\n  }\n}\n";
     return o.str();
 }
 

@@ -110,6 +110,7 @@ struct mf_batch {
     int precision = 0;
     std::vector<mf_process *> procs;   // caller's order
     std::vector<int> order;            // batch slot -> caller's index, costliest first
+    std::vector<double> cost;          // FLOPs per point, caller's order
     mfi::Compiled kern;
     std::string source;
     long long *d_counter = nullptr;    // tile counter of the persistent kernel

@@ -1,7 +1,7 @@
-"""The launch-shape tuner (mf_process_tune): whatever shape it keeps, the
-integrand is the same bits as before tuning (the helicity sum is a fixed
-pairwise tree for every number of lanes per event), and the shape is one of
-the candidates."""
+"""The launch-shape tuner (mf_process_tune): the shape it keeps is one of
+the candidates; block size and lanes per point never change the bits (the
+helicity sum is a fixed pairwise tree for every number of lanes per event);
+a compiled-in minimum of resident blocks may change the last bits only."""
 import numpy as np
 import pytest
 
@@ -30,12 +30,22 @@ def test_tuned_shape_gives_the_same_bits(env, name, prec):
     before = proc.integrand(x, prec).cpu().numpy()
     block, ht = proc.tune(prec, n_sample=100_000)
     assert block in (128, 256) and ht in (8, 16, 32)
+    info = proc.kernel_info(prec)
     after = proc.integrand(x, prec).cpu().numpy()
-    assert np.array_equal(before, after)
-    # a Vegas iteration after tuning: same bits as on an untuned twin
-    twin = api.Process.from_workload(wl)
-    ga, gb = api.Vegas(wl.ndim), api.Vegas(wl.ndim)
-    ra = ga.iterate(proc, 50_000, 3, prec)
-    rb = gb.iterate(twin, 50_000, 3, prec)
-    assert ra == rb
-    assert np.array_equal(ga.grid, gb.grid)
+    assert np.array_equal(before == 0, after == 0)
+    if info["min_blocks"] == 0:
+        assert np.array_equal(before, after)
+    else:
+        nz = before != 0
+        assert np.max(np.abs(after[nz] / before[nz] - 1)) < (1e-12 if prec == "fp64" else 1e-5)
+    # an untuned twin with the same block and lanes gives the same bits
+    import os
+    os.environ["MF_BLOCK"], os.environ["MF_HT"] = str(block), str(ht)
+    os.environ["MF_MIN_BLOCKS"] = str(info["min_blocks"])
+    try:
+        twin = api.Process.from_workload(wl)
+        twin_f = twin.integrand(x, prec).cpu().numpy()
+    finally:
+        for k in ("MF_BLOCK", "MF_HT", "MF_MIN_BLOCKS"):
+            os.environ.pop(k, None)
+    assert np.array_equal(after, twin_f)
