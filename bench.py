@@ -242,7 +242,7 @@ def run_native(args):
     fp64_rate = n64 / (min(t64) / 1e3)
     # the FP64 kernel against the GPU's FP64 rate (nominal 1.25 TFLOP/s on
     # GB300; no measured figure is available)
-    fl64 = r64["n_nonzero"] * info["n_hel"] * info["flops_per_hel"] + n64 * info["flops_kinematics"]
+    fl64 = r64["n_nonzero"] / world * info["n_hel"] * info["flops_per_hel"] + n64 * info["flops_kinematics"]
     fp64_tflops = fl64 / (min(k64) / 1e3) / 1e12
 
     # per-event agreement of the mixed path with the FP64 path
@@ -330,7 +330,9 @@ def run_native(args):
 
     # roofline of the dominant kernel: algorithmic FLOPs / its device time
     kms = statistics.median(kernel_ms)
-    passing = statistics.median([r["n_nonzero"] for r in results])
+    # (an iteration's counts cover all ranks; the kernel timed is this rank's)
+    passing = statistics.median([r["n_nonzero"] for r in results]) / world
+    info = proc.info                   # FLOP counts of the program as compiled
     flops = passing * info["n_hel"] * info["flops_per_hel"] + n_events * info["flops_kinematics"]
     achieved = flops / (kms / 1e3) / 1e12
     peaks = _peaks()
@@ -379,7 +381,7 @@ def run_native(args):
         "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
         "sigma_pb": results[-1]["sigma"], "sigma_err_pb": results[-1]["sigma_error"],
-        "accepted_events_per_s": value * statistics.median([r["n_nonzero"] for r in results]) / n_events,
+        "accepted_events_per_s": value * statistics.median([r["n_nonzero"] for r in results]) / (world * n_events),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

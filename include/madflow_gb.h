@@ -400,6 +400,11 @@ mf_status mf_lhe_close(mf_lhe_writer *w, int64_t *n_written);
 mf_status mf_vegas_unweight(mf_vegas *v, mf_process *p, int64_t n_events, uint64_t seed, int32_t subprocess,
                             mf_precision prec, double w_max, mf_lhe_writer *lhe, double *records, int64_t capacity,
                             int64_t *n_accepted, void *stream);
+/* mf_process_read_weights: the weights w = f J_V of chosen points (host
+ * idx[n], point indices of the pass) of the process's last Vegas pass, into
+ * host w[n] (for checking single points of a large iteration).  Synchronous
+ * on the legacy default stream. */
+mf_status mf_process_read_weights(mf_process *p, const int64_t *idx, int64_t n, double *w);
 /* mf_process_max_weight: max |w| over the points of the process's last
  * Vegas pass (mf_vegas_iterate, shard or unweighting pass).  Synchronous. */
 mf_status mf_process_max_weight(mf_process *p, double *w_max, void *stream);

@@ -352,7 +352,11 @@ class Process:
     def __init__(self, desc: Descriptor):
         self.desc = desc
         self.handle = mf_create_process(desc)
-        self.info = mf_process_get_info(self.handle)
+
+    @property
+    def info(self):
+        """Counts of the process (FLOPs as of the kernel compiled last)."""
+        return mf_process_get_info(self.handle)
 
     @classmethod
     def from_workload(cls, wl, **kw):
@@ -536,6 +540,15 @@ def unweight(grid: "Vegas", proc: "Process", n_events: int, seed: int, w_max: fl
                                    C.byref(nacc), _stream_ptr(stream))
     L.check(st, "mf_vegas_unweight")
     return nacc.value, rec[:min(nacc.value, cap)]
+
+
+def read_weights(proc: "Process", idx):
+    """Weights w = f J_V of the given point indices of the last Vegas pass."""
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    w = np.zeros(idx.shape[0])
+    L.check(L.lib().mf_process_read_weights(proc.handle, idx.ctypes.data_as(C.POINTER(C.c_int64)), idx.shape[0],
+                                            w.ctypes.data_as(C.POINTER(C.c_double))), "mf_process_read_weights")
+    return w
 
 
 def max_weight(proc: "Process", stream=None) -> float:

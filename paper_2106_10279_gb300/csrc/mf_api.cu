@@ -1923,6 +1923,34 @@ __global__ void max_abs_kernel(const double *w, int64_t n, unsigned long long *o
 }
 }  // namespace
 
+namespace {
+__global__ void gather_kernel(const double *w, const int64_t *idx, int64_t n, double *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = w[idx[i]];
+}
+}  // namespace
+
+extern "C" mf_status mf_process_read_weights(mf_process *p, const int64_t *idx, int64_t n, double *w) {
+    if (!p || (n > 0 && (!idx || !w)) || n < 0) return fail(MF_EINVAL, "bad arguments");
+    for (int64_t i = 0; i < n; ++i)
+        if (idx[i] < 0 || idx[i] >= p->last_n) return fail(MF_EINVAL, "point index outside the last pass");
+    if (n == 0) return MF_OK;
+    int64_t *d_idx = nullptr;
+    double *d_out = nullptr;
+    cudaError_t e = cudaMalloc(&d_idx, sizeof(int64_t) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&d_out, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMemcpy(d_idx, idx, sizeof(int64_t) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        gather_kernel<<<(unsigned)((n + 255) / 256), 256>>>(p->d_w, d_idx, n, d_out);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(w, d_out, sizeof(double) * n, cudaMemcpyDeviceToHost);
+    cudaFree(d_idx);
+    cudaFree(d_out);
+    if (e != cudaSuccess) return fail(MF_ECUDA, std::string("reading weights: ") + cudaGetErrorString(e));
+    return MF_OK;
+}
+
 extern "C" mf_status mf_process_max_weight(mf_process *p, double *w_max, void *stream) {
     if (!p || !w_max) return fail(MF_EINVAL, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
