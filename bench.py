@@ -32,7 +32,8 @@ METRIC = "events/s of gg→tt̄g(g) LO integrand: mixed/batched vs FP64 at ≤1e
 # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of a
 # 1e6-point gg->tt~gg iteration divided by its points (the traffic grows with
 # the points; the capture's kernel is the one built from this source)
-KERNEL_DRAM_BYTES_PER_POINT = {("gg_ttxgg", "mixed"): (1.031936e6 + 12.530688e6) / 1e6}
+# (empty until the kernel with helicity pairs has been captured)
+KERNEL_DRAM_BYTES_PER_POINT = {}
 WORKLOAD = "gg_ttxgg"
 
 
@@ -242,7 +243,7 @@ def run_native(args):
     fp64_rate = n64 / (min(t64) / 1e3)
     # the FP64 kernel against the GPU's FP64 rate (nominal 1.25 TFLOP/s on
     # GB300; no measured figure is available)
-    fl64 = r64["n_nonzero"] / world * info["n_hel"] * info["flops_per_hel"] + n64 * info["flops_kinematics"]
+    fl64 = r64["n_nonzero"] / world * info["flops_helicity_sum"] + n64 * info["flops_kinematics"]
     fp64_tflops = fl64 / (min(k64) / 1e3) / 1e12
 
     # per-event agreement of the mixed path with the FP64 path
@@ -333,7 +334,9 @@ def run_native(args):
     # (an iteration's counts cover all ranks; the kernel timed is this rank's)
     passing = statistics.median([r["n_nonzero"] for r in results]) / world
     info = proc.info                   # FLOP counts of the program as compiled
-    flops = passing * info["n_hel"] * info["flops_per_hel"] + n_events * info["flops_kinematics"]
+    # (the helicity sum as evaluated: a helicity pair computes the
+    # wavefunctions that do not depend on its pair leg once)
+    flops = passing * info["flops_helicity_sum"] + n_events * info["flops_kinematics"]
     achieved = flops / (kms / 1e3) / 1e12
     peaks = _peaks()
     sm_max = (peaks.get("sm_max_mhz") or 2070.0)
@@ -375,6 +378,7 @@ def run_native(args):
                      "traffic_note": "bytes per launch, scaled by points from a 1e6-point ncu capture; "
                                      f"algorithmic output {n_events * (8 + wl.ndim) / 1e6:.0f} MB",
                      "kernel": "mf_kernel (fused integrand)", "kernel_ms": kms,
+                     "flops_per_passing_point": info["flops_helicity_sum"], "helicity_pairs": info["n_pairs"],
                      "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"},
         "cpu_baseline": cpu,
         "clocks": clk,

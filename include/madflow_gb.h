@@ -185,6 +185,10 @@ typedef struct {
     int32_t n_den;           /* distinct propagator denominators per event */
     double flops_per_hel;    /* algorithmic FLOPs of one helicity (program + colour sum) */
     double flops_kinematics; /* algorithmic FLOPs per event outside the helicity loop */
+    int32_t pair_leg;        /* leg at which paired helicities differ, -1: helicities one by one */
+    int32_t n_pairs;         /* helicity pairs evaluated per event (0: no pairs) */
+    double flops_helicity_sum; /* FLOPs of one event's helicity sum as evaluated (pairs share
+                                * the wavefunctions that do not depend on pair_leg) */
 } mf_process_info;
 
 mf_status mf_process_get_info(const mf_process *p, mf_process_info *info);

@@ -50,7 +50,8 @@ class mf_process_desc(C.Structure):
 class mf_process_info(C.Structure):
     _fields_ = [("ndim", c_i32), ("n_legs", c_i32), ("n_hel", c_i32), ("n_hel_all", c_i32),
                 ("n_jamp", c_i32), ("n_ops", c_i32), ("n_den", c_i32),
-                ("flops_per_hel", C.c_double), ("flops_kinematics", C.c_double)]
+                ("flops_per_hel", C.c_double), ("flops_kinematics", C.c_double),
+                ("pair_leg", c_i32), ("n_pairs", c_i32), ("flops_helicity_sum", C.c_double)]
 
 
 class mf_lhe_init(C.Structure):

@@ -151,6 +151,38 @@ MF_DEV cx<R> FFV_AMP(const W<R> &row, const W<R> &col, const W<R> &V, cx<R> g) {
     return g * s;
 }
 
+// Two amplitudes of a helicity pair that share everything but one external
+// spinor: row_a and row_b (the row spinor differs) share (V-slash) col, and
+// col_a and col_b (the column spinor differs) share row (V-slash).
+template <typename R>
+struct A2 {
+    cx<R> a, b;
+};
+
+template <typename R>
+MF_DEV A2<R> FFV_AMP_R2(const W<R> &row_a, const W<R> &row_b, const W<R> &col, const W<R> &V, cx<R> g) {
+    cx<R> t[4];
+    vslash_col(V.c, col.c, t);
+    cx<R> sa = row_a.c[0] * t[0], sb = row_b.c[0] * t[0];
+    for (int k = 1; k < 4; ++k) {
+        sa = cfma(row_a.c[k], t[k], sa);
+        sb = cfma(row_b.c[k], t[k], sb);
+    }
+    return A2<R>{g * sa, g * sb};
+}
+
+template <typename R>
+MF_DEV A2<R> FFV_AMP_C2(const W<R> &row, const W<R> &col_a, const W<R> &col_b, const W<R> &V, cx<R> g) {
+    cx<R> t[4];
+    vslash_row(row.c, V.c, t);
+    cx<R> sa = t[0] * col_a.c[0], sb = t[0] * col_b.c[0];
+    for (int k = 1; k < 4; ++k) {
+        sa = cfma(t[k], col_a.c[k], sa);
+        sb = cfma(t[k], col_b.c[k], sb);
+    }
+    return A2<R>{g * sa, g * sb};
+}
+
 // P: momentum of the new current (into the diagram through its legs)
 template <typename R>
 MF_DEV W<R> FFV_FIN(const W<R> &col, const W<R> &V, cx<R> g, R M, R inv_den, const R *P) {
@@ -279,6 +311,14 @@ template <typename R, int S>
 MF_NOINL W<R> nVVVV_VEC(W<R> A, W<R> B, W<R> Cv, cx<R> g, R inv_den) { return VVVV_VEC<R, S>(A, B, Cv, g, inv_den); }
 template <typename R>
 MF_NOINL cx<R> nFFV_AMP(W<R> row, W<R> col, W<R> V, cx<R> g) { return FFV_AMP<R>(row, col, V, g); }
+template <typename R>
+MF_NOINL A2<R> nFFV_AMP_R2(W<R> row_a, W<R> row_b, W<R> col, W<R> V, cx<R> g) {
+    return FFV_AMP_R2<R>(row_a, row_b, col, V, g);
+}
+template <typename R>
+MF_NOINL A2<R> nFFV_AMP_C2(W<R> row, W<R> col_a, W<R> col_b, W<R> V, cx<R> g) {
+    return FFV_AMP_C2<R>(row, col_a, col_b, V, g);
+}
 template <typename R>
 MF_NOINL cx<R> nVVV_AMP(W<R> A, W<R> B, W<R> Cv, R a0, R a1, R a2, R a3, R b0, R b1, R b2, R b3, R c0, R c1, R c2,
                         R c3, cx<R> g) {

@@ -291,10 +291,14 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
             // block of helicities; with helicity sampling one lane per point
             // and its sampled helicity (one call site of the program either way)
             const bool samp = kp.hel_sample != 0;
+            // helicity pairs (summed helicities of modes 0 and 1): each lane
+            // evaluates whole pairs, whose two |M|^2 are consecutive leaves
+            // of the summation tree
+            const bool pairs = PAIR_LEG >= 0 && !TC && !samp && kp.mode <= 1 && kp.npairs > 0;
             const int EPR = samp ? BLOCK : BLOCK / HT;  // points per round
             const int sub = samp ? 0 : tid % HT;
-            const int nhp = kp.nhel_pow2;       // padded helicity count (power of two)
-            const int per = samp ? 1 : (nhp >= HT ? nhp / HT : 1);   // helicities per lane
+            const int nhp = pairs ? kp.npairs_pow2 : kp.nhel_pow2;   // padded units (power of two)
+            const int per = samp ? 1 : (nhp >= HT ? nhp / HT : 1);   // units per lane
             // every thread runs the program the same number of times (lanes
             // without an event or a helicity compute on a valid stand-in and
             // discard it), so that the program may contain block barriers
@@ -307,7 +311,20 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
                 const int hs = (samp && valid) ? (int)s_msq[ev] : 0;
                 const R *ms = s_mom + ev * NLEG * 4;
                 const R *idn = s_den + ev * NDEN1;
-                for (int k = 0; k < per; ++k) {
+                if constexpr (PAIR_LEG >= 0 && !TC) {
+                    if (pairs) {
+                        for (int k = 0; k < per; ++k) {
+                            const int u = sub * per + k;
+                            const bool uv = u < kp.npairs;
+                            const uint8_t ia = kp.pairs[uv ? u : 0][0], ib = kp.pairs[uv ? u : 0][1];
+                            R va, vb;
+                            helicity_pair_msq<R>(ms, idn, kp.hel[ia != 0xFF ? ia : ib], cpl, mass_r, va, vb);
+                            ps.add((uv && valid && ia != 0xFF) ? (double)va : 0.0);
+                            ps.add((uv && valid && ib != 0xFF) ? (double)vb : 0.0);
+                        }
+                    }
+                }
+                for (int k = 0; k < (pairs ? 0 : per); ++k) {
                     const int h = samp ? hs : sub * per + k;
                     const bool hv = h < kp.nhel;
                     double v = helicity_value<R, TC>(kp, ms, idn, kp.hel[hv ? h : 0], cpl, mass_r, tcs);

@@ -38,11 +38,17 @@ struct mf_kparams {
     int *err;                  // device error flag (expired waits), may be NULL
     const int64_t *idx;        // mode 3: global point indices
     int32_t hel_sample;        // 1: one helicity per point, drawn uniformly, f scaled by nhel
+    int32_t npairs;            // modes 0, 1: helicity pairs in pairs[] (0: one helicity at a time)
+    int32_t npairs_pow2;       // a power of two >= npairs
     int32_t pad3;
     const long long *iter_dev; // if set, the iteration index is read here (graph replays)
     double masses[8];
     double couplings[16];      // 8 complex couplings (re, im)
     int8_t hel[MF_KP_MAX_HEL][8];
+    // rows of hel[] forming a pair (same helicities except at the process's
+    // pair leg, -1 in the first member and +1 in the second); 0xFF: the row
+    // is absent (that helicity vanishes)
+    uint8_t pairs[MF_KP_MAX_HEL][2];
 };
 
 // Parameters of the batched kernel: several processes' parameter blocks, the

@@ -442,17 +442,40 @@ size_t smem_bytes_tc(const mf_process &p) {
     return tile + 2 * (size_t)128 * KP * 4 + (size_t)NP * KP * 4 + 16;
 }
 
-int padded_hel(const mf_process *p) {
-    int nhp = 1;
-    while (nhp < (int)(p->hel_all.size() / p->n_legs)) nhp <<= 1;
-    return nhp;
+int pow2_at_least(int n) {
+    int v = 1;
+    while (v < n) v <<= 1;
+    return v;
+}
+
+// Units of helicity work the lanes of one point share (a power of two): the
+// helicity pairs if the process uses them, else its helicities.  Before the
+// vanishing helicities are known (the double-precision kernel compiled at
+// creation), half the unfiltered count when a pair leg exists.
+int lane_units(const mf_process *p) {
+    if (!p->hel.empty())
+        return p->pairs.empty() ? pow2_at_least((int)(p->hel.size() / p->n_legs)) : pow2_at_least((int)p->pairs.size() / 2);
+    const int all = pow2_at_least((int)(p->hel_all.size() / p->n_legs));
+    return (mfi::pair_leg(*p) >= 0 && all > 1) ? all / 2 : all;
+}
+
+// FLOPs of one point's helicity sum as evaluated: the pair program for each
+// complete pair, one helicity's program for a pair with an absent member
+// (the absent member's work is padding), or every helicity in full.
+double helicity_sum_flops(const mf_process *p) {
+    const double fh = p->gen.flops_per_hel;
+    if (p->pairs.empty()) return fh * (double)(p->hel.size() / p->n_legs);
+    double f = 0.0;
+    for (size_t u = 0; u < p->pairs.size(); u += 2)
+        f += (p->pairs[u] != 0xFF && p->pairs[u + 1] != 0xFF) ? p->gen.flops_pair : fh;
+    return f;
 }
 
 mf_status compile_precision(mf_process *p, int prec) {
     mfi::Compiled &k = p->kern[prec];
     if (k.fn) return MF_OK;
     int block = 128;
-    const int nhp = padded_hel(p);
+    const int nhp = lane_units(p);
     int ht = nhp < 32 ? nhp : 32;
     // launch-shape overrides: block size and lanes per event
     if (const char *e = std::getenv("MF_BLOCK")) {
@@ -497,7 +520,44 @@ void fill_common(const mf_process &p, mf_kparams &kp) {
     kp.alpha_s_power = p.alpha_s_power;
     kp.err = p.d_err;
     kp.hel_sample = p.hel_sample;
+    kp.npairs = (int32_t)(p.pairs.size() / 2);
+    kp.npairs_pow2 = pow2_at_least(kp.npairs);
+    for (int u = 0; u < kp.npairs; ++u) {
+        kp.pairs[u][0] = p.pairs[2 * u];
+        kp.pairs[u][1] = p.pairs[2 * u + 1];
+    }
     kp.seed = p.hel_seed;          // Vegas passes overwrite it with their own key
+}
+
+// Pairs of kept helicities that differ only at the pair leg L, in the order
+// of their first row; used when the padded pairs cost fewer FLOPs than the
+// padded single helicities (every thread evaluates the padded count).
+void build_pairs(mf_process *p) {
+    p->pairs.clear();
+    const int L = p->gen.pair_leg, n = p->n_legs;
+    const int nh = (int)(p->hel.size() / n);
+    if (L < 0 || nh == 0) return;
+    if (const char *e = std::getenv("MF_HEL_PAIRS"))       // measurement switch: 0 = helicities one by one
+        if (std::atoi(e) == 0) return;
+    std::vector<uint8_t> t;
+    std::vector<std::vector<int8_t>> keys;
+    for (int h = 0; h < nh; ++h) {
+        const int8_t *row = &p->hel[(size_t)h * n];
+        if (row[L] != -1 && row[L] != 1) return;
+        std::vector<int8_t> key(row, row + n);
+        key[L] = 0;
+        size_t u = 0;
+        while (u < keys.size() && keys[u] != key) ++u;
+        if (u == keys.size()) {
+            keys.push_back(key);
+            t.push_back(0xFF);
+            t.push_back(0xFF);
+        }
+        t[2 * u + (row[L] == 1)] = (uint8_t)h;
+    }
+    const double single = p->gen.flops_per_hel * pow2_at_least(nh);
+    const double paired = p->gen.flops_pair * pow2_at_least((int)keys.size());
+    if (paired < single) p->pairs = t;
 }
 
 bool valid_prec(int prec) { return prec == MF_FP64 || prec == MF_MIXED || prec == MF_MIXED_TC; }
@@ -789,6 +849,7 @@ extern "C" mf_status mf_create_process(const mf_process_desc *d, mf_process **ou
                 for (int l = 0; l < n; ++l) p->hel.push_back(p->hel_all[(size_t)h * n + l]);
         }
     }
+    build_pairs(p);
     *out = p;
     return MF_OK;
 }
@@ -890,6 +951,9 @@ extern "C" mf_status mf_process_get_info(const mf_process *p, mf_process_info *i
     info->n_den = p->gen.n_den;
     info->flops_per_hel = p->gen.flops_per_hel;
     info->flops_kinematics = p->gen.flops_kin;
+    info->pair_leg = p->pairs.empty() ? -1 : p->gen.pair_leg;
+    info->n_pairs = (int32_t)(p->pairs.size() / 2);
+    info->flops_helicity_sum = helicity_sum_flops(p);
     return MF_OK;
 }
 
@@ -1461,7 +1525,7 @@ extern "C" mf_status mf_process_tune(mf_process *p, mf_precision prec, int64_t n
     cudaEvent_t a = nullptr, b = nullptr;
     if (st == MF_OK && (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess))
         st = fail(MF_ECUDA, "events");
-    const int nhp = padded_hel(p);
+    const int nhp = lane_units(p);
     float best_ms = 0.f;
     mfi::Compiled best;
     // stage 1: block size x lanes per point; stage 2: a minimum of resident
@@ -1568,8 +1632,7 @@ extern "C" mf_status mf_batch_create(mf_process *const *procs, int32_t nproc, mf
         mf_status st = compile_precision(procs[k], prec);          // also fixes HT and the FLOP counts
         if (st != MF_OK) return st;
         hts[k] = procs[k]->kern[prec].ht;
-        cost[k] = procs[k]->gen.flops_per_hel * (double)(procs[k]->hel.size() / procs[k]->n_legs) +
-                  procs[k]->gen.flops_kin;
+        cost[k] = helicity_sum_flops(procs[k]) + procs[k]->gen.flops_kin;
     }
     mf_batch *b = new (std::nothrow) mf_batch();
     if (!b) return fail(MF_ENOMEM, "host allocation");

@@ -42,6 +42,39 @@ double routine_flops(int r) {
 
 }  // namespace
 
+// FLOPs of the wavefunctions whose momentum does not flow through `leg`
+// (the part of the program two helicities differing only at `leg` share).
+double shared_flops(const mf_process &p, int leg) {
+    std::vector<uint32_t> m(p.ops.size(), 0);
+    double f = 0.0;
+    for (size_t k = 0; k < p.ops.size(); ++k) {
+        const mf_op &op = p.ops[k];
+        if (op.kind == MF_OP_AMP) continue;
+        if (op.kind == MF_OP_EXT) m[k] = 1u << op.leg;
+        for (int q = 0; q < 4; ++q)
+            if (op.in[q] >= 0) m[k] |= m[op.in[q]];
+        if (!(m[k] >> leg & 1)) f += routine_flops(op.routine);
+    }
+    return f;
+}
+
+// The leg whose helicity the fewest wavefunctions depend on (the most FLOPs
+// shared by a pair of helicities differing only there; lowest index on
+// ties), or -1 if no current is independent of every leg.
+int pair_leg(const mf_process &p) {
+    int best = -1;
+    double bf = 0.0;
+    for (int l = 0; l < p.n_legs; ++l) {
+        double f = shared_flops(p, l);
+        // the other legs' external wavefunctions alone are not worth a pair
+        double ext = 0.0;
+        for (const mf_op &op : p.ops)
+            if (op.kind == MF_OP_EXT && op.leg != l) ext += routine_flops(op.routine);
+        if (f > ext && f > bf) { best = l; bf = f; }
+    }
+    return best;
+}
+
 // Includes, the process constants and the double-precision propagator
 // denominators (shared by the integrand and the gradient sources).
 void emit_header(std::ostringstream &o, const mf_process &p, GenInfo &info, std::vector<uint32_t> &mask,
@@ -141,11 +174,18 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
     // routine's code instead of one per use.  The program then fits the
     // instruction caches far better (the inlined form is fetch-bound), at the
     // price of argument passing.  MF_CALL_ROUTINES=0 inlines them.
-    const bool calls = !(std::getenv("MF_CALL_ROUTINES") && std::atoi(std::getenv("MF_CALL_ROUTINES")) == 0);
-    auto rt = [&](const char *name) { return std::string(calls ? "n" : "") + name; };
-    auto a4 = [&](const char *name) {
-        if (!calls) return std::string(name);
+    // (MF_CALL_ROUTINES=2 inlines the amplitude routines and calls the
+    // currents, =3 the other way round: measurement variants)
+    const int call_mode = std::getenv("MF_CALL_ROUTINES") ? std::atoi(std::getenv("MF_CALL_ROUTINES")) : 1;
+    const bool calls = call_mode != 0;
+    auto rt = [&](const char *name) {
+        const bool amp = std::string(name).find("_AMP") != std::string::npos;
+        const bool call = call_mode == 1 || (call_mode == 2 && !amp) || (call_mode == 3 && amp);
+        return std::string(call ? "n" : "") + name;
+    };
+    auto a4r = [&](const char *routine, const char *name) {
         std::string n(name);
+        if (rt(routine)[0] != 'n') return n;
         return n + "[0], " + n + "[1], " + n + "[2], " + n + "[3]";
     };
 
@@ -222,75 +262,160 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
     // very large functions, so the program is cut into pieces below a size
     // budget; each part recomputes the few shared wavefunctions it needs.
     // Called routines keep the program small enough for twice the budget.
+    //
+    // Two programs are emitted: one helicity, and a pair of helicities that
+    // differ only in the helicity of leg L = pair_leg(p).  In the pair form
+    // every wavefunction whose momentum does not flow through leg L is the
+    // same for both members and is computed once; the others (and every
+    // amplitude) twice, the second copy carrying the suffix _b.
+    const int L = pair_leg(p);
+    int sync_every = 0;
+    if (const char *e = std::getenv("MF_SYNC_EVERY")) sync_every = std::atoi(e);
+    auto M = [&](int id) { return id >= 0 ? "mass[" + std::to_string(id) + "]" : std::string("R(0)"); };
+    auto emit_program = [&](const bool pair) {
+    auto dep = [&](int k) { return pair && (p.ops[k].kind == MF_OP_AMP || (mask[k] >> L & 1)); };
+    auto nm = [&](int k, const char *sfx) { return "w" + std::to_string(k) + (dep(k) ? sfx : ""); };
     double weight = 0.0;
-    for (auto &op : p.ops) weight += routine_flops(op.routine);
+    for (size_t k = 0; k < p.ops.size(); ++k) weight += routine_flops(p.ops[k].routine) * (dep((int)k) ? 2 : 1);
     if (precision == MF_FP64) weight *= 2.0;
     int parts = (int)std::ceil(weight / (calls ? 64000.0 : 32000.0));
     if (const char *e = std::getenv("MF_PROGRAM_PARTS")) parts = std::atoi(e);
     if (parts < 1) parts = 1;
     if (parts > (int)order.size()) parts = (int)order.size();
-    info.parts = parts;
-    int sync_every = 0;
-    if (const char *e = std::getenv("MF_SYNC_EVERY")) sync_every = std::atoi(e);
-    // emission: each wavefunction just before the first amplitude needing it
-    double fl = 0.0;
-    auto M = [&](int id) { return id >= 0 ? "mass[" + std::to_string(id) + "]" : std::string("R(0)"); };
+    if (!pair) info.parts = parts;
+    const std::string fn = pair ? "program_pair_part" : "program_part";
+    // one wavefunction (suffix "" or "_b": which member's inputs it takes)
+    auto emit_one = [&](int k, const char *sfx) {
+        const mf_op &op = p.ops[k];
+        const std::string wk = "w" + std::to_string(k) + sfx;
+        if (op.kind == MF_OP_EXT) {
+            int l = op.leg;
+            // leg L of a pair: member a has helicity -1, member b +1
+            const std::string h = (pair && l == L) ? (sfx[0] ? "1" : "-1") : "hel[" + std::to_string(l) + "]";
+            if (op.routine == MF_R_VXX) {
+                o << "  const W<R> " << wk << " = vxx<R>(ms + " << 4 * l << ", " << h << ", "
+                  << (p.leg_incoming[l] ? 1 : 0) << ");\n";
+            } else {
+                // column: u (incoming particle) or v (outgoing antiparticle);
+                // row: u-bar (outgoing particle) or v-bar (incoming antiparticle)
+                int anti = (op.routine == MF_R_IXX) ? (p.leg_incoming[l] ? 0 : 1) : (p.leg_incoming[l] ? 1 : 0);
+                o << "  const W<R> " << wk << " = " << (op.routine == MF_R_IXX ? "ixx" : "oxx") << "<R>(ms + " << 4 * l
+                  << ", " << M(p.leg_mass_id[l]) << ", " << h << ", " << anti << ");\n";
+            }
+            return;
+        }
+        std::string g = "cpl[" + std::to_string(op.coupling) + "]";
+        std::string den = "idn[" + std::to_string(info.op_den[k]) + "]";
+        auto in = [&](int q) { return nm(op.in[q], sfx); };
+        o << "  W<R> " << wk << ";\n  {\n";
+        switch (op.routine) {
+            case MF_R_FFV_FIN:
+            case MF_R_FFV_FOUT:
+                o << mom(mask[k], "P");
+                o << "    " << wk << " = " << rt(op.routine == MF_R_FFV_FIN ? "FFV_FIN" : "FFV_FOUT") << "<R>("
+                  << in(0) << ", " << in(1) << ", " << g << ", " << M(op.mass_id) << ", " << den << ", "
+                  << a4r("FFV_FIN", "P") << ");\n";
+                break;
+            case MF_R_FFV_VEC:
+                o << "    " << wk << " = " << rt("FFV_VEC") << "<R>(" << in(0) << ", " << in(1) << ", " << g << ", "
+                  << den << ");\n";
+                break;
+            case MF_R_VVV_VEC:
+                o << mom(mask[op.in[0]], "kA") << mom(mask[op.in[1]], "kB");
+                o << "    " << wk << " = " << rt("VVV_VEC") << "<R>(" << in(0) << ", " << in(1) << ", "
+                  << a4r("VVV_VEC", "kA") << ", " << a4r("VVV_VEC", "kB") << ", " << g << ", " << den << ");\n";
+                break;
+            default:
+                o << "    " << wk << " = " << rt("VVVV_VEC") << "<R, " << (op.routine - MF_R_VVVV1_VEC + 1) << ">("
+                  << in(0) << ", " << in(1) << ", " << in(2) << ", " << g << ", " << den << ");\n";
+                break;
+        }
+        o << "  }\n";
+    };
+    // emission: each wavefunction (both copies in a pair) just before the
+    // first amplitude needing it
     std::function<void(int)> emit_wf = [&](int k) {
         if (done[k]) return;
         const mf_op &op = p.ops[k];
         for (int q = 0; q < 4; ++q)
             if (op.in[q] >= 0) emit_wf(op.in[q]);
         done[k] = 1;
-        fl += routine_flops(op.routine);
-        if (op.kind == MF_OP_EXT) {
-            int l = op.leg;
-            if (op.routine == MF_R_VXX) {
-                o << "  const W<R> w" << k << " = vxx<R>(ms + " << 4 * l << ", hel[" << l << "], "
-                  << (p.leg_incoming[l] ? 1 : 0) << ");\n";
-            } else {
-                // column: u (incoming particle) or v (outgoing antiparticle);
-                // row: u-bar (outgoing particle) or v-bar (incoming antiparticle)
-                int anti = (op.routine == MF_R_IXX) ? (p.leg_incoming[l] ? 0 : 1) : (p.leg_incoming[l] ? 1 : 0);
-                o << "  const W<R> w" << k << " = " << (op.routine == MF_R_IXX ? "ixx" : "oxx") << "<R>(ms + " << 4 * l
-                  << ", " << M(p.leg_mass_id[l]) << ", hel[" << l << "], " << anti << ");\n";
-            }
+        emit_one(k, "");
+        if (dep(k)) emit_one(k, "_b");
+    };
+    // an amplitude's colour coefficients into the flows Jn
+    auto emit_terms = [&](const mf_op &op, const std::string &Jn, const std::string &a) {
+        for (int t = 0; t < op.n_terms; ++t) {
+            const mf_colour_term &ct = p.terms[op.first_term + t];
+            std::string Jk = Jn + "[" + std::to_string(ct.jamp) + "]";
+            if (ct.im == 0.0 && ct.re == 1.0) o << "    " << Jk << " = " << Jk << " + " << a << ";\n";
+            else if (ct.im == 0.0 && ct.re == -1.0) o << "    " << Jk << " = " << Jk << " - " << a << ";\n";
+            else if (ct.re == 0.0 && ct.im == 1.0) o << "    " << Jk << " = " << Jk << " + mul_i(" << a << ");\n";
+            else if (ct.re == 0.0 && ct.im == -1.0) o << "    " << Jk << " = " << Jk << " - mul_i(" << a << ");\n";
+            else
+                o << "    " << Jk << " = cfma(C<R>(R(" << fmt_double(ct.re) << "), R(" << fmt_double(ct.im)
+                  << ")), " << a << ", " << Jk << ");\n";
+        }
+    };
+    // one amplitude into the colour flows J (member a) or Jb (member b)
+    auto emit_amp = [&](int k, const char *sfx) {
+        const mf_op &op = p.ops[k];
+        auto in = [&](int q) { return nm(op.in[q], sfx); };
+        std::string g = "cpl[" + std::to_string(op.coupling) + "]";
+        const std::string Jn = sfx[0] ? "Jb" : "J";
+        o << "  {\n";
+        if (op.routine == MF_R_VVV_AMP) o << mom(mask[op.in[0]], "kA") << mom(mask[op.in[1]], "kB") << mom(mask[op.in[2]], "kC");
+        o << "    const cx<R> a = ";
+        switch (op.routine) {
+            case MF_R_FFV_AMP:
+                o << rt("FFV_AMP") << "<R>(" << in(0) << ", " << in(1) << ", " << in(2) << ", " << g << ")";
+                break;
+            case MF_R_VVV_AMP:
+                o << rt("VVV_AMP") << "<R>(" << in(0) << ", " << in(1) << ", " << in(2) << ", "
+                  << a4r("VVV_AMP", "kA") << ", " << a4r("VVV_AMP", "kB") << ", " << a4r("VVV_AMP", "kC") << ", " << g
+                  << ")";
+                break;
+            default:
+                o << rt("VVVV_AMP") << "<R, " << (op.routine - MF_R_VVVV1_AMP + 1) << ">(" << in(0) << ", " << in(1)
+                  << ", " << in(2) << ", " << in(3) << ", " << g << ")";
+        }
+        o << ";\n";
+        emit_terms(op, Jn, "a");
+        o << "  }\n";
+    };
+    // the two amplitudes of a pair: one call when they differ only in the
+    // row or only in the column spinor (the V-slash product shared)
+    auto emit_amp_pair = [&](int k) {
+        const mf_op &op = p.ops[k];
+        int dq = -1, ndep = 0;
+        for (int q = 0; q < 4; ++q)
+            if (op.in[q] >= 0 && dep(op.in[q])) { dq = q; ++ndep; }
+        if (op.routine != MF_R_FFV_AMP || ndep != 1 || dq > 1) {
+            emit_amp(k, "");
+            emit_amp(k, "_b");
             return;
         }
         std::string g = "cpl[" + std::to_string(op.coupling) + "]";
-        std::string den = "idn[" + std::to_string(info.op_den[k]) + "]";
-        o << "  W<R> w" << k << ";\n  {\n";
-        switch (op.routine) {
-            case MF_R_FFV_FIN:
-            case MF_R_FFV_FOUT:
-                o << mom(mask[k], "P");
-                o << "    w" << k << " = " << rt(op.routine == MF_R_FFV_FIN ? "FFV_FIN" : "FFV_FOUT") << "<R>(w"
-                  << op.in[0] << ", w" << op.in[1] << ", " << g << ", " << M(op.mass_id) << ", " << den << ", "
-                  << a4("P") << ");\n";
-                break;
-            case MF_R_FFV_VEC:
-                o << "    w" << k << " = " << rt("FFV_VEC") << "<R>(w" << op.in[0] << ", w" << op.in[1] << ", " << g
-                  << ", " << den << ");\n";
-                break;
-            case MF_R_VVV_VEC:
-                o << mom(mask[op.in[0]], "kA") << mom(mask[op.in[1]], "kB");
-                o << "    w" << k << " = " << rt("VVV_VEC") << "<R>(w" << op.in[0] << ", w" << op.in[1] << ", "
-                  << a4("kA") << ", " << a4("kB") << ", " << g << ", " << den << ");\n";
-                break;
-            default:
-                o << "    w" << k << " = " << rt("VVVV_VEC") << "<R, " << (op.routine - MF_R_VVVV1_VEC + 1) << ">(w"
-                  << op.in[0] << ", w" << op.in[1] << ", w" << op.in[2] << ", " << g << ", " << den << ");\n";
-                break;
-        }
+        const std::string r = rt(dq == 0 ? "FFV_AMP_R2" : "FFV_AMP_C2");
+        const std::string v = "w" + std::to_string(op.in[dq]);
+        o << "  {\n    const A2<R> ab = " << r << "<R>(";
+        if (dq == 0) o << v << ", " << v << "_b, w" << op.in[1];
+        else o << "w" << op.in[0] << ", " << v << ", " << v << "_b";
+        o << ", w" << op.in[2] << ", " << g << ");\n";
+        emit_terms(op, "J", "ab.a");
+        emit_terms(op, "Jb", "ab.b");
         o << "  }\n";
     };
     for (int part = 0; part < parts; ++part) {
     std::fill(done.begin(), done.end(), 0);
     const size_t lo = order.size() * part / parts, hi = order.size() * (part + 1) / parts;
-    o << "template <typename R>\n" << (parts > 1 ? "__device__ __noinline__" : "MF_DEV") << " void program_part" << part
+    o << "template <typename R>\n" << (parts > 1 ? "__device__ __noinline__" : "MF_DEV") << " void " << fn << part
       << "(const R *__restrict__ ms, const R *__restrict__ idn, const int8_t *__restrict__ hel,\n"
-         "    const mf::cx<R> *__restrict__ cpl, const R *__restrict__ mass, mf::cx<R> *__restrict__ Jout) {\n"
+         "    const mf::cx<R> *__restrict__ cpl, const R *__restrict__ mass, mf::cx<R> *__restrict__ Jout"
+      << (pair ? ", mf::cx<R> *__restrict__ Jout_b" : "") << ") {\n"
          "  using namespace mf;\n"
          "  cx<R> J[NJAMP];\n#pragma unroll\n  for (int k = 0; k < NJAMP; ++k) J[k] = C<R>(R(0), R(0));\n";
+    if (pair) o << "  cx<R> Jb[NJAMP];\n#pragma unroll\n  for (int k = 0; k < NJAMP; ++k) Jb[k] = C<R>(R(0), R(0));\n";
     for (size_t oi = lo; oi < hi; ++oi) {
         const int k = order[oi];
         // keep the block's warps on the same stretch of code, so that fetched
@@ -299,40 +424,17 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
         const mf_op &op = p.ops[k];
         for (int q = 0; q < 4; ++q)
             if (op.in[q] >= 0) emit_wf(op.in[q]);
-        fl += routine_flops(op.routine);
-        std::string g = "cpl[" + std::to_string(op.coupling) + "]";
-        o << "  {\n";
-        if (op.routine == MF_R_VVV_AMP) o << mom(mask[op.in[0]], "kA") << mom(mask[op.in[1]], "kB") << mom(mask[op.in[2]], "kC");
-        o << "    const cx<R> a = ";
-        switch (op.routine) {
-            case MF_R_FFV_AMP:
-                o << rt("FFV_AMP") << "<R>(w" << op.in[0] << ", w" << op.in[1] << ", w" << op.in[2] << ", " << g << ")";
-                break;
-            case MF_R_VVV_AMP:
-                o << rt("VVV_AMP") << "<R>(w" << op.in[0] << ", w" << op.in[1] << ", w" << op.in[2] << ", " << a4("kA")
-                  << ", " << a4("kB") << ", " << a4("kC") << ", " << g << ")";
-                break;
-            default:
-                o << rt("VVVV_AMP") << "<R, " << (op.routine - MF_R_VVVV1_AMP + 1) << ">(w" << op.in[0] << ", w"
-                  << op.in[1] << ", w" << op.in[2] << ", w" << op.in[3] << ", " << g << ")";
-        }
-        o << ";\n";
-        for (int t = 0; t < op.n_terms; ++t) {
-            const mf_colour_term &ct = p.terms[op.first_term + t];
-            std::string Jk = "J[" + std::to_string(ct.jamp) + "]";
-            fl += 8;
-            if (ct.im == 0.0 && ct.re == 1.0) o << "    " << Jk << " = " << Jk << " + a;\n";
-            else if (ct.im == 0.0 && ct.re == -1.0) o << "    " << Jk << " = " << Jk << " - a;\n";
-            else if (ct.re == 0.0 && ct.im == 1.0) o << "    " << Jk << " = " << Jk << " + mul_i(a);\n";
-            else if (ct.re == 0.0 && ct.im == -1.0) o << "    " << Jk << " = " << Jk << " - mul_i(a);\n";
-            else
-                o << "    " << Jk << " = cfma(C<R>(R(" << fmt_double(ct.re) << "), R(" << fmt_double(ct.im)
-                  << ")), a, " << Jk << ");\n";
-        }
-        o << "  }\n";
+        if (pair) emit_amp_pair(k);
+        else emit_amp(k, "");
     }
-    o << "#pragma unroll\n  for (int k = 0; k < NJAMP; ++k) Jout[k] = Jout[k] + J[k];\n}\n";
+    o << "#pragma unroll\n  for (int k = 0; k < NJAMP; ++k) Jout[k] = Jout[k] + J[k];\n";
+    if (pair) o << "#pragma unroll\n  for (int k = 0; k < NJAMP; ++k) Jout_b[k] = Jout_b[k] + Jb[k];\n";
+    o << "}\n";
     }
+    return parts;
+    };
+    const int parts = emit_program(false);
+    const int pair_parts = L >= 0 ? emit_program(true) : 0;
     // colour sum  sum_kl Re(conj(J_k) C_kl J_l) / den, C symmetric:
     // sum_k Re(conj(J_k) (C_kk J_k + 2 sum_{l>k} C_kl J_l))
     const int nj = p.n_jamp;
@@ -346,7 +448,6 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
         }
         o << "    m += J[" << k << "].re * z.re + J[" << k << "].im * z.im; }\n";
     }
-    fl += 4.0 * nj * (nj - 1) / 2 + 6.0 * nj;
     o << "  return m * R(" << fmt_double(1.0 / p.colour_den) << ");\n}\n";
     // leading colour: the diagonal of the colour matrix in the flow basis
     o << "template <typename R>\nMF_DEV R colour_sum_lc(const mf::cx<R> *J) {\n  using namespace mf;\n  R m = R(0);\n";
@@ -368,6 +469,24 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
          "                          const mf::cx<R> *cpl, const R *mass, mf::cx<R> *J) {\n"
          "  using namespace mf;\n#pragma unroll\n  for (int k = 0; k < NJAMP; ++k) J[k] = C<R>(R(0), R(0));\n";
     for (int part = 0; part < parts; ++part) o << "  program_part" << part << "<R>(ms, idn, hel, cpl, mass, J);\n";
+    o << "}\n";
+    // a pair of helicities (the kernel's row with leg PAIR_LEG at -1, then at
+    // +1): both colour-summed |M|^2
+    o << "constexpr int PAIR_LEG = " << L << ";\n"
+         "template <typename R>\n"
+         "MF_DEV void helicity_pair_msq(const R *__restrict__ ms, const R *__restrict__ idn, const int8_t *hel,\n"
+         "                              const mf::cx<R> *cpl, const R *mass, R &va, R &vb) {\n"
+         "  using namespace mf;\n";
+    if (L >= 0) {
+        o << "  cx<R> J[NJAMP], Jb[NJAMP];\n#pragma unroll\n"
+             "  for (int k = 0; k < NJAMP; ++k) { J[k] = C<R>(R(0), R(0)); Jb[k] = J[k]; }\n";
+        for (int part = 0; part < pair_parts; ++part)
+            o << "  program_pair_part" << part << "<R>(ms, idn, hel, cpl, mass, J, Jb);\n";
+        o << "  if constexpr (LEADING_COLOUR) { va = colour_sum_lc<R>(J); vb = colour_sum_lc<R>(Jb); }\n"
+             "  else { va = colour_sum_full<R>(J); vb = colour_sum_full<R>(Jb); }\n";
+    } else {
+        o << "  va = vb = R(0);\n";
+    }
     o << "}\n__device__ const int COLOUR_NUM[NJAMP * NJAMP] = {";
     for (int k = 0; k < nj * nj; ++k) o << (k ? ", " : "") << p.colour_num[k];
     o << "};\nconstexpr double INV_COLOUR_DEN = " << fmt_double(1.0 / p.colour_den) << ";\n";
@@ -389,7 +508,6 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
     // wavefunctions included (the emission above also counts the few
     // wavefunctions a later program part recomputes), the colour
     // coefficients' multiply-adds, the colour sum
-    (void)fl;
     double alg = 0.0;
     for (const mf_op &op : p.ops) {
         alg += routine_flops(op.routine);
@@ -397,6 +515,30 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
     }
     alg += 4.0 * nj * (nj - 1) / 2 + 6.0 * nj;
     info.flops_per_hel = alg;
+    info.pair_leg = L;
+    // the pair program as emitted: wavefunctions independent of leg L once,
+    // the others twice; amplitudes twice, or one shared V-slash product and
+    // two spinor products (136 FLOPs) where only a row or column differs
+    info.flops_pair = 0.0;
+    if (L >= 0) {
+        double fp = 0.0;
+        auto dep_wf = [&](int i) { return p.ops[i].kind != MF_OP_AMP && (mask[i] >> L & 1); };
+        for (size_t k = 0; k < p.ops.size(); ++k) {
+            const mf_op &op = p.ops[k];
+            const double rf = routine_flops(op.routine);
+            if (op.kind != MF_OP_AMP) {
+                fp += rf * (dep_wf((int)k) ? 2 : 1);
+                continue;
+            }
+            int ndep = 0, dq = -1;
+            for (int q = 0; q < 4; ++q)
+                if (op.in[q] >= 0 && dep_wf(op.in[q])) { ++ndep; dq = q; }
+            fp += (op.routine == MF_R_FFV_AMP && ndep == 1 && dq <= 1) ? 136.0 : 2.0 * rf;
+            fp += 16.0 * op.n_terms;
+        }
+        fp += 2.0 * (4.0 * nj * (nj - 1) / 2 + 6.0 * nj);
+        info.flops_pair = fp;
+    }
     // kinematics per event (phase space, PDFs, denominators), rough count
     info.flops_kin = 400.0 + 10.0 * info.n_den;
     return o.str();

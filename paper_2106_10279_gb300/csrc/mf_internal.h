@@ -41,7 +41,12 @@ struct GenInfo {
     double flops_per_hel = 0.0;
     double flops_kin = 0.0;
     int parts = 1;               // functions the helicity program is split into
+    int pair_leg = -1;           // leg of the helicity-pair program (-1: none)
+    double flops_pair = 0.0;     // FLOPs of the pair program (both members)
 };
+
+double shared_flops(const mf_process &p, int leg);
+int pair_leg(const mf_process &p);
 
 }  // namespace mfi
 
@@ -59,6 +64,7 @@ struct mf_process {
     int colour_den = 1;
     std::vector<int8_t> hel_all;   // [n_hel_all][n_legs]
     std::vector<int8_t> hel;       // kept after filtering
+    std::vector<uint8_t> pairs;    // [n_pairs][2] rows of hel (0xFF: absent); empty: no pairs
     double average = 1.0;
     int alpha_s_power = 0;
     double alpha_s = 0.0;
