@@ -40,6 +40,32 @@ double routine_flops(int r) {
     }
 }
 
+// an amplitude's colour coefficients as emitted: a complex add for +-1 and
+// +-i, a complex multiply-add otherwise
+double term_flops(const mf_process &p, const mf_op &op) {
+    double f = 0.0;
+    for (int t = 0; t < op.n_terms; ++t) {
+        const mf_colour_term &ct = p.terms[op.first_term + t];
+        const bool unit = (ct.im == 0.0 && (ct.re == 1.0 || ct.re == -1.0)) ||
+                          (ct.re == 0.0 && (ct.im == 1.0 || ct.im == -1.0));
+        f += unit ? 2.0 : 8.0;
+    }
+    return f;
+}
+
+// the colour sum as emitted: per flow a real-times-complex product, per
+// non-zero entry above the diagonal a real-times-complex multiply-add, per
+// flow the real part of conj(J_k) z (leading colour: c_kk |J_k|^2 per flow)
+double colour_sum_flops(const mf_process &p) {
+    const int nj = p.n_jamp;
+    if (p.leading_colour) return 5.0 * nj;        // the diagonal only: c_kk |J_k|^2
+    double f = 6.0 * nj;
+    for (int k = 0; k < nj; ++k)
+        for (int l = k + 1; l < nj; ++l)
+            if (p.colour_num[k * nj + l] != 0) f += 4.0;
+    return f;
+}
+
 }  // namespace
 
 // FLOPs of the wavefunctions whose momentum does not flow through `leg`
@@ -511,9 +537,9 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
     double alg = 0.0;
     for (const mf_op &op : p.ops) {
         alg += routine_flops(op.routine);
-        if (op.kind == MF_OP_AMP) alg += 8.0 * op.n_terms;
+        if (op.kind == MF_OP_AMP) alg += term_flops(p, op);
     }
-    alg += 4.0 * nj * (nj - 1) / 2 + 6.0 * nj;
+    alg += colour_sum_flops(p);
     info.flops_per_hel = alg;
     info.pair_leg = L;
     // the pair program as emitted: wavefunctions independent of leg L once,
@@ -534,9 +560,9 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
             for (int q = 0; q < 4; ++q)
                 if (op.in[q] >= 0 && dep_wf(op.in[q])) { ++ndep; dq = q; }
             fp += (op.routine == MF_R_FFV_AMP && ndep == 1 && dq <= 1) ? 136.0 : 2.0 * rf;
-            fp += 16.0 * op.n_terms;
+            fp += 2.0 * term_flops(p, op);
         }
-        fp += 2.0 * (4.0 * nj * (nj - 1) / 2 + 6.0 * nj);
+        fp += 2.0 * colour_sum_flops(p);
         info.flops_pair = fp;
     }
     // kinematics per event (phase space, PDFs, denominators), rough count

@@ -1,10 +1,11 @@
 """The batched persistent kernel (mf_batch_*) against per-subprocess
 mf_vegas_iterate on the mixed batch of five subprocesses (sizes scaled down
 1:100): same points, so per subprocess the same non-zero counts and bin
-counts, and estimates, errors, histograms and refined grids within 1e-12
-relative (the two kernels are compiled separately, so contraction of
-multiply-adds may differ), over two iterations; the batch runs the costliest
-subprocess's tiles first."""
+counts, and estimates and errors within 1e-12 relative (the two kernels are
+compiled separately, so contraction of multiply-adds may differ), histograms
+and refined grids within 1e-12 after the first iteration and 1e-10 after the
+second (its points are mapped through grids that differ in the last bits);
+the batch runs the costliest subprocess's tiles first."""
 import numpy as np
 import pytest
 
@@ -50,8 +51,12 @@ def test_batch_matches_separate_iterations(env, prec, rel):
             h1, c1 = g_ref[k].histogram()
             h2, c2 = g_bat[k].histogram()
             assert np.array_equal(c1, c2)
-            assert np.allclose(h1, h2, rtol=rel, atol=0)
-            assert np.allclose(g_ref[k].grid, g_bat[k].grid, rtol=rel, atol=1e-15)
+            # the second iteration maps its points through the refined grids,
+            # whose edges already differ in the last bits: a bin's sum of w^2
+            # inherits that shift, scaled by how fast w^2 varies across it
+            hrel = rel if it == 0 else 100 * rel
+            assert np.allclose(h1, h2, rtol=hrel, atol=0)
+            assert np.allclose(g_ref[k].grid, g_bat[k].grid, rtol=hrel, atol=1e-15)
     assert batch.info()["last_kernel_ms"] > 0
 
 
