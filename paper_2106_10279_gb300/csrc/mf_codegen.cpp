@@ -13,6 +13,7 @@
 #include "mf_internal.h"
 
 namespace mfi {
+bool large_program(const mf_process &p);
 namespace {
 
 std::string fmt_double(double v) {
@@ -66,6 +67,138 @@ double colour_sum_flops(const mf_process &p) {
     return f;
 }
 
+// FFV amplitudes that share the row and column spinors and the coupling
+// and whose colour coefficients agree up to a factor +-1 or +-i form one
+// unit: the amplitude is linear in its vector current, so the unit's members
+// contribute c_k(first) * FFV(row, col, sum_a phi_a V_a), phi_a the member's
+// factor (0: 1, 1: i, 2: -1, 3: -i).  Every other amplitude is a unit alone.
+struct AmpUnit {
+    std::vector<int> ops;
+    std::vector<int> phase;
+    int ph0 = 0;                  // phase of the first member's lowest-flow coefficient
+};
+
+std::vector<AmpUnit> amplitude_units(const mf_process &p) {
+    std::vector<AmpUnit> units;
+    // used for long programs (which call every vertex routine); MF_AMP_UNITS
+    // overrides (0: every amplitude alone, 1: units)
+    bool group = large_program(p);
+    if (const char *e = std::getenv("MF_AMP_UNITS")) group = std::atoi(e) != 0;
+    std::map<std::vector<double>, int> unit_of;
+    auto unit_phase = [](double re, double im) {
+        if (im == 0.0 && re == 1.0) return 0;
+        if (re == 0.0 && im == 1.0) return 1;
+        if (im == 0.0 && re == -1.0) return 2;
+        if (re == 0.0 && im == -1.0) return 3;
+        return -1;
+    };
+    for (size_t k = 0; k < p.ops.size(); ++k) {
+        const mf_op &op = p.ops[k];
+        if (op.kind != MF_OP_AMP) continue;
+        int ph = -1;
+        std::vector<double> key;
+        if (group && op.routine == MF_R_FFV_AMP && op.n_terms > 0) {
+            std::vector<std::pair<int, std::pair<double, double>>> t;
+            for (int q = 0; q < op.n_terms; ++q) {
+                const mf_colour_term &ct = p.terms[op.first_term + q];
+                t.push_back({ct.jamp, {ct.re, ct.im}});
+            }
+            std::sort(t.begin(), t.end());
+            ph = unit_phase(t[0].second.first, t[0].second.second);
+            if (ph >= 0) {
+                // divide by the first coefficient (exact for a unit phase)
+                const double cr = t[0].second.first, ci = -t[0].second.second;
+                key = {(double)op.in[0], (double)op.in[1], (double)op.coupling};
+                for (auto &e : t) {
+                    key.push_back(e.first);
+                    key.push_back(e.second.first * cr - e.second.second * ci);
+                    key.push_back(e.second.first * ci + e.second.second * cr);
+                }
+            }
+        }
+        if (ph >= 0) {
+            auto it = unit_of.find(key);
+            if (it != unit_of.end()) {
+                AmpUnit &u = units[it->second];
+                u.ops.push_back((int)k);
+                u.phase.push_back((ph - u.ph0 + 4) % 4);
+                continue;
+            }
+            unit_of[key] = (int)units.size();
+        }
+        units.push_back(AmpUnit{{(int)k}, {0}, ph >= 0 ? ph : 0});
+    }
+    return units;
+}
+
+// Peak number of internal wavefunctions live at once when the units are
+// emitted in `order` (each unit's wavefunctions just before it, a
+// wavefunction live from its definition to its last use), and the sum of the
+// live counts over the emission steps (a tie-breaker).
+std::pair<int, long> live_profile(const mf_process &p, const std::vector<AmpUnit> &units,
+                                  const std::vector<int> &order) {
+    const size_t n = p.ops.size();
+    std::vector<int> def(n, -1), last(n, -1);
+    int t = 0;
+    std::function<void(int)> emit = [&](int k) {
+        if (def[k] >= 0) return;
+        for (int q = 0; q < 4; ++q)
+            if (p.ops[k].in[q] >= 0) emit(p.ops[k].in[q]);
+        for (int q = 0; q < 4; ++q)
+            if (p.ops[k].in[q] >= 0) last[p.ops[k].in[q]] = t;
+        def[k] = t++;
+    };
+    for (int u : order) {
+        for (int a : units[u].ops)
+            for (int q = 0; q < 4; ++q)
+                if (p.ops[a].in[q] >= 0) emit(p.ops[a].in[q]);
+        for (int a : units[u].ops)
+            for (int q = 0; q < 4; ++q)
+                if (p.ops[a].in[q] >= 0) last[p.ops[a].in[q]] = t;
+        ++t;
+    }
+    std::vector<int> ev(t + 2, 0);
+    for (size_t k = 0; k < n; ++k)
+        if (def[k] >= 0 && p.ops[k].kind == MF_OP_CUR) {
+            ev[def[k]]++;
+            ev[(last[k] >= 0 ? last[k] : def[k]) + 1]--;
+        }
+    int cur = 0, peak = 0;
+    long sum = 0;
+    for (int v : ev) {
+        cur += v;
+        peak = std::max(peak, cur);
+        sum += cur;
+    }
+    return {peak, sum};
+}
+
+// Local search on the unit order: move one unit to another position and
+// keep the move when the peak (then the sum) of live wavefunctions does not
+// grow.  A fixed-seed generator keeps the result, and so the generated
+// source and its cached binary, reproducible.
+void improve_order(const mf_process &p, const std::vector<AmpUnit> &units, std::vector<int> &order, int iters) {
+    if (order.size() < 3) return;
+    auto best = live_profile(p, units, order);
+    uint64_t st = 0x9E3779B97F4A7C15ull;
+    auto next = [&](uint64_t m) {
+        st = st * 6364136223846793005ull + 1442695040888963407ull;
+        return (st >> 33) % m;
+    };
+    for (int it = 0; it < iters; ++it) {
+        std::vector<int> o = order;
+        const size_t i = next(o.size());
+        const int u = o[i];
+        o.erase(o.begin() + i);
+        o.insert(o.begin() + next(o.size() + 1), u);
+        auto s = live_profile(p, units, o);
+        if (s <= best) {
+            best = s;
+            order.swap(o);
+        }
+    }
+}
+
 }  // namespace
 
 // FLOPs of the wavefunctions whose momentum does not flow through `leg`
@@ -82,6 +215,14 @@ double shared_flops(const mf_process &p, int leg) {
         if (!(m[k] >> leg & 1)) f += routine_flops(op.routine);
     }
     return f;
+}
+
+// A program long enough to be bound by instruction fetch (the diagram
+// program of one helicity above 2e4 FLOPs; gg -> tt~gg has 4.7e4).
+bool large_program(const mf_process &p) {
+    double f = 0.0;
+    for (const mf_op &op : p.ops) f += routine_flops(op.routine);
+    return f >= 2e4;
 }
 
 // The leg whose helicity the fewest wavefunctions depend on (the most FLOPs
@@ -197,12 +338,14 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
     std::vector<uint32_t> mask;
     emit_header(o, p, info, mask, R, ns);
     // The vertex routines are called as non-inlined functions: one copy of each
-    // routine's code instead of one per use.  The program then fits the
+    // routine's code instead of one per use.  A long program then fits the
     // instruction caches far better (the inlined form is fetch-bound), at the
-    // price of argument passing.  MF_CALL_ROUTINES=0 inlines them.
-    // (MF_CALL_ROUTINES=2 inlines the amplitude routines and calls the
-    // currents, =3 the other way round: measurement variants)
-    const int call_mode = std::getenv("MF_CALL_ROUTINES") ? std::atoi(std::getenv("MF_CALL_ROUTINES")) : 1;
+    // price of argument passing: long programs call every routine (mode 1),
+    // shorter ones inline the currents and call the amplitude routines
+    // (mode 3; gg -> tt~g 1.12x faster than mode 1).  MF_CALL_ROUTINES
+    // overrides: 0 inlines everything, 2 calls the currents only.
+    int call_mode = large_program(p) ? 1 : 3;
+    if (const char *e = std::getenv("MF_CALL_ROUTINES")) call_mode = std::atoi(e);
     const bool calls = call_mode != 0;
     auto rt = [&](const char *name) {
         const bool amp = std::string(name).find("_AMP") != std::string::npos;
@@ -232,24 +375,22 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
         }
         return e.str();
     };
-    // amplitude order: greedy, the amplitude needing the fewest wavefunctions
-    // not yet computed first (ties: the one releasing most live values), which
-    // keeps the number of live wavefunctions small
-    std::vector<int> amps;
-    for (size_t k = 0; k < p.ops.size(); ++k)
-        if (p.ops[k].kind == MF_OP_AMP) amps.push_back((int)k);
-    std::vector<std::vector<int>> need_wf(p.ops.size());
+    // amplitude order: greedy over the amplitude units, the unit needing the
+    // fewest wavefunctions not yet computed first (ties: the one releasing
+    // most live values), which keeps the number of live wavefunctions small
+    const std::vector<AmpUnit> units = amplitude_units(p);
     std::function<void(int, std::vector<char> &)> closure = [&](int k, std::vector<char> &seen) {
         for (int q = 0; q < 4; ++q) {
             int i = p.ops[k].in[q];
             if (i >= 0 && !seen[i]) { seen[i] = 1; closure(i, seen); }
         }
     };
-    for (int a : amps) {
+    std::vector<std::vector<int>> need_wf(units.size());
+    for (size_t u = 0; u < units.size(); ++u) {
         std::vector<char> seen(p.ops.size(), 0);
-        closure(a, seen);
+        for (int a : units[u].ops) closure(a, seen);
         for (size_t i = 0; i < seen.size(); ++i)
-            if (seen[i]) need_wf[a].push_back((int)i);
+            if (seen[i]) need_wf[u].push_back((int)i);
     }
     std::vector<int> uses(p.ops.size(), 0);
     for (auto &op : p.ops)
@@ -257,20 +398,22 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
             if (op.in[q] >= 0) uses[op.in[q]]++;
     std::vector<char> done(p.ops.size(), 0);
     std::vector<int> remaining_uses = uses;
-    std::vector<int> order;
-    std::vector<char> taken(p.ops.size(), 0);
-    for (size_t step = 0; step < amps.size(); ++step) {
+    std::vector<int> order;               // unit indices
+    std::vector<char> taken(units.size(), 0);
+    for (size_t step = 0; step < units.size(); ++step) {
         int best = -1, bnew = 0, bfree = 0;
-        for (int a : amps) {
-            if (taken[a]) continue;
+        for (size_t u = 0; u < units.size(); ++u) {
+            if (taken[u]) continue;
             int nnew = 0;
-            for (int i : need_wf[a]) nnew += !done[i];
+            for (int i : need_wf[u]) nnew += !done[i];
+            std::map<int, int> used;
+            for (int a : units[u].ops)
+                for (int q = 0; q < 4; ++q)
+                    if (p.ops[a].in[q] >= 0) used[p.ops[a].in[q]]++;
             int nfree = 0;
-            for (int q = 0; q < 4; ++q) {
-                int i = p.ops[a].in[q];
-                if (i >= 0 && done[i] && remaining_uses[i] == 1) ++nfree;
-            }
-            if (best < 0 || nnew < bnew || (nnew == bnew && nfree > bfree)) { best = a; bnew = nnew; bfree = nfree; }
+            for (auto &e : used)
+                if (done[e.first] && remaining_uses[e.first] == e.second) ++nfree;
+            if (best < 0 || nnew < bnew || (nnew == bnew && nfree > bfree)) { best = (int)u; bnew = nnew; bfree = nfree; }
         }
         taken[best] = 1;
         order.push_back(best);
@@ -280,8 +423,19 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
                 for (int q = 0; q < 4; ++q)
                     if (p.ops[i].in[q] >= 0) remaining_uses[p.ops[i].in[q]]--;
             }
-        for (int q = 0; q < 4; ++q)
-            if (p.ops[best].in[q] >= 0) remaining_uses[p.ops[best].in[q]]--;
+        for (int a : units[best].ops)
+            for (int q = 0; q < 4; ++q)
+                if (p.ops[a].in[q] >= 0) remaining_uses[p.ops[a].in[q]]--;
+    }
+    // then a local search lowers the peak of live wavefunctions (grouped
+    // units need several vector currents at once)
+    {
+        bool grouped = false;
+        for (const AmpUnit &un : units) grouped |= un.ops.size() > 1;
+        int iters = grouped ? 4000 : 0;
+        if (const char *e = std::getenv("MF_ORDER_SEARCH")) iters = std::atoi(e);
+        improve_order(p, units, order, iters);
+        info.peak_live = live_profile(p, units, order).first;
     }
     // With inlined routines the schedule is split into parts compiled as
     // separate functions: ptxas falls back to a stack-based allocation for
@@ -295,7 +449,10 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
     // same for both members and is computed once; the others (and every
     // amplitude) twice, the second copy carrying the suffix _b.
     const int L = pair_leg(p);
-    int sync_every = 0;
+    // long programs: a block barrier every 16 amplitudes keeps the block's
+    // warps on the same stretch of code, so that the instructions one warp
+    // fetched serve the others (measured on gg -> tt~gg: 1.09x)
+    int sync_every = large_program(p) ? 16 : 0;
     if (const char *e = std::getenv("MF_SYNC_EVERY")) sync_every = std::atoi(e);
     auto M = [&](int id) { return id >= 0 ? "mass[" + std::to_string(id) + "]" : std::string("R(0)"); };
     auto emit_program = [&](const bool pair) {
@@ -432,6 +589,69 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
         emit_terms(op, "Jb", "ab.b");
         o << "  }\n";
     };
+    // a unit of several FFV amplitudes: their vector currents combined with
+    // the members' phases, one amplitude (or one pair of amplitudes), the
+    // first member's colour coefficients
+    auto emit_unit = [&](const AmpUnit &un) {
+        const mf_op &op0 = p.ops[un.ops[0]];
+        bool vdep = false;
+        for (int a : un.ops) vdep |= dep(p.ops[a].in[2]);
+        o << "  {\n";
+        const int form = std::getenv("MF_UNIT_FORM") ? std::atoi(std::getenv("MF_UNIT_FORM")) : 0;
+        auto build = [&](const char *sfx, const std::string &vs) {
+            if (form == 1) {
+                // component by component, real and imaginary parts apart
+                o << "    W<R> " << vs << ";\n";
+                for (int c = 0; c < 4; ++c)
+                    for (int ri = 0; ri < 2; ++ri) {
+                        const char *f = ri ? "im" : "re";
+                        o << "    " << vs << ".c[" << c << "]." << f << " = " << nm(op0.in[2], sfx) << ".c[" << c << "]." << f;
+                        for (size_t m = 1; m < un.ops.size(); ++m) {
+                            const std::string v = nm(p.ops[un.ops[m]].in[2], sfx) + ".c[" + std::to_string(c) + "].";
+                            const int ph = un.phase[m];
+                            // +-1: +-v; +i: i v = (-v.im, v.re); -i: (v.im, -v.re)
+                            if (ph == 0) o << " + " << v << f;
+                            else if (ph == 2) o << " - " << v << f;
+                            else if (ph == 1) o << (ri ? " + " + v + "re" : " - " + v + "im");
+                            else o << (ri ? " - " + v + "re" : " + " + v + "im");
+                        }
+                        o << ";\n";
+                    }
+                return;
+            }
+            o << "    W<R> " << vs << " = " << nm(op0.in[2], sfx) << ";\n";
+            for (size_t m = 1; m < un.ops.size(); ++m) {
+                const std::string v = nm(p.ops[un.ops[m]].in[2], sfx) + ".c[c]";
+                const int ph = un.phase[m];
+                o << "#pragma unroll\n    for (int c = 0; c < 4; ++c) " << vs << ".c[c] = " << vs << ".c[c] "
+                  << (ph == 0 ? "+ " + v : ph == 2 ? "- " + v : ph == 1 ? "+ mul_i(" + v + ")" : "- mul_i(" + v + ")")
+                  << ";\n";
+            }
+        };
+        build("", "vs");
+        if (pair && vdep) build("_b", "vs_b");
+        const std::string g = "cpl[" + std::to_string(op0.coupling) + "]";
+        const bool rdep = pair && dep(op0.in[0]), cdep = pair && dep(op0.in[1]);
+        const std::string row = "w" + std::to_string(op0.in[0]), col = "w" + std::to_string(op0.in[1]);
+        if (!pair) {
+            o << "    const cx<R> a = " << rt("FFV_AMP") << "<R>(" << row << ", " << col << ", vs, " << g << ");\n";
+            emit_terms(op0, "J", "a");
+        } else if (!vdep && rdep != cdep) {
+            o << "    const A2<R> ab = " << rt(rdep ? "FFV_AMP_R2" : "FFV_AMP_C2") << "<R>(";
+            if (rdep) o << row << ", " << row << "_b, " << col;
+            else o << row << ", " << col << ", " << col << "_b";
+            o << ", vs, " << g << ");\n";
+            emit_terms(op0, "J", "ab.a");
+            emit_terms(op0, "Jb", "ab.b");
+        } else {
+            o << "    const cx<R> a = " << rt("FFV_AMP") << "<R>(" << row << ", " << col << ", vs, " << g << ");\n";
+            o << "    const cx<R> b = " << rt("FFV_AMP") << "<R>(" << nm(op0.in[0], "_b") << ", " << nm(op0.in[1], "_b")
+              << ", " << (vdep ? "vs_b" : "vs") << ", " << g << ");\n";
+            emit_terms(op0, "J", "a");
+            emit_terms(op0, "Jb", "b");
+        }
+        o << "  }\n";
+    };
     for (int part = 0; part < parts; ++part) {
     std::fill(done.begin(), done.end(), 0);
     const size_t lo = order.size() * part / parts, hi = order.size() * (part + 1) / parts;
@@ -443,15 +663,16 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
          "  cx<R> J[NJAMP];\n#pragma unroll\n  for (int k = 0; k < NJAMP; ++k) J[k] = C<R>(R(0), R(0));\n";
     if (pair) o << "  cx<R> Jb[NJAMP];\n#pragma unroll\n  for (int k = 0; k < NJAMP; ++k) Jb[k] = C<R>(R(0), R(0));\n";
     for (size_t oi = lo; oi < hi; ++oi) {
-        const int k = order[oi];
+        const AmpUnit &un = units[order[oi]];
         // keep the block's warps on the same stretch of code, so that fetched
         // instructions serve all of them
         if (sync_every > 0 && oi > lo && (oi - lo) % sync_every == 0) o << "  MF_PROG_SYNC();\n";
-        const mf_op &op = p.ops[k];
-        for (int q = 0; q < 4; ++q)
-            if (op.in[q] >= 0) emit_wf(op.in[q]);
-        if (pair) emit_amp_pair(k);
-        else emit_amp(k, "");
+        for (int a : un.ops)
+            for (int q = 0; q < 4; ++q)
+                if (p.ops[a].in[q] >= 0) emit_wf(p.ops[a].in[q]);
+        if (un.ops.size() > 1) emit_unit(un);
+        else if (pair) emit_amp_pair(un.ops[0]);
+        else emit_amp(un.ops[0], "");
     }
     o << "#pragma unroll\n  for (int k = 0; k < NJAMP; ++k) Jout[k] = Jout[k] + J[k];\n";
     if (pair) o << "#pragma unroll\n  for (int k = 0; k < NJAMP; ++k) Jout_b[k] = Jout_b[k] + Jb[k];\n";
@@ -530,37 +751,48 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
         if (precision == MF_MIXED_TC) o << "  mf::kernel_body_tc<" << ht << ">(kp);\n}\n";
         else o << "  mf::kernel_body<" << R << ", " << block << ", " << ht << ">(kp);\n}\n";
     }
-    // algorithmic count: every operation of the diagram program once, external
-    // wavefunctions included (the emission above also counts the few
-    // wavefunctions a later program part recomputes), the colour
-    // coefficients' multiply-adds, the colour sum
+    // algorithmic count of the programs as emitted: every wavefunction once
+    // (the few a later program part recomputes are not counted), per
+    // amplitude unit one amplitude, the combination of its vector currents
+    // (a complex add per component and extra member) and the first member's
+    // colour coefficients, and the colour sum
     double alg = 0.0;
-    for (const mf_op &op : p.ops) {
-        alg += routine_flops(op.routine);
-        if (op.kind == MF_OP_AMP) alg += term_flops(p, op);
+    for (const mf_op &op : p.ops)
+        if (op.kind != MF_OP_AMP) alg += routine_flops(op.routine);
+    for (const AmpUnit &un : units) {
+        const mf_op &op0 = p.ops[un.ops[0]];
+        alg += routine_flops(op0.routine) + 8.0 * (un.ops.size() - 1) + term_flops(p, op0);
     }
     alg += colour_sum_flops(p);
     info.flops_per_hel = alg;
     info.pair_leg = L;
-    // the pair program as emitted: wavefunctions independent of leg L once,
-    // the others twice; amplitudes twice, or one shared V-slash product and
-    // two spinor products (136 FLOPs) where only a row or column differs
+    // the pair program: wavefunctions independent of leg L once, the others
+    // twice; per unit the combination once or (vector currents depending on
+    // L) twice, and one shared V-slash product with two spinor products (136
+    // FLOPs) where only the row or only the column spinor differs, else two
+    // amplitudes; both members' colour coefficients and colour sums
     info.flops_pair = 0.0;
     if (L >= 0) {
         double fp = 0.0;
         auto dep_wf = [&](int i) { return p.ops[i].kind != MF_OP_AMP && (mask[i] >> L & 1); };
-        for (size_t k = 0; k < p.ops.size(); ++k) {
-            const mf_op &op = p.ops[k];
-            const double rf = routine_flops(op.routine);
-            if (op.kind != MF_OP_AMP) {
-                fp += rf * (dep_wf((int)k) ? 2 : 1);
-                continue;
+        for (size_t k = 0; k < p.ops.size(); ++k)
+            if (p.ops[k].kind != MF_OP_AMP) fp += routine_flops(p.ops[k].routine) * (dep_wf((int)k) ? 2 : 1);
+        for (const AmpUnit &un : units) {
+            const mf_op &op0 = p.ops[un.ops[0]];
+            bool vdep = false;
+            for (int a : un.ops) vdep |= op0.routine == MF_R_FFV_AMP && dep_wf(p.ops[a].in[2]);
+            fp += 8.0 * (un.ops.size() - 1) * (vdep ? 2 : 1);
+            bool shared;
+            if (un.ops.size() > 1) {
+                shared = !vdep && (dep_wf(op0.in[0]) != dep_wf(op0.in[1]));
+            } else {
+                int ndep = 0, dq = -1;
+                for (int q = 0; q < 4; ++q)
+                    if (op0.in[q] >= 0 && dep_wf(op0.in[q])) { ++ndep; dq = q; }
+                shared = op0.routine == MF_R_FFV_AMP && ndep == 1 && dq <= 1;
             }
-            int ndep = 0, dq = -1;
-            for (int q = 0; q < 4; ++q)
-                if (op.in[q] >= 0 && dep_wf(op.in[q])) { ++ndep; dq = q; }
-            fp += (op.routine == MF_R_FFV_AMP && ndep == 1 && dq <= 1) ? 136.0 : 2.0 * rf;
-            fp += 2.0 * term_flops(p, op);
+            fp += shared ? 136.0 : 2.0 * routine_flops(op0.routine);
+            fp += 2.0 * term_flops(p, op0);
         }
         fp += 2.0 * colour_sum_flops(p);
         info.flops_pair = fp;

@@ -43,10 +43,12 @@ struct GenInfo {
     int parts = 1;               // functions the helicity program is split into
     int pair_leg = -1;           // leg of the helicity-pair program (-1: none)
     double flops_pair = 0.0;     // FLOPs of the pair program (both members)
+    int peak_live = 0;           // peak of live internal wavefunctions of the schedule
 };
 
 double shared_flops(const mf_process &p, int leg);
 int pair_leg(const mf_process &p);
+bool large_program(const mf_process &p);
 
 }  // namespace mfi
 

@@ -1,0 +1,98 @@
+"""The generated diagram programs built for the host in double precision and
+compared with the oracle's per-helicity |M|^2 (CPU only):
+
+* the program of one helicity, for every helicity row, which checks the code
+  generator's schedule, its amplitude units (FFV amplitudes with the same
+  spinors and colour coefficients equal up to +-1 or +-i evaluated once on
+  the combined vector current; the default for long programs, forced on for
+  all in a second pass) and the vertex routines;
+* the program of a helicity pair (the two rows that differ only at the pair
+  leg, evaluated with the wavefunctions independent of that leg shared), for
+  every pair.
+
+Bound: 1e-12 of the point's helicity sum per helicity, as in the GPU
+per-helicity test (the same FP64 arithmetic; only the order of operations
+differs from the oracle's)."""
+import itertools
+import os
+import re
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _build(tmp, name, units):
+    from paper_2106_10279_gb300 import api
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("no host C++ compiler")
+    desc = api.descriptor_for_workload(W.WORKLOADS[name])
+    if units is not None:
+        os.environ["MF_AMP_UNITS"] = units
+    try:
+        src = api.mf_generate_kernel_source(desc, "fp64")
+    finally:
+        os.environ.pop("MF_AMP_UNITS", None)
+    src = src[:src.index('#include "mf_kernel.cuh"')]
+    leg = int(re.search(r"constexpr int PAIR_LEG = (-?\d+);", src).group(1))
+    (tmp / "mf_program_gen.h").write_text(src)
+    exe = tmp / "program_check"
+    subprocess.run([gxx, "-std=c++17", "-O1", "-w", "-I", str(tmp),
+                    "-I", os.path.join(ROOT, "paper_2106_10279_gb300", "csrc", "device"),
+                    os.path.join(ROOT, "tests", "program_check.cpp"), "-o", str(exe)], check=True)
+    d = desc.desc
+    head = [str(d.n_masses)] + [repr(float(d.masses[i])) for i in range(d.n_masses)]
+    head += [str(d.n_couplings)] + [repr(float(d.couplings[i])) for i in range(2 * d.n_couplings)]
+
+    def run(lines):
+        res = subprocess.run([str(exe)], input=" ".join(head) + "\n" + "\n".join(lines) + "\n",
+                             capture_output=True, text=True, check=True)
+        return np.array([[float(v) for v in l.split()] for l in res.stdout.strip().splitlines()])
+    return run, leg
+
+
+def _line(cmd, hel, p):
+    return cmd + " " + " ".join(str(int(h)) for h in hel) + " " + " ".join(repr(float(v)) for v in p.ravel())
+
+
+@pytest.mark.parametrize("units", [None, "1"])
+@pytest.mark.parametrize("name,n", [("ee_mumu", 4), ("gg_ttx", 6), ("uux_ttx", 6), ("gg_ttxg", 5),
+                                    ("uux_ttxg", 5), ("gg_ttxgg", 3)])
+def test_generated_programs_match_the_oracle(tmp_path, oracle_processes, name, n, units):
+    # units None: the generator's default (amplitude units for long programs
+    # only); "1": units for every program
+    from oracle.integrand import Integrand
+    wl = W.WORKLOADS[name]
+    orc = Integrand(wl, process=oracle_processes(name))
+    run, leg = _build(tmp_path, name, units)
+    x = W.uniform_points(wl.ndim, 4 * n, 2024)
+    p, s_hat, x1, x2, jx, w, ok = orc.kinematics(x)
+    keep = ok & orc.cuts(p)
+    p = p[keep][:n]
+    assert p.shape[0] == n
+    tot, per = orc.proc.msq_summed(p, per_helicity=True)          # [H, n], rows in table order
+    nleg = p.shape[1]
+    rows = list(itertools.product((-1, 1), repeat=nleg))
+    assert len(rows) == per.shape[0]
+    # one helicity at a time
+    got = run([_line("msq", h, p[i]) for i in range(n) for h in rows]).reshape(n, len(rows))
+    err = np.abs(got - per.T) / tot[:, None]
+    assert err.max() <= 1e-12, (name, err.max())
+    # helicity pairs: rows with the pair leg at -1, their partner at +1
+    assert leg >= 0 or name == "ee_mumu"
+    if leg < 0:
+        return
+    firsts = [h for h in rows if h[leg] == -1]
+    partner = [tuple(1 if l == leg else v for l, v in enumerate(h)) for h in firsts]
+    got2 = run([_line("pair", h, p[i]) for i in range(n) for h in firsts]).reshape(n, len(firsts), 2)
+    ia = [rows.index(h) for h in firsts]
+    ib = [rows.index(h) for h in partner]
+    ea = np.abs(got2[:, :, 0] - per[ia].T) / tot[:, None]
+    eb = np.abs(got2[:, :, 1] - per[ib].T) / tot[:, None]
+    assert max(ea.max(), eb.max()) <= 1e-12, (name, ea.max(), eb.max())
