@@ -29,11 +29,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "events/s of gg→tt̄g(g) LO integrand: mixed/batched vs FP64 at ≤1e-5 rel err"
 # DRAM bytes per point of the fused integrand kernel, mixed precision:
-# dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of a
-# 1e6-point gg->tt~gg iteration divided by its points (the traffic grows with
-# the points; the capture's kernel is the one built from this source)
-# (empty until the kernel with helicity pairs has been captured)
-KERNEL_DRAM_BYTES_PER_POINT = {}
+# dram__bytes_read.sum + dram__bytes_write.sum of a one-pass ncu capture of
+# one full-size 4e7-point gg->tt~gg iteration divided by its points (the
+# capture's kernel is the one built from this source)
+KERNEL_DRAM_BYTES_PER_POINT = {("gg_ttxgg", "mixed"): (91.26e6 + 15.73e9) / 4e7}
 WORKLOAD = "gg_ttxgg"
 
 
@@ -375,7 +374,8 @@ def run_native(args):
                      "frac": achieved / fp32_peak,
                      "traffic": (KERNEL_DRAM_BYTES_PER_POINT[(wl.name, args.precision)] * n_events
                                  if (wl.name, args.precision) in KERNEL_DRAM_BYTES_PER_POINT else None),
-                     "traffic_note": "bytes per launch, scaled by points from a 1e6-point ncu capture; "
+                     "traffic_note": "bytes per launch from a one-pass ncu capture of a full-size launch, "
+                                     "scaled by points; mostly write-back of register spills; "
                                      f"algorithmic output {n_events * (8 + wl.ndim) / 1e6:.0f} MB",
                      "kernel": "mf_kernel (fused integrand)", "kernel_ms": kms,
                      "flops_per_passing_point": info["flops_helicity_sum"], "helicity_pairs": info["n_pairs"],

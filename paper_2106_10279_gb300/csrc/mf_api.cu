@@ -1524,7 +1524,13 @@ extern "C" mf_status mf_process_tune(mf_process *p, mf_precision prec, int64_t n
     mf_vegas *v = nullptr;
     mf_status st = mf_vegas_create(p->ndim, 50, 1.5, &v);
     if (st != MF_OK) return st;
-    st = ensure_scratch(p, v, n_sample);
+    // each shape is timed on a whole number of rounds of its resident grid
+    // (at least one), so that no shape is favoured by a partial last round
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t n_cap = std::max<int64_t>(n_sample, (int64_t)nsm * 2048);
+    st = ensure_scratch(p, v, n_cap);
     cudaEvent_t a = nullptr, b = nullptr;
     if (st == MF_OK && (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess))
         st = fail(MF_ECUDA, "events");
@@ -1553,8 +1559,10 @@ extern "C" mf_status mf_process_tune(mf_process *p, mf_precision prec, int64_t n
             mfi::Compiled k;
             st = compile_shape(p, prec, bl, hh, k, mb);
             if (st != MF_OK) break;
+            const int64_t round = (int64_t)nsm * std::max(k.max_blocks_per_sm, 1) * k.block;
+            const int64_t n_shape = std::min(n_cap, std::max<int64_t>(1, n_sample / round) * round);
             mf_kparams kp;
-            vegas_params(p, v, n_sample, 0, 0, 12345, kp);
+            vegas_params(p, v, n_shape, 0, 0, 12345, kp);
             float ms = 1e30f;
             mfi::Compiled saved = p->kern[prec];
             p->kern[prec] = k;
@@ -1566,6 +1574,7 @@ extern "C" mf_status mf_process_tune(mf_process *p, mf_precision prec, int64_t n
                 float t = 0.f;
                 if (st == MF_OK && rep > 0 && cudaEventElapsedTime(&t, a, b) == cudaSuccess) ms = std::min(ms, t);
             }
+            ms /= (float)n_shape;                               // time per point
             p->kern[prec] = saved;
             if (st != MF_OK) {
                 mfi::unload_kernel(k);
