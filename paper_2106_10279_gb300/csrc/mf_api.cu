@@ -539,7 +539,9 @@ void build_pairs(mf_process *p) {
     p->pairs.clear();
     const int L = p->gen.pair_leg, n = p->n_legs;
     const int nh = (int)(p->hel.size() / n);
-    if (L < 0 || nh == 0) return;
+    // (row indices are stored in one byte with 0xFF for an absent member, so
+    // a table of 256 kept rows is evaluated one helicity at a time)
+    if (L < 0 || nh == 0 || nh > 255) return;
     if (const char *e = std::getenv("MF_HEL_PAIRS"))       // measurement switch: 0 = helicities one by one
         if (std::atoi(e) == 0) return;
     std::vector<uint8_t> t;

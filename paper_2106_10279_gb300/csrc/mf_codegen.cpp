@@ -597,28 +597,7 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
         bool vdep = false;
         for (int a : un.ops) vdep |= dep(p.ops[a].in[2]);
         o << "  {\n";
-        const int form = std::getenv("MF_UNIT_FORM") ? std::atoi(std::getenv("MF_UNIT_FORM")) : 0;
         auto build = [&](const char *sfx, const std::string &vs) {
-            if (form == 1) {
-                // component by component, real and imaginary parts apart
-                o << "    W<R> " << vs << ";\n";
-                for (int c = 0; c < 4; ++c)
-                    for (int ri = 0; ri < 2; ++ri) {
-                        const char *f = ri ? "im" : "re";
-                        o << "    " << vs << ".c[" << c << "]." << f << " = " << nm(op0.in[2], sfx) << ".c[" << c << "]." << f;
-                        for (size_t m = 1; m < un.ops.size(); ++m) {
-                            const std::string v = nm(p.ops[un.ops[m]].in[2], sfx) + ".c[" + std::to_string(c) + "].";
-                            const int ph = un.phase[m];
-                            // +-1: +-v; +i: i v = (-v.im, v.re); -i: (v.im, -v.re)
-                            if (ph == 0) o << " + " << v << f;
-                            else if (ph == 2) o << " - " << v << f;
-                            else if (ph == 1) o << (ri ? " + " + v + "re" : " - " + v + "im");
-                            else o << (ri ? " - " + v + "re" : " + " + v + "im");
-                        }
-                        o << ";\n";
-                    }
-                return;
-            }
             o << "    W<R> " << vs << " = " << nm(op0.in[2], sfx) << ";\n";
             for (size_t m = 1; m < un.ops.size(); ++m) {
                 const std::string v = nm(p.ops[un.ops[m]].in[2], sfx) + ".c[c]";
