@@ -168,7 +168,10 @@ typedef struct mf_batch mf_batch;       /* opaque, library-owned */
 /* mf_create_process: validate and deep-copy *desc, drop vanishing helicities,
  * generate CUDA source specialised to the diagram program and compile it for
  * sm_103a at run time (NVRTC; cached on disk when MF_JIT_CACHE names a
- * directory).  Synchronous.  Errors: MF_EINVAL (malformed descriptor),
+ * directory).  The kept helicities are grouped into pairs that differ only at
+ * one leg where that saves arithmetic (mf_process_info: pair_leg, n_pairs);
+ * the helicity sums of mf_integrand and mf_vegas_iterate then evaluate each
+ * pair with one program.  Synchronous.  Errors: MF_EINVAL (malformed descriptor),
  * MF_EUNSUPPORTED (more than MF_MAX_LEGS legs, n_jamp > MF_MAX_JAMP),
  * MF_EJIT (compilation failed; mf_last_error has the log), MF_ECUDA, MF_ENOMEM.
  * On error *out is left NULL. */
@@ -321,13 +324,15 @@ mf_status mf_tree_reduce(const double *nodes, int32_t n_nodes, int32_t K, int64_
 
 /* mf_process_tune: time the kernel of precision prec for every launch shape
  * (128 or 256 threads per block; 8, 16 or 32 lanes per event, at most the
- * padded helicity count), then for the fastest a compiled-in minimum of 3 or
- * 4 resident blocks per SM, on n_sample (>= 1024) Vegas points of a uniform
- * grid, and keep the fastest for later calls (and for batches created
- * afterwards).  The helicity sum is a fixed pairwise tree whatever the lanes
- * per point, so block size and lanes never change the results; a minimum of
- * resident blocks changes the compiler's register budget and with it the
- * order of a few multiply-adds, i.e. the last bits.  Each shape is compiled
+ * padded count of helicity pairs, or of helicities for a process without
+ * pairs), then for the fastest a compiled-in minimum of 3 or 4 resident
+ * blocks per SM, each on about n_sample (>= 1024) Vegas points of a uniform
+ * grid rounded to a whole number of rounds of that shape's resident grid
+ * (at least one round), and keep the fastest per point for later calls (and
+ * for batches created afterwards).  The helicity sum is a fixed pairwise
+ * tree whatever the lanes per point, so block size and lanes never change
+ * the results; a minimum of resident blocks changes the compiler's register
+ * budget and with it the order of a few multiply-adds, i.e. the last bits.  Each shape is compiled
  * once (cached on disk).  *block and *ht (may be NULL) receive the choice
  * (mf_process_kernel_info gives the rest).  Synchronous on stream. */
 mf_status mf_process_tune(mf_process *p, mf_precision prec, int64_t n_sample, void *stream, int32_t *block,
