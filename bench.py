@@ -131,13 +131,34 @@ def cpu_baseline_oracle(wl, n_sample):
     return n_sample / dt, dt
 
 
+def workload_config(wl, n_events, precision, n_diagrams, n_hel, n_jamp):
+    """The `config` object of the bench line (shared by both arms)."""
+    return {"workload": f"{wl.name}: {' '.join(l.particle for l in wl.legs[:2])} -> "
+                        f"{' '.join(l.particle for l in wl.legs[2:])} at 13 TeV, {n_events:.0e} events per Vegas "
+                        f"iteration per GPU, {wl.ndim} dims, 50 bins, cuts pT(g)>{wl.pt_min_gluon:g} GeV and "
+                        f"dR(g,g)>{wl.dr_min_gluon:g}, synthetic PDF table; f32 amplitudes/colour sum, f64 "
+                        f"kinematics and accumulators",
+            "precision": precision + (" (colour sum on the tensor cores)" if precision == "mixed_tc" else ""),
+            "events_per_step_per_gpu": n_events, "diagrams": n_diagrams, "helicities": n_hel,
+            "colour_flows": n_jamp,
+            "l2": "random numbers generated in-kernel; per-step outputs (w, bins) "
+                  f"{n_events * (8 + wl.ndim) / 1e6:.0f} MB > 129 MB L2"}
+
+
 def run_reference(args):
     import workloads as W
+    from oracle.integrand import Integrand, oracle_process
     rank, world, _ = _dist()
     if rank != 0:
         return
     wl = W.WORKLOADS[args.workload]
     sample = 120 if wl.name == "gg_ttxgg" else 2000
+    # the same workload description as the native arm, structural counts
+    # from the oracle's own process
+    oproc = oracle_process(wl)
+    n_hel = len(Integrand(wl, process=oproc).nonzero_helicities())
+    config = workload_config(wl, args.events or wl.n_events, args.precision, len(oproc.diagrams), n_hel,
+                             oproc.string_basis().shape[1])
     times = []
     for i in range(args.warmup + args.steps):
         rate, dt = cpu_baseline_oracle(wl, sample)
@@ -148,10 +169,10 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": f"{wl.name}: oracle (numpy, 1 thread) on {sample} points of one Vegas "
-                                   f"iteration per step"},
+            "config": config,
             "cpu_baseline": {"value": value, "unit": "events/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{sample} points of the {wl.name} Vegas iteration"},
+                             "sample": f"{sample} points of one {wl.name} Vegas iteration per step (Philox, map, "
+                                       f"integrand, accumulate; numpy, 1 thread)"},
             "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -355,14 +376,7 @@ def run_native(args):
         "parallelism": "one Vegas iteration of N x events_per_step_per_gpu points split in whole 4096-point "
                        "chunks; one all-gather of partial-sum tree nodes per iteration" if world > 1 else "1 GPU",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": f"{wl.name}: gg->tt~gg at 13 TeV, {n_events:.0e} events per Vegas iteration "
-                               f"per GPU, {wl.ndim} dims, 50 bins, cuts pT(g)>20 GeV and dR(g,g)>0.4, synthetic "
-                               f"PDF table; f32 amplitudes/colour sum, f64 kinematics and accumulators",
-                   "precision": args.precision + (" (colour sum on the tensor cores)" if args.precision == "mixed_tc" else ""),
-                   "events_per_step_per_gpu": n_events, "diagrams": 123, "helicities": info["n_hel"],
-                   "colour_flows": info["n_jamp"],
-                   "l2": "random numbers generated in-kernel; per-step outputs (w, bins) "
-                         f"{n_events * (8 + wl.ndim) / 1e6:.0f} MB > 129 MB L2"},
+        "config": workload_config(wl, n_events, args.precision, proc.n_diagrams, info["n_hel"], info["n_jamp"]),
         "fp64": {"value": fp64_rate, "unit": "events/s", "events": n64,
                  "roofline": {"bound": "alu", "achieved": fp64_tflops, "peak": 1.25, "unit": "TFLOP/s",
                               "frac": fp64_tflops / 1.25, "peak_source": "nominal GB300 FP64 rate"}},

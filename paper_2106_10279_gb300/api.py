@@ -358,6 +358,11 @@ class Process:
         """Counts of the process (FLOPs as of the kernel compiled last)."""
         return mf_process_get_info(self.handle)
 
+    @property
+    def n_diagrams(self):
+        """Feynman diagrams of the process's program."""
+        return self.desc.prog.n_diagrams
+
     @classmethod
     def from_workload(cls, wl, **kw):
         return cls(descriptor_for_workload(wl, **kw))
