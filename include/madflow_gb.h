@@ -394,6 +394,43 @@ mf_status mf_lhe_open(const char *path, const mf_lhe_init *init, mf_lhe_writer *
 mf_status mf_lhe_write(mf_lhe_writer *w, const double *records, int64_t n);
 mf_status mf_lhe_close(mf_lhe_writer *w, int64_t *n_written);
 
+/* Observables of a final-state leg in the collider frame (the partonic
+ * centre-of-mass momenta boosted along the beam axis by the rapidity of the
+ * parton pair), for the weighted histograms of mf_vegas_observables (the
+ * differential distributions of Sec. 3.1, Fig. 2):
+ *   MF_OBS_PT              pT  = sqrt(px^2 + py^2)                (GeV)
+ *   MF_OBS_RAPIDITY        y   = (1/2) ln((E + pz) / (E - pz))
+ *   MF_OBS_PSEUDORAPIDITY  eta = asinh(pz / pT)
+ * nbins (1 .. 64) equal bins on [lo, hi): v goes to bin
+ * b = floor((v - lo) * (nbins / (hi - lo))) when 0 <= b < nbins, else nowhere. */
+typedef enum { MF_OBS_PT = 0, MF_OBS_RAPIDITY = 1, MF_OBS_PSEUDORAPIDITY = 2 } mf_observable_kind;
+#define MF_MAX_OBSERVABLES 4
+typedef struct {
+    int32_t kind;                  /* mf_observable_kind */
+    int32_t leg;                   /* final-state leg: 2 .. n_legs - 1 */
+    int32_t nbins;
+    int32_t pad;
+    double lo, hi;
+} mf_observable;
+
+/* mf_vegas_observables: one pass of n_events (>= 2) Vegas points through the
+ * grid as it stands (the points mf_vegas_unweight uses: the grid's current
+ * iteration index, subprocess index `subprocess`, Philox key seed; the grid is
+ * neither refined nor advanced), and for each of n_obs (1 ..
+ * MF_MAX_OBSERVABLES) observables the histogram of the points' weights
+ * w_i = f J_V over its bins; points failing the threshold or the cuts are
+ * not binned.  Per bin b, in observable order (host arrays of sum_k nbins_k):
+ *   sigma[b] = (1/N) sum_{i in b} w_i                     (pb in the bin)
+ *   error[b] = sqrt((sum_{i in b} w_i^2 / N - sigma[b]^2) / (N - 1))
+ *   counts[b] = points in the bin (may be NULL).
+ * The sums are taken in a fixed order (per 4096-point chunk, then a pairwise
+ * tree over the chunks), so the results do not change from run to run.
+ * MF_ENAN if some weights were not finite (those points are not binned).
+ * Synchronous. */
+mf_status mf_vegas_observables(mf_vegas *v, mf_process *p, int64_t n_events, uint64_t seed, int32_t subprocess,
+                               mf_precision prec, int32_t n_obs, const mf_observable *obs, double *sigma,
+                               double *error, int64_t *counts, void *stream);
+
 /* mf_vegas_unweight: one pass of n_events Vegas points through the grid as it
  * stands (points of the grid's current iteration index, subprocess index
  * `subprocess`, Philox key seed; the grid is neither refined nor advanced),

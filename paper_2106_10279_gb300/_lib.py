@@ -54,6 +54,15 @@ class mf_process_info(C.Structure):
                 ("pair_leg", c_i32), ("n_pairs", c_i32), ("flops_helicity_sum", C.c_double)]
 
 
+class mf_observable(C.Structure):
+    _fields_ = [("kind", c_i32), ("leg", c_i32), ("nbins", c_i32), ("pad", c_i32), ("lo", C.c_double),
+                ("hi", C.c_double)]
+
+
+MF_OBS_PT, MF_OBS_RAPIDITY, MF_OBS_PSEUDORAPIDITY = 0, 1, 2
+MF_MAX_OBSERVABLES = 4
+
+
 class mf_lhe_init(C.Structure):
     _fields_ = [("n_legs", c_i32), ("pdg", c_i32 * 8), ("mass", C.c_double * 8), ("beam_pdg", c_i32 * 2),
                 ("beam_energy", C.c_double * 2), ("xsec", C.c_double), ("xsec_error", C.c_double),
@@ -113,6 +122,8 @@ SIGNATURES = {
     "mf_vegas_unweight": (c_i32, [C.c_void_p, C.c_void_p, c_i64, C.c_uint64, c_i32, c_i32, C.c_double, C.c_void_p,
                                   P(C.c_double), c_i64, P(c_i64), C.c_void_p]),
     "mf_process_read_weights": (c_i32, [C.c_void_p, P(c_i64), c_i64, P(C.c_double)]),
+    "mf_vegas_observables": (c_i32, [C.c_void_p, C.c_void_p, c_i64, C.c_uint64, c_i32, c_i32, c_i32,
+                                     P(mf_observable), P(C.c_double), P(C.c_double), P(c_i64), C.c_void_p]),
     "mf_process_max_weight": (c_i32, [C.c_void_p, P(C.c_double), C.c_void_p]),
     "mf_vegas_save": (c_i32, [C.c_void_p, C.c_void_p, P(C.c_size_t)]),
     "mf_vegas_load": (c_i32, [C.c_void_p, C.c_void_p, C.c_size_t]),

@@ -547,6 +547,32 @@ def unweight(grid: "Vegas", proc: "Process", n_events: int, seed: int, w_max: fl
     return nacc.value, rec[:min(nacc.value, cap)]
 
 
+OBSERVABLE_KINDS = {"pt": L.MF_OBS_PT, "y": L.MF_OBS_RAPIDITY, "eta": L.MF_OBS_PSEUDORAPIDITY}
+
+
+def observables(grid: "Vegas", proc: "Process", n_events: int, seed: int, obs, precision="mixed", subprocess=0,
+                stream=None):
+    """Weighted histograms of one pass (see mf_vegas_observables).  obs: list
+    of (kind, leg, nbins, lo, hi), kind "pt", "y" or "eta"; returns one
+    (sigma, error, counts) per observable, sigma and error in pb per bin."""
+    arr = (L.mf_observable * len(obs))()
+    for a, (kind, leg, nbins, lo, hi) in zip(arr, obs):
+        a.kind, a.leg, a.nbins, a.lo, a.hi = OBSERVABLE_KINDS[kind], leg, nbins, lo, hi
+    nb = sum(o[2] for o in obs)
+    sig, err = np.zeros(nb), np.zeros(nb)
+    cnt = np.zeros(nb, dtype=np.int64)
+    L.check(L.lib().mf_vegas_observables(grid.handle, proc.handle, n_events, seed, subprocess, _PREC[precision],
+                                         len(obs), arr, sig.ctypes.data_as(C.POINTER(C.c_double)),
+                                         err.ctypes.data_as(C.POINTER(C.c_double)),
+                                         cnt.ctypes.data_as(C.POINTER(C.c_int64)), _stream_ptr(stream)),
+            "mf_vegas_observables")
+    out, o = [], 0
+    for kind, leg, nbins, lo, hi in obs:
+        out.append((sig[o:o + nbins], err[o:o + nbins], cnt[o:o + nbins]))
+        o += nbins
+    return out
+
+
 def read_weights(proc: "Process", idx):
     """Weights w = f J_V of the given point indices of the last Vegas pass."""
     idx = np.ascontiguousarray(idx, dtype=np.int64)

@@ -8,6 +8,7 @@ typedef unsigned long long uint64_t;
 typedef long long int64_t;
 typedef unsigned int uint32_t;
 typedef int int32_t;
+typedef unsigned short uint16_t;
 typedef signed char int8_t;
 typedef unsigned char uint8_t;
 #else

@@ -208,7 +208,7 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
         if (e < kp.n) {
             // ---------------- phase A: kinematics in double precision
             double y[NDIM];
-            if (kp.mode != 1 && kp.mode != 3) {
+            if (kp.mode != 1 && kp.mode != 3 && kp.mode != 4) {
 #pragma unroll
                 for (int j = 0; j < NDIM; ++j) y[j] = kp.x[(int64_t)j * kp.n + e];
             } else {
@@ -247,6 +247,26 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
                     rec[5 + 4 * i] = ok ? sh * ev.p[i][0] + ch * ev.p[i][3] : 0.0;
                 }
                 ok = false;            // no helicity work for records
+            }
+            if (kp.mode == 4) {
+                // observables of the point in the collider frame (boost along
+                // z by the rapidity of the parton pair); points failing the
+                // threshold or the cuts are not binned
+                const double ch = cosh(ev.yb), sh = sinh(ev.yb);
+                for (int k = 0; k < kp.n_obs; ++k) {
+                    uint16_t b = 0xFFFFu;
+                    if (ok) {
+                        const double *q = ev.p[kp.obs_leg[k]];
+                        const double E = ch * q[0] + sh * q[3], pz = sh * q[0] + ch * q[3];
+                        const double pt = sqrt(q[1] * q[1] + q[2] * q[2]);
+                        const int kind = kp.obs_kind[k];
+                        const double v = kind == 0 ? pt : kind == 1 ? 0.5 * log((E + pz) / (E - pz)) : asinh(pz / pt);
+                        const double t = (v - kp.obs_lo[k]) * kp.obs_scale[k];
+                        if (t >= 0.0 && t < (double)kp.obs_nbins[k]) b = (uint16_t)t;
+                    }
+                    kp.obs_out[(int64_t)k * kp.n + e] = b;
+                }
+                ok = false;            // no helicity work for observables
             }
             if (ok && kp.hel_sample) {
                 // helicity sampling: one helicity per point, uniform over the

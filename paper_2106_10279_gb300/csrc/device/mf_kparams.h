@@ -4,13 +4,15 @@
 #pragma once
 
 #define MF_KP_MAX_HEL 256
+#define MF_KP_MAX_OBS 4
 
 struct mf_kparams {
     int64_t n;                 // events
     int32_t mode;              // 0: integrand of given points, 1: Vegas,
                                // 2: per-helicity |M|^2 of given points into f[h][n],
                                // 3: event records of the Vegas points idx[0..n) into
-                               //    f[n][2 + 4 NLEG] (x1, x2, lab-frame momenta)
+                               //    f[n][2 + 4 NLEG] (x1, x2, lab-frame momenta),
+                               // 4: observable bins of the Vegas points into obs_out
     int32_t nhel;              // helicity rows in hel[]
     int32_t nhel_pow2;         // a power of two >= nhel (pairwise-sum padding)
     int32_t nb;                // Vegas bins per dimension
@@ -42,6 +44,14 @@ struct mf_kparams {
     int32_t npairs_pow2;       // a power of two >= npairs
     int32_t pad3;
     const long long *iter_dev; // if set, the iteration index is read here (graph replays)
+    uint16_t *obs_out;         // mode 4: bins [n_obs][n], 0xFFFF: not binned
+    int32_t n_obs;             // mode 4: observables
+    int32_t obs_kind[MF_KP_MAX_OBS];   // 0: pT, 1: rapidity, 2: pseudorapidity (collider frame)
+    int32_t obs_leg[MF_KP_MAX_OBS];
+    int32_t obs_nbins[MF_KP_MAX_OBS];
+    int32_t pad4;
+    double obs_lo[MF_KP_MAX_OBS];      // bin b = floor((v - lo) * scale) if 0 <= b < nbins
+    double obs_scale[MF_KP_MAX_OBS];   // nbins / (hi - lo)
     double masses[8];
     double couplings[16];      // 8 complex couplings (re, im)
     int8_t hel[MF_KP_MAX_HEL][8];

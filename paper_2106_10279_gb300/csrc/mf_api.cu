@@ -1928,6 +1928,192 @@ extern "C" mf_status mf_batch_iterate_graph(mf_batch *b, mf_vegas *const *grids,
 }
 
 // ----------------------------------------------------------------------------
+// Weighted histograms of observables of a Vegas pass.
+// ----------------------------------------------------------------------------
+static_assert(MF_KP_MAX_OBS == MF_MAX_OBSERVABLES, "observable table sizes");
+namespace {
+constexpr int kObsBins = 64;            // bins per observable at most
+
+// One block per chunk of kChunk points: per observable and bin the sums of w
+// and w^2 and the count of the chunk's points; each warp adds its kChunk/8
+// consecutive points in point order (lanes of one bin by the lowest of them,
+// in lane order), then the 8 warps' sums are added in a fixed tree.
+// Partials part[chunk][obs][kObsBins][3].  Non-finite weights are not binned.
+__global__ void __launch_bounds__(kAccThreads) obs_accumulate_kernel(const double *w, const uint16_t *obs,
+                                                                     int64_t n, int n_obs, double *part,
+                                                                     int *nan_flag) {
+    constexpr int kWarps = kAccThreads / 32, kPerWarp = kChunk / kWarps;
+    __shared__ double s1[kWarps][kObsBins], s2[kWarps][kObsBins];
+    __shared__ int sc[kWarps][kObsBins];
+    __shared__ double stage[kWarps][32];
+    const int64_t base = (int64_t)blockIdx.x * kChunk;
+    const int m = (int)((n - base) < kChunk ? (n - base) : kChunk);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = 0; k < n_obs; ++k) {
+        for (int q = lane; q < kObsBins; q += 32) {
+            s1[warp][q] = 0.0;
+            s2[warp][q] = 0.0;
+            sc[warp][q] = 0;
+        }
+        __syncwarp();
+        for (int step = 0; step < kPerWarp / 32; ++step) {
+            const int i = warp * kPerWarp + step * 32 + lane;
+            double v = 0.0;
+            int b = 0xFFFF;
+            if (i < m) {
+                v = w[base + i];
+                b = obs[(int64_t)k * n + base + i];
+                if (!isfinite(v)) {
+                    if (k == 0) atomicExch(nan_flag, 1);
+                    b = 0xFFFF;
+                }
+            }
+            stage[warp][lane] = v;
+            const unsigned peers = __match_any_sync(0xffffffffu, b);
+            __syncwarp();
+            if (b < kObsBins && lane == __ffs(peers) - 1) {
+                double a1 = s1[warp][b], a2 = s2[warp][b];
+                int c = sc[warp][b];
+                for (unsigned mk = peers; mk; mk &= mk - 1) {
+                    const double x = stage[warp][__ffs(mk) - 1];
+                    a1 += x;
+                    a2 += x * x;
+                    ++c;
+                }
+                s1[warp][b] = a1;
+                s2[warp][b] = a2;
+                sc[warp][b] = c;
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        if (threadIdx.x < kObsBins) {
+            const int q = threadIdx.x;
+            static_assert(kWarps == 8, "fixed 8-warp tree");
+            double *o = part + (((int64_t)blockIdx.x * n_obs + k) * kObsBins + q) * 3;
+            o[0] = ((s1[0][q] + s1[1][q]) + (s1[2][q] + s1[3][q])) + ((s1[4][q] + s1[5][q]) + (s1[6][q] + s1[7][q]));
+            o[1] = ((s2[0][q] + s2[1][q]) + (s2[2][q] + s2[3][q])) + ((s2[4][q] + s2[5][q]) + (s2[6][q] + s2[7][q]));
+            int c = 0;
+            for (int ww = 0; ww < kWarps; ++ww) c += sc[ww][q];
+            o[2] = (double)c;
+        }
+        __syncthreads();
+    }
+}
+
+// Fixed pairwise sum of v[lo, hi) (halves split at the midpoint).
+double pairwise_sum(const std::vector<double> &v, size_t lo, size_t hi) {
+    if (hi - lo == 0) return 0.0;
+    if (hi - lo == 1) return v[lo];
+    const size_t mid = lo + (hi - lo) / 2;
+    return pairwise_sum(v, lo, mid) + pairwise_sum(v, mid, hi);
+}
+}  // namespace
+
+extern "C" mf_status mf_vegas_observables(mf_vegas *v, mf_process *p, int64_t n_events, uint64_t seed,
+                                          int32_t subprocess, mf_precision prec, int32_t n_obs,
+                                          const mf_observable *obs, double *sigma, double *error, int64_t *counts,
+                                          void *stream) {
+    if (!v || !p || !obs || !sigma || !error) return fail(MF_EINVAL, "NULL argument");
+    if (!valid_prec(prec)) return fail(MF_EINVAL, "bad precision");
+    if (v->ndim != p->ndim) return fail(MF_EINVAL, "grid and process dimensions differ");
+    if (n_events < 2) return fail(MF_EINVAL, "need at least two points");
+    if (subprocess < 0) return fail(MF_EINVAL, "bad subprocess index");
+    if (n_obs < 1 || n_obs > MF_KP_MAX_OBS) return fail(MF_EINVAL, "n_obs must be 1 .. MF_MAX_OBSERVABLES");
+    for (int k = 0; k < n_obs; ++k) {
+        const mf_observable &o = obs[k];
+        if (o.kind < MF_OBS_PT || o.kind > MF_OBS_PSEUDORAPIDITY) return fail(MF_EINVAL, "bad observable kind");
+        if (o.leg < 2 || o.leg >= p->n_legs) return fail(MF_EINVAL, "observable leg must be a final-state leg");
+        if (o.nbins < 1 || o.nbins > kObsBins) return fail(MF_EINVAL, "nbins must be 1 .. 64");
+        if (!std::isfinite(o.lo) || !std::isfinite(o.hi) || !(o.hi > o.lo)) return fail(MF_EINVAL, "bad range");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = n_events;
+    mf_status st = compile_precision(p, prec);
+    if (st != MF_OK) return st;
+    st = ensure_scratch(p, v, n);
+    if (st != MF_OK) return st;
+    // the weights of the pass
+    mf_kparams kp;
+    vegas_params(p, v, n, 0, subprocess, seed, kp);
+    st = launch(p, prec, kp, s);
+    if (st != MF_OK) return st;
+    p->last_n = n;
+    // the observables' bins of the same points, recomputed from their Philox
+    // counters (no helicity work)
+    const int64_t nchunks = (n + kChunk - 1) / kChunk;
+    uint16_t *d_obs = nullptr;
+    double *d_part = nullptr;
+    int *d_nan = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(d_obs);
+        cudaFree(d_part);
+        cudaFree(d_nan);
+    };
+#define MF_OB(call)                                                                            \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            cleanup();                                                                         \
+            return fail(MF_ECUDA, std::string("observables: ") + cudaGetErrorString(e_));      \
+        }                                                                                      \
+    } while (0)
+    MF_OB(cudaMalloc(&d_obs, sizeof(uint16_t) * (size_t)n_obs * n));
+    MF_OB(cudaMalloc(&d_part, sizeof(double) * (size_t)nchunks * n_obs * kObsBins * 3));
+    MF_OB(cudaMalloc(&d_nan, sizeof(int)));
+    MF_OB(cudaMemsetAsync(d_nan, 0, sizeof(int), s));
+    mf_kparams ko;
+    vegas_params(p, v, n, 0, subprocess, seed, ko);
+    ko.mode = 4;
+    ko.obs_out = d_obs;
+    ko.n_obs = n_obs;
+    for (int k = 0; k < n_obs; ++k) {
+        ko.obs_kind[k] = obs[k].kind;
+        ko.obs_leg[k] = obs[k].leg;
+        ko.obs_nbins[k] = obs[k].nbins;
+        ko.obs_lo[k] = obs[k].lo;
+        ko.obs_scale[k] = obs[k].nbins / (obs[k].hi - obs[k].lo);
+    }
+    st = launch(p, prec, ko, s);
+    if (st != MF_OK) {
+        cleanup();
+        return st;
+    }
+    obs_accumulate_kernel<<<(unsigned)nchunks, kAccThreads, 0, s>>>(p->d_w, d_obs, n, n_obs, d_part, d_nan);
+    MF_OB(cudaGetLastError());
+    std::vector<double> part((size_t)nchunks * n_obs * kObsBins * 3);
+    int flag = 0, any_nan = 0;
+    MF_OB(cudaMemcpyAsync(part.data(), d_part, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, s));
+    MF_OB(cudaMemcpyAsync(&any_nan, d_nan, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MF_OB(cudaMemcpyAsync(&flag, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MF_OB(cudaStreamSynchronize(s));
+#undef MF_OB
+    cleanup();
+    st = flag_status(p, flag);
+    if (st != MF_OK) return st;
+    // chunk partials combined along a fixed pairwise tree over the chunk index
+    std::vector<double> col(nchunks);
+    size_t out = 0;
+    const double N = (double)n;
+    for (int k = 0; k < n_obs; ++k)
+        for (int b = 0; b < obs[k].nbins; ++b, ++out) {
+            double r[3];
+            for (int c = 0; c < 3; ++c) {
+                for (int64_t ch = 0; ch < nchunks; ++ch)
+                    col[ch] = part[(((size_t)ch * n_obs + k) * kObsBins + b) * 3 + c];
+                r[c] = pairwise_sum(col, 0, col.size());
+            }
+            const double sg = r[0] / N;
+            const double var = (r[1] / N - sg * sg) / (N - 1.0);
+            sigma[out] = sg;
+            error[out] = std::sqrt(var > 0.0 ? var : 0.0);
+            if (counts) counts[out] = (int64_t)r[2];
+        }
+    if (any_nan) return fail(MF_ENAN, "some points had non-finite weights (not binned)");
+    return MF_OK;
+}
+
+// ----------------------------------------------------------------------------
 // Unweighting (hit or miss against w_max) and event records.
 // ----------------------------------------------------------------------------
 namespace {

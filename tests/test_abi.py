@@ -52,7 +52,8 @@ def test_struct_layouts_match_the_c_compiler(built, tmp_path):
     # the header, against the ctypes mirror used by the binding
     structs = {"mf_op": built.mf_op, "mf_colour_term": built.mf_colour_term,
                "mf_process_desc": built.mf_process_desc, "mf_process_info": built.mf_process_info,
-               "mf_iter_result": built.mf_iter_result, "mf_lhe_init": built.mf_lhe_init}
+               "mf_iter_result": built.mf_iter_result, "mf_lhe_init": built.mf_lhe_init,
+               "mf_observable": built.mf_observable}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "madflow_gb.h"', "int main(void) {"]
     for sname, cls in structs.items():
         lines.append(f'printf("{sname} size %zu\\n", sizeof({sname}));')
