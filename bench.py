@@ -32,7 +32,7 @@ METRIC = "events/s of gg→tt̄g(g) LO integrand: mixed/batched vs FP64 at ≤1e
 # dram__bytes_read.sum + dram__bytes_write.sum of a one-pass ncu capture of
 # one full-size 4e7-point gg->tt~gg iteration divided by its points (the
 # capture's kernel is the one built from this source)
-KERNEL_DRAM_BYTES_PER_POINT = {("gg_ttxgg", "mixed"): (91.26e6 + 15.73e9) / 4e7}
+KERNEL_DRAM_BYTES_PER_POINT = {("gg_ttxgg", "mixed"): (102.06e6 + 15.39e9) / 4e7}
 WORKLOAD = "gg_ttxgg"
 
 
