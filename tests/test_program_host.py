@@ -27,7 +27,16 @@ import workloads as W
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _build(tmp, name, units):
+# A gauge vector for the host build: the device header's external vector
+# wavefunction, with helicity code 0 returning the leg's momentum over its
+# energy instead of a polarisation (a copy of the header, placed where the
+# generated program looks first; the device header itself is unchanged).
+_VXX_HEAD = "MF_DEV W<R> vxx(const R *k, int l, int incoming) {\n    W<R> w;\n"
+_VXX_GAUGE = ("    if (l == 0) {\n        for (int m = 0; m < 4; ++m) w.c[m] = C<R>(k[m] / k[0], R(0));\n"
+              "        return w;\n    }\n")
+
+
+def _build(tmp, name, units, gauge=False):
     from paper_2106_10279_gb300 import api
     gxx = shutil.which("g++")
     if gxx is None:
@@ -42,6 +51,10 @@ def _build(tmp, name, units):
     src = src[:src.index('#include "mf_kernel.cuh"')]
     leg = int(re.search(r"constexpr int PAIR_LEG = (-?\d+);", src).group(1))
     (tmp / "mf_program_gen.h").write_text(src)
+    if gauge:
+        helas = open(os.path.join(ROOT, "paper_2106_10279_gb300", "csrc", "device", "mf_helas.cuh")).read()
+        assert helas.count(_VXX_HEAD) == 1
+        (tmp / "mf_helas.cuh").write_text(helas.replace(_VXX_HEAD, _VXX_HEAD + _VXX_GAUGE))
     exe = tmp / "program_check"
     subprocess.run([gxx, "-std=c++17", "-O1", "-w", "-I", str(tmp),
                     "-I", os.path.join(ROOT, "paper_2106_10279_gb300", "csrc", "device"),
@@ -96,3 +109,35 @@ def test_generated_programs_match_the_oracle(tmp_path, oracle_processes, name, n
     ea = np.abs(got2[:, :, 0] - per[ia].T) / tot[:, None]
     eb = np.abs(got2[:, :, 1] - per[ib].T) / tot[:, None]
     assert max(ea.max(), eb.max()) <= 1e-12, (name, ea.max(), eb.max())
+
+
+@pytest.mark.parametrize("units", [None, "1"])
+@pytest.mark.parametrize("name,n", [("gg_ttx", 4), ("gg_ttxg", 4), ("uux_ttxg", 4), ("gg_ttxgg", 2)])
+def test_generated_programs_are_gauge_invariant(tmp_path, oracle_processes, name, n, units):
+    # a gluon's polarisation replaced by its momentum: every amplitude of the
+    # generated program (one helicity and pairs) vanishes with the other
+    # gluons transverse (the Ward identity), independently of the oracle's
+    # values; bound relative to the point's helicity sum, as the oracle's own
+    # gauge test
+    from oracle.integrand import Integrand
+    wl = W.WORKLOADS[name]
+    orc = Integrand(wl, process=oracle_processes(name))
+    run, leg = _build(tmp_path, name, units, gauge=True)
+    x = W.uniform_points(wl.ndim, 4 * n, 77)
+    p, s_hat, x1, x2, jx, w, ok = orc.kinematics(x)
+    p = p[ok & orc.cuts(p)][:n]
+    assert p.shape[0] == n
+    nleg = p.shape[1]
+    rows = list(itertools.product((-1, 1), repeat=nleg))
+    tot = run([_line("msq", h, p[i]) for i in range(n) for h in rows]).reshape(n, len(rows)).sum(axis=1)
+    assert np.all(tot > 0)
+    gluons = [l for l, lg in enumerate(wl.legs) if lg.particle == "g"]
+    assert gluons
+    for g in gluons:
+        grow = sorted({tuple(0 if l == g else v for l, v in enumerate(h)) for h in rows})
+        val = run([_line("msq", h, p[i]) for i in range(n) for h in grow]).reshape(n, len(grow))
+        assert np.max(np.abs(val).sum(axis=1) / tot) < 1e-12, (name, g)
+        if leg >= 0 and leg != g:
+            firsts = [h for h in grow if h[leg] == -1]
+            val2 = run([_line("pair", h, p[i]) for i in range(n) for h in firsts])
+            assert np.max(np.abs(val2).reshape(n, -1).sum(axis=1) / tot) < 1e-12, (name, g, "pair")
