@@ -141,3 +141,33 @@ def test_generated_programs_are_gauge_invariant(tmp_path, oracle_processes, name
             firsts = [h for h in grow if h[leg] == -1]
             val2 = run([_line("pair", h, p[i]) for i in range(n) for h in firsts])
             assert np.max(np.abs(val2).reshape(n, -1).sum(axis=1) / tot) < 1e-12, (name, g, "pair")
+
+
+def _boost(p, beta):
+    """General Lorentz boost of momenta p [..., 4] by velocity beta [3]."""
+    b2 = float(np.dot(beta, beta))
+    gamma = 1.0 / np.sqrt(1.0 - b2)
+    bp = p[..., 1:] @ beta
+    out = np.empty_like(p)
+    out[..., 0] = gamma * (p[..., 0] + bp)
+    out[..., 1:] = p[..., 1:] + ((gamma - 1.0) * bp / b2 + gamma * p[..., 0])[..., None] * beta
+    return out
+
+
+@pytest.mark.parametrize("name,n", [("gg_ttx", 4), ("gg_ttxg", 4), ("uux_ttxg", 4), ("gg_ttxgg", 2)])
+def test_generated_programs_are_lorentz_invariant(tmp_path, oracle_processes, name, n):
+    # the helicity sum of the generated program is the same in a boosted
+    # frame (denominators recomputed from the boosted momenta), independently
+    # of the oracle's values
+    from oracle.integrand import Integrand
+    wl = W.WORKLOADS[name]
+    orc = Integrand(wl, process=oracle_processes(name))
+    run, leg = _build(tmp_path, name, None)
+    x = W.uniform_points(wl.ndim, 4 * n, 91)
+    p, s_hat, x1, x2, jx, w, ok = orc.kinematics(x)
+    p = p[ok & orc.cuts(p)][:n]
+    q = _boost(p, np.array([0.3, -0.45, 0.6]))
+    rows = list(itertools.product((-1, 1), repeat=p.shape[1]))
+    a = run([_line("msq", h, p[i]) for i in range(n) for h in rows]).reshape(n, len(rows)).sum(axis=1)
+    b = run([_line("msq", h, q[i]) for i in range(n) for h in rows]).reshape(n, len(rows)).sum(axis=1)
+    assert np.max(np.abs(b / a - 1)) < 1e-10, name
