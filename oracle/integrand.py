@@ -236,6 +236,57 @@ class Integrand:
             f[idx] = jx[idx] * w[idx] * lum * msq / (2.0 * s_hat[idx]) * W.GEV2_TO_PB
         return f, pick
 
+    @staticmethod
+    def helicity_pairs(helicities, leg: int):
+        """The helicity list grouped into pairs that differ only at `leg`
+        (first member: helicity -1 there, second: +1; None where that
+        assignment is not in the list), in the order of each pair's first row."""
+        pairs, where = [], {}
+        for h in helicities:
+            key = tuple(v for l, v in enumerate(h) if l != leg)
+            if key not in where:
+                where[key] = len(pairs)
+                pairs.append([None, None])
+            pairs[where[key]][0 if h[leg] == -1 else 1] = tuple(h)
+        return [tuple(q) for q in pairs]
+
+    def sampled_pairs(self, x, seed: int, pairs, pick=None):
+        """f with one helicity pair per point: pair pick[i] (drawn like the
+        single helicity of `sampled`, from the first unit number of Philox
+        counter (i, 0, 0, 14), over the pair list), its present members'
+        |M_h|^2 summed and multiplied by the number of pairs (unbiased: the
+        mean over the pairs is the full helicity sum)."""
+        from oracle.philox import philox4x64_10, to_unit
+        x = np.asarray(x, dtype=np.float64)
+        N = x.shape[1]
+        npair = len(pairs)
+        if pick is None:
+            ctr = np.zeros((N, 4), dtype=np.uint64)
+            ctr[:, 0] = np.arange(N, dtype=np.uint64)
+            ctr[:, 3] = np.uint64(14)
+            u = to_unit(philox4x64_10(ctr, np.array([seed, 0], dtype=np.uint64))[:, 0])
+            pick = np.minimum((u * npair).astype(np.int64), npair - 1)
+        p, s_hat, x1, x2, jx, w, ok = self.kinematics(x)
+        keep = ok & self.cuts(p)
+        f = np.zeros(N)
+        idx = np.nonzero(keep)[0]
+        if len(idx):
+            order = {h: k for k, h in enumerate(self.proc.helicities())}
+            _, per = self.proc.msq_summed(p[idx], per_helicity=True)
+            cols = np.arange(len(idx))
+            msq = np.zeros(len(idx))
+            for m in range(2):
+                rows = [pairs[k][m] for k in pick[idx]]
+                have = np.array([r is not None for r in rows])
+                r_idx = np.array([order[r] if r is not None else 0 for r in rows])
+                msq = msq + np.where(have, per[r_idx, cols], 0.0)
+            msq = npair * msq * self.proc.average_factor()
+            lum = np.ones(len(idx))
+            if self.wl.beams:
+                lum = (self.pdfs[0].f(x1[idx], self.wl.mu_f2) * self.pdfs[1].f(x2[idx], self.wl.mu_f2))
+            f[idx] = jx[idx] * w[idx] * lum * msq / (2.0 * s_hat[idx]) * W.GEV2_TO_PB
+        return f, pick
+
     # ------------------------------------------------------------------
     # condition numbers: how far two correct evaluations of f in different
     # operation orders can drift apart, in units of eps

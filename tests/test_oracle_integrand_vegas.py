@@ -171,3 +171,33 @@ def test_helicity_sampling_is_unbiased(oracle_processes):
     _, pick = I.sampled(W.uniform_points(wl.ndim, 4000, 6), 3, hels)
     counts = np.bincount(pick, minlength=nh)
     assert counts.sum() == 4000 and np.all(np.abs(counts - 4000 / nh) < 5 * np.sqrt(4000 / nh))
+
+
+def test_helicity_pair_sampling_is_unbiased(oracle_processes):
+    # pairs of the kept helicities that differ at one leg: averaging the
+    # pair-sampled integrand over the pair choice gives the full helicity sum
+    # exactly; gg -> tt~ paired at the antitop: the 12 kept rows form 8 pairs,
+    # 4 of them with one member (equal gluon helicities keep only equal top
+    # helicities)
+    import workloads as W
+    from oracle.integrand import Integrand
+    wl = W.GG_TTX
+    I = Integrand(wl, process=oracle_processes("gg_ttx"))
+    hels = I.nonzero_helicities()
+    pairs = Integrand.helicity_pairs(hels, 3)
+    assert len(pairs) == 8
+    assert sum(1 for a, b in pairs if a is None or b is None) == 4
+    assert sorted(h for q in pairs for h in q if h is not None) == sorted(tuple(h) for h in hels)
+    for a, b in pairs:
+        if a is not None and b is not None:
+            assert a[:3] == b[:3] and (a[3], b[3]) == (-1, 1)
+    x = W.uniform_points(wl.ndim, 40, 5)
+    full = I(x)
+    mean = sum(I.sampled_pairs(x, 0, pairs, pick=np.full(40, u))[0] for u in range(8)) / 8
+    nz = full != 0
+    assert np.all((mean == 0) == (full == 0))
+    assert np.max(np.abs(mean[nz] / full[nz] - 1)) < 1e-13
+    # the same Philox draw as single-helicity sampling, over the pair list
+    _, pick = I.sampled_pairs(W.uniform_points(wl.ndim, 4000, 6), 3, pairs)
+    counts = np.bincount(pick, minlength=8)
+    assert counts.sum() == 4000 and np.all(np.abs(counts - 500) < 5 * np.sqrt(500))
