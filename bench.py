@@ -32,7 +32,7 @@ METRIC = "events/s of gg→tt̄g(g) LO integrand: mixed/batched vs FP64 at ≤1e
 # dram__bytes_read.sum + dram__bytes_write.sum of a one-pass ncu capture of
 # one full-size 4e7-point gg->tt~gg iteration divided by its points (the
 # capture's kernel is the one built from this source)
-KERNEL_DRAM_BYTES_PER_POINT = {("gg_ttxgg", "mixed"): (102.06e6 + 15.39e9) / 4e7}
+KERNEL_DRAM_BYTES_PER_POINT = {("gg_ttxgg", "mixed"): (144.32e6 + 22.65e9) / 4e7}
 WORKLOAD = "gg_ttxgg"
 
 
@@ -296,15 +296,17 @@ def run_native(args):
     e2e_value = world * n_events * args.steps / t_e2e
 
     # variants of the same kernel on a sample of the workload: the colour sum
-    # on the tensor cores, and one sampled helicity per point (a different,
-    # unbiased estimator with more variance: reported with its error)
+    # on the tensor cores, and one sampled helicity or helicity pair per point
+    # (different, unbiased estimators with more variance: reported with their
+    # errors)
     variants = {}
     if not args.no_batch:
         nv = min(n_events, 2_000_000)
         gv = api.Vegas(wl.ndim, wl.n_bins, wl.alpha_vegas)
         gv.load(start_state)
-        for tag, prec, sample in (("mixed", "mixed", False), ("mixed_tc", "mixed_tc", False),
-                                  ("mixed_helicity_sampling", "mixed", True)):
+        for tag, prec, sample in (("mixed", "mixed", 0), ("mixed_tc", "mixed_tc", 0),
+                                  ("mixed_helicity_sampling", "mixed", 1),
+                                  ("mixed_helicity_pair_sampling", "mixed", 2)):
             proc.set_helicity_sampling(sample, seed=5)
             api.mf_vegas_iterate([gv.handle], [proc.handle], [nv], seed, prec, False, stream)
             torch.cuda.synchronize()

@@ -493,14 +493,25 @@ mf_status mf_vegas_save(const mf_vegas *v, void *buf, size_t *len);
 mf_status mf_vegas_load(mf_vegas *v, const void *buf, size_t len);
 
 /* Helicity sampling (the Monte Carlo over helicities that Sec. 4 names as a
- * way to cut the cost per point): with on != 0 the integrand kernels of this
+ * way to cut the cost per point): with on = 1 the integrand kernels of this
  * process evaluate one helicity per point, drawn uniformly from the
  * non-vanishing helicities with the first unit number of Philox counter
  * (i, iteration, subprocess, 14) (Vegas passes: their key; given points:
  * counter (i, 0, 0, 14) with key (seed, 0)), and multiply its |M|^2 by their
  * number: an unbiased estimate of the helicity sum with a larger variance.
- * mf_helicity_msq and mf_grad always sum over helicities. */
+ * With on = 2 the same draw picks one helicity pair (mf_process_get_helicity_
+ * pairs) and the sum of its members' |M|^2 is multiplied by the number of
+ * pairs (a process without pairs samples single helicities).  on = 0: the
+ * full sum.  MF_EINVAL for other values.  mf_helicity_msq and mf_grad always
+ * sum over helicities. */
 mf_status mf_process_set_helicity_sampling(mf_process *p, int32_t on, uint64_t seed);
+
+/* The helicity pairs of a process: pairs[2 k], pairs[2 k + 1] (host, may be
+ * NULL, else room for 2 * n_hel entries) are the rows of
+ * mf_process_get_helicities whose pair leg (mf_process_info.pair_leg) is -1
+ * and +1, or -1 where that assignment vanishes; *n_pairs receives the count
+ * (0: helicities one at a time). */
+mf_status mf_process_get_helicity_pairs(const mf_process *p, int32_t *pairs, int32_t *n_pairs);
 /* Leading-colour approximation (the other cut of the cost per point that
  * Sec. 4 names): with on != 0 the integrand kernels keep only the diagonal
  * of the colour matrix in the colour-flow basis, sum_k C_kk |J_k|^2 / den,

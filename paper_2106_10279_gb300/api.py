@@ -383,8 +383,10 @@ class Process:
         return f
 
     def set_helicity_sampling(self, on=True, seed=0):
-        """One uniformly drawn helicity per point instead of the sum (unbiased)."""
-        L.check(L.lib().mf_process_set_helicity_sampling(self.handle, 1 if on else 0, seed),
+        """One uniformly drawn helicity (on=True or 1) or helicity pair (on=2)
+        per point instead of the sum (unbiased)."""
+        mode = (1 if on else 0) if isinstance(on, bool) else int(on)
+        L.check(L.lib().mf_process_set_helicity_sampling(self.handle, mode, seed),
                 "mf_process_set_helicity_sampling")
 
     def set_leading_colour(self, on=True):
@@ -398,6 +400,16 @@ class Process:
         out = np.zeros((n.value, self.info["n_legs"]), dtype=np.int8)
         L.check(L.lib().mf_process_get_helicities(self.handle, out.ctypes.data_as(C.POINTER(C.c_int8)),
                                                   C.byref(n)), "mf_process_get_helicities")
+        return out
+
+    def helicity_pairs(self):
+        """Rows of helicities() forming each helicity pair, int32 [n_pairs, 2]
+        (pair leg at -1, at +1; -1 where that assignment vanishes)."""
+        n = C.c_int32()
+        L.check(L.lib().mf_process_get_helicity_pairs(self.handle, None, C.byref(n)), "mf_process_get_helicity_pairs")
+        out = np.zeros((n.value, 2), dtype=np.int32)
+        L.check(L.lib().mf_process_get_helicity_pairs(self.handle, out.ctypes.data_as(C.POINTER(C.c_int32)),
+                                                      C.byref(n)), "mf_process_get_helicity_pairs")
         return out
 
     def kernel_info(self, precision="mixed"):

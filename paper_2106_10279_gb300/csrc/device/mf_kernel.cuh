@@ -181,6 +181,13 @@ MF_DEV double helicity_value(const KParams &kp, const R *ms, const R *idn, const
     }
 }
 
+// Whether helicity sampling draws pairs (mode 2, a process with pairs, not
+// the tensor-core kernel, which evaluates single helicities).
+template <bool TC>
+MF_DEV bool sample_pairs(const KParams &kp) {
+    return MF_PROC::PAIR_LEG >= 0 && !TC && kp.hel_sample == 2 && kp.npairs > 0;
+}
+
 // One tile of BLOCK events: phases A, B and C.  Ends with a block barrier.
 // With TC the colour sum of phase B runs on the tensor cores (R = float,
 // BLOCK = 128, tcs set up by the caller).
@@ -269,14 +276,16 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
                 ok = false;            // no helicity work for observables
             }
             if (ok && kp.hel_sample) {
-                // helicity sampling: one helicity per point, uniform over the
-                // non-vanishing ones, from Philox block 14 of the point's counter
+                // helicity sampling: one helicity (or, in mode 2, one helicity
+                // pair) per point, uniform over the non-vanishing ones, from
+                // Philox block 14 of the point's counter
                 uint64_t c[4] = {kp.mode == 0 ? (uint64_t)e
                                  : (kp.mode == 3 ? (uint64_t)kp.idx[e] : (uint64_t)(e + kp.ev0)),
                                  kp.mode == 0 ? 0ull : iteration, kp.mode == 0 ? 0ull : kp.subprocess, 14ull};
                 philox4x64_10(c, kp.seed, 0ull);
-                int h = (int)(unit_from_bits(c[0]) * kp.nhel);
-                if (h >= kp.nhel) h = kp.nhel - 1;
+                const int nchoice = sample_pairs<TC>(kp) ? kp.npairs : kp.nhel;
+                int h = (int)(unit_from_bits(c[0]) * nchoice);
+                if (h >= nchoice) h = nchoice - 1;
                 s_msq[tid] = (double)h;
             }
             if (ok) {
@@ -315,6 +324,7 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
             // evaluates whole pairs, whose two |M|^2 are consecutive leaves
             // of the summation tree
             const bool pairs = PAIR_LEG >= 0 && !TC && !samp && kp.mode <= 1 && kp.npairs > 0;
+            const bool samp_pair = samp && sample_pairs<TC>(kp);
             const int EPR = samp ? BLOCK : BLOCK / HT;  // points per round
             const int sub = samp ? 0 : tid % HT;
             const int nhp = pairs ? kp.npairs_pow2 : kp.nhel_pow2;   // padded units (power of two)
@@ -332,6 +342,14 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
                 const R *ms = s_mom + ev * NLEG * 4;
                 const R *idn = s_den + ev * NDEN1;
                 if constexpr (PAIR_LEG >= 0 && !TC) {
+                    if (samp_pair) {
+                        // the sampled pair: its present members' |M|^2
+                        const uint8_t ia = kp.pairs[hs][0], ib = kp.pairs[hs][1];
+                        R va, vb;
+                        helicity_pair_msq<R>(ms, idn, kp.hel[ia != 0xFF ? ia : ib], cpl, mass_r, va, vb);
+                        ps.add((valid && ia != 0xFF) ? (double)va : 0.0);
+                        ps.add((valid && ib != 0xFF) ? (double)vb : 0.0);
+                    }
                     if (pairs) {
                         for (int k = 0; k < per; ++k) {
                             const int u = sub * per + k;
@@ -344,7 +362,7 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
                         }
                     }
                 }
-                for (int k = 0; k < (pairs ? 0 : per); ++k) {
+                for (int k = 0; k < ((pairs || samp_pair) ? 0 : per); ++k) {
                     const int h = samp ? hs : sub * per + k;
                     const bool hv = h < kp.nhel;
                     double v = helicity_value<R, TC>(kp, ms, idn, kp.hel[hv ? h : 0], cpl, mass_r, tcs);
@@ -354,7 +372,7 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
                 }
                 double part = ps.total();
                 if (samp) {
-                    if (valid) s_msq[ev] = part * (double)kp.nhel;
+                    if (valid) s_msq[ev] = part * (double)(samp_pair ? kp.npairs : kp.nhel);
                 } else {
 #pragma unroll
                     for (int off = 1; off < HT; off <<= 1) {

@@ -970,8 +970,18 @@ extern "C" mf_status mf_process_last_kernel_ms(const mf_process *p, double *ms) 
 
 extern "C" mf_status mf_process_set_helicity_sampling(mf_process *p, int32_t on, uint64_t seed) {
     if (!p) return fail(MF_EINVAL, "NULL process");
-    p->hel_sample = on ? 1 : 0;
+    if (on < 0 || on > 2) return fail(MF_EINVAL, "helicity sampling mode must be 0, 1 or 2");
+    // mode 2 samples helicity pairs; a process without pairs samples single helicities
+    p->hel_sample = (on == 2 && p->pairs.empty()) ? 1 : on;
     p->hel_seed = seed;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_process_get_helicity_pairs(const mf_process *p, int32_t *pairs, int32_t *n_pairs) {
+    if (!p || !n_pairs) return fail(MF_EINVAL, "NULL argument");
+    *n_pairs = (int32_t)(p->pairs.size() / 2);
+    if (pairs)
+        for (size_t k = 0; k < p->pairs.size(); ++k) pairs[k] = p->pairs[k] == 0xFF ? -1 : (int32_t)p->pairs[k];
     return MF_OK;
 }
 
