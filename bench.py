@@ -112,6 +112,22 @@ def _peaks():
         return {}
 
 
+def measured_peaks(device):
+    """The device's FP32 (FFMA and packed FFMA2), FP64 (DFMA) and TF32 MMA
+    peaks from the library's own microbenchmarks (mf_measure_peak), with the
+    SM clocks sampled while they run."""
+    from paper_2106_10279_gb300 import api
+    out = {}
+    for kind in ("fp32_ffma", "fp32_ffma2", "fp64_dfma", "tf32_mma"):
+        clk = Clocks(device)
+        clk.start()
+        tf, ms = api.mf_measure_peak(kind, reps=20)
+        c = clk.stop()
+        out[kind] = {"tflops": tf, "ms": ms, "sm_mhz": c["sm_mhz"] if c else None,
+                     "reasons": c["reasons"] if c else None}
+    return out
+
+
 def cpu_baseline_oracle(wl, n_sample):
     """The oracle as it stands, single-threaded numpy, on n_sample points."""
     import numpy as np
@@ -261,8 +277,7 @@ def run_native(args):
         t64.append(a.elapsed_time(b))
         k64.append(api.mf_process_last_kernel_ms(proc.handle))
     fp64_rate = n64 / (min(t64) / 1e3)
-    # the FP64 kernel against the GPU's FP64 rate (nominal 1.25 TFLOP/s on
-    # GB300; no measured figure is available)
+    # the FP64 kernel's achieved FLOP rate (against the measured DFMA peak below)
     fl64 = r64["n_nonzero"] / world * info["flops_helicity_sum"] + n64 * info["flops_kinematics"]
     fp64_tflops = fl64 / (min(k64) / 1e3) / 1e12
 
@@ -360,9 +375,13 @@ def run_native(args):
     # wavefunctions that do not depend on its pair leg once)
     flops = passing * info["flops_helicity_sum"] + n_events * info["flops_kinematics"]
     achieved = flops / (kms / 1e3) / 1e12
-    peaks = _peaks()
-    sm_max = (peaks.get("sm_max_mhz") or 2070.0)
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    # the roofline denominators, measured here by the library's own
+    # microbenchmarks (FP32: the faster of scalar and packed-pair FMAs)
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    mp = measured_peaks(local)
+    fp32_kind = max(("fp32_ffma", "fp32_ffma2"), key=lambda k: mp[k]["tflops"])
+    fp32_peak = mp[fp32_kind]["tflops"]
+    fp64_peak = mp["fp64_dfma"]["tflops"]
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -380,8 +399,10 @@ def run_native(args):
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": workload_config(wl, n_events, args.precision, proc.n_diagrams, info["n_hel"], info["n_jamp"]),
         "fp64": {"value": fp64_rate, "unit": "events/s", "events": n64,
-                 "roofline": {"bound": "alu", "achieved": fp64_tflops, "peak": 1.25, "unit": "TFLOP/s",
-                              "frac": fp64_tflops / 1.25, "peak_source": "nominal GB300 FP64 rate"}},
+                 "roofline": {"bound": "alu", "achieved": fp64_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+                              "frac": fp64_tflops / fp64_peak,
+                              "peak_source": "measured: mf_measure_peak fp64_dfma (DFMA chains, all SMs)"}},
+        "peaks": {"sms": n_sm, "measured": mp},
         "batch": batch,
         "kernel_variants": variants,
         "accuracy": {"median_rel_mixed_vs_fp64": float(np.median(rel)), "max_rel_mixed_vs_fp64": float(rel.max()),
@@ -392,10 +413,15 @@ def run_native(args):
                                  if (wl.name, args.precision) in KERNEL_DRAM_BYTES_PER_POINT else None),
                      "traffic_note": "bytes per launch from a one-pass ncu capture of a full-size launch, "
                                      "scaled by points; mostly write-back of register spills; "
-                                     f"algorithmic output {n_events * (8 + wl.ndim) / 1e6:.0f} MB",
+                                     f"algorithmic output {n_events * (8 + wl.ndim) / 1e6:.0f} MB; "
+                                     "DRAM is not the bound (see traffic_gbs against the HBM peak)",
+                     "traffic_gbs": (KERNEL_DRAM_BYTES_PER_POINT[(wl.name, args.precision)] * n_events / (kms / 1e3)
+                                     / 1e9 if (wl.name, args.precision) in KERNEL_DRAM_BYTES_PER_POINT else None),
+                     "hbm_peak_gbs": _peaks().get("hbm_gbs"),
                      "kernel": "mf_kernel (fused integrand)", "kernel_ms": kms,
                      "flops_per_passing_point": info["flops_helicity_sum"], "helicity_pairs": info["n_pairs"],
-                     "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"},
+                     "peak_source": f"measured: mf_measure_peak {fp32_kind} ({n_sm} SMs, FMA chains, "
+                                    f"{mp[fp32_kind]['sm_mhz']} MHz median SM clock)"},
         "cpu_baseline": cpu,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -470,16 +470,20 @@ mf_status mf_process_max_weight(mf_process *p, double *w_max, void *stream);
  * to start at zero: every call writes each element before reading it.
  *
  * Set-up: the first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, which may load the library's device code); make that
- * first call before any stream capture.  The process kernel of the requested
- * precision must already be compiled, by an earlier mf_integrand or
- * mf_vegas_iterate call with that precision (compiling allocates): otherwise
- * MF_EINVAL.
+ * (cudaGetSymbolAddress, which may load the library's device code) and keeps
+ * it for later calls; make that first call before any stream capture.  The
+ * kept address belongs to the device's primary context: after a
+ * cudaDeviceReset it is stale, and this entry point must not be called again
+ * in that process.  The process kernel of the requested precision (MF_FP64,
+ * MF_MIXED or MF_MIXED_TC) must already be compiled, by an earlier
+ * mf_integrand or mf_vegas_iterate call with that precision (compiling
+ * allocates): otherwise MF_EINVAL.
  *
  * Calls that overlap in time on the same device share the one array and race:
  * serialise them (one stream, or synchronise between calls, across all
  * threads).  Synchronous: returns after *out (host) is filled.  MF_ENAN as
- * mf_vegas_iterate. */
+ * mf_vegas_iterate; MF_ETIMEOUT or MF_ECUDA when the process kernel flagged
+ * an error (see mf_process_check): the iteration is then not counted. */
 mf_status mf_vegas_iterate_static(mf_vegas *v, mf_process *p, int64_t n_events, uint64_t seed,
                                   mf_precision prec, int32_t refine, mf_iter_result *out, void *stream);
 
@@ -567,6 +571,36 @@ mf_status mf_generate_kernel_source(const mf_process_desc *desc, mf_precision pr
  * given order), as mf_generate_kernel_source. */
 mf_status mf_generate_batch_source(const mf_process_desc *const *descs, int32_t nproc, mf_precision prec,
                                    int32_t compile, char *buf, size_t *len);
+
+/* mf_colour_sum: the colour sum of Sec. 2.4 for n rows of colour flows,
+ * out[r] = sum_kl Re(conj(J_rk) C_kl J_rl) / den with C = cnum / den (host
+ * [nj][nj] integer numerators, symmetric), J (device, FP32, [2 nj][n]: Re J_k
+ * in row 2k, Im J_k in row 2k + 1), out (device FP32 [n]).  use_tc != 0: on
+ * the tensor cores (tcgen05.mma kind::tf32 with J split into a TF32 high and
+ * low part, FP32 accumulation; the fused kernels' MF_MIXED_TC colour sum);
+ * use_tc == 0: FP32 FMAs in the symmetric form of the generated kernels.
+ * nj in {2, 4, 6, 24} (MF_EUNSUPPORTED otherwise).  MF_ETIMEOUT if a bounded
+ * wait on the MMAs' completion expired (results unspecified).  Synchronous
+ * on stream. */
+mf_status mf_colour_sum(const float *J, int64_t n, const int32_t *cnum, int32_t nj, int32_t den,
+                        int32_t use_tc, float *out, void *stream);
+
+/* mf_measure_peak: the device's arithmetic peak measured by the library's
+ * own microbenchmark kernels, the denominators of the fused kernels' roofline
+ * fractions (the paper has no counterpart).  kind 0: FP32 FFMA (8 independent
+ * a = a b + c chains per thread, 4 blocks of 256 threads per SM); kind 1:
+ * FP64 DFMA (the same in double precision); kind 3: FP32 FMA on packed
+ * pairs (fma.rn.f32x2, two FMAs per instruction, otherwise as kind 0);
+ * kind 2: TF32 tensor-core MMA
+ * (one 128-thread block per SM issuing tcgen05.mma kind::tf32 M = 128,
+ * N = 256, K = 8 back to back from shared memory in the no-swizzle K-major
+ * layout of the colour-sum kernel into tensor memory).  One untimed launch,
+ * then reps (>= 1) launches each timed with CUDA events on stream; *tflops
+ * (host) receives the best rate in TFLOP/s (2 FLOPs per FMA lane, 2 M N K
+ * per MMA) and *ms (host, may be NULL) that launch's duration.  Allocates a
+ * few bytes of scratch.  MF_ETIMEOUT if the MMA completion wait (bounded by
+ * 2 s per block) expired.  Synchronous. */
+mf_status mf_measure_peak(int32_t kind, int32_t reps, double *tflops, double *ms, void *stream);
 
 /* Thread-local description of the last error (empty string if none). */
 const char *mf_last_error(void);

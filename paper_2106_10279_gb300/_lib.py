@@ -129,6 +129,8 @@ SIGNATURES = {
     "mf_vegas_save": (c_i32, [C.c_void_p, C.c_void_p, P(C.c_size_t)]),
     "mf_vegas_load": (c_i32, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "mf_generate_kernel_source": (c_i32, [P(mf_process_desc), c_i32, c_i32, C.c_char_p, P(C.c_size_t)]),
+    "mf_colour_sum": (c_i32, [C.c_void_p, c_i64, P(c_i32), c_i32, c_i32, c_i32, C.c_void_p, C.c_void_p]),
+    "mf_measure_peak": (c_i32, [c_i32, c_i32, P(C.c_double), P(C.c_double), C.c_void_p]),
     "mf_last_error": (C.c_char_p, []),
 }
 

@@ -148,6 +148,19 @@ def mf_process_last_kernel_ms(h) -> float:
     return ms.value
 
 
+PEAK_KINDS = {"fp32_ffma": 0, "fp64_dfma": 1, "tf32_mma": 2, "fp32_ffma2": 3}
+
+
+def mf_measure_peak(kind: str, reps: int = 10, stream=None):
+    """The device's measured arithmetic peak of one kind (fp32_ffma,
+    fp32_ffma2, fp64_dfma or tf32_mma): (TFLOP/s of the best of reps timed launches,
+    that launch's ms)."""
+    tf, ms = C.c_double(), C.c_double()
+    L.check(L.lib().mf_measure_peak(PEAK_KINDS[kind], reps, C.byref(tf), C.byref(ms), _stream_ptr(stream)),
+            "mf_measure_peak")
+    return tf.value, ms.value
+
+
 def _stream_ptr(stream):
     if stream is None:
         import torch

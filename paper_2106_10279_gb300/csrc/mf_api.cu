@@ -1206,20 +1206,41 @@ void vegas_params(const mf_process *p, const mf_vegas *v, int64_t n, int64_t ev0
     kp.subprocess = (uint64_t)subprocess;
 }
 
-// Chunk partial sums of the process scratch's n points into v->d_slots.
-mf_status accumulate(mf_process *p, mf_vegas *v, int64_t n, cudaStream_t s) {
-    const int64_t nchunks = (n + kChunk - 1) / kChunk;
-    const size_t acc_smem = sizeof(double) * 2 * kChunk;
-    static bool attr_set = false;
-    if (!attr_set) {
+// Dynamic shared memory of vegas_accumulate_kernel (one chunk's w and w^2),
+// and its attribute, set once per device.
+constexpr size_t kAccSmem = sizeof(double) * 2 * kChunk;
+constexpr int kAccMaxDevices = 64;
+std::mutex g_acc_mutex;
+bool g_acc_attr[kAccMaxDevices];
+
+mf_status accumulate_attribute() {
+    int dev = 0;
+    MF_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kAccMaxDevices) return fail(MF_EUNSUPPORTED, "device index beyond the attribute table");
+    std::lock_guard<std::mutex> lock(g_acc_mutex);
+    if (!g_acc_attr[dev]) {
         MF_CUDA(cudaFuncSetAttribute(vegas_accumulate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)acc_smem));
-        attr_set = true;
+                                     (int)kAccSmem));
+        g_acc_attr[dev] = true;
     }
-    vegas_accumulate_kernel<<<(unsigned)nchunks, kAccThreads, acc_smem, s>>>(p->d_w, p->d_bins, n, v->ndim, v->nbins,
-                                                                              v->d_slots, nchunks);
+    return MF_OK;
+}
+
+// Chunk partial sums of n points (w, bins) into slots [K][nchunks].
+mf_status accumulate_into(const double *w, const uint8_t *bins, int64_t n, const mf_vegas *v, double *slots,
+                          cudaStream_t s) {
+    const int64_t nchunks = (n + kChunk - 1) / kChunk;
+    mf_status st = accumulate_attribute();
+    if (st != MF_OK) return st;
+    vegas_accumulate_kernel<<<(unsigned)nchunks, kAccThreads, kAccSmem, s>>>(w, bins, n, v->ndim, v->nbins, slots,
+                                                                              nchunks);
     MF_CUDA(cudaGetLastError());
     return MF_OK;
+}
+
+// Chunk partial sums of the process scratch's n points into v->d_slots.
+mf_status accumulate(mf_process *p, mf_vegas *v, int64_t n, cudaStream_t s) {
+    return accumulate_into(p->d_w, p->d_bins, n, v, v->d_slots, s);
 }
 
 // Evaluate points [ev0, ev0 + n) of iteration v->iteration into the process
@@ -1836,8 +1857,8 @@ mf_status capture_batch(mf_batch *b, mf_vegas *const *grids, const int64_t *n_ev
         roots[2 * k + 1] = 0;
     }
     MF_CUDA(cudaMemcpy(b->d_root_ids, roots.data(), sizeof(int64_t) * roots.size(), cudaMemcpyHostToDevice));
-    const size_t acc_smem = sizeof(double) * 2 * kChunk;
-    MF_CUDA(cudaFuncSetAttribute(vegas_accumulate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc_smem));
+    mf_status ast = accumulate_attribute();
+    if (ast != MF_OK) return ast;
     mf_batch_params bp;
     std::memset(&bp, 0, sizeof bp);
     bp.counter = b->d_counter;
@@ -1863,7 +1884,7 @@ mf_status capture_batch(mf_batch *b, mf_vegas *const *grids, const int64_t *n_ev
         const int64_t n = n_events[k];
         const int64_t nchunks = (n + kChunk - 1) / kChunk;
         const int K = partial_size(v);
-        vegas_accumulate_kernel<<<(unsigned)nchunks, kAccThreads, acc_smem, c>>>(p->d_w, p->d_bins, n, v->ndim,
+        vegas_accumulate_kernel<<<(unsigned)nchunks, kAccThreads, kAccSmem, c>>>(p->d_w, p->d_bins, n, v->ndim,
                                                                                   v->nbins, v->d_slots, nchunks);
         vegas_tree_kernel<<<dim3((unsigned)K, 1), kTreeThreads, 0, c>>>(v->d_slots, nchunks, 0, nchunks, K,
                                                                          b->d_root_ids + 2 * k, v->d_tree_out);
@@ -2496,7 +2517,7 @@ __global__ void static_root_kernel(int64_t *ids, int level) {
 extern "C" mf_status mf_vegas_iterate_static(mf_vegas *v, mf_process *p, int64_t n_events, uint64_t seed,
                                              mf_precision prec, int32_t refine, mf_iter_result *out, void *stream) {
     if (!v || !p || !out) return fail(MF_EINVAL, "NULL argument");
-    if (prec != MF_FP64 && prec != MF_MIXED) return fail(MF_EINVAL, "bad precision");
+    if (!valid_prec(prec)) return fail(MF_EINVAL, "bad precision");
     if (v->ndim != p->ndim) return fail(MF_EINVAL, "grid and process dimensions differ");
     if (n_events < 2) return fail(MF_EINVAL, "need at least two events per iteration");
     if (n_events > MF_STATIC_MAX_EVENTS)
@@ -2535,18 +2556,22 @@ extern "C" mf_status mf_vegas_iterate_static(mf_vegas *v, mf_process *p, int64_t
     kp.subprocess = 0;
     st = launch(p, prec, kp, s);
     if (st != MF_OK) return st;
-    const size_t acc_smem = sizeof(double) * 2 * kChunk + kChunk;
-    MF_CUDA(cudaFuncSetAttribute(vegas_accumulate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc_smem));
-    vegas_accumulate_kernel<<<(unsigned)nchunks, kAccThreads, acc_smem, s>>>(w, bins, n, v->ndim, v->nbins, slots,
-                                                                              nchunks);
+    st = accumulate_into(w, bins, n, v, slots, s);
+    if (st != MF_OK) return st;
     static_root_kernel<<<1, 1, 0, s>>>(ids, tree_levels(nchunks));
     vegas_tree_kernel<<<dim3((unsigned)K, 1), kTreeThreads, 0, s>>>(slots, nchunks, 0, nchunks, K, ids, tot);
     MF_CUDA(cudaGetLastError());
     st = finish(v, tot, n, refine, s);
     if (st != MF_OK) return st;
     double r[8];
+    int flag = 0;
     MF_CUDA(cudaMemcpyAsync(r, v->d_result, sizeof(double) * 7, cudaMemcpyDeviceToHost, s));
+    MF_CUDA(cudaMemcpyAsync(&flag, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     MF_CUDA(cudaStreamSynchronize(s));
+    // a process-kernel error (expired wait, too little shared memory) leaves
+    // the weights unspecified: report it here, the iteration not advanced
+    st = flag_status(p, flag);
+    if (st != MF_OK) return st;
     fill_result(*out, v, n, r);
     v->iteration += 1;
     if (out->n_nan > 0) return fail(MF_ENAN, "some points had non-finite weights (counted as zero)");

@@ -11,6 +11,7 @@
 #include <cstdlib>
 #include <fstream>
 #include <cmath>
+#include <map>
 #include <mutex>
 #include <sstream>
 
@@ -94,13 +95,23 @@ mf_status jit_compile(const std::string &source, const std::string &name, std::v
     key += std::to_string(vmaj) + "." + std::to_string(vmin);
     char hex[32];
     std::snprintf(hex, sizeof hex, "%016llx", (unsigned long long)fnv1a(key));
+    // binaries compiled earlier in this process (keyed by the whole key text)
+    static std::map<std::string, std::vector<char>> memo;
+    auto hit = memo.find(key);
+    if (hit != memo.end()) {
+        cubin = hit->second;
+        return MF_OK;
+    }
     const char *dir = std::getenv("MF_JIT_CACHE");
     std::string path = dir && *dir ? std::string(dir) + "/mf_" + hex + ".cubin" : std::string();
     if (!path.empty()) {
         std::ifstream in(path, std::ios::binary);
         if (in) {
             cubin.assign(std::istreambuf_iterator<char>(in), std::istreambuf_iterator<char>());
-            if (!cubin.empty()) return MF_OK;
+            if (!cubin.empty()) {
+                memo[key] = cubin;
+                return MF_OK;
+            }
         }
     }
     nvrtcProgram prog;
@@ -123,6 +134,7 @@ mf_status jit_compile(const std::string &source, const std::string &name, std::v
     cubin.resize(n);
     g_nvrtc.cubin(prog, cubin.data());
     g_nvrtc.destroy(&prog);
+    memo[key] = cubin;
     if (!path.empty()) {
         std::string tmp = path + ".tmp" + std::to_string((long long)std::rand());
         std::ofstream out(tmp, std::ios::binary);

@@ -167,3 +167,12 @@ def test_batched_kernel_of_the_mixed_batch_compiles(built):
     from paper_2106_10279_gb300 import _lib as L
     with pytest.raises(L.MfError):
         api.mf_generate_batch_source([_desc("gg_ttx")] * 9, "mixed")
+
+
+def test_measure_peak_rejects_bad_arguments_without_a_device(built):
+    # argument checks come before any CUDA call
+    lib = built.lib()
+    tf = C.c_double()
+    assert lib.mf_measure_peak(7, 1, C.byref(tf), None, None) == built.MF_EINVAL
+    assert lib.mf_measure_peak(0, 0, C.byref(tf), None, None) == built.MF_EINVAL
+    assert lib.mf_measure_peak(0, 1, None, None, None) == built.MF_EINVAL
