@@ -121,6 +121,57 @@ typedef struct {
 #define MF_CHUNK 4096          /* points per accumulation chunk */
 #define MF_STATIC_MAX_EVENTS 262144  /* points per mf_vegas_iterate_static call */
 
+/* Code-generation and launch options of a process (the paper has no
+ * counterpart: these choose how the diagram program is emitted and launched,
+ * never what it computes).  A field set to MF_OPT_AUTO (-1) lets the library
+ * decide; mf_process_options_init sets every field to it, and a descriptor
+ * whose options pointer is NULL uses the defaults.
+ *   amplitude_units  1: FFV amplitudes that share the row and column spinors
+ *                    and whose colour coefficients agree up to +-1, +-i are
+ *                    evaluated as one amplitude of the summed vector currents;
+ *                    0: one amplitude at a time (default: 1 for programs
+ *                    above 2e4 FLOPs per helicity);
+ *   call_routines    0: every vertex routine inlined; 1: every routine called
+ *                    as a non-inlined function; 2: the currents called; 3: the
+ *                    amplitudes called (default: 1 for long programs, else 3);
+ *   order_search     iterations of the local search on the amplitude order
+ *                    (default: 4000 where amplitude units exist, else 0);
+ *   sync_every       block barrier every this many amplitudes in the program,
+ *                    0: none (default: 16 for long programs, else 0);
+ *   program_parts    functions the program is split into (default: by size);
+ *   min_blocks       minimum of resident blocks per SM the compiler must
+ *                    allow (__launch_bounds__), 0: none (default 0);
+ *   helicity_pairs   0: helicities one at a time; 1: pairs where they save
+ *                    FLOPs (default 1);
+ *   block            threads per block, 128 or 256 (default: 256 for long
+ *                    programs, 128 otherwise and for MF_MIXED_TC);
+ *   lanes            lanes per point, 1..32 and a power of two, at most the
+ *                    padded count of pairs or helicities (default: that count,
+ *                    at most 32);
+ *   blocks_per_sm    resident blocks per SM the grid is sized for, 1..8
+ *                    (default: the occupancy the compiled kernel reports);
+ *   ptxas_level      optimisation level 0..3 of the device assembler for the
+ *                    process kernels (default 3).
+ * Block, lanes and blocks_per_sm never change results; the other fields may
+ * change the last bits (the order of floating-point operations). */
+#define MF_OPT_AUTO (-1)
+typedef struct {
+    int32_t amplitude_units;
+    int32_t call_routines;
+    int32_t order_search;
+    int32_t sync_every;
+    int32_t program_parts;
+    int32_t min_blocks;
+    int32_t helicity_pairs;
+    int32_t block;
+    int32_t lanes;
+    int32_t blocks_per_sm;
+    int32_t ptxas_level;
+} mf_process_options;
+
+/* Set every field of *opt to MF_OPT_AUTO. */
+mf_status mf_process_options_init(mf_process_options *opt);
+
 typedef struct {
     /* external legs; legs 0 and 1 are the incoming partons along +z and -z */
     int32_t n_legs;
@@ -159,6 +210,7 @@ typedef struct {
     /* cuts on the legs flagged in leg_cut */
     double pt_min;                  /* pT > pt_min (GeV), 0 = none */
     double dr_min;                  /* Delta R > dr_min between flagged pairs, 0 = none */
+    const mf_process_options *options;  /* host, may be NULL (all defaults); copied */
 } mf_process_desc;
 
 typedef struct mf_process mf_process;   /* opaque, library-owned */
@@ -167,8 +219,13 @@ typedef struct mf_batch mf_batch;       /* opaque, library-owned */
 
 /* mf_create_process: validate and deep-copy *desc, drop vanishing helicities,
  * generate CUDA source specialised to the diagram program and compile it for
- * sm_103a at run time (NVRTC; cached on disk when MF_JIT_CACHE names a
- * directory).  The kept helicities are grouped into pairs that differ only at
+ * sm_103a at run time (NVRTC; compiled binaries are kept for the life of the
+ * process, and on disk when the environment variable MF_JIT_CACHE names a
+ * directory; MF_NVRTC_LIBRARY names the NVRTC shared library to load instead
+ * of the one found at build time; MF_JIT_VERBOSE=1 prints the assembler's
+ * resource report of each compilation to stderr).  The process's code-
+ * generation and launch options come from desc->options (see
+ * mf_process_options).  The kept helicities are grouped into pairs that differ only at
  * one leg where that saves arithmetic (mf_process_info: pair_leg, n_pairs);
  * the helicity sums of mf_integrand and mf_vegas_iterate then evaluate each
  * pair with one program.  Synchronous.  Errors: MF_EINVAL (malformed descriptor),
@@ -192,6 +249,9 @@ typedef struct {
     int32_t n_pairs;         /* helicity pairs evaluated per event (0: no pairs) */
     double flops_helicity_sum; /* FLOPs of one event's helicity sum as evaluated (pairs share
                                 * the wavefunctions that do not depend on pair_leg) */
+    int32_t helicity_sampling; /* sampling mode in effect (mf_process_set_helicity_sampling): 0 sum,
+                                * 1 single helicities, 2 helicity pairs (MF_MIXED_TC kernels sample
+                                * single helicities in mode 2) */
 } mf_process_info;
 
 mf_status mf_process_get_info(const mf_process *p, mf_process_info *info);
@@ -505,7 +565,11 @@ mf_status mf_vegas_load(mf_vegas *v, const void *buf, size_t len);
  * number: an unbiased estimate of the helicity sum with a larger variance.
  * With on = 2 the same draw picks one helicity pair (mf_process_get_helicity_
  * pairs) and the sum of its members' |M|^2 is multiplied by the number of
- * pairs (a process without pairs samples single helicities).  on = 0: the
+ * pairs.  A process without pairs (none differ at one leg, pairs cost more
+ * FLOPs than single helicities, or the option helicity_pairs = 0) samples
+ * single helicities instead, and so does the MF_MIXED_TC kernel, which
+ * evaluates single helicities; mf_process_info.helicity_sampling reports the
+ * mode in effect.  on = 0: the
  * full sum.  MF_EINVAL for other values.  mf_helicity_msq and mf_grad always
  * sum over helicities. */
 mf_status mf_process_set_helicity_sampling(mf_process *p, int32_t on, uint64_t seed);

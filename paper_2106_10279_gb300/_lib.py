@@ -31,6 +31,15 @@ class mf_colour_term(C.Structure):
     _fields_ = [("jamp", c_i32), ("pad_", c_i32), ("re", C.c_double), ("im", C.c_double)]
 
 
+class mf_process_options(C.Structure):
+    _fields_ = [("amplitude_units", c_i32), ("call_routines", c_i32), ("order_search", c_i32),
+                ("sync_every", c_i32), ("program_parts", c_i32), ("min_blocks", c_i32), ("helicity_pairs", c_i32),
+                ("block", c_i32), ("lanes", c_i32), ("blocks_per_sm", c_i32), ("ptxas_level", c_i32)]
+
+
+MF_OPT_AUTO = -1
+
+
 class mf_process_desc(C.Structure):
     _fields_ = [
         ("n_legs", c_i32), ("leg_kind", P(c_i32)), ("leg_incoming", P(c_i32)), ("leg_mass_id", P(c_i32)),
@@ -43,7 +52,7 @@ class mf_process_desc(C.Structure):
         ("sqrt_s", C.c_double), ("hadronic", c_i32), ("pdf", P(C.c_double) * 2),
         ("pdf_nx", c_i32), ("pdf_nq", c_i32), ("pdf_x_min", C.c_double), ("pdf_x_max", C.c_double),
         ("pdf_q2_min", C.c_double), ("pdf_q2_max", C.c_double), ("mu_f2", C.c_double),
-        ("pt_min", C.c_double), ("dr_min", C.c_double),
+        ("pt_min", C.c_double), ("dr_min", C.c_double), ("options", P(mf_process_options)),
     ]
 
 
@@ -51,7 +60,8 @@ class mf_process_info(C.Structure):
     _fields_ = [("ndim", c_i32), ("n_legs", c_i32), ("n_hel", c_i32), ("n_hel_all", c_i32),
                 ("n_jamp", c_i32), ("n_ops", c_i32), ("n_den", c_i32),
                 ("flops_per_hel", C.c_double), ("flops_kinematics", C.c_double),
-                ("pair_leg", c_i32), ("n_pairs", c_i32), ("flops_helicity_sum", C.c_double)]
+                ("pair_leg", c_i32), ("n_pairs", c_i32), ("flops_helicity_sum", C.c_double),
+                ("helicity_sampling", c_i32)]
 
 
 class mf_observable(C.Structure):
@@ -130,6 +140,7 @@ SIGNATURES = {
     "mf_vegas_load": (c_i32, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "mf_generate_kernel_source": (c_i32, [P(mf_process_desc), c_i32, c_i32, C.c_char_p, P(C.c_size_t)]),
     "mf_colour_sum": (c_i32, [C.c_void_p, c_i64, P(c_i32), c_i32, c_i32, c_i32, C.c_void_p, C.c_void_p]),
+    "mf_process_options_init": (c_i32, [P(mf_process_options)]),
     "mf_measure_peak": (c_i32, [c_i32, c_i32, P(C.c_double), P(C.c_double), C.c_void_p]),
     "mf_last_error": (C.c_char_p, []),
 }

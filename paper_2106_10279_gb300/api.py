@@ -26,7 +26,7 @@ class Descriptor:
 
     def __init__(self, prog: ProcessProgram, *, sqrt_s: float, m_top: float, alpha_s: float,
                  pdf_tables=None, pdf_axes=None, mu_f2: float = 0.0, pt_min: float = 0.0,
-                 dr_min: float = 0.0, helicities=None):
+                 dr_min: float = 0.0, helicities=None, options=None):
         n = len(prog.legs)
         self.prog = prog
         masses = [m_top]
@@ -104,6 +104,13 @@ class Descriptor:
             d.mu_f2 = mu_f2
         d.pt_min = pt_min
         d.dr_min = dr_min
+        if options:
+            o = L.mf_process_options()
+            L.check(L.lib().mf_process_options_init(C.byref(o)), "mf_process_options_init")
+            for k, v in options.items():
+                setattr(o, k, int(v))
+            self._keep.append(o)
+            d.options = C.pointer(o)
         self.desc = d
 
     def _k(self, arr):
@@ -111,8 +118,9 @@ class Descriptor:
         return C.cast(arr, C.POINTER(arr._type_))
 
 
-def descriptor_for_workload(wl, m_top=None, alpha_s=None, q2_slope: float = 0.0, helicities=None):
-    """Descriptor of one of the synthetic workloads (``workloads`` module)."""
+def descriptor_for_workload(wl, m_top=None, alpha_s=None, q2_slope: float = 0.0, helicities=None, options=None):
+    """Descriptor of one of the synthetic workloads (``workloads`` module);
+    options: a dict of mf_process_options fields (the rest MF_OPT_AUTO)."""
     import workloads as W
     mt = wl.m_top if m_top is None else m_top
     a_s = wl.alpha_s if alpha_s is None else alpha_s
@@ -122,7 +130,8 @@ def descriptor_for_workload(wl, m_top=None, alpha_s=None, q2_slope: float = 0.0,
         tables = [W.pdf_table(b, q2_slope) for b in wl.beams]
         axes = (W.PDF_X_MIN, W.PDF_X_MAX, W.PDF_Q2_MIN, W.PDF_Q2_MAX)
     return Descriptor(prog, sqrt_s=wl.sqrt_s, m_top=mt, alpha_s=a_s, pdf_tables=tables, pdf_axes=axes,
-                      mu_f2=wl.mu_f2, pt_min=wl.pt_min_gluon, dr_min=wl.dr_min_gluon, helicities=helicities)
+                      mu_f2=wl.mu_f2, pt_min=wl.pt_min_gluon, dr_min=wl.dr_min_gluon, helicities=helicities,
+                      options=options)
 
 
 # ---------------------------------------------------------------- C entry points

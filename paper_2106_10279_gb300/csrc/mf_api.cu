@@ -31,6 +31,13 @@ using mfi::fail;
 
 extern "C" const char *mf_last_error(void) { return mfi::g_err.c_str(); }
 
+extern "C" mf_status mf_process_options_init(mf_process_options *opt) {
+    if (!opt) return fail(MF_EINVAL, "NULL options");
+    int32_t *f = &opt->amplitude_units;
+    for (size_t i = 0; i < sizeof(mf_process_options) / sizeof(int32_t); ++i) f[i] = MF_OPT_AUTO;
+    return MF_OK;
+}
+
 #define MF_CUDA(call)                                                                      \
     do {                                                                                   \
         cudaError_t e_ = (call);                                                           \
@@ -421,7 +428,8 @@ mf_status compile_shape(mf_process *p, int prec, int block, int ht, mfi::Compile
     std::string src = mfi::generate_source(*p, prec, k.block, k.ht, info, "proc", true, min_blocks);
     std::vector<char> cubin;
     mf_status st = mfi::jit_compile(src, prec == MF_FP64 ? "mf_proc_f64.cu" : prec == MF_MIXED ? "mf_proc_mixed.cu"
-                                                                                  : "mf_proc_mixed_tc.cu", cubin);
+                                                                                  : "mf_proc_mixed_tc.cu", cubin,
+                                    p->opt.ptxas_level);
     if (st != MF_OK) return st;
     // the shared-memory size depends on the program's denominator count
     p->source[prec] = src;
@@ -480,15 +488,9 @@ mf_status compile_precision(mf_process *p, int prec) {
     int block = (mfi::large_program(*p) && prec != MF_MIXED_TC) ? 256 : 128;
     const int nhp = lane_units(p);
     int ht = nhp < 32 ? nhp : 32;
-    // launch-shape overrides: block size and lanes per event
-    if (const char *e = std::getenv("MF_BLOCK")) {
-        int b = std::atoi(e);
-        if ((b == 64 || b == 128 || b == 256 || b == 512) && prec != MF_MIXED_TC) block = b;
-    }
-    if (const char *e = std::getenv("MF_HT")) {
-        int h = std::atoi(e);
-        if (h >= 1 && h <= 32 && (h & (h - 1)) == 0 && h <= nhp) ht = h;
-    }
+    // launch-shape options: block size and lanes per event
+    if (p->opt.block > 0 && prec != MF_MIXED_TC) block = p->opt.block;
+    if (p->opt.lanes > 0 && p->opt.lanes <= nhp) ht = p->opt.lanes;
     return compile_shape(p, prec, block, ht, k);
 }
 
@@ -500,7 +502,7 @@ mf_status compile_grad(mf_process *p) {
     mfi::GenInfo info;
     p->source[2] = mfi::generate_grad_source(*p, k.block, info);
     std::vector<char> cubin;
-    mf_status st = mfi::jit_compile(p->source[2], "mf_proc_grad.cu", cubin);
+    mf_status st = mfi::jit_compile(p->source[2], "mf_proc_grad.cu", cubin, p->opt.ptxas_level);
     if (st != MF_OK) return st;
     return mfi::load_kernel(cubin, k, "mf_grad_kernel");
 }
@@ -542,8 +544,7 @@ void build_pairs(mf_process *p) {
     // (row indices are stored in one byte with 0xFF for an absent member, so
     // a table of 256 kept rows is evaluated one helicity at a time)
     if (L < 0 || nh == 0 || nh > 255) return;
-    if (const char *e = std::getenv("MF_HEL_PAIRS"))       // measurement switch: 0 = helicities one by one
-        if (std::atoi(e) == 0) return;
+    if (p->opt.helicity_pairs == 0) return;                // the option: helicities one by one
     std::vector<uint8_t> t;
     std::vector<std::vector<int8_t>> keys;
     for (int h = 0; h < nh; ++h) {
@@ -594,11 +595,8 @@ mf_status launch(mf_process *p, int prec, mf_kparams &kp, cudaStream_t s) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     int per_sm = k.max_blocks_per_sm;
-    // launch-shape override (for measurements): resident blocks per SM assumed
-    if (const char *e = std::getenv("MF_BLOCKS_PER_SM")) {
-        int b = std::atoi(e);
-        if (b >= 1 && b <= 8) per_sm = b;
-    }
+    // launch-shape option: resident blocks per SM the grid is sized for
+    if (p->opt.blocks_per_sm >= 1) per_sm = p->opt.blocks_per_sm;
     int64_t grid = (int64_t)nsm * per_sm;
     if (grid > ntiles) grid = ntiles;
     if (grid < 1) grid = 1;
@@ -606,8 +604,22 @@ mf_status launch(mf_process *p, int prec, mf_kparams &kp, cudaStream_t s) {
     return mfi::launch_kernel(k, (unsigned)grid, args, s);
 }
 
+// Ranges of the process options (MF_OPT_AUTO allowed everywhere).
+mf_status validate_options(const mf_process_options *o) {
+    if (!o) return MF_OK;
+    auto in = [](int v, int lo, int hi) { return v == MF_OPT_AUTO || (v >= lo && v <= hi); };
+    const bool pow2 = o->lanes == MF_OPT_AUTO || (o->lanes >= 1 && o->lanes <= 32 && (o->lanes & (o->lanes - 1)) == 0);
+    if (!in(o->amplitude_units, 0, 1) || !in(o->call_routines, 0, 3) || !in(o->order_search, 0, 1 << 24) ||
+        !in(o->sync_every, 0, 1 << 20) || !in(o->program_parts, 1, 4096) || !in(o->min_blocks, 0, 8) ||
+        !in(o->helicity_pairs, 0, 1) || !(o->block == MF_OPT_AUTO || o->block == 128 || o->block == 256) || !pow2 ||
+        !in(o->blocks_per_sm, 1, 8) || !in(o->ptxas_level, 0, 3))
+        return fail(MF_EINVAL, "process option out of range");
+    return MF_OK;
+}
+
 mf_status validate(const mf_process_desc *d) {
     if (!d) return fail(MF_EINVAL, "NULL descriptor");
+    if (validate_options(d->options) != MF_OK) return MF_EINVAL;
     if (d->n_legs < 3) return fail(MF_EINVAL, "need at least 3 legs");
     if (d->n_legs > MF_MAX_LEGS) return fail(MF_EUNSUPPORTED, "too many legs");
     if (!d->leg_kind || !d->leg_incoming || !d->leg_mass_id || !d->leg_cut)
@@ -738,6 +750,7 @@ extern "C" mf_status mf_create_process(const mf_process_desc *d, mf_process **ou
     p->n_jamp = d->n_jamp;
     p->colour_num.assign(d->colour_num, d->colour_num + d->n_jamp * d->n_jamp);
     p->colour_den = d->colour_den;
+    if (d->options) p->opt = *d->options;
     if (d->n_hel > 0) {
         p->hel_all.assign(d->helicities, d->helicities + (size_t)d->n_hel * n);
     } else {
@@ -878,16 +891,18 @@ int shell_from_desc(const mf_process_desc *d, mf_process &p) {
     p.n_jamp = d->n_jamp;
     p.colour_num.assign(d->colour_num, d->colour_num + d->n_jamp * d->n_jamp);
     p.colour_den = d->colour_den;
+    if (d->options) p.opt = *d->options;
     int nh = d->n_hel > 0 ? d->n_hel : (1 << n);
     int nhp = 1;
     while (nhp < nh) nhp <<= 1;
     return nhp < 32 ? nhp : 32;
 }
 
-mf_status emit_source(const std::string &src, const char *name, int32_t compile, char *buf, size_t *len) {
+mf_status emit_source(const std::string &src, const char *name, int32_t compile, char *buf, size_t *len,
+                      int ptxas_level = -1) {
     if (compile) {
         std::vector<char> cubin;
-        mf_status st = mfi::jit_compile(src, name, cubin);
+        mf_status st = mfi::jit_compile(src, name, cubin, ptxas_level);
         if (st != MF_OK) return st;
     }
     size_t need = src.size() + 1;
@@ -910,7 +925,7 @@ extern "C" mf_status mf_generate_kernel_source(const mf_process_desc *d, mf_prec
                                      : mfi::generate_source(p, prec, 128, ht, info);
     return emit_source(src, (int)prec == 2 ? "mf_proc_grad.cu" : prec == MF_FP64 ? "mf_proc_f64.cu"
                                               : prec == MF_MIXED ? "mf_proc_mixed.cu" : "mf_proc_mixed_tc.cu",
-                       compile, buf, len);
+                       compile, buf, len, p.opt.ptxas_level);
 }
 
 extern "C" mf_status mf_generate_batch_source(const mf_process_desc *const *descs, int32_t nproc, mf_precision prec,
@@ -959,6 +974,7 @@ extern "C" mf_status mf_process_get_info(const mf_process *p, mf_process_info *i
     info->pair_leg = p->pairs.empty() ? -1 : p->gen.pair_leg;
     info->n_pairs = (int32_t)(p->pairs.size() / 2);
     info->flops_helicity_sum = helicity_sum_flops(p);
+    info->helicity_sampling = p->hel_sample;
     return MF_OK;
 }
 

@@ -80,10 +80,10 @@ struct AmpUnit {
 
 std::vector<AmpUnit> amplitude_units(const mf_process &p) {
     std::vector<AmpUnit> units;
-    // used for long programs (which call every vertex routine); MF_AMP_UNITS
-    // overrides (0: every amplitude alone, 1: units)
+    // used for long programs (which call every vertex routine) unless the
+    // process options say otherwise (0: every amplitude alone, 1: units)
     bool group = large_program(p);
-    if (const char *e = std::getenv("MF_AMP_UNITS")) group = std::atoi(e) != 0;
+    if (p.opt.amplitude_units >= 0) group = p.opt.amplitude_units != 0;
     std::map<std::vector<double>, int> unit_of;
     auto unit_phase = [](double re, double im) {
         if (im == 0.0 && re == 1.0) return 0;
@@ -342,10 +342,10 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
     // instruction caches far better (the inlined form is fetch-bound), at the
     // price of argument passing: long programs call every routine (mode 1),
     // shorter ones inline the currents and call the amplitude routines
-    // (mode 3; gg -> tt~g 1.12x faster than mode 1).  MF_CALL_ROUTINES
-    // overrides: 0 inlines everything, 2 calls the currents only.
+    // (mode 3; gg -> tt~g 1.12x faster than mode 1).  The process option
+    // call_routines overrides: 0 inlines everything, 2 calls the currents only.
     int call_mode = large_program(p) ? 1 : 3;
-    if (const char *e = std::getenv("MF_CALL_ROUTINES")) call_mode = std::atoi(e);
+    if (p.opt.call_routines >= 0) call_mode = p.opt.call_routines;
     const bool calls = call_mode != 0;
     auto rt = [&](const char *name) {
         const bool amp = std::string(name).find("_AMP") != std::string::npos;
@@ -433,7 +433,7 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
         bool grouped = false;
         for (const AmpUnit &un : units) grouped |= un.ops.size() > 1;
         int iters = grouped ? 4000 : 0;
-        if (const char *e = std::getenv("MF_ORDER_SEARCH")) iters = std::atoi(e);
+        if (p.opt.order_search >= 0) iters = p.opt.order_search;
         improve_order(p, units, order, iters);
         info.peak_live = live_profile(p, units, order).first;
     }
@@ -453,7 +453,7 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
     // warps on the same stretch of code, so that the instructions one warp
     // fetched serve the others (measured on gg -> tt~gg: 1.09x)
     int sync_every = large_program(p) ? 16 : 0;
-    if (const char *e = std::getenv("MF_SYNC_EVERY")) sync_every = std::atoi(e);
+    if (p.opt.sync_every >= 0) sync_every = p.opt.sync_every;
     auto M = [&](int id) { return id >= 0 ? "mass[" + std::to_string(id) + "]" : std::string("R(0)"); };
     auto emit_program = [&](const bool pair) {
     auto dep = [&](int k) { return pair && (p.ops[k].kind == MF_OP_AMP || (mask[k] >> L & 1)); };
@@ -462,7 +462,7 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
     for (size_t k = 0; k < p.ops.size(); ++k) weight += routine_flops(p.ops[k].routine) * (dep((int)k) ? 2 : 1);
     if (precision == MF_FP64) weight *= 2.0;
     int parts = (int)std::ceil(weight / (calls ? 64000.0 : 32000.0));
-    if (const char *e = std::getenv("MF_PROGRAM_PARTS")) parts = std::atoi(e);
+    if (p.opt.program_parts >= 1) parts = p.opt.program_parts;
     if (parts < 1) parts = 1;
     if (parts > (int)order.size()) parts = (int)order.size();
     if (!pair) info.parts = parts;
@@ -720,10 +720,7 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
     if (kernel) {
         o << "#include \"mf_kernel.cuh\"\n";
         // optional minimum of resident blocks per SM (trades registers for occupancy)
-        if (min_blocks < 0) {
-            min_blocks = 0;
-            if (const char *e = std::getenv("MF_MIN_BLOCKS")) min_blocks = std::atoi(e);
-        }
+        if (min_blocks < 0) min_blocks = p.opt.min_blocks > 0 ? p.opt.min_blocks : 0;
         o << "extern \"C\" __global__ void __launch_bounds__(" << block;
         if (min_blocks >= 1 && min_blocks <= 8) o << ", " << min_blocks;
         o << ") mf_kernel(const mf::KParams kp) {\n";

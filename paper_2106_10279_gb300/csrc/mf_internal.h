@@ -54,6 +54,9 @@ bool large_program(const mf_process &p);
 
 struct mf_process {
     int device = 0;
+    // code-generation and launch options (MF_OPT_AUTO: the library decides)
+    mf_process_options opt = {MF_OPT_AUTO, MF_OPT_AUTO, MF_OPT_AUTO, MF_OPT_AUTO, MF_OPT_AUTO, MF_OPT_AUTO,
+                              MF_OPT_AUTO, MF_OPT_AUTO, MF_OPT_AUTO, MF_OPT_AUTO, MF_OPT_AUTO};
     // deep copy of the descriptor
     int n_legs = 0, n_out = 0, ndim = 0;
     std::vector<int32_t> leg_kind, leg_incoming, leg_mass_id, leg_cut;
@@ -153,7 +156,8 @@ std::string generate_batch_source(const std::vector<const mf_process *> &ps, int
                                   const std::vector<int> &hts, std::vector<GenInfo> &infos);
 std::string generate_grad_source(const mf_process &p, int block, GenInfo &info);
 // run-time compilation (mf_jit.cpp)
-mf_status jit_compile(const std::string &source, const std::string &name, std::vector<char> &cubin);
+mf_status jit_compile(const std::string &source, const std::string &name, std::vector<char> &cubin,
+                      int ptxas_level = -1);
 mf_status load_kernel(const std::vector<char> &cubin, Compiled &out, const char *name = "mf_kernel");
 void unload_kernel(Compiled &k);
 mf_status launch_kernel(const Compiled &k, unsigned grid, void **args, cudaStream_t s);

@@ -79,12 +79,16 @@ bool open_nvrtc(std::string &err) {
 
 namespace mfi {
 
-mf_status jit_compile(const std::string &source, const std::string &name, std::vector<char> &cubin) {
+mf_status jit_compile(const std::string &source, const std::string &name, std::vector<char> &cubin,
+                      int ptxas_level) {
     std::lock_guard<std::mutex> lock(g_jit_mutex);
     std::string oerr;
     if (!open_nvrtc(oerr)) return fail(MF_EJIT, "cannot load NVRTC: " + oerr);
     std::vector<const char *> opts = {"--gpu-architecture=sm_103a", "--std=c++17", "-lineinfo",
                                       "--device-as-default-execution-space"};
+    static const char *kLevels[4] = {"--ptxas-options=-O0", "--ptxas-options=-O1", "--ptxas-options=-O2",
+                                     "--ptxas-options=-O3"};
+    if (ptxas_level >= 0 && ptxas_level <= 2) opts.push_back(kLevels[ptxas_level]);
     const char *verbose = std::getenv("MF_JIT_VERBOSE");
     if (verbose && *verbose == '1') opts.push_back("--ptxas-options=-v");
     int vmaj = 0, vmin = 0;

@@ -7,7 +7,6 @@ FP64 and mixed precision, for integrands and a Vegas iteration.  The oracle
 parity tests of the integrand run through the pairs as well (they are the
 default wherever they save work).
 """
-import os
 
 import numpy as np
 import pytest
@@ -29,11 +28,7 @@ def env():
 
 
 def _unpaired(api, wl):
-    os.environ["MF_HEL_PAIRS"] = "0"
-    try:
-        return api.Process.from_workload(wl)
-    finally:
-        os.environ.pop("MF_HEL_PAIRS", None)
+    return api.Process.from_workload(wl, options={"helicity_pairs": 0})
 
 
 @pytest.mark.parametrize("name", ["gg_ttx", "uux_ttx", "gg_ttxg", "uux_ttxg", "gg_ttxgg"])

@@ -39,13 +39,6 @@ def test_tuned_shape_gives_the_same_bits(env, name, prec):
         nz = before != 0
         assert np.max(np.abs(after[nz] / before[nz] - 1)) < (1e-12 if prec == "fp64" else 1e-5)
     # an untuned twin with the same block and lanes gives the same bits
-    import os
-    os.environ["MF_BLOCK"], os.environ["MF_HT"] = str(block), str(ht)
-    os.environ["MF_MIN_BLOCKS"] = str(info["min_blocks"])
-    try:
-        twin = api.Process.from_workload(wl)
-        twin_f = twin.integrand(x, prec).cpu().numpy()
-    finally:
-        for k in ("MF_BLOCK", "MF_HT", "MF_MIN_BLOCKS"):
-            os.environ.pop(k, None)
+    twin = api.Process.from_workload(wl, options={"block": block, "lanes": ht, "min_blocks": info["min_blocks"]})
+    twin_f = twin.integrand(x, prec).cpu().numpy()
     assert np.array_equal(after, twin_f)

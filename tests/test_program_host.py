@@ -41,13 +41,9 @@ def _build(tmp, name, units, gauge=False):
     gxx = shutil.which("g++")
     if gxx is None:
         pytest.skip("no host C++ compiler")
-    desc = api.descriptor_for_workload(W.WORKLOADS[name])
-    if units is not None:
-        os.environ["MF_AMP_UNITS"] = units
-    try:
-        src = api.mf_generate_kernel_source(desc, "fp64")
-    finally:
-        os.environ.pop("MF_AMP_UNITS", None)
+    desc = api.descriptor_for_workload(W.WORKLOADS[name],
+                                       options=None if units is None else {"amplitude_units": int(units)})
+    src = api.mf_generate_kernel_source(desc, "fp64")
     src = src[:src.index('#include "mf_kernel.cuh"')]
     leg = int(re.search(r"constexpr int PAIR_LEG = (-?\d+);", src).group(1))
     (tmp / "mf_program_gen.h").write_text(src)
