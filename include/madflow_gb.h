@@ -151,7 +151,12 @@ typedef struct {
  *   blocks_per_sm    resident blocks per SM the grid is sized for, 1..8
  *                    (default: the occupancy the compiled kernel reports);
  *   ptxas_level      optimisation level 0..3 of the device assembler for the
- *                    process kernels (default 3).
+ *                    process kernels (default 3);
+ *   wait_polls       polls of the bounded wait on each round of tensor-core
+ *                    MMAs in MF_MIXED_TC kernels before the round is given up
+ *                    and MF_ETIMEOUT flagged, 0 .. 2^30 (default 2^24; the
+ *                    wait before tensor memory is released always uses the
+ *                    default).
  * Block, lanes and blocks_per_sm never change results; the other fields may
  * change the last bits (the order of floating-point operations). */
 #define MF_OPT_AUTO (-1)
@@ -167,6 +172,7 @@ typedef struct {
     int32_t lanes;
     int32_t blocks_per_sm;
     int32_t ptxas_level;
+    int32_t wait_polls;
 } mf_process_options;
 
 /* Set every field of *opt to MF_OPT_AUTO. */
@@ -261,8 +267,10 @@ mf_status mf_process_get_info(const mf_process *p, mf_process_info *info);
  * [n]); sigma = integral of f over the hypercube.  Hadronic processes use x_0,
  * x_1 for the momentum fractions (tau = tau_min^x0, x1 = tau^x1, x2 = tau/x1)
  * and the rest for the phase space; points failing the cuts or below threshold
- * give f = 0.  No Vegas Jacobian is applied.  Asynchronous.  n = 0 is a no-op.
- * MF_EINVAL for NULL pointers with n > 0 or n < 0. */
+ * give f = 0.  No Vegas Jacobian is applied.  A point with a non-finite
+ * coordinate gives f = NaN; any non-finite f raises the process's
+ * non-finite flag, which mf_process_check reports as MF_ENAN.  Asynchronous.
+ * n = 0 is a no-op.  MF_EINVAL for NULL pointers with n > 0 or n < 0. */
 mf_status mf_integrand(mf_process *p, const double *x, int64_t n, double *f,
                        mf_precision prec, void *stream);
 
@@ -601,9 +609,9 @@ mf_status mf_process_kernel_info(const mf_process *p, mf_precision prec, int32_t
 
 /* mf_process_check: whether a kernel of this process flagged an error: a
  * bounded wait expired (the tensor-core colour sum waits on the completion
- * of its MMAs; that launch's results are unspecified): MF_ETIMEOUT; or the
+ * of its MMAs; that launch's results are unspecified): MF_ETIMEOUT; the
  * launch gave less dynamic shared memory than the kernel needs (nothing
- * written): MF_ECUDA.  Reads and clears the flag (synchronises the device).
+ * written): MF_ECUDA; mf_integrand wrote a non-finite value: MF_ENAN.  Reads and clears the flag (synchronises the device).
  * The synchronous entry points (mf_create_process, mf_vegas_iterate, the
  * shard and batch iterations) check it by themselves. */
 mf_status mf_process_check(mf_process *p);
@@ -665,6 +673,15 @@ mf_status mf_colour_sum(const float *J, int64_t n, const int32_t *cnum, int32_t 
  * few bytes of scratch.  MF_ETIMEOUT if the MMA completion wait (bounded by
  * 2 s per block) expired.  Synchronous. */
 mf_status mf_measure_peak(int32_t kind, int32_t reps, double *tflops, double *ms, void *stream);
+
+/* mf_debug_fail_allocation: a test hook for the library's allocation-failure
+ * paths (the paper has no counterpart).  With after >= 0, the library's next
+ * after device or pinned-host allocations succeed and the one after them
+ * fails as if the device were out of memory (the entry point that made it
+ * returns MF_ENOMEM and releases what it had allocated); later allocations
+ * succeed again.  after = -1 disarms the hook.  Process-wide, thread-safe;
+ * no device work. */
+mf_status mf_debug_fail_allocation(int64_t after);
 
 /* Thread-local description of the last error (empty string if none). */
 const char *mf_last_error(void);

@@ -34,7 +34,8 @@ class mf_colour_term(C.Structure):
 class mf_process_options(C.Structure):
     _fields_ = [("amplitude_units", c_i32), ("call_routines", c_i32), ("order_search", c_i32),
                 ("sync_every", c_i32), ("program_parts", c_i32), ("min_blocks", c_i32), ("helicity_pairs", c_i32),
-                ("block", c_i32), ("lanes", c_i32), ("blocks_per_sm", c_i32), ("ptxas_level", c_i32)]
+                ("block", c_i32), ("lanes", c_i32), ("blocks_per_sm", c_i32), ("ptxas_level", c_i32),
+                ("wait_polls", c_i32)]
 
 
 MF_OPT_AUTO = -1
@@ -140,6 +141,7 @@ SIGNATURES = {
     "mf_vegas_load": (c_i32, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "mf_generate_kernel_source": (c_i32, [P(mf_process_desc), c_i32, c_i32, C.c_char_p, P(C.c_size_t)]),
     "mf_colour_sum": (c_i32, [C.c_void_p, c_i64, P(c_i32), c_i32, c_i32, c_i32, C.c_void_p, C.c_void_p]),
+    "mf_debug_fail_allocation": (c_i32, [c_i64]),
     "mf_process_options_init": (c_i32, [P(mf_process_options)]),
     "mf_measure_peak": (c_i32, [c_i32, c_i32, P(C.c_double), P(C.c_double), C.c_void_p]),
     "mf_last_error": (C.c_char_p, []),

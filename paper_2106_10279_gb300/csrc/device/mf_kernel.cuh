@@ -209,7 +209,7 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
     const uint64_t iteration = kp.iter_dev ? (uint64_t)*kp.iter_dev : kp.iteration;
     {
         const int64_t e = tile * BLOCK + tid;
-        bool ok = false;
+        bool ok = false, finite_in = true;
         double pref = 0.0, jv = 1.0;
         uint8_t bins[NDIM];
         if (e < kp.n) {
@@ -217,7 +217,10 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
             double y[NDIM];
             if (kp.mode != 1 && kp.mode != 3 && kp.mode != 4) {
 #pragma unroll
-                for (int j = 0; j < NDIM; ++j) y[j] = kp.x[(int64_t)j * kp.n + e];
+                for (int j = 0; j < NDIM; ++j) {
+                    y[j] = kp.x[(int64_t)j * kp.n + e];
+                    finite_in &= isfinite(y[j]);
+                }
             } else {
                 const uint64_t gi = kp.mode == 3 ? (uint64_t)kp.idx[e] : (uint64_t)(e + kp.ev0);
 #pragma unroll
@@ -238,7 +241,7 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
                 }
             }
             EventKin<double> ev;
-            ok = phase_a<double>(kp, y, kp.masses, kp.ln_tau_min, ev);
+            ok = phase_a<double>(kp, y, kp.masses, kp.ln_tau_min, ev) && finite_in;
             if (kp.mode == 3) {
                 // event record: x1, x2 and the momenta boosted along z from the
                 // partonic centre-of-mass frame to the collider frame
@@ -389,6 +392,11 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
         if (e < kp.n) {
             double fval = ok ? s_pref[tid] * s_msq[tid] : 0.0;
             if (kp.mode == 0) {
+                // a point with a non-finite coordinate gives NaN; any
+                // non-finite value raises the non-finite flag (3) unless a
+                // more serious error is flagged already
+                if (!finite_in) fval = __longlong_as_double(0x7FF8000000000000ll);
+                if (!isfinite(fval) && kp.err) atomicCAS(kp.err, 0, 3);
                 kp.f[e] = fval;
             } else if (kp.mode == 1) {
                 kp.w_out[e] = fval * jv;
@@ -440,7 +448,7 @@ MF_DEV void kernel_body_tc(const KParams &kp) {
     constexpr size_t tile_bytes = (tile_smem_bytes<float, BLOCK>() + 1023) / 1024 * 1024;
     if (!smem_ok(kp, tile_bytes + tc::Plan<NJAMP>::SMEM)) return;
     tc::State tcs;
-    tc::setup<NJAMP>(tcs, smem_raw + tile_bytes, kp.err);
+    tc::setup<NJAMP>(tcs, smem_raw + tile_bytes, kp.err, kp.wait_polls);
     tc::load_colour<NJAMP>(tcs, COLOUR_NUM);
     load_block_constants<float, BLOCK>(kp, s_grid, cpl, mass_r);
     __syncthreads();

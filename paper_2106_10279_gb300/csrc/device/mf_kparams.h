@@ -43,6 +43,7 @@ struct mf_kparams {
     int32_t npairs;            // modes 0, 1: helicity pairs in pairs[] (0: one helicity at a time)
     int32_t npairs_pow2;       // a power of two >= npairs
     int32_t pad3;
+    int64_t wait_polls;        // polls of a bounded wait per tensor-core colour-sum round
     const long long *iter_dev; // if set, the iteration index is read here (graph replays)
     uint16_t *obs_out;         // mode 4: bins [n_obs][n], 0xFFFF: not binned
     int32_t n_obs;             // mode 4: observables

@@ -23,7 +23,10 @@
 //
 // Every wait on the MMA's completion is bounded; on expiry the block records
 // an error (the results of that round are then unspecified) and goes on, so
-// that no block can hang.
+// that no block can hang.  Before the tensor memory is released, one more
+// commit on a separate barrier tracks every MMA the block issued, and the
+// block waits for it with the full limit: tensor memory is never released
+// under an MMA still in flight, whatever the per-round limit was.
 #pragma once
 #include "mf_common.cuh"
 
@@ -31,7 +34,7 @@ namespace mf {
 namespace tc {
 
 constexpr int ROWS = 128;                    // rows per MMA (one per thread of a 128-thread block)
-constexpr long long WAIT_LIMIT = 1ll << 24;  // polls of the completion barrier before giving up
+constexpr long long WAIT_LIMIT = 1ll << 24;  // polls of a completion barrier before giving up (default)
 
 template <int NJ>
 struct Plan {
@@ -41,8 +44,9 @@ struct Plan {
     static constexpr int COLS = NP <= 32 ? 32 : NP <= 64 ? 64 : NP <= 128 ? 128 : 256;   // tensor-memory columns
     static constexpr int A_BYTES = ROWS * KP * 4;
     static constexpr int B_BYTES = NP * KP * 4;
-    // shared-memory bytes: A_hi, A_lo, B (1 KB aligned), then the barrier and the tensor-memory address
-    static constexpr int SMEM = 2 * A_BYTES + B_BYTES + 16;
+    // shared-memory bytes: A_hi, A_lo, B (1 KB aligned), then the round and
+    // drain barriers and the tensor-memory address
+    static constexpr int SMEM = 2 * A_BYTES + B_BYTES + 24;
 };
 
 MF_DEV uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -72,9 +76,11 @@ MF_DEV float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFF
 // tensor-memory base address and the barrier phase.
 struct State {
     unsigned char *a_hi, *a_lo, *b;
-    uint64_t *mbar;
+    uint64_t *mbar;           // completion of each round's MMAs
+    uint64_t *drain;          // completion of every MMA issued (teardown)
     uint32_t *tmem_slot;
     uint32_t phase;
+    long long wait_limit;     // polls per round
     int *err;                 // global error flag (may be NULL)
     bool failed;
 };
@@ -82,14 +88,16 @@ struct State {
 // Carve the buffers out of `smem` (1 KB aligned, Plan<NJ>::SMEM bytes),
 // allocate tensor memory (warp 0) and initialise the barrier.  All threads.
 template <int NJ>
-MF_DEV void setup(State &s, unsigned char *smem, int *err) {
+MF_DEV void setup(State &s, unsigned char *smem, int *err, long long wait_limit = WAIT_LIMIT) {
     using P = Plan<NJ>;
     s.a_hi = smem;
     s.a_lo = smem + P::A_BYTES;
     s.b = smem + 2 * P::A_BYTES;
     s.mbar = reinterpret_cast<uint64_t *>(smem + 2 * P::A_BYTES + P::B_BYTES);
-    s.tmem_slot = reinterpret_cast<uint32_t *>(smem + 2 * P::A_BYTES + P::B_BYTES + 8);
+    s.drain = reinterpret_cast<uint64_t *>(smem + 2 * P::A_BYTES + P::B_BYTES + 8);
+    s.tmem_slot = reinterpret_cast<uint32_t *>(smem + 2 * P::A_BYTES + P::B_BYTES + 16);
     s.phase = 0;
+    s.wait_limit = wait_limit < 0 ? WAIT_LIMIT : wait_limit;
     s.err = err;
     s.failed = false;
     if (threadIdx.x < 32) {
@@ -99,6 +107,7 @@ MF_DEV void setup(State &s, unsigned char *smem, int *err) {
     }
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(s.mbar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(s.drain)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -121,9 +130,9 @@ MF_DEV void load_colour(State &s, const int *cnum) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-MF_DEV bool wait_phase(uint64_t *mbar, uint32_t phase) {
+MF_DEV bool wait_phase(uint64_t *mbar, uint32_t phase, long long limit = WAIT_LIMIT) {
     const uint32_t addr = smem_u32(mbar);
-    for (long long it = 0; it < WAIT_LIMIT; ++it) {
+    for (long long it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -155,24 +164,30 @@ MF_DEV void ld_cols<16>(uint32_t taddr, float *out) {
 // One round: every thread of the block passes its row's amplitudes J
 // (NJ complex) and receives sum_kl Re(conj(J_k) C_kl J_l) (numerators only:
 // divide by the colour denominator).  Must be called by all 128 threads.
+// If a round's wait expires in any thread, the whole block (one decision,
+// taken at a barrier) records the error and from then on neither writes
+// the operands, nor issues MMAs, nor reads tensor memory: its results are 0
+// and unspecified, and no access races an MMA still in flight.
 template <int NJ>
 MF_DEV float colour_sum(State &s, const cx<float> *J) {
     using P = Plan<NJ>;
     const int r = threadIdx.x;
-    // this row of A_hi and A_lo: [Re J | Im J], zero padded to KP
+    if (!s.failed) {
+        // this row of A_hi and A_lo: [Re J | Im J], zero padded to KP
 #pragma unroll
-    for (int k = 0; k < P::KP; ++k) {
-        const float a = k < NJ ? J[k].re : (k < 2 * NJ ? J[k - NJ].im : 0.f);
-        const float hi = tf32_hi(a);
-        *reinterpret_cast<float *>(s.a_hi + core_offset(r, k, P::KP)) = hi;
-        *reinterpret_cast<float *>(s.a_lo + core_offset(r, k, P::KP)) = a - hi;
+        for (int k = 0; k < P::KP; ++k) {
+            const float a = k < NJ ? J[k].re : (k < 2 * NJ ? J[k - NJ].im : 0.f);
+            const float hi = tf32_hi(a);
+            *reinterpret_cast<float *>(s.a_hi + core_offset(r, k, P::KP)) = hi;
+            *reinterpret_cast<float *>(s.a_lo + core_offset(r, k, P::KP)) = a - hi;
+        }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *s.tmem_slot;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && !s.failed) {
         constexpr uint32_t idesc = InstrDesc<ROWS, P::NP>::value;
         constexpr uint32_t sbo = (uint32_t)P::KP * 32;
         const uint32_t a0 = smem_u32(s.a_hi), a1 = smem_u32(s.a_lo), b0 = smem_u32(s.b);
@@ -193,25 +208,31 @@ MF_DEV float colour_sum(State &s, const cx<float> *J) {
                          smem_u32(s.mbar))
                      : "memory");
     }
-    const bool ok = wait_phase(s.mbar, s.phase);
-    s.phase ^= 1u;
-    if (!ok) {
-        s.failed = true;
-        if (s.err) atomicExch(s.err, 1);
+    bool ok = false;
+    if (!s.failed) {
+        ok = wait_phase(s.mbar, s.phase, s.wait_limit);
+        s.phase ^= 1u;
     }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // this row of Z, 16 columns at a time (warp w reads lanes 32w .. 32w+31)
-    const uint32_t trow = tmem + ((uint32_t)((threadIdx.x >> 5) * 32) << 16);
+    // one decision for the block
+    if (__syncthreads_or(!ok) && !s.failed) {
+        s.failed = true;
+        if (s.err && threadIdx.x == 0) atomicExch(s.err, 1);
+    }
     float m = 0.f;
+    if (!s.failed) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // this row of Z, 16 columns at a time (warp w reads lanes 32w .. 32w+31)
+        const uint32_t trow = tmem + ((uint32_t)((threadIdx.x >> 5) * 32) << 16);
 #pragma unroll
-    for (int c0 = 0; c0 < P::NP; c0 += 16) {
-        float z[16];
-        ld_cols<16>(trow + c0, z);
+        for (int c0 = 0; c0 < P::NP; c0 += 16) {
+            float z[16];
+            ld_cols<16>(trow + c0, z);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const int c = c0 + i;
-            if (c < NJ) m += J[c].re * z[i];
-            else if (c < 2 * NJ) m += J[c - NJ].im * z[i];
+            for (int i = 0; i < 16; ++i) {
+                const int c = c0 + i;
+                if (c < NJ) m += J[c].re * z[i];
+                else if (c < 2 * NJ) m += J[c - NJ].im * z[i];
+            }
         }
     }
     // the next round rewrites A and the accumulator only after every thread
@@ -222,12 +243,23 @@ MF_DEV float colour_sum(State &s, const cx<float> *J) {
     return m;
 }
 
-// Release the tensor memory (warp 0) after a final barrier.  All threads.
+// Release the tensor memory (warp 0) once every MMA the block issued has
+// completed: thread 0 commits them to the drain barrier (a commit tracks all
+// earlier MMAs of the issuing thread) and every thread waits for its first
+// phase with the full limit.  All threads.
 template <int NJ>
 MF_DEV void teardown(State &s) {
-    // after an expired wait, give the outstanding MMAs one more bounded wait
-    // before the tensor memory is released
-    if (s.failed) wait_phase(s.mbar, s.phase);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (threadIdx.x == 0)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(s.drain))
+                     : "memory");
+    if (!wait_phase(s.drain, 0u)) {
+        s.failed = true;
+        if (s.err) atomicExch(s.err, 1);
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");

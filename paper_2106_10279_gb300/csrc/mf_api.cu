@@ -2,6 +2,7 @@
 // Vegas iteration (accumulation, fixed pairwise-tree reduction over chunks,
 // refinement and the combination of iterations; Sec. 2.2 and Lepage 1978).
 #include <algorithm>
+#include <atomic>
 #include <array>
 #include <cmath>
 #include <cstdio>
@@ -25,7 +26,40 @@ mf_status fail(mf_status st, const std::string &msg) {
     g_err = msg;
     return st;
 }
+
+// allocations left before the injected failure (-1: none armed)
+static std::atomic<long long> g_alloc_countdown{-1};
+
+static bool injected_failure() {
+    long long c = g_alloc_countdown.load();
+    while (c >= 0) {
+        if (g_alloc_countdown.compare_exchange_weak(c, c - 1)) return c == 0;
+    }
+    return false;
+}
+
+cudaError_t dev_malloc_raw(void **p, size_t bytes) {
+    if (injected_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t host_malloc_raw(void **p, size_t bytes) {
+    if (injected_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocHost(p, bytes);
+}
 }  // namespace mfi
+
+extern "C" mf_status mf_debug_fail_allocation(int64_t after) {
+    if (after < -1) return mfi::fail(MF_EINVAL, "after must be -1 or non-negative");
+    mfi::g_alloc_countdown.store(after);
+    return MF_OK;
+}
 
 using mfi::fail;
 
@@ -439,7 +473,8 @@ mf_status compile_shape(mf_process *p, int prec, int block, int ht, mfi::Compile
 }
 
 // Tile buffers (FP32, 128 threads) rounded up to 1 KB, then the tensor-core
-// operands: A_hi and A_lo (128 x KP), B (NP x KP), barrier and address.
+// operands: A_hi and A_lo (128 x KP), B (NP x KP), the round and drain
+// barriers and the tensor-memory address (mf::tc::Plan<NJ>::SMEM).
 size_t smem_bytes_tc(const mf_process &p) {
     const int K2 = 2 * p.n_jamp, KP = (K2 + 7) / 8 * 8, NP = (K2 + 15) / 16 * 16;
     const int nden1 = p.gen.n_den > 0 ? p.gen.n_den : 1, block = 128;
@@ -447,7 +482,7 @@ size_t smem_bytes_tc(const mf_process &p) {
     tile += (16 - (((size_t)block * nden1 * 4) % 16)) % 16;
     tile += (size_t)block * 8 * 2 + (size_t)block * 4 + (block / 32 + 1) * 4;
     tile = (tile + 1023) / 1024 * 1024;
-    return tile + 2 * (size_t)128 * KP * 4 + (size_t)NP * KP * 4 + 16;
+    return tile + 2 * (size_t)128 * KP * 4 + (size_t)NP * KP * 4 + 24;
 }
 
 int pow2_at_least(int n) {
@@ -509,6 +544,7 @@ mf_status compile_grad(mf_process *p) {
 
 void fill_common(const mf_process &p, mf_kparams &kp) {
     std::memset(&kp, 0, sizeof kp);
+    kp.wait_polls = p.opt.wait_polls;   // negative: the kernels' default limit
     kp.S = p.sqrt_s * p.sqrt_s;
     kp.ln_tau_min = p.ln_tau_min;
     kp.w0_const = p.w0_const;
@@ -569,12 +605,17 @@ void build_pairs(mf_process *p) {
 bool valid_prec(int prec) { return prec == MF_FP64 || prec == MF_MIXED || prec == MF_MIXED_TC; }
 
 // A process kernel's error flag: 1 = a bounded wait expired, 2 = the launch
-// gave less dynamic shared memory than the kernel needs.  Read after the
-// stream has been synchronised; clears the flag.
-mf_status flag_status(mf_process *p, int flag) {
-    if (!flag) return MF_OK;
+// gave less dynamic shared memory than the kernel needs, 3 = mf_integrand
+// wrote a non-finite value.  Read after the stream has been synchronised;
+// clears the flag.  The synchronous Vegas paths pass nonfinite = false:
+// they count their own non-finite weights, and leave a flag 3 raised by an
+// earlier mf_integrand call to mf_process_check.
+mf_status flag_status(mf_process *p, int flag, bool nonfinite = false) {
+    if (!flag || (flag == 3 && !nonfinite)) return MF_OK;
     cudaMemset(p->d_err, 0, sizeof(int));
     if (flag == 2) return fail(MF_ECUDA, "process kernel launched with too little shared memory (results not written)");
+    if (flag == 3)
+        return fail(MF_ENAN, "the integrand wrote non-finite values (non-finite coordinates, or overflow)");
     return fail(MF_ETIMEOUT, "a bounded wait in a process kernel expired; that launch's results are unspecified");
 }
 
@@ -612,7 +653,7 @@ mf_status validate_options(const mf_process_options *o) {
     if (!in(o->amplitude_units, 0, 1) || !in(o->call_routines, 0, 3) || !in(o->order_search, 0, 1 << 24) ||
         !in(o->sync_every, 0, 1 << 20) || !in(o->program_parts, 1, 4096) || !in(o->min_blocks, 0, 8) ||
         !in(o->helicity_pairs, 0, 1) || !(o->block == MF_OPT_AUTO || o->block == 128 || o->block == 256) || !pow2 ||
-        !in(o->blocks_per_sm, 1, 8) || !in(o->ptxas_level, 0, 3))
+        !in(o->blocks_per_sm, 1, 8) || !in(o->ptxas_level, 0, 3) || !in(o->wait_polls, 0, 1 << 30))
         return fail(MF_EINVAL, "process option out of range");
     return MF_OK;
 }
@@ -779,7 +820,7 @@ extern "C" mf_status mf_create_process(const mf_process_desc *d, mf_process **ou
     const int no = p->n_out;
     p->w0_const = std::pow(2.0 * kPi, 4 - 3 * no) * std::pow(kPi / 2.0, no - 1) / (factorial(no - 1) * factorial(no - 2));
     p->pref_const = p->average * kGeV2pb / 2.0;
-    if (cudaMalloc(&p->d_err, sizeof(int)) != cudaSuccess || cudaMemset(p->d_err, 0, sizeof(int)) != cudaSuccess) {
+    if (mfi::dev_malloc(&p->d_err, sizeof(int)) != cudaSuccess || cudaMemset(p->d_err, 0, sizeof(int)) != cudaSuccess) {
         mf_destroy_process(p);
         return fail(MF_ENOMEM, "error flag");
     }
@@ -792,8 +833,8 @@ extern "C" mf_status mf_create_process(const mf_process_desc *d, mf_process **ou
         double b0 = std::log(d->pdf_q2_min);
         double hb = (std::log(d->pdf_q2_max) - b0) / (nq - 1);
         double *d_tab = nullptr;
-        if (cudaMalloc(&p->d_pdf_rows, sizeof(double) * 4 * nx) != cudaSuccess ||
-            cudaMalloc(&d_tab, sizeof(double) * (size_t)nx * nq) != cudaSuccess) {
+        if (mfi::dev_malloc(&p->d_pdf_rows, sizeof(double) * 4 * nx) != cudaSuccess ||
+            mfi::dev_malloc(&d_tab, sizeof(double) * (size_t)nx * nq) != cudaSuccess) {
             cudaFree(d_tab);
             mf_destroy_process(p);
             return fail(MF_ENOMEM, "PDF rows");
@@ -825,8 +866,8 @@ extern "C" mf_status mf_create_process(const mf_process_desc *d, mf_process **ou
         for (auto &v : hx) v = ((splitmix64(s) >> 11) | 1ull) * 0x1p-53;
         const int nh = (int)(p->hel_all.size() / n);
         double *dx = nullptr, *df = nullptr;
-        if (cudaMalloc(&dx, sizeof(double) * hx.size()) != cudaSuccess ||
-            cudaMalloc(&df, sizeof(double) * (size_t)nh * npts) != cudaSuccess) {
+        if (mfi::dev_malloc(&dx, sizeof(double) * hx.size()) != cudaSuccess ||
+            mfi::dev_malloc(&df, sizeof(double) * (size_t)nh * npts) != cudaSuccess) {
             cudaFree(dx);
             mf_destroy_process(p);
             return fail(MF_ENOMEM, "helicity filter scratch");
@@ -1038,7 +1079,7 @@ extern "C" mf_status mf_process_check(mf_process *p) {
     int flag = 0;
     MF_CUDA(cudaDeviceSynchronize());
     MF_CUDA(cudaMemcpy(&flag, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-    return flag_status(p, flag);
+    return flag_status(p, flag, true);
 }
 
 extern "C" mf_status mf_integrand(mf_process *p, const double *x, int64_t n, double *f, mf_precision prec,
@@ -1185,8 +1226,8 @@ mf_status ensure_scratch(mf_process *p, mf_vegas *v, int64_t n) {
         p->d_w = nullptr;
         p->d_bins = nullptr;
         p->scratch_n = 0;
-        MF_CUDA(cudaMalloc(&p->d_w, sizeof(double) * n));
-        MF_CUDA(cudaMalloc(&p->d_bins, (size_t)p->ndim * n));
+        MF_CUDA(mfi::dev_malloc(&p->d_w, sizeof(double) * n));
+        MF_CUDA(mfi::dev_malloc(&p->d_bins, (size_t)p->ndim * n));
         p->scratch_n = n;
     }
     const int64_t nchunks = (n + kChunk - 1) / kChunk;
@@ -1195,7 +1236,7 @@ mf_status ensure_scratch(mf_process *p, mf_vegas *v, int64_t n) {
         cudaFree(v->d_slots);
         v->d_slots = nullptr;
         v->slots_cap = 0;
-        MF_CUDA(cudaMalloc(&v->d_slots, sizeof(double) * (nchunks * K + K)));
+        MF_CUDA(mfi::dev_malloc(&v->d_slots, sizeof(double) * (nchunks * K + K)));
         v->slots_cap = nchunks * K + K;
     }
     if (!p->ev_start) {
@@ -1330,14 +1371,14 @@ extern "C" mf_status mf_vegas_create(int32_t ndim, int32_t nbins, double alpha, 
     v->alpha = alpha;
     v->max_iter = MF_MAX_ITER;
     const int K = partial_size(v);
-    if (cudaMalloc(&v->d_grid, sizeof(double) * ndim * (nbins + 1)) != cudaSuccess ||
-        cudaMalloc(&v->d_hist, sizeof(double) * ndim * nbins) != cudaSuccess ||
-        cudaMalloc(&v->d_count, sizeof(long long) * ndim * nbins) != cudaSuccess ||
-        cudaMalloc(&v->d_hist_iter, sizeof(double) * 2 * v->max_iter) != cudaSuccess ||
-        cudaMalloc(&v->d_result, sizeof(double) * 8) != cudaSuccess ||
-        cudaMalloc(&v->d_tree_ids, sizeof(int64_t) * 2 * MF_MAX_TREE_NODES) != cudaSuccess ||
-        cudaMalloc(&v->d_tree_out, sizeof(double) * (size_t)K * MF_MAX_TREE_NODES) != cudaSuccess ||
-        cudaMalloc(&v->d_tot, sizeof(double) * K) != cudaSuccess) {
+    if (mfi::dev_malloc(&v->d_grid, sizeof(double) * ndim * (nbins + 1)) != cudaSuccess ||
+        mfi::dev_malloc(&v->d_hist, sizeof(double) * ndim * nbins) != cudaSuccess ||
+        mfi::dev_malloc(&v->d_count, sizeof(long long) * ndim * nbins) != cudaSuccess ||
+        mfi::dev_malloc(&v->d_hist_iter, sizeof(double) * 2 * v->max_iter) != cudaSuccess ||
+        mfi::dev_malloc(&v->d_result, sizeof(double) * 8) != cudaSuccess ||
+        mfi::dev_malloc(&v->d_tree_ids, sizeof(int64_t) * 2 * MF_MAX_TREE_NODES) != cudaSuccess ||
+        mfi::dev_malloc(&v->d_tree_out, sizeof(double) * (size_t)K * MF_MAX_TREE_NODES) != cudaSuccess ||
+        mfi::dev_malloc(&v->d_tot, sizeof(double) * K) != cudaSuccess) {
         mf_vegas_destroy(v);
         return fail(MF_ENOMEM, "Vegas grid");
     }
@@ -1722,7 +1763,7 @@ extern "C" mf_status mf_batch_create(mf_process *const *procs, int32_t nproc, mf
         b->kern.smem = smem;
         st = mfi::load_kernel(cubin, b->kern, "mf_batch_kernel");
     }
-    if (st == MF_OK && cudaMalloc(&b->d_counter, sizeof(long long)) != cudaSuccess)
+    if (st == MF_OK && mfi::dev_malloc(&b->d_counter, sizeof(long long)) != cudaSuccess)
         st = fail(MF_ENOMEM, "batch counter");
     if (st == MF_OK && (cudaEventCreate(&b->ev_start) != cudaSuccess || cudaEventCreate(&b->ev_stop) != cudaSuccess))
         st = fail(MF_ECUDA, "batch events");
@@ -1858,11 +1899,11 @@ mf_status capture_batch(mf_batch *b, mf_vegas *const *grids, const int64_t *n_ev
     }
     if (!b->capture_stream) MF_CUDA(cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking));
     if (!b->d_iters) {
-        MF_CUDA(cudaMalloc(&b->d_iters, sizeof(long long) * nproc));
-        MF_CUDA(cudaMalloc(&b->d_root_ids, sizeof(int64_t) * 2 * nproc));
-        MF_CUDA(cudaMallocHost(&b->h_iters, sizeof(long long) * nproc));
-        MF_CUDA(cudaMallocHost(&b->h_res, sizeof(double) * 8 * nproc));
-        MF_CUDA(cudaMallocHost(&b->h_flags, sizeof(int) * nproc));
+        MF_CUDA(mfi::dev_malloc(&b->d_iters, sizeof(long long) * nproc));
+        MF_CUDA(mfi::dev_malloc(&b->d_root_ids, sizeof(int64_t) * 2 * nproc));
+        MF_CUDA(mfi::host_malloc(&b->h_iters, sizeof(long long) * nproc));
+        MF_CUDA(mfi::host_malloc(&b->h_res, sizeof(double) * 8 * nproc));
+        MF_CUDA(mfi::host_malloc(&b->h_flags, sizeof(int) * nproc));
     }
     std::vector<int64_t> roots(2 * nproc);
     for (int k = 0; k < nproc; ++k) {
@@ -2105,9 +2146,9 @@ extern "C" mf_status mf_vegas_observables(mf_vegas *v, mf_process *p, int64_t n_
             return fail(MF_ECUDA, std::string("observables: ") + cudaGetErrorString(e_));      \
         }                                                                                      \
     } while (0)
-    MF_OB(cudaMalloc(&d_obs, sizeof(uint16_t) * (size_t)n_obs * n));
-    MF_OB(cudaMalloc(&d_part, sizeof(double) * (size_t)nchunks * n_obs * kObsBins * 3));
-    MF_OB(cudaMalloc(&d_nan, sizeof(int)));
+    MF_OB(mfi::dev_malloc(&d_obs, sizeof(uint16_t) * (size_t)n_obs * n));
+    MF_OB(mfi::dev_malloc(&d_part, sizeof(double) * (size_t)nchunks * n_obs * kObsBins * 3));
+    MF_OB(mfi::dev_malloc(&d_nan, sizeof(int)));
     MF_OB(cudaMemsetAsync(d_nan, 0, sizeof(int), s));
     mf_kparams ko;
     vegas_params(p, v, n, 0, subprocess, seed, ko);
@@ -2247,8 +2288,8 @@ extern "C" mf_status mf_process_read_weights(mf_process *p, const int64_t *idx, 
     if (n == 0) return MF_OK;
     int64_t *d_idx = nullptr;
     double *d_out = nullptr;
-    cudaError_t e = cudaMalloc(&d_idx, sizeof(int64_t) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&d_out, sizeof(double) * n);
+    cudaError_t e = mfi::dev_malloc(&d_idx, sizeof(int64_t) * n);
+    if (e == cudaSuccess) e = mfi::dev_malloc(&d_out, sizeof(double) * n);
     if (e == cudaSuccess) e = cudaMemcpy(d_idx, idx, sizeof(int64_t) * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         gather_kernel<<<(unsigned)((n + 255) / 256), 256>>>(p->d_w, d_idx, n, d_out);
@@ -2265,7 +2306,7 @@ extern "C" mf_status mf_process_max_weight(mf_process *p, double *w_max, void *s
     if (!p || !w_max) return fail(MF_EINVAL, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
     unsigned long long *d = nullptr;
-    MF_CUDA(cudaMalloc(&d, sizeof(unsigned long long)));
+    MF_CUDA(mfi::dev_malloc(&d, sizeof(unsigned long long)));
     unsigned long long h = 0;
     cudaError_t e = cudaMemsetAsync(d, 0, sizeof h, s);
     if (e == cudaSuccess && p->last_n > 0) {
@@ -2330,9 +2371,9 @@ extern "C" mf_status mf_vegas_unweight(mf_vegas *v, mf_process *p, int64_t n_eve
             return fail(MF_ECUDA, std::string("unweighting: ") + cudaGetErrorString(e_));       \
         }                                                                                      \
     } while (0)
-    MF_UW(cudaMalloc(&d_acc, (size_t)n));
-    MF_UW(cudaMalloc(&d_cnt, sizeof(int) * nchunks));
-    MF_UW(cudaMalloc(&d_off, sizeof(int64_t) * nchunks));
+    MF_UW(mfi::dev_malloc(&d_acc, (size_t)n));
+    MF_UW(mfi::dev_malloc(&d_cnt, sizeof(int) * nchunks));
+    MF_UW(mfi::dev_malloc(&d_off, sizeof(int64_t) * nchunks));
     unweight_count_kernel<<<(unsigned)nchunks, kUwThreads, 0, s>>>(p->d_w, n, seed, (uint64_t)v->iteration,
                                                                    (uint64_t)subprocess, w_max, d_acc, d_cnt);
     MF_UW(cudaGetLastError());
@@ -2352,9 +2393,9 @@ extern "C" mf_status mf_vegas_unweight(mf_vegas *v, mf_process *p, int64_t n_eve
     *n_accepted = nacc;
     if (nacc > 0 && (capacity > 0 || lhe)) {
         MF_UW(cudaMemcpyAsync(d_off, off.data(), sizeof(int64_t) * nchunks, cudaMemcpyHostToDevice, s));
-        MF_UW(cudaMalloc(&d_idx, sizeof(int64_t) * nacc));
-        MF_UW(cudaMalloc(&d_wk, sizeof(double) * nacc));
-        MF_UW(cudaMalloc(&d_rec, sizeof(double) * RW * nacc));
+        MF_UW(mfi::dev_malloc(&d_idx, sizeof(int64_t) * nacc));
+        MF_UW(mfi::dev_malloc(&d_wk, sizeof(double) * nacc));
+        MF_UW(mfi::dev_malloc(&d_rec, sizeof(double) * RW * nacc));
         unweight_compact_kernel<<<(unsigned)nchunks, kUwThreads, 0, s>>>(d_acc, p->d_w, n, d_off, d_idx, d_wk);
         MF_UW(cudaGetLastError());
         // the kept points' kinematics, recomputed from their Philox counters

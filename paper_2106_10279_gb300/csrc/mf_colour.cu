@@ -91,7 +91,7 @@ extern "C" mf_status mf_colour_sum(const float *J, int64_t n, const int32_t *cnu
     if (n == 0) return MF_OK;
     cudaStream_t s = (cudaStream_t)stream;
     int *d_c = nullptr, *d_err = nullptr;
-    if (cudaMalloc(&d_c, sizeof(int) * nj * nj) != cudaSuccess || cudaMalloc(&d_err, sizeof(int)) != cudaSuccess) {
+    if (mfi::dev_malloc(&d_c, sizeof(int) * nj * nj) != cudaSuccess || mfi::dev_malloc(&d_err, sizeof(int)) != cudaSuccess) {
         cudaFree(d_c);
         return fail(MF_ENOMEM, "colour sum scratch");
     }

@@ -17,6 +17,19 @@ namespace mfi {
 void set_error(const std::string &msg);
 mf_status fail(mf_status st, const std::string &msg);
 
+// Every device (and pinned host) allocation of the library goes through
+// these, so that a test can make one of them fail (mf_debug_fail_allocation).
+cudaError_t dev_malloc_raw(void **p, size_t bytes);
+cudaError_t host_malloc_raw(void **p, size_t bytes);
+template <typename T>
+cudaError_t dev_malloc(T **p, size_t bytes) {
+    return dev_malloc_raw(reinterpret_cast<void **>(p), bytes);
+}
+template <typename T>
+cudaError_t host_malloc(T **p, size_t bytes) {
+    return host_malloc_raw(reinterpret_cast<void **>(p), bytes);
+}
+
 struct DenSlot {
     uint32_t mask;   // legs whose signed momenta sum to the current's momentum
     int32_t mass_id; // -1 = massless propagator
@@ -56,7 +69,7 @@ struct mf_process {
     int device = 0;
     // code-generation and launch options (MF_OPT_AUTO: the library decides)
     mf_process_options opt = {MF_OPT_AUTO, MF_OPT_AUTO, MF_OPT_AUTO, MF_OPT_AUTO, MF_OPT_AUTO, MF_OPT_AUTO,
-                              MF_OPT_AUTO, MF_OPT_AUTO, MF_OPT_AUTO, MF_OPT_AUTO, MF_OPT_AUTO};
+                              MF_OPT_AUTO, MF_OPT_AUTO, MF_OPT_AUTO, MF_OPT_AUTO, MF_OPT_AUTO, MF_OPT_AUTO};
     // deep copy of the descriptor
     int n_legs = 0, n_out = 0, ndim = 0;
     std::vector<int32_t> leg_kind, leg_incoming, leg_mass_id, leg_cut;

@@ -177,8 +177,8 @@ extern "C" mf_status mf_measure_peak(int32_t kind, int32_t reps, double *tflops,
         return fail(MF_ECUDA, "mf_measure_peak: no device");
     void *d_sink = nullptr;
     int *d_err = nullptr;
-    if (cudaMalloc(&d_sink, kFmaThreads * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&d_err, sizeof(int)) != cudaSuccess) {
+    if (mfi::dev_malloc(&d_sink, kFmaThreads * sizeof(double)) != cudaSuccess ||
+        mfi::dev_malloc(&d_err, sizeof(int)) != cudaSuccess) {
         cudaFree(d_sink);
         return fail(MF_ENOMEM, "mf_measure_peak: scratch");
     }
