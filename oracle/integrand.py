@@ -106,15 +106,20 @@ class Integrand:
             pt = np.hypot(p[:, i, 1], p[:, i, 2])
             keep &= pt > wl.pt_min_gluon
         if wl.dr_min_gluon > 0:
+            # Delta R only where the pT cuts kept the point: there every
+            # gluon has pT > 0, so its rapidity is finite (a gluon along the
+            # beam has none)
+            k = np.flatnonzero(keep)
+            q = p[k]
             for a in range(len(self.gluon_finals)):
                 for b in range(a + 1, len(self.gluon_finals)):
                     i, j = self.gluon_finals[a], self.gluon_finals[b]
-                    yi = 0.5 * np.log((p[:, i, 0] + p[:, i, 3]) / (p[:, i, 0] - p[:, i, 3]))
-                    yj = 0.5 * np.log((p[:, j, 0] + p[:, j, 3]) / (p[:, j, 0] - p[:, j, 3]))
-                    dphi = np.arctan2(p[:, i, 2], p[:, i, 1]) - np.arctan2(p[:, j, 2], p[:, j, 1])
+                    yi = 0.5 * np.log((q[:, i, 0] + q[:, i, 3]) / (q[:, i, 0] - q[:, i, 3]))
+                    yj = 0.5 * np.log((q[:, j, 0] + q[:, j, 3]) / (q[:, j, 0] - q[:, j, 3]))
+                    dphi = np.arctan2(q[:, i, 2], q[:, i, 1]) - np.arctan2(q[:, j, 2], q[:, j, 1])
                     dphi = np.angle(np.exp(1j * dphi))
                     dr = np.sqrt((yi - yj) ** 2 + dphi ** 2)
-                    keep &= dr > wl.dr_min_gluon
+                    keep[k] &= dr > wl.dr_min_gluon
         return keep
 
     def __call__(self, x, return_parts=False):

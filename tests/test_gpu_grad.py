@@ -11,7 +11,8 @@
   numbers (relative <= 1e-9);
 * the value it returns against the oracle with the FP64 parity bound;
 * the summed pathwise dsigma/dm_t against the finite difference of sigma over
-  the same points, and the boundary term reported separately;
+  the same points, and the boundary term reported separately (gg->tt~g and
+  gg->tt~gg), with dsigma/dalpha_s = k sigma / alpha_s;
 * the torch.autograd wrapper.
 """
 import math
@@ -119,12 +120,12 @@ def test_dmt_matches_central_differences(torch_cuda, procs, name, n):
     assert err.max() < 1e-4, (name, err.max())
 
 
-@pytest.mark.parametrize("name", ["gg_ttx", "gg_ttxg", "uux_ttxg"])
+@pytest.mark.parametrize("name", ["gg_ttx", "gg_ttxg", "uux_ttxg", "gg_ttxgg"])
 def test_dalphas_is_exact(torch_cuda, procs, name):
     wl = W.WORKLOADS[name]
     x = W.uniform_points(wl.ndim, 100, 44)
     f, dp, dx = _grad(torch_cuda, procs(name), x)
-    k = {"gg_ttx": 2, "gg_ttxg": 3, "uux_ttxg": 3}[name]
+    k = {"gg_ttx": 2, "gg_ttxg": 3, "uux_ttxg": 3, "gg_ttxgg": 4}[name]
     nz = f != 0
     assert np.allclose(dp[1][nz], k * f[nz] / wl.alpha_s, rtol=1e-14)
     h = 1e-3 * wl.alpha_s
@@ -166,25 +167,31 @@ def test_grad_matches_oracle_richardson(torch_cuda, procs, name, n):
         assert err.max() < 1e-6, (j, err.max())
 
 
-def test_summed_dsigma_dmt_and_boundary_term(torch_cuda, procs):
+@pytest.mark.parametrize("name,n", [("gg_ttxg", 20000), ("gg_ttxgg", 20000)])
+def test_summed_dsigma_dmt_and_boundary_term(torch_cuda, procs, name, n):
     # pathwise estimator of dsigma/dm_t = mean df/dm_t against the finite
     # difference of the same-point mean, restricted to points that keep their
     # cut status; the full finite difference also contains the boundary term
-    wl = W.GG_TTXG
-    n = 20000
+    # (points entering or leaving the cuts and the threshold as m_t moves)
+    wl = W.WORKLOADS[name]
     x = W.uniform_points(wl.ndim, n, 46)
     h = 1e-3 * wl.m_top
-    f, dp, dx = _grad(torch_cuda, procs("gg_ttxg"), x)
-    fp = _f(torch_cuda, procs("gg_ttxg", m_top=wl.m_top + h), x)
-    fm = _f(torch_cuda, procs("gg_ttxg", m_top=wl.m_top - h), x)
+    f, dp, dx = _grad(torch_cuda, procs(name), x)
+    fp = _f(torch_cuda, procs(name, m_top=wl.m_top + h), x)
+    fm = _f(torch_cuda, procs(name, m_top=wl.m_top - h), x)
     same = (fp != 0) & (fm != 0) & (f != 0)
     pathwise = np.mean(np.where(same, dp[0], 0.0))
     fd_same = np.mean(np.where(same, (fp - fm) / (2 * h), 0.0))
     fd_all = np.mean((fp - fm) / (2 * h))
-    assert abs(pathwise / fd_same - 1) < 1e-4
+    assert abs(pathwise / fd_same - 1) < 1e-4, (pathwise, fd_same)
     boundary = fd_all - fd_same
+    print(f"{name}: dsigma/dm_t pathwise {pathwise:.6g} pb/GeV, finite difference {fd_all:.6g}, "
+          f"boundary term {boundary:.3g} ({boundary / fd_all:.2%})")
     # moving the cut boundary is a small effect at pT > 20 GeV
     assert abs(boundary) < 0.05 * abs(fd_all)
+    # dsigma/dalpha_s = k sigma / alpha_s over the same points
+    k = {"gg_ttxg": 3, "gg_ttxgg": 4}[name]
+    assert np.mean(dp[1]) == pytest.approx(k * np.mean(f) / wl.alpha_s, rel=1e-13)
 
 
 def test_autograd_wrapper(torch_cuda, procs):
@@ -204,7 +211,7 @@ def test_autograd_wrapper(torch_cuda, procs):
 
 
 @pytest.mark.parametrize("name,n", [("ee_mumu", 30), ("gg_ttx", 40), ("uux_ttx", 40), ("gg_ttxg", 20),
-                                    ("uux_ttxg", 20), ("gg_ttxgg", 4)])
+                                    ("uux_ttxg", 20), ("gg_ttxgg", 32)])
 def test_grad_matches_oracle_dual_numbers(torch_cuda, procs, oracle_processes, name, n):
     # both sides exact to rounding: the GPU's forward tangents plus
     # hand-written adjoints against the oracle's forward-mode dual numbers
@@ -216,6 +223,7 @@ def test_grad_matches_oracle_dual_numbers(torch_cuda, procs, oracle_processes, n
     fo, dxo, dmo = I.gradient(x)
     nz = fo != 0
     assert np.array_equal(f == 0, fo == 0)
+    assert nz.sum() >= min(16, n // 2), nz.sum()
     err = np.abs(dx - dxo)[:, nz] / (np.abs(dxo) + np.abs(fo))[:, nz]
     assert err.max() < 1e-9, err.max()
     mt = wl.m_top
