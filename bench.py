@@ -34,6 +34,9 @@ METRIC = "events/s of gg→tt̄g(g) LO integrand: mixed/batched vs FP64 at ≤1e
 # capture's kernel is the one built from this source)
 KERNEL_DRAM_BYTES_PER_POINT = {("gg_ttxgg", "mixed"): (144.32e6 + 22.65e9) / 4e7}
 WORKLOAD = "gg_ttxgg"
+# FP64 FLOPs per point executed by the gradient kernel (2 x DFMA + DADD +
+# DMUL thread instructions of one ncu capture divided by its points)
+GRAD_FP64_FLOPS_PER_POINT = {}
 
 
 def _args():
@@ -145,6 +148,60 @@ def cpu_baseline_oracle(wl, n_sample):
     vegas.accumulate(w, bins, wl.n_bins)
     dt = time.perf_counter() - t0
     return n_sample / dt, dt
+
+
+_ORACLE = {}
+
+
+def _oracle_worker_init(name):
+    # one process per host core, one numpy thread each; the oracle's one-time
+    # set-up (colour matrix) happens here, outside the timed work
+    import workloads as W
+    from oracle.integrand import Integrand
+    I = Integrand(W.WORKLOADS[name])
+    I.proc.colour_matrix()
+    _ORACLE["I"] = I
+
+
+def _oracle_chunk(args):
+    seed, first, n, name = args
+    import workloads as W
+    from oracle import vegas
+    from oracle.philox import vegas_uniforms
+    wl = W.WORKLOADS[name]
+    grid = vegas.uniform_grid(wl.ndim, wl.n_bins)
+    y = vegas_uniforms(seed, 0, 0, first, n, wl.ndim)
+    x, jac, bins = vegas.vegas_map(grid, y)
+    w = _ORACLE["I"](x) * jac
+    vegas.accumulate(w, bins, wl.n_bins)
+    return n
+
+
+def cpu_baseline_oracle_all_cores(wl, n_per_core):
+    """The oracle on every host core: one spawned worker process per core
+    (one numpy thread each) evaluating its own n_per_core points of the
+    same Vegas iteration; events/s over the wall time of the timed map."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in env_keys}
+    for k in env_keys:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(cores, initializer=_oracle_worker_init, initargs=(wl.name,)) as pool:
+            pool.map(_oracle_chunk, [(1, 10 ** 9 + i * 16, 16, wl.name) for i in range(cores)])   # warm
+            jobs = [(1, i * n_per_core, n_per_core, wl.name) for i in range(cores)]
+            t0 = time.perf_counter()
+            done = sum(pool.map(_oracle_chunk, jobs, chunksize=1))
+            dt = time.perf_counter() - t0
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return done / dt, dt, cores, done
 
 
 def workload_config(wl, n_events, precision, n_diagrams, n_hel, n_jamp):
@@ -366,6 +423,35 @@ def run_native(args):
                  "same_sigma_as_separate": all(a["sigma"] == b["sigma"] for a, b in zip(res_b, res_s)),
                  "kernel_ms": bt.info()["last_kernel_ms"]}
 
+    # the gradient kernel (mf_grad: f, df/dm_t, df/dalpha_s, df/dx in FP64) on
+    # uniform points of the same process: points/s and, from the FP64
+    # arithmetic ncu counted per point of that kernel, its FP64 rate
+    grad = None
+    if not args.no_batch:
+        ng = min(n_events, 200_000)
+        xg = torch.from_numpy(W.uniform_points(wl.ndim, ng, 91)).cuda()
+        proc.grad(xg[:, :1024].contiguous(), stream=stream)     # compiles the gradient kernel
+        torch.cuda.synchronize()
+        gts, out = [], None
+        for _ in range(3):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            out = proc.grad(xg, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            gts.append(a.elapsed_time(b))
+        gms = min(gts)
+        fg, dpg, _ = out
+        grad = {"events": ng, "ms": gms, "events_per_s": ng / (gms / 1e3),
+                "dsigma_dmt_pb_per_gev_pathwise": float(dpg[0].mean()),
+                "dsigma_dalphas_pb": float(dpg[1].mean()), "sigma_pb": float(fg.mean())}
+        fl = GRAD_FP64_FLOPS_PER_POINT.get(wl.name)
+        if fl:
+            grad["roofline"] = {"bound": "alu", "achieved": fl * ng / (gms / 1e3) / 1e12, "unit": "TFLOP/s",
+                                "flops_per_point": fl, "flops_source": "executed FP64 FMA x2 + add + mul per point "
+                                                                      "of mf_grad_kernel (ncu counters)"}
+
     # roofline of the dominant kernel: algorithmic FLOPs / its device time
     kms = statistics.median(kernel_ms)
     # (an iteration's counts cover all ranks; the kernel timed is this rank's)
@@ -382,14 +468,23 @@ def run_native(args):
     fp32_kind = max(("fp32_ffma", "fp32_ffma2"), key=lambda k: mp[k]["tflops"])
     fp32_peak = mp[fp32_kind]["tflops"]
     fp64_peak = mp["fp64_dfma"]["tflops"]
+    if grad and "roofline" in grad:
+        grad["roofline"].update(peak=fp64_peak, frac=grad["roofline"]["achieved"] / fp64_peak,
+                                peak_source="measured: mf_measure_peak fp64_dfma")
 
-    cpu = None
+    cpu = cpu1 = None
     if rank == 0 and not args.no_cpu_baseline:
         sample = 2000 if wl.name == "gg_ttxgg" else 20000
         rate, dt = cpu_baseline_oracle(wl, sample)
-        cpu = {"value": rate, "unit": "events/s", "cores": 1, "kind": "oracle",
-               "sample": f"{sample} points of one {wl.name} Vegas iteration (Philox, map, integrand, "
-                         f"accumulate), {dt:.1f} s"}
+        cpu1 = {"value": rate, "unit": "events/s", "cores": 1, "kind": "oracle",
+                "sample": f"{sample} points of one {wl.name} Vegas iteration (Philox, map, integrand, "
+                          f"accumulate), {dt:.1f} s"}
+        per_core = max(100, int(rate * 12))          # about 12 s of work per core
+        rate_all, dt_all, cores, done = cpu_baseline_oracle_all_cores(wl, per_core)
+        cpu = {"value": rate_all, "unit": "events/s", "cores": cores, "kind": "oracle",
+               "sample": f"{done} points of one {wl.name} Vegas iteration (Philox, map, integrand, accumulate) "
+                         f"split over {cores} spawned processes, one per host core (nproc = {cores}), "
+                         f"one numpy thread each, {dt_all:.1f} s wall"}
     launches_per_step = 5          # integrand, accumulate, tree reduction, finalize, refine
     line = {
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
@@ -404,6 +499,7 @@ def run_native(args):
                               "peak_source": "measured: mf_measure_peak fp64_dfma (DFMA chains, all SMs)"}},
         "peaks": {"sms": n_sm, "measured": mp},
         "batch": batch,
+        "grad": grad,
         "kernel_variants": variants,
         "accuracy": {"median_rel_mixed_vs_fp64": float(np.median(rel)), "max_rel_mixed_vs_fp64": float(rel.max()),
                      "points": int(nz.sum())},
@@ -423,6 +519,7 @@ def run_native(args):
                      "peak_source": f"measured: mf_measure_peak {fp32_kind} ({n_sm} SMs, FMA chains, "
                                     f"{mp[fp32_kind]['sm_mhz']} MHz median SM clock)"},
         "cpu_baseline": cpu,
+        "cpu_baseline_single_thread": cpu1,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,

@@ -454,16 +454,18 @@ size_t smem_bytes(const mf_process &p, int prec, int block) {
 
 // Generate, compile and load the process kernel of precision prec with the
 // launch shape (block, ht) into k.
-mf_status compile_shape(mf_process *p, int prec, int block, int ht, mfi::Compiled &k, int min_blocks = -1) {
+mf_status compile_shape(mf_process *p, int prec, int block, int ht, mfi::Compiled &k, int min_blocks = -1,
+                        int level = -1) {
     k.block = block;
     k.ht = ht;
     k.min_blocks = min_blocks;
+    k.ptxas_level = level >= 0 ? level : p->opt.ptxas_level;
     mfi::GenInfo info;
     std::string src = mfi::generate_source(*p, prec, k.block, k.ht, info, "proc", true, min_blocks);
     std::vector<char> cubin;
     mf_status st = mfi::jit_compile(src, prec == MF_FP64 ? "mf_proc_f64.cu" : prec == MF_MIXED ? "mf_proc_mixed.cu"
                                                                                   : "mf_proc_mixed_tc.cu", cubin,
-                                    p->opt.ptxas_level);
+                                    k.ptxas_level);
     if (st != MF_OK) return st;
     // the shared-memory size depends on the program's denominator count
     p->source[prec] = src;
@@ -514,6 +516,83 @@ double helicity_sum_flops(const mf_process *p) {
     return f;
 }
 
+void fill_common(const mf_process &p, mf_kparams &kp);
+void set_hel(mf_kparams &kp, const std::vector<int8_t> &hel, int n_legs);
+mf_status launch(mf_process *p, int prec, mf_kparams &kp, cudaStream_t s);
+mf_status flag_status(mf_process *p, int flag, bool nonfinite);
+
+// Self-check of a compiled kernel's helicity-pair program.  The same kernel
+// evaluates the helicity sum with the pair program (the process's pair
+// table) or, given no pairs, one helicity at a time; on 256 seeded points
+// the two must agree to rounding.  They did not for one FP64 gg -> tt~g
+// program (amplitude units, searched order, amplitude routines called):
+// the same source built at device-assembler level 0 or 1 was right, at 2 or
+// 3 wrong at every point -- an optimisation of the assembler, not the
+// generated program, which also passes on the host.  On disagreement the
+// kernel is therefore rebuilt at level 1, then 0; if it still disagrees the
+// process cannot be used (MF_EJIT).  Kernels without pairs and the
+// tensor-core kernel (single helicities) have nothing to check.
+mf_status verify_pairs(mf_process *p, int prec) {
+    if (p->pairs.empty() || prec == MF_MIXED_TC || !p->kern[prec].fn) return MF_OK;
+    const int npts = 256;
+    std::vector<double> hx((size_t)p->ndim * npts);
+    uint64_t seed = 0xC0FFEEu;
+    for (auto &v : hx) v = ((splitmix64(seed) >> 11) | 1ull) * 0x1p-53;
+    double *dx = nullptr, *df = nullptr;
+    if (mfi::dev_malloc(&dx, sizeof(double) * hx.size()) != cudaSuccess ||
+        mfi::dev_malloc(&df, sizeof(double) * 2 * npts) != cudaSuccess) {
+        cudaFree(dx);
+        return fail(MF_ENOMEM, "pair-program check scratch");
+    }
+    mf_status st = MF_OK;
+    const double tol = prec == MF_FP64 ? 1e-10 : 1e-3;
+    const int levels[3] = {-1, 1, 0};
+    bool ok = false;
+    for (int attempt = 0; attempt < 3 && st == MF_OK && !ok; ++attempt) {
+        mfi::Compiled &k = p->kern[prec];
+        if (attempt > 0) {
+            if (p->opt.ptxas_level >= 0 && p->opt.ptxas_level <= levels[attempt]) break;
+            mfi::Compiled rebuilt;
+            st = compile_shape(p, prec, k.block, k.ht, rebuilt, k.min_blocks, levels[attempt]);
+            if (st != MF_OK) break;
+            mfi::unload_kernel(k);
+            k = rebuilt;
+        }
+        std::vector<double> hf(2 * npts);
+        int flag = 0;
+        cudaError_t e = cudaMemcpy(dx, hx.data(), sizeof(double) * hx.size(), cudaMemcpyHostToDevice);
+        for (int pass = 0; pass < 2 && e == cudaSuccess && st == MF_OK; ++pass) {
+            mf_kparams kp;
+            fill_common(*p, kp);
+            set_hel(kp, p->hel, p->n_legs);
+            kp.hel_sample = 0;
+            if (pass == 1) kp.npairs = 0;            // one helicity at a time
+            kp.mode = 0;
+            kp.n = npts;
+            kp.x = dx;
+            kp.f = df + pass * npts;
+            st = launch(p, prec, kp, nullptr);
+        }
+        if (st == MF_OK && e == cudaSuccess) e = cudaMemcpy(hf.data(), df, sizeof(double) * hf.size(), cudaMemcpyDeviceToHost);
+        if (st == MF_OK && e == cudaSuccess) e = cudaMemcpy(&flag, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+        if (st == MF_OK && e != cudaSuccess) st = fail(MF_ECUDA, std::string("pair-program check: ") + cudaGetErrorString(e));
+        if (st == MF_OK) st = flag_status(p, flag, true);
+        if (st != MF_OK) break;
+        ok = true;
+        for (int i = 0; i < npts && ok; ++i) {
+            const double a = hf[i], b = hf[npts + i];
+            ok = (a == 0.0) == (b == 0.0) && std::fabs(a - b) <= tol * std::fabs(b);
+        }
+    }
+    cudaFree(dx);
+    cudaFree(df);
+    if (st != MF_OK) return st;
+    if (!ok)
+        return fail(MF_EJIT, "the compiled helicity-pair program disagrees with the single-helicity program "
+                             "(device assembler at every level tried)");
+    return MF_OK;
+}
+
 mf_status compile_precision(mf_process *p, int prec) {
     mfi::Compiled &k = p->kern[prec];
     if (k.fn) return MF_OK;
@@ -526,7 +605,9 @@ mf_status compile_precision(mf_process *p, int prec) {
     // launch-shape options: block size and lanes per event
     if (p->opt.block > 0 && prec != MF_MIXED_TC) block = p->opt.block;
     if (p->opt.lanes > 0 && p->opt.lanes <= nhp) ht = p->opt.lanes;
-    return compile_shape(p, prec, block, ht, k);
+    mf_status st = compile_shape(p, prec, block, ht, k);
+    if (st != MF_OK) return st;
+    return verify_pairs(p, prec);
 }
 
 mf_status compile_grad(mf_process *p) {
@@ -909,6 +990,12 @@ extern "C" mf_status mf_create_process(const mf_process_desc *d, mf_process **ou
         }
     }
     build_pairs(p);
+    st = verify_pairs(p, MF_FP64);
+    if (st != MF_OK) {
+        std::string msg = mf_last_error();
+        mf_destroy_process(p);
+        return fail(st, msg);
+    }
     *out = p;
     return MF_OK;
 }
@@ -1692,6 +1779,8 @@ extern "C" mf_status mf_process_tune(mf_process *p, mf_precision prec, int64_t n
     mfi::GenInfo info;
     p->source[prec] = mfi::generate_source(*p, prec, best.block, best.ht, info, "proc", true, best.min_blocks);
     p->gen = info;
+    st = verify_pairs(p, prec);
+    if (st != MF_OK) return st;
     if (block) *block = best.block;
     if (ht) *ht = best.ht;
     return MF_OK;

@@ -45,6 +45,7 @@ struct Compiled {
     int regs = 0;
     size_t local_bytes = 0;
     int min_blocks = -1;           // __launch_bounds__ minimum (-1: the default)
+    int ptxas_level = -1;          // device-assembler level it was built at (-1: the default, 3)
 };
 
 struct GenInfo {

@@ -23,4 +23,8 @@ def fp64_tolerance(oracle, x):
     f, parts = oracle(x, return_parts=True)
     with np.errstate(invalid="ignore"):
         tol = 1e-12 + 64 * EPS * parts["condition"]
+    # an undefined condition number goes with f = 0 (a density or the phase
+    # space vanishing: only the zero pattern is compared); a point with a
+    # value but no condition number gets the bare 1e-12
+    tol = np.where(np.isnan(tol) & (f != 0), 1e-12, tol)
     return f, np.where(np.isnan(tol), np.inf, tol)

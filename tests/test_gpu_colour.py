@@ -91,7 +91,8 @@ def test_vegas_iteration_with_tensor_core_colour_sum(env):
     assert abs(ra["sigma"] / rb["sigma"] - 1) < 1e-4
 
 
-@pytest.mark.parametrize("name,n", [("gg_ttx", 800), ("uux_ttx", 800), ("uux_ttxg", 300), ("gg_ttxg", 300)])
+@pytest.mark.parametrize("name,n", [("gg_ttx", 800), ("uux_ttx", 800), ("uux_ttxg", 300), ("gg_ttxg", 300),
+                                    ("gg_ttxgg", 64)])
 def test_leading_colour_matches_the_oracle(env, oracle_processes, name, n):
     # the diagonal of the colour matrix in the colour-flow (string) basis, on
     # both sides; turning it off restores the full colour sum

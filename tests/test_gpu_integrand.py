@@ -154,3 +154,29 @@ def test_helicity_filtering(torch_cuda, gpu_process, oracle_integrand):
         got = gpu_process(name).helicities()
         ref = np.array(oracle_integrand(name).nonzero_helicities(), dtype=np.int8)
         assert np.array_equal(got, ref), name
+
+
+def test_fp64_error_budget(torch_cuda, gpu_process, oracle_integrand, capsys):
+    # how the FP64 errors sit against the bare 1e-12: over every workload,
+    # the share of points above it and the condition number of the worst
+    # point, which must lie within its own bound
+    rows, total, above = [], 0, 0
+    for name, n in CASES:
+        wl = W.WORKLOADS[name]
+        x = W.uniform_points(wl.ndim, n, 101)
+        got = _eval(torch_cuda, gpu_process(name), x, "fp64")
+        ref, tol = fp64_tolerance(oracle_integrand(name), x)
+        _, parts = oracle_integrand(name)(x, return_parts=True)
+        nz = ref != 0
+        r = relerr(got, ref)[nz]
+        k = parts["condition"][nz]
+        total += nz.sum()
+        above += int((r > 1e-12).sum())
+        i = int(np.argmax(r))
+        rows.append((name, int(nz.sum()), int((r > 1e-12).sum()), float(r[i]), float(k[i]),
+                     float(np.median(r))))
+        assert r[i] <= tol[nz][i]
+    with capsys.disabled():
+        for row in rows:
+            print("fp64 %-9s points %5d above 1e-12 %4d worst %.2e (condition %.3g) median %.1e" % row)
+    assert above <= 0.05 * total, (above, total)
