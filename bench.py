@@ -36,7 +36,7 @@ KERNEL_DRAM_BYTES_PER_POINT = {("gg_ttxgg", "mixed"): (144.32e6 + 22.65e9) / 4e7
 WORKLOAD = "gg_ttxgg"
 # FP64 FLOPs per point executed by the gradient kernel (2 x DFMA + DADD +
 # DMUL thread instructions of one ncu capture divided by its points)
-GRAD_FP64_FLOPS_PER_POINT = {}
+GRAD_FP64_FLOPS_PER_POINT = {"gg_ttxgg": (2 * 53663185372 + 39529294092 + 38450987098) / 20000}
 
 
 def _args():

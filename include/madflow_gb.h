@@ -442,7 +442,9 @@ mf_status mf_batch_iterate_graph(mf_batch *b, mf_vegas *const *grids, const int6
  * and starts a writer thread; events handed to it are formatted and written
  * while the caller's GPU work goes on.  mf_lhe_close drains the queue, ends
  * the file, joins the thread and frees the writer (*n_written, may be NULL:
- * the number of events written).  Colour tags are not assigned (0). */
+ * the number of events written).  Each event's colour and anticolour tags
+ * (ICOLUP) are those of its colour flow (record field 3) in the table
+ * colour_tags; an event whose flow is -1 or outside the table gets 0. */
 typedef struct mf_lhe_writer mf_lhe_writer;
 typedef struct {
     int32_t n_legs;                /* particles per event, incoming first */
@@ -455,10 +457,16 @@ typedef struct {
     int32_t process_id;
     double scale;                  /* event scale (GeV) */
     double alpha_qed, alpha_s;
+    int32_t n_flows;               /* colour flows in colour_tags (0: no tags) */
+    int32_t pad;
+    const int32_t *colour_tags;    /* host [n_flows][n_legs][2]: per colour flow of the process (the
+                                    * descriptor's colour-basis order) and leg, the LHE colour and
+                                    * anticolour line numbers (0: none); copied at open */
 } mf_lhe_init;
 mf_status mf_lhe_open(const char *path, const mf_lhe_init *init, mf_lhe_writer **out);
-/* Queue n events given as host records (3 + 4 n_legs doubles each: weight,
- * x1, x2, then per leg E, px, py, pz); the data are copied. */
+/* Queue n events given as host records (4 + 4 n_legs doubles each: weight,
+ * x1, x2, colour-flow index (-1: none), then per leg E, px, py, pz); the
+ * data are copied. */
 mf_status mf_lhe_write(mf_lhe_writer *w, const double *records, int64_t n);
 mf_status mf_lhe_close(mf_lhe_writer *w, int64_t *n_written);
 
@@ -506,11 +514,16 @@ mf_status mf_vegas_observables(mf_vegas *v, mf_process *p, int64_t n_events, uin
  * |w_i| > u_i w_max, u_i the first unit number of Philox counter
  * (i, iteration, subprocess, 15).  A kept point becomes an event of weight
  * sign(w_i) max(|w_i|, w_max) / n_events (pb), so the events' weights add up
- * to the integral estimate.  Records (host [capacity][3 + 4 n_legs], may be
- * NULL): event weight, x1, x2, then per leg (E, px, py, pz) in the collider
- * frame, in point order; at most capacity are written, *n_accepted receives
- * the number kept.  With lhe != NULL the events also go to that writer.
- * Synchronous. */
+ * to the integral estimate.  Each kept event also gets a colour flow k of
+ * the process's colour basis, drawn with probability proportional to its
+ * leading-colour weight sum_h C_kk |J_k,h|^2 (the helicity sum of the flow's
+ * diagonal colour-matrix term, Sec. 2.5's colour assignment of events) by
+ * the first unit number of Philox counter (i, iteration, subprocess, 13);
+ * the LHE writer turns it into colour tags.  Records (host
+ * [capacity][4 + 4 n_legs], may be NULL): event weight, x1, x2, colour-flow
+ * index, then per leg (E, px, py, pz) in the collider frame, in point order;
+ * at most capacity are written, *n_accepted receives the number kept.  With
+ * lhe != NULL the events also go to that writer.  Synchronous. */
 mf_status mf_vegas_unweight(mf_vegas *v, mf_process *p, int64_t n_events, uint64_t seed, int32_t subprocess,
                             mf_precision prec, double w_max, mf_lhe_writer *lhe, double *records, int64_t capacity,
                             int64_t *n_accepted, void *stream);

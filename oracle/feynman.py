@@ -410,6 +410,40 @@ class Process:
         self._B = np.stack(basis, axis=1) if basis else np.ones((1, 1))
         return self._B
 
+    def string_labels(self):
+        """The strings of string_basis in its order: per basis element a tuple
+        of (row leg, column leg, gluon legs in order along the string) per
+        quark line."""
+        rows, cols, gluons = [], [], []
+        for i, (part, inc) in enumerate(self.legs):
+            kind, flav, _ = PARTICLES[part]
+            if COLOUR_DIM[flav] == 8:
+                gluons.append(i)
+            elif COLOUR_DIM[flav] == 3:
+                (rows if self.lines[i][2] == "out" else cols).append(i)
+        out = []
+        for perm in itertools.permutations(cols):
+            for assign in itertools.product(range(len(rows)), repeat=len(gluons)):
+                groups = [[g for g, s in zip(gluons, assign) if s == k] for k in range(len(rows))]
+                for orders in itertools.product(*[list(itertools.permutations(gr)) for gr in groups]):
+                    out.append(tuple((rows[k], perm[k], tuple(orders[k])) for k in range(len(rows))))
+        return out if out else [()]
+
+    def leading_colour_weights(self, p):
+        """Per point and string, sum over helicities of G_ss |A_s|^2 (the
+        terms of msq_leading_colour), [N, basis]."""
+        p = np.asarray(p, dtype=np.float64)
+        B = self.string_basis()
+        C = self.colour_tensors()
+        P = np.linalg.pinv(B) @ C
+        norms = np.real(np.sum(np.conj(B) * B, axis=0))
+        cache = {}
+        tot = np.zeros((B.shape[1], p.shape[0]))
+        for hel in self.helicities():
+            A = P @ self.amplitudes(p, hel, cache)
+            tot += norms[:, None] * np.abs(A) ** 2
+        return tot.T
+
     def msq_leading_colour(self, p):
         """sum over helicities of sum_s G_ss |A_s|^2 (no averaging), with A the
         exact coefficients of the colour-dressed amplitude in the string basis

@@ -78,7 +78,7 @@ class mf_lhe_init(C.Structure):
     _fields_ = [("n_legs", c_i32), ("pdg", c_i32 * 8), ("mass", C.c_double * 8), ("beam_pdg", c_i32 * 2),
                 ("beam_energy", C.c_double * 2), ("xsec", C.c_double), ("xsec_error", C.c_double),
                 ("w_max", C.c_double), ("process_id", c_i32), ("scale", C.c_double), ("alpha_qed", C.c_double),
-                ("alpha_s", C.c_double)]
+                ("alpha_s", C.c_double), ("n_flows", c_i32), ("pad", c_i32), ("colour_tags", P(c_i32))]
 
 
 class mf_iter_result(C.Structure):

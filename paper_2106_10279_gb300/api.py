@@ -532,7 +532,10 @@ class LheWriter:
     """An LHE 3.0 file written by a background thread (see mf_lhe_open)."""
 
     def __init__(self, path, pdg, masses, beam_pdg=(2212, 2212), beam_energy=(6500.0, 6500.0), xsec=0.0,
-                 xsec_error=0.0, w_max=0.0, process_id=1, scale=173.0, alpha_qed=1 / 128, alpha_s=0.118):
+                 xsec_error=0.0, w_max=0.0, process_id=1, scale=173.0, alpha_qed=1 / 128, alpha_s=0.118,
+                 colour_tags=None):
+        """colour_tags: [n_flows, n_legs, 2] LHE colour/anticolour tags per
+        colour flow (process.lhe_colour_tags), or None (tags 0)."""
         init = L.mf_lhe_init()
         init.n_legs = len(pdg)
         for i, (p, m) in enumerate(zip(pdg, masses)):
@@ -542,13 +545,17 @@ class LheWriter:
         init.beam_energy[:] = list(beam_energy)
         init.xsec, init.xsec_error, init.w_max = xsec, xsec_error, w_max
         init.process_id, init.scale, init.alpha_qed, init.alpha_s = process_id, scale, alpha_qed, alpha_s
+        if colour_tags is not None:
+            t = np.ascontiguousarray(colour_tags, dtype=np.int32).reshape(-1, len(pdg), 2)
+            init.n_flows = t.shape[0]
+            init.colour_tags = t.ctypes.data_as(C.POINTER(C.c_int32))
         h = C.c_void_p()
         L.check(L.lib().mf_lhe_open(str(path).encode(), C.byref(init), C.byref(h)), "mf_lhe_open")
         self.handle = h
         self.n_legs = len(pdg)
 
     def write(self, records):
-        r = np.ascontiguousarray(records, dtype=np.float64).reshape(-1, 3 + 4 * self.n_legs)
+        r = np.ascontiguousarray(records, dtype=np.float64).reshape(-1, 4 + 4 * self.n_legs)
         L.check(L.lib().mf_lhe_write(self.handle, r.ctypes.data_as(C.POINTER(C.c_double)), r.shape[0]),
                 "mf_lhe_write")
 
@@ -569,10 +576,11 @@ class LheWriter:
 def unweight(grid: "Vegas", proc: "Process", n_events: int, seed: int, w_max: float, precision="mixed",
              subprocess=0, lhe: LheWriter = None, capacity=None, stream=None):
     """Hit-or-miss unweighted events of one pass (see mf_vegas_unweight):
-    (number kept, records [min(kept, capacity), 3 + 4 n_legs])."""
+    (number kept, records [min(kept, capacity), 4 + 4 n_legs]: event
+    weight, x1, x2, colour-flow index, momenta)."""
     nl = proc.info["n_legs"]
     cap = n_events if capacity is None else capacity
-    rec = np.zeros((max(cap, 0), 3 + 4 * nl))
+    rec = np.zeros((max(cap, 0), 4 + 4 * nl))
     nacc = C.c_int64()
     st = L.lib().mf_vegas_unweight(grid.handle, proc.handle, n_events, seed, subprocess, _PREC[precision], w_max,
                                    lhe.handle if lhe else None, rec.ctypes.data_as(C.POINTER(C.c_double)), cap,

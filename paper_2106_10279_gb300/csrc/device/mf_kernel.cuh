@@ -147,13 +147,14 @@ constexpr size_t tile_smem_bytes() {
            (BLOCK / 32 + 1) * 4;
 }
 
-// Per-block constants of a process: the Vegas grid (mode 1) and the
-// couplings and masses in the matrix-element precision.
+// Per-block constants of a process: the Vegas grid (the modes that map
+// Philox points through it: 1, 3, 4 and 5) and the couplings and masses in
+// the matrix-element precision.
 template <typename R, int BLOCK>
 MF_DEV void load_block_constants(const KParams &kp, double *s_grid, cx<R> *cpl, R *mass_r) {
     using namespace MF_PROC;
     const int tid = threadIdx.x;
-    if (kp.mode == 1 || kp.mode == 3) {
+    if (kp.mode == 1 || kp.mode == 3 || kp.mode == 4 || kp.mode == 5) {
         for (int i = tid; i < NDIM * (kp.nb + 1); i += BLOCK) s_grid[i] = kp.grid[i];
     }
     if (tid < 8) {
@@ -190,8 +191,10 @@ MF_DEV bool sample_pairs(const KParams &kp) {
 
 // One tile of BLOCK events: phases A, B and C.  Ends with a block barrier.
 // With TC the colour sum of phase B runs on the tensor cores (R = float,
-// BLOCK = 128, tcs set up by the caller).
-template <typename R, int BLOCK, int HT, bool TC = false>
+// BLOCK = 128, tcs set up by the caller).  With FLOW (a kernel of its own,
+// so that the integrand kernel carries none of its code) phase B is
+// replaced by the leading-colour flow draw of mode 5.
+template <typename R, int BLOCK, int HT, bool TC = false, bool FLOW = false>
 MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem_raw, const double *s_grid,
                       const cx<R> *cpl, const R *mass_r, tc::State *tcs = nullptr) {
     using namespace MF_PROC;
@@ -215,14 +218,14 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
         if (e < kp.n) {
             // ---------------- phase A: kinematics in double precision
             double y[NDIM];
-            if (kp.mode != 1 && kp.mode != 3 && kp.mode != 4) {
+            if (kp.mode != 1 && kp.mode != 3 && kp.mode != 4 && kp.mode != 5) {
 #pragma unroll
                 for (int j = 0; j < NDIM; ++j) {
                     y[j] = kp.x[(int64_t)j * kp.n + e];
                     finite_in &= isfinite(y[j]);
                 }
             } else {
-                const uint64_t gi = kp.mode == 3 ? (uint64_t)kp.idx[e] : (uint64_t)(e + kp.ev0);
+                const uint64_t gi = (kp.mode == 3 || kp.mode == 5) ? (uint64_t)kp.idx[e] : (uint64_t)(e + kp.ev0);
 #pragma unroll
                 for (int b = 0; b < (NDIM + 3) / 4; ++b) {
                     uint64_t c[4] = {gi, iteration, kp.subprocess, (uint64_t)b};
@@ -317,8 +320,68 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
         if (ok) s_list[s_warp[warp] + __popc(bal & ((1u << lane32) - 1u))] = tid;
         const int npass = s_warp[BLOCK / 32];
         __syncthreads();
+        // ---------------- phase B': the leading-colour flow of an event
+        // (mode 5): per flow k the helicity sum of C_kk |J_k|^2 (the lanes'
+        // helicities, then a butterfly over the HT lanes), and a flow drawn
+        // with probability proportional to it by the first unit number of
+        // Philox counter (point, iteration, subprocess, 13)
+        if constexpr (FLOW) {
+            const int EPR = BLOCK / HT, sub = tid % HT;
+            const int nhp = kp.nhel_pow2;
+            const int per = nhp >= HT ? nhp / HT : 1;
+            for (int base = 0; base < npass; base += EPR) {
+                const int slot = base + tid / HT;
+                const bool valid = slot < npass;
+                const int ev = s_list[valid ? slot : 0];
+                const R *ms = s_mom + ev * NLEG * 4;
+                const R *idn = s_den + ev * NDEN1;
+                double wk[NJAMP];
+#pragma unroll
+                for (int k = 0; k < NJAMP; ++k) wk[k] = 0.0;
+                for (int q = 0; q < per; ++q) {
+                    const int h = sub * per + q;
+                    const bool hv = h < kp.nhel;
+                    cx<R> J[NJAMP];
+                    helicity_jamp<R>(ms, idn, kp.hel[hv ? h : 0], cpl, mass_r, J);
+                    if (hv && valid) {
+#pragma unroll
+                        for (int k = 0; k < NJAMP; ++k)
+                            wk[k] += (double)COLOUR_NUM[k * NJAMP + k] *
+                                     ((double)J[k].re * (double)J[k].re + (double)J[k].im * (double)J[k].im);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < NJAMP; ++k)
+#pragma unroll
+                    for (int off = 1; off < HT; off <<= 1) {
+                        const double o = __shfl_xor_sync(0xffffffffu, wk[k], off);
+                        wk[k] = (sub & off) ? (o + wk[k]) : (wk[k] + o);
+                    }
+                if (sub == 0 && valid) {
+                    const int64_t pe = tile * BLOCK + ev;
+                    uint64_t c[4] = {(uint64_t)kp.idx[pe], iteration, kp.subprocess, 13ull};
+                    philox4x64_10(c, kp.seed, 0ull);
+                    double tot = 0.0;
+#pragma unroll
+                    for (int k = 0; k < NJAMP; ++k) tot += wk[k];
+                    const double target = unit_from_bits(c[0]) * tot;
+                    int pick = -1;
+                    double cum = 0.0;
+#pragma unroll
+                    for (int k = 0; k < NJAMP; ++k) {
+                        cum += wk[k];
+                        if (pick < 0 && wk[k] > 0.0 && target < cum) pick = k;
+                    }
+                    if (pick < 0 && tot > 0.0) {     // target rounded onto the total
+                        for (int k = NJAMP - 1; k >= 0 && pick < 0; --k)
+                            if (wk[k] > 0.0) pick = k;
+                    }
+                    kp.flow_out[pe] = pick;
+                }
+            }
+        }
         // ---------------- phase B: helicity amplitudes, HT lanes per event
-        {
+        if constexpr (!FLOW) {
             // HT lanes per point, each running the program for a contiguous
             // block of helicities; with helicity sampling one lane per point
             // and its sampled helicity (one call site of the program either way)
@@ -418,8 +481,9 @@ MF_DEV bool smem_ok(const KParams &kp, size_t need) {
     return false;
 }
 
-// The single-process kernel: a grid-stride loop over tiles.
-template <typename R, int BLOCK, int HT>
+// The single-process kernel: a grid-stride loop over tiles (FLOW: the
+// leading-colour flow kernel of mode 5).
+template <typename R, int BLOCK, int HT, bool FLOW = false>
 MF_DEV void kernel_body(const KParams &kp) {
     using namespace MF_PROC;
     if (!smem_ok(kp, tile_smem_bytes<R, BLOCK>())) return;
@@ -431,7 +495,7 @@ MF_DEV void kernel_body(const KParams &kp) {
     __syncthreads();
     const int64_t ntiles = (kp.n + BLOCK - 1) / BLOCK;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
-        tile_body<R, BLOCK, HT>(kp, tile, smem_raw, s_grid, cpl, mass_r);
+        tile_body<R, BLOCK, HT, false, FLOW>(kp, tile, smem_raw, s_grid, cpl, mass_r);
 }
 
 // The single-process kernel with the colour sum on the tensor cores

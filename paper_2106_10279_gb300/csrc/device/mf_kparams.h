@@ -12,7 +12,9 @@ struct mf_kparams {
                                // 2: per-helicity |M|^2 of given points into f[h][n],
                                // 3: event records of the Vegas points idx[0..n) into
                                //    f[n][2 + 4 NLEG] (x1, x2, lab-frame momenta),
-                               // 4: observable bins of the Vegas points into obs_out
+                               // 4: observable bins of the Vegas points into obs_out,
+                               // 5: leading-colour flow drawn for the Vegas points
+                               //    idx[0..n) into flow_out
     int32_t nhel;              // helicity rows in hel[]
     int32_t nhel_pow2;         // a power of two >= nhel (pairwise-sum padding)
     int32_t nb;                // Vegas bins per dimension
@@ -46,6 +48,7 @@ struct mf_kparams {
     int64_t wait_polls;        // polls of a bounded wait per tensor-core colour-sum round
     const long long *iter_dev; // if set, the iteration index is read here (graph replays)
     uint16_t *obs_out;         // mode 4: bins [n_obs][n], 0xFFFF: not binned
+    int32_t *flow_out;         // mode 5: colour-flow index [n], -1: none
     int32_t n_obs;             // mode 4: observables
     int32_t obs_kind[MF_KP_MAX_OBS];   // 0: pT, 1: rapidity, 2: pseudorapidity (collider frame)
     int32_t obs_leg[MF_KP_MAX_OBS];

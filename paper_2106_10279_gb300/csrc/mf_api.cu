@@ -723,7 +723,7 @@ mf_status launch(mf_process *p, int prec, mf_kparams &kp, cudaStream_t s) {
     if (grid > ntiles) grid = ntiles;
     if (grid < 1) grid = 1;
     void *args[] = {&kp};
-    return mfi::launch_kernel(k, (unsigned)grid, args, s);
+    return mfi::launch_kernel(k, (unsigned)grid, args, s, kp.mode == 5);
 }
 
 // Ranges of the process options (MF_OPT_AUTO allowed everywhere).
@@ -1845,8 +1845,17 @@ extern "C" mf_status mf_batch_create(mf_process *const *procs, int32_t nproc, mf
     }
     std::vector<mfi::GenInfo> infos;
     b->source = mfi::generate_batch_source(ps, prec, 128, hs, infos);
+    // the batch holds the same programs: it is built at the lowest
+    // device-assembler level any of its processes' kernels needed (see
+    // verify_pairs)
+    int level = -1;
+    for (int k = 0; k < nproc; ++k) {
+        const int lk = procs[k]->kern[prec].ptxas_level;
+        if (lk >= 0 && (level < 0 || lk < level)) level = lk;
+    }
     std::vector<char> cubin;
-    mf_status st = mfi::jit_compile(b->source, prec == MF_FP64 ? "mf_batch_f64.cu" : "mf_batch_mixed.cu", cubin);
+    mf_status st = mfi::jit_compile(b->source, prec == MF_FP64 ? "mf_batch_f64.cu" : "mf_batch_mixed.cu", cubin,
+                                    level);
     if (st == MF_OK) {
         b->kern.block = 128;
         b->kern.smem = smem;
@@ -2440,6 +2449,7 @@ extern "C" mf_status mf_vegas_unweight(mf_vegas *v, mf_process *p, int64_t n_eve
     int *d_cnt = nullptr;
     int64_t *d_off = nullptr, *d_idx = nullptr;
     double *d_wk = nullptr, *d_rec = nullptr;
+    int32_t *d_flow = nullptr;
     std::vector<int> cnt(nchunks);
     std::vector<int64_t> off(nchunks);
     int64_t nacc = 0;
@@ -2451,6 +2461,7 @@ extern "C" mf_status mf_vegas_unweight(mf_vegas *v, mf_process *p, int64_t n_eve
         cudaFree(d_idx);
         cudaFree(d_wk);
         cudaFree(d_rec);
+        cudaFree(d_flow);
     };
 #define MF_UW(call)                                                                            \
     do {                                                                                       \
@@ -2485,6 +2496,7 @@ extern "C" mf_status mf_vegas_unweight(mf_vegas *v, mf_process *p, int64_t n_eve
         MF_UW(mfi::dev_malloc(&d_idx, sizeof(int64_t) * nacc));
         MF_UW(mfi::dev_malloc(&d_wk, sizeof(double) * nacc));
         MF_UW(mfi::dev_malloc(&d_rec, sizeof(double) * RW * nacc));
+        MF_UW(mfi::dev_malloc(&d_flow, sizeof(int32_t) * nacc));
         unweight_compact_kernel<<<(unsigned)nchunks, kUwThreads, 0, s>>>(d_acc, p->d_w, n, d_off, d_idx, d_wk);
         MF_UW(cudaGetLastError());
         // the kept points' kinematics, recomputed from their Philox counters
@@ -2498,17 +2510,38 @@ extern "C" mf_status mf_vegas_unweight(mf_vegas *v, mf_process *p, int64_t n_eve
             cleanup();
             return st;
         }
+        // their leading-colour flows (the full helicity sum per flow; no
+        // helicity sampling), drawn on the device
+        mf_kparams kc;
+        vegas_params(p, v, nacc, 0, subprocess, seed, kc);
+        kc.mode = 5;
+        kc.hel_sample = 0;
+        kc.idx = d_idx;
+        kc.flow_out = d_flow;
+        st = launch(p, prec, kc, s);
+        if (st != MF_OK) {
+            cleanup();
+            return st;
+        }
         std::vector<double> wk(nacc), rec((size_t)RW * nacc);
+        std::vector<int32_t> flow(nacc);
         MF_UW(cudaMemcpyAsync(wk.data(), d_wk, sizeof(double) * nacc, cudaMemcpyDeviceToHost, s));
         MF_UW(cudaMemcpyAsync(rec.data(), d_rec, sizeof(double) * RW * nacc, cudaMemcpyDeviceToHost, s));
+        MF_UW(cudaMemcpyAsync(flow.data(), d_flow, sizeof(int32_t) * nacc, cudaMemcpyDeviceToHost, s));
         MF_UW(cudaStreamSynchronize(s));
-        const int OW = RW + 1;
+        // record: event weight, x1, x2, colour flow, momenta
+        const int OW = RW + 2;
         std::vector<double> out((size_t)OW * nacc);
         for (int64_t k = 0; k < nacc; ++k) {
             const double w = wk[k];
             const double ew = (w < 0.0 ? -1.0 : 1.0) * std::max(std::fabs(w), w_max) / (double)n;
-            out[(size_t)k * OW] = ew;
-            std::copy(rec.begin() + (size_t)k * RW, rec.begin() + (size_t)(k + 1) * RW, out.begin() + (size_t)k * OW + 1);
+            double *o = out.data() + (size_t)k * OW;
+            const double *r = rec.data() + (size_t)k * RW;
+            o[0] = ew;
+            o[1] = r[0];
+            o[2] = r[1];
+            o[3] = (double)flow[k];
+            std::copy(r + 2, r + RW, o + 4);
         }
         if (capacity > 0)
             std::copy(out.begin(), out.begin() + (size_t)OW * std::min(capacity, nacc), records);

@@ -726,6 +726,10 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
         o << ") mf_kernel(const mf::KParams kp) {\n";
         if (precision == MF_MIXED_TC) o << "  mf::kernel_body_tc<" << ht << ">(kp);\n}\n";
         else o << "  mf::kernel_body<" << R << ", " << block << ", " << ht << ">(kp);\n}\n";
+        // the leading-colour flow kernel (mode 5) of the same programs
+        const int fblock = precision == MF_MIXED_TC ? 128 : block;
+        o << "extern \"C\" __global__ void __launch_bounds__(" << fblock << ") mf_flow_kernel(const mf::KParams kp) {\n"
+          << "  mf::kernel_body<" << R << ", " << fblock << ", " << ht << ", true>(kp);\n}\n";
     }
     // algorithmic count of the programs as emitted: every wavefunction once
     // (the few a later program part recomputes are not counted), per

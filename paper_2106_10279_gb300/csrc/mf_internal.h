@@ -38,6 +38,7 @@ struct DenSlot {
 struct Compiled {
     CUmodule module = nullptr;
     CUfunction fn = nullptr;
+    CUfunction fn_flow = nullptr;  // the module's leading-colour flow kernel (mode 5), if any
     int block = 128;
     int ht = 32;
     size_t smem = 0;
@@ -174,5 +175,5 @@ mf_status jit_compile(const std::string &source, const std::string &name, std::v
                       int ptxas_level = -1);
 mf_status load_kernel(const std::vector<char> &cubin, Compiled &out, const char *name = "mf_kernel");
 void unload_kernel(Compiled &k);
-mf_status launch_kernel(const Compiled &k, unsigned grid, void **args, cudaStream_t s);
+mf_status launch_kernel(const Compiled &k, unsigned grid, void **args, cudaStream_t s, bool flow = false);
 }  // namespace mfi

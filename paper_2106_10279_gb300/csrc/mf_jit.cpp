@@ -206,6 +206,10 @@ mf_status load_kernel(const std::vector<char> &cubin, Compiled &out, const char 
     if (r != CUDA_SUCCESS) return fail(MF_ECUDA, "cuModuleLoadData: " + drv_err(r));
     r = g_drv.moduleGetFunction(&out.fn, out.module, name);
     if (r != CUDA_SUCCESS) return fail(MF_ECUDA, "cuModuleGetFunction: " + drv_err(r));
+    // the flow kernel of a process module (absent in other modules)
+    if (g_drv.moduleGetFunction(&out.fn_flow, out.module, "mf_flow_kernel") != CUDA_SUCCESS) out.fn_flow = nullptr;
+    if (out.fn_flow && out.smem > 48 * 1024)
+        g_drv.funcSetAttribute(out.fn_flow, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)out.smem);
     int regs = 0, local = 0;
     g_drv.funcGetAttribute(&regs, CU_FUNC_ATTRIBUTE_NUM_REGS, out.fn);
     g_drv.funcGetAttribute(&local, CU_FUNC_ATTRIBUTE_LOCAL_SIZE_BYTES, out.fn);
@@ -240,10 +244,13 @@ void unload_kernel(Compiled &k) {
     if (k.module && g_drv.ok) g_drv.moduleUnload(k.module);
     k.module = nullptr;
     k.fn = nullptr;
+    k.fn_flow = nullptr;
 }
 
-mf_status launch_kernel(const Compiled &k, unsigned grid, void **args, cudaStream_t s) {
-    CUresult r = g_drv.launch(k.fn, grid, 1, 1, (unsigned)k.block, 1, 1, (unsigned)k.smem, (CUstream)s, args, nullptr);
+mf_status launch_kernel(const Compiled &k, unsigned grid, void **args, cudaStream_t s, bool flow) {
+    if (flow && !k.fn_flow) return fail(MF_EUNSUPPORTED, "the module has no flow kernel");
+    CUresult r = g_drv.launch(flow ? k.fn_flow : k.fn, grid, 1, 1, (unsigned)k.block, 1, 1, (unsigned)k.smem,
+                              (CUstream)s, args, nullptr);
     if (r != CUDA_SUCCESS) return fail(MF_ECUDA, "process kernel launch: " + drv_err(r));
     return MF_OK;
 }

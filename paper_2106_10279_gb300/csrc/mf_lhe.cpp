@@ -20,7 +20,8 @@ struct mf_lhe_writer {
     std::thread th;
     std::mutex mu;
     std::condition_variable cv;
-    std::deque<std::vector<double>> q;      // batches of records [n][3 + 4 n_legs]
+    std::deque<std::vector<double>> q;      // batches of records [n][4 + 4 n_legs]
+    std::vector<int32_t> tags;              // [n_flows][n_legs][2] colour, anticolour
     bool closing = false;
     bool io_error = false;
     int64_t written = 0;
@@ -28,26 +29,32 @@ struct mf_lhe_writer {
 
 namespace {
 
-// One event: weight, then per leg PDG id, status, mothers, colour (unassigned),
-// momentum (px, py, pz, E), mass, lifetime, spin (unknown).
+// One event: weight, then per leg PDG id, status, mothers, colour and
+// anticolour tags of the event's colour flow (0 where the flow index is
+// outside the table), momentum (px, py, pz, E), mass, lifetime, spin
+// (unknown).
 void write_event(mf_lhe_writer *w, const double *rec) {
     const mf_lhe_init &in = w->init;
     const int n = in.n_legs;
     std::FILE *f = w->f;
+    const int flow = (int)rec[3];
+    const int32_t *tag = (flow >= 0 && flow < in.n_flows && !w->tags.empty())
+                             ? w->tags.data() + (size_t)flow * n * 2 : nullptr;
     std::fprintf(f, "<event>\n%d %d %.10e %.8e %.8e %.8e\n", n, in.process_id, rec[0], in.scale, in.alpha_qed,
                  in.alpha_s);
     for (int i = 0; i < n; ++i) {
-        const double *p = rec + 3 + 4 * i;
+        const double *p = rec + 4 + 4 * i;
         const int incoming = i < 2;
         const double m = in.mass[i];
         std::fprintf(f, " %8d %2d %4d %4d %4d %4d %+.12e %+.12e %+.12e %.12e %.8e %.1f %.1f\n", in.pdg[i],
-                     incoming ? -1 : 1, incoming ? 0 : 1, incoming ? 0 : 2, 0, 0, p[1], p[2], p[3], p[0], m, 0.0, 9.0);
+                     incoming ? -1 : 1, incoming ? 0 : 1, incoming ? 0 : 2, tag ? tag[2 * i] : 0,
+                     tag ? tag[2 * i + 1] : 0, p[1], p[2], p[3], p[0], m, 0.0, 9.0);
     }
     std::fprintf(f, "</event>\n");
 }
 
 void run(mf_lhe_writer *w) {
-    const int rec = 3 + 4 * w->init.n_legs;
+    const int rec = 4 + 4 * w->init.n_legs;
     for (;;) {
         std::vector<double> batch;
         {
@@ -70,7 +77,7 @@ void run(mf_lhe_writer *w) {
 }  // namespace
 
 namespace mfi {
-// Hand a batch of records (3 + 4 n_legs doubles each) to the writer thread.
+// Hand a batch of records (4 + 4 n_legs doubles each) to the writer thread.
 mf_status lhe_push(mf_lhe_writer *w, std::vector<double> &&records) {
     if (records.empty()) return MF_OK;
     std::lock_guard<std::mutex> lock(w->mu);
@@ -87,6 +94,7 @@ extern "C" mf_status mf_lhe_open(const char *path, const mf_lhe_init *init, mf_l
     *out = nullptr;
     if (!path || !init) return fail(MF_EINVAL, "NULL argument");
     if (init->n_legs < 3 || init->n_legs > MF_MAX_LEGS) return fail(MF_EINVAL, "n_legs out of range");
+    if (init->n_flows < 0 || (init->n_flows > 0 && !init->colour_tags)) return fail(MF_EINVAL, "bad colour tags");
     std::FILE *f = std::fopen(path, "w");
     if (!f) return fail(MF_EINVAL, std::string("cannot open ") + path);
     mf_lhe_writer *w = new (std::nothrow) mf_lhe_writer();
@@ -96,6 +104,9 @@ extern "C" mf_status mf_lhe_open(const char *path, const mf_lhe_init *init, mf_l
     }
     w->f = f;
     w->init = *init;
+    if (init->n_flows > 0)
+        w->tags.assign(init->colour_tags, init->colour_tags + (size_t)init->n_flows * init->n_legs * 2);
+    w->init.colour_tags = nullptr;            // the copy above is used
     // header and the <init> block: beams, PDF sets (none: -1), weighting
     // strategy 3 (unweighted), one process with its cross section
     std::fprintf(f, "<LesHouchesEvents version=\"3.0\">\n<header>\n<generator name=\"madflow-gb300\" />\n</header>\n");
@@ -109,7 +120,7 @@ extern "C" mf_status mf_lhe_open(const char *path, const mf_lhe_init *init, mf_l
 
 extern "C" mf_status mf_lhe_write(mf_lhe_writer *w, const double *records, int64_t n) {
     if (!w || (n > 0 && !records) || n < 0) return fail(MF_EINVAL, "bad arguments");
-    const size_t rec = 3 + 4 * (size_t)w->init.n_legs;
+    const size_t rec = 4 + 4 * (size_t)w->init.n_legs;
     return mfi::lhe_push(w, std::vector<double>(records, records + rec * (size_t)n));
 }
 

@@ -441,5 +441,35 @@ def build_program(name, legs, masses, alpha_s, alpha):
                           n_diagrams, avg, k_as, labels)
 
 
+def lhe_colour_tags(prog: ProcessProgram) -> np.ndarray:
+    """Les Houches colour and anticolour tags of every colour flow of the
+    program, [n_flows, n_legs, 2] (the flow order of the colour basis).
+
+    A flow is a product of open strings (t^g1 ... t^gk)_{row, column}.  Along
+    a string the colour line of the row quark (an outgoing quark, or an
+    incoming antiquark) passes each gluon in turn -- the gluon absorbs it as
+    its anticolour and emits a new line as its colour -- and ends as the
+    anticolour of the column quark (an outgoing antiquark or an incoming
+    quark); these are the all-outgoing assignments, and an incoming particle
+    carries them swapped.  Lines are numbered from 501."""
+    n = len(prog.legs)
+    tags = np.zeros((len(prog.basis_labels), n, 2), dtype=np.int32)
+    for k, label in enumerate(prog.basis_labels):
+        line = 500
+        c = {}
+        for row, col, gluons in label:
+            line += 1
+            c[(row, 0)] = line
+            for g in gluons:
+                c[(g, 1)] = line
+                line += 1
+                c[(g, 0)] = line
+            c[(col, 1)] = line
+        for i, (_, incoming) in enumerate(prog.legs):
+            colour, anticolour = c.get((i, 0), 0), c.get((i, 1), 0)
+            tags[k, i] = (anticolour, colour) if incoming else (colour, anticolour)
+    return tags
+
+
 def helicity_table(n_legs):
     return [list(h) for h in itertools.product((-1, 1), repeat=n_legs)]

@@ -32,8 +32,12 @@ def test_events_round_trip(api, tmp_path):
     pdg = [21, 21, 6, -6, 21]
     masses = [0.0, 0.0, 173.0, 173.0, 0.0]
     path = tmp_path / "ev.lhe"
-    w = api.LheWriter(path, pdg, masses, xsec=1101.2, xsec_error=0.5, w_max=3.0e-3, scale=173.0)
-    batches = [rng.normal(size=(n, 3 + 4 * 5)) for n in (7, 0, 13, 1)]
+    tags = rng.integers(0, 600, size=(6, 5, 2)).astype(np.int32)
+    w = api.LheWriter(path, pdg, masses, xsec=1101.2, xsec_error=0.5, w_max=3.0e-3, scale=173.0,
+                      colour_tags=tags)
+    batches = [rng.normal(size=(n, 4 + 4 * 5)) for n in (7, 0, 13, 1)]
+    for b in batches:
+        b[:, 3] = rng.integers(-1, 8, size=b.shape[0])       # flow index; -1 and 6, 7: outside the table
     for b in batches:
         w.write(b)
     assert w.close() == 21
@@ -45,11 +49,14 @@ def test_events_round_trip(api, tmp_path):
     assert len(events) == rec.shape[0]
     for r, (head, parts) in zip(rec, events):
         assert int(head[0]) == 5 and float(head[2]) == pytest.approx(r[0], rel=1e-10)
+        flow = int(r[3])
         for i, row in enumerate(parts):
             assert int(row[0]) == pdg[i]
             assert int(row[1]) == (-1 if i < 2 else 1)
+            want = tuple(tags[flow, i]) if 0 <= flow < tags.shape[0] else (0, 0)
+            assert (int(row[4]), int(row[5])) == want
             px, py, pz, e, m = map(float, row[6:11])
-            assert np.allclose([e, px, py, pz], r[3 + 4 * i:7 + 4 * i], rtol=1e-11, atol=0)
+            assert np.allclose([e, px, py, pz], r[4 + 4 * i:8 + 4 * i], rtol=1e-11, atol=0)
             assert m == masses[i]
 
 

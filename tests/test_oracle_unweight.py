@@ -2,6 +2,7 @@
 import numpy as np
 import pytest
 
+import workloads as W
 from oracle import unweight as uw
 from oracle.philox import vegas_uniforms
 
@@ -58,3 +59,68 @@ def test_lab_frame_boost():
     m2 = lambda a: np.einsum("nm,m,nm->n", a, MDOT, a)
     assert np.allclose(m2(q[:, 2]), m2(p[:, 2]), rtol=1e-10, atol=1e-8)
     assert np.array_equal(q[:, :, 1:3], p[:, :, 1:3])
+
+
+# ------------------------------------------------------------ colour flows
+def test_colour_tags_of_gg_to_ttbar():
+    # (t^a1 t^a2)_{t, tbar}: the top's colour line runs through gluon 1 then
+    # gluon 2 into the antitop; incoming gluons carry colour and anticolour
+    # swapped with respect to the all-outgoing assignment
+    from oracle.integrand import oracle_process
+    from oracle.unweight import colour_tags
+    op = oracle_process(W.GG_TTX)
+    tags = colour_tags(op.string_labels(), op.legs)
+    assert tags.tolist() == [[[501, 502], [502, 503], [501, 0], [0, 503]],
+                             [[502, 503], [501, 502], [501, 0], [0, 503]]]
+    op = oracle_process(W.UUX_TTX)
+    tags = colour_tags(op.string_labels(), op.legs)
+    # u u~ -> t t~: annihilation lines (u with u~, t with t~) and exchange
+    # lines (u's colour into t, u~'s anticolour into t~)
+    assert tags.tolist() == [[[501, 0], [0, 501], [502, 0], [0, 502]],
+                             [[502, 0], [0, 501], [502, 0], [0, 501]]]
+
+
+@pytest.mark.parametrize("name", ["ee_mumu", "gg_ttx", "uux_ttx", "gg_ttxg", "uux_ttxg", "gg_ttxgg"])
+def test_colour_tags_conserve_colour(name):
+    # every line appears once as an outgoing colour or incoming anticolour and
+    # once as an outgoing anticolour or incoming colour; gluons carry both,
+    # (anti)quarks one, colourless particles none
+    from oracle.integrand import oracle_process
+    from oracle.unweight import colour_tags
+    from oracle.feynman import PARTICLES, COLOUR_DIM
+    wl = W.WORKLOADS[name]
+    op = oracle_process(wl)
+    tags = colour_tags(op.string_labels(), op.legs)
+    assert tags.shape[0] == op.string_basis().shape[1]
+    for t in tags:
+        src, snk = [], []
+        for i, (part, inc) in enumerate(op.legs):
+            c, a = t[i]
+            dim = COLOUR_DIM[PARTICLES[part][1]]
+            assert int(c != 0) + int(a != 0) == {1: 0, 3: 1, 8: 2}[dim]
+            (snk if inc else src).append(c)
+            (src if inc else snk).append(a)
+        src = sorted(v for v in src if v)
+        snk = sorted(v for v in snk if v)
+        assert src == snk and len(set(src)) == len(src)
+
+
+def test_flow_draw_follows_the_weights():
+    from oracle.unweight import colour_uniforms, draw_flows
+    wts = np.array([[0.0, 1.0, 3.0, 0.0, 6.0]] * 200_000)
+    pick, gap = draw_flows(wts, colour_uniforms(5, 2, 1, np.arange(200_000)))
+    freq = np.bincount(pick, minlength=5) / 200_000
+    assert freq[0] == 0 and freq[3] == 0
+    assert np.allclose(freq, [0, 0.1, 0.3, 0, 0.6], atol=0.005)
+
+
+@pytest.mark.parametrize("name", ["gg_ttx", "uux_ttxg"])
+def test_leading_colour_weights_sum_to_the_leading_colour_msq(name):
+    from oracle.integrand import Integrand
+    wl = W.WORKLOADS[name]
+    I = Integrand(wl)
+    x = W.uniform_points(wl.ndim, 20, 3)
+    p, s_hat, x1, x2, jx, wps, ok = I.kinematics(x)
+    w = I.proc.leading_colour_weights(p)
+    assert np.allclose(w.sum(axis=1), I.proc.msq_leading_colour(p), rtol=1e-13, atol=0)
+    assert np.all(w >= 0)

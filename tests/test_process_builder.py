@@ -145,3 +145,20 @@ def test_program_reproduces_oracle_msq(name, n, programs, oracle_processes):
     ref = proc.msq_avg(p)
     got = _program_msq(programs[name], p)
     assert np.max(np.abs(got / ref - 1)) < 1e-12
+
+
+@pytest.mark.parametrize("name", ["ee_mumu", "gg_ttx", "uux_ttx", "gg_ttxg", "uux_ttxg", "gg_ttxgg"])
+def test_lhe_colour_tags_agree_with_the_oracle(name):
+    # the builder's tags per colour flow against the oracle's, written
+    # independently from each side's own string labels (same basis order:
+    # the basis tensors are compared element by element first)
+    from paper_2106_10279_gb300 import api
+    from paper_2106_10279_gb300.process import ColourSpace, lhe_colour_tags
+    from oracle.integrand import oracle_process
+    from oracle.unweight import colour_tags
+    wl = W.WORKLOADS[name]
+    d = api.descriptor_for_workload(wl)
+    op = oracle_process(wl)
+    B, _ = ColourSpace(d.prog.legs).flow_basis()
+    assert np.array_equal(B, op.string_basis())
+    assert np.array_equal(lhe_colour_tags(d.prog), colour_tags(op.string_labels(), op.legs))
