@@ -367,27 +367,44 @@ def run_native(args):
         t_e2e = float(t.item())
     e2e_value = world * n_events * args.steps / t_e2e
 
-    # variants of the same kernel on a sample of the workload: the colour sum
-    # on the tensor cores, and one sampled helicity or helicity pair per point
-    # (different, unbiased estimators with more variance: reported with their
-    # errors)
+    # variants of the same kernel on a sample of the workload, each over 5
+    # seeds of 2e6 points on the adapted grid: the colour sum on the tensor
+    # cores, and the Monte Carlo estimators over helicities (one helicity or
+    # helicity pair per point), over colour (one colour flow per point) and
+    # over both: different unbiased estimators with more variance, compared
+    # by efficiency = 1 / (error^2 x kernel time) relative to the full sum
     variants = {}
     if not args.no_batch:
         nv = min(n_events, 2_000_000)
         gv = api.Vegas(wl.ndim, wl.n_bins, wl.alpha_vegas)
         gv.load(start_state)
-        for tag, prec, sample in (("mixed", "mixed", 0), ("mixed_tc", "mixed_tc", 0),
-                                  ("mixed_helicity_sampling", "mixed", 1),
-                                  ("mixed_helicity_pair_sampling", "mixed", 2)):
+        estimators = (("mixed", "mixed", 0, False), ("mixed_tc", "mixed_tc", 0, False),
+                      ("mixed_helicity_sampling", "mixed", 1, False),
+                      ("mixed_helicity_pair_sampling", "mixed", 2, False),
+                      ("mixed_colour_sampling", "mixed", 0, True),
+                      ("mixed_colour_and_pair_sampling", "mixed", 2, True))
+        for tag, prec, sample, colour in estimators:
             proc.set_helicity_sampling(sample, seed=5)
+            proc.set_colour_sampling(colour)
             api.mf_vegas_iterate([gv.handle], [proc.handle], [nv], seed, prec, False, stream)
             torch.cuda.synchronize()
-            r = api.mf_vegas_iterate([gv.handle], [proc.handle], [nv], seed, prec, False, stream)[0]
-            kms_v = api.mf_process_last_kernel_ms(proc.handle)
-            variants[tag] = {"events": nv, "kernel_ms": kms_v, "events_per_s": nv / (kms_v / 1e3),
-                             "integral_pb": r["integral"], "error_pb": r["error"],
+            kms_s, err_s, int_s = [], [], []
+            for s_ in range(5):
+                r = api.mf_vegas_iterate([gv.handle], [proc.handle], [nv], seed + 101 + s_, prec, False, stream)[0]
+                kms_s.append(api.mf_process_last_kernel_ms(proc.handle))
+                err_s.append(r["error"])
+                int_s.append(r["integral"])
+            variants[tag] = {"events": nv, "seeds": 5, "kernel_ms": statistics.median(kms_s),
+                             "events_per_s": nv / (statistics.median(kms_s) / 1e3),
+                             "integral_pb": statistics.mean(int_s),
+                             "error_pb_rms": math.sqrt(statistics.mean([e * e for e in err_s])),
                              "launch": proc.kernel_info(prec)}
         proc.set_helicity_sampling(False)
+        proc.set_colour_sampling(False)
+        ref = variants["mixed"]
+        for v_ in variants.values():
+            v_["efficiency_vs_full"] = (ref["error_pb_rms"] ** 2 * ref["kernel_ms"]) / (v_["error_pb_rms"] ** 2
+                                                                                        * v_["kernel_ms"])
 
     # the mixed batch of five subprocesses (gg->tt~, uu~->tt~, gg->tt~g,
     # uu~->tt~g, gg->tt~gg; 4e7 points per iteration in all), each with its own

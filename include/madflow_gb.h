@@ -595,6 +595,20 @@ mf_status mf_vegas_load(mf_vegas *v, const void *buf, size_t len);
  * sum over helicities. */
 mf_status mf_process_set_helicity_sampling(mf_process *p, int32_t on, uint64_t seed);
 
+/* Colour sampling (the Monte Carlo over colour configurations of Sec. 4,
+ * beside the one over helicities): with on = 1 the integrand kernels of this
+ * process (mf_integrand, the Vegas passes) replace each helicity's colour sum
+ * by NJAMP Re(conj(J_k) sum_l C_kl J_l) / den for one colour flow k per
+ * point, drawn uniformly from the first unit number of Philox counter
+ * (i, iteration, subprocess, 12) (given points: (i, 0, 0, 12) with the key
+ * of mf_process_set_helicity_sampling): an unbiased estimate of the colour
+ * sum, with a larger variance (the amplitudes are computed in full; only the
+ * colour sum is sampled).  Combines with helicity sampling and with the
+ * leading-colour approximation (then NJAMP C_kk |J_k|^2 / den).  on = 0:
+ * the full colour sum.  Runs in a kernel of its own in the process module;
+ * mf_helicity_msq, mf_grad and batches always sum the colours. */
+mf_status mf_process_set_colour_sampling(mf_process *p, int32_t on);
+
 /* The helicity pairs of a process: pairs[2 k], pairs[2 k + 1] (host, may be
  * NULL, else room for 2 * n_hel entries) are the rows of
  * mf_process_get_helicities whose pair leg (mf_process_info.pair_leg) is -1

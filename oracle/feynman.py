@@ -444,6 +444,25 @@ class Process:
             tot += norms[:, None] * np.abs(A) ** 2
         return tot.T
 
+    def colour_row_sums(self, p, k):
+        """Per point i: sum over helicities of Re(conj(A_k) (G A)_k) with
+        k = k[i], A the string coefficients of the colour-dressed amplitude
+        and G = B^dagger B the strings' colour matrix (no averaging), [N]."""
+        p = np.asarray(p, dtype=np.float64)
+        k = np.asarray(k)
+        B = self.string_basis()
+        C = self.colour_tensors()
+        P = np.linalg.pinv(B) @ C
+        G = B.conj().T @ B
+        cache = {}
+        tot = np.zeros(p.shape[0])
+        cols = np.arange(p.shape[0])
+        for hel in self.helicities():
+            A = P @ self.amplitudes(p, hel, cache)      # [basis, N]
+            GA = G @ A
+            tot += np.real(np.conj(A[k, cols]) * GA[k, cols])
+        return tot
+
     def msq_leading_colour(self, p):
         """sum over helicities of sum_s G_ss |A_s|^2 (no averaging), with A the
         exact coefficients of the colour-dressed amplitude in the string basis

@@ -241,6 +241,38 @@ class Integrand:
             f[idx] = jx[idx] * w[idx] * lum * msq / (2.0 * s_hat[idx]) * W.GEV2_TO_PB
         return f, pick
 
+    def sampled_colour(self, x, seed: int, leading=False, pick=None):
+        """f with the colour sum of every helicity replaced by the estimate
+        from one colour string k per point: n_strings Re(conj(A_k) (G A)_k)
+        (leading: n_strings G_kk |A_k|^2), k drawn uniformly from the first
+        unit number of Philox counter (i, 0, 0, 12), key (seed, 0) (or given
+        by pick); an unbiased estimate of f."""
+        from oracle.philox import philox4x64_10, to_unit
+        x = np.asarray(x, dtype=np.float64)
+        N = x.shape[1]
+        ns = self.proc.string_basis().shape[1]
+        if pick is None:
+            ctr = np.zeros((N, 4), dtype=np.uint64)
+            ctr[:, 0] = np.arange(N, dtype=np.uint64)
+            ctr[:, 3] = np.uint64(12)
+            u = to_unit(philox4x64_10(ctr, np.array([seed, 0], dtype=np.uint64))[:, 0])
+            pick = np.minimum((u * ns).astype(np.int64), ns - 1)
+        p, s_hat, x1, x2, jx, w, ok = self.kinematics(x)
+        keep = ok & self.cuts(p)
+        f = np.zeros(N)
+        idx = np.nonzero(keep)[0]
+        if len(idx):
+            if leading:
+                rows = self.proc.leading_colour_weights(p[idx])[np.arange(len(idx)), pick[idx]]
+            else:
+                rows = self.proc.colour_row_sums(p[idx], pick[idx])
+            msq = ns * rows * self.proc.average_factor()
+            lum = np.ones(len(idx))
+            if self.wl.beams:
+                lum = (self.pdfs[0].f(x1[idx], self.wl.mu_f2) * self.pdfs[1].f(x2[idx], self.wl.mu_f2))
+            f[idx] = jx[idx] * w[idx] * lum * msq / (2.0 * s_hat[idx]) * W.GEV2_TO_PB
+        return f, pick
+
     @staticmethod
     def helicity_pairs(helicities, leg: int):
         """The helicity list grouped into pairs that differ only at `leg`

@@ -117,6 +117,7 @@ SIGNATURES = {
     "mf_process_kernel_info": (c_i32, [C.c_void_p, c_i32, P(c_i32), P(c_i32), P(c_i32), P(c_i32), P(c_i32)]),
     "mf_process_set_helicity_sampling": (c_i32, [C.c_void_p, c_i32, C.c_uint64]),
     "mf_process_set_leading_colour": (c_i32, [C.c_void_p, c_i32]),
+    "mf_process_set_colour_sampling": (c_i32, [C.c_void_p, c_i32]),
     "mf_process_get_helicities": (c_i32, [C.c_void_p, P(C.c_int8), P(c_i32)]),
     "mf_process_get_helicity_pairs": (c_i32, [C.c_void_p, P(c_i32), P(c_i32)]),
     "mf_process_tune": (c_i32, [C.c_void_p, c_i32, c_i64, C.c_void_p, P(c_i32), P(c_i32)]),

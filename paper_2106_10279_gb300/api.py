@@ -404,6 +404,12 @@ class Process:
         mf_integrand(self.handle, x, n, f, precision, stream)
         return f
 
+    def set_colour_sampling(self, on=True):
+        """One uniformly drawn colour flow per point instead of the colour
+        sum (unbiased; see mf_process_set_colour_sampling)."""
+        L.check(L.lib().mf_process_set_colour_sampling(self.handle, 1 if on else 0),
+                "mf_process_set_colour_sampling")
+
     def set_helicity_sampling(self, on=True, seed=0):
         """One uniformly drawn helicity (on=True or 1) or helicity pair (on=2)
         per point instead of the sum (unbiased)."""

@@ -163,22 +163,76 @@ MF_DEV void load_block_constants(const KParams &kp, double *s_grid, cx<R> *cpl, 
     }
 }
 
+// Colour sampling: the unbiased estimate of a helicity's colour sum from
+// one colour flow k of the NJAMP, drawn uniformly per point:
+// NJAMP Re(conj(J_k) sum_l C_kl J_l) / den (with the leading-colour
+// approximation, NJAMP C_kk |J_k|^2 / den).
+template <typename R>
+MF_DEV double sampled_colour_value(const cx<R> *J, int k) {
+    using namespace MF_PROC;
+    double v;
+    if constexpr (LEADING_COLOUR) {
+        cx<R> jk = C<R>(R(0), R(0));
+#pragma unroll
+        for (int l = 0; l < NJAMP; ++l)
+            if (l == k) jk = J[l];
+        v = (double)COLOUR_NUM[k * NJAMP + k] * ((double)jk.re * (double)jk.re + (double)jk.im * (double)jk.im);
+    } else {
+        v = (double)colour_row<R>(J, k);
+    }
+    return v * (double)NJAMP * INV_COLOUR_DEN;
+}
+
+// The colour flow a colour-sampled kernel uses for point e of a launch: the
+// first unit number of Philox counter (point, iteration, subprocess, 12)
+// (given points: (e, 0, 0, 12) with the process's sampling key).
+MF_DEV int sampled_colour_flow(const KParams &kp, int64_t e, uint64_t iteration) {
+    const bool given = kp.mode == 0 || kp.mode == 2;
+    uint64_t c[4] = {given ? (uint64_t)e : ((kp.mode == 3 || kp.mode == 5) ? (uint64_t)kp.idx[e] : (uint64_t)(e + kp.ev0)),
+                     given ? 0ull : iteration, given ? 0ull : kp.subprocess, 12ull};
+    philox4x64_10(c, kp.seed, 0ull);
+    int k = (int)(unit_from_bits(c[0]) * MF_PROC::NJAMP);
+    return k < MF_PROC::NJAMP ? k : MF_PROC::NJAMP - 1;
+}
+
 // Colour-summed |M|^2 of one helicity: the colour flows of the program, then
 // the full colour sum (FMA units, or the tensor cores with TC) or, for a
 // process generated with the leading-colour approximation, only the diagonal
-// of the colour matrix.  With TC every thread of the block must call it the
-// same number of times.
-template <typename R, bool TC>
+// of the colour matrix; with CS, the colour-sampled estimate of flow krow.
+// With TC every thread of the block must call it the same number of times.
+template <typename R, bool TC, bool CS = false>
 MF_DEV double helicity_value(const KParams &kp, const R *ms, const R *idn, const int8_t *hel, const cx<R> *cpl,
-                             const R *mass_r, tc::State *tcs) {
+                             const R *mass_r, tc::State *tcs, int krow = -1) {
     using namespace MF_PROC;
-    if constexpr (LEADING_COLOUR || TC) {
+    if constexpr (CS) {
+        cx<R> J[NJAMP];
+        helicity_jamp<R>(ms, idn, hel, cpl, mass_r, J);
+        return sampled_colour_value<R>(J, krow);
+    } else if constexpr (LEADING_COLOUR || TC) {
         cx<R> J[NJAMP];
         helicity_jamp<R>(ms, idn, hel, cpl, mass_r, J);
         if constexpr (LEADING_COLOUR) return (double)colour_sum_lc<R>(J);
         else return (double)(tc::colour_sum<NJAMP>(*tcs, J) * (float)INV_COLOUR_DEN);
     } else {
         return (double)helicity_msq<R>(ms, idn, hel, cpl, mass_r);
+    }
+}
+
+// Both members' values of a helicity pair: their colour sums, or with CS
+// their colour-sampled estimates from flow krow.
+template <typename R, bool CS>
+MF_DEV void pair_values(const R *ms, const R *idn, const int8_t *hel, const cx<R> *cpl, const R *mass_r, int krow,
+                        double &va, double &vb) {
+    if constexpr (CS) {
+        cx<R> J[MF_PROC::NJAMP], Jb[MF_PROC::NJAMP];
+        MF_PROC::helicity_pair_jamp<R>(ms, idn, hel, cpl, mass_r, J, Jb);
+        va = sampled_colour_value<R>(J, krow);
+        vb = sampled_colour_value<R>(Jb, krow);
+    } else {
+        R a, b;
+        MF_PROC::helicity_pair_msq<R>(ms, idn, hel, cpl, mass_r, a, b);
+        va = (double)a;
+        vb = (double)b;
     }
 }
 
@@ -191,10 +245,12 @@ MF_DEV bool sample_pairs(const KParams &kp) {
 
 // One tile of BLOCK events: phases A, B and C.  Ends with a block barrier.
 // With TC the colour sum of phase B runs on the tensor cores (R = float,
-// BLOCK = 128, tcs set up by the caller).  With FLOW (a kernel of its own,
-// so that the integrand kernel carries none of its code) phase B is
-// replaced by the leading-colour flow draw of mode 5.
-template <typename R, int BLOCK, int HT, bool TC = false, bool FLOW = false>
+// BLOCK = 128, tcs set up by the caller).  VARIANT 1 (the flow kernel)
+// replaces phase B by the leading-colour flow draw of mode 5; VARIANT 2
+// (the colour-sampled kernel) replaces each colour sum by the estimate from
+// one colour flow per point.  Each variant is a kernel of its own, so that
+// the integrand kernel carries none of their code.
+template <typename R, int BLOCK, int HT, bool TC = false, int VARIANT = 0>
 MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem_raw, const double *s_grid,
                       const cx<R> *cpl, const R *mass_r, tc::State *tcs = nullptr) {
     using namespace MF_PROC;
@@ -325,7 +381,7 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
         // helicities, then a butterfly over the HT lanes), and a flow drawn
         // with probability proportional to it by the first unit number of
         // Philox counter (point, iteration, subprocess, 13)
-        if constexpr (FLOW) {
+        if constexpr (VARIANT == 1) {
             const int EPR = BLOCK / HT, sub = tid % HT;
             const int nhp = kp.nhel_pow2;
             const int per = nhp >= HT ? nhp / HT : 1;
@@ -381,7 +437,7 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
             }
         }
         // ---------------- phase B: helicity amplitudes, HT lanes per event
-        if constexpr (!FLOW) {
+        if constexpr (VARIANT != 1) {
             // HT lanes per point, each running the program for a contiguous
             // block of helicities; with helicity sampling one lane per point
             // and its sampled helicity (one call site of the program either way)
@@ -407,31 +463,35 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
                 const int hs = (samp && valid) ? (int)s_msq[ev] : 0;
                 const R *ms = s_mom + ev * NLEG * 4;
                 const R *idn = s_den + ev * NDEN1;
+                int krow = -1;
+                if constexpr (VARIANT == 2) krow = sampled_colour_flow(kp, tile * BLOCK + ev, iteration);
                 if constexpr (PAIR_LEG >= 0 && !TC) {
                     if (samp_pair) {
                         // the sampled pair: its present members' |M|^2
                         const uint8_t ia = kp.pairs[hs][0], ib = kp.pairs[hs][1];
-                        R va, vb;
-                        helicity_pair_msq<R>(ms, idn, kp.hel[ia != 0xFF ? ia : ib], cpl, mass_r, va, vb);
-                        ps.add((valid && ia != 0xFF) ? (double)va : 0.0);
-                        ps.add((valid && ib != 0xFF) ? (double)vb : 0.0);
+                        double va, vb;
+                        pair_values<R, VARIANT == 2>(ms, idn, kp.hel[ia != 0xFF ? ia : ib], cpl, mass_r, krow, va, vb);
+                        ps.add((valid && ia != 0xFF) ? va : 0.0);
+                        ps.add((valid && ib != 0xFF) ? vb : 0.0);
                     }
                     if (pairs) {
                         for (int k = 0; k < per; ++k) {
                             const int u = sub * per + k;
                             const bool uv = u < kp.npairs;
                             const uint8_t ia = kp.pairs[uv ? u : 0][0], ib = kp.pairs[uv ? u : 0][1];
-                            R va, vb;
-                            helicity_pair_msq<R>(ms, idn, kp.hel[ia != 0xFF ? ia : ib], cpl, mass_r, va, vb);
-                            ps.add((uv && valid && ia != 0xFF) ? (double)va : 0.0);
-                            ps.add((uv && valid && ib != 0xFF) ? (double)vb : 0.0);
+                            double va, vb;
+                            pair_values<R, VARIANT == 2>(ms, idn, kp.hel[ia != 0xFF ? ia : ib], cpl, mass_r, krow, va,
+                                                         vb);
+                            ps.add((uv && valid && ia != 0xFF) ? va : 0.0);
+                            ps.add((uv && valid && ib != 0xFF) ? vb : 0.0);
                         }
                     }
                 }
                 for (int k = 0; k < ((pairs || samp_pair) ? 0 : per); ++k) {
                     const int h = samp ? hs : sub * per + k;
                     const bool hv = h < kp.nhel;
-                    double v = helicity_value<R, TC>(kp, ms, idn, kp.hel[hv ? h : 0], cpl, mass_r, tcs);
+                    double v = helicity_value<R, TC, VARIANT == 2>(kp, ms, idn, kp.hel[hv ? h : 0], cpl, mass_r, tcs,
+                                                                   krow);
                     if (!(hv && valid)) v = 0.0;
                     if (kp.mode == 2 && hv && valid) kp.f[(int64_t)h * kp.n + tile * BLOCK + ev] = v;
                     ps.add(v);
@@ -481,9 +541,9 @@ MF_DEV bool smem_ok(const KParams &kp, size_t need) {
     return false;
 }
 
-// The single-process kernel: a grid-stride loop over tiles (FLOW: the
-// leading-colour flow kernel of mode 5).
-template <typename R, int BLOCK, int HT, bool FLOW = false>
+// The single-process kernel: a grid-stride loop over tiles (VARIANT 1: the
+// leading-colour flow kernel of mode 5; 2: the colour-sampled integrand).
+template <typename R, int BLOCK, int HT, int VARIANT = 0>
 MF_DEV void kernel_body(const KParams &kp) {
     using namespace MF_PROC;
     if (!smem_ok(kp, tile_smem_bytes<R, BLOCK>())) return;
@@ -495,7 +555,7 @@ MF_DEV void kernel_body(const KParams &kp) {
     __syncthreads();
     const int64_t ntiles = (kp.n + BLOCK - 1) / BLOCK;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
-        tile_body<R, BLOCK, HT, false, FLOW>(kp, tile, smem_raw, s_grid, cpl, mass_r);
+        tile_body<R, BLOCK, HT, false, VARIANT>(kp, tile, smem_raw, s_grid, cpl, mass_r);
 }
 
 // The single-process kernel with the colour sum on the tensor cores

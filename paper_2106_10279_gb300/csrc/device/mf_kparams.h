@@ -49,6 +49,9 @@ struct mf_kparams {
     const long long *iter_dev; // if set, the iteration index is read here (graph replays)
     uint16_t *obs_out;         // mode 4: bins [n_obs][n], 0xFFFF: not binned
     int32_t *flow_out;         // mode 5: colour-flow index [n], -1: none
+    int32_t variant;           // kernel of the module to launch (host side): 0 the integrand
+                               // kernel, 1 the flow kernel (mode 5), 2 the colour-sampled kernel
+    int32_t colour_sample;     // the process samples one colour flow per point
     int32_t n_obs;             // mode 4: observables
     int32_t obs_kind[MF_KP_MAX_OBS];   // 0: pT, 1: rapidity, 2: pseudorapidity (collider frame)
     int32_t obs_leg[MF_KP_MAX_OBS];

@@ -566,6 +566,8 @@ mf_status verify_pairs(mf_process *p, int prec) {
             fill_common(*p, kp);
             set_hel(kp, p->hel, p->n_legs);
             kp.hel_sample = 0;
+            kp.colour_sample = 0;
+            kp.variant = 0;
             if (pass == 1) kp.npairs = 0;            // one helicity at a time
             kp.mode = 0;
             kp.n = npts;
@@ -626,6 +628,8 @@ mf_status compile_grad(mf_process *p) {
 void fill_common(const mf_process &p, mf_kparams &kp) {
     std::memset(&kp, 0, sizeof kp);
     kp.wait_polls = p.opt.wait_polls;   // negative: the kernels' default limit
+    kp.colour_sample = p.colour_sample;
+    kp.variant = p.colour_sample ? 2 : 0;
     kp.S = p.sqrt_s * p.sqrt_s;
     kp.ln_tau_min = p.ln_tau_min;
     kp.w0_const = p.w0_const;
@@ -723,7 +727,7 @@ mf_status launch(mf_process *p, int prec, mf_kparams &kp, cudaStream_t s) {
     if (grid > ntiles) grid = ntiles;
     if (grid < 1) grid = 1;
     void *args[] = {&kp};
-    return mfi::launch_kernel(k, (unsigned)grid, args, s, kp.mode == 5);
+    return mfi::launch_kernel(k, (unsigned)grid, args, s, kp.mode == 5 ? 1 : kp.variant);
 }
 
 // Ranges of the process options (MF_OPT_AUTO allowed everywhere).
@@ -959,6 +963,8 @@ extern "C" mf_status mf_create_process(const mf_process_desc *d, mf_process **ou
         fill_common(*p, kp);
         set_hel(kp, p->hel_all, n);
         kp.mode = 2;
+        kp.variant = 0;
+    kp.variant = 0;                       // per-helicity values: the integrand kernel
         kp.n = npts;
         kp.x = dx;
         kp.f = df;
@@ -1121,6 +1127,13 @@ extern "C" mf_status mf_process_set_helicity_sampling(mf_process *p, int32_t on,
     return MF_OK;
 }
 
+extern "C" mf_status mf_process_set_colour_sampling(mf_process *p, int32_t on) {
+    if (!p) return fail(MF_EINVAL, "NULL process");
+    if (on != 0 && on != 1) return fail(MF_EINVAL, "colour sampling must be 0 or 1");
+    p->colour_sample = on;
+    return MF_OK;
+}
+
 extern "C" mf_status mf_process_get_helicity_pairs(const mf_process *p, int32_t *pairs, int32_t *n_pairs) {
     if (!p || !n_pairs) return fail(MF_EINVAL, "NULL argument");
     *n_pairs = (int32_t)(p->pairs.size() / 2);
@@ -1201,6 +1214,7 @@ extern "C" mf_status mf_helicity_msq(mf_process *p, const double *x, int64_t n, 
     fill_common(*p, kp);
     set_hel(kp, p->hel_all, p->n_legs);
     kp.mode = 2;
+    kp.variant = 0;                       // per-helicity values: the integrand kernel
     kp.hel_sample = 0;
     kp.n = n;
     kp.x = x;
@@ -1225,6 +1239,8 @@ extern "C" mf_status mf_grad(mf_process *p, const double *x, int64_t n, double *
     kp.f = f;
     kp.g_dparam = df_dparam;
     kp.g_dx = df_dx;
+    kp.variant = 0;                       // the gradient always sums the colours
+    kp.colour_sample = 0;
     return launch(p, 2, kp, (cudaStream_t)stream);
 }
 

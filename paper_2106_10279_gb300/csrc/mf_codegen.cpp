@@ -713,9 +713,25 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
     } else {
         o << "  va = vb = R(0);\n";
     }
+    o << "}\n";
+    // the colour flows of a helicity pair without their colour sums
+    o << "template <typename R>\n"
+         "MF_DEV void helicity_pair_jamp(const R *__restrict__ ms, const R *__restrict__ idn, const int8_t *hel,\n"
+         "                               const mf::cx<R> *cpl, const R *mass, mf::cx<R> *J, mf::cx<R> *Jb) {\n"
+         "  using namespace mf;\n#pragma unroll\n"
+         "  for (int k = 0; k < NJAMP; ++k) { J[k] = C<R>(R(0), R(0)); Jb[k] = J[k]; }\n";
+    for (int part = 0; part < pair_parts; ++part)
+        o << "  program_pair_part" << part << "<R>(ms, idn, hel, cpl, mass, J, Jb);\n";
     o << "}\n__device__ const int COLOUR_NUM[NJAMP * NJAMP] = {";
     for (int k = 0; k < nj * nj; ++k) o << (k ? ", " : "") << p.colour_num[k];
     o << "};\nconstexpr double INV_COLOUR_DEN = " << fmt_double(1.0 / p.colour_den) << ";\n";
+    // one row of the colour sum: Re(conj(J_k) sum_l C_kl J_l) (numerators),
+    // k chosen at run time (selected, not indexed, so J stays in registers)
+    o << "template <typename R>\nMF_DEV R colour_row(const mf::cx<R> *J, int k) {\n  using namespace mf;\n"
+         "  cx<R> jk = C<R>(R(0), R(0)), z = jk;\n#pragma unroll\n"
+         "  for (int l = 0; l < NJAMP; ++l) {\n    if (l == k) jk = J[l];\n"
+         "    z = z + R(COLOUR_NUM[k * NJAMP + l]) * J[l];\n  }\n"
+         "  return jk.re * z.re + jk.im * z.im;\n}\n";
     o << "}  // namespace " << ns << "\n";
     if (kernel) {
         o << "#include \"mf_kernel.cuh\"\n";
@@ -726,10 +742,13 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
         o << ") mf_kernel(const mf::KParams kp) {\n";
         if (precision == MF_MIXED_TC) o << "  mf::kernel_body_tc<" << ht << ">(kp);\n}\n";
         else o << "  mf::kernel_body<" << R << ", " << block << ", " << ht << ">(kp);\n}\n";
-        // the leading-colour flow kernel (mode 5) of the same programs
+        // the leading-colour flow kernel (mode 5) and the colour-sampled
+        // integrand kernel of the same programs
         const int fblock = precision == MF_MIXED_TC ? 128 : block;
         o << "extern \"C\" __global__ void __launch_bounds__(" << fblock << ") mf_flow_kernel(const mf::KParams kp) {\n"
-          << "  mf::kernel_body<" << R << ", " << fblock << ", " << ht << ", true>(kp);\n}\n";
+          << "  mf::kernel_body<" << R << ", " << fblock << ", " << ht << ", 1>(kp);\n}\n";
+        o << "extern \"C\" __global__ void __launch_bounds__(" << fblock << ") mf_csamp_kernel(const mf::KParams kp) {\n"
+          << "  mf::kernel_body<" << R << ", " << fblock << ", " << ht << ", 2>(kp);\n}\n";
     }
     // algorithmic count of the programs as emitted: every wavefunction once
     // (the few a later program part recomputes are not counted), per

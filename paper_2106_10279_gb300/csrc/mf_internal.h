@@ -39,6 +39,7 @@ struct Compiled {
     CUmodule module = nullptr;
     CUfunction fn = nullptr;
     CUfunction fn_flow = nullptr;  // the module's leading-colour flow kernel (mode 5), if any
+    CUfunction fn_csamp = nullptr; // the module's colour-sampled integrand kernel, if any
     int block = 128;
     int ht = 32;
     size_t smem = 0;
@@ -109,6 +110,7 @@ struct mf_process {
     int64_t last_n = 0;            // points of the last Vegas pass held in d_w
     int hel_sample = 0;            // one sampled helicity per point
     int leading_colour = 0;        // generate the leading-colour approximation
+    int colour_sample = 0;         // one colour flow per point (the colour-sampled kernel)
     uint64_t hel_seed = 0;         // Philox key of the sampling of given points
 };
 
@@ -175,5 +177,5 @@ mf_status jit_compile(const std::string &source, const std::string &name, std::v
                       int ptxas_level = -1);
 mf_status load_kernel(const std::vector<char> &cubin, Compiled &out, const char *name = "mf_kernel");
 void unload_kernel(Compiled &k);
-mf_status launch_kernel(const Compiled &k, unsigned grid, void **args, cudaStream_t s, bool flow = false);
+mf_status launch_kernel(const Compiled &k, unsigned grid, void **args, cudaStream_t s, int variant = 0);
 }  // namespace mfi

@@ -208,8 +208,9 @@ mf_status load_kernel(const std::vector<char> &cubin, Compiled &out, const char 
     if (r != CUDA_SUCCESS) return fail(MF_ECUDA, "cuModuleGetFunction: " + drv_err(r));
     // the flow kernel of a process module (absent in other modules)
     if (g_drv.moduleGetFunction(&out.fn_flow, out.module, "mf_flow_kernel") != CUDA_SUCCESS) out.fn_flow = nullptr;
-    if (out.fn_flow && out.smem > 48 * 1024)
-        g_drv.funcSetAttribute(out.fn_flow, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)out.smem);
+    if (g_drv.moduleGetFunction(&out.fn_csamp, out.module, "mf_csamp_kernel") != CUDA_SUCCESS) out.fn_csamp = nullptr;
+    for (CUfunction f : {out.fn_flow, out.fn_csamp})
+        if (f && out.smem > 48 * 1024) g_drv.funcSetAttribute(f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)out.smem);
     int regs = 0, local = 0;
     g_drv.funcGetAttribute(&regs, CU_FUNC_ATTRIBUTE_NUM_REGS, out.fn);
     g_drv.funcGetAttribute(&local, CU_FUNC_ATTRIBUTE_LOCAL_SIZE_BYTES, out.fn);
@@ -245,12 +246,13 @@ void unload_kernel(Compiled &k) {
     k.module = nullptr;
     k.fn = nullptr;
     k.fn_flow = nullptr;
+    k.fn_csamp = nullptr;
 }
 
-mf_status launch_kernel(const Compiled &k, unsigned grid, void **args, cudaStream_t s, bool flow) {
-    if (flow && !k.fn_flow) return fail(MF_EUNSUPPORTED, "the module has no flow kernel");
-    CUresult r = g_drv.launch(flow ? k.fn_flow : k.fn, grid, 1, 1, (unsigned)k.block, 1, 1, (unsigned)k.smem,
-                              (CUstream)s, args, nullptr);
+mf_status launch_kernel(const Compiled &k, unsigned grid, void **args, cudaStream_t s, int variant) {
+    CUfunction f = variant == 1 ? k.fn_flow : variant == 2 ? k.fn_csamp : k.fn;
+    if (!f) return fail(MF_EUNSUPPORTED, "the process module has no kernel of this variant");
+    CUresult r = g_drv.launch(f, grid, 1, 1, (unsigned)k.block, 1, 1, (unsigned)k.smem, (CUstream)s, args, nullptr);
     if (r != CUDA_SUCCESS) return fail(MF_ECUDA, "process kernel launch: " + drv_err(r));
     return MF_OK;
 }

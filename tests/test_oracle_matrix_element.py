@@ -285,3 +285,22 @@ def test_string_basis_norms_and_leading_colour(oracle_processes):
     lc = I.leading_colour(x)
     nz = full != 0
     assert np.allclose(lc[nz] / full[nz], 1.25, rtol=1e-12)
+
+
+@pytest.mark.parametrize("name", ["gg_ttx", "uux_ttxg", "gg_ttxg"])
+def test_colour_sampled_estimate_averages_to_the_colour_sum(name):
+    # the mean over the strings of n_strings Re(conj(A_k) (G A)_k), from the
+    # string-basis projection, equals the brute-force colour sum over
+    # explicit colour assignments; likewise the leading-colour version
+    import workloads as W
+    from oracle.integrand import Integrand
+    wl = W.WORKLOADS[name]
+    I = Integrand(wl)
+    x = W.uniform_points(wl.ndim, 25, 9)
+    f, lc = I(x), I.leading_colour(x)
+    ns = I.proc.string_basis().shape[1]
+    tot = sum(I.sampled_colour(x, 1, pick=np.full(25, k))[0] for k in range(ns)) / ns
+    totl = sum(I.sampled_colour(x, 1, leading=True, pick=np.full(25, k))[0] for k in range(ns)) / ns
+    nz = f != 0
+    assert np.allclose(tot[nz], f[nz], rtol=1e-13, atol=0)
+    assert np.allclose(totl[nz], lc[nz], rtol=1e-13, atol=0)
