@@ -434,11 +434,31 @@ def run_native(args):
         gs = [api.Vegas(p.ndim) for p in procs]
         rate_s, res_s = timed(lambda: api.mf_vegas_iterate([g.handle for g in gs], [p.handle for p in procs],
                                                            nb_ev, 4242, "mixed", True, stream))
+        # the same batch as one CUDA-graph replay per iteration
+        gg_ = [api.Vegas(p.ndim) for p in procs]
+        rate_g, res_g = timed(lambda: bt.iterate(gg_, nb_ev, 4242, True, stream, graph=True))
+        # the four short programs as one batch (their own register budget)
+        # and gg -> tt~gg on its own
+        heavy = [i for i, (name, _) in enumerate(W.MIXED_BATCH) if name == "gg_ttxgg"]
+        light = [i for i in range(len(procs)) if i not in heavy]
+        bt_l = api.Batch([procs[i] for i in light], "mixed")
+        gl = [api.Vegas(procs[i].ndim) for i in light]
+        gh = [api.Vegas(procs[i].ndim) for i in heavy]
+
+        def split():
+            a_ = bt_l.iterate(gl, [nb_ev[i] for i in light], 4242, True, stream)
+            b_ = api.mf_vegas_iterate([g.handle for g in gh], [procs[i].handle for i in heavy],
+                                      [nb_ev[i] for i in heavy], 4242, "mixed", True, stream)
+            return a_ + b_
+        rate_split, _ = timed(split)
         batch = {"workload": "mixed batch " + ", ".join(f"{n} {e:.0e}" for n, e in W.MIXED_BATCH),
-                 "value": rate_b, "unit": "events/s", "separate_launches": rate_s,
+                 "value": rate_b, "unit": "events/s", "separate_launches": rate_s, "graph_replay": rate_g,
+                 "light_batch_plus_heavy_alone": rate_split,
                  "sigma_total_pb": sum(r["sigma"] for r in res_b),
                  "same_sigma_as_separate": all(a["sigma"] == b["sigma"] for a, b in zip(res_b, res_s)),
-                 "kernel_ms": bt.info()["last_kernel_ms"]}
+                 "same_sigma_graph": all(a["sigma"] == b["sigma"] for a, b in zip(res_b, res_g)),
+                 "kernel_ms": bt.info()["last_kernel_ms"], "registers": bt.info().get("regs"),
+                 "light_batch_registers": bt_l.info().get("regs")}
 
     # the gradient kernel (mf_grad: f, df/dm_t, df/dalpha_s, df/dx in FP64) on
     # uniform points of the same process: points/s and, from the FP64

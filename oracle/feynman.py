@@ -317,13 +317,23 @@ class Process:
             return T_SU3
         return np.ones((1, 1, 1), dtype=np.complex128)
 
-    def _colour(self, tree):
-        """(legs, array) with axes legs + (open index,)."""
+    def _colour(self, tree, fixed=None, cache=None):
+        """(legs, array) with axes legs + (open index,).  A leg in `fixed`
+        (leg -> colour index) keeps only that colour (an axis of size 1);
+        `cache` (a dict) shares subtrees between the terms of one pass."""
+        if cache is not None and tree in cache:
+            return cache[tree]
         if tree[0] == "L":
             d = self._colour_dim_leg(tree[1])
-            return (tree[1],), np.eye(d, dtype=np.complex128)
+            e = np.eye(d, dtype=np.complex128)
+            if fixed and tree[1] in fixed:
+                e = e[[fixed[tree[1]]]]
+            out = ((tree[1],), e)
+            if cache is not None:
+                cache[tree] = out
+            return out
         _, kind, line, children, var = tree
-        ch = [self._colour(c) for c in children]
+        ch = [self._colour(c, fixed, cache) for c in children]
         legs = sum((c[0] for c in ch), ())
         ops = []
         # children: axes (legs..., X_i) with X_i = 40 + i; output label 45; e = 46
@@ -347,27 +357,58 @@ class Process:
         elif kind == "vvvv":
             ops += [F4_SU3[var - 1], [40, 41, 42, 45]]
         out = np.einsum(*ops, list(legs) + [45])
+        if cache is not None:
+            cache[tree] = (legs, out)
         return legs, out
+
+    def _colour_columns(self, fixed=None):
+        """[colours, t]: the colour factor of every term over the external
+        colour assignments, the legs in `fixed` held at their colour (axes in
+        leg order, flattened)."""
+        cols = []
+        cache = {} if fixed else None
+        for t in self.terms:
+            legs, arr = self._colour(t, fixed, cache)
+            # open index = colour of the root leg
+            order = list(legs) + [self.n - 1]
+            arr = np.transpose(arr, np.argsort(order))
+            cols.append(arr.reshape(-1))
+        return np.stack(cols, axis=1)
 
     def colour_tensors(self):
         """C[colours, t]: the colour factor of every term over all external
         colour assignments (axes in leg order, flattened)."""
         if getattr(self, "_C", None) is None:
-            cols = []
-            for t in self.terms:
-                legs, arr = self._colour(t)
-                # open index = colour of the root leg
-                order = list(legs) + [self.n - 1]
-                arr = np.transpose(arr, np.argsort(order))
-                cols.append(arr.reshape(-1))
-            self._C = np.stack(cols, axis=1)
+            self._C = self._colour_columns()
         return self._C
 
+    # colour assignments x terms above which the colour matrix is summed in
+    # chunks instead of from the whole colour tensor
+    COLOUR_CHUNK = 1 << 26
+
     def colour_matrix(self):
-        """G[t1, t2] = sum over all external colours of conj(c_t1) c_t2."""
+        """G[t1, t2] = sum over all external colours of conj(c_t1) c_t2.
+        For a process whose whole colour tensor is large (seven legs), the sum
+        runs over chunks of colour assignments: the colours of the first
+        gluon legs are held fixed in turn, and each chunk's C^dagger C is
+        added; the colour tensor itself is never stored."""
         if self._G is None:
-            C = self.colour_tensors()
-            self._G = C.conj().T @ C
+            dims = [self._colour_dim_leg(i) for i in range(self.n)]
+            total = int(np.prod(dims)) * len(self.terms)
+            if total <= self.COLOUR_CHUNK:
+                C = self.colour_tensors()
+                self._G = C.conj().T @ C
+            else:
+                gl = [i for i in range(self.n - 1) if dims[i] == 8]
+                k = 0
+                while total > self.COLOUR_CHUNK // 4 and k < len(gl):
+                    total //= 8
+                    k += 1
+                G = np.zeros((len(self.terms), len(self.terms)), dtype=np.complex128)
+                for vals in itertools.product(range(8), repeat=k):
+                    Cc = self._colour_columns(dict(zip(gl[:k], vals)))
+                    G += Cc.conj().T @ Cc
+                self._G = G
         return self._G
 
     # ---------------------------------------------------------------- leading colour

@@ -25,6 +25,8 @@ residual is checked) and the coefficients are small rationals.
 from __future__ import annotations
 
 import itertools
+import json
+import os
 import math
 from dataclasses import dataclass, field
 from fractions import Fraction
@@ -308,9 +310,64 @@ class ProcessProgram:
     basis_labels: list
 
 
+# Programs whose construction takes minutes (gg -> tt~ggg: 1240 diagrams, a
+# 120-flow colour basis) are stored once as JSON under programs/ by
+# programs/store_programs.py; build_program loads a stored structure when
+# one exists for the same name and legs and fills in the masses and
+# couplings of the call.
+PROGRAM_STORE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "programs")
+
+
+def _couplings(alpha_s, alpha):
+    g_s = math.sqrt(4 * math.pi * alpha_s)
+    e = math.sqrt(4 * math.pi * alpha)
+    return [1j * g_s, 1j * e, g_s + 0j, -1j * g_s * g_s]
+
+
+def store_program(prog: "ProcessProgram", masses: dict, path: str):
+    """Write the structure of a program (masses as flavour names) to JSON."""
+    inv = {}
+    for flav, m in masses.items():
+        inv.setdefault(float(m), flav)
+
+    def flav_of(m):
+        return "" if m == 0.0 else inv[float(m)]
+    rec = {"name": prog.name, "legs": [[p, bool(i)] for p, i in prog.legs], "leg_kind": list(prog.leg_kind),
+           "leg_mass": [flav_of(m) for m in prog.leg_mass],
+           "ops": [[o.kind, o.routine, list(o.inputs), o.leg, o.coupling, flav_of(o.mass),
+                    [[k, re, im] for k, re, im in o.terms]] for o in prog.ops],
+           "colour_num": prog.colour_num.tolist(), "colour_den": int(prog.colour_den),
+           "n_diagrams": prog.n_diagrams, "average": prog.average, "alpha_s_power": prog.alpha_s_power,
+           "basis_labels": [[[r, c, list(g)] for r, c, g in label] for label in prog.basis_labels]}
+    with open(path, "w") as fh:
+        json.dump(rec, fh, separators=(",", ":"))
+
+
+def _stored_program(name, legs, masses, alpha_s, alpha):
+    path = os.path.join(PROGRAM_STORE, name + ".json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        rec = json.load(fh)
+    if [(p, bool(i)) for p, i in rec["legs"]] != legs:
+        return None
+
+    def mass(flav):
+        return float(masses.get(flav, 0.0)) if flav else 0.0
+    ops = [Op(k, r, tuple(ins), leg=leg, coupling=c, mass=mass(mf), terms=[tuple(t) for t in terms])
+           for k, r, ins, leg, c, mf, terms in rec["ops"]]
+    labels = [tuple((r, c, tuple(g)) for r, c, g in label) for label in rec["basis_labels"]]
+    return ProcessProgram(rec["name"], legs, rec["leg_kind"], [mass(f) for f in rec["leg_mass"]], ops,
+                          _couplings(alpha_s, alpha), np.array(rec["colour_num"], dtype=np.int64),
+                          rec["colour_den"], rec["n_diagrams"], rec["average"], rec["alpha_s_power"], labels)
+
+
 def build_program(name, legs, masses, alpha_s, alpha):
     """legs: [(particle, incoming)], incoming first. masses: flavour -> mass."""
     legs = [(p, bool(i)) for p, i in legs]
+    stored = _stored_program(name, legs, masses, alpha_s, alpha)
+    if stored is not None:
+        return stored
     n = len(legs)
     topo = Topology(legs)
     lines = topo.lines
@@ -327,9 +384,7 @@ def build_program(name, legs, masses, alpha_s, alpha):
         return Node(t.kind, t.line, tuple(strip(c) for c in t.children), t.leg, 0)
     n_diagrams = len({strip(t) for t in tops})
 
-    g_s = math.sqrt(4 * math.pi * alpha_s)
-    e = math.sqrt(4 * math.pi * alpha)
-    couplings = [1j * g_s, 1j * e, g_s + 0j, -1j * g_s * g_s]
+    couplings = _couplings(alpha_s, alpha)
     C_FFV_G, C_FFV_A, C_VVV, C_VVVV = 0, 1, 2, 3
 
     def mass_of(line):

@@ -139,7 +139,12 @@ UUX_TTXG = Workload("uux_ttxg", _legs("u u~ -> t t~ g"), SQRT_S_LHC, ("u", "ubar
 GG_TTXGG = Workload("gg_ttxgg", _legs("g g -> t t~ g g"), SQRT_S_LHC, ("g", "g"), M_TOP ** 2,
                     pt_min_gluon=20.0, dr_min_gluon=0.4, n_events=40_000_000, n_iter=10)
 
-WORKLOADS = {w.name: w for w in (EE_MUMU, GG_TTX, UUX_TTX, GG_TTXG, UUX_TTXG, GG_TTXGG)}
+# the heavier workload of the paper's Sec. 3.2 (its pp -> tt~ggg with 100k
+# events): the gg channel, 1240 diagrams, 120 colour flows
+GG_TTXGGG = Workload("gg_ttxggg", _legs("g g -> t t~ g g g"), SQRT_S_LHC, ("g", "g"), M_TOP ** 2,
+                     pt_min_gluon=20.0, dr_min_gluon=0.4, n_events=100_000, n_iter=10)
+
+WORKLOADS = {w.name: w for w in (EE_MUMU, GG_TTX, UUX_TTX, GG_TTXG, UUX_TTXG, GG_TTXGG, GG_TTXGGG)}
 
 # the mixed batch: one persistent launch over five subprocesses
 MIXED_BATCH = (("gg_ttx", 20_000_000), ("uux_ttx", 5_000_000), ("gg_ttxg", 10_000_000),
