@@ -142,7 +142,10 @@ typedef struct {
  *   min_blocks       minimum of resident blocks per SM the compiler must
  *                    allow (__launch_bounds__), 0: none (default 0);
  *   helicity_pairs   0: helicities one at a time; 1: pairs where they save
- *                    FLOPs (default 1);
+ *                    FLOPs (default: 1, except for programs above 1.5e5
+ *                    FLOPs per helicity, whose pair program is not
+ *                    generated: their single-helicity program alone takes
+ *                    minutes to compile);
  *   block            threads per block, 128 or 256 (default: 256 for long
  *                    programs, 128 otherwise and for MF_MIXED_TC);
  *   lanes            lanes per point, 1..32 and a power of two, at most the

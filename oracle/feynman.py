@@ -42,6 +42,7 @@ gauge invariance, Lorentz invariance, Bose symmetry and diagram counts.
 from __future__ import annotations
 
 import itertools
+import os
 import math
 from functools import lru_cache
 
@@ -221,6 +222,17 @@ def _unordered3(S):
         for B, C in _unordered2(BC):
             out.append((A, B, C))
     return out
+
+
+def _colour_gram_part(args):
+    """Sum over the given colour chunks of C^dagger C (see
+    Process.colour_matrix)."""
+    proc, chunks = args
+    G = np.zeros((len(proc.terms), len(proc.terms)), dtype=np.complex128)
+    for fixed in chunks:
+        Cc = proc._colour_columns(fixed)
+        G += Cc.conj().T @ Cc
+    return G
 
 
 class Process:
@@ -404,11 +416,18 @@ class Process:
                 while total > self.COLOUR_CHUNK // 4 and k < len(gl):
                     total //= 8
                     k += 1
-                G = np.zeros((len(self.terms), len(self.terms)), dtype=np.complex128)
-                for vals in itertools.product(range(8), repeat=k):
-                    Cc = self._colour_columns(dict(zip(gl[:k], vals)))
-                    G += Cc.conj().T @ Cc
-                self._G = G
+                chunks = [dict(zip(gl[:k], vals)) for vals in itertools.product(range(8), repeat=k)]
+                workers = int(os.environ.get("MF_ORACLE_WORKERS", "0")) or (os.cpu_count() or 1)
+                if workers > 1:
+                    # chunks shared out over spawned processes (one numpy
+                    # thread each); each returns the sum of its chunks
+                    import multiprocessing as mp
+                    parts = [chunks[w::workers] for w in range(workers)]
+                    with mp.get_context("spawn").Pool(workers) as pool:
+                        Gs = pool.map(_colour_gram_part, [(self, part) for part in parts if part])
+                    self._G = np.sum(Gs, axis=0)
+                else:
+                    self._G = _colour_gram_part((self, chunks))
         return self._G
 
     # ---------------------------------------------------------------- leading colour

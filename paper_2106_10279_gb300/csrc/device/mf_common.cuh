@@ -49,6 +49,19 @@ template <typename R> MF_DEV cx<R> cfma(cx<R> b, cx<R> c, cx<R> a) {
     return {a.re + b.re * c.re - b.im * c.im, a.im + b.re * c.im + b.im * c.re};
 }
 
+// Product with a factor whose phase class is known when the program is
+// generated: PH 1 a real factor (f.im == 0), PH 2 an imaginary one
+// (f.re == 0), PH 0 a general complex factor.  The couplings of the vertex
+// routines are real or imaginary in QCD (i g_s, g_s, -i g_s^2), which turns
+// their complex products into real-times-complex ones.
+template <int PH, typename R> MF_DEV cx<R> pmul(cx<R> f, cx<R> a) {
+    if constexpr (PH == 1) return {f.re * a.re, f.re * a.im};
+    else if constexpr (PH == 2) return {-(f.im * a.im), f.im * a.re};
+    else return f * a;
+}
+// the phase class of i f (or -i f) from that of f
+constexpr int rotate_phase(int ph) { return ph == 1 ? 2 : ph == 2 ? 1 : 0; }
+
 // Wavefunction: four complex components.  Its momentum (flowing into the
 // diagram through the legs it contains) is a signed sum of external momenta
 // known when the program is generated, and is formed where a routine needs it.

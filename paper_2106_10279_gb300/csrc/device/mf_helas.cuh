@@ -140,7 +140,8 @@ MF_DEV void qslash_row(const cx<R> *r, const R *q, R M, cx<R> *o) {
 }
 
 // ---------------------------------------------------------------- vertices
-template <typename R>
+// PH: the phase class of the coupling g (pmul); 0 keeps every product general.
+template <typename R, int PH = 0>
 MF_DEV cx<R> FFV_AMP(const W<R> &row, const W<R> &col, const W<R> &V, cx<R> g) {
     cx<R> t[4];
     vslash_col(V.c, col.c, t);
@@ -148,7 +149,7 @@ MF_DEV cx<R> FFV_AMP(const W<R> &row, const W<R> &col, const W<R> &V, cx<R> g) {
     s = cfma(row.c[1], t[1], s);
     s = cfma(row.c[2], t[2], s);
     s = cfma(row.c[3], t[3], s);
-    return g * s;
+    return pmul<PH>(g, s);
 }
 
 // Two amplitudes of a helicity pair that share everything but one external
@@ -159,7 +160,7 @@ struct A2 {
     cx<R> a, b;
 };
 
-template <typename R>
+template <typename R, int PH = 0>
 MF_DEV A2<R> FFV_AMP_R2(const W<R> &row_a, const W<R> &row_b, const W<R> &col, const W<R> &V, cx<R> g) {
     cx<R> t[4];
     vslash_col(V.c, col.c, t);
@@ -168,10 +169,10 @@ MF_DEV A2<R> FFV_AMP_R2(const W<R> &row_a, const W<R> &row_b, const W<R> &col, c
         sa = cfma(row_a.c[k], t[k], sa);
         sb = cfma(row_b.c[k], t[k], sb);
     }
-    return A2<R>{g * sa, g * sb};
+    return A2<R>{pmul<PH>(g, sa), pmul<PH>(g, sb)};
 }
 
-template <typename R>
+template <typename R, int PH = 0>
 MF_DEV A2<R> FFV_AMP_C2(const W<R> &row, const W<R> &col_a, const W<R> &col_b, const W<R> &V, cx<R> g) {
     cx<R> t[4];
     vslash_row(row.c, V.c, t);
@@ -180,22 +181,22 @@ MF_DEV A2<R> FFV_AMP_C2(const W<R> &row, const W<R> &col_a, const W<R> &col_b, c
         sa = cfma(t[k], col_a.c[k], sa);
         sb = cfma(t[k], col_b.c[k], sb);
     }
-    return A2<R>{g * sa, g * sb};
+    return A2<R>{pmul<PH>(g, sa), pmul<PH>(g, sb)};
 }
 
 // P: momentum of the new current (into the diagram through its legs)
-template <typename R>
+template <typename R, int PH = 0>
 MF_DEV W<R> FFV_FIN(const W<R> &col, const W<R> &V, cx<R> g, R M, R inv_den, const R *P) {
     W<R> w;
     cx<R> t[4], u[4];
     vslash_col(V.c, col.c, t);
     qslash_col(P, M, t, u);
     cx<R> f = mul_i(g) * inv_den;
-    for (int k = 0; k < 4; ++k) w.c[k] = f * u[k];
+    for (int k = 0; k < 4; ++k) w.c[k] = pmul<rotate_phase(PH)>(f, u[k]);
     return w;
 }
 
-template <typename R>
+template <typename R, int PH = 0>
 MF_DEV W<R> FFV_FOUT(const W<R> &row, const W<R> &V, cx<R> g, R M, R inv_den, const R *P) {
     W<R> w;
     R q[4] = {-P[0], -P[1], -P[2], -P[3]};
@@ -203,11 +204,11 @@ MF_DEV W<R> FFV_FOUT(const W<R> &row, const W<R> &V, cx<R> g, R M, R inv_den, co
     vslash_row(row.c, V.c, t);
     qslash_row(t, q, M, u);
     cx<R> f = mul_i(g) * inv_den;
-    for (int k = 0; k < 4; ++k) w.c[k] = f * u[k];
+    for (int k = 0; k < 4; ++k) w.c[k] = pmul<rotate_phase(PH)>(f, u[k]);
     return w;
 }
 
-template <typename R>
+template <typename R, int PH = 0>
 MF_DEV W<R> FFV_VEC(const W<R> &row, const W<R> &col, cx<R> g, R inv_den) {
     W<R> w;
     const cx<R> *a = row.c, *s = col.c;
@@ -216,12 +217,13 @@ MF_DEV W<R> FFV_VEC(const W<R> &row, const W<R> &col, cx<R> g, R inv_den) {
     cx<R> j2 = mul_i(a[1] * s[2] - a[0] * s[3] + a[2] * s[1] - a[3] * s[0]);
     cx<R> j3 = a[0] * s[2] - a[1] * s[3] - a[2] * s[0] + a[3] * s[1];
     cx<R> f = mul_mi(g) * inv_den;
-    w.c[0] = f * j0; w.c[1] = f * j1; w.c[2] = f * j2; w.c[3] = f * j3;
+    constexpr int F = rotate_phase(PH);
+    w.c[0] = pmul<F>(f, j0); w.c[1] = pmul<F>(f, j1); w.c[2] = pmul<F>(f, j2); w.c[3] = pmul<F>(f, j3);
     return w;
 }
 
 // kA, kB, kC: momenta into the vertex along A, B, C
-template <typename R>
+template <typename R, int PH = 0>
 MF_DEV cx<R> VVV_AMP(const W<R> &A, const W<R> &B, const W<R> &Cv, const R *kA, const R *kB, const R *kC,
                      cx<R> g) {
     R d12[4], d23[4], d31[4];
@@ -233,10 +235,10 @@ MF_DEV cx<R> VVV_AMP(const W<R> &A, const W<R> &B, const W<R> &Cv, const R *kA, 
     cx<R> r = mdot(A.c, B.c) * mdot(d12, Cv.c);
     r = cfma(mdot(B.c, Cv.c), mdot(d23, A.c), r);
     r = cfma(mdot(Cv.c, A.c), mdot(d31, B.c), r);
-    return g * r;
+    return pmul<PH>(g, r);
 }
 
-template <typename R>
+template <typename R, int PH = 0>
 MF_DEV W<R> VVV_VEC(const W<R> &A, const W<R> &B, const R *kA, const R *kB, cx<R> g, R inv_den) {
     W<R> w;
     R d12[4], d23[4], d31[4];
@@ -254,21 +256,21 @@ MF_DEV W<R> VVV_VEC(const W<R> &A, const W<R> &B, const R *kA, const R *kB, cx<R
         cx<R> v = ab * d12[k];
         v = cfma(B.c[k], fb, v);
         v = cfma(A.c[k], fa, v);
-        w.c[k] = f * v;
+        w.c[k] = pmul<rotate_phase(PH)>(f, v);
     }
     return w;
 }
 
-template <typename R, int S>
+template <typename R, int S, int PH = 0>
 MF_DEV cx<R> VVVV_AMP(const W<R> &A, const W<R> &B, const W<R> &Cv, const W<R> &D, cx<R> g) {
     cx<R> r;
     if (S == 1) r = mdot(A.c, Cv.c) * mdot(B.c, D.c) - mdot(A.c, D.c) * mdot(B.c, Cv.c);
     else if (S == 2) r = mdot(A.c, B.c) * mdot(Cv.c, D.c) - mdot(A.c, D.c) * mdot(B.c, Cv.c);
     else r = mdot(A.c, B.c) * mdot(Cv.c, D.c) - mdot(A.c, Cv.c) * mdot(B.c, D.c);
-    return g * r;
+    return pmul<PH>(g, r);
 }
 
-template <typename R, int S>
+template <typename R, int S, int PH = 0>
 MF_DEV W<R> VVVV_VEC(const W<R> &A, const W<R> &B, const W<R> &Cv, cx<R> g, R inv_den) {
     W<R> w;
     cx<R> f = mul_mi(g) * inv_den;
@@ -277,7 +279,7 @@ MF_DEV W<R> VVVV_VEC(const W<R> &A, const W<R> &B, const W<R> &Cv, cx<R> g, R in
     if (S == 1) { x = mdot(A.c, Cv.c); X = &B; y = mdot(B.c, Cv.c); Y = &A; }
     else if (S == 2) { x = mdot(A.c, B.c); X = &Cv; y = mdot(B.c, Cv.c); Y = &A; }
     else { x = mdot(A.c, B.c); X = &Cv; y = mdot(A.c, Cv.c); Y = &B; }
-    for (int k = 0; k < 4; ++k) w.c[k] = f * (x * X->c[k] - y * Y->c[k]);
+    for (int k = 0; k < 4; ++k) w.c[k] = pmul<rotate_phase(PH)>(f, x * X->c[k] - y * Y->c[k]);
     return w;
 }
 
@@ -290,43 +292,45 @@ MF_DEV W<R> VVVV_VEC(const W<R> &A, const W<R> &B, const W<R> &Cv, cx<R> g, R in
 #else
 #define MF_NOINL inline
 #endif
-template <typename R>
+template <typename R, int PH = 0>
 MF_NOINL W<R> nFFV_FIN(W<R> col, W<R> V, cx<R> g, R M, R inv_den, R p0, R p1, R p2, R p3) {
     const R P[4] = {p0, p1, p2, p3};
-    return FFV_FIN<R>(col, V, g, M, inv_den, P);
+    return FFV_FIN<R, PH>(col, V, g, M, inv_den, P);
 }
-template <typename R>
+template <typename R, int PH = 0>
 MF_NOINL W<R> nFFV_FOUT(W<R> row, W<R> V, cx<R> g, R M, R inv_den, R p0, R p1, R p2, R p3) {
     const R P[4] = {p0, p1, p2, p3};
-    return FFV_FOUT<R>(row, V, g, M, inv_den, P);
+    return FFV_FOUT<R, PH>(row, V, g, M, inv_den, P);
 }
-template <typename R>
-MF_NOINL W<R> nFFV_VEC(W<R> row, W<R> col, cx<R> g, R inv_den) { return FFV_VEC<R>(row, col, g, inv_den); }
-template <typename R>
+template <typename R, int PH = 0>
+MF_NOINL W<R> nFFV_VEC(W<R> row, W<R> col, cx<R> g, R inv_den) { return FFV_VEC<R, PH>(row, col, g, inv_den); }
+template <typename R, int PH = 0>
 MF_NOINL W<R> nVVV_VEC(W<R> A, W<R> B, R a0, R a1, R a2, R a3, R b0, R b1, R b2, R b3, cx<R> g, R inv_den) {
     const R kA[4] = {a0, a1, a2, a3}, kB[4] = {b0, b1, b2, b3};
-    return VVV_VEC<R>(A, B, kA, kB, g, inv_den);
+    return VVV_VEC<R, PH>(A, B, kA, kB, g, inv_den);
 }
-template <typename R, int S>
-MF_NOINL W<R> nVVVV_VEC(W<R> A, W<R> B, W<R> Cv, cx<R> g, R inv_den) { return VVVV_VEC<R, S>(A, B, Cv, g, inv_den); }
-template <typename R>
-MF_NOINL cx<R> nFFV_AMP(W<R> row, W<R> col, W<R> V, cx<R> g) { return FFV_AMP<R>(row, col, V, g); }
-template <typename R>
+template <typename R, int S, int PH = 0>
+MF_NOINL W<R> nVVVV_VEC(W<R> A, W<R> B, W<R> Cv, cx<R> g, R inv_den) {
+    return VVVV_VEC<R, S, PH>(A, B, Cv, g, inv_den);
+}
+template <typename R, int PH = 0>
+MF_NOINL cx<R> nFFV_AMP(W<R> row, W<R> col, W<R> V, cx<R> g) { return FFV_AMP<R, PH>(row, col, V, g); }
+template <typename R, int PH = 0>
 MF_NOINL A2<R> nFFV_AMP_R2(W<R> row_a, W<R> row_b, W<R> col, W<R> V, cx<R> g) {
-    return FFV_AMP_R2<R>(row_a, row_b, col, V, g);
+    return FFV_AMP_R2<R, PH>(row_a, row_b, col, V, g);
 }
-template <typename R>
+template <typename R, int PH = 0>
 MF_NOINL A2<R> nFFV_AMP_C2(W<R> row, W<R> col_a, W<R> col_b, W<R> V, cx<R> g) {
-    return FFV_AMP_C2<R>(row, col_a, col_b, V, g);
+    return FFV_AMP_C2<R, PH>(row, col_a, col_b, V, g);
 }
-template <typename R>
+template <typename R, int PH = 0>
 MF_NOINL cx<R> nVVV_AMP(W<R> A, W<R> B, W<R> Cv, R a0, R a1, R a2, R a3, R b0, R b1, R b2, R b3, R c0, R c1, R c2,
                         R c3, cx<R> g) {
     const R kA[4] = {a0, a1, a2, a3}, kB[4] = {b0, b1, b2, b3}, kC[4] = {c0, c1, c2, c3};
-    return VVV_AMP<R>(A, B, Cv, kA, kB, kC, g);
+    return VVV_AMP<R, PH>(A, B, Cv, kA, kB, kC, g);
 }
-template <typename R, int S>
-MF_NOINL cx<R> nVVVV_AMP(W<R> A, W<R> B, W<R> Cv, W<R> D, cx<R> g) { return VVVV_AMP<R, S>(A, B, Cv, D, g); }
+template <typename R, int S, int PH = 0>
+MF_NOINL cx<R> nVVVV_AMP(W<R> A, W<R> B, W<R> Cv, W<R> D, cx<R> g) { return VVVV_AMP<R, S, PH>(A, B, Cv, D, g); }
 #undef MF_NOINL
 
 }  // namespace mf

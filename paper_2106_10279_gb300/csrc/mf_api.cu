@@ -1022,6 +1022,7 @@ int shell_from_desc(const mf_process_desc *d, mf_process &p) {
     p.masses.assign(d->masses, d->masses + d->n_masses);
     p.ops.assign(d->ops, d->ops + d->n_ops);
     if (d->n_terms > 0) p.terms.assign(d->terms, d->terms + d->n_terms);
+    p.couplings.assign(d->couplings, d->couplings + 2 * d->n_couplings);
     p.n_jamp = d->n_jamp;
     p.colour_num.assign(d->colour_num, d->colour_num + d->n_jamp * d->n_jamp);
     p.colour_den = d->colour_den;

@@ -41,6 +41,19 @@ double routine_flops(int r) {
     }
 }
 
+// FLOPs of one op's routine as emitted: a coupling that is real or
+// imaginary (pmul) turns each product with the coupling factor into a
+// real-times-complex one, 4 FLOPs fewer (four per current, one per
+// amplitude)
+double op_flops(const mf_process &p, const mf_op &op) {
+    double f = routine_flops(op.routine);
+    const int c = op.coupling;
+    if (op.kind == MF_OP_EXT || c < 0 || 2 * c + 1 >= (int)p.couplings.size()) return f;
+    const double re = p.couplings[2 * c], im = p.couplings[2 * c + 1];
+    if (re != 0.0 && im != 0.0) return f;
+    return f - (op.kind == MF_OP_CUR ? 16.0 : 4.0);
+}
+
 // an amplitude's colour coefficients as emitted: a complex add for +-1 and
 // +-i, a complex multiply-add otherwise
 double term_flops(const mf_process &p, const mf_op &op) {
@@ -229,6 +242,15 @@ bool large_program(const mf_process &p) {
 // shared by a pair of helicities differing only there; lowest index on
 // ties), or -1 if no current is independent of every leg.
 int pair_leg(const mf_process &p) {
+    // no pair program when the option turns pairs off, and by default for
+    // programs above 1.5e5 FLOPs per helicity (gg -> tt~ggg: 3.7e5), whose
+    // single-helicity program alone takes minutes to compile
+    if (p.opt.helicity_pairs == 0) return -1;
+    if (p.opt.helicity_pairs < 0) {
+        double f = 0.0;
+        for (const mf_op &op : p.ops) f += routine_flops(op.routine);
+        if (f >= 1.5e5) return -1;
+    }
     int best = -1;
     double bf = 0.0;
     for (int l = 0; l < p.n_legs; ++l) {
@@ -455,6 +477,13 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
     int sync_every = large_program(p) ? 16 : 0;
     if (p.opt.sync_every >= 0) sync_every = p.opt.sync_every;
     auto M = [&](int id) { return id >= 0 ? "mass[" + std::to_string(id) + "]" : std::string("R(0)"); };
+    // the phase class of coupling c for the routines' products (pmul): 1
+    // real, 2 imaginary, 0 general
+    auto PH = [&](int c) {
+        if (c < 0 || 2 * c + 1 >= (int)p.couplings.size()) return std::string("0");
+        const double re = p.couplings[2 * c], im = p.couplings[2 * c + 1];
+        return std::to_string(im == 0.0 ? 1 : re == 0.0 ? 2 : 0);
+    };
     auto emit_program = [&](const bool pair) {
     auto dep = [&](int k) { return pair && (p.ops[k].kind == MF_OP_AMP || (mask[k] >> L & 1)); };
     auto nm = [&](int k, const char *sfx) { return "w" + std::to_string(k) + (dep(k) ? sfx : ""); };
@@ -495,21 +524,25 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
             case MF_R_FFV_FIN:
             case MF_R_FFV_FOUT:
                 o << mom(mask[k], "P");
-                o << "    " << wk << " = " << rt(op.routine == MF_R_FFV_FIN ? "FFV_FIN" : "FFV_FOUT") << "<R>("
+                o << "    " << wk << " = " << rt(op.routine == MF_R_FFV_FIN ? "FFV_FIN" : "FFV_FOUT") << "<R, "
+                  << PH(op.coupling) << ">("
                   << in(0) << ", " << in(1) << ", " << g << ", " << M(op.mass_id) << ", " << den << ", "
                   << a4r("FFV_FIN", "P") << ");\n";
                 break;
             case MF_R_FFV_VEC:
-                o << "    " << wk << " = " << rt("FFV_VEC") << "<R>(" << in(0) << ", " << in(1) << ", " << g << ", "
+                o << "    " << wk << " = " << rt("FFV_VEC") << "<R, " << PH(op.coupling) << ">(" << in(0) << ", "
+                  << in(1) << ", " << g << ", "
                   << den << ");\n";
                 break;
             case MF_R_VVV_VEC:
                 o << mom(mask[op.in[0]], "kA") << mom(mask[op.in[1]], "kB");
-                o << "    " << wk << " = " << rt("VVV_VEC") << "<R>(" << in(0) << ", " << in(1) << ", "
+                o << "    " << wk << " = " << rt("VVV_VEC") << "<R, " << PH(op.coupling) << ">(" << in(0) << ", "
+                  << in(1) << ", "
                   << a4r("VVV_VEC", "kA") << ", " << a4r("VVV_VEC", "kB") << ", " << g << ", " << den << ");\n";
                 break;
             default:
-                o << "    " << wk << " = " << rt("VVVV_VEC") << "<R, " << (op.routine - MF_R_VVVV1_VEC + 1) << ">("
+                o << "    " << wk << " = " << rt("VVVV_VEC") << "<R, " << (op.routine - MF_R_VVVV1_VEC + 1) << ", "
+                  << PH(op.coupling) << ">("
                   << in(0) << ", " << in(1) << ", " << in(2) << ", " << g << ", " << den << ");\n";
                 break;
         }
@@ -551,15 +584,18 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
         o << "    const cx<R> a = ";
         switch (op.routine) {
             case MF_R_FFV_AMP:
-                o << rt("FFV_AMP") << "<R>(" << in(0) << ", " << in(1) << ", " << in(2) << ", " << g << ")";
+                o << rt("FFV_AMP") << "<R, " << PH(op.coupling) << ">(" << in(0) << ", " << in(1) << ", " << in(2)
+                  << ", " << g << ")";
                 break;
             case MF_R_VVV_AMP:
-                o << rt("VVV_AMP") << "<R>(" << in(0) << ", " << in(1) << ", " << in(2) << ", "
+                o << rt("VVV_AMP") << "<R, " << PH(op.coupling) << ">(" << in(0) << ", " << in(1) << ", " << in(2)
+                  << ", "
                   << a4r("VVV_AMP", "kA") << ", " << a4r("VVV_AMP", "kB") << ", " << a4r("VVV_AMP", "kC") << ", " << g
                   << ")";
                 break;
             default:
-                o << rt("VVVV_AMP") << "<R, " << (op.routine - MF_R_VVVV1_AMP + 1) << ">(" << in(0) << ", " << in(1)
+                o << rt("VVVV_AMP") << "<R, " << (op.routine - MF_R_VVVV1_AMP + 1) << ", " << PH(op.coupling) << ">("
+                  << in(0) << ", " << in(1)
                   << ", " << in(2) << ", " << in(3) << ", " << g << ")";
         }
         o << ";\n";
@@ -581,7 +617,7 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
         std::string g = "cpl[" + std::to_string(op.coupling) + "]";
         const std::string r = rt(dq == 0 ? "FFV_AMP_R2" : "FFV_AMP_C2");
         const std::string v = "w" + std::to_string(op.in[dq]);
-        o << "  {\n    const A2<R> ab = " << r << "<R>(";
+        o << "  {\n    const A2<R> ab = " << r << "<R, " << PH(op.coupling) << ">(";
         if (dq == 0) o << v << ", " << v << "_b, w" << op.in[1];
         else o << "w" << op.in[0] << ", " << v << ", " << v << "_b";
         o << ", w" << op.in[2] << ", " << g << ");\n";
@@ -613,18 +649,21 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
         const bool rdep = pair && dep(op0.in[0]), cdep = pair && dep(op0.in[1]);
         const std::string row = "w" + std::to_string(op0.in[0]), col = "w" + std::to_string(op0.in[1]);
         if (!pair) {
-            o << "    const cx<R> a = " << rt("FFV_AMP") << "<R>(" << row << ", " << col << ", vs, " << g << ");\n";
+            o << "    const cx<R> a = " << rt("FFV_AMP") << "<R, " << PH(op0.coupling) << ">(" << row << ", " << col
+              << ", vs, " << g << ");\n";
             emit_terms(op0, "J", "a");
         } else if (!vdep && rdep != cdep) {
-            o << "    const A2<R> ab = " << rt(rdep ? "FFV_AMP_R2" : "FFV_AMP_C2") << "<R>(";
+            o << "    const A2<R> ab = " << rt(rdep ? "FFV_AMP_R2" : "FFV_AMP_C2") << "<R, " << PH(op0.coupling) << ">(";
             if (rdep) o << row << ", " << row << "_b, " << col;
             else o << row << ", " << col << ", " << col << "_b";
             o << ", vs, " << g << ");\n";
             emit_terms(op0, "J", "ab.a");
             emit_terms(op0, "Jb", "ab.b");
         } else {
-            o << "    const cx<R> a = " << rt("FFV_AMP") << "<R>(" << row << ", " << col << ", vs, " << g << ");\n";
-            o << "    const cx<R> b = " << rt("FFV_AMP") << "<R>(" << nm(op0.in[0], "_b") << ", " << nm(op0.in[1], "_b")
+            o << "    const cx<R> a = " << rt("FFV_AMP") << "<R, " << PH(op0.coupling) << ">(" << row << ", " << col
+              << ", vs, " << g << ");\n";
+            o << "    const cx<R> b = " << rt("FFV_AMP") << "<R, " << PH(op0.coupling) << ">(" << nm(op0.in[0], "_b")
+              << ", " << nm(op0.in[1], "_b")
               << ", " << (vdep ? "vs_b" : "vs") << ", " << g << ");\n";
             emit_terms(op0, "J", "a");
             emit_terms(op0, "Jb", "b");
@@ -757,10 +796,10 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
     // colour coefficients, and the colour sum
     double alg = 0.0;
     for (const mf_op &op : p.ops)
-        if (op.kind != MF_OP_AMP) alg += routine_flops(op.routine);
+        if (op.kind != MF_OP_AMP) alg += op_flops(p, op);
     for (const AmpUnit &un : units) {
         const mf_op &op0 = p.ops[un.ops[0]];
-        alg += routine_flops(op0.routine) + 8.0 * (un.ops.size() - 1) + term_flops(p, op0);
+        alg += op_flops(p, op0) + 8.0 * (un.ops.size() - 1) + term_flops(p, op0);
     }
     alg += colour_sum_flops(p);
     info.flops_per_hel = alg;
@@ -775,7 +814,7 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
         double fp = 0.0;
         auto dep_wf = [&](int i) { return p.ops[i].kind != MF_OP_AMP && (mask[i] >> L & 1); };
         for (size_t k = 0; k < p.ops.size(); ++k)
-            if (p.ops[k].kind != MF_OP_AMP) fp += routine_flops(p.ops[k].routine) * (dep_wf((int)k) ? 2 : 1);
+            if (p.ops[k].kind != MF_OP_AMP) fp += op_flops(p, p.ops[k]) * (dep_wf((int)k) ? 2 : 1);
         for (const AmpUnit &un : units) {
             const mf_op &op0 = p.ops[un.ops[0]];
             bool vdep = false;
@@ -790,7 +829,9 @@ std::string generate_source(const mf_process &p, int precision, int block, int h
                     if (op0.in[q] >= 0 && dep_wf(op0.in[q])) { ++ndep; dq = q; }
                 shared = op0.routine == MF_R_FFV_AMP && ndep == 1 && dq <= 1;
             }
-            fp += shared ? 136.0 : 2.0 * routine_flops(op0.routine);
+            // (the shared form's two products with the coupling: 2 x 4 FLOPs
+            // fewer for a real or imaginary coupling, as op_flops)
+            fp += shared ? 136.0 - 2.0 * (routine_flops(op0.routine) - op_flops(p, op0)) : 2.0 * op_flops(p, op0);
             fp += 2.0 * term_flops(p, op0);
         }
         fp += 2.0 * colour_sum_flops(p);

@@ -1,0 +1,66 @@
+"""gg -> tt~ggg (1240 diagrams, 128 helicities, 120 colour flows) on the GPU
+against the oracle, per point, in FP64 and in mixed precision.
+
+Opt-in (MF_HEAVY_TESTS=1): building its kernels takes about five minutes per
+precision (the single-helicity program alone is 3712 operations) and the
+oracle's colour matrix is a sum over 294912 colour assignments of 1890
+terms, spread over spawned processes on the host cores.  The same
+tolerances as the other workloads: FP64 within 1e-12 plus 64 eps times the
+oracle's condition number of the point, mixed within 1e-5 (median) and 1e-3
+(max); identical zero patterns.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from _tolerance import fp64_tolerance, relerr
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(os.environ.get("MF_HEAVY_TESTS") != "1",
+                                 reason="gg->tt~ggg kernels take minutes to build: set MF_HEAVY_TESTS=1")]
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2106_10279_gb300 import api
+    return torch, api
+
+
+def test_gg_ttxggg_matches_the_oracle(env, capsys):
+    torch, api = env
+    from oracle.integrand import Integrand, oracle_process
+    wl = W.GG_TTXGGG
+    proc = api.Process.from_workload(wl)
+    info = proc.info
+    assert info["n_jamp"] == 120 and info["n_hel_all"] == 128 and proc.n_diagrams == 1240
+    x = W.uniform_points(wl.ndim, 40, 4242)
+    xd = torch.from_numpy(x).cuda()
+    f64 = proc.integrand(xd, "fp64").cpu().numpy()
+    fmx = proc.integrand(xd, "mixed").cpu().numpy()
+    I = Integrand(wl, process=oracle_process(wl))
+    ref, tol = fp64_tolerance(I, x)
+    assert np.array_equal(f64 == 0, ref == 0)
+    nz = ref != 0
+    assert nz.sum() >= 16
+    r64 = relerr(f64, ref)[nz]
+    rmx = relerr(fmx, ref)[nz]
+    with capsys.disabled():
+        print(f"gg->tt~ggg: {nz.sum()} points, FP64 max {r64.max():.2e} median {np.median(r64):.1e}; "
+              f"mixed median {np.median(rmx):.1e} max {rmx.max():.1e}")
+    assert np.all(relerr(f64, ref) <= tol)
+    assert np.median(rmx) <= 1e-5 and rmx.max() <= 1e-3
+    # a Vegas pass of the integrand kernel
+    v = api.Vegas(wl.ndim)
+    r = v.iterate(proc, 200_000, 3, "mixed")
+    assert r["n_nonzero"] > 0 and np.isfinite(r["integral"]) and r["integral"] > 0
+    with capsys.disabled():
+        ms = api.mf_process_last_kernel_ms(proc.handle)
+        print(f"gg->tt~ggg: Vegas pass of 2e5 points {ms:.1f} ms ({2e5 / (ms / 1e3):.3g} points/s), "
+              f"sigma {r['integral']:.4g} +- {r['error']:.2g} pb; launch {proc.kernel_info('mixed')}")

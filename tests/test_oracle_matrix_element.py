@@ -304,3 +304,39 @@ def test_colour_sampled_estimate_averages_to_the_colour_sum(name):
     nz = f != 0
     assert np.allclose(tot[nz], f[nz], rtol=1e-13, atol=0)
     assert np.allclose(totl[nz], lc[nz], rtol=1e-13, atol=0)
+
+
+def test_chunked_colour_matrix_equals_the_one_pass_sum():
+    # the colour matrix summed over chunks of colour assignments (the first
+    # gluon legs' colours held fixed in turn), as the oracle does for seven
+    # legs, against the sum over the whole colour tensor
+    import workloads as W
+    from oracle.integrand import oracle_process
+    full = oracle_process(W.GG_TTXG).colour_matrix()
+    chunked = oracle_process(W.GG_TTXG)
+    chunked.COLOUR_CHUNK = 4096                # forces chunks of one or two fixed gluon colours
+    G = chunked.colour_matrix()
+    assert np.allclose(G, full, rtol=0, atol=1e-12 * np.abs(full).max())
+
+
+def test_seven_leg_oracle_counts_diagrams_and_is_gauge_invariant():
+    # gg -> tt~ggg: 1240 Feynman diagrams; with a gluon's polarisation
+    # replaced by its momentum every colour-dressed amplitude vanishes (here
+    # on the colour assignments with the incoming gluons' colours fixed,
+    # 4608 of the 294912: the whole colour tensor is never built)
+    import workloads as W
+    from oracle.integrand import oracle_process
+    wl = W.GG_TTXGGG
+    proc = oracle_process(wl)
+    assert len(proc.diagrams) == 1240
+    I = Integrand(wl, process=proc)
+    x = W.uniform_points(wl.ndim, 8, 5)
+    p, s_hat, x1, x2, jx, w, ok = I.kinematics(x)
+    p = p[ok & I.cuts(p)][:2]
+    Cc = proc._colour_columns({0: 3, 1: 5})
+    hels = proc.helicities()
+    for hi in (17, 100):
+        A = Cc @ proc.amplitudes(p, hels[hi], {})
+        for leg in (0, 1, 4, 5, 6):
+            Ag = Cc @ proc.amplitudes(p, hels[hi], {}, gauge_leg=leg)
+            assert np.abs(Ag).max() < 1e-12 * np.abs(A).max(), (hi, leg)
