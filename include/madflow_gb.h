@@ -226,7 +226,10 @@ typedef struct mf_process mf_process;   /* opaque, library-owned */
 typedef struct mf_vegas mf_vegas;       /* opaque, library-owned */
 typedef struct mf_batch mf_batch;       /* opaque, library-owned */
 
-/* mf_create_process: validate and deep-copy *desc, drop vanishing helicities,
+/* mf_create_process (the process a MadFlow run integrates: the Matrix class
+ * of Sec. 2.3 -- external states, vertices and the colour matrix of the
+ * helicity-amplitude evaluation -- with the PDF tables and cuts of the
+ * integrand of Fig. 1): validate and deep-copy *desc, drop vanishing helicities,
  * generate CUDA source specialised to the diagram program and compile it for
  * sm_103a at run time (NVRTC; compiled binaries are kept for the life of the
  * process, and on disk when the environment variable MF_JIT_CACHE names a
@@ -571,9 +574,11 @@ mf_status mf_process_max_weight(mf_process *p, double *w_max, void *stream);
 mf_status mf_vegas_iterate_static(mf_vegas *v, mf_process *p, int64_t n_events, uint64_t seed,
                                   mf_precision prec, int32_t refine, mf_iter_result *out, void *stream);
 
-/* ---- Checkpoint of a grid: edges, last histogram and counts, and the
- * (I_k, sigma_k) of the iterations so far, so that a run resumes with the same
- * combination.  mf_vegas_save with buf == NULL stores the size needed in *len;
+/* ---- Checkpoint of a grid (the Vegas state of Sec. 2.2 that VegasFlow
+ * carries from one iteration to the next: the adapted bin edges, and the
+ * per-iteration estimates that the final result combines): edges, last
+ * histogram and counts, and the (I_k, sigma_k) of the iterations so far, so
+ * that a run resumes with the same combination.  mf_vegas_save with buf == NULL stores the size needed in *len;
  * otherwise *len is the capacity on entry and the size written on return
  * (MF_EINVAL if too small).  mf_vegas_load checks the record (tag, shape,
  * size, edges) and restores it into a grid of the same ndim and nbins. */

@@ -93,3 +93,38 @@ def test_rejects_bad_observables(env):
         with pytest.raises(RuntimeError):
             api.observables(grid, proc, 1000, 1, bad, precision="fp64")
     assert L.MF_MAX_OBSERVABLES == 4
+
+
+def test_histograms_of_gg_ttxgg_match_the_oracle(oracle_processes):
+    # the headline process: a final gluon's pT and pseudorapidity and the
+    # top's rapidity, 4000 Philox points (the cuts leave about two thirds)
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2106_10279_gb300 import api
+    from oracle import observables as ob
+    from oracle import unweight as uw
+    from oracle import vegas as ov
+    from oracle.integrand import Integrand
+    from oracle.philox import vegas_uniforms
+    wl = W.GG_TTXGG
+    n = 4000
+    obs = [("pt", 4, 20, 0.0, 400.0), ("y", 2, 16, -4.0, 4.0), ("eta", 5, 16, -5.0, 5.0)]
+    I = Integrand(wl, process=oracle_processes("gg_ttxgg"))
+    y = vegas_uniforms(SEED, 0, 0, 0, n, wl.ndim)
+    x, jac, _ = ov.vegas_map(ov.uniform_grid(wl.ndim, wl.n_bins), y)
+    w = I(x) * jac
+    p, s_hat, x1, x2, jx, wps, ok = I.kinematics(x)
+    passing = ok & I.cuts(p)
+    kinds = {"pt": ob.PT, "y": ob.RAPIDITY, "eta": ob.PSEUDORAPIDITY}
+    ref = ob.histograms(uw.lab_frame(p, x1, x2), passing, w, [(kinds[k], l, nb, lo, hi) for k, l, nb, lo, hi in obs])
+    proc = api.Process.from_workload(wl)
+    for prec, tol in (("fp64", 1e-10), ("mixed", 1e-5)):
+        got = api.observables(api.Vegas(wl.ndim), proc, n, SEED, obs, precision=prec)
+        for (s, e, c), (rs, re, rc), o in zip(got, ref, obs):
+            assert np.array_equal(c, rc), (prec, o)
+            nz = rs != 0
+            assert np.all(s[~nz] == 0)
+            assert np.max(np.abs(s[nz] / rs[nz] - 1)) <= tol, (prec, o)
