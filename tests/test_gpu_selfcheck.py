@@ -1,13 +1,13 @@
 """The compile-time self-check of the helicity-pair program.
 
-gg -> tt~g generated with amplitude units (an option, off by default for
-this short program): its FP64 pair program, built by the device assembler
-at its default optimisation level, was wrong at every point while the same
+gg -> tt~g generated with amplitude units (the default) and the searched
+amplitude order: its FP64 pair program, built by the device assembler at
+its default optimisation level, was wrong at every point while the same
 source at levels 0 and 1, the host build and every other program form were
 right.  The create-time check compares the pair program with the
 single-helicity program of the same kernel and rebuilds the kernel at a
-lower level when they disagree; the process then matches the oracle and the
-default process.
+lower level when they disagree; the process then matches the oracle and a
+process without units.
 """
 import numpy as np
 import pytest
@@ -38,7 +38,7 @@ def test_units_in_short_programs_give_correct_values(env, oracle_processes, opti
     x = W.uniform_points(wl.ndim, 600, 71)
     xd = torch.from_numpy(x).cuda()
     p = api.Process.from_workload(wl, options=options)
-    default = api.Process.from_workload(wl)
+    default = api.Process.from_workload(wl, options={"amplitude_units": 0})
     f64 = p.integrand(xd, "fp64").cpu().numpy()
     ref, tol = fp64_tolerance(Integrand(wl, process=oracle_processes("gg_ttxg")), x)
     assert np.array_equal(f64 == 0, ref == 0)
