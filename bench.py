@@ -31,8 +31,9 @@ METRIC = "events/s of gg→tt̄g(g) LO integrand: mixed/batched vs FP64 at ≤1e
 # DRAM bytes per point of the fused integrand kernel, mixed precision:
 # dram__bytes_read.sum + dram__bytes_write.sum of a one-pass ncu capture of
 # one full-size 4e7-point gg->tt~gg iteration divided by its points (the
-# capture's kernel is the one built from this source)
-KERNEL_DRAM_BYTES_PER_POINT = {("gg_ttxgg", "mixed"): (144.32e6 + 22.65e9) / 4e7}
+# capture's kernel is the one built from this source: vertex routines
+# specialised on their couplings' phase)
+KERNEL_DRAM_BYTES_PER_POINT = {("gg_ttxgg", "mixed"): (92887552 + 15598926592) / 4e7}
 WORKLOAD = "gg_ttxgg"
 # FP64 FLOPs per point executed by the gradient kernel (2 x DFMA + DADD +
 # DMUL thread instructions of one ncu capture divided by its points)
@@ -472,6 +473,29 @@ def run_native(args):
                                       [nb_ev[i] for i in heavy], 4242, "mixed", True, stream)
             return a_ + b_
         rate_split, _ = timed(split)
+        # the same five subprocesses at 1/1000 of the points (an iteration of
+        # 4e4 points: latency-bound, where one launch and one graph replay
+        # per iteration count)
+        small = [max(1024, e // 1000) for e in nb_ev]
+        gs_s = [api.Vegas(p.ndim) for p in procs]
+        gb_s = [api.Vegas(p.ndim) for p in procs]
+        gg_s = [api.Vegas(p.ndim) for p in procs]
+
+        def timed_small(run, reps=20):
+            for _ in range(3):
+                run()
+            torch.cuda.synchronize()
+            t0_ = time.perf_counter()
+            for _ in range(reps):
+                run()
+            torch.cuda.synchronize()
+            return sum(small) * reps / (time.perf_counter() - t0_)
+        small_rates = {
+            "separate_launches": timed_small(lambda: api.mf_vegas_iterate([g.handle for g in gs_s],
+                                                                          [p.handle for p in procs], small, 4343,
+                                                                          "mixed", True, stream)),
+            "batch": timed_small(lambda: bt.iterate(gb_s, small, 4343, True, stream)),
+            "graph_replay": timed_small(lambda: bt.iterate(gg_s, small, 4343, True, stream, graph=True))}
         batch = {"workload": "mixed batch " + ", ".join(f"{n} {e:.0e}" for n, e in W.MIXED_BATCH),
                  "value": rate_b, "unit": "events/s", "separate_launches": rate_s, "graph_replay": rate_g,
                  "light_batch_plus_heavy_alone": rate_split,
@@ -479,7 +503,9 @@ def run_native(args):
                  "same_sigma_as_separate": all(a["sigma"] == b["sigma"] for a, b in zip(res_b, res_s)),
                  "same_sigma_graph": all(a["sigma"] == b["sigma"] for a, b in zip(res_b, res_g)),
                  "kernel_ms": bt.info()["last_kernel_ms"], "registers": bt.info().get("regs"),
-                 "light_batch_registers": bt_l.info().get("regs")}
+                 "light_batch_registers": bt_l.info().get("regs"),
+                 "small_iterations": {"points": small, "unit": "events/s (host wall clock, synchronous calls)",
+                                      **small_rates}}
 
     # the gradient kernel (mf_grad: f, df/dm_t, df/dalpha_s, df/dx in FP64) on
     # uniform points of the same process: points/s and, from the FP64
