@@ -69,9 +69,20 @@ class Integrand:
         self.gluon_finals = [i for i, l in enumerate(wl.legs) if not l.incoming and l.particle == "g"]
 
     # ------------------------------------------------------------------
-    def kinematics(self, x, final_masses=None):
+    def use_channels(self, s0: float, t0: float):
+        """Switch on the multichannel phase space of oracle/channels.py with
+        regulators s0 (s-channel) and t0 (t-channel), GeV^2; returns the
+        channels in their canonical order."""
+        from . import channels as chmod
+        self.channels = chmod.derive_channels(self.proc)
+        self.s0, self.t0 = float(s0), float(t0)
+        return self.channels
+
+    def kinematics(self, x, final_masses=None, channel=None):
         """Momenta [N, n, 4], s-hat, x1, x2, J_x and W for points x [ndim, N]
-        (final-state masses as given, else the workload's)."""
+        (final-state masses as given, else the workload's).  With a channel
+        index (after use_channels) the momenta come from that channel and W
+        is a_i / g_i, the channel's share of the partition over its density."""
         from oracle.dual import as_f64
         x = as_f64(x)
         N = x.shape[1]
@@ -89,9 +100,18 @@ class Integrand:
             u = x
         rs = np.sqrt(s_hat)
         n_out = self.wl.n_out
-        p0 = ps.massless_diet(u, rs)
-        k, wfac, ok = ps.massive(p0, fm, rs)
-        w = ps.massless_weight(n_out, s_hat) * wfac
+        if channel is not None:
+            from . import channels as chmod
+            if final_masses is not None:
+                raise ValueError("the multichannel path takes the workload's masses")
+            k, inv_g, ok = chmod.generate(self.channels[channel], u, rs, fm, self.s0, self.t0, [self.m_top])
+            pa = np.stack([rs / 2, 0 * rs, 0 * rs, rs / 2], axis=1)
+            a = chmod.partition(self.channels, pa, k, self.s0, self.t0, [self.m_top])[:, channel]
+            w = a * inv_g
+        else:
+            p0 = ps.massless_diet(u, rs)
+            k, wfac, ok = ps.massive(p0, fm, rs)
+            w = ps.massless_weight(n_out, s_hat) * wfac
         p = np.zeros((N, n_out + 2, 4), like=k)
         p[:, 0] = np.stack([rs / 2, 0 * rs, 0 * rs, rs / 2], axis=1)
         p[:, 1] = np.stack([rs / 2, 0 * rs, 0 * rs, -rs / 2], axis=1)
@@ -122,10 +142,10 @@ class Integrand:
                     keep[k] &= dr > wl.dr_min_gluon
         return keep
 
-    def __call__(self, x, return_parts=False):
+    def __call__(self, x, return_parts=False, channel=None):
         x = np.asarray(x, dtype=np.float64)
         N = x.shape[1]
-        p, s_hat, x1, x2, jx, w, ok = self.kinematics(x)
+        p, s_hat, x1, x2, jx, w, ok = self.kinematics(x, channel=channel)
         keep = ok & self.cuts(p)
         f = np.zeros(N)
         if np.any(keep):
