@@ -343,6 +343,110 @@ mf_status mf_vegas_iterate(mf_vegas *const *grids, mf_process *const *procs,
                            mf_precision prec, int32_t refine, mf_iter_result *out,
                            void *stream);
 
+/* ---- Multichannel phase space (the outlook of Sec. 4 and the caveat of
+ * Sec. 2.6 "Scope": a phase space built from the process topology in place
+ * of the flat RAMBO of Sec. 2.4, whose unweighting efficiency Sec. 2.5
+ * puts at about 5 %; multichannel weights after Kleiss & Pittau, the
+ * paper's reference for it).
+ *
+ * Channels.  Every AMP op of the program is one diagram; its currents are
+ * its propagators.  A current holding exactly one of the incoming legs 0, 1
+ * is a t-channel propagator; its final legs on the side of leg 0 form the
+ * set F_j, and these sets nest, F_1 < .. < F_{k-1}.  Every other current is
+ * an s-channel propagator of a cluster of final legs (for a current holding
+ * both incoming legs: the final legs outside it).  The clusters
+ * c_j = F_j \ F_{j-1} (F_0 = {}, F_k = all final legs) sit along the path
+ * from leg 0 to leg 1; inside a cluster the s-channel propagators form a
+ * binary tree, whose left child holds the smallest final index.  Diagrams
+ * with a four-gluon vertex are left out, and diagrams that give equal
+ * channels are merged.  Channels are numbered in ascending order of their
+ * key:
+ *   (k, masks of c_1..c_k, mass ids of the k-1 t-channel propagators,
+ *    number of s-channel clusters, then their (mask, mass id) pairs in
+ *    ascending order),
+ * where the masks have bit i for final leg i (leg 2 + i) and mass id -1
+ * means massless.  A process with more than six final legs has no channels.
+ *
+ * Map of the 3n-4 phase-space unit numbers (after x1, x2 for hadronic
+ * processes; n final legs) to momenta in the partonic centre-of-mass frame,
+ * in this order:
+ *   (i)   masses s of the clusters c_j with two or more legs, j = 1..k:
+ *         range [m(c_j)^2, (sqrt(s-hat) - sum_{i<j} sqrt(s_{c_i})
+ *         - sum_{i>j} m(c_i))^2] (m(X): sum of the final masses in X);
+ *   (ii)  masses of the remainders R_j = c_{j+1} + .. + c_k, j = 1..k-2,
+ *         flat on [(sum_{i>j} sqrt(s_{c_i}))^2,
+ *         (sqrt(s_{R_{j-1}}) - sqrt(s_{c_j}))^2], R_0 = all;
+ *   (iii) for j = 1..k-1 the split R_{j-1} -> c_j + R_j in the rest frame of
+ *         R_{j-1}: the polar angle of c_j about the direction of
+ *         q = p_0 - c_1 - .. - c_{j-1} with density proportional to
+ *         1 / (M^2 + t0 - t), t = (q - c_j)^2 and M the t-channel
+ *         propagator's mass (one number), then the azimuth, flat, in the
+ *         frame R_z(phi_q) R_y(theta_q) of that axis (one number);
+ *   (iv)  for every cluster in spine order, its nodes X -> (L, R) in
+ *         pre-order: s_L (if L is a cluster) on [m(L)^2, (sqrt(s_X) -
+ *         m(R))^2], s_R (if R is a cluster) on [m(R)^2, (sqrt(s_X) -
+ *         sqrt(s_L))^2], then L's direction, isotropic in X's rest frame
+ *         (cos theta, phi about the fixed axes).
+ * A cluster mass has density proportional to 1 / (s - M^2 + s0) on its range
+ * (M its propagator's mass; flat if the range's lower end has
+ * lo - M^2 + s0 <= 0).  Two-body momenta are built in the parent's rest
+ * frame and boosted back without rotation.
+ *
+ * Weight.  A point of channel i weighs a_i / g_i in place of the RAMBO
+ * weight: g_i is the channel's density relative to
+ * dPhi_n = prod ds/(2 pi) prod lambda^(1/2)/(32 pi^2 s) dOmega, and
+ * a_i = P_i / sum_j P_j with P_i the product over channel i's propagators
+ * of 1 / (|x - M^2| + r)^2 (x the propagator's s -- s-hat for the
+ * propagator into a one-cluster final state -- or t; r = s0 or t0).  The
+ * a_i sum to one, so the cross section is the sum of the channels'
+ * integrals of f a_i / g_i, each over its own unit hypercube. */
+
+/* mf_process_channels: the number of channels of the process (0 if it has
+ * none; the channel calls then return MF_EUNSUPPORTED). */
+mf_status mf_process_channels(const mf_process *p, int32_t *n_channels);
+
+/* mf_process_set_channel_regulators: the regulators s0 and t0 (GeV^2, > 0)
+ * of the channels' s- and t-channel densities and of the partition
+ * (default: max(pt_min, 1 GeV)^2 for both). */
+mf_status mf_process_set_channel_regulators(mf_process *p, double s0, double t0);
+
+/* mf_channel_integrand: as mf_integrand (x: device SoA [ndim][n], f: device
+ * [n]), with the momenta and weight of channel `channel`. */
+mf_status mf_channel_integrand(mf_process *p, int32_t channel, const double *x, int64_t n, double *f,
+                               mf_precision prec, void *stream);
+
+/* mf_vegas_iterate_channels: one Vegas iteration of every channel of the
+ * process, grids[k] (host [n_channels], distinct, n_channels =
+ * mf_process_channels) serving channel k with n_events[k] >= 2 points.
+ * Point i of channel k in iteration t draws its unit numbers as point i of
+ * subprocess k in mf_vegas_iterate; accumulation, refinement and
+ * combination are those of mf_vegas_iterate, per channel.  out: host
+ * [n_channels].  The iteration's cross section is the sum of the channels'
+ * integrals and its variance the sum of theirs.  Synchronous. */
+mf_status mf_vegas_iterate_channels(mf_vegas *const *grids, mf_process *p, const int64_t *n_events,
+                                    int32_t n_channels, uint64_t seed, mf_precision prec, int32_t refine,
+                                    mf_iter_result *out, void *stream);
+
+/* mf_channels_allocate (host only): Neyman's allocation of n_total points
+ * over n_channels channels whose weights have per-point standard deviations
+ * sigma[k] (host): n_out[k] = n_floor + floor(F * (sigma[k] / S)), F =
+ * n_total - n_channels n_floor, S = sigma[0] + .. (summed in order); equal
+ * shares n_floor + F / n_channels when S = 0.  MF_EINVAL if F < 0 or a sigma
+ * is negative or not finite. */
+mf_status mf_channels_allocate(int32_t n_channels, const double *sigma, int64_t n_total, int64_t n_floor,
+                               int64_t *n_out);
+
+/* mf_channels_describe (host only): the channels a descriptor's program
+ * gives, without creating a process.  *n_channels is set; if keys is not
+ * NULL, row k of keys (host [n][key_stride]) holds the key's length and then
+ * the key of channel k (lengths are at most 24; MF_EINVAL if key_stride is
+ * smaller than a row needs).
+ * mf_channels_table (host only): the int32 table the kernels read (the
+ * layout of csrc/device/mf_channels.cuh); *len is set to its length, and
+ * the table copied if table is not NULL (MF_EINVAL if *len was smaller). */
+mf_status mf_channels_describe(const mf_process_desc *d, int32_t *n_channels, int32_t *keys, int32_t key_stride);
+mf_status mf_channels_table(const mf_process_desc *d, int32_t *table, int32_t *len);
+
 /* ---- Data-parallel iterations (Sec. 2.3: points are independent, so one
  * iteration splits across devices with one exchange of partial sums).
  *

@@ -156,10 +156,26 @@ class Integrand:
                 lum = (self.pdfs[0].f(x1[idx], self.wl.mu_f2) * self.pdfs[1].f(x2[idx], self.wl.mu_f2))
             f[idx] = jx[idx] * w[idx] * lum * msq / (2.0 * s_hat[idx]) * W.GEV2_TO_PB
         if return_parts:
+            cond = self.condition(p, s_hat, x1, x2)
+            if channel is not None:
+                cond = cond + self.channel_condition(s_hat)
             return f, dict(p=p, s_hat=s_hat, x1=x1, x2=x2, jx=jx, w=w, keep=keep,
-                           pdf_condition=self._pdf_condition(x1, x2),
-                           condition=self.condition(p, s_hat, x1, x2))
+                           pdf_condition=self._pdf_condition(x1, x2), condition=cond)
         return f
+
+    def channel_condition(self, s_hat):
+        """Bound on the condition number of a channel point's weight a_i / g_i:
+        every propagator factor 1/(|x - M^2| + r)^2 of the partition and every
+        t-channel density 1/(M^2 + t0 - t) moves by at most 2 eps s-hat / r
+        when its invariant, formed from components up to sqrt(s-hat), moves by
+        eps s-hat; summed over the largest channel's factors (numerator and
+        denominator of the share, and the density)."""
+        from . import channels as chmod
+        n_fac = 0
+        for ch in self.channels:
+            n_prop = sum(1 for c in ch.spine for _ in chmod._clusters(c)) + ch.k - 1
+            n_fac = max(n_fac, n_prop)
+        return (3 * n_fac) * 2.0 * s_hat / min(self.s0, self.t0)
 
     # ------------------------------------------------------------------
     # derivatives by forward-mode dual numbers

@@ -100,6 +100,14 @@ SIGNATURES = {
     "mf_vegas_iterate": (c_i32, [P(C.c_void_p), P(C.c_void_p), P(c_i64), c_i32, C.c_uint64, c_i32, c_i32,
                                  P(mf_iter_result), C.c_void_p]),
     "mf_process_last_kernel_ms": (c_i32, [C.c_void_p, P(C.c_double)]),
+    "mf_process_channels": (c_i32, [C.c_void_p, P(c_i32)]),
+    "mf_process_set_channel_regulators": (c_i32, [C.c_void_p, C.c_double, C.c_double]),
+    "mf_channel_integrand": (c_i32, [C.c_void_p, c_i32, C.c_void_p, c_i64, C.c_void_p, c_i32, C.c_void_p]),
+    "mf_vegas_iterate_channels": (c_i32, [P(C.c_void_p), C.c_void_p, P(c_i64), c_i32, C.c_uint64, c_i32, c_i32,
+                                          P(mf_iter_result), C.c_void_p]),
+    "mf_channels_allocate": (c_i32, [c_i32, P(C.c_double), c_i64, c_i64, P(c_i64)]),
+    "mf_channels_describe": (c_i32, [P(mf_process_desc), P(c_i32), P(c_i32), c_i32]),
+    "mf_channels_table": (c_i32, [P(mf_process_desc), P(c_i32), P(c_i32)]),
     "mf_vegas_get_grid": (c_i32, [C.c_void_p, P(C.c_double)]),
     "mf_vegas_set_grid": (c_i32, [C.c_void_p, P(C.c_double)]),
     "mf_vegas_get_histogram": (c_i32, [C.c_void_p, P(C.c_double), P(c_i64)]),

@@ -224,6 +224,67 @@ def mf_vegas_iterate(grids, procs, n_events, seed: int, precision="fp64", refine
     return [_result(r) for r in out]
 
 
+def mf_process_channels(h) -> int:
+    n = C.c_int32()
+    L.check(L.lib().mf_process_channels(h, C.byref(n)), "mf_process_channels")
+    return n.value
+
+
+def mf_process_set_channel_regulators(h, s0: float, t0: float):
+    L.check(L.lib().mf_process_set_channel_regulators(h, float(s0), float(t0)), "mf_process_set_channel_regulators")
+
+
+def mf_channel_integrand(h, channel: int, x, n: int, f, precision="fp64", stream=None):
+    """x [ndim, n], f [n]: device tensors or pointers."""
+    xp = x if isinstance(x, int) else x.data_ptr()
+    fp = f if isinstance(f, int) else f.data_ptr()
+    return L.check(L.lib().mf_channel_integrand(h, channel, C.c_void_p(xp), n, C.c_void_p(fp), _PREC[precision],
+                                                _stream_ptr(stream)), "mf_channel_integrand")
+
+
+def mf_vegas_iterate_channels(grids, h, n_events, seed: int, precision="fp64", refine: bool = True, stream=None):
+    k = len(grids)
+    G = (C.c_void_p * k)(*[g.value for g in grids])
+    N = (C.c_int64 * k)(*[int(v) for v in n_events])
+    out = (L.mf_iter_result * k)()
+    st = L.lib().mf_vegas_iterate_channels(G, h, N, k, seed, _PREC[precision], 1 if refine else 0, out,
+                                           _stream_ptr(stream))
+    L.check(st, "mf_vegas_iterate_channels", allow=(L.MF_OK, L.MF_ENAN))
+    return [_result(r) for r in out]
+
+
+def mf_channels_allocate(sigma, n_total: int, n_floor: int):
+    k = len(sigma)
+    S = (C.c_double * k)(*[float(v) for v in sigma])
+    out = (C.c_int64 * k)()
+    L.check(L.lib().mf_channels_allocate(k, S, int(n_total), int(n_floor), out), "mf_channels_allocate")
+    return [int(v) for v in out]
+
+
+def mf_channels_describe(desc: Descriptor):
+    """The channel keys of a descriptor's program (host only), in channel order."""
+    n = C.c_int32()
+    L.check(L.lib().mf_channels_describe(C.byref(desc.desc), C.byref(n), None, 0), "mf_channels_describe")
+    stride = 32
+    keys = (C.c_int32 * (max(n.value, 1) * stride))()
+    L.check(L.lib().mf_channels_describe(C.byref(desc.desc), C.byref(n), keys, stride), "mf_channels_describe")
+    out = []
+    for i in range(n.value):
+        ln = keys[i * stride]
+        out.append(tuple(keys[i * stride + 1: i * stride + 1 + ln]))
+    return out
+
+
+def mf_channels_table(desc: Descriptor):
+    """The int32 channel table the kernels read (host only)."""
+    import numpy as np
+    n = C.c_int32(0)
+    L.check(L.lib().mf_channels_table(C.byref(desc.desc), None, C.byref(n)), "mf_channels_table")
+    buf = (C.c_int32 * max(n.value, 1))()
+    L.check(L.lib().mf_channels_table(C.byref(desc.desc), buf, C.byref(n)), "mf_channels_table")
+    return np.array(buf[:n.value], dtype=np.int32)
+
+
 def _result(r):
     return {name: getattr(r, name) for name, _ in r._fields_}
 
@@ -404,6 +465,27 @@ class Process:
         mf_integrand(self.handle, x, n, f, precision, stream)
         return f
 
+    @property
+    def n_channels(self):
+        """Channels of the multichannel phase space (0: the process has none)."""
+        return mf_process_channels(self.handle)
+
+    def set_channel_regulators(self, s0: float, t0: float):
+        mf_process_set_channel_regulators(self.handle, s0, t0)
+
+    def channel_integrand(self, x, channel: int, precision="fp64", out=None, stream=None):
+        """f at points x [ndim, n] through phase-space channel `channel`
+        (weight a_i / g_i in place of the flat phase space's)."""
+        import torch
+        if x.dtype != torch.float64 or not x.is_cuda or not x.is_contiguous():
+            raise ValueError("x must be a contiguous float64 CUDA tensor [ndim, n]")
+        if x.shape[0] != self.ndim:
+            raise ValueError(f"x must have {self.ndim} rows")
+        n = x.shape[1]
+        f = torch.empty(n, dtype=torch.float64, device=x.device) if out is None else out
+        mf_channel_integrand(self.handle, channel, x, n, f, precision, stream)
+        return f
+
     def set_colour_sampling(self, on=True):
         """One uniformly drawn colour flow per point instead of the colour
         sum (unbiased; see mf_process_set_colour_sampling)."""
@@ -532,6 +614,53 @@ class Vegas:
             self.close()
         except Exception:
             pass
+
+
+class MultiChannel:
+    """Vegas over the multichannel phase space of a process: one grid per
+    channel, the cross section the sum of the channels' integrals, and the
+    points of each iteration shared out by Neyman's rule from the previous
+    iteration's per-point standard deviations (equal shares first)."""
+
+    def __init__(self, proc: "Process", nbins: int = 50, alpha: float = 1.5):
+        self.proc = proc
+        self.K = proc.n_channels
+        if self.K == 0:
+            raise ValueError("the process has no phase-space channels")
+        self.grids = [Vegas(proc.ndim, nbins, alpha) for _ in range(self.K)]
+        self.sigma = None
+
+    def allocation(self, n_total: int, n_floor=None):
+        if n_floor is None:
+            n_floor = max(2, n_total // (10 * self.K))
+        sig = self.sigma if self.sigma is not None else [0.0] * self.K
+        return mf_channels_allocate(sig, n_total, n_floor)
+
+    def iterate(self, n_total: int, seed: int, precision="fp64", refine=True, adapt=True, n_floor=None,
+                stream=None):
+        import math
+        n = self.allocation(n_total, n_floor)
+        res = mf_vegas_iterate_channels([g.handle for g in self.grids], self.proc.handle, n, seed, precision,
+                                        refine, stream)
+        if adapt:
+            self.sigma = [r["error"] * math.sqrt(k) for r, k in zip(res, n)]
+        tot = {
+            "n_events": sum(n),
+            "integral": sum(r["integral"] for r in res),
+            "error": math.sqrt(sum(r["error"] ** 2 for r in res)),
+            "sigma": sum(r["sigma"] for r in res),
+            "sigma_error": math.sqrt(sum(r["sigma_error"] ** 2 for r in res)),
+            "n_nonzero": sum(r["n_nonzero"] for r in res),
+            "n_nan": sum(r["n_nan"] for r in res),
+            "per_channel": res,
+            "allocation": n,
+        }
+        return tot
+
+    def close(self):
+        for g in self.grids:
+            g.close()
+        self.grids = []
 
 
 class LheWriter:

@@ -18,8 +18,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmadflow_gb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 EMBED = ["mf_common.cuh", "mf_dual.cuh", "mf_kinematics.cuh", "mf_helas.cuh", "mf_kparams.h", "mf_kernel.cuh",
-         "mf_helas_adj.cuh", "mf_grad.cuh", "mf_tc.cuh"]
-SOURCES = ["mf_api.cu", "mf_colour.cu", "mf_peaks.cu", "mf_codegen.cpp", "mf_jit.cpp", "mf_lhe.cpp"]
+         "mf_helas_adj.cuh", "mf_grad.cuh", "mf_tc.cuh", "mf_channels.cuh"]
+SOURCES = ["mf_api.cu", "mf_colour.cu", "mf_peaks.cu", "mf_codegen.cpp", "mf_jit.cpp", "mf_lhe.cpp",
+           "mf_channels.cpp"]
 
 
 def _nvcc() -> str:

@@ -26,6 +26,7 @@
 #include "mf_helas.cuh"
 #include "mf_kparams.h"
 #include "mf_tc.cuh"
+#include "mf_channels.cuh"
 
 namespace mf {
 
@@ -100,12 +101,27 @@ MF_DEV bool phase_a(const KParams &kp, const T *y, const T *masses, const T &ln_
     p[0][0] = 0.5 * rs; p[0][1] = T(0.0); p[0][2] = T(0.0); p[0][3] = 0.5 * rs;
     p[1][0] = 0.5 * rs; p[1][1] = T(0.0); p[1][2] = T(0.0); p[1][3] = -0.5 * rs;
     T (*pout)[4] = reinterpret_cast<T (*)[4]>(&p[2][0]);
-    massless_diet<NOUT>(u, rs, pout);
     T mout[NOUT];
 #pragma unroll
     for (int i = 0; i < NOUT; ++i) mout[i] = LEG_MASS_ID[2 + i] >= 0 ? masses[LEG_MASS_ID[2 + i]] : T(0.0);
-    T wfac = massive_rescale<NOUT>(pout, mout, rs);
-    bool ok = value(wfac) > 0.0;
+    T wfac;
+    bool ok;
+    // a multichannel point (double-precision kernels; the gradient kernel
+    // always takes the flat phase space)
+    bool chan = false;
+    if constexpr (sizeof(T) == sizeof(double)) chan = kp.channel >= 0;
+    if (chan) {
+        if constexpr (sizeof(T) == sizeof(double)) {
+            double inv_g;
+            ok = channel_generate<NOUT>(kp.chan, kp.channel, u, rs, mout, kp.masses, kp.ch_s0, kp.ch_t0, pout,
+                                        inv_g);
+            wfac = inv_g;
+        }
+    } else {
+        massless_diet<NOUT>(u, rs, pout);
+        wfac = massive_rescale<NOUT>(pout, mout, rs);
+        ok = value(wfac) > 0.0;
+    }
     // cuts on the flagged legs (decided on values)
     if (ok && NCUT > 0) {
         double pv[NLEG][4];
@@ -123,9 +139,15 @@ MF_DEV bool phase_a(const KParams &kp, const T *y, const T *masses, const T &ln_
         }
     }
     if (!ok) return false;
-    T wps = kp.w0_const * wfac;
+    T wps;
+    if (chan) {
+        if constexpr (sizeof(T) == sizeof(double))
+            wps = wfac * channel_share<NOUT>(kp.chan, kp.channel, rs, pout, kp.masses, kp.ch_s0, kp.ch_t0);
+    } else {
+        wps = kp.w0_const * wfac;
 #pragma unroll
-    for (int i = 0; i < NOUT - 2; ++i) wps = wps * s_hat;
+        for (int i = 0; i < NOUT - 2; ++i) wps = wps * s_hat;
+    }
     if (HADRONIC) {
         const double *r = kp.pdf_rows;
         const int nx = kp.pdf_nx;

@@ -59,6 +59,10 @@ struct mf_kparams {
     int32_t pad4;
     double obs_lo[MF_KP_MAX_OBS];      // bin b = floor((v - lo) * scale) if 0 <= b < nbins
     double obs_scale[MF_KP_MAX_OBS];   // nbins / (hi - lo)
+    const int32_t *chan;       // multichannel table (device/mf_channels.cuh), may be NULL
+    int32_t channel;           // modes 0, 1: phase-space channel of the points, -1: RAMBO
+    int32_t pad5;
+    double ch_s0, ch_t0;       // channel propagator regulators (GeV^2)
     double masses[8];
     double couplings[16];      // 8 complex couplings (re, im)
     int8_t hel[MF_KP_MAX_HEL][8];

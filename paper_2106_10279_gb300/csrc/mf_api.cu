@@ -658,6 +658,10 @@ void fill_common(const mf_process &p, mf_kparams &kp) {
         kp.pairs[u][1] = p.pairs[2 * u + 1];
     }
     kp.seed = p.hel_seed;          // Vegas passes overwrite it with their own key
+    kp.chan = p.d_chan;
+    kp.channel = -1;               // the flat phase space unless a channel call sets one
+    kp.ch_s0 = p.ch_s0;
+    kp.ch_t0 = p.ch_t0;
 }
 
 // Pairs of kept helicities that differ only at the pair leg L, in the order
@@ -914,6 +918,23 @@ extern "C" mf_status mf_create_process(const mf_process_desc *d, mf_process **ou
         mf_destroy_process(p);
         return fail(MF_ENOMEM, "error flag");
     }
+    // channels of the multichannel phase space (none for programs outside the
+    // table's limits; the flat phase space is always available)
+    {
+        mf_status cst = mfi::derive_channels(p->n_legs, p->ops, p->channels);
+        if (cst != MF_OK) {
+            p->channels = mfi::ChannelSet();
+        } else if (p->channels.K > 0) {
+            const size_t bytes = sizeof(int32_t) * p->channels.table.size();
+            if (mfi::dev_malloc(&p->d_chan, bytes) != cudaSuccess ||
+                cudaMemcpy(p->d_chan, p->channels.table.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+                mf_destroy_process(p);
+                return fail(MF_ENOMEM, "channel table");
+            }
+        }
+        const double r = std::max(p->pt_min, 1.0);
+        p->ch_s0 = p->ch_t0 = r * r;
+    }
     // PDF rows at fixed mu_F^2
     if (p->hadronic) {
         const int nx = d->pdf_nx, nq = d->pdf_nq;
@@ -1094,6 +1115,7 @@ extern "C" mf_status mf_destroy_process(mf_process *p) {
     if (p->ev_stop) cudaEventDestroy(p->ev_stop);
     cudaFree(p->d_pdf_rows);
     cudaFree(p->d_err);
+    cudaFree(p->d_chan);
     cudaFree(p->d_w);
     cudaFree(p->d_bins);
     delete p;
@@ -1412,7 +1434,7 @@ mf_status accumulate(mf_process *p, mf_vegas *v, int64_t n, cudaStream_t s) {
 // Evaluate points [ev0, ev0 + n) of iteration v->iteration into the process
 // scratch (w, bins) and accumulate their chunks into v->d_slots.
 mf_status run_points(mf_process *p, mf_vegas *v, int prec, int64_t n, int64_t ev0, int subprocess, uint64_t seed,
-                     cudaStream_t s) {
+                     cudaStream_t s, int channel = -1) {
     mf_status st = compile_precision(p, prec);
     if (st != MF_OK) return st;
     st = ensure_scratch(p, v, n);
@@ -1421,6 +1443,7 @@ mf_status run_points(mf_process *p, mf_vegas *v, int prec, int64_t n, int64_t ev
     if (n == 0) return MF_OK;
     mf_kparams kp;
     vegas_params(p, v, n, ev0, subprocess, seed, kp);
+    kp.channel = channel;
     MF_CUDA(cudaEventRecord(p->ev_start, s));
     st = launch(p, prec, kp, s);
     if (st != MF_OK) return st;
@@ -1604,6 +1627,98 @@ extern "C" mf_status mf_vegas_iterate(mf_vegas *const *grids, mf_process *const 
     bool any_nan = false;
     for (int k = 0; k < nproc; ++k) {
         fill_result(out[k], grids[k], n_events[k], res[k].data());
+        any_nan |= out[k].n_nan > 0;
+        grids[k]->iteration += 1;
+    }
+    if (any_nan) return fail(MF_ENAN, "some points had non-finite weights (counted as zero)");
+    return MF_OK;
+}
+
+extern "C" mf_status mf_process_channels(const mf_process *p, int32_t *n_channels) {
+    if (!p || !n_channels) return fail(MF_EINVAL, "NULL argument");
+    *n_channels = p->channels.K;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_process_set_channel_regulators(mf_process *p, double s0, double t0) {
+    if (!p) return fail(MF_EINVAL, "NULL process");
+    if (!(s0 > 0.0) || !(t0 > 0.0) || !std::isfinite(s0) || !std::isfinite(t0))
+        return fail(MF_EINVAL, "regulators must be positive and finite");
+    p->ch_s0 = s0;
+    p->ch_t0 = t0;
+    return MF_OK;
+}
+
+extern "C" mf_status mf_channel_integrand(mf_process *p, int32_t channel, const double *x, int64_t n, double *f,
+                                          mf_precision prec, void *stream) {
+    if (!p) return fail(MF_EINVAL, "NULL process");
+    if (p->channels.K == 0) return fail(MF_EUNSUPPORTED, "the process has no phase-space channels");
+    if (channel < 0 || channel >= p->channels.K) return fail(MF_EINVAL, "channel out of range");
+    if (n < 0) return fail(MF_EINVAL, "negative n");
+    if (!valid_prec(prec)) return fail(MF_EINVAL, "bad precision");
+    if (n == 0) return MF_OK;
+    if (!x || !f) return fail(MF_EINVAL, "NULL x or f");
+    mf_status st = compile_precision(p, prec);
+    if (st != MF_OK) return st;
+    mf_kparams kp;
+    fill_common(*p, kp);
+    set_hel(kp, p->hel, p->n_legs);
+    kp.mode = 0;
+    kp.n = n;
+    kp.x = x;
+    kp.f = f;
+    kp.channel = channel;
+    return launch(p, prec, kp, (cudaStream_t)stream);
+}
+
+extern "C" mf_status mf_vegas_iterate_channels(mf_vegas *const *grids, mf_process *p, const int64_t *n_events,
+                                               int32_t n_channels, uint64_t seed, mf_precision prec, int32_t refine,
+                                               mf_iter_result *out, void *stream) {
+    if (!grids || !p || !n_events || !out) return fail(MF_EINVAL, "bad arguments");
+    if (p->channels.K == 0) return fail(MF_EUNSUPPORTED, "the process has no phase-space channels");
+    if (n_channels != p->channels.K) return fail(MF_EINVAL, "one grid per channel of the process");
+    if (!valid_prec(prec)) return fail(MF_EINVAL, "bad precision");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int k = 0; k < n_channels; ++k) {
+        if (!grids[k]) return fail(MF_EINVAL, "NULL grid");
+        if (grids[k]->ndim != p->ndim) return fail(MF_EINVAL, "grid and process dimensions differ");
+        if (n_events[k] < 2) return fail(MF_EINVAL, "need at least two events per channel");
+        if ((n_events[k] + kChunk - 1) / kChunk > ((int64_t)1 << kTreeMaxLevel))
+            return fail(MF_EINVAL, "too many events per iteration");
+        if (grids[k]->iteration >= grids[k]->max_iter) return fail(MF_EUNSUPPORTED, "too many iterations");
+    }
+    {
+        // every grid once (a sorted copy: n_channels can be in the hundreds)
+        std::vector<const mf_vegas *> g(grids, grids + n_channels);
+        std::sort(g.begin(), g.end());
+        if (std::adjacent_find(g.begin(), g.end()) != g.end()) return fail(MF_EINVAL, "a grid appears twice");
+    }
+    std::vector<double> res((size_t)n_channels * 8);
+    std::vector<int> flags(n_channels, 0);
+    for (int k = 0; k < n_channels; ++k) {
+        mf_vegas *v = grids[k];
+        const int64_t n = n_events[k];
+        mf_status st = run_points(p, v, prec, n, 0, k, seed, s, k);
+        if (st != MF_OK) return st;
+        const int64_t nchunks = (n + kChunk - 1) / kChunk;
+        const std::vector<int64_t> root = {tree_levels(nchunks), 0};
+        st = tree_nodes(v, nchunks, 0, nchunks, root, s);
+        if (st != MF_OK) return st;
+        st = finish(v, v->d_tree_out, n, refine, s);
+        if (st != MF_OK) return st;
+        MF_CUDA(cudaMemcpyAsync(&res[(size_t)k * 8], v->d_result, sizeof(double) * 7, cudaMemcpyDeviceToHost, s));
+        MF_CUDA(cudaMemcpyAsync(&flags[k], p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    }
+    MF_CUDA(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p->ev_start, p->ev_stop) == cudaSuccess) p->last_kernel_ms = ms;
+    for (int k = 0; k < n_channels; ++k) {
+        mf_status st = flag_status(p, flags[k]);
+        if (st != MF_OK) return st;
+    }
+    bool any_nan = false;
+    for (int k = 0; k < n_channels; ++k) {
+        fill_result(out[k], grids[k], n_events[k], &res[(size_t)k * 8]);
         any_nan |= out[k].n_nan > 0;
         grids[k]->iteration += 1;
     }

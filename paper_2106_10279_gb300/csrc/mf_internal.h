@@ -66,6 +66,15 @@ double shared_flops(const mf_process &p, int leg);
 int pair_leg(const mf_process &p);
 bool large_program(const mf_process &p);
 
+
+// Channels of the multichannel phase space (mf_channels.cpp): the device
+// table of device/mf_channels.cuh and each channel's canonical key.
+struct ChannelSet {
+    int K = 0;
+    std::vector<int32_t> table;
+    std::vector<std::vector<int>> keys;
+};
+mf_status derive_channels(int n_legs, const std::vector<mf_op> &ops, ChannelSet &out);
 }  // namespace mfi
 
 struct mf_process {
@@ -112,6 +121,11 @@ struct mf_process {
     int leading_colour = 0;        // generate the leading-colour approximation
     int colour_sample = 0;         // one colour flow per point (the colour-sampled kernel)
     uint64_t hel_seed = 0;         // Philox key of the sampling of given points
+    // multichannel phase space: the channels derived from the program, their
+    // device table and the propagator regulators (GeV^2)
+    mfi::ChannelSet channels;
+    int32_t *d_chan = nullptr;
+    double ch_s0 = 1.0, ch_t0 = 1.0;
 };
 
 struct mf_vegas {

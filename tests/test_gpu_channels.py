@@ -1,0 +1,166 @@
+"""The multichannel phase space on the GPU against the oracle.
+
+* Per point, through every channel (gg -> tt~, uu~ -> tt~g, gg -> tt~g) or a
+  seeded sample of them (gg -> tt~gg): f of mf_channel_integrand in FP64
+  within 1e-12 plus 64 eps times the oracle's condition number (which adds
+  the bound on the channel weight's), in mixed precision within 1e-5
+  (median) and 1e-3 (max); identical zero patterns.
+* The first iteration of mf_vegas_iterate_channels from uniform grids draws
+  the same Philox numbers as the oracle's Vegas with subprocess k for
+  channel k: identical per-bin counts, sums within 1e-11.
+* The channels' summed cross section of gg -> tt~ agrees with the quadrature
+  value and that of gg -> tt~gg with the flat phase space's, within the
+  combined errors; the multichannel error is the smaller at equal points.
+* Argument checks: a channel out of range, a grid count other than the
+  process's channels.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from _tolerance import fp64_tolerance, relerr
+
+pytestmark = pytest.mark.gpu
+R0 = 400.0
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2106_10279_gb300 import api
+    return torch, api
+
+
+def _oracle(name):
+    from oracle.integrand import Integrand
+    I = Integrand(W.WORKLOADS[name])
+    r = max(W.WORKLOADS[name].pt_min_gluon, 1.0) ** 2
+    I.use_channels(r, r)
+    return I
+
+
+@pytest.mark.parametrize("name,n_ch,n_pts", [("ee_mumu", None, 64), ("gg_ttx", None, 300), ("uux_ttxg", None, 200),
+                                             ("gg_ttxg", None, 60), ("gg_ttxgg", 10, 12)])
+def test_channel_points_match_the_oracle(env, name, n_ch, n_pts):
+    torch, api = env
+    wl = W.WORKLOADS[name]
+    proc = api.Process.from_workload(wl)
+    I = _oracle(name)
+    K = proc.n_channels
+    assert K == len(I.channels)
+    rng = np.random.default_rng(31)
+    picks = range(K) if n_ch is None else sorted(rng.choice(K, n_ch, replace=False))
+    n_nonzero = 0
+    for i in picks:
+        x = W.uniform_points(wl.ndim, n_pts, 1000 + int(i))
+        xd = torch.from_numpy(x).cuda()
+        f64 = proc.channel_integrand(xd, int(i), "fp64").cpu().numpy()
+        fmx = proc.channel_integrand(xd, int(i), "mixed").cpu().numpy()
+        ref, tol = fp64_tolerance(lambda y, return_parts=False: I(y, return_parts=return_parts, channel=int(i)), x)
+        assert np.array_equal(f64 == 0, ref == 0), i
+        assert np.array_equal(fmx == 0, ref == 0), i
+        assert np.all(relerr(f64, ref) <= tol), (i, np.max(relerr(f64, ref) / tol))
+        nz = ref != 0
+        n_nonzero += int(nz.sum())
+        if nz.any():
+            r = relerr(fmx, ref)[nz]
+            assert np.median(r) <= 1e-5 and r.max() <= 1e-3, (i, np.median(r), r.max())
+    assert n_nonzero >= 10
+
+
+def _oracle_channel_iteration(I, ch, ndim, n, seed, chunk=20000):
+    from oracle import vegas
+    from oracle.philox import vegas_uniforms
+    grid = vegas.uniform_grid(ndim, 50)
+    s1 = s2 = 0.0
+    dsum = np.zeros((ndim, 50))
+    cnt = np.zeros_like(dsum, dtype=np.int64)
+    for start in range(0, n, chunk):
+        m = min(chunk, n - start)
+        y = vegas_uniforms(seed, 0, ch, start, m, ndim)
+        x, jac, bins = vegas.vegas_map(grid, y)
+        w = I(x, channel=ch) * jac
+        a, b, dd, cc = vegas.accumulate(w, bins, 50)
+        s1 += a; s2 += b; dsum += dd; cnt += cc
+    I_k, err = vegas.iteration_result(s1, s2, n)
+    return I_k, err, dsum, cnt
+
+
+@pytest.mark.parametrize("name,n", [("gg_ttx", 20000), ("gg_ttxg", 3000)])
+def test_first_channel_iteration_matches_the_oracle(env, name, n):
+    torch, api = env
+    wl = W.WORKLOADS[name]
+    proc = api.Process.from_workload(wl)
+    K = proc.n_channels
+    grids = [api.Vegas(wl.ndim, 50, 1.5) for _ in range(K)]
+    res = api.mf_vegas_iterate_channels([g.handle for g in grids], proc.handle, [n] * K, 777, "fp64")
+    I = _oracle(name)
+    for k in range(K):
+        I_k, err, dsum, cnt = _oracle_channel_iteration(I, k, wl.ndim, n, 777)
+        hs, hc = grids[k].histogram()
+        assert np.array_equal(hc, cnt), k
+        assert abs(res[k]["integral"] - I_k) <= 1e-11 * abs(I_k) + 1e-300, k
+        assert abs(res[k]["error"] - err) <= 1e-9 * err + 1e-300, k
+        assert np.allclose(hs, dsum, rtol=1e-10, atol=1e-300), k
+
+
+def test_gg_ttx_sigma_by_channels(env):
+    torch, api = env
+    wl = W.WORKLOADS["gg_ttx"]
+    proc = api.Process.from_workload(wl)
+    mc = api.MultiChannel(proc)
+    for it in range(6):
+        r = mc.iterate(600_000, seed=2024, precision="fp64")
+    assert abs(r["sigma"] - 699.76413) < 4 * r["sigma_error"], r
+    assert r["sigma_error"] < 2e-3 * r["sigma"]
+    mc.close()
+
+
+def test_gg_ttxgg_channels_agree_with_flat_and_beat_it(env, capsys):
+    torch, api = env
+    wl = W.WORKLOADS["gg_ttxgg"]
+    proc = api.Process.from_workload(wl)
+    n = 2_000_000
+    flat = api.Vegas(wl.ndim)
+    for it in range(5):
+        rf = flat.iterate(proc, n, seed=99, precision="mixed")
+    mc = api.MultiChannel(proc)
+    for it in range(5):
+        rm = mc.iterate(n, seed=99, precision="mixed")
+    d = abs(rf["sigma"] - rm["sigma"])
+    comb = math.hypot(rf["sigma_error"], rm["sigma_error"])
+    with capsys.disabled():
+        print(f"gg->tt~gg: flat {rf['sigma']:.5g} +- {rf['sigma_error']:.3g}, "
+              f"{proc.n_channels} channels {rm['sigma']:.5g} +- {rm['sigma_error']:.3g} pb "
+              f"(last iteration: flat {rf['error']:.3g}, channels {rm['error']:.3g})")
+    assert d < 4 * comb
+    assert rm["error"] < rf["error"]
+    mc.close()
+
+
+def test_channel_argument_checks(env):
+    torch, api = env
+    from paper_2106_10279_gb300 import _lib as L
+    wl = W.WORKLOADS["gg_ttx"]
+    proc = api.Process.from_workload(wl)
+    assert proc.n_channels == 3
+    x = torch.from_numpy(W.uniform_points(wl.ndim, 8, 1)).cuda()
+    for bad in (-1, 3):
+        with pytest.raises(L.MfError) as e:
+            proc.channel_integrand(x, bad)
+        assert e.value.status == L.MF_EINVAL
+    grids = [api.Vegas(wl.ndim) for _ in range(2)]
+    with pytest.raises(L.MfError) as e:
+        api.mf_vegas_iterate_channels([g.handle for g in grids], proc.handle, [100, 100], 1, "fp64")
+    assert e.value.status == L.MF_EINVAL
+    with pytest.raises(L.MfError) as e:
+        proc.set_channel_regulators(0.0, 1.0)
+    assert e.value.status == L.MF_EINVAL
+    ee = api.Process.from_workload(W.WORKLOADS["ee_mumu"])
+    assert ee.n_channels == 1
