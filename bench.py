@@ -51,6 +51,7 @@ def _args():
     ap.add_argument("--fp64-events", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed-batch and variant measurements")
+    ap.add_argument("--no-channels", action="store_true", help="skip the multichannel phase-space measurement")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_tc"],
                     help="arithmetic of the timed iterations (mixed_tc: colour sum on the tensor cores)")
     return ap.parse_args()
@@ -428,6 +429,51 @@ def run_native(args):
             v_["efficiency_vs_full"] = (ref["error_pb_rms"] ** 2 * ref["kernel_ms"]) / (v_["error_pb_rms"] ** 2
                                                                                         * v_["kernel_ms"])
 
+    # the multichannel phase space against the flat one on the same
+    # workload: equal points per iteration, five adapting iterations each
+    # (the grids, and the channels' Neyman allocation), then five seeds
+    # without adaptation: the error and the device time of the whole
+    # iteration (every channel's launches and accumulation); efficiency =
+    # 1 / (error^2 x time) relative to the flat phase space
+    phase_space = None
+    if not args.no_channels and proc.n_channels > 0 and rank == 0:
+        nps = min(n_events, 2_000_000)
+
+        def timed_iter(fn):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            r = fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            return r, a.elapsed_time(b)
+        gf = api.Vegas(wl.ndim, wl.n_bins, wl.alpha_vegas)
+        mc = api.MultiChannel(proc, wl.n_bins, wl.alpha_vegas)
+        for it in range(5):
+            gf.iterate(proc, nps, seed + 500 + it, "mixed", True, stream)
+            mc.iterate(nps, seed + 500 + it, "mixed", True, True, stream=stream)
+        legs = {"flat": ([], [], []), "multichannel": ([], [], [])}
+        for s_ in range(5):
+            r, ms = timed_iter(lambda: gf.iterate(proc, nps, seed + 600 + s_, "mixed", False, stream))
+            for lst, v_ in zip(legs["flat"], (ms, r["error"], r["integral"])):
+                lst.append(v_)
+            r, ms = timed_iter(lambda: mc.iterate(nps, seed + 600 + s_, "mixed", False, False, stream=stream))
+            for lst, v_ in zip(legs["multichannel"], (ms, r["error"], r["integral"])):
+                lst.append(v_)
+        phase_space = {"events_per_iteration": nps, "adapt_iterations": 5, "seeds": 5, "channels": proc.n_channels,
+                       "regulators_gev2": max(wl.pt_min_gluon, 1.0) ** 2}
+        for tag, (ms_l, err_l, int_l) in legs.items():
+            phase_space[tag] = {"iteration_ms": statistics.median(ms_l),
+                                "events_per_s": nps / (statistics.median(ms_l) / 1e3),
+                                "error_pb_rms": math.sqrt(statistics.mean([e * e for e in err_l])),
+                                "integral_pb": statistics.mean(int_l)}
+        f_, m_ = phase_space["flat"], phase_space["multichannel"]
+        phase_space["efficiency_vs_flat"] = (f_["error_pb_rms"] ** 2 * f_["iteration_ms"]) / (
+            m_["error_pb_rms"] ** 2 * m_["iteration_ms"])
+        phase_space["allocation_min_max"] = [min(mc.allocation(nps)), max(mc.allocation(nps))]
+        mc.close()
+
     # the mixed batch of five subprocesses (gg->tt~, uu~->tt~, gg->tt~g,
     # uu~->tt~g, gg->tt~gg; 4e7 points per iteration in all), each with its own
     # grid: one persistent launch per iteration against one launch per
@@ -585,6 +631,7 @@ def run_native(args):
         "batch": batch,
         "grad": grad,
         "kernel_variants": variants,
+        "phase_space": phase_space,
         "accuracy": {"median_rel_mixed_vs_fp64": float(np.median(rel)), "max_rel_mixed_vs_fp64": float(rel.max()),
                      "points": int(nz.sum())},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
