@@ -472,6 +472,16 @@ def run_native(args):
         phase_space["efficiency_vs_flat"] = (f_["error_pb_rms"] ** 2 * f_["iteration_ms"]) / (
             m_["error_pb_rms"] ** 2 * m_["iteration_ms"])
         phase_space["allocation_min_max"] = [min(mc.allocation(nps)), max(mc.allocation(nps))]
+        # unweighting efficiency <W> / max W of one iteration's event weights
+        # (the paper puts the flat phase space's at about 5 %, Sec. 2.5); a
+        # channel-k point weighs W = w N / n_k in the combined sample
+        gf.iterate(proc, nps, seed + 700, "mixed", False, stream)
+        wf = api.read_weights(proc, np.arange(nps))
+        rm = mc.iterate(nps, seed + 700, "mixed", False, False, stream=stream)
+        alloc = rm["allocation"]
+        wm = api.read_weights(proc, np.arange(sum(alloc))) * np.repeat([sum(alloc) / k for k in alloc], alloc)
+        phase_space["flat"]["unweighting_efficiency"] = float(wf.mean() / np.abs(wf).max())
+        phase_space["multichannel"]["unweighting_efficiency"] = float(wm.mean() / np.abs(wm).max())
         mc.close()
 
     # the mixed batch of five subprocesses (gg->tt~, uu~->tt~, gg->tt~g,

@@ -420,9 +420,11 @@ mf_status mf_channel_integrand(mf_process *p, int32_t channel, const double *x, 
  * mf_process_channels) serving channel k with n_events[k] >= 2 points.
  * Point i of channel k in iteration t draws its unit numbers as point i of
  * subprocess k in mf_vegas_iterate; accumulation, refinement and
- * combination are those of mf_vegas_iterate, per channel.  out: host
- * [n_channels].  The iteration's cross section is the sum of the channels'
- * integrals and its variance the sum of theirs.  Synchronous. */
+ * combination are those of mf_vegas_iterate, per channel.  All channels'
+ * points are evaluated in one kernel launch, so the grids must have the
+ * same number of bins and the same iteration count (MF_EINVAL otherwise).
+ * out: host [n_channels].  The iteration's cross section is the sum of the
+ * channels' integrals and its variance the sum of theirs.  Synchronous. */
 mf_status mf_vegas_iterate_channels(mf_vegas *const *grids, mf_process *p, const int64_t *n_events,
                                     int32_t n_channels, uint64_t seed, mf_precision prec, int32_t refine,
                                     mf_iter_result *out, void *stream);

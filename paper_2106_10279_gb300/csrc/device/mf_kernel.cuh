@@ -79,7 +79,8 @@ struct EventKin {
 };
 
 template <typename T>
-MF_DEV bool phase_a(const KParams &kp, const T *y, const T *masses, const T &ln_tau_min, EventKin<T> &ev) {
+MF_DEV bool phase_a(const KParams &kp, const T *y, const T *masses, const T &ln_tau_min, EventKin<T> &ev,
+                    int channel = -1) {
     using namespace MF_PROC;
     T s_hat = T(kp.S), jx = T(1.0), lum = T(1.0);
     XMap<T> xm;
@@ -109,11 +110,11 @@ MF_DEV bool phase_a(const KParams &kp, const T *y, const T *masses, const T &ln_
     // a multichannel point (double-precision kernels; the gradient kernel
     // always takes the flat phase space)
     bool chan = false;
-    if constexpr (sizeof(T) == sizeof(double)) chan = kp.channel >= 0;
+    if constexpr (sizeof(T) == sizeof(double)) chan = channel >= 0;
     if (chan) {
         if constexpr (sizeof(T) == sizeof(double)) {
             double inv_g;
-            ok = channel_generate<NOUT>(kp.chan, kp.channel, u, rs, mout, kp.masses, kp.ch_s0, kp.ch_t0, pout,
+            ok = channel_generate<NOUT>(kp.chan, channel, u, rs, mout, kp.masses, kp.ch_s0, kp.ch_t0, pout,
                                         inv_g);
             wfac = inv_g;
         }
@@ -142,7 +143,7 @@ MF_DEV bool phase_a(const KParams &kp, const T *y, const T *masses, const T &ln_
     T wps;
     if (chan) {
         if constexpr (sizeof(T) == sizeof(double))
-            wps = wfac * channel_share<NOUT>(kp.chan, kp.channel, rs, pout, kp.masses, kp.ch_s0, kp.ch_t0);
+            wps = wfac * channel_share<NOUT>(kp.chan, channel, rs, pout, kp.masses, kp.ch_s0, kp.ch_t0);
     } else {
         wps = kp.w0_const * wfac;
 #pragma unroll
@@ -176,13 +177,25 @@ template <typename R, int BLOCK>
 MF_DEV void load_block_constants(const KParams &kp, double *s_grid, cx<R> *cpl, R *mass_r) {
     using namespace MF_PROC;
     const int tid = threadIdx.x;
-    if (kp.mode == 1 || kp.mode == 3 || kp.mode == 4 || kp.mode == 5) {
+    if ((kp.mode == 1 && !kp.ch_off) || kp.mode == 3 || kp.mode == 4 || kp.mode == 5) {
         for (int i = tid; i < NDIM * (kp.nb + 1); i += BLOCK) s_grid[i] = kp.grid[i];
     }
     if (tid < 8) {
         mass_r[tid] = (R)kp.masses[tid];
         cpl[tid] = C<R>((R)kp.couplings[2 * tid], (R)kp.couplings[2 * tid + 1]);
     }
+}
+
+// The channel of point e of a launch over every channel (mode 1 with
+// ch_off): the k with ch_off[k] <= e < ch_off[k+1].
+MF_DEV int point_channel(const KParams &kp, int64_t e) {
+    int lo = 0, hi = kp.ch_count;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (kp.ch_off[mid] <= e) lo = mid;
+        else hi = mid;
+    }
+    return lo;
 }
 
 // Colour sampling: the unbiased estimate of a helicity's colour sum from
@@ -210,8 +223,14 @@ MF_DEV double sampled_colour_value(const cx<R> *J, int k) {
 // (given points: (e, 0, 0, 12) with the process's sampling key).
 MF_DEV int sampled_colour_flow(const KParams &kp, int64_t e, uint64_t iteration) {
     const bool given = kp.mode == 0 || kp.mode == 2;
-    uint64_t c[4] = {given ? (uint64_t)e : ((kp.mode == 3 || kp.mode == 5) ? (uint64_t)kp.idx[e] : (uint64_t)(e + kp.ev0)),
-                     given ? 0ull : iteration, given ? 0ull : kp.subprocess, 12ull};
+    uint64_t gi = given ? (uint64_t)e : ((kp.mode == 3 || kp.mode == 5) ? (uint64_t)kp.idx[e] : (uint64_t)(e + kp.ev0));
+    uint64_t sub = given ? 0ull : kp.subprocess;
+    if (kp.mode == 1 && kp.ch_off) {
+        const int k = point_channel(kp, e);
+        gi = (uint64_t)(e - kp.ch_off[k]);
+        sub = (uint64_t)k;
+    }
+    uint64_t c[4] = {gi, given ? 0ull : iteration, sub, 12ull};
     philox4x64_10(c, kp.seed, 0ull);
     int k = (int)(unit_from_bits(c[0]) * MF_PROC::NJAMP);
     return k < MF_PROC::NJAMP ? k : MF_PROC::NJAMP - 1;
@@ -293,6 +312,8 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
         bool ok = false, finite_in = true;
         double pref = 0.0, jv = 1.0;
         uint8_t bins[NDIM];
+        int chn = kp.channel;                       // phase-space channel of the point (-1: flat)
+        int64_t bin_base = e, bin_stride = kp.n;    // where the point's bin indices go (mode 1)
         if (e < kp.n) {
             // ---------------- phase A: kinematics in double precision
             double y[NDIM];
@@ -303,10 +324,22 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
                     finite_in &= isfinite(y[j]);
                 }
             } else {
-                const uint64_t gi = (kp.mode == 3 || kp.mode == 5) ? (uint64_t)kp.idx[e] : (uint64_t)(e + kp.ev0);
+                uint64_t gi = (kp.mode == 3 || kp.mode == 5) ? (uint64_t)kp.idx[e] : (uint64_t)(e + kp.ev0);
+                uint64_t sub = kp.subprocess;
+                const double *grid = s_grid;
+                if (kp.mode == 1 && kp.ch_off) {
+                    // one launch over every channel: point e is point gi of channel chn
+                    chn = point_channel(kp, e);
+                    const int64_t off = kp.ch_off[chn];
+                    gi = (uint64_t)(e - off);
+                    sub = (uint64_t)chn;
+                    grid = kp.ch_grids[chn];
+                    bin_base = off * NDIM + (e - off);
+                    bin_stride = kp.ch_off[chn + 1] - off;
+                }
 #pragma unroll
                 for (int b = 0; b < (NDIM + 3) / 4; ++b) {
-                    uint64_t c[4] = {gi, iteration, kp.subprocess, (uint64_t)b};
+                    uint64_t c[4] = {gi, iteration, sub, (uint64_t)b};
                     philox4x64_10(c, kp.seed, 0ull);
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
@@ -316,13 +349,13 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
                 for (int j = 0; j < NDIM; ++j) {
                     double xj;
                     int bj;
-                    jv *= vegas_map1(s_grid + j * (kp.nb + 1), kp.nb, y[j], xj, bj);
+                    jv *= vegas_map1(grid + j * (kp.nb + 1), kp.nb, y[j], xj, bj);
                     y[j] = xj;
                     bins[j] = (uint8_t)bj;
                 }
             }
             EventKin<double> ev;
-            ok = phase_a<double>(kp, y, kp.masses, kp.ln_tau_min, ev) && finite_in;
+            ok = phase_a<double>(kp, y, kp.masses, kp.ln_tau_min, ev, chn) && finite_in;
             if (kp.mode == 3) {
                 // event record: x1, x2 and the momenta boosted along z from the
                 // partonic centre-of-mass frame to the collider frame
@@ -363,9 +396,12 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
                 // helicity sampling: one helicity (or, in mode 2, one helicity
                 // pair) per point, uniform over the non-vanishing ones, from
                 // Philox block 14 of the point's counter
+                const bool per_channel = kp.mode == 1 && kp.ch_off;
                 uint64_t c[4] = {kp.mode == 0 ? (uint64_t)e
-                                 : (kp.mode == 3 ? (uint64_t)kp.idx[e] : (uint64_t)(e + kp.ev0)),
-                                 kp.mode == 0 ? 0ull : iteration, kp.mode == 0 ? 0ull : kp.subprocess, 14ull};
+                                 : (kp.mode == 3 ? (uint64_t)kp.idx[e]
+                                                 : (per_channel ? (uint64_t)(e - kp.ch_off[chn]) : (uint64_t)(e + kp.ev0))),
+                                 kp.mode == 0 ? 0ull : iteration,
+                                 kp.mode == 0 ? 0ull : (per_channel ? (uint64_t)chn : kp.subprocess), 14ull};
                 philox4x64_10(c, kp.seed, 0ull);
                 const int nchoice = sample_pairs<TC>(kp) ? kp.npairs : kp.nhel;
                 int h = (int)(unit_from_bits(c[0]) * nchoice);
@@ -546,7 +582,7 @@ MF_DEV void tile_body(const KParams &kp, const int64_t tile, unsigned char *smem
             } else if (kp.mode == 1) {
                 kp.w_out[e] = fval * jv;
 #pragma unroll
-                for (int j = 0; j < NDIM; ++j) kp.bins_out[(int64_t)j * kp.n + e] = bins[j];
+                for (int j = 0; j < NDIM; ++j) kp.bins_out[bin_base + (int64_t)j * bin_stride] = bins[j];
             }
         }
         __syncthreads();

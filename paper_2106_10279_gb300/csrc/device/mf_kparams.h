@@ -61,8 +61,13 @@ struct mf_kparams {
     double obs_scale[MF_KP_MAX_OBS];   // nbins / (hi - lo)
     const int32_t *chan;       // multichannel table (device/mf_channels.cuh), may be NULL
     int32_t channel;           // modes 0, 1: phase-space channel of the points, -1: RAMBO
-    int32_t pad5;
+    int32_t ch_count;          // mode 1 with ch_off: channels of the launch
     double ch_s0, ch_t0;       // channel propagator regulators (GeV^2)
+    // mode 1, one launch over every channel: points [ch_off[k], ch_off[k+1])
+    // are points 0.. of channel k, mapped through grid ch_grids[k]; their bin
+    // indices go to bins_out + ch_off[k] NDIM as SoA [NDIM][n_k]
+    const long long *ch_off;
+    const double *const *ch_grids;
     double masses[8];
     double couplings[16];      // 8 complex couplings (re, im)
     int8_t hel[MF_KP_MAX_HEL][8];

@@ -1116,6 +1116,8 @@ extern "C" mf_status mf_destroy_process(mf_process *p) {
     cudaFree(p->d_pdf_rows);
     cudaFree(p->d_err);
     cudaFree(p->d_chan);
+    cudaFree(p->d_ch_off);
+    cudaFree(p->d_ch_grids);
     cudaFree(p->d_w);
     cudaFree(p->d_bins);
     delete p;
@@ -1350,6 +1352,8 @@ mf_status tree_reduce(const double *nodes, int n_nodes, int K, int64_t nchunks, 
 int partial_size(const mf_vegas *v) { return 4 + 2 * v->ndim * v->nbins; }
 
 // Process scratch (w, bins) for n points and grid slots for their chunks.
+mf_status ensure_slots(mf_vegas *v, int64_t n);
+
 mf_status ensure_scratch(mf_process *p, mf_vegas *v, int64_t n) {
     if (p->scratch_n < n) {
         cudaFree(p->d_w);
@@ -1361,6 +1365,19 @@ mf_status ensure_scratch(mf_process *p, mf_vegas *v, int64_t n) {
         MF_CUDA(mfi::dev_malloc(&p->d_bins, (size_t)p->ndim * n));
         p->scratch_n = n;
     }
+    if (v) {
+        mf_status st = ensure_slots(v, n);
+        if (st != MF_OK) return st;
+    }
+    if (!p->ev_start) {
+        MF_CUDA(cudaEventCreate(&p->ev_start));
+        MF_CUDA(cudaEventCreate(&p->ev_stop));
+    }
+    return MF_OK;
+}
+
+// Chunk slots of a grid for an iteration of n points.
+mf_status ensure_slots(mf_vegas *v, int64_t n) {
     const int64_t nchunks = (n + kChunk - 1) / kChunk;
     const int K = partial_size(v);
     if (v->slots_cap < nchunks * K + K) {
@@ -1369,10 +1386,6 @@ mf_status ensure_scratch(mf_process *p, mf_vegas *v, int64_t n) {
         v->slots_cap = 0;
         MF_CUDA(mfi::dev_malloc(&v->d_slots, sizeof(double) * (nchunks * K + K)));
         v->slots_cap = nchunks * K + K;
-    }
-    if (!p->ev_start) {
-        MF_CUDA(cudaEventCreate(&p->ev_start));
-        MF_CUDA(cudaEventCreate(&p->ev_stop));
     }
     return MF_OK;
 }
@@ -1434,7 +1447,7 @@ mf_status accumulate(mf_process *p, mf_vegas *v, int64_t n, cudaStream_t s) {
 // Evaluate points [ev0, ev0 + n) of iteration v->iteration into the process
 // scratch (w, bins) and accumulate their chunks into v->d_slots.
 mf_status run_points(mf_process *p, mf_vegas *v, int prec, int64_t n, int64_t ev0, int subprocess, uint64_t seed,
-                     cudaStream_t s, int channel = -1) {
+                     cudaStream_t s) {
     mf_status st = compile_precision(p, prec);
     if (st != MF_OK) return st;
     st = ensure_scratch(p, v, n);
@@ -1443,7 +1456,6 @@ mf_status run_points(mf_process *p, mf_vegas *v, int prec, int64_t n, int64_t ev
     if (n == 0) return MF_OK;
     mf_kparams kp;
     vegas_params(p, v, n, ev0, subprocess, seed, kp);
-    kp.channel = channel;
     MF_CUDA(cudaEventRecord(p->ev_start, s));
     st = launch(p, prec, kp, s);
     if (st != MF_OK) return st;
@@ -1693,12 +1705,50 @@ extern "C" mf_status mf_vegas_iterate_channels(mf_vegas *const *grids, mf_proces
         std::sort(g.begin(), g.end());
         if (std::adjacent_find(g.begin(), g.end()) != g.end()) return fail(MF_EINVAL, "a grid appears twice");
     }
+    for (int k = 1; k < n_channels; ++k)
+        if (grids[k]->nbins != grids[0]->nbins || grids[k]->iteration != grids[0]->iteration)
+            return fail(MF_EINVAL, "the channels' grids differ in bins or iteration");
+    // one launch over every channel's points: channel k takes points
+    // [off[k], off[k+1]) of the launch, as points 0.. of its own stream
+    std::vector<long long> off(n_channels + 1, 0);
+    std::vector<const double *> gptr(n_channels);
+    for (int k = 0; k < n_channels; ++k) {
+        off[k + 1] = off[k] + n_events[k];
+        gptr[k] = grids[k]->d_grid;
+    }
+    const int64_t N = off[n_channels];
+    mf_status st = compile_precision(p, prec);
+    if (st != MF_OK) return st;
+    st = ensure_scratch(p, nullptr, N);
+    if (st != MF_OK) return st;
+    for (int k = 0; k < n_channels; ++k) {
+        st = ensure_slots(grids[k], n_events[k]);
+        if (st != MF_OK) return st;
+    }
+    if (!p->d_ch_off) {
+        MF_CUDA(mfi::dev_malloc(&p->d_ch_off, sizeof(long long) * (n_channels + 1)));
+        MF_CUDA(mfi::dev_malloc(&p->d_ch_grids, sizeof(double *) * n_channels));
+    }
+    // pageable sources: the copies are staged before the calls return
+    MF_CUDA(cudaMemcpyAsync(p->d_ch_off, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice, s));
+    MF_CUDA(cudaMemcpyAsync(p->d_ch_grids, gptr.data(), sizeof(double *) * gptr.size(), cudaMemcpyHostToDevice, s));
+    p->last_n = N;
+    mf_kparams kp;
+    vegas_params(p, grids[0], N, 0, 0, seed, kp);
+    kp.grid = nullptr;
+    kp.ch_off = p->d_ch_off;
+    kp.ch_grids = p->d_ch_grids;
+    kp.ch_count = n_channels;
+    MF_CUDA(cudaEventRecord(p->ev_start, s));
+    st = launch(p, prec, kp, s);
+    if (st != MF_OK) return st;
+    MF_CUDA(cudaEventRecord(p->ev_stop, s));
     std::vector<double> res((size_t)n_channels * 8);
-    std::vector<int> flags(n_channels, 0);
+    int flag = 0;
     for (int k = 0; k < n_channels; ++k) {
         mf_vegas *v = grids[k];
         const int64_t n = n_events[k];
-        mf_status st = run_points(p, v, prec, n, 0, k, seed, s, k);
+        st = accumulate_into(p->d_w + off[k], p->d_bins + off[k] * p->ndim, n, v, v->d_slots, s);
         if (st != MF_OK) return st;
         const int64_t nchunks = (n + kChunk - 1) / kChunk;
         const std::vector<int64_t> root = {tree_levels(nchunks), 0};
@@ -1707,15 +1757,13 @@ extern "C" mf_status mf_vegas_iterate_channels(mf_vegas *const *grids, mf_proces
         st = finish(v, v->d_tree_out, n, refine, s);
         if (st != MF_OK) return st;
         MF_CUDA(cudaMemcpyAsync(&res[(size_t)k * 8], v->d_result, sizeof(double) * 7, cudaMemcpyDeviceToHost, s));
-        MF_CUDA(cudaMemcpyAsync(&flags[k], p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     }
+    MF_CUDA(cudaMemcpyAsync(&flag, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     MF_CUDA(cudaStreamSynchronize(s));
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, p->ev_start, p->ev_stop) == cudaSuccess) p->last_kernel_ms = ms;
-    for (int k = 0; k < n_channels; ++k) {
-        mf_status st = flag_status(p, flags[k]);
-        if (st != MF_OK) return st;
-    }
+    st = flag_status(p, flag);
+    if (st != MF_OK) return st;
     bool any_nan = false;
     for (int k = 0; k < n_channels; ++k) {
         fill_result(out[k], grids[k], n_events[k], &res[(size_t)k * 8]);

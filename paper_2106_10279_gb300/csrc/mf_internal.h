@@ -126,6 +126,8 @@ struct mf_process {
     mfi::ChannelSet channels;
     int32_t *d_chan = nullptr;
     double ch_s0 = 1.0, ch_t0 = 1.0;
+    long long *d_ch_off = nullptr;      // [K+1] point offsets of a launch over every channel
+    double **d_ch_grids = nullptr;      // [K] the channels' grids
 };
 
 struct mf_vegas {
