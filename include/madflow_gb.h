@@ -638,6 +638,25 @@ mf_status mf_vegas_observables(mf_vegas *v, mf_process *p, int64_t n_events, uin
 mf_status mf_vegas_unweight(mf_vegas *v, mf_process *p, int64_t n_events, uint64_t seed, int32_t subprocess,
                             mf_precision prec, double w_max, mf_lhe_writer *lhe, double *records, int64_t capacity,
                             int64_t *n_accepted, void *stream);
+
+/* mf_vegas_unweight_channel: mf_vegas_unweight for phase-space channel
+ * `channel` (see mf_vegas_iterate_channels): the points are those of the
+ * channel's own stream (subprocess index = channel) through its grid v, with
+ * the channel's momenta and weight a_i / g_i.  To unweight the combined
+ * sample of an iteration of N points (n_k in channel k) against one
+ * maximum W of the combined weights W = w N / n_k, pass w_max = W n_k / N
+ * for channel k: every event then weighs W / N.  MF_EUNSUPPORTED if the
+ * process has no channels, MF_EINVAL for a channel out of range. */
+mf_status mf_vegas_unweight_channel(mf_vegas *v, mf_process *p, int32_t channel, int64_t n_events, uint64_t seed,
+                                    mf_precision prec, double w_max, mf_lhe_writer *lhe, double *records,
+                                    int64_t capacity, int64_t *n_accepted, void *stream);
+
+/* mf_process_channel_max_weights: after mf_vegas_iterate_channels with
+ * n_events[k] points in channel k, the largest |w| of each channel's points
+ * into host w_max[n_channels].  MF_EINVAL if the counts do not add up to
+ * that pass's points.  Synchronous. */
+mf_status mf_process_channel_max_weights(mf_process *p, const int64_t *n_events, int32_t n_channels, double *w_max,
+                                         void *stream);
 /* mf_process_read_weights: the weights w = f J_V of chosen points (host
  * idx[n], point indices of the pass) of the process's last Vegas pass, into
  * host w[n] (for checking single points of a large iteration).  Synchronous

@@ -657,6 +657,22 @@ class MultiChannel:
         }
         return tot
 
+    def unweight(self, n_total: int, seed: int, W_max: float, precision="mixed", lhe: LheWriter = None,
+                 n_floor=None, stream=None):
+        """Unweighted events of one pass of n_total points over the channels
+        (the current allocation) against one maximum W_max of the combined
+        weights W = w N / n_k: channel k is unweighted against W_max n_k / N,
+        so every event weighs W_max / N.  Returns (number kept, records)."""
+        n = self.allocation(n_total, n_floor)
+        N = sum(n)
+        tot, recs = 0, []
+        for k, nk in enumerate(n):
+            acc, rec = unweight_channel(self.grids[k], self.proc, k, nk, seed, W_max * nk / N, precision, lhe,
+                                        stream=stream)
+            tot += acc
+            recs.append(rec)
+        return tot, np.concatenate(recs) if recs else np.zeros((0, 0))
+
     def close(self):
         for g in self.grids:
             g.close()
@@ -722,6 +738,34 @@ def unweight(grid: "Vegas", proc: "Process", n_events: int, seed: int, w_max: fl
                                    C.byref(nacc), _stream_ptr(stream))
     L.check(st, "mf_vegas_unweight")
     return nacc.value, rec[:min(nacc.value, cap)]
+
+
+def unweight_channel(grid: "Vegas", proc: "Process", channel: int, n_events: int, seed: int, w_max: float,
+                     precision="mixed", lhe: LheWriter = None, capacity=None, stream=None):
+    """Hit-or-miss unweighted events of one pass of phase-space channel
+    `channel` through its grid (see mf_vegas_unweight_channel); returns as
+    unweight."""
+    nl = proc.info["n_legs"]
+    cap = n_events if capacity is None else capacity
+    rec = np.zeros((max(cap, 0), 4 + 4 * nl))
+    nacc = C.c_int64()
+    st = L.lib().mf_vegas_unweight_channel(grid.handle, proc.handle, channel, n_events, seed, _PREC[precision],
+                                           w_max, lhe.handle if lhe else None,
+                                           rec.ctypes.data_as(C.POINTER(C.c_double)), cap, C.byref(nacc),
+                                           _stream_ptr(stream))
+    L.check(st, "mf_vegas_unweight_channel")
+    return nacc.value, rec[:min(nacc.value, cap)]
+
+
+def channel_max_weights(proc: "Process", n_events, stream=None):
+    """Largest |w| of each channel's points in the last mf_vegas_iterate_channels
+    pass of n_events[k] points per channel."""
+    k = len(n_events)
+    N = (C.c_int64 * k)(*[int(v) for v in n_events])
+    out = (C.c_double * k)()
+    L.check(L.lib().mf_process_channel_max_weights(proc.handle, N, k, out, _stream_ptr(stream)),
+            "mf_process_channel_max_weights")
+    return [float(v) for v in out]
 
 
 OBSERVABLE_KINDS = {"pt": L.MF_OBS_PT, "y": L.MF_OBS_RAPIDITY, "eta": L.MF_OBS_PSEUDORAPIDITY}

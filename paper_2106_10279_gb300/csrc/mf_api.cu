@@ -2606,9 +2606,13 @@ extern "C" mf_status mf_process_max_weight(mf_process *p, double *w_max, void *s
     return MF_OK;
 }
 
-extern "C" mf_status mf_vegas_unweight(mf_vegas *v, mf_process *p, int64_t n_events, uint64_t seed,
-                                       int32_t subprocess, mf_precision prec, double w_max, mf_lhe_writer *lhe,
-                                       double *records, int64_t capacity, int64_t *n_accepted, void *stream) {
+namespace {
+
+// Unweighting of the points of one subprocess stream; channel >= 0 takes
+// the points' momenta and weights from that phase-space channel.
+mf_status unweight_impl(mf_vegas *v, mf_process *p, int64_t n_events, uint64_t seed, int32_t subprocess,
+                        int32_t channel, mf_precision prec, double w_max, mf_lhe_writer *lhe, double *records,
+                        int64_t capacity, int64_t *n_accepted, void *stream) {
     if (!v || !p || !n_accepted) return fail(MF_EINVAL, "NULL argument");
     if (!valid_prec(prec)) return fail(MF_EINVAL, "bad precision");
     if (v->ndim != p->ndim) return fail(MF_EINVAL, "grid and process dimensions differ");
@@ -2626,6 +2630,7 @@ extern "C" mf_status mf_vegas_unweight(mf_vegas *v, mf_process *p, int64_t n_eve
     // the weights of the pass
     mf_kparams kp;
     vegas_params(p, v, n, 0, subprocess, seed, kp);
+    kp.channel = channel;
     st = launch(p, prec, kp, s);
     if (st != MF_OK) return st;
     p->last_n = n;
@@ -2690,6 +2695,7 @@ extern "C" mf_status mf_vegas_unweight(mf_vegas *v, mf_process *p, int64_t n_eve
         kr.mode = 3;
         kr.idx = d_idx;
         kr.f = d_rec;
+        kr.channel = channel;
         st = launch(p, prec, kr, s);
         if (st != MF_OK) {
             cleanup();
@@ -2703,6 +2709,7 @@ extern "C" mf_status mf_vegas_unweight(mf_vegas *v, mf_process *p, int64_t n_eve
         kc.hel_sample = 0;
         kc.idx = d_idx;
         kc.flow_out = d_flow;
+        kc.channel = channel;
         st = launch(p, prec, kc, s);
         if (st != MF_OK) {
             cleanup();
@@ -2740,6 +2747,58 @@ extern "C" mf_status mf_vegas_unweight(mf_vegas *v, mf_process *p, int64_t n_eve
     }
 #undef MF_UW
     cleanup();
+    return MF_OK;
+}
+
+}  // namespace
+
+extern "C" mf_status mf_vegas_unweight(mf_vegas *v, mf_process *p, int64_t n_events, uint64_t seed,
+                                       int32_t subprocess, mf_precision prec, double w_max, mf_lhe_writer *lhe,
+                                       double *records, int64_t capacity, int64_t *n_accepted, void *stream) {
+    return unweight_impl(v, p, n_events, seed, subprocess, -1, prec, w_max, lhe, records, capacity, n_accepted,
+                         stream);
+}
+
+extern "C" mf_status mf_vegas_unweight_channel(mf_vegas *v, mf_process *p, int32_t channel, int64_t n_events,
+                                               uint64_t seed, mf_precision prec, double w_max, mf_lhe_writer *lhe,
+                                               double *records, int64_t capacity, int64_t *n_accepted,
+                                               void *stream) {
+    if (!p) return fail(MF_EINVAL, "NULL process");
+    if (p->channels.K == 0) return fail(MF_EUNSUPPORTED, "the process has no phase-space channels");
+    if (channel < 0 || channel >= p->channels.K) return fail(MF_EINVAL, "channel out of range");
+    return unweight_impl(v, p, n_events, seed, channel, channel, prec, w_max, lhe, records, capacity, n_accepted,
+                         stream);
+}
+
+extern "C" mf_status mf_process_channel_max_weights(mf_process *p, const int64_t *n_events, int32_t n_channels,
+                                                    double *w_max, void *stream) {
+    if (!p || !n_events || !w_max) return fail(MF_EINVAL, "NULL argument");
+    if (n_channels < 1 || n_channels != p->channels.K) return fail(MF_EINVAL, "one count per channel of the process");
+    int64_t tot = 0;
+    for (int k = 0; k < n_channels; ++k) {
+        if (n_events[k] < 0) return fail(MF_EINVAL, "negative count");
+        tot += n_events[k];
+    }
+    if (tot != p->last_n) return fail(MF_EINVAL, "the counts do not add up to the last pass's points");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long *d = nullptr;
+    MF_CUDA(mfi::dev_malloc(&d, sizeof(unsigned long long) * n_channels));
+    std::vector<unsigned long long> h(n_channels, 0);
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned long long) * n_channels, s);
+    int64_t off = 0;
+    for (int k = 0; k < n_channels && e == cudaSuccess; ++k) {
+        if (n_events[k] > 0) {
+            max_abs_kernel<<<304, 256, 0, s>>>(p->d_w + off, n_events[k], d + k);
+            e = cudaGetLastError();
+        }
+        off += n_events[k];
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d, sizeof(unsigned long long) * n_channels,
+                                              cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(MF_ECUDA, std::string("max weights: ") + cudaGetErrorString(e));
+    for (int k = 0; k < n_channels; ++k) std::memcpy(&w_max[k], &h[k], sizeof(double));
     return MF_OK;
 }
 

@@ -13,6 +13,12 @@
 * The channels' summed cross section of gg -> tt~ agrees with the quadrature
   value and that of gg -> tt~gg with the flat phase space's, within the
   combined errors; the multichannel error is the smaller at equal points.
+* The largest weight of each channel's points (mf_process_channel_max_weights)
+  is the oracle's within the per-point tolerance.
+* Unweighted events of a channel (mf_vegas_unweight_channel): the same
+  points kept as by the oracle on the channel's Philox stream, with the same
+  event weights, momentum fractions, collider-frame momenta (FP64) and
+  leading-colour flows.
 * Argument checks: a channel out of range, a grid count other than the
   process's channels.
 """
@@ -87,6 +93,7 @@ def _oracle_channel_iteration(I, ch, ndim, n, seed, chunk=20000):
     dsum = np.zeros((ndim, 50))
     bound = np.zeros((ndim, 50))
     cnt = np.zeros_like(dsum, dtype=np.int64)
+    wmax, wtol = 0.0, 0.0
     for start in range(0, n, chunk):
         m = min(chunk, n - start)
         y = vegas_uniforms(seed, 0, ch, start, m, ndim)
@@ -98,8 +105,11 @@ def _oracle_channel_iteration(I, ch, ndim, n, seed, chunk=20000):
         t2 = np.where(np.isfinite(tol), 2 * tol, 0.0) * w * w
         for j in range(ndim):
             np.add.at(bound[j], bins[j], t2)
+        a = np.abs(w)
+        if a.max() > wmax:
+            wmax, wtol = float(a.max()), float(tol[np.argmax(a)])
     I_k, err = vegas.iteration_result(s1, s2, n)
-    return I_k, err, dsum, cnt, bound
+    return I_k, err, dsum, cnt, bound, (wmax, wtol)
 
 
 @pytest.mark.parametrize("name,n", [("gg_ttx", 20000), ("gg_ttxg", 3000)])
@@ -111,8 +121,10 @@ def test_first_channel_iteration_matches_the_oracle(env, name, n):
     grids = [api.Vegas(wl.ndim, 50, 1.5) for _ in range(K)]
     res = api.mf_vegas_iterate_channels([g.handle for g in grids], proc.handle, [n] * K, 777, "fp64")
     I = _oracle(name)
+    mw = api.channel_max_weights(proc, [n] * K)
     for k in range(K):
-        I_k, err, dsum, cnt, bound = _oracle_channel_iteration(I, k, wl.ndim, n, 777)
+        I_k, err, dsum, cnt, bound, (wmax, wtol) = _oracle_channel_iteration(I, k, wl.ndim, n, 777)
+        assert abs(mw[k] - wmax) <= wtol * wmax, (k, mw[k], wmax)
         hs, hc = grids[k].histogram()
         assert np.array_equal(hc, cnt), k
         assert abs(res[k]["integral"] - I_k) <= 1e-11 * abs(I_k) + 1e-300, k
@@ -174,3 +186,37 @@ def test_channel_argument_checks(env):
     assert e.value.status == L.MF_EINVAL
     ee = api.Process.from_workload(W.WORKLOADS["ee_mumu"])
     assert ee.n_channels == 1
+
+
+def test_channel_unweighting_matches_the_oracle(env):
+    torch, api = env
+    from oracle import unweight as uw
+    from oracle import vegas as ov
+    from oracle.philox import vegas_uniforms
+    name, k, n, seed = "gg_ttxg", 6, 20000, 21
+    wl = W.WORKLOADS[name]
+    I = _oracle(name)
+    op = I.proc
+    y = vegas_uniforms(seed, 0, k, 0, n, wl.ndim)
+    x, jac, _ = ov.vegas_map(ov.uniform_grid(wl.ndim, wl.n_bins), y)
+    w = I(x, channel=k) * jac
+    w_max = float(np.quantile(np.abs(w[w != 0]), 0.6))
+    u = uw.accept_uniforms(seed, 0, k, n)
+    keep = uw.keep(w, u, w_max)
+    assert not (np.abs(np.abs(w) - u * w_max) <= 1e-9 * w_max).any()
+    idx = np.nonzero(keep)[0]
+    p, s_hat, x1, x2, jx, wps, ok = I.kinematics(x[:, idx], channel=k)
+    p_lab = uw.lab_frame(p, x1, x2)
+    pick, gap = uw.draw_flows(op.leading_colour_weights(p), uw.colour_uniforms(seed, 0, k, idx))
+    proc = api.Process.from_workload(wl)
+    grid = api.Vegas(wl.ndim)
+    nacc, rec = api.unweight_channel(grid, proc, k, n, seed, w_max, precision="fp64")
+    assert nacc == len(idx) and nacc > 100
+    assert np.allclose(rec[:, 0], uw.event_weights(w[idx], w_max, n), rtol=1e-11, atol=0)
+    assert np.allclose(rec[:, 1], x1, rtol=1e-13, atol=0)
+    assert np.allclose(rec[:, 2], x2, rtol=1e-13, atol=0)
+    mom = rec[:, 4:].reshape(nacc, len(wl.legs), 4)
+    assert np.max(np.abs(mom - p_lab)) < 1e-9 * wl.sqrt_s
+    clear = gap > 1e-9
+    assert clear.mean() > 0.99
+    assert np.array_equal(rec[clear, 3].astype(int), pick[clear])
