@@ -146,9 +146,8 @@ __device__ double block_tree_sum(double *buf, int m) {
     return r;
 }
 
-__global__ void __launch_bounds__(kAccThreads) vegas_accumulate_kernel(const double *w, const uint8_t *bins,
-                                                                       int64_t n, int ndim, int nb, double *slots,
-                                                                       int64_t ld) {
+__device__ void accumulate_chunk(const double *w, const uint8_t *bins, int64_t n, int ndim, int nb, double *slots,
+                                 int64_t ld, int64_t chunk) {
     extern __shared__ double sh[];
     double *sw = sh;                    // [kChunk] sanitised w
     double *buf = sh + kChunk;          // [kChunk] tree buffer
@@ -156,9 +155,9 @@ __global__ void __launch_bounds__(kAccThreads) vegas_accumulate_kernel(const dou
     __shared__ int wcnt[kAccThreads / 32][64];
     __shared__ double stage[kAccThreads / 32][32];
     __shared__ int s_nz, s_nan;
-    const int64_t base = (int64_t)blockIdx.x * kChunk;
+    const int64_t base = chunk * kChunk;
     const int m = (int)((n - base) < kChunk ? (n - base) : kChunk);
-    double *slot = slots + blockIdx.x;      // component k at slot[k * ld]
+    double *slot = slots + chunk;           // component k at slot[k * ld]
     if (threadIdx.x == 0) { s_nz = 0; s_nan = 0; }
     __syncthreads();
     int nz = 0, nn = 0;
@@ -227,19 +226,56 @@ __global__ void __launch_bounds__(kAccThreads) vegas_accumulate_kernel(const dou
     }
 }
 
+__global__ void __launch_bounds__(kAccThreads) vegas_accumulate_kernel(const double *w, const uint8_t *bins,
+                                                                       int64_t n, int ndim, int nb, double *slots,
+                                                                       int64_t ld) {
+    accumulate_chunk(w, bins, n, ndim, nb, slots, ld, blockIdx.x);
+}
+
+// Per-channel state of a multichannel iteration's bookkeeping (one record
+// per channel, device memory): its segment of the launch's weights and bin
+// indices, its chunk count and tree level, and its grid's buffers.
+struct ChanAcc {
+    const double *w;
+    const uint8_t *bins;
+    long long n, nchunks;
+    int level, iteration;
+    double alpha;
+    double *slots, *tree_out, *hist, *hist_iter, *result, *grid;
+    long long *count;
+    double *result_copy;        // the 7 results again, in one array for all channels
+};
+
+__device__ int chunk_channel(const long long *chunk_off, int nch, long long b) {
+    int lo = 0, hi = nch;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (chunk_off[mid] <= b) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Every channel's chunks in one launch: block b is chunk b - chunk_off[k] of
+// channel k (chunk_off[k] <= b < chunk_off[k+1]).
+__global__ void __launch_bounds__(kAccThreads) vegas_accumulate_channels_kernel(const ChanAcc *ca,
+                                                                                const long long *chunk_off, int nch,
+                                                                                int ndim, int nb) {
+    const int k = chunk_channel(chunk_off, nch, blockIdx.x);
+    const ChanAcc &c = ca[k];
+    accumulate_chunk(c.w, c.bins, c.n, ndim, nb, c.slots, c.nchunks, (int64_t)blockIdx.x - chunk_off[k]);
+}
+
 // Reduction over chunks along a fixed pairwise tree (mf_tree_reduce states the
 // tree).  Block (k, j) computes component k of node j = (level, index) from the
 // chunk partials slots[k * ld + c - c0] of the chunks the node covers: each
 // thread folds an aligned segment of 2^s chunks with a binary-counter stack
 // (which performs exactly the tree's additions, the last incomplete subtree
 // folded from its right end), then the segments are paired in shared memory.
-__global__ void __launch_bounds__(kTreeThreads) vegas_tree_kernel(const double *slots, int64_t ld, int64_t c0,
-                                                                  int64_t nchunks, int K, const int64_t *node_ids,
-                                                                  double *out) {
+__device__ double tree_node(const double *slots, int64_t ld, int64_t c0, int64_t nchunks, int k, int level,
+                            int64_t index) {
     __shared__ double red[kTreeThreads];
-    const int k = blockIdx.x;
-    const int level = (int)node_ids[2 * blockIdx.y];
-    const int64_t first = node_ids[2 * blockIdx.y + 1] << level;
+    const int64_t first = index << level;
     const int s = level > kTreeLog ? level - kTreeLog : 0;
     const int64_t nseg = ((int64_t)1 << level) >> s;                // <= kTreeThreads
     const int64_t seg_first = first + ((int64_t)threadIdx.x << s);
@@ -279,15 +315,32 @@ __global__ void __launch_bounds__(kTreeThreads) vegas_tree_kernel(const double *
         m = (m + 1) >> 1;
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[(size_t)blockIdx.y * K + k] = red[0];
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kTreeThreads) vegas_tree_kernel(const double *slots, int64_t ld, int64_t c0,
+                                                                  int64_t nchunks, int K, const int64_t *node_ids,
+                                                                  double *out) {
+    const int k = blockIdx.x;
+    const double r = tree_node(slots, ld, c0, nchunks, k, (int)node_ids[2 * blockIdx.y], node_ids[2 * blockIdx.y + 1]);
+    if (threadIdx.x == 0) out[(size_t)blockIdx.y * K + k] = r;
+}
+
+// Block (k, c): component k of channel c's root node.
+__global__ void __launch_bounds__(kTreeThreads) vegas_tree_channels_kernel(const ChanAcc *ca, int K) {
+    const ChanAcc &c = ca[blockIdx.y];
+    const double r = tree_node(c.slots, c.nchunks, 0, c.nchunks, blockIdx.x, c.level, 0);
+    if (threadIdx.x == 0) c.tree_out[blockIdx.x] = r;
 }
 
 // Iteration estimate, the histogram, and the inverse-variance combination of
 // all iterations so far (iterations with zero variance are exact: if any, the
 // result is their mean with zero error).  res: [I, err, sigma, sigma_err,
 // chi2/dof, nonzero, nan].
-__global__ void vegas_finalize_kernel(const double *tot, int64_t n, int ndim, int nb, int it, double *hist,
-                                      long long *count, double *iters, double *res) {
+__device__ void finalize_body(const double *tot, int64_t n, int ndim, int nb, int it, double *hist,
+                              long long *count, double *iters, double *res) {
     for (int i = threadIdx.x; i < ndim * nb; i += blockDim.x) {
         hist[i] = tot[4 + i];
         count[i] = (long long)tot[4 + ndim * nb + i];
@@ -326,6 +379,19 @@ __global__ void vegas_finalize_kernel(const double *tot, int64_t n, int ndim, in
     }
     res[0] = I; res[1] = err; res[2] = mean; res[3] = merr; res[4] = chi2;
     res[5] = tot[2]; res[6] = tot[3];
+}
+
+__global__ void vegas_finalize_kernel(const double *tot, int64_t n, int ndim, int nb, int it, double *hist,
+                                      long long *count, double *iters, double *res) {
+    finalize_body(tot, n, ndim, nb, it, hist, count, iters, res);
+}
+
+// Block c: channel c's finalisation.
+__global__ void vegas_finalize_channels_kernel(const ChanAcc *ca, int ndim, int nb) {
+    const ChanAcc &c = ca[blockIdx.x];
+    finalize_body(c.tree_out, c.n, ndim, nb, c.iteration, c.hist, c.count, c.hist_iter, c.result);
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 7; ++q) c.result_copy[q] = c.result[q];
 }
 
 // The same with the iteration index read from device memory (graph replays).
@@ -377,9 +443,20 @@ __global__ void vegas_finalize_dev_kernel(const double *tot, int64_t n, int ndim
 }
 
 // Lepage refinement of every dimension (one thread per dimension).
+__device__ void refine_dim(double *grid, const double *hist, int ndim, int nb, int64_t n, double alpha, int j);
+
 __global__ void vegas_refine_kernel(double *grid, const double *hist, int ndim, int nb, int64_t n, double alpha) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= ndim) return;
+    if (j < ndim) refine_dim(grid, hist, ndim, nb, n, alpha, j);
+}
+
+// Block c: channel c's refinement, one thread per dimension.
+__global__ void vegas_refine_channels_kernel(const ChanAcc *ca, int ndim, int nb) {
+    const ChanAcc &c = ca[blockIdx.x];
+    if ((int)threadIdx.x < ndim) refine_dim(c.grid, c.hist, ndim, nb, c.n, c.alpha, threadIdx.x);
+}
+
+__device__ void refine_dim(double *grid, const double *hist, int ndim, int nb, int64_t n, double alpha, int j) {
     double *g = grid + (size_t)j * (nb + 1);
     const double *d = hist + (size_t)j * nb;
     double sm[256], comp[256], newe[257];
@@ -1118,6 +1195,9 @@ extern "C" mf_status mf_destroy_process(mf_process *p) {
     cudaFree(p->d_chan);
     cudaFree(p->d_ch_off);
     cudaFree(p->d_ch_grids);
+    cudaFree(p->d_ch_chunk_off);
+    cudaFree(p->d_ch_res);
+    cudaFree(p->d_ch_acc);
     cudaFree(p->d_w);
     cudaFree(p->d_bins);
     delete p;
@@ -1725,10 +1805,12 @@ extern "C" mf_status mf_vegas_iterate_channels(mf_vegas *const *grids, mf_proces
         st = ensure_slots(grids[k], n_events[k]);
         if (st != MF_OK) return st;
     }
-    if (!p->d_ch_off) {
-        MF_CUDA(mfi::dev_malloc(&p->d_ch_off, sizeof(long long) * (n_channels + 1)));
-        MF_CUDA(mfi::dev_malloc(&p->d_ch_grids, sizeof(double *) * n_channels));
-    }
+    // per-process buffers of the channel launches (K is fixed per process)
+    if (!p->d_ch_off) MF_CUDA(mfi::dev_malloc(&p->d_ch_off, sizeof(long long) * (n_channels + 1)));
+    if (!p->d_ch_grids) MF_CUDA(mfi::dev_malloc(&p->d_ch_grids, sizeof(double *) * n_channels));
+    if (!p->d_ch_chunk_off) MF_CUDA(mfi::dev_malloc(&p->d_ch_chunk_off, sizeof(long long) * (n_channels + 1)));
+    if (!p->d_ch_res) MF_CUDA(mfi::dev_malloc(&p->d_ch_res, sizeof(double) * 8 * n_channels));
+    if (!p->d_ch_acc) MF_CUDA(mfi::dev_malloc(&p->d_ch_acc, sizeof(ChanAcc) * n_channels));
     // pageable sources: the copies are staged before the calls return
     MF_CUDA(cudaMemcpyAsync(p->d_ch_off, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice, s));
     MF_CUDA(cudaMemcpyAsync(p->d_ch_grids, gptr.data(), sizeof(double *) * gptr.size(), cudaMemcpyHostToDevice, s));
@@ -1743,21 +1825,48 @@ extern "C" mf_status mf_vegas_iterate_channels(mf_vegas *const *grids, mf_proces
     st = launch(p, prec, kp, s);
     if (st != MF_OK) return st;
     MF_CUDA(cudaEventRecord(p->ev_stop, s));
-    std::vector<double> res((size_t)n_channels * 8);
-    int flag = 0;
+    // the channels' bookkeeping, four launches for all of them: chunk
+    // partial sums, each channel's root of the chunk tree, finalisation and
+    // refinement (the same arithmetic as the one-grid kernels)
+    std::vector<ChanAcc> ca(n_channels);
+    std::vector<long long> chunk_off(n_channels + 1, 0);
     for (int k = 0; k < n_channels; ++k) {
         mf_vegas *v = grids[k];
-        const int64_t n = n_events[k];
-        st = accumulate_into(p->d_w + off[k], p->d_bins + off[k] * p->ndim, n, v, v->d_slots, s);
-        if (st != MF_OK) return st;
-        const int64_t nchunks = (n + kChunk - 1) / kChunk;
-        const std::vector<int64_t> root = {tree_levels(nchunks), 0};
-        st = tree_nodes(v, nchunks, 0, nchunks, root, s);
-        if (st != MF_OK) return st;
-        st = finish(v, v->d_tree_out, n, refine, s);
-        if (st != MF_OK) return st;
-        MF_CUDA(cudaMemcpyAsync(&res[(size_t)k * 8], v->d_result, sizeof(double) * 7, cudaMemcpyDeviceToHost, s));
+        const long long nch = (n_events[k] + kChunk - 1) / kChunk;
+        chunk_off[k + 1] = chunk_off[k] + nch;
+        ChanAcc &c = ca[k];
+        c.w = p->d_w + off[k];
+        c.bins = p->d_bins + off[k] * p->ndim;
+        c.n = n_events[k];
+        c.nchunks = nch;
+        c.level = tree_levels(nch);
+        c.iteration = v->iteration;
+        c.alpha = v->alpha;
+        c.slots = v->d_slots;
+        c.tree_out = v->d_tree_out;
+        c.hist = v->d_hist;
+        c.hist_iter = v->d_hist_iter;
+        c.result = v->d_result;
+        c.grid = v->d_grid;
+        c.count = v->d_count;
+        c.result_copy = p->d_ch_res + (size_t)k * 8;
     }
+    MF_CUDA(cudaMemcpyAsync(p->d_ch_acc, ca.data(), sizeof(ChanAcc) * n_channels, cudaMemcpyHostToDevice, s));
+    MF_CUDA(cudaMemcpyAsync(p->d_ch_chunk_off, chunk_off.data(), sizeof(long long) * (n_channels + 1),
+                            cudaMemcpyHostToDevice, s));
+    const ChanAcc *d_ca = static_cast<const ChanAcc *>(p->d_ch_acc);
+    st = accumulate_attribute();
+    if (st != MF_OK) return st;
+    const int nb = grids[0]->nbins, Kp = partial_size(grids[0]);
+    vegas_accumulate_channels_kernel<<<(unsigned)chunk_off[n_channels], kAccThreads, kAccSmem, s>>>(
+        d_ca, p->d_ch_chunk_off, n_channels, p->ndim, nb);
+    vegas_tree_channels_kernel<<<dim3((unsigned)Kp, (unsigned)n_channels), kTreeThreads, 0, s>>>(d_ca, Kp);
+    vegas_finalize_channels_kernel<<<(unsigned)n_channels, 128, 0, s>>>(d_ca, p->ndim, nb);
+    if (refine) vegas_refine_channels_kernel<<<(unsigned)n_channels, 32, 0, s>>>(d_ca, p->ndim, nb);
+    MF_CUDA(cudaGetLastError());
+    std::vector<double> res((size_t)n_channels * 8);
+    int flag = 0;
+    MF_CUDA(cudaMemcpyAsync(res.data(), p->d_ch_res, sizeof(double) * 8 * n_channels, cudaMemcpyDeviceToHost, s));
     MF_CUDA(cudaMemcpyAsync(&flag, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     MF_CUDA(cudaStreamSynchronize(s));
     float ms = 0.f;

@@ -128,6 +128,9 @@ struct mf_process {
     double ch_s0 = 1.0, ch_t0 = 1.0;
     long long *d_ch_off = nullptr;      // [K+1] point offsets of a launch over every channel
     double **d_ch_grids = nullptr;      // [K] the channels' grids
+    long long *d_ch_chunk_off = nullptr;  // [K+1] chunk offsets of the channels' accumulation
+    double *d_ch_res = nullptr;         // [K][8] the channels' iteration results
+    void *d_ch_acc = nullptr;           // [K] per-channel bookkeeping records (mf_api.cu)
 };
 
 struct mf_vegas {
