@@ -1487,8 +1487,9 @@ void vegas_params(const mf_process *p, const mf_vegas *v, int64_t n, int64_t ev0
     kp.subprocess = (uint64_t)subprocess;
 }
 
-// Dynamic shared memory of vegas_accumulate_kernel (one chunk's w and w^2),
-// and its attribute, set once per device.
+// Dynamic shared memory of vegas_accumulate_kernel and
+// vegas_accumulate_channels_kernel (one chunk's w and w^2), and their
+// attribute, set once per device.
 constexpr size_t kAccSmem = sizeof(double) * 2 * kChunk;
 constexpr int kAccMaxDevices = 64;
 std::mutex g_acc_mutex;
@@ -1501,6 +1502,8 @@ mf_status accumulate_attribute() {
     std::lock_guard<std::mutex> lock(g_acc_mutex);
     if (!g_acc_attr[dev]) {
         MF_CUDA(cudaFuncSetAttribute(vegas_accumulate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kAccSmem));
+        MF_CUDA(cudaFuncSetAttribute(vegas_accumulate_channels_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)kAccSmem));
         g_acc_attr[dev] = true;
     }
