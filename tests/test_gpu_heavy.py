@@ -7,7 +7,8 @@ oracle's colour matrix is a sum over 294912 colour assignments of 1890
 terms, spread over spawned processes on the host cores.  The same
 tolerances as the other workloads: FP64 within 1e-12 plus 64 eps times the
 oracle's condition number of the point, mixed within 1e-5 (median) and 1e-3
-(max); identical zero patterns.
+(max); identical zero patterns.  Two of its 945 phase-space channels are
+checked the same way in FP64.
 """
 import os
 
@@ -56,6 +57,16 @@ def test_gg_ttxggg_matches_the_oracle(env, capsys):
               f"mixed median {np.median(rmx):.1e} max {rmx.max():.1e}")
     assert np.all(relerr(f64, ref) <= tol)
     assert np.median(rmx) <= 1e-5 and rmx.max() <= 1e-3
+    # two of the 945 phase-space channels, per point in FP64
+    r0 = max(wl.pt_min_gluon, 1.0) ** 2
+    I.use_channels(r0, r0)
+    assert proc.n_channels == len(I.channels) == 945
+    for ch in (0, 700):
+        xc = W.uniform_points(wl.ndim, 12, 4300 + ch)
+        fc = proc.channel_integrand(torch.from_numpy(xc).cuda(), ch, "fp64").cpu().numpy()
+        rc, tc = fp64_tolerance(lambda y, return_parts=False: I(y, return_parts=return_parts, channel=ch), xc)
+        assert np.array_equal(fc == 0, rc == 0), ch
+        assert np.all(relerr(fc, rc) <= tc), ch
     # a Vegas pass of the integrand kernel
     v = api.Vegas(wl.ndim)
     r = v.iterate(proc, 200_000, 3, "mixed")
