@@ -618,6 +618,15 @@ mf_status mf_vegas_observables(mf_vegas *v, mf_process *p, int64_t n_events, uin
                                mf_precision prec, int32_t n_obs, const mf_observable *obs, double *sigma,
                                double *error, int64_t *counts, void *stream);
 
+/* mf_vegas_observables_channel: mf_vegas_observables for phase-space
+ * channel `channel` (see mf_vegas_iterate_channels): its own points
+ * (subprocess index = channel) through its grid v, with the channel's
+ * momenta and weight a_i / g_i.  The histograms of the whole cross section
+ * are the sums over the channels (errors in quadrature). */
+mf_status mf_vegas_observables_channel(mf_vegas *v, mf_process *p, int32_t channel, int64_t n_events, uint64_t seed,
+                                       mf_precision prec, int32_t n_obs, const mf_observable *obs, double *sigma,
+                                       double *error, int64_t *counts, void *stream);
+
 /* mf_vegas_unweight: one pass of n_events Vegas points through the grid as it
  * stands (points of the grid's current iteration index, subprocess index
  * `subprocess`, Philox key seed; the grid is neither refined nor advanced),

@@ -148,6 +148,9 @@ SIGNATURES = {
     "mf_process_read_weights": (c_i32, [C.c_void_p, P(c_i64), c_i64, P(C.c_double)]),
     "mf_vegas_observables": (c_i32, [C.c_void_p, C.c_void_p, c_i64, C.c_uint64, c_i32, c_i32, c_i32,
                                      P(mf_observable), P(C.c_double), P(C.c_double), P(c_i64), C.c_void_p]),
+    "mf_vegas_observables_channel": (c_i32, [C.c_void_p, C.c_void_p, c_i32, c_i64, C.c_uint64, c_i32, c_i32,
+                                             P(mf_observable), P(C.c_double), P(C.c_double), P(c_i64),
+                                             C.c_void_p]),
     "mf_process_max_weight": (c_i32, [C.c_void_p, P(C.c_double), C.c_void_p]),
     "mf_vegas_save": (c_i32, [C.c_void_p, C.c_void_p, P(C.c_size_t)]),
     "mf_vegas_load": (c_i32, [C.c_void_p, C.c_void_p, C.c_size_t]),

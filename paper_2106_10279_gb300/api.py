@@ -673,6 +673,55 @@ class MultiChannel:
             recs.append(rec)
         return tot, np.concatenate(recs) if recs else np.zeros((0, 0))
 
+    def observables(self, n_total: int, seed: int, obs, precision="mixed", n_floor=None, stream=None):
+        """Weighted histograms of one pass of n_total points over the channels
+        (the current allocation): per observable (sigma, error, counts), the
+        sums over the channels (errors in quadrature)."""
+        n = self.allocation(n_total, n_floor)
+        tot = None
+        for k, nk in enumerate(n):
+            h = observables(self.grids[k], self.proc, nk, seed, obs, precision, stream=stream, channel=k)
+            if tot is None:
+                tot = [[s.copy(), e ** 2, c.copy()] for s, e, c in h]
+            else:
+                for t, (s_, e_, c_) in zip(tot, h):
+                    t[0] += s_
+                    t[1] += e_ ** 2
+                    t[2] += c_
+        return [(s_, np.sqrt(v_), c_) for s_, v_, c_ in tot]
+
+    def save(self) -> bytes:
+        """Checkpoint of every channel's grid and the allocation state."""
+        import struct
+        parts = [b"MFMC1", struct.pack("<ii", self.K, 0 if self.sigma is None else 1)]
+        if self.sigma is not None:
+            parts.append(struct.pack("<%dd" % self.K, *self.sigma))
+        for g in self.grids:
+            blob = g.save()
+            parts.append(struct.pack("<q", len(blob)))
+            parts.append(blob)
+        return b"".join(parts)
+
+    def load(self, data: bytes):
+        import struct
+        if data[:5] != b"MFMC1":
+            raise ValueError("not a multichannel checkpoint")
+        K, has = struct.unpack_from("<ii", data, 5)
+        if K != self.K:
+            raise ValueError(f"checkpoint of {K} channels, process has {self.K}")
+        o = 13
+        self.sigma = None
+        if has:
+            self.sigma = list(struct.unpack_from("<%dd" % K, data, o))
+            o += 8 * K
+        for g in self.grids:
+            (ln,) = struct.unpack_from("<q", data, o)
+            o += 8
+            g.load(data[o:o + ln])
+            o += ln
+        if o != len(data):
+            raise ValueError("trailing bytes in the checkpoint")
+
     def close(self):
         for g in self.grids:
             g.close()
@@ -772,21 +821,26 @@ OBSERVABLE_KINDS = {"pt": L.MF_OBS_PT, "y": L.MF_OBS_RAPIDITY, "eta": L.MF_OBS_P
 
 
 def observables(grid: "Vegas", proc: "Process", n_events: int, seed: int, obs, precision="mixed", subprocess=0,
-                stream=None):
-    """Weighted histograms of one pass (see mf_vegas_observables).  obs: list
-    of (kind, leg, nbins, lo, hi), kind "pt", "y" or "eta"; returns one
-    (sigma, error, counts) per observable, sigma and error in pb per bin."""
+                stream=None, channel=None):
+    """Weighted histograms of one pass (see mf_vegas_observables; with a
+    channel, mf_vegas_observables_channel).  obs: list of (kind, leg, nbins,
+    lo, hi), kind "pt", "y" or "eta"; returns one (sigma, error, counts) per
+    observable, sigma and error in pb per bin."""
     arr = (L.mf_observable * len(obs))()
     for a, (kind, leg, nbins, lo, hi) in zip(arr, obs):
         a.kind, a.leg, a.nbins, a.lo, a.hi = OBSERVABLE_KINDS[kind], leg, nbins, lo, hi
     nb = sum(o[2] for o in obs)
     sig, err = np.zeros(nb), np.zeros(nb)
     cnt = np.zeros(nb, dtype=np.int64)
-    L.check(L.lib().mf_vegas_observables(grid.handle, proc.handle, n_events, seed, subprocess, _PREC[precision],
-                                         len(obs), arr, sig.ctypes.data_as(C.POINTER(C.c_double)),
-                                         err.ctypes.data_as(C.POINTER(C.c_double)),
-                                         cnt.ctypes.data_as(C.POINTER(C.c_int64)), _stream_ptr(stream)),
-            "mf_vegas_observables")
+    bufs = (sig.ctypes.data_as(C.POINTER(C.c_double)), err.ctypes.data_as(C.POINTER(C.c_double)),
+            cnt.ctypes.data_as(C.POINTER(C.c_int64)), _stream_ptr(stream))
+    if channel is None:
+        L.check(L.lib().mf_vegas_observables(grid.handle, proc.handle, n_events, seed, subprocess, _PREC[precision],
+                                             len(obs), arr, *bufs), "mf_vegas_observables")
+    else:
+        L.check(L.lib().mf_vegas_observables_channel(grid.handle, proc.handle, channel, n_events, seed,
+                                                     _PREC[precision], len(obs), arr, *bufs),
+                "mf_vegas_observables_channel")
     out, o = [], 0
     for kind, leg, nbins, lo, hi in obs:
         out.append((sig[o:o + nbins], err[o:o + nbins], cnt[o:o + nbins]))

@@ -2493,10 +2493,33 @@ double pairwise_sum(const std::vector<double> &v, size_t lo, size_t hi) {
 }
 }  // namespace
 
+namespace {
+mf_status observables_impl(mf_vegas *v, mf_process *p, int64_t n_events, uint64_t seed, int32_t subprocess,
+                           int32_t channel, mf_precision prec, int32_t n_obs, const mf_observable *obs, double *sigma,
+                           double *error, int64_t *counts, void *stream);
+}  // namespace
+
 extern "C" mf_status mf_vegas_observables(mf_vegas *v, mf_process *p, int64_t n_events, uint64_t seed,
                                           int32_t subprocess, mf_precision prec, int32_t n_obs,
                                           const mf_observable *obs, double *sigma, double *error, int64_t *counts,
                                           void *stream) {
+    return observables_impl(v, p, n_events, seed, subprocess, -1, prec, n_obs, obs, sigma, error, counts, stream);
+}
+
+extern "C" mf_status mf_vegas_observables_channel(mf_vegas *v, mf_process *p, int32_t channel, int64_t n_events,
+                                                  uint64_t seed, mf_precision prec, int32_t n_obs,
+                                                  const mf_observable *obs, double *sigma, double *error,
+                                                  int64_t *counts, void *stream) {
+    if (!p) return fail(MF_EINVAL, "NULL process");
+    if (p->channels.K == 0) return fail(MF_EUNSUPPORTED, "the process has no phase-space channels");
+    if (channel < 0 || channel >= p->channels.K) return fail(MF_EINVAL, "channel out of range");
+    return observables_impl(v, p, n_events, seed, channel, channel, prec, n_obs, obs, sigma, error, counts, stream);
+}
+
+namespace {
+mf_status observables_impl(mf_vegas *v, mf_process *p, int64_t n_events, uint64_t seed, int32_t subprocess,
+                           int32_t channel, mf_precision prec, int32_t n_obs, const mf_observable *obs, double *sigma,
+                           double *error, int64_t *counts, void *stream) {
     if (!v || !p || !obs || !sigma || !error) return fail(MF_EINVAL, "NULL argument");
     if (!valid_prec(prec)) return fail(MF_EINVAL, "bad precision");
     if (v->ndim != p->ndim) return fail(MF_EINVAL, "grid and process dimensions differ");
@@ -2519,6 +2542,7 @@ extern "C" mf_status mf_vegas_observables(mf_vegas *v, mf_process *p, int64_t n_
     // the weights of the pass
     mf_kparams kp;
     vegas_params(p, v, n, 0, subprocess, seed, kp);
+    kp.channel = channel;
     st = launch(p, prec, kp, s);
     if (st != MF_OK) return st;
     p->last_n = n;
@@ -2548,6 +2572,7 @@ extern "C" mf_status mf_vegas_observables(mf_vegas *v, mf_process *p, int64_t n_
     mf_kparams ko;
     vegas_params(p, v, n, 0, subprocess, seed, ko);
     ko.mode = 4;
+    ko.channel = channel;
     ko.obs_out = d_obs;
     ko.n_obs = n_obs;
     for (int k = 0; k < n_obs; ++k) {
@@ -2595,6 +2620,7 @@ extern "C" mf_status mf_vegas_observables(mf_vegas *v, mf_process *p, int64_t n_
     if (any_nan) return fail(MF_ENAN, "some points had non-finite weights (not binned)");
     return MF_OK;
 }
+}  // namespace
 
 // ----------------------------------------------------------------------------
 // Unweighting (hit or miss against w_max) and event records.

@@ -220,3 +220,52 @@ def test_channel_unweighting_matches_the_oracle(env):
     clear = gap > 1e-9
     assert clear.mean() > 0.99
     assert np.array_equal(rec[clear, 3].astype(int), pick[clear])
+
+
+def test_channel_histograms_match_the_oracle(env):
+    # observables of one channel's pass: the points of its own stream, its
+    # momenta and weights (gg -> tt~, the t-channel map)
+    torch, api = env
+    from oracle import observables as ob
+    from oracle import unweight as uw
+    from oracle import vegas as ov
+    from oracle.philox import vegas_uniforms
+    name, k, n, seed = "gg_ttx", 1, 30000, 5
+    obs = [("pt", 2, 20, 0.0, 500.0), ("y", 2, 16, -4.0, 4.0)]
+    wl = W.WORKLOADS[name]
+    I = _oracle(name)
+    y = vegas_uniforms(seed, 0, k, 0, n, wl.ndim)
+    x, jac, _ = ov.vegas_map(ov.uniform_grid(wl.ndim, wl.n_bins), y)
+    w = I(x, channel=k) * jac
+    p, s_hat, x1, x2, jx, wps, ok = I.kinematics(x, channel=k)
+    passing = ok & I.cuts(p)
+    kinds = {"pt": ob.PT, "y": ob.RAPIDITY}
+    ref = ob.histograms(uw.lab_frame(p, x1, x2), passing, w, [(kinds[a], l, nb, lo, hi) for a, l, nb, lo, hi in obs])
+    proc = api.Process.from_workload(wl)
+    got = api.observables(api.Vegas(wl.ndim), proc, n, seed, obs, precision="fp64", channel=k)
+    for (s, e, c), (rs, re, rc), o in zip(got, ref, obs):
+        assert np.array_equal(c, rc), o
+        nz = rs != 0
+        assert np.all(s[~nz] == 0)
+        assert np.max(np.abs(s[nz] / rs[nz] - 1)) <= 1e-10, o
+        assert np.max(np.abs(e[nz] / re[nz] - 1)) <= 1e-8, o
+
+
+def test_multichannel_checkpoint_resumes_bit_for_bit(env):
+    torch, api = env
+    wl = W.WORKLOADS["gg_ttxg"]
+    proc = api.Process.from_workload(wl)
+    a = api.MultiChannel(proc)
+    for it in range(2):
+        a.iterate(100_000, seed=3, precision="fp64")
+    blob = a.save()
+    b = api.MultiChannel(proc)
+    b.load(blob)
+    assert b.sigma == a.sigma
+    ra = a.iterate(100_000, seed=3, precision="fp64")
+    rb = b.iterate(100_000, seed=3, precision="fp64")
+    assert ra["allocation"] == rb["allocation"]
+    assert (ra["integral"], ra["error"], ra["sigma"], ra["sigma_error"]) == \
+        (rb["integral"], rb["error"], rb["sigma"], rb["sigma_error"])
+    with pytest.raises(ValueError):
+        api.MultiChannel(api.Process.from_workload(W.WORKLOADS["gg_ttx"])).load(blob)
