@@ -48,7 +48,10 @@ typedef enum {
  * single precision; phase space, invariants and propagator denominators, PDFs,
  * weights and all accumulators in double precision.  MF_MIXED_TC: MF_MIXED
  * with the colour sum on the tensor cores (tcgen05, split TF32; see
- * mf_colour_sum), 128 threads per block.  (Value 2 is the gradient kernel in
+ * mf_colour_sum), 128 threads per block; up to 64 colour flows the operand
+ * rows are [Re J | Im J] against diag(C, C), above 64 the real and imaginary
+ * parts are stacked as separate rows against C (two MMA rounds per call, the
+ * Vegas grid read from global memory).  (Value 2 is the gradient kernel in
  * mf_generate_kernel_source.) */
 typedef enum { MF_FP64 = 0, MF_MIXED = 1, MF_MIXED_TC = 3 } mf_precision;
 

@@ -174,10 +174,10 @@ constexpr size_t tile_smem_bytes() {
 // Philox points through it: 1, 3, 4 and 5) and the couplings and masses in
 // the matrix-element precision.
 template <typename R, int BLOCK>
-MF_DEV void load_block_constants(const KParams &kp, double *s_grid, cx<R> *cpl, R *mass_r) {
+MF_DEV void load_block_constants(const KParams &kp, double *s_grid, cx<R> *cpl, R *mass_r, bool copy_grid = true) {
     using namespace MF_PROC;
     const int tid = threadIdx.x;
-    if ((kp.mode == 1 && !kp.ch_off) || kp.mode == 3 || kp.mode == 4 || kp.mode == 5) {
+    if (copy_grid && ((kp.mode == 1 && !kp.ch_off) || kp.mode == 3 || kp.mode == 4 || kp.mode == 5)) {
         for (int i = tid; i < NDIM * (kp.nb + 1); i += BLOCK) s_grid[i] = kp.grid[i];
     }
     if (tid < 8) {
@@ -623,8 +623,11 @@ template <int HT>
 MF_DEV void kernel_body_tc(const KParams &kp) {
     using namespace MF_PROC;
     constexpr int BLOCK = 128;
+    // with the stacked operands (many colour flows) the shared memory goes to
+    // the tensor-core operands and the grid is read from global memory
+    constexpr bool GRID_GLOBAL = tc::Plan<NJAMP>::STACKED;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ double s_grid[NDIM * 65];
+    __shared__ double s_grid[GRID_GLOBAL ? 1 : NDIM * 65];
     __shared__ cx<float> cpl[8];
     __shared__ float mass_r[8];
     constexpr size_t tile_bytes = (tile_smem_bytes<float, BLOCK>() + 1023) / 1024 * 1024;
@@ -632,11 +635,12 @@ MF_DEV void kernel_body_tc(const KParams &kp) {
     tc::State tcs;
     tc::setup<NJAMP>(tcs, smem_raw + tile_bytes, kp.err, kp.wait_polls);
     tc::load_colour<NJAMP>(tcs, COLOUR_NUM);
-    load_block_constants<float, BLOCK>(kp, s_grid, cpl, mass_r);
+    load_block_constants<float, BLOCK>(kp, s_grid, cpl, mass_r, !GRID_GLOBAL);
     __syncthreads();
+    const double *grid = GRID_GLOBAL ? kp.grid : s_grid;
     const int64_t ntiles = (kp.n + BLOCK - 1) / BLOCK;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
-        tile_body<float, BLOCK, HT, true>(kp, tile, smem_raw, s_grid, cpl, mass_r, &tcs);
+        tile_body<float, BLOCK, HT, true>(kp, tile, smem_raw, grid, cpl, mass_r, &tcs);
     tc::teardown<NJAMP>(tcs);
 }
 

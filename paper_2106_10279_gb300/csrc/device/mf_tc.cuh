@@ -36,17 +36,27 @@ namespace tc {
 constexpr int ROWS = 128;                    // rows per MMA (one per thread of a 128-thread block)
 constexpr long long WAIT_LIMIT = 1ll << 24;  // polls of a completion barrier before giving up (default)
 
+// Two operand layouts.  Side by side (2 NJ <= 128): row r of A is
+// [Re J_r | Im J_r] and B = diag(C, C), one round of 128 rows per call.
+// Stacked (2 NJ > 128, where diag(C, C) would not fit in shared memory):
+// rows 2i and 2i+1 of A are Re J_i and Im J_i of item i and B = C; a round
+// holds 64 items and a call takes two rounds (threads 0-63, then 64-127).
+// Each row r then gives sum_c A_rc Z_rc, and an item's value is the sum of
+// its two rows (Re(J^dagger C J) = Re J . C Re J + Im J . C Im J, C real
+// symmetric).
 template <int NJ>
 struct Plan {
-    static constexpr int K2 = 2 * NJ;
+    static constexpr bool STACKED = 2 * NJ > 128;
+    static constexpr int K2 = STACKED ? NJ : 2 * NJ;
     static constexpr int KP = (K2 + 7) / 8 * 8;        // K: multiple of the tf32 MMA step (8)
     static constexpr int NP = (K2 + 15) / 16 * 16;     // N: multiple of 16 for M = 128
     static constexpr int COLS = NP <= 32 ? 32 : NP <= 64 ? 64 : NP <= 128 ? 128 : 256;   // tensor-memory columns
     static constexpr int A_BYTES = ROWS * KP * 4;
     static constexpr int B_BYTES = NP * KP * 4;
     // shared-memory bytes: A_hi, A_lo, B (1 KB aligned), then the round and
-    // drain barriers and the tensor-memory address
-    static constexpr int SMEM = 2 * A_BYTES + B_BYTES + 24;
+    // drain barriers and the tensor-memory address; stacked: then the
+    // per-thread results of a call (16-byte aligned)
+    static constexpr int SMEM = STACKED ? 2 * A_BYTES + B_BYTES + 32 + ROWS * 4 : 2 * A_BYTES + B_BYTES + 24;
 };
 
 MF_DEV uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -79,6 +89,7 @@ struct State {
     uint64_t *mbar;           // completion of each round's MMAs
     uint64_t *drain;          // completion of every MMA issued (teardown)
     uint32_t *tmem_slot;
+    float *out;               // stacked layout: [ROWS] results of a call
     uint32_t phase;
     long long wait_limit;     // polls per round
     int *err;                 // global error flag (may be NULL)
@@ -96,6 +107,7 @@ MF_DEV void setup(State &s, unsigned char *smem, int *err, long long wait_limit 
     s.mbar = reinterpret_cast<uint64_t *>(smem + 2 * P::A_BYTES + P::B_BYTES);
     s.drain = reinterpret_cast<uint64_t *>(smem + 2 * P::A_BYTES + P::B_BYTES + 8);
     s.tmem_slot = reinterpret_cast<uint32_t *>(smem + 2 * P::A_BYTES + P::B_BYTES + 16);
+    s.out = reinterpret_cast<float *>(smem + 2 * P::A_BYTES + P::B_BYTES + 32);
     s.phase = 0;
     s.wait_limit = wait_limit < 0 ? WAIT_LIMIT : wait_limit;
     s.err = err;
@@ -124,7 +136,8 @@ MF_DEV void load_colour(State &s, const int *cnum) {
         const int n = i / P::KP, k = i % P::KP;
         float v = 0.f;
         if (n < NJ && k < NJ) v = (float)cnum[n * NJ + k];
-        else if (n >= NJ && n < 2 * NJ && k >= NJ && k < 2 * NJ) v = (float)cnum[(n - NJ) * NJ + (k - NJ)];
+        else if (!P::STACKED && n >= NJ && n < 2 * NJ && k >= NJ && k < 2 * NJ)
+            v = (float)cnum[(n - NJ) * NJ + (k - NJ)];
         *reinterpret_cast<float *>(s.b + core_offset(n, k, P::KP)) = v;
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -161,27 +174,17 @@ MF_DEV void ld_cols<16>(uint32_t taddr, float *out) {
     for (int i = 0; i < 16; ++i) out[i] = __uint_as_float(r[i]);
 }
 
-// One round: every thread of the block passes its row's amplitudes J
-// (NJ complex) and receives sum_kl Re(conj(J_k) C_kl J_l) (numerators only:
-// divide by the colour denominator).  Must be called by all 128 threads.
-// If a round's wait expires in any thread, the whole block (one decision,
-// taken at a barrier) records the error and from then on neither writes
-// the operands, nor issues MMAs, nor reads tensor memory: its results are 0
-// and unspecified, and no access races an MMA still in flight.
+// The MMAs of one round over the operands now in A (issued by thread 0:
+// Z = A_hi B + A_lo B into tensor memory), the bounded wait for them and one
+// block-wide decision on its outcome.  Must be called by all 128 threads
+// after they have written their rows of A.  If a round's wait expires in any
+// thread, the whole block (one decision, taken at a barrier) records the
+// error and from then on neither writes the operands, nor issues MMAs, nor
+// reads tensor memory: its results are 0 and unspecified, and no access
+// races an MMA still in flight.
 template <int NJ>
-MF_DEV float colour_sum(State &s, const cx<float> *J) {
+MF_DEV void mma_round(State &s) {
     using P = Plan<NJ>;
-    const int r = threadIdx.x;
-    if (!s.failed) {
-        // this row of A_hi and A_lo: [Re J | Im J], zero padded to KP
-#pragma unroll
-        for (int k = 0; k < P::KP; ++k) {
-            const float a = k < NJ ? J[k].re : (k < 2 * NJ ? J[k - NJ].im : 0.f);
-            const float hi = tf32_hi(a);
-            *reinterpret_cast<float *>(s.a_hi + core_offset(r, k, P::KP)) = hi;
-            *reinterpret_cast<float *>(s.a_lo + core_offset(r, k, P::KP)) = a - hi;
-        }
-    }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -218,29 +221,108 @@ MF_DEV float colour_sum(State &s, const cx<float> *J) {
         s.failed = true;
         if (s.err && threadIdx.x == 0) atomicExch(s.err, 1);
     }
-    float m = 0.f;
-    if (!s.failed) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // this row of Z, 16 columns at a time (warp w reads lanes 32w .. 32w+31)
-        const uint32_t trow = tmem + ((uint32_t)((threadIdx.x >> 5) * 32) << 16);
-#pragma unroll
-        for (int c0 = 0; c0 < P::NP; c0 += 16) {
-            float z[16];
-            ld_cols<16>(trow + c0, z);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int c = c0 + i;
-                if (c < NJ) m += J[c].re * z[i];
-                else if (c < 2 * NJ) m += J[c - NJ].im * z[i];
-            }
-        }
-    }
-    // the next round rewrites A and the accumulator only after every thread
-    // has read its row
+}
+
+// The next round rewrites A and the accumulator only after every thread has
+// read its row.
+MF_DEV void round_done() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    return m;
+}
+
+// Stacked layout (2 NJ > 128): two rounds of 64 items; the thread reading
+// row r of Z (warp r/32 reads lanes 32 (r/32) ..) takes row r of A back from
+// shared memory (A_hi + A_lo is exactly the FP32 amplitude), and the two rows
+// of an item, adjacent lanes of one warp, are added by a shuffle.
+template <int NJ>
+MF_DEV float colour_sum_stacked(State &s, const cx<float> *J) {
+    using P = Plan<NJ>;
+    const int t = threadIdx.x;
+#pragma unroll 1
+    for (int round = 0; round < 2; ++round) {
+        if (!s.failed && (t >> 6) == round) {
+            const int r0 = 2 * (t & 63);      // this thread's item: rows r0 (Re J) and r0 + 1 (Im J)
+#pragma unroll 4
+            for (int k = 0; k < P::KP; ++k) {
+                const float re = k < NJ ? J[k].re : 0.f, im = k < NJ ? J[k].im : 0.f;
+                const float rh = tf32_hi(re), ih = tf32_hi(im);
+                *reinterpret_cast<float *>(s.a_hi + core_offset(r0, k, P::KP)) = rh;
+                *reinterpret_cast<float *>(s.a_lo + core_offset(r0, k, P::KP)) = re - rh;
+                *reinterpret_cast<float *>(s.a_hi + core_offset(r0 + 1, k, P::KP)) = ih;
+                *reinterpret_cast<float *>(s.a_lo + core_offset(r0 + 1, k, P::KP)) = im - ih;
+            }
+        }
+        mma_round<NJ>(s);
+        float m = 0.f;
+        if (!s.failed) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t trow = *s.tmem_slot + ((uint32_t)((t >> 5) * 32) << 16);
+#pragma unroll 1
+            for (int c0 = 0; c0 < P::NP; c0 += 16) {
+                float z[16];
+                ld_cols<16>(trow + c0, z);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int c = c0 + i;
+                    if (c < NJ) {
+                        const uint32_t o = core_offset(t, c, P::KP);
+                        const float a = *reinterpret_cast<const float *>(s.a_hi + o) +
+                                        *reinterpret_cast<const float *>(s.a_lo + o);
+                        m += a * z[i];
+                    }
+                }
+            }
+        }
+        const float pair = m + __shfl_xor_sync(0xffffffffu, m, 1);
+        if (!(t & 1)) s.out[64 * round + (t >> 1)] = pair;
+        round_done();
+    }
+    return s.failed ? 0.f : s.out[t];
+}
+
+// One call: every thread of the block passes its (point, helicity) row's
+// amplitudes J (NJ complex) and receives sum_kl Re(conj(J_k) C_kl J_l)
+// (numerators only: divide by the colour denominator).  Must be called by
+// all 128 threads.
+template <int NJ>
+MF_DEV float colour_sum(State &s, const cx<float> *J) {
+    using P = Plan<NJ>;
+    if constexpr (P::STACKED) {
+        return colour_sum_stacked<NJ>(s, J);
+    } else {
+        const int r = threadIdx.x;
+        if (!s.failed) {
+            // this row of A_hi and A_lo: [Re J | Im J], zero padded to KP
+#pragma unroll
+            for (int k = 0; k < P::KP; ++k) {
+                const float a = k < NJ ? J[k].re : (k < 2 * NJ ? J[k - NJ].im : 0.f);
+                const float hi = tf32_hi(a);
+                *reinterpret_cast<float *>(s.a_hi + core_offset(r, k, P::KP)) = hi;
+                *reinterpret_cast<float *>(s.a_lo + core_offset(r, k, P::KP)) = a - hi;
+            }
+        }
+        mma_round<NJ>(s);
+        float m = 0.f;
+        if (!s.failed) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // this row of Z, 16 columns at a time (warp w reads lanes 32w .. 32w+31)
+            const uint32_t trow = *s.tmem_slot + ((uint32_t)((threadIdx.x >> 5) * 32) << 16);
+#pragma unroll
+            for (int c0 = 0; c0 < P::NP; c0 += 16) {
+                float z[16];
+                ld_cols<16>(trow + c0, z);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int c = c0 + i;
+                    if (c < NJ) m += J[c].re * z[i];
+                    else if (c < 2 * NJ) m += J[c - NJ].im * z[i];
+                }
+            }
+        }
+        round_done();
+        return m;
+    }
 }
 
 // Release the tensor memory (warp 0) once every MMA the block issued has

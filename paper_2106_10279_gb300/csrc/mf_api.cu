@@ -555,13 +555,16 @@ mf_status compile_shape(mf_process *p, int prec, int block, int ht, mfi::Compile
 // operands: A_hi and A_lo (128 x KP), B (NP x KP), the round and drain
 // barriers and the tensor-memory address (mf::tc::Plan<NJ>::SMEM).
 size_t smem_bytes_tc(const mf_process &p) {
-    const int K2 = 2 * p.n_jamp, KP = (K2 + 7) / 8 * 8, NP = (K2 + 15) / 16 * 16;
+    // the operand plan of device/mf_tc.cuh (Plan<NJ>): side by side, or
+    // stacked when 2 NJ > 128
+    const bool stacked = 2 * p.n_jamp > 128;
+    const int K2 = stacked ? p.n_jamp : 2 * p.n_jamp, KP = (K2 + 7) / 8 * 8, NP = (K2 + 15) / 16 * 16;
     const int nden1 = p.gen.n_den > 0 ? p.gen.n_den : 1, block = 128;
     size_t tile = (size_t)block * p.n_legs * 4 * 4 + (size_t)block * nden1 * 4;
     tile += (16 - (((size_t)block * nden1 * 4) % 16)) % 16;
     tile += (size_t)block * 8 * 2 + (size_t)block * 4 + (block / 32 + 1) * 4;
     tile = (tile + 1023) / 1024 * 1024;
-    return tile + 2 * (size_t)128 * KP * 4 + (size_t)NP * KP * 4 + 24;
+    return tile + 2 * (size_t)128 * KP * 4 + (size_t)NP * KP * 4 + (stacked ? 32 + 128 * 4 : 24);
 }
 
 int pow2_at_least(int n) {

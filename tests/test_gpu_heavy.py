@@ -7,8 +7,9 @@ oracle's colour matrix is a sum over 294912 colour assignments of 1890
 terms, spread over spawned processes on the host cores.  The same
 tolerances as the other workloads: FP64 within 1e-12 plus 64 eps times the
 oracle's condition number of the point, mixed within 1e-5 (median) and 1e-3
-(max); identical zero patterns.  Two of its 945 phase-space channels are
-checked the same way in FP64.
+(max); identical zero patterns.  The colour sum on the tensor cores
+(MF_MIXED_TC, stacked operands: 120 flows) within the mixed bounds.  Two of
+its 945 phase-space channels are checked the same way in FP64.
 """
 import os
 
@@ -45,6 +46,7 @@ def test_gg_ttxggg_matches_the_oracle(env, capsys):
     xd = torch.from_numpy(x).cuda()
     f64 = proc.integrand(xd, "fp64").cpu().numpy()
     fmx = proc.integrand(xd, "mixed").cpu().numpy()
+    ftc = proc.integrand(xd, "mixed_tc").cpu().numpy()
     I = Integrand(wl, process=oracle_process(wl))
     ref, tol = fp64_tolerance(I, x)
     assert np.array_equal(f64 == 0, ref == 0)
@@ -52,11 +54,15 @@ def test_gg_ttxggg_matches_the_oracle(env, capsys):
     assert nz.sum() >= 16
     r64 = relerr(f64, ref)[nz]
     rmx = relerr(fmx, ref)[nz]
+    rtc = relerr(ftc, ref)[nz]
     with capsys.disabled():
         print(f"gg->tt~ggg: {nz.sum()} points, FP64 max {r64.max():.2e} median {np.median(r64):.1e}; "
-              f"mixed median {np.median(rmx):.1e} max {rmx.max():.1e}")
+              f"mixed median {np.median(rmx):.1e} max {rmx.max():.1e}; "
+              f"tensor-core colour sum median {np.median(rtc):.1e} max {rtc.max():.1e}")
     assert np.all(relerr(f64, ref) <= tol)
     assert np.median(rmx) <= 1e-5 and rmx.max() <= 1e-3
+    assert np.array_equal(ftc == 0, ref == 0)
+    assert np.median(rtc) <= 1e-5 and rtc.max() <= 1e-3
     # two of the 945 phase-space channels, per point in FP64
     r0 = max(wl.pt_min_gluon, 1.0) ** 2
     I.use_channels(r0, r0)
