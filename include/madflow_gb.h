@@ -434,12 +434,17 @@ mf_status mf_vegas_iterate_channels(mf_vegas *const *grids, mf_process *p, const
 
 /* mf_channels_allocate (host only): Neyman's allocation of n_total points
  * over n_channels channels whose weights have per-point standard deviations
- * sigma[k] (host): n_out[k] = n_floor + floor(F * (sigma[k] / S)), F =
- * n_total - n_channels n_floor, S = sigma[0] + .. (summed in order); equal
- * shares n_floor + F / n_channels when S = 0.  MF_EINVAL if F < 0 or a sigma
- * is negative or not finite. */
-mf_status mf_channels_allocate(int32_t n_channels, const double *sigma, int64_t n_total, int64_t n_floor,
-                               int64_t *n_out);
+ * sigma[k] (host): n_out[k] = n_floor + floor(F * (s[k] / S)), F =
+ * n_total - n_channels n_floor, S = s[0] + .. (summed in order); equal
+ * shares n_floor + F / n_channels when S = 0.  s = sigma if n_prev is NULL;
+ * otherwise each deviation, estimated from n_prev[k] points, is shrunk
+ * towards the pooled one as if m0 more points had shown the pooled variance:
+ * s[k] = sqrt((n_k sigma_k^2 + m0 P) / (n_k + m0)), P = sum n_k sigma_k^2 /
+ * sum n_k (a channel whose few points missed its peak is not starved).
+ * MF_EINVAL if F < 0, m0 < 0, or a sigma or count is negative or not
+ * finite. */
+mf_status mf_channels_allocate(int32_t n_channels, const double *sigma, const int64_t *n_prev, double m0,
+                               int64_t n_total, int64_t n_floor, int64_t *n_out);
 
 /* mf_channels_describe (host only): the channels a descriptor's program
  * gives, without creating a process.  *n_channels is set; if keys is not

@@ -63,7 +63,10 @@ the channel integrals and its variance the sum of theirs.
 Allocation.  The points of an iteration are shared out by Neyman's rule for
 a sum of independent estimates: n_i = n_floor + floor(F sigma_i / sum_j
 sigma_j), F = N - K n_floor, sigma_i the per-point standard deviation of
-channel i's weights (equal shares when every sigma_i is zero).
+channel i's weights (equal shares when every sigma_i is zero).  A deviation
+estimated from few points is unreliable (a channel whose few points missed
+its peak would be starved), so it is first shrunk towards the pooled one as
+if m0 more points had shown the pooled variance.
 """
 from __future__ import annotations
 
@@ -468,10 +471,27 @@ def partition(channels, pa, p, s0, t0, masses):
 # ----------------------------------------------------------------------------
 # allocation
 # ----------------------------------------------------------------------------
-def allocate(sigma, n_total: int, n_floor: int):
+def shrink(sigma, n_prev, m0: float):
+    """Per-point standard deviations estimated from n_prev[k] points each,
+    shrunk towards the pooled one as if m0 more points had shown the pooled
+    variance: sqrt((n_k s_k^2 + m0 s^2) / (n_k + m0)), s^2 = sum_k n_k s_k^2 /
+    sum_k n_k (sums in channel order)."""
+    num, den = 0.0, 0.0
+    for s_, n_ in zip(sigma, n_prev):
+        num += float(n_) * float(s_) * float(s_)
+        den += float(n_)
+    pooled = num / den if den > 0.0 else 0.0
+    return [math.sqrt((float(n_) * float(s_) * float(s_) + m0 * pooled) / (float(n_) + m0)) if float(n_) + m0 > 0.0
+            else 0.0 for s_, n_ in zip(sigma, n_prev)]
+
+
+def allocate(sigma, n_total: int, n_floor: int, n_prev=None, m0: float = 0.0):
     """Neyman allocation of n_total points over channels with per-point
-    standard deviations sigma (every channel keeps n_floor)."""
+    standard deviations sigma (every channel keeps n_floor); with n_prev, the
+    deviations are first shrunk (shrink) with m0 pseudo-points."""
     sigma = [float(s) for s in sigma]
+    if n_prev is not None:
+        sigma = shrink(sigma, n_prev, float(m0))
     K = len(sigma)
     free = n_total - K * n_floor
     if free < 0:

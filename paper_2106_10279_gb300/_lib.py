@@ -105,7 +105,7 @@ SIGNATURES = {
     "mf_channel_integrand": (c_i32, [C.c_void_p, c_i32, C.c_void_p, c_i64, C.c_void_p, c_i32, C.c_void_p]),
     "mf_vegas_iterate_channels": (c_i32, [P(C.c_void_p), C.c_void_p, P(c_i64), c_i32, C.c_uint64, c_i32, c_i32,
                                           P(mf_iter_result), C.c_void_p]),
-    "mf_channels_allocate": (c_i32, [c_i32, P(C.c_double), c_i64, c_i64, P(c_i64)]),
+    "mf_channels_allocate": (c_i32, [c_i32, P(C.c_double), P(c_i64), C.c_double, c_i64, c_i64, P(c_i64)]),
     "mf_vegas_unweight_channel": (c_i32, [C.c_void_p, C.c_void_p, c_i32, c_i64, C.c_uint64, c_i32, C.c_double,
                                           C.c_void_p, P(C.c_double), c_i64, P(c_i64), C.c_void_p]),
     "mf_process_channel_max_weights": (c_i32, [C.c_void_p, P(c_i64), c_i32, P(C.c_double), C.c_void_p]),

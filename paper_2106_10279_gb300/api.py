@@ -253,11 +253,13 @@ def mf_vegas_iterate_channels(grids, h, n_events, seed: int, precision="fp64", r
     return [_result(r) for r in out]
 
 
-def mf_channels_allocate(sigma, n_total: int, n_floor: int):
+def mf_channels_allocate(sigma, n_total: int, n_floor: int, n_prev=None, m0: float = 0.0):
     k = len(sigma)
     S = (C.c_double * k)(*[float(v) for v in sigma])
+    Np = None if n_prev is None else (C.c_int64 * k)(*[int(v) for v in n_prev])
     out = (C.c_int64 * k)()
-    L.check(L.lib().mf_channels_allocate(k, S, int(n_total), int(n_floor), out), "mf_channels_allocate")
+    L.check(L.lib().mf_channels_allocate(k, S, Np, float(m0), int(n_total), int(n_floor), out),
+            "mf_channels_allocate")
     return [int(v) for v in out]
 
 
@@ -620,21 +622,25 @@ class MultiChannel:
     """Vegas over the multichannel phase space of a process: one grid per
     channel, the cross section the sum of the channels' integrals, and the
     points of each iteration shared out by Neyman's rule from the previous
-    iteration's per-point standard deviations (equal shares first)."""
+    iteration's per-point standard deviations, shrunk towards the pooled one
+    with m0 pseudo-points (equal shares first)."""
 
-    def __init__(self, proc: "Process", nbins: int = 50, alpha: float = 1.5):
+    def __init__(self, proc: "Process", nbins: int = 50, alpha: float = 1.5, m0: float = 1000.0):
         self.proc = proc
         self.K = proc.n_channels
         if self.K == 0:
             raise ValueError("the process has no phase-space channels")
         self.grids = [Vegas(proc.ndim, nbins, alpha) for _ in range(self.K)]
         self.sigma = None
+        self.n_prev = None
+        self.m0 = m0
 
     def allocation(self, n_total: int, n_floor=None):
         if n_floor is None:
             n_floor = max(2, n_total // (10 * self.K))
-        sig = self.sigma if self.sigma is not None else [0.0] * self.K
-        return mf_channels_allocate(sig, n_total, n_floor)
+        if self.sigma is None:
+            return mf_channels_allocate([0.0] * self.K, n_total, n_floor)
+        return mf_channels_allocate(self.sigma, n_total, n_floor, self.n_prev, self.m0)
 
     def iterate(self, n_total: int, seed: int, precision="fp64", refine=True, adapt=True, n_floor=None,
                 stream=None):
@@ -644,6 +650,7 @@ class MultiChannel:
                                         refine, stream)
         if adapt:
             self.sigma = [r["error"] * math.sqrt(k) for r, k in zip(res, n)]
+            self.n_prev = list(n)
         tot = {
             "n_events": sum(n),
             "integral": sum(r["integral"] for r in res),
@@ -696,6 +703,7 @@ class MultiChannel:
         parts = [b"MFMC1", struct.pack("<ii", self.K, 0 if self.sigma is None else 1)]
         if self.sigma is not None:
             parts.append(struct.pack("<%dd" % self.K, *self.sigma))
+            parts.append(struct.pack("<%dq" % self.K, *self.n_prev))
         for g in self.grids:
             blob = g.save()
             parts.append(struct.pack("<q", len(blob)))
@@ -711,8 +719,11 @@ class MultiChannel:
             raise ValueError(f"checkpoint of {K} channels, process has {self.K}")
         o = 13
         self.sigma = None
+        self.n_prev = None
         if has:
             self.sigma = list(struct.unpack_from("<%dd" % K, data, o))
+            o += 8 * K
+            self.n_prev = list(struct.unpack_from("<%dq" % K, data, o))
             o += 8 * K
         for g in self.grids:
             (ln,) = struct.unpack_from("<q", data, o)

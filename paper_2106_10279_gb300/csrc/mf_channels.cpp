@@ -277,18 +277,35 @@ extern "C" mf_status mf_channels_table(const mf_process_desc *d, int32_t *table,
     return MF_OK;
 }
 
-extern "C" mf_status mf_channels_allocate(int32_t n_channels, const double *sigma, int64_t n_total, int64_t n_floor,
-                                          int64_t *n_out) {
+extern "C" mf_status mf_channels_allocate(int32_t n_channels, const double *sigma, const int64_t *n_prev, double m0,
+                                          int64_t n_total, int64_t n_floor, int64_t *n_out) {
     if (n_channels < 1 || !sigma || !n_out || n_floor < 0) return mfi::fail(MF_EINVAL, "bad arguments");
+    if (!(m0 >= 0.0) || !std::isfinite(m0)) return mfi::fail(MF_EINVAL, "bad m0");
     const int64_t free_pts = n_total - (int64_t)n_channels * n_floor;
     if (free_pts < 0) return mfi::fail(MF_EINVAL, "fewer points than the floors need");
-    double S = 0.0;
+    std::vector<double> sg(n_channels);
     for (int i = 0; i < n_channels; ++i) {
         if (!(sigma[i] >= 0.0) || !std::isfinite(sigma[i])) return mfi::fail(MF_EINVAL, "bad sigma");
-        S += sigma[i];
+        if (n_prev && n_prev[i] < 0) return mfi::fail(MF_EINVAL, "bad n_prev");
+        sg[i] = sigma[i];
     }
+    if (n_prev) {
+        // shrink every deviation towards the pooled one (m0 pseudo-points)
+        double num = 0.0, den = 0.0;
+        for (int i = 0; i < n_channels; ++i) {
+            num += (double)n_prev[i] * sigma[i] * sigma[i];
+            den += (double)n_prev[i];
+        }
+        const double pooled = den > 0.0 ? num / den : 0.0;
+        for (int i = 0; i < n_channels; ++i) {
+            const double n = (double)n_prev[i];
+            sg[i] = n + m0 > 0.0 ? std::sqrt((n * sigma[i] * sigma[i] + m0 * pooled) / (n + m0)) : 0.0;
+        }
+    }
+    double S = 0.0;
+    for (int i = 0; i < n_channels; ++i) S += sg[i];
     for (int i = 0; i < n_channels; ++i)
-        n_out[i] = S > 0.0 ? n_floor + (int64_t)std::floor((double)free_pts * (sigma[i] / S))
+        n_out[i] = S > 0.0 ? n_floor + (int64_t)std::floor((double)free_pts * (sg[i] / S))
                            : n_floor + free_pts / n_channels;
     return MF_OK;
 }

@@ -115,6 +115,9 @@ def test_allocation_matches_the_oracle(api):
         N = int(rng.integers(K * 10, 10 ** 7))
         floor = int(rng.integers(0, N // K + 1))
         assert api.mf_channels_allocate(sigma, N, floor) == C.allocate(sigma, N, floor)
+        n_prev = [int(v) for v in rng.integers(0, 5000, K)]
+        m0 = float(rng.choice([0.0, 10.0, 1000.0]))
+        assert api.mf_channels_allocate(sigma, N, floor, n_prev, m0) == C.allocate(sigma, N, floor, n_prev, m0)
     assert api.mf_channels_allocate([0.0] * 7, 1000, 3) == C.allocate([0.0] * 7, 1000, 3)
     from paper_2106_10279_gb300 import _lib as L
     with pytest.raises(RuntimeError):

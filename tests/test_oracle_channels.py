@@ -267,6 +267,13 @@ def test_sigma_gg_ttx_by_channels_matches_quadrature():
 
 def test_neyman_allocation_by_hand():
     assert C.allocate([1.0, 3.0, 0.0, 4.0], 1000, 10) == [130, 370, 10, 490]
+    # shrinkage: sigma (1, 3) from 100 points each, m0 = 100: pooled variance
+    # (100 + 900) / 200 = 5, shrunk deviations sqrt(3) and sqrt(7), so the
+    # shares are sqrt(3) / (sqrt(3) + sqrt(7)) = 0.39564.. and 0.60435..
+    assert C.allocate([1.0, 3.0], 1000, 0, n_prev=[100, 100], m0=100.0) == [395, 604]
+    # with m0 = 0 the shrinkage is the identity; with no points, the pooled deviation
+    assert C.allocate([1.0, 3.0], 1000, 0, n_prev=[50, 70], m0=0.0) == [250, 750]
+    assert C.allocate([1.0, 3.0], 1000, 0, n_prev=[0, 100], m0=10.0) == [500, 500]
     assert C.allocate([0.0, 0.0, 0.0], 100, 5) == [33, 33, 33]
     assert C.allocate([2.0], 4096, 4096) == [4096]
     with pytest.raises(ValueError):
