@@ -625,7 +625,7 @@ class MultiChannel:
     iteration's per-point standard deviations, shrunk towards the pooled one
     with m0 pseudo-points (equal shares first)."""
 
-    def __init__(self, proc: "Process", nbins: int = 50, alpha: float = 1.5, m0: float = 1000.0):
+    def __init__(self, proc: "Process", nbins: int = 50, alpha: float = 1.5, m0: float = 100.0):
         self.proc = proc
         self.K = proc.n_channels
         if self.K == 0:
