@@ -249,9 +249,10 @@ class Integrand:
         hels = self.proc.helicities()
         return [hels[h] for h in range(len(hels)) if np.any(np.abs(per[h]) > 1e-12 * tot)]
 
-    def sampled(self, x, seed: int, helicities, pick=None):
+    def sampled(self, x, seed: int, helicities, pick=None, channel=None):
         """f with the helicity of point i drawn from the first unit number of
-        Philox counter (i, 0, 0, 14), key (seed, 0) (or given by pick)."""
+        Philox counter (i, 0, 0, 14), key (seed, 0) (or given by pick); with a
+        channel index (after use_channels), through that phase-space channel."""
         from oracle.philox import philox4x64_10, to_unit
         x = np.asarray(x, dtype=np.float64)
         N = x.shape[1]
@@ -262,7 +263,7 @@ class Integrand:
             ctr[:, 3] = np.uint64(14)
             u = to_unit(philox4x64_10(ctr, np.array([seed, 0], dtype=np.uint64))[:, 0])
             pick = np.minimum((u * nh).astype(np.int64), nh - 1)
-        p, s_hat, x1, x2, jx, w, ok = self.kinematics(x)
+        p, s_hat, x1, x2, jx, w, ok = self.kinematics(x, channel=channel)
         keep = ok & self.cuts(p)
         f = np.zeros(N)
         idx = np.nonzero(keep)[0]

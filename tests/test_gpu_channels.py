@@ -269,3 +269,37 @@ def test_multichannel_checkpoint_resumes_bit_for_bit(env):
         (rb["integral"], rb["error"], rb["sigma"], rb["sigma_error"])
     with pytest.raises(ValueError):
         api.MultiChannel(api.Process.from_workload(W.WORKLOADS["gg_ttx"])).load(blob)
+
+
+def test_helicity_sampled_channel_iteration_matches_the_oracle(env):
+    # one launch over every channel with one sampled helicity per point: point
+    # i of channel k draws its helicity from Philox counter (i, 0, k, 14)
+    torch, api = env
+    from oracle import vegas
+    from oracle.philox import philox4x64_10, to_unit, vegas_uniforms
+    name, n, seed = "gg_ttxg", 1500, 4321
+    wl = W.WORKLOADS[name]
+    I = _oracle(name)
+    hels = I.nonzero_helicities()
+    proc = api.Process.from_workload(wl)
+    proc.set_helicity_sampling(True, seed=9)
+    K = proc.n_channels
+    grids = [api.Vegas(wl.ndim, 50, 1.5) for _ in range(K)]
+    res = api.mf_vegas_iterate_channels([g.handle for g in grids], proc.handle, [n] * K, seed, "fp64")
+    grid = vegas.uniform_grid(wl.ndim, 50)
+    for k in (0, 4, 9, K - 1):
+        y = vegas_uniforms(seed, 0, k, 0, n, wl.ndim)
+        x, jac, bins = vegas.vegas_map(grid, y)
+        ctr = np.zeros((n, 4), dtype=np.uint64)
+        ctr[:, 0] = np.arange(n, dtype=np.uint64)
+        ctr[:, 2] = np.uint64(k)
+        ctr[:, 3] = np.uint64(14)
+        u = to_unit(philox4x64_10(ctr, np.array([seed, 0], dtype=np.uint64))[:, 0])
+        pick = np.minimum((u * len(hels)).astype(np.int64), len(hels) - 1)
+        f, _ = I.sampled(x, seed, hels, pick=pick, channel=k)
+        w = f * jac
+        s1, s2, dsum, cnt = vegas.accumulate(w, bins, 50)
+        I_k, err = vegas.iteration_result(s1, s2, n)
+        hs, hc = grids[k].histogram()
+        assert np.array_equal(hc, cnt), k
+        assert abs(res[k]["integral"] - I_k) <= 1e-10 * abs(I_k) + 1e-300, (k, res[k]["integral"], I_k)
