@@ -33,7 +33,7 @@ METRIC = "events/s of gg→tt̄g(g) LO integrand: mixed/batched vs FP64 at ≤1e
 # one full-size 4e7-point gg->tt~gg iteration divided by its points (the
 # capture's kernel is the one built from this source: vertex routines
 # specialised on their couplings' phase)
-KERNEL_DRAM_BYTES_PER_POINT = {("gg_ttxgg", "mixed"): (92887552 + 15598926592) / 4e7}
+KERNEL_DRAM_BYTES_PER_POINT = {("gg_ttxgg", "mixed"): (170401024 + 22289582336) / 4e7}
 WORKLOAD = "gg_ttxgg"
 # FP64 FLOPs per point executed by the gradient kernel (2 x DFMA + DADD +
 # DMUL thread instructions of one ncu capture divided by its points)
