@@ -426,6 +426,10 @@ mf_status mf_channel_integrand(mf_process *p, int32_t channel, const double *x, 
  * combination are those of mf_vegas_iterate, per channel.  All channels'
  * points are evaluated in one kernel launch, so the grids must have the
  * same number of bins and the same iteration count (MF_EINVAL otherwise).
+ * With refine != 0, a channel's grid is refined only if the channel had at
+ * least 20 points per bin (n_events[k] >= 20 nbins): a grid refined on a
+ * few points per bin follows the few points that landed and leaves the rest
+ * of the channel unsampled.
  * out: host [n_channels].  The iteration's cross section is the sum of the
  * channels' integrals and its variance the sum of theirs.  Synchronous. */
 mf_status mf_vegas_iterate_channels(mf_vegas *const *grids, mf_process *p, const int64_t *n_events,

@@ -88,6 +88,7 @@ constexpr int kAccThreads = 256;
 constexpr int kTreeLog = 8;            // vegas_tree_kernel: 2^kTreeLog threads
 constexpr int kTreeThreads = 1 << kTreeLog;
 constexpr int kTreeMaxLevel = 40;      // at most 2^40 chunks per iteration
+constexpr int kChannelRefinePerBin = 20;  // points per bin a channel's grid needs to be refined
 constexpr double kGeV2pb = 0.3893793721e9;
 constexpr double kPi = 3.14159265358979323846;
 
@@ -240,6 +241,7 @@ struct ChanAcc {
     const uint8_t *bins;
     long long n, nchunks;
     int level, iteration;
+    int refine, pad;            // refine this channel's grid
     double alpha;
     double *slots, *tree_out, *hist, *hist_iter, *result, *grid;
     long long *count;
@@ -453,7 +455,7 @@ __global__ void vegas_refine_kernel(double *grid, const double *hist, int ndim, 
 // Block c: channel c's refinement, one thread per dimension.
 __global__ void vegas_refine_channels_kernel(const ChanAcc *ca, int ndim, int nb) {
     const ChanAcc &c = ca[blockIdx.x];
-    if ((int)threadIdx.x < ndim) refine_dim(c.grid, c.hist, ndim, nb, c.n, c.alpha, threadIdx.x);
+    if (c.refine && (int)threadIdx.x < ndim) refine_dim(c.grid, c.hist, ndim, nb, c.n, c.alpha, threadIdx.x);
 }
 
 __device__ void refine_dim(double *grid, const double *hist, int ndim, int nb, int64_t n, double alpha, int j) {
@@ -1847,6 +1849,11 @@ extern "C" mf_status mf_vegas_iterate_channels(mf_vegas *const *grids, mf_proces
         c.nchunks = nch;
         c.level = tree_levels(nch);
         c.iteration = v->iteration;
+        // a grid refined on a few points per bin chases the few points that
+        // landed (and forgets the rest): a channel's grid adapts only from
+        // kChannelRefinePerBin points per bin on
+        c.refine = refine && n_events[k] >= (int64_t)kChannelRefinePerBin * v->nbins ? 1 : 0;
+        c.pad = 0;
         c.alpha = v->alpha;
         c.slots = v->d_slots;
         c.tree_out = v->d_tree_out;
