@@ -427,7 +427,7 @@ mf_status mf_channel_integrand(mf_process *p, int32_t channel, const double *x, 
  * points are evaluated in one kernel launch, so the grids must have the
  * same number of bins and the same iteration count (MF_EINVAL otherwise).
  * With refine != 0, a channel's grid is refined only if the channel had at
- * least 20 points per bin (n_events[k] >= 20 nbins): a grid refined on a
+ * least 100 points per bin (n_events[k] >= 100 nbins): a grid refined on a
  * few points per bin follows the few points that landed and leaves the rest
  * of the channel unsampled.
  * out: host [n_channels].  The iteration's cross section is the sum of the

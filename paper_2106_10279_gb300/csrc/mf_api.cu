@@ -88,7 +88,7 @@ constexpr int kAccThreads = 256;
 constexpr int kTreeLog = 8;            // vegas_tree_kernel: 2^kTreeLog threads
 constexpr int kTreeThreads = 1 << kTreeLog;
 constexpr int kTreeMaxLevel = 40;      // at most 2^40 chunks per iteration
-constexpr int kChannelRefinePerBin = 20;  // points per bin a channel's grid needs to be refined
+constexpr int kChannelRefinePerBin = 100;  // points per bin a channel's grid needs to be refined
 constexpr double kGeV2pb = 0.3893793721e9;
 constexpr double kPi = 3.14159265358979323846;
 
