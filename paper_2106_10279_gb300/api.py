@@ -622,10 +622,11 @@ class MultiChannel:
     """Vegas over the multichannel phase space of a process: one grid per
     channel, the cross section the sum of the channels' integrals, and the
     points of each iteration shared out by Neyman's rule from the previous
-    iteration's per-point standard deviations, shrunk towards the pooled one
-    with m0 pseudo-points (equal shares first)."""
+    iteration's per-point standard deviations (equal shares first; with
+    m0 > 0 each deviation is first shrunk towards the pooled one with m0
+    pseudo-points)."""
 
-    def __init__(self, proc: "Process", nbins: int = 50, alpha: float = 1.5, m0: float = 100.0):
+    def __init__(self, proc: "Process", nbins: int = 50, alpha: float = 1.5, m0: float = 0.0):
         self.proc = proc
         self.K = proc.n_channels
         if self.K == 0:
