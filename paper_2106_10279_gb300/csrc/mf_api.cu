@@ -1777,6 +1777,7 @@ extern "C" mf_status mf_vegas_iterate_channels(mf_vegas *const *grids, mf_proces
     if (!grids || !p || !n_events || !out) return fail(MF_EINVAL, "bad arguments");
     if (p->channels.K == 0) return fail(MF_EUNSUPPORTED, "the process has no phase-space channels");
     if (n_channels != p->channels.K) return fail(MF_EINVAL, "one grid per channel of the process");
+    if (n_channels > 65535) return fail(MF_EUNSUPPORTED, "more channels than one launch's grid rows");
     if (!valid_prec(prec)) return fail(MF_EINVAL, "bad precision");
     cudaStream_t s = (cudaStream_t)stream;
     for (int k = 0; k < n_channels; ++k) {
