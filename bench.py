@@ -462,7 +462,7 @@ def run_native(args):
             for lst, v_ in zip(legs["multichannel"], (ms, r["error"], r["integral"])):
                 lst.append(v_)
         phase_space = {"events_per_iteration": nps, "adapt_iterations": 5, "seeds": 5, "channels": proc.n_channels,
-                       "regulators_gev2": max(wl.pt_min_gluon, 1.0) ** 2}
+                       "regulators_gev2": (4.0 * max(wl.pt_min_gluon, 1.0)) ** 2}
         for tag, (ms_l, err_l, int_l) in legs.items():
             phase_space[tag] = {"iteration_ms": statistics.median(ms_l),
                                 "events_per_s": nps / (statistics.median(ms_l) / 1e3),

@@ -410,7 +410,7 @@ mf_status mf_process_channels(const mf_process *p, int32_t *n_channels);
 
 /* mf_process_set_channel_regulators: the regulators s0 and t0 (GeV^2, > 0)
  * of the channels' s- and t-channel densities and of the partition
- * (default: max(pt_min, 1 GeV)^2 for both). */
+ * (default: (4 max(pt_min, 1 GeV))^2 for both). */
 mf_status mf_process_set_channel_regulators(mf_process *p, double s0, double t0);
 
 /* mf_channel_integrand: as mf_integrand (x: device SoA [ndim][n], f: device

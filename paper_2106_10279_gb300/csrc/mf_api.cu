@@ -1014,7 +1014,7 @@ extern "C" mf_status mf_create_process(const mf_process_desc *d, mf_process **ou
                 return fail(MF_ENOMEM, "channel table");
             }
         }
-        const double r = std::max(p->pt_min, 1.0);
+        const double r = 4.0 * std::max(p->pt_min, 1.0);
         p->ch_s0 = p->ch_t0 = r * r;
     }
     // PDF rows at fixed mu_F^2

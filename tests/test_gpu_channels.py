@@ -31,7 +31,6 @@ import workloads as W
 from _tolerance import fp64_tolerance, relerr
 
 pytestmark = pytest.mark.gpu
-R0 = 400.0
 
 
 @pytest.fixture(scope="module")
@@ -48,7 +47,7 @@ def env():
 def _oracle(name):
     from oracle.integrand import Integrand
     I = Integrand(W.WORKLOADS[name])
-    r = max(W.WORKLOADS[name].pt_min_gluon, 1.0) ** 2
+    r = (4.0 * max(W.WORKLOADS[name].pt_min_gluon, 1.0)) ** 2  # the library's default regulators
     I.use_channels(r, r)
     return I
 

@@ -64,7 +64,7 @@ def test_gg_ttxggg_matches_the_oracle(env, capsys):
     assert np.array_equal(ftc == 0, ref == 0)
     assert np.median(rtc) <= 1e-5 and rtc.max() <= 1e-3
     # two of the 945 phase-space channels, per point in FP64
-    r0 = max(wl.pt_min_gluon, 1.0) ** 2
+    r0 = (4.0 * max(wl.pt_min_gluon, 1.0)) ** 2
     I.use_channels(r0, r0)
     assert proc.n_channels == len(I.channels) == 945
     for ch in (0, 700):
