@@ -302,3 +302,29 @@ def test_helicity_sampled_channel_iteration_matches_the_oracle(env):
         hs, hc = grids[k].histogram()
         assert np.array_equal(hc, cnt), k
         assert abs(res[k]["integral"] - I_k) <= 1e-10 * abs(I_k) + 1e-300, (k, res[k]["integral"], I_k)
+
+
+def test_regulators_set_per_process(env):
+    # other regulators than the default: the library's points and weights
+    # follow the oracle's with the same s0 and t0
+    torch, api = env
+    from oracle.integrand import Integrand
+    wl = W.WORKLOADS["gg_ttxg"]
+    proc = api.Process.from_workload(wl)
+    proc.set_channel_regulators(900.0, 2500.0)
+    I = Integrand(wl)
+    I.use_channels(900.0, 2500.0)
+    x = W.uniform_points(wl.ndim, 40, 77)
+    xd = torch.from_numpy(x).cuda()
+    got = {}
+    for ch in (0, 7, 14):
+        f = proc.channel_integrand(xd, ch, "fp64").cpu().numpy()
+        ref, tol = fp64_tolerance(lambda y, return_parts=False: I(y, return_parts=return_parts, channel=ch), x)
+        assert np.array_equal(f == 0, ref == 0), ch
+        assert np.all(relerr(f, ref) <= tol), ch
+        got[ch] = f
+    # and they change the weights
+    proc.set_channel_regulators(6400.0, 6400.0)
+    g = proc.channel_integrand(xd, 7, "fp64").cpu().numpy()
+    nz = (g != 0) & (got[7] != 0)
+    assert nz.sum() > 10 and np.max(np.abs(g[nz] / got[7][nz] - 1)) > 1e-3
