@@ -328,3 +328,32 @@ def test_regulators_set_per_process(env):
     g = proc.channel_integrand(xd, 7, "fp64").cpu().numpy()
     nz = (g != 0) & (got[7] != 0)
     assert nz.sum() > 10 and np.max(np.abs(g[nz] / got[7][nz] - 1)) > 1e-3
+
+
+def test_channel_iteration_with_tensor_core_sum_and_colour_sampling(env):
+    # the one launch over every channel in the other kernels of a process:
+    # the tensor-core colour sum (same points, integrals within the mixed
+    # precision bound) and the colour-sampled kernel (an unbiased estimator
+    # of the same cross section)
+    torch, api = env
+    wl = W.WORKLOADS["gg_ttxgg"]
+    proc = api.Process.from_workload(wl)
+    K = proc.n_channels
+    n = [3000] * K
+    ga = [api.Vegas(wl.ndim) for _ in range(K)]
+    gb = [api.Vegas(wl.ndim) for _ in range(K)]
+    ra = api.mf_vegas_iterate_channels([g.handle for g in ga], proc.handle, n, 11, "mixed", False)
+    rb = api.mf_vegas_iterate_channels([g.handle for g in gb], proc.handle, n, 11, "mixed_tc", False)
+    for k in range(K):
+        assert ra[k]["n_nonzero"] == rb[k]["n_nonzero"], k
+        assert abs(rb[k]["integral"] - ra[k]["integral"]) <= 1e-4 * abs(ra[k]["integral"]) + 1e-300, k
+    proc.set_colour_sampling(True)
+    gc = [api.Vegas(wl.ndim) for _ in range(K)]
+    rc = api.mf_vegas_iterate_channels([g.handle for g in gc], proc.handle, n, 11, "mixed", False)
+    proc.set_colour_sampling(False)
+    sa = sum(r["integral"] for r in ra)
+    sc = sum(r["integral"] for r in rc)
+    ea = math.sqrt(sum(r["error"] ** 2 for r in ra))
+    ec = math.sqrt(sum(r["error"] ** 2 for r in rc))
+    assert all(rc[k]["n_nonzero"] == ra[k]["n_nonzero"] for k in range(K))
+    assert abs(sc - sa) < 5 * math.hypot(ea, ec), (sa, ea, sc, ec)
