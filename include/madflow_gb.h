@@ -309,6 +309,15 @@ mf_status mf_helicity_msq(mf_process *p, const double *x, int64_t n, double *out
 mf_status mf_grad(mf_process *p, const double *x, int64_t n, double *f, double *df_dparam,
                   double *df_dx, void *stream);
 
+/* mf_grad_channel: mf_grad for points mapped through phase-space channel
+ * `channel` (see mf_vegas_iterate_channels): the derivatives follow the
+ * channel's momenta and its weight a_i / g_i (through the sampled ranges,
+ * the mapped densities and the partition; m_t also enters the top
+ * propagators' masses there).  MF_EUNSUPPORTED if the process has no
+ * channels, MF_EINVAL for a channel out of range. */
+mf_status mf_grad_channel(mf_process *p, int32_t channel, const double *x, int64_t n, double *f, double *df_dparam,
+                          double *df_dx, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Vegas (Sec. 2.2; G.P. Lepage, J. Comput. Phys. 27 (1978) 192).              */
 /* ------------------------------------------------------------------------ */

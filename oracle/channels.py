@@ -202,8 +202,19 @@ def derive_channels(proc: Process):
 
 
 # ----------------------------------------------------------------------------
-# kinematics helpers (vectorised over points)
+# kinematics helpers (vectorised over points; plain arrays or the dual numbers
+# of oracle/dual.py, for derivatives)
 # ----------------------------------------------------------------------------
+def _total(xs):
+    """Sum of a list of numbers or dual numbers (0 when empty)."""
+    out = 0.0
+    for x in xs:
+        out = x + out
+    return out
+
+
+def _clip1(c):
+    return np.minimum(np.maximum(c, -1.0), 1.0)
 def _mdot(a, b):
     return a[..., 0] * b[..., 0] - a[..., 1] * b[..., 1] - a[..., 2] * b[..., 2] - a[..., 3] * b[..., 3]
 
@@ -271,14 +282,17 @@ def generate(ch: Channel, u, rs, fm, s0: float, t0: float, masses):
     """Final-state momenta [N, n, 4] (partonic CM frame), 1/g_i [N] and a
     validity flag [N] from unit numbers u [3n-4, N] through channel ch.
     fm: final masses [n]; masses: mass ids -> GeV (masses[0] = m_t)."""
-    u = np.asarray(u, dtype=np.float64)
-    rs = np.asarray(rs, dtype=np.float64)
+    from .dual import Dual, as_f64
+    u = as_f64(u)
+    rs = as_f64(rs)
     N = u.shape[1]
     nf = len(fm)
-    fm = np.asarray(fm, dtype=np.float64)
+    if not any(isinstance(v, Dual) for v in fm):
+        fm = np.asarray(fm, dtype=np.float64)
     s_hat = rs * rs
-    p = np.zeros((N, nf, 4))
-    inv_g = np.ones(N)
+    like = next((v for v in (u, rs) if isinstance(v, Dual)), None)
+    p = np.zeros((N, nf, 4), like=like) if like is not None else np.zeros((N, nf, 4))
+    inv_g = 1.0 + 0.0 * rs
     ok = np.ones(N, dtype=bool)
     col = [0]
 
@@ -288,10 +302,13 @@ def generate(ch: Channel, u, rs, fm, s0: float, t0: float, masses):
         return v
 
     def M2(mid):
-        return 0.0 if mid < 0 else float(masses[mid]) ** 2
+        return 0.0 if mid < 0 else masses[mid] ** 2
 
     def mmin(x):
-        return float(sum(fm[i] for i in _legs(x)))
+        return _total([fm[i] for i in sorted(_legs(x))])
+
+    def const(v):
+        return v + 0.0 * rs
 
     def mass_step(lo, hi, M2v, reg):
         nonlocal ok
@@ -307,13 +324,13 @@ def generate(ch: Channel, u, rs, fm, s0: float, t0: float, masses):
     for j in range(k):
         c = spine[j]
         if not isinstance(c, Cluster):
-            s_c[j] = np.full(N, fm[c] ** 2)
+            s_c[j] = const(fm[c] ** 2)
             continue
         if k == 1:
             s_c[j] = s_hat
             continue
-        top = rs - sum(np.sqrt(s_c[i]) for i in range(j)) - sum(mmin(spine[i]) for i in range(j + 1, k))
-        lo = np.full(N, mmin(c) ** 2)
+        top = rs - _total([np.sqrt(s_c[i]) for i in range(j)]) - _total([mmin(spine[i]) for i in range(j + 1, k)])
+        lo = const(mmin(c) ** 2)
         s, inv = mass_step(lo, np.maximum(top, 0.0) ** 2, M2(c.mass), s0)
         s_c[j] = s
         inv_g = inv_g * inv / TWO_PI
@@ -322,7 +339,7 @@ def generate(ch: Channel, u, rs, fm, s0: float, t0: float, masses):
     if k >= 2:
         s_R[k - 1] = s_c[k - 1]
     for j in range(1, k - 1):
-        lo = sum(np.sqrt(s_c[i]) for i in range(j, k)) ** 2
+        lo = _total([np.sqrt(s_c[i]) for i in range(j, k)]) ** 2
         hi = np.maximum(np.sqrt(s_R[j - 1]) - np.sqrt(s_c[j - 1]), 0.0) ** 2
         ok = ok & (hi >= lo)
         hi = np.maximum(hi, lo)
@@ -352,7 +369,7 @@ def generate(ch: Channel, u, rs, fm, s0: float, t0: float, masses):
         L = np.log1p(2.0 * Bs / AmB)
         uc = take()
         c_pole = -1.0 - (A + Bs) * np.expm1(-uc * L) / Bs
-        cth = np.clip(np.where(pole, c_pole, 2.0 * uc - 1.0), -1.0, 1.0)
+        cth = _clip1(np.where(pole, c_pole, 2.0 * uc - 1.0))
         inv_h = np.where(pole, (A - Bs * cth) * L / Bs, 2.0)
         phi = TWO_PI * take()
         # axis frame: R_z(phi_q) R_y(theta_q)
@@ -381,19 +398,19 @@ def generate(ch: Channel, u, rs, fm, s0: float, t0: float, masses):
         nonlocal inv_g, ok
         L, R = node.left, node.right
         if isinstance(L, Cluster):
-            lo = np.full(N, mmin(L) ** 2)
+            lo = const(mmin(L) ** 2)
             hi = np.maximum(np.sqrt(sX) - mmin(R), 0.0) ** 2
             sL, inv = mass_step(lo, hi, M2(L.mass), s0)
             inv_g = inv_g * inv / TWO_PI
         else:
-            sL = np.full(N, fm[L] ** 2)
+            sL = const(fm[L] ** 2)
         if isinstance(R, Cluster):
-            lo = np.full(N, mmin(R) ** 2)
+            lo = const(mmin(R) ** 2)
             hi = np.maximum(np.sqrt(sX) - np.sqrt(sL), 0.0) ** 2
             sR, inv = mass_step(lo, hi, M2(R.mass), s0)
             inv_g = inv_g * inv / TWO_PI
         else:
-            sR = np.full(N, fm[R] ** 2)
+            sR = const(fm[R] ** 2)
         cth = 2.0 * take() - 1.0
         phi = TWO_PI * take()
         PL, PR, lam = _two_body(X, sX, sL, sR, _direction(cth, phi))
@@ -435,17 +452,17 @@ def propagator_products(channels, pa, p, s0: float, t0: float, masses):
     1 / (|x - M^2| + r)^2, at final momenta p [N, n, 4] and incoming a
     momentum pa [N, 4]."""
     N = p.shape[0]
-    out = np.ones((N, len(channels)))
+    cols = []
 
     def M2(mid):
-        return 0.0 if mid < 0 else float(masses[mid]) ** 2
+        return 0.0 if mid < 0 else masses[mid] ** 2
 
     def inv(x, m2, r):
         d = np.abs(x - m2) + r
         return 1.0 / (d * d)
 
     for i, ch in enumerate(channels):
-        P = np.ones(N)
+        P = 1.0
         for c in ch.spine:
             for X in _clusters(c):
                 if ch.k == 1 and X is c:
@@ -458,14 +475,14 @@ def propagator_products(channels, pa, p, s0: float, t0: float, masses):
         for j in range(ch.k - 1):
             q = q - np.sum(p[:, sorted(_legs(ch.spine[j]))], axis=1)
             P = P * inv(_mdot(q, q), M2(ch.t_mass[j]), t0)
-        out[:, i] = P
-    return out
+        cols.append(P + 0.0 * pa[:, 0])
+    return np.stack(cols, axis=1)
 
 
 def partition(channels, pa, p, s0, t0, masses):
     """a_i [N, K] = P_i / sum_j P_j."""
     P = propagator_products(channels, pa, p, s0, t0, masses)
-    return P / np.sum(P, axis=1, keepdims=True)
+    return P / np.sum(P, axis=1)[:, None]
 
 
 # ----------------------------------------------------------------------------

@@ -216,6 +216,10 @@ class Dual:
                 return Dual(r, d * r[..., None])
             if ufunc is np.log:
                 return Dual(np.log(v), d / v[..., None])
+            if ufunc is np.log1p:
+                return Dual(np.log1p(v), d / (1.0 + v)[..., None])
+            if ufunc is np.expm1:
+                return Dual(np.expm1(v), d * np.exp(v)[..., None])
             if ufunc is np.sin:
                 return Dual(np.sin(v), d * np.cos(v)[..., None])
             if ufunc is np.cos:

@@ -78,7 +78,7 @@ class Integrand:
         self.s0, self.t0 = float(s0), float(t0)
         return self.channels
 
-    def kinematics(self, x, final_masses=None, channel=None):
+    def kinematics(self, x, final_masses=None, channel=None, masses=None):
         """Momenta [N, n, 4], s-hat, x1, x2, J_x and W for points x [ndim, N]
         (final-state masses as given, else the workload's).  With a channel
         index (after use_channels) the momenta come from that channel and W
@@ -102,11 +102,10 @@ class Integrand:
         n_out = self.wl.n_out
         if channel is not None:
             from . import channels as chmod
-            if final_masses is not None:
-                raise ValueError("the multichannel path takes the workload's masses")
-            k, inv_g, ok = chmod.generate(self.channels[channel], u, rs, fm, self.s0, self.t0, [self.m_top])
+            mt = [self.m_top] if masses is None else masses
+            k, inv_g, ok = chmod.generate(self.channels[channel], u, rs, fm, self.s0, self.t0, mt)
             pa = np.stack([rs / 2, 0 * rs, 0 * rs, rs / 2], axis=1)
-            a = chmod.partition(self.channels, pa, k, self.s0, self.t0, [self.m_top])[:, channel]
+            a = chmod.partition(self.channels, pa, k, self.s0, self.t0, mt)[:, channel]
             w = a * inv_g
         else:
             p0 = ps.massless_diet(u, rs)
@@ -179,7 +178,7 @@ class Integrand:
 
     # ------------------------------------------------------------------
     # derivatives by forward-mode dual numbers
-    def gradient(self, x):
+    def gradient(self, x, channel=None):
         """(f [N], df/dx [ndim, N], df/dm_t [N]) at points x [ndim, N]: the
         integrand evaluated once in dual arithmetic with tangents along every
         coordinate of x and along the top mass (which enters the threshold
@@ -199,7 +198,7 @@ class Integrand:
         saved = self.proc.masses
         self.proc.masses = {**saved, "t": mt}
         try:
-            p, s_hat, x1, x2, jx, w, ok = self.kinematics(X, final_masses=fm)
+            p, s_hat, x1, x2, jx, w, ok = self.kinematics(X, final_masses=fm, channel=channel, masses=[mt])
             pv = p.v if isinstance(p, Dual) else p
             keep = ok & self.cuts(pv)
             f = Dual(np.zeros(N), np.zeros((N, K)))

@@ -95,6 +95,8 @@ SIGNATURES = {
     "mf_integrand": (c_i32, [C.c_void_p, C.c_void_p, c_i64, C.c_void_p, c_i32, C.c_void_p]),
     "mf_helicity_msq": (c_i32, [C.c_void_p, C.c_void_p, c_i64, C.c_void_p, c_i32, C.c_void_p]),
     "mf_grad": (c_i32, [C.c_void_p, C.c_void_p, c_i64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mf_grad_channel": (c_i32, [C.c_void_p, c_i32, C.c_void_p, c_i64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                C.c_void_p]),
     "mf_vegas_create": (c_i32, [c_i32, c_i32, C.c_double, P(C.c_void_p)]),
     "mf_vegas_destroy": (c_i32, [C.c_void_p]),
     "mf_vegas_iterate": (c_i32, [P(C.c_void_p), P(C.c_void_p), P(c_i64), c_i32, C.c_uint64, c_i32, c_i32,

@@ -195,9 +195,14 @@ def mf_helicity_msq(h, x, n: int, out, precision="fp64", stream=None):
                                            _stream_ptr(stream)), "mf_helicity_msq")
 
 
-def mf_grad(h, x, n: int, f, df_dparam, df_dx=None, stream=None):
-    """Device tensors or pointers: x [ndim, n], f [n], df_dparam [2, n], df_dx [ndim, n] or None."""
+def mf_grad(h, x, n: int, f, df_dparam, df_dx=None, stream=None, channel=None):
+    """Device tensors or pointers: x [ndim, n], f [n], df_dparam [2, n], df_dx [ndim, n] or None
+    (with a channel: mf_grad_channel)."""
     ptr = lambda t: 0 if t is None else (t if isinstance(t, int) else t.data_ptr())
+    if channel is not None:
+        return L.check(L.lib().mf_grad_channel(h, channel, C.c_void_p(ptr(x)), n, C.c_void_p(ptr(f)),
+                                               C.c_void_p(ptr(df_dparam)), C.c_void_p(ptr(df_dx) or None),
+                                               _stream_ptr(stream)), "mf_grad_channel")
     return L.check(L.lib().mf_grad(h, C.c_void_p(ptr(x)), n, C.c_void_p(ptr(f)), C.c_void_p(ptr(df_dparam)),
                                    C.c_void_p(ptr(df_dx) or None), _stream_ptr(stream)), "mf_grad")
 
@@ -542,14 +547,15 @@ class Process:
                                         C.byref(h)), "mf_process_tune")
         return b.value, h.value
 
-    def grad(self, x, with_dx=True, stream=None):
-        """(f [n], df/dparam [2, n] (m_t, alpha_s), df/dx [ndim, n] or None)."""
+    def grad(self, x, with_dx=True, stream=None, channel=None):
+        """(f [n], df/dparam [2, n] (m_t, alpha_s), df/dx [ndim, n] or None);
+        with a channel, through that phase-space channel."""
         import torch
         n = x.shape[1]
         f = torch.empty(n, dtype=torch.float64, device=x.device)
         dp = torch.empty((2, n), dtype=torch.float64, device=x.device)
         dx = torch.empty((self.ndim, n), dtype=torch.float64, device=x.device) if with_dx else None
-        mf_grad(self.handle, x, n, f, dp, dx, stream)
+        mf_grad(self.handle, x, n, f, dp, dx, stream, channel)
         return f, dp, dx
 
     def helicity_msq(self, x, precision="fp64", stream=None):

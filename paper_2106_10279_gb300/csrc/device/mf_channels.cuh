@@ -37,6 +37,7 @@
 //   channels at 16 + 4 E: K records of MF_CH_STRIDE (offsets below).
 #pragma once
 #include "mf_common.cuh"
+#include "mf_dual.cuh"
 
 #define MF_CH_MAX_FINAL 6
 #define MF_CH_MAX_EDGES 128
@@ -62,18 +63,21 @@
 
 namespace mf {
 
-MF_DEV double ch_sqrt_lambda(double s, double s1, double s2) {
-    const double m1 = sqrt(s1), m2 = sqrt(s2);
-    double a = s - (m1 + m2) * (m1 + m2), b = s - (m1 - m2) * (m1 - m2);
-    a = a > 0.0 ? a : 0.0;
-    b = b > 0.0 ? b : 0.0;
+// T is double, or a dual number carrying derivatives (the gradient kernel).
+template <typename T>
+MF_DEV T ch_sqrt_lambda(const T &s, const T &s1, const T &s2) {
+    const T m1 = sqrt(s1), m2 = sqrt(s2);
+    T a = s - (m1 + m2) * (m1 + m2), b = s - (m1 - m2) * (m1 - m2);
+    a = a > 0.0 ? a : T(0.0);
+    b = b > 0.0 ? b : T(0.0);
     return sqrt(a * b);
 }
 
 // p (given in the frame where Q = (Q0, Q)) -> rest frame of Q (mass M)
-MF_DEV void ch_boost_to_rest(const double *p, const double *Q, double M, double *out) {
-    const double e = (Q[0] * p[0] - Q[1] * p[1] - Q[2] * p[2] - Q[3] * p[3]) / M;
-    const double c = (p[0] + e) / (Q[0] + M);
+template <typename T>
+MF_DEV void ch_boost_to_rest(const T *p, const T *Q, const T &M, T *out) {
+    const T e = (Q[0] * p[0] - Q[1] * p[1] - Q[2] * p[2] - Q[3] * p[3]) / M;
+    const T c = (p[0] + e) / (Q[0] + M);
     out[0] = e;
     out[1] = p[1] - c * Q[1];
     out[2] = p[2] - c * Q[2];
@@ -81,9 +85,10 @@ MF_DEV void ch_boost_to_rest(const double *p, const double *Q, double M, double 
 }
 
 // p (given in the rest frame of Q, mass M) -> frame of Q
-MF_DEV void ch_boost_from_rest(const double *p, const double *Q, double M, double *out) {
-    const double e = (Q[0] * p[0] + Q[1] * p[1] + Q[2] * p[2] + Q[3] * p[3]) / M;
-    const double c = (p[0] + e) / (Q[0] + M);
+template <typename T>
+MF_DEV void ch_boost_from_rest(const T *p, const T *Q, const T &M, T *out) {
+    const T e = (Q[0] * p[0] + Q[1] * p[1] + Q[2] * p[2] + Q[3] * p[3]) / M;
+    const T c = (p[0] + e) / (Q[0] + M);
     out[0] = e;
     out[1] = p[1] + c * Q[1];
     out[2] = p[2] + c * Q[2];
@@ -92,11 +97,12 @@ MF_DEV void ch_boost_from_rest(const double *p, const double *Q, double M, doubl
 
 // s on [lo, hi] with density 1 / (s - M2 + reg) (flat where lo - M2 + reg
 // <= 0); inv = 1 / density
-MF_DEV double ch_mass_sample(double u, double lo, double hi, double M2, double reg, double &inv) {
-    const double a = lo - M2 + reg;
+template <typename T>
+MF_DEV T ch_mass_sample(const T &u, const T &lo, const T &hi, const T &M2, double reg, T &inv) {
+    const T a = lo - M2 + reg;
     if (a > 0.0) {
-        const double L = log1p((hi - lo) / a);
-        const double s = lo + a * expm1(u * L);
+        const T L = log1p((hi - lo) / a);
+        const T s = lo + a * expm1(u * L);
         inv = (a * exp(u * L)) * L;
         return s;
     }
@@ -106,22 +112,23 @@ MF_DEV double ch_mass_sample(double u, double lo, double hi, double M2, double r
 
 // daughters of X (mass^2 sX) with masses^2 sL, sR, L along the unit vector n
 // in X's rest frame; momenta in X's frame; returns lambda^(1/2)(sX, sL, sR)
-MF_DEV double ch_two_body(const double *X, double sX, double sL, double sR, const double *n, double *L,
-                          double *R) {
-    const double M = sqrt(sX);
-    const double lam = ch_sqrt_lambda(sX, sL, sR);
-    const double p = lam / (2.0 * M);
-    const double l[4] = {(sX + sL - sR) / (2.0 * M), p * n[0], p * n[1], p * n[2]};
-    const double r[4] = {(sX + sR - sL) / (2.0 * M), -p * n[0], -p * n[1], -p * n[2]};
+template <typename T>
+MF_DEV T ch_two_body(const T *X, const T &sX, const T &sL, const T &sR, const T *n, T *L, T *R) {
+    const T M = sqrt(sX);
+    const T lam = ch_sqrt_lambda(sX, sL, sR);
+    const T p = lam / (2.0 * M);
+    const T l[4] = {(sX + sL - sR) / (2.0 * M), p * n[0], p * n[1], p * n[2]};
+    const T r[4] = {(sX + sR - sL) / (2.0 * M), -(p * n[0]), -(p * n[1]), -(p * n[2])};
     ch_boost_from_rest(l, X, M, L);
     ch_boost_from_rest(r, X, M, R);
     return lam;
 }
 
-MF_DEV void ch_direction(double c, double phi, double *n) {
-    double s2 = (1.0 - c) * (1.0 + c);
-    const double st = s2 > 0.0 ? sqrt(s2) : 0.0;
-    double sp, cp;
+template <typename T>
+MF_DEV void ch_direction(const T &c, const T &phi, T *n) {
+    T s2 = (1.0 - c) * (1.0 + c);
+    const T st = s2 > 0.0 ? sqrt(s2) : T(0.0);
+    T sp, cp;
     sincos(phi, &sp, &cp);
     n[0] = st * cp;
     n[1] = st * sp;
@@ -132,16 +139,17 @@ MF_DEV const int32_t *ch_record(const int32_t *tab, int ch) {
     return tab + MF_CH_HDR + MF_CH_EDGE * tab[1] + MF_CH_STRIDE * ch;
 }
 
-template <int NOUT>
-MF_DEV double ch_mmin(int mask, const double *fm) {
-    double m = 0.0;
+template <int NOUT, typename T>
+MF_DEV T ch_mmin(int mask, const T *fm) {
+    T m = T(0.0);
 #pragma unroll
     for (int i = 0; i < NOUT; ++i)
-        if ((mask >> i) & 1) m += fm[i];
+        if ((mask >> i) & 1) m = m + fm[i];
     return m;
 }
 
-MF_DEV double ch_m2(int id, const double *masses) { return id < 0 ? 0.0 : masses[id] * masses[id]; }
+template <typename T>
+MF_DEV T ch_m2(int id, const T *masses) { return id < 0 ? T(0.0) : masses[id] * masses[id]; }
 
 MF_DEV int ch_lowest(int mask) {
     int i = 0;
@@ -153,24 +161,24 @@ MF_DEV int ch_lowest(int mask) {
 // u[0 .. 3 NOUT - 4); fm: final masses, masses: the process's mass table.
 // Returns false where a sampled range came out empty (the point then has
 // weight zero).
-template <int NOUT>
-MF_CH_FN bool channel_generate(const int32_t *tab, int ch, const double *u, double rs, const double *fm,
-                               const double *masses, double s0, double t0, double (*p)[4], double &inv_g) {
+template <int NOUT, typename T = double>
+MF_CH_FN bool channel_generate(const int32_t *tab, int ch, const T *u, T rs, const T *fm, const T *masses, double s0,
+                               double t0, T (*p)[4], T &inv_g) {
     const double two_pi = 6.283185307179586;
     const double pi = 3.141592653589793;
     const double pi2_32 = 32.0 * (pi * pi);
     const int32_t *c = ch_record(tab, ch);
     const int k = c[MF_CH_K];
-    const double s_hat = rs * rs;
+    const T s_hat = rs * rs;
     int col = 0;
     bool ok = true;
-    double ig = 1.0;
-    double sc[NOUT], sR[NOUT], mom[NOUT][4];
+    T ig = T(1.0);
+    T sc[NOUT], sR[NOUT], mom[NOUT][4];
     // (i) masses of the clusters on the spine
     for (int j = 0; j < k; ++j) {
         const int node = c[MF_CH_CNODE + j];
         if (node < 0) {
-            const double m = fm[ch_lowest(c[MF_CH_CMASK + j])];
+            const T m = fm[ch_lowest(c[MF_CH_CMASK + j])];
             sc[j] = m * m;
             continue;
         }
@@ -178,88 +186,88 @@ MF_CH_FN bool channel_generate(const int32_t *tab, int ch, const double *u, doub
             sc[j] = s_hat;
             continue;
         }
-        double before = 0.0, after = 0.0;
-        for (int i = 0; i < j; ++i) before += sqrt(sc[i]);
-        for (int i = j + 1; i < k; ++i) after += ch_mmin<NOUT>(c[MF_CH_CMASK + i], fm);
-        double top = rs - before - after;
-        top = top > 0.0 ? top : 0.0;
-        const double m0 = ch_mmin<NOUT>(c[MF_CH_CMASK + j], fm);
-        const double lo = m0 * m0;
-        double hi = top * top;
+        T before = T(0.0), after = T(0.0);
+        for (int i = 0; i < j; ++i) before = before + sqrt(sc[i]);
+        for (int i = j + 1; i < k; ++i) after = after + ch_mmin<NOUT>(c[MF_CH_CMASK + i], fm);
+        T top = rs - before - after;
+        top = top > 0.0 ? top : T(0.0);
+        const T m0 = ch_mmin<NOUT>(c[MF_CH_CMASK + j], fm);
+        const T lo = m0 * m0;
+        T hi = top * top;
         ok = ok && hi >= lo;
         hi = hi > lo ? hi : lo;
-        double inv;
+        T inv;
         sc[j] = ch_mass_sample(u[col++], lo, hi, ch_m2(c[MF_CH_NODES + MF_CH_NODE_W * node + 1], masses), s0, inv);
-        ig *= inv / two_pi;
+        ig = ig * (inv / two_pi);
     }
     // (ii) the remainders of the chain
     sR[0] = s_hat;
     if (k >= 2) sR[k - 1] = sc[k - 1];
     for (int j = 1; j < k - 1; ++j) {
-        double lo = 0.0;
-        for (int i = j; i < k; ++i) lo += sqrt(sc[i]);
+        T lo = T(0.0);
+        for (int i = j; i < k; ++i) lo = lo + sqrt(sc[i]);
         lo = lo * lo;
-        double hi = sqrt(sR[j - 1]) - sqrt(sc[j - 1]);
-        hi = hi > 0.0 ? hi * hi : 0.0;
+        T hi = sqrt(sR[j - 1]) - sqrt(sc[j - 1]);
+        hi = hi > 0.0 ? hi * hi : T(0.0);
         ok = ok && hi >= lo;
         hi = hi > lo ? hi : lo;
         sR[j] = lo + u[col++] * (hi - lo);
-        ig *= (hi - lo) / two_pi;
+        ig = ig * ((hi - lo) / two_pi);
     }
     // (iii) the chain R_{j-1} -> c_j + R_j
-    double R[4] = {rs, 0.0, 0.0, 0.0};
-    double q[4] = {0.5 * rs, 0.0, 0.0, 0.5 * rs};
+    T R[4] = {rs, T(0.0), T(0.0), T(0.0)};
+    T q[4] = {0.5 * rs, T(0.0), T(0.0), 0.5 * rs};
     for (int j = 1; j < k; ++j) {
-        const double sRp = sR[j - 1], scj = sc[j - 1], sRj = sR[j];
-        const double Mr = sqrt(sRp);
-        double qs[4];
+        const T sRp = sR[j - 1], scj = sc[j - 1], sRj = sR[j];
+        const T Mr = sqrt(sRp);
+        T qs[4];
         ch_boost_to_rest(q, R, Mr, qs);
-        const double qabs = sqrt(qs[1] * qs[1] + qs[2] * qs[2] + qs[3] * qs[3]);
-        const double q2 = q[0] * q[0] - q[1] * q[1] - q[2] * q[2] - q[3] * q[3];
-        const double Ec = (sRp + scj - sRj) / (2.0 * Mr);
-        const double pc = ch_sqrt_lambda(sRp, scj, sRj) / (2.0 * Mr);
-        const double A = ch_m2(c[MF_CH_TMASS + j - 1], masses) + t0 - q2 - scj + 2.0 * qs[0] * Ec;
-        const double B = 2.0 * qabs * pc;
-        const double uc = u[col++];
-        double cth, inv_h;
+        const T qabs = sqrt(qs[1] * qs[1] + qs[2] * qs[2] + qs[3] * qs[3]);
+        const T q2 = q[0] * q[0] - q[1] * q[1] - q[2] * q[2] - q[3] * q[3];
+        const T Ec = (sRp + scj - sRj) / (2.0 * Mr);
+        const T pc = ch_sqrt_lambda(sRp, scj, sRj) / (2.0 * Mr);
+        const T A = ch_m2(c[MF_CH_TMASS + j - 1], masses) + t0 - q2 - scj + 2.0 * qs[0] * Ec;
+        const T B = 2.0 * qabs * pc;
+        const T uc = u[col++];
+        T cth, inv_h;
         if (B > 0.0 && A - B > 0.0) {
-            const double L = log1p(2.0 * B / (A - B));
-            cth = -1.0 - (A + B) * expm1(-uc * L) / B;
-            cth = cth < -1.0 ? -1.0 : (cth > 1.0 ? 1.0 : cth);
+            const T L = log1p(2.0 * B / (A - B));
+            cth = -1.0 - (A + B) * expm1(-(uc * L)) / B;
+            cth = cth < -1.0 ? T(-1.0) : (cth > 1.0 ? T(1.0) : cth);
             inv_h = (A - B * cth) * L / B;
         } else {
             cth = 2.0 * uc - 1.0;
-            cth = cth < -1.0 ? -1.0 : (cth > 1.0 ? 1.0 : cth);
-            inv_h = 2.0;
+            cth = cth < -1.0 ? T(-1.0) : (cth > 1.0 ? T(1.0) : cth);
+            inv_h = T(2.0);
         }
-        const double phi = two_pi * u[col++];
+        const T phi = two_pi * u[col++];
         // axis frame R_z(phi_q) R_y(theta_q) of the direction of q
-        double hx = 0.0, hy = 0.0, hz = 1.0;
+        T hx = T(0.0), hy = T(0.0), hz = T(1.0);
         if (qabs > 0.0) {
             hx = qs[1] / qabs;
             hy = qs[2] / qabs;
             hz = qs[3] / qabs;
         }
-        const double rho = sqrt(hx * hx + hy * hy);
-        double cq = 1.0, sq = 0.0;
+        const T rho = sqrt(hx * hx + hy * hy);
+        T cq = T(1.0), sq = T(0.0);
         if (rho > 0.0) {
             cq = hx / rho;
             sq = hy / rho;
         }
-        double nl[3], n[3];
+        T nl[3], n[3];
         ch_direction(cth, phi, nl);
-        const double vx = hz * nl[0] + rho * nl[2];
-        const double vy = nl[1];
-        const double vz = -rho * nl[0] + hz * nl[2];
+        const T vx = hz * nl[0] + rho * nl[2];
+        const T vy = nl[1];
+        const T vz = hz * nl[2] - rho * nl[0];
         n[0] = cq * vx - sq * vy;
         n[1] = sq * vx + cq * vy;
         n[2] = vz;
-        double Rn[4];
-        const double lam = ch_two_body(R, sRp, scj, sRj, n, mom[j - 1], Rn);
-        ig *= lam / (pi2_32 * sRp) * two_pi * inv_h;
+        T Rn[4];
+        const T lam = ch_two_body(R, sRp, scj, sRj, n, mom[j - 1], Rn);
+        ig = ig * (lam / (pi2_32 * sRp) * two_pi * inv_h);
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-            q[a] -= mom[j - 1][a];
+            q[a] = q[a] - mom[j - 1][a];
             R[a] = Rn[a];
         }
     }
@@ -267,7 +275,7 @@ MF_CH_FN bool channel_generate(const int32_t *tab, int ch, const double *u, doub
     for (int a = 0; a < 4; ++a) mom[k - 1][a] = R[a];
     // (iv) inside the clusters, nodes in pre-order
     const int nn = c[MF_CH_NNODE];
-    double ns[NOUT], nmom[NOUT][4];
+    T ns[NOUT], nmom[NOUT][4];
     for (int j = 0; j < k; ++j) {
         const int node = c[MF_CH_CNODE + j];
         if (node < 0) {
@@ -285,43 +293,43 @@ MF_CH_FN bool channel_generate(const int32_t *tab, int ch, const double *u, doub
         const int left = nd[2], right = nd[3];
         const int lmask = left >= 0 ? c[MF_CH_NODES + MF_CH_NODE_W * left] : (1 << (-1 - left));
         const int rmask = right >= 0 ? c[MF_CH_NODES + MF_CH_NODE_W * right] : (1 << (-1 - right));
-        const double sX = ns[i];
-        double sL, sRr;
+        const T sX = ns[i];
+        T sL, sRr;
         if (left >= 0) {
-            const double m0 = ch_mmin<NOUT>(lmask, fm);
-            const double lo = m0 * m0;
-            double hi = sqrt(sX) - ch_mmin<NOUT>(rmask, fm);
-            hi = hi > 0.0 ? hi * hi : 0.0;
+            const T m0 = ch_mmin<NOUT>(lmask, fm);
+            const T lo = m0 * m0;
+            T hi = sqrt(sX) - ch_mmin<NOUT>(rmask, fm);
+            hi = hi > 0.0 ? hi * hi : T(0.0);
             ok = ok && hi >= lo;
             hi = hi > lo ? hi : lo;
-            double inv;
+            T inv;
             sL = ch_mass_sample(u[col++], lo, hi, ch_m2(c[MF_CH_NODES + MF_CH_NODE_W * left + 1], masses), s0, inv);
-            ig *= inv / two_pi;
+            ig = ig * (inv / two_pi);
         } else {
-            const double m = fm[-1 - left];
+            const T m = fm[-1 - left];
             sL = m * m;
         }
         if (right >= 0) {
-            const double m0 = ch_mmin<NOUT>(rmask, fm);
-            const double lo = m0 * m0;
-            double hi = sqrt(sX) - sqrt(sL);
-            hi = hi > 0.0 ? hi * hi : 0.0;
+            const T m0 = ch_mmin<NOUT>(rmask, fm);
+            const T lo = m0 * m0;
+            T hi = sqrt(sX) - sqrt(sL);
+            hi = hi > 0.0 ? hi * hi : T(0.0);
             ok = ok && hi >= lo;
             hi = hi > lo ? hi : lo;
-            double inv;
+            T inv;
             sRr = ch_mass_sample(u[col++], lo, hi, ch_m2(c[MF_CH_NODES + MF_CH_NODE_W * right + 1], masses), s0, inv);
-            ig *= inv / two_pi;
+            ig = ig * (inv / two_pi);
         } else {
-            const double m = fm[-1 - right];
+            const T m = fm[-1 - right];
             sRr = m * m;
         }
-        const double cth = 2.0 * u[col] - 1.0;
-        const double phi = two_pi * u[col + 1];
+        const T cth = 2.0 * u[col] - 1.0;
+        const T phi = two_pi * u[col + 1];
         col += 2;
-        double n[3], PL[4], PR[4];
+        T n[3], PL[4], PR[4];
         ch_direction(cth, phi, n);
-        const double lam = ch_two_body(nmom[i], sX, sL, sRr, n, PL, PR);
-        ig *= lam / (pi2_32 * sX) * (2.0 * two_pi);
+        const T lam = ch_two_body(nmom[i], sX, sL, sRr, n, PL, PR);
+        ig = ig * (lam / (pi2_32 * sX) * (2.0 * two_pi));
         if (left >= 0) {
             ns[left] = sL;
 #pragma unroll
@@ -345,37 +353,36 @@ MF_CH_FN bool channel_generate(const int32_t *tab, int ch, const double *u, doub
 
 // Channel ch's share a_ch = P_ch / sum_j P_j of the partition at final
 // momenta p (partonic CM frame, beam a along +z with energy rs/2).
-template <int NOUT>
-MF_CH_FN double channel_share(const int32_t *tab, int ch, double rs, const double (*p)[4], const double *masses,
-                              double s0, double t0) {
+template <int NOUT, typename T = double>
+MF_CH_FN T channel_share(const int32_t *tab, int ch, T rs, const T (*p)[4], const T *masses, double s0, double t0) {
     const int K = tab[0], E = tab[1];
-    double fac[MF_CH_MAX_EDGES];
-    const double pa[4] = {0.5 * rs, 0.0, 0.0, 0.5 * rs};
+    T fac[MF_CH_MAX_EDGES];
+    const T pa[4] = {0.5 * rs, T(0.0), T(0.0), 0.5 * rs};
     for (int e = 0; e < E; ++e) {
         const int32_t *ed = tab + MF_CH_HDR + MF_CH_EDGE * e;
         const int mask = ed[1];
-        double Q[4] = {0.0, 0.0, 0.0, 0.0};
+        T Q[4] = {T(0.0), T(0.0), T(0.0), T(0.0)};
 #pragma unroll
         for (int i = 0; i < NOUT; ++i)
             if ((mask >> i) & 1) {
 #pragma unroll
-                for (int a = 0; a < 4; ++a) Q[a] += p[i][a];
+                for (int a = 0; a < 4; ++a) Q[a] = Q[a] + p[i][a];
             }
         if (ed[0] == 1) {
 #pragma unroll
             for (int a = 0; a < 4; ++a) Q[a] = pa[a] - Q[a];
         }
-        const double x = Q[0] * Q[0] - Q[1] * Q[1] - Q[2] * Q[2] - Q[3] * Q[3];
-        const double d = fabs(x - ch_m2(ed[2], masses)) + (ed[0] == 1 ? t0 : s0);
+        const T x = Q[0] * Q[0] - Q[1] * Q[1] - Q[2] * Q[2] - Q[3] * Q[3];
+        const T d = fabs(x - ch_m2(ed[2], masses)) + (ed[0] == 1 ? t0 : s0);
         fac[e] = 1.0 / (d * d);
     }
-    double tot = 0.0, own = 0.0;
+    T tot = T(0.0), own = T(0.0);
     for (int i = 0; i < K; ++i) {
         const int32_t *c = ch_record(tab, i);
-        double P = 1.0;
+        T P = T(1.0);
         const int ne = c[MF_CH_NEDGE];
-        for (int a = 0; a < ne; ++a) P *= fac[c[MF_CH_EDGES + a]];
-        tot += P;
+        for (int a = 0; a < ne; ++a) P = P * fac[c[MF_CH_EDGES + a]];
+        tot = tot + P;
         if (i == ch) own = P;
     }
     return own / tot;

@@ -11,10 +11,12 @@ namespace mf {
 using ::atan2;
 using ::cos;
 using ::exp;
+using ::expm1;
 using ::fabs;
 using ::floor;
 using ::fmax;
 using ::log;
+using ::log1p;
 using ::pow;
 using ::sin;
 using ::sincos;
@@ -105,6 +107,8 @@ template <int K> MF_DEV Dual<K> chain(const Dual<K> &a, double f, double df) {
 template <int K> MF_DEV Dual<K> sqrt(const Dual<K> &a) { double s = ::sqrt(a.v); return chain(a, s, s > 0.0 ? 0.5 / s : 0.0); }
 template <int K> MF_DEV Dual<K> exp(const Dual<K> &a) { double e = ::exp(a.v); return chain(a, e, e); }
 template <int K> MF_DEV Dual<K> log(const Dual<K> &a) { return chain(a, ::log(a.v), 1.0 / a.v); }
+template <int K> MF_DEV Dual<K> log1p(const Dual<K> &a) { return chain(a, ::log1p(a.v), 1.0 / (1.0 + a.v)); }
+template <int K> MF_DEV Dual<K> expm1(const Dual<K> &a) { return chain(a, ::expm1(a.v), ::exp(a.v)); }
 template <int K> MF_DEV Dual<K> sin(const Dual<K> &a) { return chain(a, ::sin(a.v), ::cos(a.v)); }
 template <int K> MF_DEV Dual<K> cos(const Dual<K> &a) { return chain(a, ::cos(a.v), -::sin(a.v)); }
 template <int K> MF_DEV void sincos(const Dual<K> &a, Dual<K> *s, Dual<K> *c) {

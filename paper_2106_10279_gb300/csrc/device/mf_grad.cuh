@@ -40,7 +40,7 @@ MF_DEV void grad_body(const KParams &kp) {
             ln_tau_min = 2.0 * log(msum) - ::log(kp.S);
         }
         EventKin<D> ev;
-        const bool ok = phase_a<D>(kp, y, masses, ln_tau_min, ev);
+        const bool ok = phase_a<D>(kp, y, masses, ln_tau_min, ev, kp.channel);
         double f = 0.0, df[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) df[k] = 0.0;

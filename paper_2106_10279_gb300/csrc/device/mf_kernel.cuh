@@ -107,17 +107,11 @@ MF_DEV bool phase_a(const KParams &kp, const T *y, const T *masses, const T &ln_
     for (int i = 0; i < NOUT; ++i) mout[i] = LEG_MASS_ID[2 + i] >= 0 ? masses[LEG_MASS_ID[2 + i]] : T(0.0);
     T wfac;
     bool ok;
-    // a multichannel point (double-precision kernels; the gradient kernel
-    // always takes the flat phase space)
-    bool chan = false;
-    if constexpr (sizeof(T) == sizeof(double)) chan = channel >= 0;
+    // a multichannel point: the channel's momenta and 1/g (in the gradient
+    // kernel with their derivatives)
+    const bool chan = channel >= 0;
     if (chan) {
-        if constexpr (sizeof(T) == sizeof(double)) {
-            double inv_g;
-            ok = channel_generate<NOUT>(kp.chan, channel, u, rs, mout, kp.masses, kp.ch_s0, kp.ch_t0, pout,
-                                        inv_g);
-            wfac = inv_g;
-        }
+        ok = channel_generate<NOUT, T>(kp.chan, channel, u, rs, mout, masses, kp.ch_s0, kp.ch_t0, pout, wfac);
     } else {
         massless_diet<NOUT>(u, rs, pout);
         wfac = massive_rescale<NOUT>(pout, mout, rs);
@@ -142,8 +136,7 @@ MF_DEV bool phase_a(const KParams &kp, const T *y, const T *masses, const T &ln_
     if (!ok) return false;
     T wps;
     if (chan) {
-        if constexpr (sizeof(T) == sizeof(double))
-            wps = wfac * channel_share<NOUT>(kp.chan, channel, rs, pout, kp.masses, kp.ch_s0, kp.ch_t0);
+        wps = wfac * channel_share<NOUT, T>(kp.chan, channel, rs, pout, masses, kp.ch_s0, kp.ch_t0);
     } else {
         wps = kp.w0_const * wfac;
 #pragma unroll

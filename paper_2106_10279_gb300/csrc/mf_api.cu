@@ -1337,8 +1337,27 @@ extern "C" mf_status mf_helicity_msq(mf_process *p, const double *x, int64_t n, 
     return launch(p, prec, kp, (cudaStream_t)stream);
 }
 
+namespace {
+mf_status grad_impl(mf_process *p, int32_t channel, const double *x, int64_t n, double *f, double *df_dparam,
+                    double *df_dx, void *stream);
+}  // namespace
+
 extern "C" mf_status mf_grad(mf_process *p, const double *x, int64_t n, double *f, double *df_dparam,
                              double *df_dx, void *stream) {
+    return grad_impl(p, -1, x, n, f, df_dparam, df_dx, stream);
+}
+
+extern "C" mf_status mf_grad_channel(mf_process *p, int32_t channel, const double *x, int64_t n, double *f,
+                                     double *df_dparam, double *df_dx, void *stream) {
+    if (!p) return fail(MF_EINVAL, "NULL process");
+    if (p->channels.K == 0) return fail(MF_EUNSUPPORTED, "the process has no phase-space channels");
+    if (channel < 0 || channel >= p->channels.K) return fail(MF_EINVAL, "channel out of range");
+    return grad_impl(p, channel, x, n, f, df_dparam, df_dx, stream);
+}
+
+namespace {
+mf_status grad_impl(mf_process *p, int32_t channel, const double *x, int64_t n, double *f, double *df_dparam,
+                    double *df_dx, void *stream) {
     if (!p) return fail(MF_EINVAL, "NULL process");
     if (n < 0) return fail(MF_EINVAL, "negative n");
     if (n == 0) return MF_OK;
@@ -1356,8 +1375,10 @@ extern "C" mf_status mf_grad(mf_process *p, const double *x, int64_t n, double *
     kp.g_dx = df_dx;
     kp.variant = 0;                       // the gradient always sums the colours
     kp.colour_sample = 0;
+    kp.channel = channel;
     return launch(p, 2, kp, (cudaStream_t)stream);
 }
+}  // namespace
 
 // ----------------------------------------------------------------------------
 // Vegas

@@ -357,3 +357,33 @@ def test_channel_iteration_with_tensor_core_sum_and_colour_sampling(env):
     ec = math.sqrt(sum(r["error"] ** 2 for r in rc))
     assert all(rc[k]["n_nonzero"] == ra[k]["n_nonzero"] for k in range(K))
     assert abs(sc - sa) < 5 * math.hypot(ea, ec), (sa, ea, sc, ec)
+
+
+@pytest.mark.parametrize("name,chans,n", [("gg_ttx", (0, 1, 2), 16), ("gg_ttxg", (0, 6, 14), 8)])
+def test_channel_gradient_matches_the_oracle(env, name, chans, n):
+    # mf_grad_channel: forward tangents through the channel's map, density
+    # and partition, against the oracle's dual numbers through the same
+    torch, api = env
+    wl = W.WORKLOADS[name]
+    proc = api.Process.from_workload(wl)
+    I = _oracle(name)
+    k = proc.desc.prog.alpha_s_power
+    x = np.clip(W.uniform_points(wl.ndim, n, 57), 1e-3, 1 - 1e-3)
+    xd = torch.from_numpy(x).cuda()
+    n_nz = 0
+    for ch in chans:
+        f, dp, dx = (t.cpu().numpy() for t in proc.grad(xd, channel=ch))
+        fo, dxo, dmo = I.gradient(x, channel=ch)
+        ref, tol = fp64_tolerance(lambda y, return_parts=False: I(y, return_parts=return_parts, channel=ch), x)
+        assert np.array_equal(f == 0, fo == 0), ch
+        assert np.all(relerr(f, ref) <= tol), ch
+        nz = fo != 0
+        n_nz += int(nz.sum())
+        if not nz.any():
+            continue
+        err = np.abs(dx - dxo)[:, nz] / (np.abs(dxo) + np.abs(fo))[:, nz]
+        assert err.max() < 1e-8, (ch, err.max())
+        errm = np.abs(dp[0] - dmo)[nz] / (np.abs(dmo) + np.abs(fo) / wl.m_top)[nz]
+        assert errm.max() < 1e-8, (ch, errm.max())
+        assert np.allclose(dp[1][nz], k * f[nz] / wl.alpha_s, rtol=1e-14)
+    assert n_nz >= n

@@ -278,3 +278,29 @@ def test_neyman_allocation_by_hand():
     assert C.allocate([2.0], 4096, 4096) == [4096]
     with pytest.raises(ValueError):
         C.allocate([1.0, 1.0], 10, 8)
+
+
+def test_channel_gradient_matches_central_differences():
+    # the oracle's dual-number derivative of a channel's integrand with
+    # respect to the unit numbers and the top mass, against central
+    # differences (gg -> tt~ has no cuts: the integrand is smooth)
+    wl = W.WORKLOADS["gg_ttx"]
+    I = Integrand(wl)
+    I.use_channels(R0, R0)
+    x = 0.1 + 0.8 * W.uniform_points(wl.ndim, 5, 3)
+    h = 1e-6
+    for ch in range(3):
+        f, dfdx, dfdm = I.gradient(x, channel=ch)
+        assert np.allclose(f, I(x, channel=ch), rtol=1e-13, atol=0)
+        for j in range(wl.ndim):
+            xp, xm = x.copy(), x.copy()
+            xp[j] += h
+            xm[j] -= h
+            fd = (I(xp, channel=ch) - I(xm, channel=ch)) / (2 * h)
+            assert np.allclose(dfdx[j], fd, rtol=2e-6, atol=1e-9 * np.abs(f).max()), (ch, j)
+        Ip = Integrand(wl, m_top=wl.m_top + 1e-4)
+        Im = Integrand(wl, m_top=wl.m_top - 1e-4)
+        Ip.use_channels(R0, R0)
+        Im.use_channels(R0, R0)
+        fd = (Ip(x, channel=ch) - Im(x, channel=ch)) / 2e-4
+        assert np.allclose(dfdm, fd, rtol=1e-5, atol=1e-9 * np.abs(f).max()), ch
