@@ -4,6 +4,10 @@
 //   table L t_0 .. t_{L-1}                       -> (load a channel table)
 //   gen n ch rs s0 t0 m_t fm_0..fm_{n-1} u_0..u_{3n-5}
 //                                                 -> ok 1/g share p_00 .. p_{n-1,3}
+//   gend (same arguments)                         -> ok, then 1/g, share, p_00 .. p_{n-1,3},
+//                                                    each as a value and its derivatives with
+//                                                    respect to u_0 .. u_{3n-5} and m_t
+//                                                    (the top legs' masses are m_t)
 #include <cstdint>
 #include <cstdio>
 #include <iostream>
@@ -32,6 +36,35 @@ static void gen(std::istringstream &in) {
     std::printf("\n");
 }
 
+template <int N>
+static void gend(std::istringstream &in) {
+    constexpr int K = 3 * N - 3;              // the 3N-4 unit numbers and m_t
+    using D = mf::Dual<K>;
+    int ch;
+    double rs, s0, t0, mt, fmv[N], uv[3 * N - 4];
+    in >> ch >> rs >> s0 >> t0 >> mt;
+    for (int i = 0; i < N; ++i) in >> fmv[i];
+    for (int i = 0; i < 3 * N - 4; ++i) in >> uv[i];
+    D u[3 * N - 4], fm[N], p[N][4];
+    for (int i = 0; i < 3 * N - 4; ++i) u[i] = D::seed(uv[i], i);
+    const D m = D::seed(mt, K - 1);
+    for (int i = 0; i < N; ++i) fm[i] = fmv[i] > 0.0 ? m : D(0.0);
+    const D masses[1] = {m};
+    D inv_g(0.0);
+    const bool ok = mf::channel_generate<N, D>(g_table.data(), ch, u, D(rs), fm, masses, s0, t0, p, inv_g);
+    const D share = mf::channel_share<N, D>(g_table.data(), ch, D(rs), p, masses, s0, t0);
+    auto put = [](const D &x) {
+        std::printf(" %.17g", x.v);
+        for (int k = 0; k < K; ++k) std::printf(" %.17g", x.d[k]);
+    };
+    std::printf("%d", ok ? 1 : 0);
+    put(inv_g);
+    put(share);
+    for (int i = 0; i < N; ++i)
+        for (int q = 0; q < 4; ++q) put(p[i][q]);
+    std::printf("\n");
+}
+
 int main() {
     std::string line;
     while (std::getline(std::cin, line)) {
@@ -43,6 +76,15 @@ int main() {
             in >> n;
             g_table.assign(n, 0);
             for (int i = 0; i < n; ++i) in >> g_table[i];
+        } else if (cmd == "gend") {
+            int n;
+            in >> n;
+            switch (n) {
+                case 2: gend<2>(in); break;
+                case 3: gend<3>(in); break;
+                case 4: gend<4>(in); break;
+                default: std::printf("bad n\n");
+            }
         } else if (cmd == "gen") {
             int n;
             in >> n;

@@ -8,6 +8,9 @@
   momenta, 1/g and partition share for the same unit numbers, channel by
   channel (relative 1e-12; shares and weights of points where the oracle
   flags an empty range are not compared, there are none at these sizes);
+* the same generator and share in dual numbers (the gradient kernel's
+  instantiation): values and derivatives with respect to every unit number
+  and m_t equal the oracle's dual numbers within the same bound;
 * Neyman's allocation (mf_channels_allocate) equals the oracle's, integer
   for integer.
 """
@@ -125,3 +128,52 @@ def test_allocation_matches_the_oracle(api):
     with pytest.raises(RuntimeError):
         api.mf_channels_allocate([1.0, -1.0], 10, 1)
     assert L.MF_EINVAL != 0
+
+
+@pytest.mark.parametrize("name,n_ch", [("gg_ttx", None), ("uux_ttxg", None), ("gg_ttxg", 6), ("gg_ttxgg", 6)])
+def test_dual_generation_matches_the_oracle(api, cc, name, n_ch):
+    # the device header's channel generator and share in dual numbers (as the
+    # gradient kernel runs them), built for the host: values and derivatives
+    # with respect to every unit number and m_t against the oracle's own
+    # dual numbers through its generator and partition
+    from oracle.dual import Dual
+    wl = W.WORKLOADS[name]
+    table = api.mf_channels_table(api.descriptor_for_workload(wl))
+    chans = C.derive_channels(oracle_process(wl))
+    fm = np.array([wl.m_top if l.particle.startswith("t") else 0.0 for l in wl.legs if not l.incoming])
+    n = len(fm)
+    K = 3 * n - 3
+    rng = np.random.default_rng(19)
+    picks = range(len(chans)) if n_ch is None else sorted(rng.choice(len(chans), n_ch, replace=False))
+    lines = ["table %d %s" % (len(table), " ".join(str(int(v)) for v in table))]
+    cases = []
+    for i in picks:
+        for _ in range(3):
+            u = 0.05 + 0.9 * rng.random(3 * n - 4)
+            rs = float(600.0 + 2400.0 * rng.random())
+            lines.append("gend %d %d %s %s %s %s %s %s" % (n, i, _fmt(rs), _fmt(R0), _fmt(R0), _fmt(wl.m_top),
+                                                            " ".join(_fmt(v) for v in fm),
+                                                            " ".join(_fmt(v) for v in u)))
+            cases.append((i, u, rs))
+    out = cc(lines)
+    for (i, u, rs), row in zip(cases, out):
+        ud = np.zeros((3 * n - 4, 1, K))
+        for j in range(3 * n - 4):
+            ud[j, 0, j] = 1.0
+        U = Dual(u[:, None], ud)
+        mt = Dual(np.array(wl.m_top), np.eye(K)[K - 1])
+        fmd = [mt if m > 0 else Dual(np.array(0.0), np.zeros(K)) for m in fm]
+        rsa = np.array([rs])
+        p, inv_g, ok = C.generate(chans[i], U, rsa, fmd, R0, R0, [mt])
+        pa = np.stack([rsa / 2, 0 * rsa, 0 * rsa, rsa / 2], axis=1)
+        share = C.partition(chans, pa, p, R0, R0, [mt])[:, i]
+        assert int(row[0]) == int(ok[0])
+        vals = np.array(row[1:]).reshape(-1, K + 1)
+        ref = [inv_g[0], share[0]] + [p[0, a, q] for a in range(n) for q in range(4)]
+        for got, r in zip(vals, ref):
+            rv, rd = float(np.asarray(r.v)), np.asarray(r.d).reshape(-1)
+            scale = max(abs(rv), np.abs(rd).max(), 1e-300)
+            kappa = 2.0 * rs ** 2 / R0
+            tol = (1e-12 + 64 * EPS * kappa) * scale
+            assert abs(got[0] - rv) <= tol + 1e-12 * rs, (chans[i].key, got[0], rv)
+            assert np.max(np.abs(got[1:] - rd)) <= tol + 1e-12 * rs, (chans[i].key, np.max(np.abs(got[1:] - rd)))
